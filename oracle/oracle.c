@@ -1,0 +1,460 @@
+/*
+ * oracle.c -- plain, slow, single-threaded FP64 reference for the matrix
+ * square root of Gao, Kressner and Shao, "A mixed precision algorithm for the
+ * matrix square root" (arXiv 2607.12430).
+ *
+ * THIS IS TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load it.  The GPU library never links
+ * or calls it, and it shares no source, header, table or helper with the GPU
+ * code.
+ *
+ * Every routine follows a definition stated in the paper, written out with
+ * no blocking or reordering beyond what that definition states:
+ *
+ *   orc_hessenberg     complex Householder reduction A = Q H Q^H (first stage
+ *                      of the Schur method, Sec. 1 / Sec. 2.1).
+ *   orc_schur_qr       complex single-shift (Wilkinson) implicit QR sweeps on
+ *                      the Hessenberg form, H = Z T Z^H with T upper
+ *                      triangular (Schur decomposition, Sec. 1 / Sec. 2.1).
+ *   orc_csqrt          principal complex square root of a scalar (the
+ *                      diagonal step of Sec. 2.2.1, principal branch as in the
+ *                      definition of Sec. 1).
+ *   orc_trisqrt        point back-substitution for T^{1/2} (Sec. 2.2.1,
+ *                      Eq. (subst)).
+ *   orc_sqrtm_schur    the FP64 Schur method X = Q T^{1/2} Q^H (Sec. 1); for
+ *                      real A the real part is returned.
+ *   orc_jacobi_eig     cyclic two-sided Jacobi for symmetric A = V diag(l) V^T
+ *                      (spectral decomposition of Algorithm 3, step 1).
+ *   orc_bs_solve       point Bartels-Stewart substitution for S Y + Y St = C
+ *                      with S, St upper triangular (base case of Algorithm 1).
+ *   orc_rtrsyl         the block recursion of Algorithm 1 (Sec. 2.2.2).
+ *
+ * Storage: column-major, element (i,j) of an m-by-n array with leading
+ * dimension ld at a[i + j*ld].  Complex values use C99 double complex.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex zc;
+
+#define IDX(i, j, ld) ((size_t)(i) + (size_t)(j) * (size_t)(ld))
+
+static const double ORC_EPS = 1.1102230246251565e-16; /* 2^-53 */
+
+/* ------------------------------------------------------------------------ */
+/* Householder reduction to upper Hessenberg form.                          */
+/* For column k the reflector P = I - 2 v v^H / (v^H v), v = x + phase(x0)  */
+/* ||x|| e1, maps x = H(k+1:n, k) to a multiple of e1.  P is Hermitian and  */
+/* unitary, so H <- P H P and Q <- Q P keep A = Q H Q^H at every step.      */
+/* H (in/out, n x n, ld = ldh) starts as A; Q (out, n x n, ld = ldq).       */
+/* ------------------------------------------------------------------------ */
+void orc_hessenberg(int n, zc *H, int ldh, zc *Q, int ldq)
+{
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) Q[IDX(i, j, ldq)] = (i == j) ? 1.0 : 0.0;
+    zc *v = (zc *)malloc(sizeof(zc) * (size_t)(n > 0 ? n : 1));
+    for (int k = 0; k + 2 < n; ++k) {
+        int m = n - k - 1; /* reflector acts on rows/cols k+1 .. n-1 */
+        double xnorm2 = 0.0;
+        for (int i = 0; i < m; ++i) {
+            zc x = H[IDX(k + 1 + i, k, ldh)];
+            xnorm2 += creal(x) * creal(x) + cimag(x) * cimag(x);
+        }
+        double tail2 = 0.0;
+        for (int i = 1; i < m; ++i) {
+            zc x = H[IDX(k + 1 + i, k, ldh)];
+            tail2 += creal(x) * creal(x) + cimag(x) * cimag(x);
+        }
+        if (tail2 == 0.0) continue; /* column already a multiple of e1 */
+        double xnorm = sqrt(xnorm2);
+        zc x0 = H[IDX(k + 1, k, ldh)];
+        double ax0 = cabs(x0);
+        zc phase = (ax0 == 0.0) ? 1.0 : x0 / ax0;
+        for (int i = 0; i < m; ++i) v[i] = H[IDX(k + 1 + i, k, ldh)];
+        v[0] += phase * xnorm;
+        double vnorm2 = 0.0;
+        for (int i = 0; i < m; ++i) vnorm2 += creal(v[i]) * creal(v[i]) + cimag(v[i]) * cimag(v[i]);
+        double beta = 2.0 / vnorm2;
+        /* left: H(k+1:n, :) <- H - beta v (v^H H) */
+        for (int j = 0; j < n; ++j) {
+            zc w = 0.0;
+            for (int i = 0; i < m; ++i) w += conj(v[i]) * H[IDX(k + 1 + i, j, ldh)];
+            w *= beta;
+            for (int i = 0; i < m; ++i) H[IDX(k + 1 + i, j, ldh)] -= v[i] * w;
+        }
+        /* right: H(:, k+1:n) <- H - beta (H v) v^H */
+        for (int i = 0; i < n; ++i) {
+            zc w = 0.0;
+            for (int l = 0; l < m; ++l) w += H[IDX(i, k + 1 + l, ldh)] * v[l];
+            w *= beta;
+            for (int l = 0; l < m; ++l) H[IDX(i, k + 1 + l, ldh)] -= w * conj(v[l]);
+        }
+        /* accumulate: Q(:, k+1:n) <- Q - beta (Q v) v^H */
+        for (int i = 0; i < n; ++i) {
+            zc w = 0.0;
+            for (int l = 0; l < m; ++l) w += Q[IDX(i, k + 1 + l, ldq)] * v[l];
+            w *= beta;
+            for (int l = 0; l < m; ++l) Q[IDX(i, k + 1 + l, ldq)] -= w * conj(v[l]);
+        }
+        /* the annihilated entries are exactly zero by construction */
+        H[IDX(k + 1, k, ldh)] = -phase * xnorm;
+        for (int i = k + 2; i < n; ++i) H[IDX(i, k, ldh)] = 0.0;
+    }
+    free(v);
+}
+
+/* Complex Givens rotation G = [c s; -conj(s) c], c real, with
+ * G [x; y] = [r; 0]. */
+static void orc_givens(zc x, zc y, double *c, zc *s, zc *r)
+{
+    double ax = cabs(x), ay = cabs(y);
+    if (ay == 0.0) { *c = 1.0; *s = 0.0; *r = x; return; }
+    if (ax == 0.0) { *c = 0.0; *s = conj(y) / ay; *r = ay; return; }
+    double nrm = hypot(ax, ay);
+    zc ph = x / ax;
+    *c = ax / nrm;
+    *s = ph * conj(y) / nrm;
+    *r = ph * nrm;
+}
+
+/* rows (p, p+1) <- G rows, columns [j0, j1) */
+static void orc_rot_rows(zc *H, int ld, int p, int j0, int j1, double c, zc s)
+{
+    for (int j = j0; j < j1; ++j) {
+        zc a = H[IDX(p, j, ld)], b = H[IDX(p + 1, j, ld)];
+        H[IDX(p, j, ld)] = c * a + s * b;
+        H[IDX(p + 1, j, ld)] = -conj(s) * a + c * b;
+    }
+}
+
+/* columns (p, p+1) <- columns G^H, rows [i0, i1) */
+static void orc_rot_cols(zc *H, int ld, int p, int i0, int i1, double c, zc s)
+{
+    for (int i = i0; i < i1; ++i) {
+        zc a = H[IDX(i, p, ld)], b = H[IDX(i, p + 1, ld)];
+        H[IDX(i, p, ld)] = c * a + conj(s) * b;
+        H[IDX(i, p + 1, ld)] = -s * a + c * b;
+    }
+}
+
+/* Eigenvalue of the 2x2 block [a b; c d] closer to d (Wilkinson shift). */
+static zc orc_wilkinson(zc a, zc b, zc c, zc d)
+{
+    zc half = 0.5 * (a - d);
+    zc disc = csqrt(half * half + b * c);
+    zc m1 = d - b * c / (half + disc);
+    zc m2 = d - b * c / (half - disc);
+    /* m1, m2 are d + half -/+ disc written without cancellation; pick the
+       finite one closer to d */
+    int ok1 = isfinite(creal(m1)) && isfinite(cimag(m1));
+    int ok2 = isfinite(creal(m2)) && isfinite(cimag(m2));
+    if (ok1 && (!ok2 || cabs(m1 - d) <= cabs(m2 - d))) return m1;
+    if (ok2) return m2;
+    return d;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Complex Schur form by single-shift implicit QR sweeps on the Hessenberg  */
+/* matrix H (in: Hessenberg, out: upper triangular T).  Z (in/out) is       */
+/* right-multiplied by every rotation, so if A = Z H Z^H on entry then      */
+/* A = Z T Z^H on exit.  A subdiagonal entry is set to zero when            */
+/* |h(k,k-1)| <= eps (|h(k,k)| + |h(k-1,k-1)|).  Returns 0, or 3 when       */
+/* an eigenvalue needs more than 60 sweeps.                                 */
+/* ------------------------------------------------------------------------ */
+int orc_schur_qr(int n, zc *H, int ldh, zc *Z, int ldz)
+{
+    int hi = n - 1;
+    int iter = 0;
+    while (hi > 0) {
+        /* find the active block [lo, hi] */
+        int lo = hi;
+        while (lo > 0) {
+            double sub = cabs(H[IDX(lo, lo - 1, ldh)]);
+            double dsum = cabs(H[IDX(lo, lo, ldh)]) + cabs(H[IDX(lo - 1, lo - 1, ldh)]);
+            if (sub <= ORC_EPS * dsum || sub == 0.0) {
+                H[IDX(lo, lo - 1, ldh)] = 0.0;
+                break;
+            }
+            --lo;
+        }
+        if (lo == hi) { /* 1x1 block deflated */
+            --hi;
+            iter = 0;
+            continue;
+        }
+        if (++iter > 60) return 3;
+        zc mu;
+        if (iter % 10 == 0) {
+            /* exceptional shift after a run of sweeps without deflation */
+            mu = H[IDX(hi, hi, ldh)] + 0.75 * cabs(H[IDX(hi, hi - 1, ldh)]);
+        } else {
+            mu = orc_wilkinson(H[IDX(hi - 1, hi - 1, ldh)], H[IDX(hi - 1, hi, ldh)],
+                               H[IDX(hi, hi - 1, ldh)], H[IDX(hi, hi, ldh)]);
+        }
+        /* first rotation from the shifted first column */
+        double c; zc s, r;
+        orc_givens(H[IDX(lo, lo, ldh)] - mu, H[IDX(lo + 1, lo, ldh)], &c, &s, &r);
+        for (int k = lo; k < hi; ++k) {
+            if (k > lo) {
+                orc_givens(H[IDX(k, k - 1, ldh)], H[IDX(k + 1, k - 1, ldh)], &c, &s, &r);
+            }
+            int j0 = (k > lo) ? k - 1 : k;
+            orc_rot_rows(H, ldh, k, j0, n, c, s);
+            if (k > lo) H[IDX(k + 1, k - 1, ldh)] = 0.0; /* bulge annihilated */
+            int i1 = (k + 2 < hi) ? k + 2 : hi;
+            orc_rot_cols(H, ldh, k, 0, i1 + 1, c, s);
+            orc_rot_cols(Z, ldz, k, 0, n, c, s);
+        }
+    }
+    /* strictly lower part is zero in exact arithmetic; make it explicit */
+    for (int j = 0; j < n; ++j)
+        for (int i = j + 1; i < n; ++i) H[IDX(i, j, ldh)] = 0.0;
+    return 0;
+}
+
+/* Principal square root of z (real part > 0 unless z is on the branch cut),
+ * from sqrt(z) = t + i y/(2t), t = sqrt((|x| + |z|)/2) when x >= 0, and the
+ * mirrored form |y|/(2t) + i sign(y) t when x < 0 (no cancellation). */
+zc orc_csqrt(zc z)
+{
+    double x = creal(z), y = cimag(z);
+    if (x == 0.0 && y == 0.0) return 0.0;
+    double t = sqrt(0.5 * (fabs(x) + cabs(z)));
+    if (x >= 0.0) return t + I * (y / (2.0 * t));
+    return fabs(y) / (2.0 * t) + I * copysign(t, y);
+}
+
+/* ------------------------------------------------------------------------ */
+/* S = T^{1/2} for upper triangular T (Sec. 2.2.1, Eq. (subst)):            */
+/*   s_jj = sqrt(t_jj);                                                      */
+/*   for j = 2..n, i = j-1 down to 1:                                        */
+/*     s_ij = (t_ij - sum_{k=i+1}^{j-1} s_ik s_kj) / (s_ii + s_jj).          */
+/* Returns 0, or 2 when some s_ii + s_jj is exactly zero.                    */
+/* ------------------------------------------------------------------------ */
+int orc_trisqrt(int n, const zc *T, int ldt, zc *S, int lds)
+{
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) S[IDX(i, j, lds)] = 0.0;
+    for (int j = 0; j < n; ++j) S[IDX(j, j, lds)] = orc_csqrt(T[IDX(j, j, ldt)]);
+    for (int j = 1; j < n; ++j) {
+        for (int i = j - 1; i >= 0; --i) {
+            zc acc = T[IDX(i, j, ldt)];
+            for (int k = i + 1; k < j; ++k) acc -= S[IDX(i, k, lds)] * S[IDX(k, j, lds)];
+            zc den = S[IDX(i, i, lds)] + S[IDX(j, j, lds)];
+            if (den == 0.0) return 2;
+            S[IDX(i, j, lds)] = acc / den;
+        }
+    }
+    return 0;
+}
+
+/* C = alpha * op(A) * op(B) + beta * C, all n x n complex; op = 'N', 'C'
+ * (conjugate transpose).  Plain triple loop. */
+static void orc_zgemm(char ta, char tb, int n, zc alpha, const zc *A, int lda, const zc *B,
+                      int ldb, zc beta, zc *C, int ldc)
+{
+    zc *col = (zc *)malloc(sizeof(zc) * (size_t)n);
+    for (int j = 0; j < n; ++j) {
+        for (int i = 0; i < n; ++i) {
+            zc acc = 0.0;
+            for (int k = 0; k < n; ++k) {
+                zc a = (ta == 'N') ? A[IDX(i, k, lda)] : conj(A[IDX(k, i, lda)]);
+                zc b = (tb == 'N') ? B[IDX(k, j, ldb)] : conj(B[IDX(j, k, ldb)]);
+                acc += a * b;
+            }
+            col[i] = acc;
+        }
+        for (int i = 0; i < n; ++i)
+            C[IDX(i, j, ldc)] = alpha * col[i] + (beta == 0.0 ? 0.0 : beta * C[IDX(i, j, ldc)]);
+    }
+    free(col);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Complex Schur decomposition of a real matrix, A = Q T Q^H (Sec. 1):      */
+/* Householder Hessenberg reduction followed by single-shift QR sweeps.    */
+/* A real n x n (lda); Q, T complex n x n with ld = n.  Returns 0 or 3.     */
+/* ------------------------------------------------------------------------ */
+int orc_schur(int n, const double *A, int lda, zc *Q, zc *T)
+{
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) T[IDX(i, j, n)] = A[IDX(i, j, lda)];
+    orc_hessenberg(n, T, n, Q, n);
+    return orc_schur_qr(n, T, n, Q, n);
+}
+
+/* ------------------------------------------------------------------------ */
+/* The FP64 Schur method for the principal square root (Sec. 1):            */
+/*   A = Q T Q^H, S = T^{1/2} by Eq. (subst), X = Q S Q^H.                  */
+/* A: real n x n (lda), X: real part of the result (ldx).  Optional outputs  */
+/* (may be NULL): Qout, Tout, Sout complex n x n with ld = n.                */
+/* Returns 0, 2 (an eigenvalue on the closed negative real axis, or         */
+/* s_ii + s_jj = 0) or 3 (QR iteration cap).                                 */
+/* ------------------------------------------------------------------------ */
+int orc_sqrtm_schur(int n, const double *A, int lda, double *X, int ldx, zc *Qout, zc *Tout,
+                    zc *Sout)
+{
+    size_t nn = (size_t)n * (size_t)n;
+    if (nn == 0) nn = 1;
+    zc *T = (zc *)calloc(nn, sizeof(zc));
+    zc *Q = (zc *)calloc(nn, sizeof(zc));
+    zc *S = (zc *)calloc(nn, sizeof(zc));
+    zc *W = (zc *)calloc(nn, sizeof(zc));
+    zc *P = (zc *)calloc(nn, sizeof(zc));
+    int st = orc_schur(n, A, lda, Q, T);
+    if (st == 0) {
+        for (int i = 0; i < n; ++i) {
+            zc t = T[IDX(i, i, n)];
+            if (creal(t) <= 0.0 && cimag(t) == 0.0) st = 2;
+        }
+    }
+    if (st == 0) st = orc_trisqrt(n, T, n, S, n);
+    if (st == 0) {
+        orc_zgemm('N', 'N', n, 1.0, Q, n, S, n, 0.0, W, n);
+        orc_zgemm('N', 'C', n, 1.0, W, n, Q, n, 0.0, P, n); /* P = Q S Q^H */
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) X[IDX(i, j, ldx)] = creal(P[IDX(i, j, n)]);
+    }
+    if (Qout) memcpy(Qout, Q, sizeof(zc) * (size_t)n * (size_t)n);
+    if (Tout) memcpy(Tout, T, sizeof(zc) * (size_t)n * (size_t)n);
+    if (Sout) memcpy(Sout, S, sizeof(zc) * (size_t)n * (size_t)n);
+    free(T); free(Q); free(S); free(W); free(P);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cyclic two-sided Jacobi for real symmetric A = V diag(lam) V^T.          */
+/* A (in, destroyed), V (out, orthogonal), lam (out, unsorted).             */
+/* Each rotation zeroes a_pq with t = sign(tau)/(|tau| + sqrt(1 + tau^2)),  */
+/* tau = (a_qq - a_pp) / (2 a_pq).  Stops when the off-diagonal Frobenius   */
+/* norm is <= eps * ||A||_F.  Returns 0, or 3 after 100 sweeps.             */
+/* ------------------------------------------------------------------------ */
+int orc_jacobi_eig(int n, double *A, int lda, double *V, int ldv, double *lam)
+{
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) V[IDX(i, j, ldv)] = (i == j) ? 1.0 : 0.0;
+    double fro2 = 0.0;
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) fro2 += A[IDX(i, j, lda)] * A[IDX(i, j, lda)];
+    int st = 3;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off2 = 0.0;
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i)
+                if (i != j) off2 += A[IDX(i, j, lda)] * A[IDX(i, j, lda)];
+        if (off2 <= ORC_EPS * ORC_EPS * fro2) { st = 0; break; }
+        for (int p = 0; p < n - 1; ++p) {
+            for (int q = p + 1; q < n; ++q) {
+                double apq = A[IDX(p, q, lda)];
+                if (apq == 0.0) continue;
+                double tau = (A[IDX(q, q, lda)] - A[IDX(p, p, lda)]) / (2.0 * apq);
+                double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+                /* A <- J^T A J with J = [c s; -s c] acting on (p, q) */
+                for (int k = 0; k < n; ++k) {
+                    double akp = A[IDX(k, p, lda)], akq = A[IDX(k, q, lda)];
+                    A[IDX(k, p, lda)] = c * akp - s * akq;
+                    A[IDX(k, q, lda)] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double apk = A[IDX(p, k, lda)], aqk = A[IDX(q, k, lda)];
+                    A[IDX(p, k, lda)] = c * apk - s * aqk;
+                    A[IDX(q, k, lda)] = s * apk + c * aqk;
+                }
+                A[IDX(p, q, lda)] = 0.0;
+                A[IDX(q, p, lda)] = 0.0;
+                for (int k = 0; k < n; ++k) {
+                    double vkp = V[IDX(k, p, ldv)], vkq = V[IDX(k, q, ldv)];
+                    V[IDX(k, p, ldv)] = c * vkp - s * vkq;
+                    V[IDX(k, q, ldv)] = s * vkp + c * vkq;
+                }
+            }
+        }
+    }
+    for (int i = 0; i < n; ++i) lam[i] = A[IDX(i, i, lda)];
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Point Bartels-Stewart substitution for S Y + Y St = C, with S (m x m)    */
+/* and St (n x n) upper triangular (base case of Algorithm 1):               */
+/*   y_ij = (c_ij - sum_{k>i} s_ik y_kj - sum_{k<j} y_ik st_kj)              */
+/*          / (s_ii + st_jj),                                                */
+/* columns left to right, rows bottom to top.  C is overwritten by Y.       */
+/* Returns 0, or 2 when a denominator is exactly zero.                      */
+/* ------------------------------------------------------------------------ */
+int orc_bs_solve(int m, int n, const zc *S, int lds, const zc *St, int ldst, zc *C, int ldc)
+{
+    for (int j = 0; j < n; ++j) {
+        for (int i = m - 1; i >= 0; --i) {
+            zc acc = C[IDX(i, j, ldc)];
+            for (int k = i + 1; k < m; ++k) acc -= S[IDX(i, k, lds)] * C[IDX(k, j, ldc)];
+            for (int k = 0; k < j; ++k) acc -= C[IDX(i, k, ldc)] * St[IDX(k, j, ldst)];
+            zc den = S[IDX(i, i, lds)] + St[IDX(j, j, ldst)];
+            if (den == 0.0) return 2;
+            C[IDX(i, j, ldc)] = acc / den;
+        }
+    }
+    return 0;
+}
+
+/* C(m x n) -= A(m x k) * B(k x n), plain loops */
+static void orc_gemm_sub(int m, int n, int k, const zc *A, int lda, const zc *B, int ldb, zc *C,
+                         int ldc)
+{
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < m; ++i) {
+            zc acc = 0.0;
+            for (int l = 0; l < k; ++l) acc += A[IDX(i, l, lda)] * B[IDX(l, j, ldb)];
+            C[IDX(i, j, ldc)] -= acc;
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1, Y = rtrsyl(S, St, C, blks): recursive blocked solve of      */
+/* S Y + Y St = C with S (m x m) and St (n x n) upper triangular.  The      */
+/* right-hand side (written C in the algorithm's body, R in its header) is  */
+/* overwritten with Y.  Split point: first block of size ceil(size/2).      */
+/* Returns 0 or 2.                                                           */
+/* ------------------------------------------------------------------------ */
+int orc_rtrsyl(int m, int n, const zc *S, int lds, const zc *St, int ldst, zc *C, int ldc,
+               int blks)
+{
+    if (m <= 0 || n <= 0) return 0;
+    if (m <= blks && n <= blks) return orc_bs_solve(m, n, S, lds, St, ldst, C, ldc);
+    int st;
+    if (n <= m / 2) {
+        /* split rows only: S = [S11 S12; 0 S22], C = [C1; C2] */
+        int m1 = (m + 1) / 2, m2 = m - m1;
+        const zc *S12 = S + IDX(0, m1, lds), *S22 = S + IDX(m1, m1, lds);
+        zc *C1 = C, *C2 = C + IDX(m1, 0, ldc);
+        if ((st = orc_rtrsyl(m2, n, S22, lds, St, ldst, C2, ldc, blks))) return st;
+        orc_gemm_sub(m1, n, m2, S12, lds, C2, ldc, C1, ldc);
+        return orc_rtrsyl(m1, n, S, lds, St, ldst, C1, ldc, blks);
+    }
+    if (m <= n / 2) {
+        /* split columns only: St = [St11 St12; 0 St22], C = [C1 C2] */
+        int n1 = (n + 1) / 2, n2 = n - n1;
+        const zc *St12 = St + IDX(0, n1, ldst), *St22 = St + IDX(n1, n1, ldst);
+        zc *C1 = C, *C2 = C + IDX(0, n1, ldc);
+        if ((st = orc_rtrsyl(m, n1, S, lds, St, ldst, C1, ldc, blks))) return st;
+        orc_gemm_sub(m, n2, n1, C1, ldc, St12, ldst, C2, ldc);
+        return orc_rtrsyl(m, n2, S, lds, St22, ldst, C2, ldc, blks);
+    }
+    /* four-way split */
+    int m1 = (m + 1) / 2, m2 = m - m1, n1 = (n + 1) / 2, n2 = n - n1;
+    const zc *S12 = S + IDX(0, m1, lds), *S22 = S + IDX(m1, m1, lds);
+    const zc *St12 = St + IDX(0, n1, ldst), *St22 = St + IDX(n1, n1, ldst);
+    zc *C11 = C, *C21 = C + IDX(m1, 0, ldc), *C12 = C + IDX(0, n1, ldc),
+       *C22 = C + IDX(m1, n1, ldc);
+    if ((st = orc_rtrsyl(m2, n1, S22, lds, St, ldst, C21, ldc, blks))) return st;
+    orc_gemm_sub(m1, n1, m2, S12, lds, C21, ldc, C11, ldc);
+    orc_gemm_sub(m2, n2, n1, C21, ldc, St12, ldst, C22, ldc);
+    if ((st = orc_rtrsyl(m1, n1, S, lds, St, ldst, C11, ldc, blks))) return st;
+    if ((st = orc_rtrsyl(m2, n2, S22, lds, St22, ldst, C22, ldc, blks))) return st;
+    orc_gemm_sub(m1, n2, m2, S12, lds, C22, ldc, C12, ldc);
+    orc_gemm_sub(m1, n2, n1, C11, ldc, St12, ldst, C12, ldc);
+    return orc_rtrsyl(m1, n2, S, lds, St22, ldst, C12, ldc, blks);
+}
