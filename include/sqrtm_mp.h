@@ -1,0 +1,163 @@
+/*
+ * sqrtm_mp.h -- C ABI of a GB300 (sm_103a) library for the principal matrix
+ * square root by the mixed-precision method of Gao, Kressner and Shao,
+ * "A mixed precision algorithm for the matrix square root" (arXiv 2607.12430).
+ *
+ * The principal square root X of A (no eigenvalue on the closed negative real
+ * axis) is the unique X with X^2 = A and every eigenvalue of X in the open
+ * right half plane (Sec. 1).
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are real, FP64, column-major: element (i, j) of a matrix with
+ *     leading dimension ld sits at p[i + j*ld]; ld >= max(1, n).
+ *   - Matrix pointers are DEVICE pointers into caller-owned memory unless an
+ *     argument says otherwise.  The library never frees or keeps caller
+ *     buffers beyond the call.  Input and output buffers must not overlap.
+ *   - Work is enqueued on the handle's stream.  A call returns after its work
+ *     is complete on that stream (the convergence test of the refinement
+ *     loop reads one scalar back to the host each step), so outputs and the
+ *     info struct are valid on return.
+ *   - All scratch memory (workspace, saved factors) belongs to the handle and
+ *     grows on demand with cudaMalloc; sqrtm_destroy releases it.
+ *   - One handle serves one host thread at a time.
+ *
+ * Return values (LAPACK-style INFO):
+ *    0  success
+ *   -i  argument i is invalid (1-based position in the call)
+ *    1  the refinement loop did not reach the tolerance within maxit steps;
+ *       X holds the last iterate
+ *    2  an eigenvalue lies on or next to the closed negative real axis, or a
+ *       Sylvester denominator s_ii + s_jj vanished (Sec. 1, Sec. 2.1)
+ *    3  the Schur QR iteration (or the eigensolver) hit its iteration cap
+ *    4  the refinement diverged (the residual grew twice in a row)
+ *    5  the input holds NaN or Inf
+ *    6  a device-side bounded wait gave up
+ *    7  CUDA error or allocation failure
+ *    8  no factors saved on the handle (sqrtm_backward before a forward call)
+ */
+#ifndef SQRTM_MP_H
+#define SQRTM_MP_H
+
+#include <stdint.h>
+
+/* Exported symbols: the library is built with hidden default visibility. */
+#if defined(__GNUC__)
+#define SQRTM_API __attribute__((visibility("default")))
+#else
+#define SQRTM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sqrtm_handle_s *sqrtm_handle_t;
+
+/* Matrix kind: AUTO takes the symmetric positive definite path (Algorithm 3)
+ * when A is bitwise symmetric, the general path (Algorithm 2) otherwise. */
+enum { SQRTM_KIND_AUTO = 0, SQRTM_KIND_GENERAL = 1, SQRTM_KIND_SPD = 2 };
+
+/* Precision of the low-precision dense products (transforms of Algorithm 2/3
+ * steps 3, 8 and 10 and the GEMM updates inside the Sylvester and triangular
+ * square root solvers).  FP32 is IEEE single on the CUDA cores; TF32X3 is a
+ * three-term split-TF32 product on the tensor cores with FP32 accumulation
+ * (error comparable to FP32). */
+enum { SQRTM_PREC_FP32 = 0, SQRTM_PREC_TF32X3 = 1 };
+
+typedef struct {
+    double tol;      /* stop when ||A - X^2||_F <= tol ||A||_F (Algorithm 2,
+                        step 6); default 1e-12 (Sec. 5) */
+    int maxit;       /* refinement loop runs k = 0..maxit (Algorithm 2, step
+                        4); default 10 */
+    int blks;        /* block size of the Sylvester and triangular square
+                        root solvers (Algorithm 1); default 32 (Sec. 5) */
+    int kind;        /* SQRTM_KIND_* */
+    int precision;   /* SQRTM_PREC_* */
+    int steps;       /* >= 0: apply exactly this many corrections with the
+                        stopping test nullified (the accuracy-run protocol of
+                        Sec. 5.1); -1 (default): use tol / maxit */
+} sqrtm_opts;
+
+#define SQRTM_MAX_HISTORY 64
+
+typedef struct {
+    int status;          /* same code as the return value */
+    int kind_used;       /* SQRTM_KIND_GENERAL or SQRTM_KIND_SPD */
+    int iterations;      /* corrections applied */
+    int scale_exponent;  /* e with A_s = 4^-e A, X = 2^e sqrt(A_s) */
+    double norm_a;       /* ||A||_F */
+    /* relative residual ||A - X_k^2||_F / ||A||_F before correction k
+       (entry k), and after the last correction when it was evaluated */
+    int history_len;
+    double history[SQRTM_MAX_HISTORY];
+    /* wall time of the phases in milliseconds, from CUDA events on the
+       handle's stream: Schur / spectral decomposition, triangular square root
+       plus X0, refinement loop */
+    double ms_schur, ms_trisqrt, ms_refine;
+    /* of ms_schur: the Hessenberg (or tridiagonal) reduction alone */
+    double ms_reduction;
+    /* QR sweeps and Givens rotations of the Schur iteration (general path) */
+    int schur_sweeps;
+    int64_t schur_rotations;
+} sqrtm_info;
+
+/* Create a handle bound to a CUDA stream (cudaStream_t passed as void*;
+ * NULL = legacy default stream).  Returns 0 or 7. */
+SQRTM_API int sqrtm_create(sqrtm_handle_t *handle, void *stream);
+
+/* Release the handle and all device memory it owns.  Returns 0. */
+SQRTM_API int sqrtm_destroy(sqrtm_handle_t handle);
+
+/* Rebind the handle to another stream. */
+SQRTM_API int sqrtm_set_stream(sqrtm_handle_t handle, void *stream);
+
+/* Fill opts with the defaults listed above. */
+SQRTM_API void sqrtm_default_opts(sqrtm_opts *opts);
+
+/* Mixed-precision principal square root, Algorithm 2 (general A) or
+ * Algorithm 3 (symmetric positive definite A):
+ *   Schur / spectral decomposition A = Q T Q^H in FP32, S = T^{1/2} in FP32
+ *   (blocked, Sec. 2.2.1), X_0 = Q S Q^H rounded to FP32, then refinement
+ *   X_{k+1} = X_k + Q Y Q^H with S Y + Y S = Q^H (A - X_k^2) Q, residual and
+ *   update in FP64, transforms and Sylvester solve in low precision.
+ * dA: n x n input (lda); dX: n x n output (ldx).  tol overrides opts->tol when
+ * opts is NULL (defaults otherwise).  opts and info may be NULL.  The Schur
+ * factors are kept on the handle for a following sqrtm_backward. */
+SQRTM_API int sqrtm_mixed(sqrtm_handle_t handle, const double *dA, int64_t n, int64_t lda, double tol,
+                double *dX, int64_t ldx, const sqrtm_opts *opts, sqrtm_info *info);
+
+/* Plain FP64 Schur method (Sec. 1): A = Q T Q^H, S = T^{1/2}, X = Q S Q^H,
+ * all in FP64 on the GPU, no refinement.  tol is accepted for a uniform
+ * signature and ignored.  The same kernels as sqrtm_mixed, instantiated in
+ * FP64. */
+SQRTM_API int sqrtm_schur_fp64(sqrtm_handle_t handle, const double *dA, int64_t n, int64_t lda,
+                     double tol, double *dX, int64_t ldx, const sqrtm_opts *opts,
+                     sqrtm_info *info);
+
+/* Adjoint of the square root at the last sqrtm_mixed call on this handle:
+ * given a cotangent Gbar (n x n, ldg), returns the gradient of <Gbar, X> with
+ * respect to A, i.e. the solution Y (ldy) of X^T Y + Y X^T = Gbar.  Uses the
+ * saved low-precision factors (X = Q S Q^H) for the correction solves
+ * (Eq. (triangsylv) with the transposed operator) and refines with FP64
+ * residuals Gbar - X^T Y - Y X^T until the relative residual is <= tol.
+ * Returns 8 when no forward factors are stored. */
+SQRTM_API int sqrtm_backward(sqrtm_handle_t handle, const double *dGbar, int64_t n, int64_t ldg,
+                   double tol, double *dY, int64_t ldy, sqrtm_info *info);
+
+/* Batched mixed-precision square roots of independent matrices of varying
+ * sizes.  dA, dX: HOST arrays of `batch` device pointers; n, lda, ldx: HOST
+ * arrays of sizes.  status: HOST array of `batch` ints receiving each
+ * matrix's code.  opts may be NULL.  Returns the first nonzero code, else 0. */
+SQRTM_API int sqrtm_mixed_batched(sqrtm_handle_t handle, int batch, const double *const *dA,
+                        const int64_t *n, const int64_t *lda, double tol,
+                        double *const *dX, const int64_t *ldx, const sqrtm_opts *opts,
+                        int *status);
+
+/* Human-readable text for a status code (static storage). */
+SQRTM_API const char *sqrtm_status_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SQRTM_MP_H */

@@ -1,0 +1,94 @@
+/*
+ * sqrtm_mp_steps.h -- the individual steps of the mixed-precision matrix
+ * square root (arXiv 2607.12430, Algorithms 1-3), each exposed on raw device
+ * pointers so that it can be checked and timed on its own.  sqrtm_mixed
+ * (sqrtm_mp.h) chains exactly these kernels.
+ *
+ * Layouts: column-major.  "c64" arrays are interleaved complex FP32
+ * (re, im) pairs, "c128" interleaved complex FP64; real arrays are float or
+ * double as named.  Square low-precision work arrays use leading dimension
+ * n.  `fp64` selects the FP64 instantiation of a step (complex128 / double
+ * storage) instead of the low-precision one (complex64 / float).
+ * All pointers are device pointers unless named *_host.  Work runs on the
+ * handle's stream; calls that return a scalar synchronise the stream.
+ * Return values use the codes of sqrtm_mp.h.
+ */
+#ifndef SQRTM_MP_STEPS_H
+#define SQRTM_MP_STEPS_H
+
+#include <stdint.h>
+#include "sqrtm_mp.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Scaling before the cast to low precision (Sec. 5 asks for an overflow-safe
+ * scaling without fixing one): e with ||A||_F / sqrt(n) = m 2^p, m in
+ * [1/2, 1), e = ceil(p/2); A_s = 4^-e A, stored as complex (imaginary part
+ * 0) in dAs (n x n, ld n; c64, or c128 when fp64).  *e_host receives e,
+ * *norm_host ||A||_F. */
+SQRTM_API int sqrtm_step_scale(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, void *dAs,
+                     int fp64, int *e_host, double *norm_host);
+
+/* Complex Schur decomposition (Algorithm 2, step 1): dT (in: A_s, out: T
+ * upper triangular) and dQ (out: unitary) with A_s = Q T Q^H: Householder
+ * Hessenberg reduction, then single-shift QR sweeps.  Returns 0 or 3. */
+SQRTM_API int sqrtm_step_schur(sqrtm_handle_t h, void *dT, void *dQ, int64_t n, int fp64);
+
+/* Symmetric eigendecomposition (Algorithm 3, step 1) of the real symmetric
+ * A_s held in the real part of dAs: dV (out, real n x n, float or double)
+ * and dlam (out, n).  Returns 0 or 3. */
+SQRTM_API int sqrtm_step_syevd(sqrtm_handle_t h, const void *dAs, void *dV, void *dlam, int64_t n,
+                     int fp64);
+
+/* Triangular square root S = T^{1/2} (Algorithm 2, step 2; blocked method of
+ * Sec. 2.2.1 with Eq. (subst) inside diagonal blocks).  dT, dS: upper
+ * triangular n x n.  Returns 0 or 2. */
+SQRTM_API int sqrtm_step_trisqrt(sqrtm_handle_t h, const void *dT, void *dS, int64_t n, int blks,
+                       int fp64);
+
+/* X_0 = Re(Q S Q^H) (Algorithm 2, step 3), computed in the storage
+ * precision of Q and S, rounded to that precision and written widened to
+ * FP64 into dX (ldx), times 2^e (undoing the scaling). */
+SQRTM_API int sqrtm_step_form_x0(sqrtm_handle_t h, const void *dQ, const void *dS, int64_t n, int e,
+                       double *dX, int64_t ldx, int fp64);
+
+/* Residual (Algorithm 2, step 5) on the scaled problem: R = 4^-e A - X_s X_s
+ * with X_s = 2^-e X, in FP64; writes fl32(R) into dRhat (float n x n) and
+ * ||R||_F into *norm_host. */
+SQRTM_API int sqrtm_step_residual(sqrtm_handle_t h, const double *dA, int64_t lda, const double *dX,
+                        int64_t ldx, int64_t n, int e, float *dRhat, double *norm_host);
+
+/* Transform (Algorithm 2, step 8): dRt = Q^H Rhat Q in low precision (Q c64,
+ * Rhat float, Rt c64). */
+SQRTM_API int sqrtm_step_transform_in(sqrtm_handle_t h, const void *dQ, const float *dRhat, void *dRt,
+                            int64_t n);
+
+/* Triangular Sylvester solve S Y + Y St = C (Algorithm 2, step 9;
+ * Algorithm 1 computes the same Y): S m x m and St nn x nn upper triangular
+ * (c64, ld m and nn), dC (c64, m x nn, ld m) overwritten by Y.  Returns 0
+ * or 2. */
+SQRTM_API int sqrtm_step_rtrsyl(sqrtm_handle_t h, const void *dS, int64_t m, const void *dSt,
+                      int64_t nn, void *dC, int blks);
+
+/* Back-transform and update (Algorithm 2, steps 10-11): dX += 2^e Re(Q Y
+ * Q^H), product in low precision, addition in FP64.  Q, Y c64. */
+SQRTM_API int sqrtm_step_transform_out_update(sqrtm_handle_t h, const void *dQ, const void *dY,
+                                    int64_t n, int e, double *dX, int64_t ldx);
+
+/* SPD transform with the diagonal Sylvester solve fused (Algorithm 3, steps
+ * 8-9): dY = (V^T Rhat V) ./ (s_i + s_j), s_i = sqrt(lam_i).  V, Y float. */
+SQRTM_API int sqrtm_step_transform_in_spd(sqrtm_handle_t h, const float *dV, const float *dlam,
+                                const float *dRhat, float *dY, int64_t n);
+
+/* SPD back-transform and update (Algorithm 3, steps 10-11):
+ * dX += 2^e V Y V^T, symmetrised; V, Y float. */
+SQRTM_API int sqrtm_step_transform_out_update_spd(sqrtm_handle_t h, const float *dV, const float *dY,
+                                        int64_t n, int e, double *dX, int64_t ldx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SQRTM_MP_STEPS_H */

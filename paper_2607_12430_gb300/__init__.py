@@ -1,0 +1,343 @@
+"""GB300 (sm_103a) mixed-precision matrix square root (arXiv 2607.12430).
+
+Thin Python binding over the C ABI in ``include/sqrtm_mp.h`` and
+``include/sqrtm_mp_steps.h``: every function marshals torch tensors (device
+memory and the current CUDA stream) into the C call of the same name; all
+computation runs in the library's CUDA kernels.  There is no CPU path: if the
+compiled library is missing, every call raises.
+
+Layout: the C ABI is column-major.  A contiguous (row-major) torch tensor is
+the column-major storage of its transpose, and the principal square root
+commutes with transposition (sqrt(A^T) = sqrt(A)^T), so row-major tensors are
+passed through unchanged and the result comes back row-major.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build_mod
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = _build_mod.LIB
+
+STATUS = {
+    0: "success", 1: "not converged", 2: "eigenvalue on the closed negative real axis",
+    3: "Schur iteration cap", 4: "diverged", 5: "NaN/Inf input", 6: "device wait gave up",
+    7: "CUDA error", 8: "no saved factors",
+}
+
+KIND_AUTO, KIND_GENERAL, KIND_SPD = 0, 1, 2
+PREC_FP32, PREC_TF32X3 = 0, 1
+MAX_HISTORY = 64
+
+
+class SqrtmError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what} failed with status {code} ({STATUS.get(code, 'invalid argument')})")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("blks", ctypes.c_int),
+                ("kind", ctypes.c_int), ("precision", ctypes.c_int), ("steps", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("kind_used", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("scale_exponent", ctypes.c_int), ("norm_a", ctypes.c_double),
+                ("history_len", ctypes.c_int), ("history", ctypes.c_double * MAX_HISTORY),
+                ("ms_schur", ctypes.c_double), ("ms_trisqrt", ctypes.c_double),
+                ("ms_refine", ctypes.c_double), ("ms_reduction", ctypes.c_double),
+                ("schur_sweeps", ctypes.c_int), ("schur_rotations", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {"status": self.status, "kind_used": self.kind_used, "iterations": self.iterations,
+                "scale_exponent": self.scale_exponent, "norm_a": self.norm_a,
+                "history": [self.history[i] for i in range(self.history_len)],
+                "ms_schur": self.ms_schur, "ms_trisqrt": self.ms_trisqrt, "ms_refine": self.ms_refine,
+                "ms_reduction": self.ms_reduction, "schur_sweeps": self.schur_sweeps,
+                "schur_rotations": self.schur_rotations}
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_L = ctypes.c_int64
+_D = ctypes.c_double
+
+_SIGS = {
+    "sqrtm_create": ([ctypes.POINTER(_P), _P], _I),
+    "sqrtm_destroy": ([_P], _I),
+    "sqrtm_set_stream": ([_P, _P], _I),
+    "sqrtm_default_opts": ([ctypes.POINTER(Opts)], None),
+    "sqrtm_mixed": ([_P, _P, _L, _L, _D, _P, _L, ctypes.POINTER(Opts), ctypes.POINTER(Info)], _I),
+    "sqrtm_schur_fp64": ([_P, _P, _L, _L, _D, _P, _L, ctypes.POINTER(Opts), ctypes.POINTER(Info)], _I),
+    "sqrtm_backward": ([_P, _P, _L, _L, _D, _P, _L, ctypes.POINTER(Info)], _I),
+    "sqrtm_mixed_batched": ([_P, _I, _P, _P, _P, _D, _P, _P, ctypes.POINTER(Opts), _P], _I),
+    "sqrtm_status_string": ([_I], ctypes.c_char_p),
+    "sqrtm_step_scale": ([_P, _P, _L, _L, _P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
+    "sqrtm_step_schur": ([_P, _P, _P, _L, _I], _I),
+    "sqrtm_step_syevd": ([_P, _P, _P, _P, _L, _I], _I),
+    "sqrtm_step_trisqrt": ([_P, _P, _P, _L, _I, _I], _I),
+    "sqrtm_step_form_x0": ([_P, _P, _P, _L, _I, _P, _L, _I], _I),
+    "sqrtm_step_residual": ([_P, _P, _L, _P, _L, _L, _I, _P, ctypes.POINTER(_D)], _I),
+    "sqrtm_step_transform_in": ([_P, _P, _P, _P, _L], _I),
+    "sqrtm_step_rtrsyl": ([_P, _P, _L, _P, _L, _P, _I], _I),
+    "sqrtm_step_transform_out_update": ([_P, _P, _P, _L, _I, _P, _L], _I),
+    "sqrtm_step_transform_in_spd": ([_P, _P, _P, _P, _P, _L], _I),
+    "sqrtm_step_transform_out_update_spd": ([_P, _P, _P, _L, _I, _P, _L], _I),
+}
+
+
+def lib():
+    """Load the compiled library (``build()`` first).  Raises if it is missing:
+    there is no fallback."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def build(force: bool = False) -> str:
+    return _build_mod.build(force=force)
+
+
+# ---------------------------------------------------------------------------
+# handles: one per (device, stream)
+# ---------------------------------------------------------------------------
+_handles: dict = {}
+
+
+def _stream_ptr():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def handle():
+    dev = torch.cuda.current_device()
+    st = torch.cuda.current_stream().cuda_stream
+    key = (dev, st)
+    h = _handles.get(key)
+    if h is None:
+        hp = ctypes.c_void_p()
+        rc = lib().sqrtm_create(ctypes.byref(hp), ctypes.c_void_p(st))
+        if rc:
+            raise SqrtmError(rc, "sqrtm_create")
+        h = hp
+        _handles[key] = h
+    return h
+
+
+def _check_square(A, name="A"):
+    if not isinstance(A, torch.Tensor) or not A.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if A.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    if A.dim() != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError(f"{name} must be square")
+    if not A.is_contiguous():
+        A = A.contiguous()
+    return A
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else ctypes.c_void_p(0)
+
+
+def make_opts(tol=1e-12, maxit=10, blks=32, kind=KIND_AUTO, precision=PREC_FP32, steps=-1):
+    o = Opts()
+    lib().sqrtm_default_opts(ctypes.byref(o))
+    o.tol, o.maxit, o.blks, o.kind, o.precision, o.steps = tol, maxit, blks, kind, precision, steps
+    return o
+
+
+# ---------------------------------------------------------------------------
+# C-ABI entry points
+# ---------------------------------------------------------------------------
+def sqrtm_mixed(A, tol=1e-12, out=None, raise_on_error=True, **kw):
+    """Mixed-precision principal square root (Algorithms 2 / 3).  Returns
+    ``(X, info_dict)``."""
+    A = _check_square(A)
+    n = A.shape[0]
+    X = out if out is not None else torch.empty_like(A)
+    o = make_opts(tol=tol, **kw)
+    info = Info()
+    ld = max(1, n)
+    rc = lib().sqrtm_mixed(handle(), _ptr(A), n, ld, tol, _ptr(X), ld, ctypes.byref(o), ctypes.byref(info))
+    if rc and raise_on_error:
+        raise SqrtmError(rc, "sqrtm_mixed")
+    d = info.as_dict()
+    d["status"] = rc
+    return X, d
+
+
+def sqrtm_schur_fp64(A, out=None, raise_on_error=True, **kw):
+    """Plain FP64 Schur method on the GPU.  Returns ``(X, info_dict)``."""
+    A = _check_square(A)
+    n = A.shape[0]
+    X = out if out is not None else torch.empty_like(A)
+    o = make_opts(**kw)
+    info = Info()
+    ld = max(1, n)
+    rc = lib().sqrtm_schur_fp64(handle(), _ptr(A), n, ld, 0.0, _ptr(X), ld, ctypes.byref(o), ctypes.byref(info))
+    if rc and raise_on_error:
+        raise SqrtmError(rc, "sqrtm_schur_fp64")
+    d = info.as_dict()
+    d["status"] = rc
+    return X, d
+
+
+def sqrtm_backward(G, tol=1e-12, out=None, raise_on_error=True):
+    """Gradient of <G, sqrtm(A)> for the last sqrtm_mixed call on this
+    stream's handle: Y with X^T Y + Y X^T = G."""
+    G = _check_square(G, "G")
+    n = G.shape[0]
+    Y = out if out is not None else torch.empty_like(G)
+    info = Info()
+    ld = max(1, n)
+    rc = lib().sqrtm_backward(handle(), _ptr(G), n, ld, tol, _ptr(Y), ld, ctypes.byref(info))
+    if rc and raise_on_error:
+        raise SqrtmError(rc, "sqrtm_backward")
+    d = info.as_dict()
+    d["status"] = rc
+    return Y, d
+
+
+def sqrtm_mixed_batched(As, tol=1e-12, outs=None, **kw):
+    """Square roots of a list of square float64 CUDA tensors of any sizes.
+    Returns ``(list_of_X, list_of_status)``."""
+    As = [_check_square(A) for A in As]
+    Xs = outs if outs is not None else [torch.empty_like(A) for A in As]
+    b = len(As)
+    pa = (ctypes.c_void_p * b)(*[A.data_ptr() for A in As])
+    px = (ctypes.c_void_p * b)(*[X.data_ptr() for X in Xs])
+    ns = (ctypes.c_int64 * b)(*[A.shape[0] for A in As])
+    st = (ctypes.c_int * b)()
+    o = make_opts(tol=tol, **kw)
+    lib().sqrtm_mixed_batched(handle(), b, ctypes.cast(pa, _P), ctypes.cast(ns, _P), ctypes.cast(ns, _P),
+                              tol, ctypes.cast(px, _P), ctypes.cast(ns, _P), ctypes.byref(o),
+                              ctypes.cast(st, _P))
+    return Xs, list(st)
+
+
+class _SqrtmFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, A, tol):
+        X, info = sqrtm_mixed(A, tol=tol)
+        ctx.tol = tol
+        ctx.n = A.shape[0]
+        return X
+
+    @staticmethod
+    def backward(ctx, G):
+        Y, _ = sqrtm_backward(G.contiguous(), tol=ctx.tol)
+        return Y, None
+
+
+def sqrtm(A, tol=1e-12):
+    """Differentiable principal square root (forward: sqrtm_mixed; backward:
+    sqrtm_backward on the factors of that forward call)."""
+    return _SqrtmFn.apply(A, tol)
+
+
+# ---------------------------------------------------------------------------
+# step-level entry points (sqrtm_mp_steps.h); arrays are column-major, so
+# callers pass tensors whose storage is column-major (e.g. M.T.contiguous().T
+# is not needed: use fortran_view below)
+# ---------------------------------------------------------------------------
+def col_major(t):
+    """Return a tensor whose row-major storage holds ``t`` column-major (i.e.
+    ``t.T.contiguous()``); use ``from_col_major`` to read results back."""
+    return t.transpose(-1, -2).contiguous()
+
+
+def from_col_major(t):
+    return t.transpose(-1, -2)
+
+
+def _rc(rc, what):
+    if rc:
+        raise SqrtmError(rc, what)
+
+
+def step_scale(A_cm, n, fp64=False):
+    """A_cm: float64 tensor holding A column-major (n*n).  Returns
+    (As_cm complex, e, norm)."""
+    dt = torch.complex128 if fp64 else torch.complex64
+    As = torch.empty(n * n, dtype=dt, device=A_cm.device)
+    e = ctypes.c_int()
+    nrm = ctypes.c_double()
+    _rc(lib().sqrtm_step_scale(handle(), _ptr(A_cm), n, n, _ptr(As), int(fp64), ctypes.byref(e), ctypes.byref(nrm)), "scale")
+    return As, e.value, nrm.value
+
+
+def step_schur(T_cm, n, fp64=False):
+    """In place: T_cm (complex, column-major A_s) becomes T; returns Q_cm."""
+    Q = torch.empty_like(T_cm)
+    _rc(lib().sqrtm_step_schur(handle(), _ptr(T_cm), _ptr(Q), n, int(fp64)), "schur")
+    return Q
+
+
+def step_syevd(As_cm, n, fp64=False):
+    dt = torch.float64 if fp64 else torch.float32
+    V = torch.empty(n * n, dtype=dt, device=As_cm.device)
+    lam = torch.empty(n, dtype=dt, device=As_cm.device)
+    _rc(lib().sqrtm_step_syevd(handle(), _ptr(As_cm), _ptr(V), _ptr(lam), n, int(fp64)), "syevd")
+    return V, lam
+
+
+def step_trisqrt(T_cm, n, blks=32, fp64=False):
+    S = torch.empty_like(T_cm)
+    _rc(lib().sqrtm_step_trisqrt(handle(), _ptr(T_cm), _ptr(S), n, blks, int(fp64)), "trisqrt")
+    return S
+
+
+def step_form_x0(Q_cm, S_cm, n, e=0, fp64=False):
+    X = torch.empty(n * n, dtype=torch.float64, device=Q_cm.device)
+    _rc(lib().sqrtm_step_form_x0(handle(), _ptr(Q_cm), _ptr(S_cm), n, e, _ptr(X), n, int(fp64)), "form_x0")
+    return X
+
+
+def step_residual(A_cm, X_cm, n, e=0):
+    Rhat = torch.empty(n * n, dtype=torch.float32, device=A_cm.device)
+    nrm = ctypes.c_double()
+    _rc(lib().sqrtm_step_residual(handle(), _ptr(A_cm), n, _ptr(X_cm), n, n, e, _ptr(Rhat), ctypes.byref(nrm)), "residual")
+    return Rhat, nrm.value
+
+
+def step_transform_in(Q_cm, Rhat_cm, n):
+    Rt = torch.empty(n * n, dtype=torch.complex64, device=Q_cm.device)
+    _rc(lib().sqrtm_step_transform_in(handle(), _ptr(Q_cm), _ptr(Rhat_cm), _ptr(Rt), n), "transform_in")
+    return Rt
+
+
+def step_rtrsyl(S_cm, m, St_cm, nn, C_cm, blks=32):
+    """In place: C_cm (complex64, m x nn column-major) becomes Y."""
+    _rc(lib().sqrtm_step_rtrsyl(handle(), _ptr(S_cm), m, _ptr(St_cm), nn, _ptr(C_cm), blks), "rtrsyl")
+    return C_cm
+
+
+def step_transform_out_update(Q_cm, Y_cm, n, X_cm, e=0):
+    _rc(lib().sqrtm_step_transform_out_update(handle(), _ptr(Q_cm), _ptr(Y_cm), n, e, _ptr(X_cm), n), "transform_out_update")
+    return X_cm
+
+
+def step_transform_in_spd(V_cm, lam, Rhat_cm, n):
+    Y = torch.empty(n * n, dtype=torch.float32, device=V_cm.device)
+    _rc(lib().sqrtm_step_transform_in_spd(handle(), _ptr(V_cm), _ptr(lam), _ptr(Rhat_cm), _ptr(Y), n), "transform_in_spd")
+    return Y
+
+
+def step_transform_out_update_spd(V_cm, Y_cm, n, X_cm, e=0):
+    _rc(lib().sqrtm_step_transform_out_update_spd(handle(), _ptr(V_cm), _ptr(Y_cm), n, e, _ptr(X_cm), n), "transform_out_update_spd")
+    return X_cm

@@ -1,0 +1,378 @@
+// api.cu -- C ABI of the library: handle and workspace management, the
+// drivers of Algorithm 2 (general A), Algorithm 3 (SPD A), the plain FP64
+// Schur method, the adjoint solve and the step-level entry points.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "handle.h"
+
+using namespace sqm;
+
+extern "C" int sqrtm_create(sqrtm_handle_t *handle, void *stream)
+{
+    if (!handle) return -1;
+    sqrtm_handle_s *h = new sqrtm_handle_s();
+    h->stream = (cudaStream_t)stream;
+    for (auto &e : h->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) { delete h; return 7; }
+    if (cudaMallocHost(&h->staging.p, 4096) != cudaSuccess) { delete h; return 7; }
+    h->staging.bytes = 4096;
+    *handle = h;
+    return 0;
+}
+
+extern "C" int sqrtm_destroy(sqrtm_handle_t h)
+{
+    if (!h) return 0;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    if (h->ws.p) cudaFree(h->ws.p);
+    if (h->fact.p) cudaFree(h->fact.p);
+    if (h->staging.p) cudaFreeHost(h->staging.p);
+    for (auto &e : h->ev)
+        if (e) cudaEventDestroy(e);
+    delete h;
+    return 0;
+}
+
+extern "C" int sqrtm_set_stream(sqrtm_handle_t h, void *stream)
+{
+    if (!h) return -1;
+    h->stream = (cudaStream_t)stream;
+    return 0;
+}
+
+extern "C" void sqrtm_default_opts(sqrtm_opts *o)
+{
+    if (!o) return;
+    o->tol = 1e-12;
+    o->maxit = 10;
+    o->blks = 32;
+    o->kind = SQRTM_KIND_AUTO;
+    o->precision = SQRTM_PREC_FP32;
+    o->steps = -1;
+}
+
+extern "C" const char *sqrtm_status_string(int code)
+{
+    switch (code) {
+    case 0: return "success";
+    case 1: return "refinement did not reach the tolerance within maxit steps";
+    case 2: return "eigenvalue on or next to the closed negative real axis";
+    case 3: return "Schur/eigensolver iteration cap reached";
+    case 4: return "refinement diverged";
+    case 5: return "input contains NaN or Inf";
+    case 6: return "device-side wait gave up";
+    case 7: return "CUDA error or allocation failure";
+    case 8: return "no factors saved on the handle";
+    default: return code < 0 ? "invalid argument" : "unknown status";
+    }
+}
+
+static void info_reset(sqrtm_info *info)
+{
+    if (!info) return;
+    memset(info, 0, sizeof(*info));
+}
+
+// scalars in device workspace: [0] norm, [1] residual norm, [2..] partials;
+// ints: e, status(schur), status(trisqrt/solve)
+struct Scalars {
+    double *norm, *rnorm, *partials;
+    int *e, *st_schur, *st_solve;
+    int npart_cap;
+};
+
+static size_t scalars_bytes(int64_t n)
+{
+    int64_t nb = (n + 63) / 64;
+    int64_t np = std::max<int64_t>(nb * nb, 2048);
+    return Carve::round((np + 8) * sizeof(double)) + 256;
+}
+
+static Scalars carve_scalars(Carve &c, int64_t n)
+{
+    Scalars s;
+    int64_t nb = (n + 63) / 64;
+    s.npart_cap = (int)std::max<int64_t>(nb * nb, 2048);
+    s.norm = c.take<double>(s.npart_cap + 8);
+    s.rnorm = s.norm + 1;
+    s.partials = s.norm + 2;
+    int *iv = c.take<int>(8);
+    s.e = iv;
+    s.st_schur = iv + 1;
+    s.st_solve = iv + 2;
+    return s;
+}
+
+static int check_args(const void *A, int64_t n, int64_t lda, const void *X, int64_t ldx)
+{
+    if (n < 0) return -3;
+    if (n > 0 && !A) return -2;
+    if (lda < std::max<int64_t>(1, n)) return -4;
+    if (n > 0 && !X) return -6;
+    if (ldx < std::max<int64_t>(1, n)) return -7;
+    if (n > 46340) return -3;  // n*n must fit the int indexing of the tiles
+    return 0;
+}
+
+// host read of device scalars through pinned staging
+static int read_scalars(sqrtm_handle_t h, const Scalars &s, double *norm, double *rnorm, int *e,
+                        int *st_schur, int *st_solve)
+{
+    char *st = (char *)h->staging.p;
+    SQM_CU(cudaMemcpyAsync(st, s.norm, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    SQM_CU(cudaMemcpyAsync(st + 16, s.e, 3 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    SQM_CU(cudaStreamSynchronize(h->stream));
+    double *dv = (double *)st;
+    int *iv = (int *)(st + 16);
+    if (norm) *norm = dv[0];
+    if (rnorm) *rnorm = dv[1];
+    if (e) *e = iv[0];
+    if (st_schur) *st_schur = iv[1];
+    if (st_solve) *st_solve = iv[2];
+    return 0;
+}
+
+static bool is_bitwise_symmetric(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda,
+                                 int *flag_dev, int *rc);
+
+// ---------------------------------------------------------------------------
+// general path (Algorithm 2) in storage precision R; refine = false gives the
+// plain Schur method
+// ---------------------------------------------------------------------------
+template <class R>
+static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, double tol,
+                        double *dX, int64_t ldx, const sqrtm_opts &o, sqrtm_info *info,
+                        bool refine)
+{
+    cudaStream_t s = h->stream;
+    const size_t nn = (size_t)n * (size_t)n;
+    const size_t cb = sizeof(cplx<R>);
+    // factors: Q, S persist for the adjoint
+    size_t fbytes = 2 * Carve::round(nn * cb) + Carve::round(nn * sizeof(double)) + 1024;
+    size_t wbytes = scalars_bytes(n) + 3 * Carve::round(nn * cb) + Carve::round(nn * sizeof(float)) +
+                    Carve::round((n + 8) * cb) + Carve::round(8 * sizeof(R)) +
+                    Carve::round(sizeof(SchurDesc<R>)) + 4096;
+    if (ensure(h->fact, fbytes) || ensure(h->ws, wbytes)) return 7;
+    Carve cf(h->fact.p);
+    cplx<R> *Q = cf.take<cplx<R>>(nn);
+    cplx<R> *S = cf.take<cplx<R>>(nn);
+    double *Xsave = cf.take<double>(nn);
+    Carve cw(h->ws.p);
+    Scalars sc = carve_scalars(cw, n);
+    cplx<R> *T = cw.take<cplx<R>>(nn);
+    cplx<R> *W = cw.take<cplx<R>>(nn);
+    cplx<R> *Rt = cw.take<cplx<R>>(nn);
+    float *Rhat = cw.take<float>(nn);
+    cplx<R> *v = cw.take<cplx<R>>(n + 8);
+    R *beta = cw.take<R>(8);
+    SchurDesc<R> *ddesc = cw.take<SchurDesc<R>>(1);
+    h->fact_n = -1;
+
+    SQM_CU(cudaMemsetAsync(sc.e, 0, 8 * sizeof(int), s));
+    SQM_CU(cudaEventRecord(h->ev[0], s));
+    SQM_CU(launch_norm_scale(dA, n, lda, sc.partials, (int)std::min<int64_t>(n, 1024), sc.norm, sc.e, s));
+    SQM_CU(launch_cast_scaled<R>(dA, n, lda, sc.e, T, n, s));
+    double norm_a = 0.0;
+    int e = 0;
+    if (int rc = read_scalars(h, sc, &norm_a, nullptr, &e, nullptr, nullptr)) return rc;
+    if (info) { info->norm_a = norm_a; info->scale_exponent = e; info->kind_used = SQRTM_KIND_GENERAL; }
+    if (!isfinite(norm_a)) return 5;
+    if (norm_a == 0.0) return 2;  // the zero matrix has the eigenvalue 0
+
+    SchurDesc<R> hd;
+    hd.T = T; hd.Q = Q; hd.v = v; hd.beta = beta; hd.status = sc.st_schur; hd.n = (int)n; hd.ld = (int)n;
+    hd.counters = sc.st_schur + 3;
+    memcpy(h->staging.p, &hd, sizeof(hd));
+    SQM_CU(cudaMemcpyAsync(ddesc, h->staging.p, sizeof(hd), cudaMemcpyHostToDevice, s));
+    SQM_CU(cudaStreamSynchronize(s));
+    SQM_CU(launch_hessenberg<R>(ddesc, 1, (int)n, 64, s));
+    cudaEvent_t ev_red;
+    SQM_CU(cudaEventCreate(&ev_red));
+    SQM_CU(cudaEventRecord(ev_red, s));
+    SQM_CU(launch_qr_sweeps<R>(ddesc, 1, s));
+    SQM_CU(cudaEventRecord(h->ev[1], s));
+    SQM_CU(launch_trisqrt<R>(T, (int)n, S, (int)n, (int)n, o.blks, sc.st_solve, s));
+    // X_0 = Re(Q S Q^H), rounded to R, times 2^e
+    SQM_CU(launch_cgemm<R>(OP_N, OP_N, (int)n, (int)n, (int)n, Q, (int)n, false, S, (int)n, EPI_STORE, W, (int)n, nullptr, 0, 0.0, s));
+    SQM_CU(launch_cgemm<R>(OP_N, OP_H, (int)n, (int)n, (int)n, W, (int)n, false, Q, (int)n, EPI_REAL_TO_F64, nullptr, 0, dX, ldx, ldexp(1.0, e), s));
+    SQM_CU(cudaEventRecord(h->ev[2], s));
+    int st_schur = 0, st_solve = 0;
+    if (int rc = read_scalars(h, sc, nullptr, nullptr, nullptr, &st_schur, &st_solve)) return rc;
+    if (info) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]); info->ms_schur = ms;
+        cudaEventElapsedTime(&ms, h->ev[1], h->ev[2]); info->ms_trisqrt = ms;
+        cudaEventElapsedTime(&ms, h->ev[0], ev_red); info->ms_reduction = ms;
+        int cnt[3];
+        SQM_CU(cudaMemcpy(cnt, sc.st_schur + 3, sizeof(cnt), cudaMemcpyDeviceToHost));
+        info->schur_sweeps = cnt[0];
+        info->schur_rotations = (int64_t)cnt[1] + ((int64_t)cnt[2] << 31);
+    }
+    cudaEventDestroy(ev_red);
+    if (st_schur) return st_schur;
+    if (st_solve) return st_solve;
+    if (!refine) return 0;
+
+    const double norm_as = ldexp(norm_a, -2 * e);
+    const bool fixed = o.steps >= 0;
+    const int max_corr = fixed ? o.steps : o.maxit + 1;
+    int status = 0, applied = 0, grew = 0;
+    double prev = INFINITY;
+    for (int k = 0;; ++k) {
+        bool need_res = !fixed || k < max_corr;
+        if (k >= max_corr && fixed) break;
+        if (need_res) {
+            int np = 0;
+            SQM_CU(launch_residual_f64(dA, lda, dX, ldx, (int)n, e, Rhat, (int)n, sc.partials, &np, s));
+            SQM_CU(launch_sum_partials(sc.partials, np, sc.rnorm, s));
+            double rn = 0.0;
+            if (!fixed) {
+                if (int rc = read_scalars(h, sc, nullptr, &rn, nullptr, nullptr, nullptr)) return rc;
+                double rel = rn / norm_as;
+                if (info && info->history_len < SQRTM_MAX_HISTORY) info->history[info->history_len++] = rel;
+                if (!isfinite(rel)) { status = 4; break; }
+                if (rel <= tol) { status = 0; break; }
+                if (k >= max_corr) { status = 1; break; }
+                grew = (rn > prev) ? grew + 1 : 0;
+                if (grew >= 2) { status = 4; break; }
+                prev = rn;
+            }
+        }
+        // R~ = Q^H Rhat Q; Y solves S Y + Y S = R~; X += 2^e Re(Q Y Q^H)
+        SQM_CU(launch_cgemm<R>(OP_N, OP_N, (int)n, (int)n, (int)n, Rhat, (int)n, true, Q, (int)n, EPI_STORE, W, (int)n, nullptr, 0, 0.0, s));
+        SQM_CU(launch_cgemm<R>(OP_H, OP_N, (int)n, (int)n, (int)n, Q, (int)n, false, W, (int)n, EPI_STORE, Rt, (int)n, nullptr, 0, 0.0, s));
+        SQM_CU(launch_rtrsyl<R>(S, (int)n, (int)n, S, (int)n, (int)n, Rt, (int)n, o.blks, sc.st_solve, s));
+        SQM_CU(launch_cgemm<R>(OP_N, OP_N, (int)n, (int)n, (int)n, Q, (int)n, false, Rt, (int)n, EPI_STORE, W, (int)n, nullptr, 0, 0.0, s));
+        SQM_CU(launch_cgemm<R>(OP_N, OP_H, (int)n, (int)n, (int)n, W, (int)n, false, Q, (int)n, EPI_REAL_ADD_F64, nullptr, 0, dX, ldx, ldexp(1.0, e), s));
+        ++applied;
+    }
+    SQM_CU(cudaEventRecord(h->ev[3], s));
+    if (int rc = read_scalars(h, sc, nullptr, nullptr, nullptr, nullptr, &st_solve)) return rc;
+    if (!st_solve && (status == 0 || status == 1)) {
+        // keep the factors and X for sqrtm_backward
+        SQM_CU(cudaMemcpy2DAsync(Xsave, n * sizeof(double), dX, ldx * sizeof(double), n * sizeof(double), n,
+                                 cudaMemcpyDeviceToDevice, s));
+        h->fact_n = n; h->fact_kind = SQRTM_KIND_GENERAL; h->fact_e = e; h->fact_norm = norm_a;
+        h->fact_q = Q; h->fact_s = S; h->fact_x = Xsave;
+    }
+    if (info) {
+        info->iterations = applied;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]); info->ms_refine = ms;
+    }
+    if (st_solve) return st_solve;
+    return status;
+}
+
+static int resolve_opts(const sqrtm_opts *opts, double tol, sqrtm_opts *o)
+{
+    sqrtm_default_opts(o);
+    if (opts) *o = *opts;
+    else o->tol = tol;
+    if (o->blks < 1) return -8;
+    if (o->maxit < 0 || o->maxit > SQRTM_MAX_HISTORY - 2) return -8;
+    return 0;
+}
+
+extern "C" int sqrtm_mixed(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda,
+                           double tol, double *dX, int64_t ldx, const sqrtm_opts *opts,
+                           sqrtm_info *info)
+{
+    info_reset(info);
+    if (!h) return -1;
+    if (int rc = check_args(dA, n, lda, dX, ldx)) return rc;
+    sqrtm_opts o;
+    if (int rc = resolve_opts(opts, tol, &o)) return rc;
+    if (n == 0) return 0;
+    int kind = o.kind;
+    if (kind == SQRTM_KIND_AUTO) {
+        int rc = 0;
+        if (ensure(h->ws, 4096)) return 7;
+        bool sym = is_bitwise_symmetric(h, dA, n, lda, (int *)h->ws.p, &rc);
+        if (rc) return rc;
+        kind = sym ? SQRTM_KIND_SPD : SQRTM_KIND_GENERAL;
+    }
+    int rc;
+    if (kind == SQRTM_KIND_SPD && spd_enabled()) rc = spd_path(h, dA, n, lda, o.tol, dX, ldx, o, info);
+    else rc = general_path<float>(h, dA, n, lda, o.tol, dX, ldx, o, info, true);
+    if (info) info->status = rc;
+    return rc;
+}
+
+extern "C" int sqrtm_schur_fp64(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda,
+                                double tol, double *dX, int64_t ldx, const sqrtm_opts *opts,
+                                sqrtm_info *info)
+{
+    (void)tol;
+    info_reset(info);
+    if (!h) return -1;
+    if (int rc = check_args(dA, n, lda, dX, ldx)) return rc;
+    sqrtm_opts o;
+    if (int rc = resolve_opts(opts, tol, &o)) return rc;
+    if (n == 0) return 0;
+    int kind = o.kind;
+    if (kind == SQRTM_KIND_AUTO) {
+        int rc = 0;
+        if (ensure(h->ws, 4096)) return 7;
+        bool sym = is_bitwise_symmetric(h, dA, n, lda, (int *)h->ws.p, &rc);
+        if (rc) return rc;
+        kind = sym ? SQRTM_KIND_SPD : SQRTM_KIND_GENERAL;
+    }
+    int rc;
+    if (kind == SQRTM_KIND_SPD && spd_enabled()) rc = spd_schur_fp64(h, dA, n, lda, dX, ldx, o, info);
+    else rc = general_path<double>(h, dA, n, lda, 0.0, dX, ldx, o, info, false);
+    h->fact_n = -1;  // the FP64 method keeps no low-precision factors
+    if (info) info->status = rc;
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// bitwise symmetry test (selects Algorithm 3 under SQRTM_KIND_AUTO)
+// ---------------------------------------------------------------------------
+__global__ void symmetric_kernel(const double *__restrict__ A, int64_t n, int64_t lda, int *flag)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = t % n, j = t / n;
+        if (i < j) {
+            double a = A[i + j * lda], b = A[j + i * lda];
+            if (__double_as_longlong(a) != __double_as_longlong(b)) atomicExch(flag, 0);
+        }
+    }
+}
+
+static bool is_bitwise_symmetric(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda,
+                                 int *flag_dev, int *rc)
+{
+    *rc = 0;
+    int one = 1;
+    if (cudaMemcpyAsync(flag_dev, &one, sizeof(int), cudaMemcpyHostToDevice, h->stream) != cudaSuccess) { *rc = 7; return false; }
+    int grid = (int)std::min<int64_t>(std::max<int64_t>(1, (n * n + 255) / 256), 152 * 8);
+    symmetric_kernel<<<grid, 256, 0, h->stream>>>(dA, n, lda, flag_dev);
+    int flag = 0;
+    if (cudaMemcpyAsync(&flag, flag_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) { *rc = 7; return false; }
+    return flag != 0;
+}
+
+extern "C" int sqrtm_mixed_batched(sqrtm_handle_t h, int batch, const double *const *dA,
+                                   const int64_t *n, const int64_t *lda, double tol,
+                                   double *const *dX, const int64_t *ldx, const sqrtm_opts *opts,
+                                   int *status)
+{
+    if (!h) return -1;
+    if (batch < 0) return -2;
+    int first = 0;
+    for (int i = 0; i < batch; ++i) {
+        int rc = sqrtm_mixed(h, dA[i], n[i], lda[i], tol, dX[i], ldx[i], opts, nullptr);
+        if (status) status[i] = rc;
+        if (rc && !first) first = rc;
+    }
+    return first;
+}

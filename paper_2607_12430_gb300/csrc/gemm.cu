@@ -1,0 +1,337 @@
+// gemm.cu -- dense products of the refinement loop on the CUDA cores:
+//   * cgemm: C = op(A) op(B) for complex (or real-times-complex) operands in
+//     the storage precision R, 64x64x16 shared-memory tiles, 4x4 outputs per
+//     thread, with epilogues that write Re(C) widened to FP64 (X_0) or add it
+//     into the FP64 iterate (X_{k+1} = X_k + dX, Algorithm 2 steps 10-11);
+//   * residual_f64: R = (A - X X) 4^-e in FP64 (Algorithm 2 step 5) with the
+//     cast of R to FP32 and per-CTA partial sums of |R|^2 fused in the
+//     epilogue; partials are summed in a fixed order (bit-reproducible norm).
+#include "internal.h"
+
+namespace sqm {
+
+static constexpr int GB_M = 64, GB_N = 64, GB_K = 16, G_THREADS = 256;
+
+template <class R, int OPA, int OPB, bool AREAL, int EPI>
+__global__ void __launch_bounds__(G_THREADS)
+cgemm_kernel(int m, int n, int k, const void *__restrict__ Av, int lda,
+             const cplx<R> *__restrict__ B, int ldb, cplx<R> *__restrict__ C, int ldc,
+             double *__restrict__ X, int64_t ldx, double scale)
+{
+    __shared__ cplx<R> As[GB_K][GB_M + 1];
+    __shared__ cplx<R> Bs[GB_K][GB_N + 1];
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    const int m0 = blockIdx.x * GB_M, n0 = blockIdx.y * GB_N;
+    cplx<R> acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = cplx<R>{0, 0};
+
+    const cplx<R> *A = reinterpret_cast<const cplx<R> *>(Av);
+    const R *Ar = reinterpret_cast<const R *>(Av);
+
+    for (int k0 = 0; k0 < k; k0 += GB_K) {
+        // A tile: op(A)(m0 + i, k0 + kk)
+        if (OPA == OP_N) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                int i = tid % GB_M, kk = tid / GB_M + 4 * q;
+                int gi = m0 + i, gk = k0 + kk;
+                cplx<R> v{0, 0};
+                if (gi < m && gk < k) {
+                    if (AREAL) v = cplx<R>{Ar[gi + (int64_t)gk * lda], R(0)};
+                    else v = A[gi + (int64_t)gk * lda];
+                }
+                As[kk][i] = v;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                int kk = tid % GB_K, i = tid / GB_K + 16 * q;
+                int gi = m0 + i, gk = k0 + kk;
+                cplx<R> v{0, 0};
+                if (gi < m && gk < k) {
+                    if (AREAL) v = cplx<R>{Ar[gk + (int64_t)gi * lda], R(0)};
+                    else v = conj(A[gk + (int64_t)gi * lda]);
+                }
+                As[kk][i] = v;
+            }
+        }
+        // B tile: op(B)(k0 + kk, n0 + j)
+        if (OPB == OP_N) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                int kk = tid % GB_K, j = tid / GB_K + 16 * q;
+                int gk = k0 + kk, gj = n0 + j;
+                Bs[kk][j] = (gk < k && gj < n) ? B[gk + (int64_t)gj * ldb] : cplx<R>{0, 0};
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                int j = tid % GB_N, kk = tid / GB_N + 4 * q;
+                int gk = k0 + kk, gj = n0 + j;
+                Bs[kk][j] = (gk < k && gj < n) ? conj(B[gj + (int64_t)gk * ldb]) : cplx<R>{0, 0};
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GB_K; ++kk) {
+            cplx<R> a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], b[j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int gi = m0 + ty * 4 + i;
+        if (gi >= m) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int gj = n0 + tx * 4 + j;
+            if (gj >= n) continue;
+            if (EPI == EPI_STORE) C[gi + (int64_t)gj * ldc] = acc[i][j];
+            else if (EPI == EPI_REAL_TO_F64) X[gi + gj * ldx] = (double)((R)acc[i][j].x) * scale;
+            else if (EPI == EPI_REAL_ADD_F64) X[gi + gj * ldx] += (double)acc[i][j].x * scale;
+            else X[gj + gi * ldx] += (double)acc[i][j].x * scale;
+        }
+    }
+}
+
+template <class R, int OPA, int OPB, bool AREAL>
+static cudaError_t dispatch_epi(int epi, dim3 g, cudaStream_t s, int m, int n, int k,
+                                const void *A, int lda, const cplx<R> *B, int ldb, cplx<R> *C,
+                                int ldc, double *X, int64_t ldx, double scale)
+{
+    switch (epi) {
+    case EPI_STORE:
+        cgemm_kernel<R, OPA, OPB, AREAL, EPI_STORE><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale);
+        break;
+    case EPI_REAL_TO_F64:
+        cgemm_kernel<R, OPA, OPB, AREAL, EPI_REAL_TO_F64><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale);
+        break;
+    case EPI_REAL_ADD_F64:
+        cgemm_kernel<R, OPA, OPB, AREAL, EPI_REAL_ADD_F64><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale);
+        break;
+    default:
+        cgemm_kernel<R, OPA, OPB, AREAL, EPI_REAL_ADD_F64_T><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale);
+    }
+    return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_cgemm(int opA, int opB, int m, int n, int k, const void *A, int lda,
+                         bool a_real, const cplx<R> *B, int ldb, int epi, cplx<R> *C, int ldc,
+                         double *X, int64_t ldx, double scale, cudaStream_t s)
+{
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    dim3 g((unsigned)cdiv_i(m, GB_M), (unsigned)cdiv_i(n, GB_N));
+#define SQM_D(OA, OB, AR) return dispatch_epi<R, OA, OB, AR>(epi, g, s, m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale)
+    if (a_real) {
+        if (opA == OP_N && opB == OP_N) SQM_D(OP_N, OP_N, true);
+        if (opA == OP_N && opB == OP_H) SQM_D(OP_N, OP_H, true);
+        if (opA == OP_H && opB == OP_N) SQM_D(OP_H, OP_N, true);
+        return cudaErrorInvalidValue;
+    }
+    if (opA == OP_N && opB == OP_N) SQM_D(OP_N, OP_N, false);
+    if (opA == OP_N && opB == OP_H) SQM_D(OP_N, OP_H, false);
+    if (opA == OP_H && opB == OP_N) SQM_D(OP_H, OP_N, false);
+    SQM_D(OP_H, OP_H, false);
+#undef SQM_D
+}
+
+template cudaError_t launch_cgemm<float>(int, int, int, int, int, const void *, int, bool, const cplx<float> *, int, int, cplx<float> *, int, double *, int64_t, double, cudaStream_t);
+template cudaError_t launch_cgemm<double>(int, int, int, int, int, const void *, int, bool, const cplx<double> *, int, int, cplx<double> *, int, double *, int64_t, double, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// FP64 residual
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(G_THREADS)
+residual_f64_kernel(const double *__restrict__ A, int64_t lda, const double *__restrict__ X,
+                    int64_t ldx, int n, double sc, float *__restrict__ Rhat, int ldr,
+                    double *__restrict__ partials)
+{
+    __shared__ double As[GB_K][GB_M + 1];
+    __shared__ double Bs[GB_K][GB_N + 1];
+    __shared__ double red[G_THREADS / 32];
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    const int m0 = blockIdx.x * GB_M, n0 = blockIdx.y * GB_N;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int k0 = 0; k0 < n; k0 += GB_K) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int i = tid % GB_M, kk = tid / GB_M + 4 * q;
+            int gi = m0 + i, gk = k0 + kk;
+            As[kk][i] = (gi < n && gk < n) ? X[gi + gk * ldx] : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int kk = tid % GB_K, j = tid / GB_K + 16 * q;
+            int gk = k0 + kk, gj = n0 + j;
+            Bs[kk][j] = (gk < n && gj < n) ? X[gk + gj * ldx] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GB_K; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    double ss = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int gi = m0 + ty * 4 + i;
+        if (gi >= n) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int gj = n0 + tx * 4 + j;
+            if (gj >= n) continue;
+            double r = (A[gi + gj * lda] - acc[i][j]) * sc;
+            Rhat[gi + (int64_t)gj * ldr] = (float)r;
+            ss = fma(r, r, ss);
+        }
+    }
+    ss = warp_sum(ss);
+    if ((tid & 31) == 0) red[tid >> 5] = ss;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < G_THREADS / 32; ++w) t += red[w];
+        partials[blockIdx.x + blockIdx.y * gridDim.x] = t;
+    }
+}
+
+cudaError_t launch_residual_f64(const double *A, int64_t lda, const double *X, int64_t ldx,
+                                int n, int e, float *Rhat, int ldr, double *partials,
+                                int *nparts, cudaStream_t s)
+{
+    dim3 g((unsigned)cdiv_i(n, GB_M), (unsigned)cdiv_i(n, GB_N));
+    *nparts = (int)(g.x * g.y);
+    if (n <= 0) return cudaSuccess;
+    residual_f64_kernel<<<g, G_THREADS, 0, s>>>(A, lda, X, ldx, n, ldexp(1.0, -2 * e), Rhat, ldr, partials);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP64 adjoint residual G - (X^T Y + Y X^T)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(G_THREADS)
+adjoint_residual_f64_kernel(const double *__restrict__ G, int64_t ldg, const double *__restrict__ X,
+                            int64_t ldx, const double *__restrict__ Y, int64_t ldy, int n,
+                            float *__restrict__ Rhat, int ldr, double *__restrict__ partials)
+{
+    __shared__ double A1[GB_K][GB_M + 1];   // X^T(i, k) = X(k, i)
+    __shared__ double B1[GB_K][GB_N + 1];   // Y(k, j)
+    __shared__ double A2[GB_K][GB_M + 1];   // Y(i, k)
+    __shared__ double B2[GB_K][GB_N + 1];   // X^T(k, j) = X(j, k)
+    __shared__ double red[G_THREADS / 32];
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    const int m0 = blockIdx.x * GB_M, n0 = blockIdx.y * GB_N;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int k0 = 0; k0 < n; k0 += GB_K) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int kk = tid % GB_K, i = tid / GB_K + 16 * q;
+            int gi = m0 + i, gk = k0 + kk, gj = n0 + i;
+            A1[kk][i] = (gi < n && gk < n) ? X[gk + gi * ldx] : 0.0;
+            B1[kk][i] = (gj < n && gk < n) ? Y[gk + gj * ldy] : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int i = tid % GB_M, kk = tid / GB_M + 4 * q;
+            int gi = m0 + i, gk = k0 + kk, gj = n0 + i;
+            A2[kk][i] = (gi < n && gk < n) ? Y[gi + gk * ldy] : 0.0;
+            B2[kk][i] = (gj < n && gk < n) ? X[gj + gk * ldx] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GB_K; ++kk) {
+            double a[4], b[4], c[4], d[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { a[i] = A1[kk][ty * 4 + i]; c[i] = A2[kk][ty * 4 + i]; }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) { b[j] = B1[kk][tx * 4 + j]; d[j] = B2[kk][tx * 4 + j]; }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], fma(c[i], d[j], acc[i][j]));
+        }
+        __syncthreads();
+    }
+    double ss = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int gi = m0 + ty * 4 + i;
+        if (gi >= n) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int gj = n0 + tx * 4 + j;
+            if (gj >= n) continue;
+            double r = G[gi + gj * ldg] - acc[i][j];
+            Rhat[gi + (int64_t)gj * ldr] = (float)r;
+            ss = fma(r, r, ss);
+        }
+    }
+    ss = warp_sum(ss);
+    if ((tid & 31) == 0) red[tid >> 5] = ss;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < G_THREADS / 32; ++w) t += red[w];
+        partials[blockIdx.x + blockIdx.y * gridDim.x] = t;
+    }
+}
+
+cudaError_t launch_adjoint_residual_f64(const double *G, int64_t ldg, const double *X, int64_t ldx,
+                                        const double *Y, int64_t ldy, int n, float *Rhat, int ldr,
+                                        double *partials, int *nparts, cudaStream_t s)
+{
+    dim3 g((unsigned)cdiv_i(n, GB_M), (unsigned)cdiv_i(n, GB_N));
+    *nparts = (int)(g.x * g.y);
+    if (n <= 0) return cudaSuccess;
+    adjoint_residual_f64_kernel<<<g, G_THREADS, 0, s>>>(G, ldg, X, ldx, Y, ldy, n, Rhat, ldr, partials);
+    return cudaGetLastError();
+}
+
+__global__ void sum_partials_kernel(const double *__restrict__ p, int np, double *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < np; ++i) s += p[i];
+        *out = sqrt(s);
+    }
+}
+
+cudaError_t launch_sum_partials(const double *partials, int np, double *d_out, cudaStream_t s)
+{
+    sum_partials_kernel<<<1, 32, 0, s>>>(partials, np, d_out);
+    return cudaGetLastError();
+}
+
+}  // namespace sqm

@@ -1,0 +1,81 @@
+// internal.h -- launchers shared between the translation units of the
+// library.  Host-side declarations only; every launcher enqueues work on the
+// given stream and returns a cudaError_t from the launch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace sqm {
+
+// One matrix of a (possibly batched) Schur stage.  All arrays are device
+// memory, column-major with leading dimension ld.
+template <class R>
+struct SchurDesc {
+    cplx<R> *T;      // in: A_s, out: upper triangular T (n x n)
+    cplx<R> *Q;      // out: unitary Schur vectors (n x n)
+    cplx<R> *v;      // scratch: Householder vector (>= n entries)
+    R *beta;         // scratch: reflector scalars [beta, |x|, phase.x, phase.y]
+    int *status;     // out: 0 / 3 (iteration cap)
+    int *counters;   // out: [0] sweeps, [1..2] rotations (int64 split lo/hi)
+    int n;
+    int ld;
+};
+
+// ---- scaling / norms (scale.cu) ----
+// Deterministic ||A||_F: partials[nblk] then finalize; writes norm, e.
+cudaError_t launch_norm_scale(const double *A, int64_t n, int64_t lda, double *partials,
+                              int nblk, double *d_norm, int *d_e, cudaStream_t s);
+template <class R>
+cudaError_t launch_cast_scaled(const double *A, int64_t n, int64_t lda, const int *d_e,
+                               cplx<R> *As, int64_t ldas, cudaStream_t s);
+template <class R>
+cudaError_t launch_cast_scaled_real(const double *A, int64_t n, int64_t lda, const int *d_e,
+                                    R *As, int64_t ldas, cudaStream_t s);
+
+// ---- Schur stage (schur.cu) ----
+template <class R>
+cudaError_t launch_hessenberg(const SchurDesc<R> *d_desc, int batch, int nmax,
+                              int ctas_per_matrix, cudaStream_t s);
+template <class R>
+cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, cudaStream_t s);
+
+// ---- triangular solvers (trisolve.cu) ----
+// S = T^{1/2}, blocked; status receives 2 on a zero denominator or an
+// eigenvalue on the closed negative real axis.
+template <class R>
+cudaError_t launch_trisqrt(const cplx<R> *T, int ldt, cplx<R> *S, int lds, int n, int blks,
+                           int *d_status, cudaStream_t s);
+// S Y + Y St = C (C overwritten by Y), blocked wavefront.
+template <class R>
+cudaError_t launch_rtrsyl(const cplx<R> *S, int lds, int m, const cplx<R> *St, int ldst, int nn,
+                          cplx<R> *C, int ldc, int blks, int *d_status, cudaStream_t s);
+
+// ---- dense products (gemm.cu) ----
+enum OpT { OP_N = 0, OP_H = 1 };
+enum Epi { EPI_STORE = 0, EPI_REAL_TO_F64 = 1, EPI_REAL_ADD_F64 = 2, EPI_REAL_ADD_F64_T = 3 };
+// C = op(A) op(B) (m x n, inner k).  A complex or (a_real) real R.
+// EPI_STORE:        C (complex) = result
+// EPI_REAL_TO_F64:  X[i,j] = double(R(Re(result))) * scale
+// EPI_REAL_ADD_F64: X[i,j] += double(Re(result)) * scale
+// EPI_REAL_ADD_F64_T: X[j,i] += double(Re(result)) * scale (transposed)
+template <class R>
+cudaError_t launch_cgemm(int opA, int opB, int m, int n, int k, const void *A, int lda,
+                         bool a_real, const cplx<R> *B, int ldb, int epi, cplx<R> *C, int ldc,
+                         double *X, int64_t ldx, double scale, cudaStream_t s);
+// R = (A - X X) * 4^-e in FP64; Rhat = fl32(R); partial sums of squares per
+// CTA into partials (count returned through *nparts).
+cudaError_t launch_residual_f64(const double *A, int64_t lda, const double *X, int64_t ldx,
+                                int n, int e, float *Rhat, int ldr, double *partials,
+                                int *nparts, cudaStream_t s);
+// Adjoint residual Res = G - (X^T Y + Y X^T) in FP64; Rhat = fl32(Res) and
+// per-CTA partial sums of |Res|^2.
+cudaError_t launch_adjoint_residual_f64(const double *G, int64_t ldg, const double *X, int64_t ldx,
+                                        const double *Y, int64_t ldy, int n, float *Rhat, int ldr,
+                                        double *partials, int *nparts, cudaStream_t s);
+// norm = sqrt(sum(partials[0:np])) in a fixed order
+cudaError_t launch_sum_partials(const double *partials, int np, double *d_out, cudaStream_t s);
+
+}  // namespace sqm

@@ -1,0 +1,665 @@
+// spd.cu -- symmetric positive definite path (Algorithm 3).
+//
+// Spectral decomposition A_s = V diag(lam) V^T (Algorithm 3, step 1):
+//   1. Householder tridiagonalisation in the storage precision R (FP32 for
+//      the mixed method): three launches per column -- reflector + product
+//      p = beta A v (one warp per column of the trailing block), the
+//      symmetric rank-2 update A -= v w^T + w v^T with w = p - (beta/2)(v.p)
+//      v, and Q <- Q (I - beta v v^T);
+//   2. eigenvalues of the tridiagonal matrix by bisection on Sturm counts,
+//      one thread per eigenvalue, in FP64;
+//   3. eigenvectors of the tridiagonal matrix from twisted factorisations
+//      T - lam I = L D+ L^T = U D- U^T (one thread per eigenvalue, FP64):
+//      with r = argmin |D+_r + D-_r - (d_r - lam)|, z_r = 1,
+//      z_i = -(e_i / D+_i) z_{i+1} above r, z_{i+1} = -(e_i / D-_{i+1}) z_i
+//      below r, normalised;
+//   4. V = Q Z in R.
+// Steps 2-3 are O(n^2) work; the O(n^3) steps 1 and 4 run in R.
+//
+// Refinement (Algorithm 3, steps 4-12): FP64 symmetric residual, then
+// Y = (V^T Rhat V) ./ (s_i + s_j) with the division fused into the second
+// product, X += 2^e V Y V^T with a mirrored FP64 epilogue (X stays exactly
+// symmetric).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "handle.h"
+#include "spd_internal.h"
+
+namespace sqm {
+
+static constexpr int kTriThreads2 = 256;
+
+// reflector for x = A(k+1:n, k) (real): v = x + sign(x0) ||x|| e1,
+// beta = 2 / ||v||^2, P x = -sign(x0) ||x|| e1
+template <class R>
+__device__ void real_reflector(const R *__restrict__ col, int m, R *vsh, R *scal /* beta, xn, sign */)
+{
+    __shared__ R red[2][kTriThreads2 / 32];
+    R t_all = 0, t_tail = 0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        R x = col[i];
+        vsh[i] = x;
+        t_all = fma(x, x, t_all);
+        if (i > 0) t_tail = fma(x, x, t_tail);
+    }
+    t_all = warp_sum(t_all);
+    t_tail = warp_sum(t_tail);
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = t_all; red[1][threadIdx.x >> 5] = t_tail; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        R xn2 = 0, tail2 = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { xn2 += red[0][q]; tail2 += red[1][q]; }
+        if (tail2 == R(0) || m <= 0) {
+            scal[0] = 0; scal[1] = 0; scal[2] = 1;
+        } else {
+            R xn = sqrt(xn2);
+            R x0 = vsh[0];
+            R sg = (x0 >= R(0)) ? R(1) : R(-1);
+            R v0 = x0 + sg * xn;
+            vsh[0] = v0;
+            scal[0] = R(2) / (v0 * v0 + tail2);
+            scal[1] = xn;
+            scal[2] = sg;
+        }
+    }
+    __syncthreads();
+}
+
+template <class R>
+__global__ void __launch_bounds__(kTriThreads2)
+tri_symv_kernel(const R *__restrict__ A, int n, int ld, int k, R *__restrict__ wsv,
+                R *__restrict__ wsp, R *__restrict__ wss)
+{
+    extern __shared__ unsigned char smraw[];
+    R *vsh = reinterpret_cast<R *>(smraw);
+    __shared__ R scal[3];
+    const int m = n - k - 1;
+    real_reflector<R>(A + (k + 1) + (int64_t)k * ld, m, vsh, scal);
+    const R beta = scal[0];
+    if (blockIdx.x == 0) {
+        for (int i = threadIdx.x; i < m; i += blockDim.x) wsv[i] = vsh[i];
+        if (threadIdx.x < 3) wss[threadIdx.x] = scal[threadIdx.x];
+    }
+    if (beta == R(0)) return;
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    // p_j = beta * sum_i A(k+1+i, k+1+j) v_i  (column j of the symmetric block)
+    for (int j = gw; j < m; j += nw) {
+        const R *c = A + (k + 1) + (int64_t)(k + 1 + j) * ld;
+        R acc = 0;
+        for (int i = lane; i < m; i += 32) acc = fma(c[i], vsh[i], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) wsp[j] = beta * acc;
+    }
+}
+
+template <class R>
+__global__ void __launch_bounds__(kTriThreads2)
+tri_update_kernel(R *__restrict__ A, int n, int ld, int k, const R *__restrict__ wsv,
+                  const R *__restrict__ wsp, const R *__restrict__ wss)
+{
+    extern __shared__ unsigned char smraw[];
+    const int m = n - k - 1;
+    R *vsh = reinterpret_cast<R *>(smraw);
+    R *wsh = vsh + m;
+    __shared__ R red[kTriThreads2 / 32];
+    __shared__ R s_K;
+    const R beta = wss[0];
+    if (beta == R(0)) return;
+    R acc = 0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        R v = wsv[i], p = wsp[i];
+        vsh[i] = v;
+        wsh[i] = p;
+        acc = fma(v, p, acc);
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        R t = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+        s_K = R(0.5) * beta * t;
+    }
+    __syncthreads();
+    const R K = s_K;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) wsh[i] = fma(-K, vsh[i], wsh[i]);
+    __syncthreads();
+    if (blockIdx.x == 0) {
+        const R xn = wss[1], sg = wss[2];
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            R val = (i == 0) ? -sg * xn : R(0);
+            A[(k + 1 + i) + (int64_t)k * ld] = val;
+            A[k + (int64_t)(k + 1 + i) * ld] = val;
+        }
+    }
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int j = gw; j < m; j += nw) {
+        R *c = A + (k + 1) + (int64_t)(k + 1 + j) * ld;
+        const R vj = vsh[j], wj = wsh[j];
+        for (int i = lane; i < m; i += 32) c[i] = fma(-vsh[i], wj, fma(-wsh[i], vj, c[i]));
+    }
+}
+
+// Q(:, k+1:n) <- Q(:, k+1:n) - beta (Q v) v^T ; blockDim (32, 8)
+template <class R>
+__global__ void __launch_bounds__(kTriThreads2)
+tri_q_kernel(R *__restrict__ Q, int n, int ldq, int k, const R *__restrict__ wsv,
+             const R *__restrict__ wss)
+{
+    extern __shared__ unsigned char smraw[];
+    R *vsh = reinterpret_cast<R *>(smraw);
+    __shared__ R part[8][33];
+    const int m = n - k - 1;
+    const R beta = wss[0];
+    if (beta == R(0)) return;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    for (int i = tid; i < m; i += 256) vsh[i] = wsv[i];
+    __syncthreads();
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const bool valid = i < n;
+    R acc = 0;
+    if (valid)
+        for (int l = threadIdx.y; l < m; l += 8) acc = fma(Q[i + (int64_t)(k + 1 + l) * ldq], vsh[l], acc);
+    part[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    R u = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) u += part[q][threadIdx.x];
+    u *= beta;
+    if (valid)
+        for (int l = threadIdx.y; l < m; l += 8) {
+            R &e = Q[i + (int64_t)(k + 1 + l) * ldq];
+            e = fma(-u, vsh[l], e);
+        }
+}
+
+template <class R>
+__global__ void eye_real_kernel(R *Q, int n, int ldq)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)n * n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int i = (int)(t % n), j = (int)(t / n);
+        Q[i + (int64_t)j * ldq] = (R)(i == j);
+    }
+}
+
+template <class R>
+cudaError_t launch_tridiag(R *A, int n, int ld, R *Q, int ldq, R *ws, cudaStream_t s)
+{
+    R *wsv = ws, *wsp = ws + n, *wss = ws + 2 * n;
+    size_t sm1 = (size_t)std::max(n, 1) * sizeof(R);
+    size_t sm2 = 2 * sm1;
+    cudaError_t err;
+    if (sm2 > 48 * 1024) {
+        if ((err = cudaFuncSetAttribute(tri_symv_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1))) return err;
+        if ((err = cudaFuncSetAttribute(tri_update_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2))) return err;
+        if ((err = cudaFuncSetAttribute(tri_q_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1))) return err;
+    }
+    eye_real_kernel<R><<<(int)std::min<int64_t>(cdiv_i((int64_t)n * n, 256), 152 * 8), 256, 0, s>>>(Q, n, ldq);
+    for (int k = 0; k + 2 < n; ++k) {
+        int m = n - k - 1;
+        int ctas = (int)std::min<int64_t>(cdiv_i(m, kTriThreads2 / 32), 304);
+        tri_symv_kernel<R><<<ctas, kTriThreads2, sm1, s>>>(A, n, ld, k, wsv, wsp, wss);
+        tri_update_kernel<R><<<ctas, kTriThreads2, sm2, s>>>(A, n, ld, k, wsv, wsp, wss);
+        tri_q_kernel<R><<<(int)cdiv_i(n, 32), dim3(32, 8), sm1, s>>>(Q, n, ldq, k, wsv, wss);
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_tridiag<float>(float *, int, int, float *, int, float *, cudaStream_t);
+template cudaError_t launch_tridiag<double>(double *, int, int, double *, int, double *, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// tridiagonal eigensolver in FP64
+// ---------------------------------------------------------------------------
+// d, e, e^2, Gershgorin interval [gl, gu] and the pivot floor
+template <class R>
+__global__ void tri_extract_kernel(const R *__restrict__ A, int n, int ld, double *d, double *e,
+                                   double *e2, double *bounds)
+{
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        d[i] = (double)A[i + (int64_t)i * ld];
+        double ei = (i + 1 < n) ? (double)A[(i + 1) + (int64_t)i * ld] : 0.0;
+        e[i] = ei;
+        e2[i] = ei * ei;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double gl = INFINITY, gu = -INFINITY, emax2 = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double r = fabs(e[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0);
+            gl = fmin(gl, d[i] - r);
+            gu = fmax(gu, d[i] + r);
+            emax2 = fmax(emax2, e2[i]);
+        }
+        double w = fmax(fabs(gl), fabs(gu));
+        bounds[0] = gl - 4.0 * 1.1102230246251565e-16 * w * n - 1e-300;
+        bounds[1] = gu + 4.0 * 1.1102230246251565e-16 * w * n + 1e-300;
+        bounds[2] = 2.2250738585072014e-308 * fmax(1.0, emax2);
+    }
+}
+
+// number of eigenvalues of the tridiagonal matrix smaller than x
+__device__ __forceinline__ int sturm_count(const double *__restrict__ d, const double *__restrict__ e2,
+                                           int n, double x, double pivmin)
+{
+    double q = d[0] - x;
+    if (fabs(q) < pivmin) q = -pivmin;
+    int c = q < 0.0;
+    for (int i = 1; i < n; ++i) {
+        q = (d[i] - x) - e2[i - 1] / q;
+        if (fabs(q) < pivmin) q = -pivmin;
+        c += q < 0.0;
+    }
+    return c;
+}
+
+__global__ void bisect_kernel(const double *__restrict__ d, const double *__restrict__ e2, int n,
+                              const double *__restrict__ bounds, double *__restrict__ lam)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double lo = bounds[0], hi = bounds[1];
+    const double pivmin = bounds[2];
+    for (int it = 0; it < 160; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (hi - lo <= 2.0 * 1.1102230246251565e-16 * fmax(fabs(lo), fabs(hi)) + pivmin) break;
+        if (sturm_count(d, e2, n, mid, pivmin) > j) hi = mid;
+        else lo = mid;
+    }
+    lam[j] = 0.5 * (lo + hi);
+}
+
+// twisted factorisation eigenvectors for eigenvalues [j0, j0 + cnt);
+// Dp, Dm: scratch [i * cnt + (j - j0)] (coalesced across threads);
+// ZT row j (ld n) receives eigenvector j
+__global__ void twisted_kernel(const double *__restrict__ d, const double *__restrict__ e,
+                               const double *__restrict__ e2, int n,
+                               const double *__restrict__ bounds, const double *__restrict__ lam,
+                               int j0, int cnt, double *__restrict__ Dp, double *__restrict__ Dm,
+                               double *__restrict__ ZT)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    const int j = j0 + t;
+    const double x = lam[j];
+    const double pivmin = bounds[2];
+    // backward: D-_{n-1} = d_{n-1} - x; D-_i = d_i - x - e_i^2 / D-_{i+1}
+    double q = d[n - 1] - x;
+    if (fabs(q) < pivmin) q = -pivmin;
+    Dm[(int64_t)(n - 1) * cnt + t] = q;
+    for (int i = n - 2; i >= 0; --i) {
+        q = (d[i] - x) - e2[i] / q;
+        if (fabs(q) < pivmin) q = -pivmin;
+        Dm[(int64_t)i * cnt + t] = q;
+    }
+    // forward: D+_0 = d_0 - x; D+_i = d_i - x - e_{i-1}^2 / D+_{i-1};
+    // twist index r minimises |gamma_r| = |D+_r + D-_r - (d_r - x)|
+    double p = d[0] - x;
+    if (fabs(p) < pivmin) p = -pivmin;
+    Dp[t] = p;
+    int r = 0;
+    double gbest = fabs(p + Dm[t] - (d[0] - x));
+    for (int i = 1; i < n; ++i) {
+        p = (d[i] - x) - e2[i - 1] / p;
+        if (fabs(p) < pivmin) p = -pivmin;
+        Dp[(int64_t)i * cnt + t] = p;
+        double g = fabs(p + Dm[(int64_t)i * cnt + t] - (d[i] - x));
+        if (g < gbest) { gbest = g; r = i; }
+    }
+    // ZT holds Z^T column-major: component i of eigenvector j at ZT[j + i n],
+    // so the threads of a warp (consecutive j) write consecutive addresses
+    ZT[j + (int64_t)r * n] = 1.0;
+    double nrm2 = 1.0;
+    double zi = 1.0;
+    for (int i = r - 1; i >= 0; --i) {
+        zi = -(e[i] / Dp[(int64_t)i * cnt + t]) * zi;
+        ZT[j + (int64_t)i * n] = zi;
+        nrm2 = fma(zi, zi, nrm2);
+    }
+    zi = 1.0;
+    for (int i = r; i + 1 < n; ++i) {
+        zi = -(e[i] / Dm[(int64_t)(i + 1) * cnt + t]) * zi;
+        ZT[j + (int64_t)(i + 1) * n] = zi;
+        nrm2 = fma(zi, zi, nrm2);
+    }
+    const double inv = 1.0 / sqrt(nrm2);
+    for (int i = 0; i < n; ++i) ZT[j + (int64_t)i * n] *= inv;
+}
+
+template <class R>
+cudaError_t launch_tridiag_eig(const R *A, int n, int ld, double *lam, double *ZT,
+                               double *scratch, int chunk, cudaStream_t s)
+{
+    double *d = scratch, *e = d + n, *e2 = e + n, *bounds = e2 + n;
+    double *Dp = bounds + 8;
+    double *Dm = Dp + (size_t)n * chunk;
+    tri_extract_kernel<R><<<1, 256, 0, s>>>(A, n, ld, d, e, e2, bounds);
+    bisect_kernel<<<(int)cdiv_i(n, 64), 64, 0, s>>>(d, e2, n, bounds, lam);
+    for (int j0 = 0; j0 < n; j0 += chunk) {
+        int cnt = std::min(chunk, n - j0);
+        twisted_kernel<<<(int)cdiv_i(cnt, 64), 64, 0, s>>>(d, e, e2, n, bounds, lam, j0, cnt, Dp, Dm, ZT);
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_tridiag_eig<float>(const float *, int, int, double *, double *, double *, int, cudaStream_t);
+template cudaError_t launch_tridiag_eig<double>(const double *, int, int, double *, double *, double *, int, cudaStream_t);
+
+// small elementwise helpers
+// ZT <- 1.5 ZT - 0.5 P  (one Newton-Schulz step towards orthogonality:
+// Z <- Z (3 I - Z^T Z) / 2, written for Z^T)
+__global__ void newton_schulz_combine_kernel(double *__restrict__ ZT, const double *__restrict__ P, int64_t count)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
+        ZT[t] = fma(-0.5, P[t], 1.5 * ZT[t]);
+}
+
+template <class R>
+__global__ void cast_from_f64_kernel(const double *__restrict__ src, R *__restrict__ dst, int64_t count)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
+        dst[t] = (R)src[t];
+}
+
+// s_i = sqrt(lam_i) (lam rounded to R first); status 2 for lam_i <= 0
+template <class R>
+__global__ void sqrt_eig_kernel(const double *__restrict__ lam, R *__restrict__ lamr, R *__restrict__ s,
+                                int n, int *status)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        R l = (R)lam[i];
+        lamr[i] = l;
+        if (!(l > R(0))) { atomicExch(status, 2); s[i] = R(1); }
+        else s[i] = sqrt(l);
+    }
+}
+
+// W(:, j) = V(:, j) * s_j
+template <class R>
+__global__ void scale_cols_kernel(const R *__restrict__ V, const R *__restrict__ s, R *__restrict__ W, int n)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)n * n; t += (int64_t)gridDim.x * blockDim.x)
+        W[t] = V[t] * s[t / n];
+}
+
+static int grid1(int64_t count)
+{
+    return (int)std::max<int64_t>(1, std::min<int64_t>(cdiv_i(count, 256), 152 * 8));
+}
+
+}  // namespace sqm
+
+using namespace sqm;
+
+// ---------------------------------------------------------------------------
+// spectral decomposition driver: As (real R, n x n) -> V (R), lam (R), s (R)
+// ---------------------------------------------------------------------------
+namespace {
+
+template <class R>
+struct SpdWork {
+    R *As, *V, *lamr, *s, *W, *Y, *Qh, *vecws;
+    double *lam, *ZT, *eigscratch;
+    float *Rhat;
+    double *xsave;   // FP64 copy of X for the adjoint
+    double *dscal;   // [0] norm, [1] rnorm, [2..] partials
+    int *iscal;      // [0] e, [1] status
+    int chunk;
+};
+
+template <class R>
+size_t spd_bytes(int64_t n, int chunk)
+{
+    size_t nn = (size_t)n * n;
+    int64_t nb = (n + 63) / 64;
+    size_t np = (size_t)std::max<int64_t>(nb * nb, 2048) + 8;
+    return Carve::round(np * sizeof(double)) + 256 + 3 * Carve::round(nn * sizeof(R)) +
+           Carve::round(nn * sizeof(float)) + Carve::round(nn * sizeof(double)) +
+           Carve::round((2 * (size_t)n * chunk + 3 * n + 8) * sizeof(double)) +
+           Carve::round(n * sizeof(double)) + 2 * Carve::round(n * sizeof(R)) +
+           Carve::round((2 * n + 8) * sizeof(R)) + 8192;
+}
+
+template <class R>
+int spd_carve(sqrtm_handle_t h, int64_t n, SpdWork<R> *w)
+{
+    int chunk = (int)std::min<int64_t>(n, 2048);
+    size_t nn = (size_t)n * n;
+    // factors V, lamr, s persist for the adjoint / reuse
+    size_t fbytes = Carve::round(nn * sizeof(R)) + 2 * Carve::round(n * sizeof(R)) +
+                    Carve::round(nn * sizeof(double)) + 1024;
+    if (ensure(h->fact, fbytes) || ensure(h->ws, spd_bytes<R>(n, chunk))) return 7;
+    Carve cf(h->fact.p);
+    w->V = cf.take<R>(nn);
+    w->lamr = cf.take<R>(n);
+    w->s = cf.take<R>(n);
+    w->xsave = cf.take<double>(nn);
+    Carve c(h->ws.p);
+    int64_t nb = (n + 63) / 64;
+    size_t np = (size_t)std::max<int64_t>(nb * nb, 2048) + 8;
+    w->dscal = c.take<double>(np);
+    w->iscal = c.take<int>(8);
+    w->As = c.take<R>(nn);
+    w->W = c.take<R>(nn);
+    w->Qh = c.take<R>(nn);
+    w->Y = w->As;  // As is dead after the tridiagonalisation
+    w->Rhat = c.take<float>(nn);
+    w->ZT = c.take<double>(nn);
+    w->eigscratch = c.take<double>(2 * (size_t)n * chunk + 3 * n + 8);
+    w->lam = c.take<double>(n);
+    w->vecws = c.take<R>(2 * n + 8);
+    w->chunk = chunk;
+    return 0;
+}
+
+// A_s (already in w->As) -> V, lamr, s; returns status
+template <class R>
+int spd_decompose(sqrtm_handle_t h, int64_t n, SpdWork<R> &w)
+{
+    cudaStream_t s = h->stream;
+    const int ni = (int)n;
+    if (launch_tridiag<R>(w.As, ni, ni, w.Qh, ni, w.vecws, s)) return 7;
+    if (launch_tridiag_eig<R>(w.As, ni, ni, w.lam, w.ZT, w.eigscratch, w.chunk, s)) return 7;
+    if (sizeof(R) == sizeof(double)) {
+        // Eigenvectors of close eigenvalues from independent twisted
+        // factorisations are orthogonal only to O(u ||T|| / gap); one
+        // Newton-Schulz step restores orthogonality to working precision in
+        // the FP64 method (in the FP32 method the rounding to FP32 dominates).
+        // (R is double here, so W and As hold n x n doubles; As is free once
+        // launch_tridiag_eig has read the tridiagonal entries.)
+        double *M = (double *)w.W, *P = (double *)w.As;
+        if (launch_rgemm<double>(0, 1, ni, ni, ni, w.ZT, ni, w.ZT, ni, RG_STORE, M, ni, nullptr, nullptr, 0, 0.0, s)) return 7;
+        if (launch_rgemm<double>(0, 0, ni, ni, ni, M, ni, w.ZT, ni, RG_STORE, P, ni, nullptr, nullptr, 0, 0.0, s)) return 7;
+        newton_schulz_combine_kernel<<<grid1((int64_t)n * n), 256, 0, s>>>(w.ZT, P, (int64_t)n * n);
+    }
+    // V = Qh Z = Qh (ZT)^T
+    R *ZTr = w.W;
+    cast_from_f64_kernel<R><<<grid1((int64_t)n * n), 256, 0, s>>>(w.ZT, ZTr, (int64_t)n * n);
+    if (launch_rgemm<R>(0, 1, ni, ni, ni, w.Qh, ni, ZTr, ni, RG_STORE, w.V, ni, nullptr, nullptr, 0, 0.0, s)) return 7;
+    sqrt_eig_kernel<R><<<grid1(n), 256, 0, s>>>(w.lam, w.lamr, w.s, ni, w.iscal + 1);
+    return cudaGetLastError() ? 7 : 0;
+}
+
+template <class R>
+int fetch_scalar(sqrtm_handle_t h, void *dst, const void *src, size_t bytes)
+{
+    if (cudaMemcpyAsync(h->staging.p, src, bytes, cudaMemcpyDeviceToHost, h->stream)) return 7;
+    if (cudaStreamSynchronize(h->stream)) return 7;
+    memcpy(dst, h->staging.p, bytes);
+    return 0;
+}
+
+template <class R>
+int spd_common(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, double tol, double *dX,
+               int64_t ldx, const sqrtm_opts &o, sqrtm_info *info, bool refine)
+{
+    cudaStream_t s = h->stream;
+    const int ni = (int)n;
+    SpdWork<R> w;
+    if (int rc = spd_carve<R>(h, n, &w)) return rc;
+    h->fact_n = -1;
+    if (cudaMemsetAsync(w.iscal, 0, 8 * sizeof(int), s)) return 7;
+    if (cudaEventRecord(h->ev[0], s)) return 7;
+    if (launch_norm_scale(dA, n, lda, w.dscal + 2, (int)std::min<int64_t>(n, 1024), w.dscal, w.iscal, s)) return 7;
+    if (launch_cast_scaled_real<R>(dA, n, lda, w.iscal, w.As, n, s)) return 7;
+    double norm_a = 0.0;
+    int e = 0;
+    if (fetch_scalar<R>(h, &norm_a, w.dscal, sizeof(double)) || fetch_scalar<R>(h, &e, w.iscal, sizeof(int))) return 7;
+    if (info) { info->norm_a = norm_a; info->scale_exponent = e; info->kind_used = SQRTM_KIND_SPD; }
+    if (!isfinite(norm_a)) return 5;
+    if (norm_a == 0.0) return 2;
+    if (int rc = spd_decompose<R>(h, n, w)) return rc;
+    if (cudaEventRecord(h->ev[1], s)) return 7;
+    // X_0 = V diag(s) V^T, rounded to R, times 2^e (mirrored)
+    scale_cols_kernel<R><<<grid1((int64_t)n * n), 256, 0, s>>>(w.V, w.s, w.W, ni);
+    if (launch_rgemm<R>(0, 1, ni, ni, ni, w.W, ni, w.V, ni, RG_SYM_TO_F64, nullptr, 0, nullptr, dX, ldx, ldexp(1.0, e), s)) return 7;
+    if (cudaEventRecord(h->ev[2], s)) return 7;
+    int st = 0;
+    if (fetch_scalar<R>(h, &st, w.iscal + 1, sizeof(int))) return 7;
+    if (info) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]); info->ms_schur = ms;
+        cudaEventElapsedTime(&ms, h->ev[1], h->ev[2]); info->ms_trisqrt = ms;
+    }
+    if (st) return st;
+    if (!refine) return 0;
+    const double norm_as = ldexp(norm_a, -2 * e);
+    const bool fixed = o.steps >= 0;
+    const int max_corr = fixed ? o.steps : o.maxit + 1;
+    int status = 0, applied = 0, grew = 0;
+    double prev = INFINITY;
+    for (int k = 0;; ++k) {
+        if (fixed && k >= max_corr) break;
+        int np = 0;
+        if (launch_residual_sym_f64(dA, lda, dX, ldx, ni, e, w.Rhat, ni, w.dscal + 2, &np, s)) return 7;
+        if (launch_sum_partials(w.dscal + 2, np, w.dscal + 1, s)) return 7;
+        if (!fixed) {
+            double rn = 0.0;
+            if (fetch_scalar<R>(h, &rn, w.dscal + 1, sizeof(double))) return 7;
+            double rel = rn / norm_as;
+            if (info && info->history_len < SQRTM_MAX_HISTORY) info->history[info->history_len++] = rel;
+            if (!isfinite(rel)) { status = 4; break; }
+            if (rel <= tol) { status = 0; break; }
+            if (k >= max_corr) { status = 1; break; }
+            grew = (rn > prev) ? grew + 1 : 0;
+            if (grew >= 2) { status = 4; break; }
+            prev = rn;
+        }
+        // Y = (V^T Rhat V) ./ (s_i + s_j);  X += 2^e V Y V^T
+        if (launch_rgemm<float>(0, 0, ni, ni, ni, w.Rhat, ni, (const float *)w.V, ni, RG_STORE, (float *)w.W, ni, nullptr, nullptr, 0, 0.0, s)) return 7;
+        if (launch_rgemm<float>(1, 0, ni, ni, ni, (const float *)w.V, ni, (const float *)w.W, ni, RG_DIAG_SOLVE, (float *)w.Y, ni, (const float *)w.s, nullptr, 0, 0.0, s)) return 7;
+        if (launch_rgemm<float>(0, 0, ni, ni, ni, (const float *)w.V, ni, (const float *)w.Y, ni, RG_STORE, (float *)w.W, ni, nullptr, nullptr, 0, 0.0, s)) return 7;
+        if (launch_rgemm<float>(0, 1, ni, ni, ni, (const float *)w.W, ni, (const float *)w.V, ni, RG_SYM_ADD_F64, nullptr, 0, nullptr, dX, ldx, ldexp(1.0, e), s)) return 7;
+        ++applied;
+    }
+    if (cudaEventRecord(h->ev[3], s)) return 7;
+    if (status == 0 || status == 1) {
+        if (cudaMemcpy2DAsync(w.xsave, n * sizeof(double), dX, ldx * sizeof(double), n * sizeof(double), n,
+                              cudaMemcpyDeviceToDevice, s)) return 7;
+        h->fact_n = n; h->fact_kind = SQRTM_KIND_SPD; h->fact_e = e; h->fact_norm = norm_a;
+        h->fact_q = w.V; h->fact_s = w.s; h->fact_x = w.xsave;
+    }
+    if (cudaStreamSynchronize(s)) return 7;
+    if (info) {
+        info->iterations = applied;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]); info->ms_refine = ms;
+    }
+    return status;
+}
+
+}  // namespace
+
+int spd_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, double tol, double *dX,
+             int64_t ldx, const sqrtm_opts &o, sqrtm_info *info)
+{
+    return spd_common<float>(h, dA, n, lda, tol, dX, ldx, o, info, true);
+}
+
+int spd_schur_fp64(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, double *dX,
+                   int64_t ldx, const sqrtm_opts &o, sqrtm_info *info)
+{
+    return spd_common<double>(h, dA, n, lda, 0.0, dX, ldx, o, info, false);
+}
+
+// ---------------------------------------------------------------------------
+// step-level entry points of Algorithm 3
+// ---------------------------------------------------------------------------
+extern "C" int sqrtm_step_syevd(sqrtm_handle_t h, const void *dAs, void *dV, void *dlam, int64_t n,
+                                int fp64)
+{
+    if (!h) return -1;
+    if (n < 0) return -5;
+    if (n == 0) return 0;
+    if (n > 46340) return -5;
+    auto run = [&](auto tag) -> int {
+        using R = decltype(tag);
+        SpdWork<R> w;
+        if (int rc = spd_carve<R>(h, n, &w)) return rc;
+        if (cudaMemsetAsync(w.iscal, 0, 8 * sizeof(int), h->stream)) return 7;
+        if (cudaMemcpyAsync(w.As, dAs, (size_t)n * n * sizeof(R), cudaMemcpyDeviceToDevice, h->stream)) return 7;
+        if (int rc = spd_decompose<R>(h, n, w)) return rc;
+        if (cudaMemcpyAsync(dV, w.V, (size_t)n * n * sizeof(R), cudaMemcpyDeviceToDevice, h->stream)) return 7;
+        if (cudaMemcpyAsync(dlam, w.lamr, (size_t)n * sizeof(R), cudaMemcpyDeviceToDevice, h->stream)) return 7;
+        h->fact_n = -1;
+        int st = 0;
+        if (fetch_scalar<R>(h, &st, w.iscal + 1, sizeof(int))) return 7;
+        return st == 2 ? 0 : st;  // a non-positive eigenvalue is a valid decomposition here
+    };
+    return fp64 ? run(double(0)) : run(float(0));
+}
+
+namespace sqm {
+__global__ void sqrt_vec_kernel(const float *__restrict__ lam, float *__restrict__ s, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        s[i] = sqrtf(lam[i]);
+}
+}  // namespace sqm
+
+extern "C" int sqrtm_step_transform_in_spd(sqrtm_handle_t h, const float *dV, const float *dlam,
+                                           const float *dRhat, float *dY, int64_t n)
+{
+    if (!h) return -1;
+    if (n < 0) return -6;
+    if (n == 0) return 0;
+    const size_t nn = (size_t)n * n;
+    if (ensure(h->ws, Carve::round(nn * sizeof(float)) + Carve::round(n * sizeof(float)) + 1024)) return 7;
+    Carve c(h->ws.p);
+    float *W = c.take<float>(nn);
+    float *sv = c.take<float>(n);
+    const int ni = (int)n;
+    cudaStream_t st = h->stream;
+    sqrt_vec_kernel<<<grid1(n), 256, 0, st>>>(dlam, sv, ni);
+    if (launch_rgemm<float>(0, 0, ni, ni, ni, dRhat, ni, dV, ni, RG_STORE, W, ni, nullptr, nullptr, 0, 0.0, st)) return 7;
+    if (launch_rgemm<float>(1, 0, ni, ni, ni, dV, ni, W, ni, RG_DIAG_SOLVE, dY, ni, sv, nullptr, 0, 0.0, st)) return 7;
+    return cudaStreamSynchronize(st) ? 7 : 0;
+}
+
+extern "C" int sqrtm_step_transform_out_update_spd(sqrtm_handle_t h, const float *dV,
+                                                   const float *dY, int64_t n, int e, double *dX,
+                                                   int64_t ldx)
+{
+    if (!h) return -1;
+    if (n < 0) return -4;
+    if (ldx < std::max<int64_t>(1, n)) return -7;
+    if (n == 0) return 0;
+    const size_t nn = (size_t)n * n;
+    if (ensure(h->ws, Carve::round(nn * sizeof(float)) + 1024)) return 7;
+    Carve c(h->ws.p);
+    float *W = c.take<float>(nn);
+    const int ni = (int)n;
+    cudaStream_t st = h->stream;
+    if (launch_rgemm<float>(0, 0, ni, ni, ni, dV, ni, dY, ni, RG_STORE, W, ni, nullptr, nullptr, 0, 0.0, st)) return 7;
+    if (launch_rgemm<float>(0, 1, ni, ni, ni, W, ni, dV, ni, RG_SYM_ADD_F64, nullptr, 0, nullptr, dX, ldx, ldexp(1.0, e), st)) return 7;
+    return cudaStreamSynchronize(st) ? 7 : 0;
+}

@@ -1,0 +1,36 @@
+// spd_internal.h -- launchers of the symmetric positive definite path
+// (Algorithm 3): real products, tridiagonalisation and the tridiagonal
+// eigensolver.
+#pragma once
+
+#include "internal.h"
+
+namespace sqm {
+
+enum { RG_STORE = 0, RG_DIAG_SOLVE = 1, RG_SYM_TO_F64 = 2, RG_SYM_ADD_F64 = 3, RG_ADD_F64 = 4 };
+
+// C = op(A) op(B), op 0 = N, 1 = T; see rgemm.cu for the epilogues.
+template <class R>
+cudaError_t launch_rgemm(int opA, int opB, int m, int n, int k, const R *A, int lda, const R *B,
+                         int ldb, int epi, R *C, int ldc, const R *s, double *X, int64_t ldx,
+                         double scale, cudaStream_t st);
+
+// R = (A - X X) 4^-e for symmetric X; upper tiles, mirrored.
+cudaError_t launch_residual_sym_f64(const double *A, int64_t lda, const double *X, int64_t ldx,
+                                    int n, int e, float *Rhat, int ldr, double *partials,
+                                    int *nparts, cudaStream_t s);
+
+// Householder tridiagonalisation A = Q Tri Q^T (A overwritten; Q out).
+// ws: >= 2 n + 8 elements of R.
+template <class R>
+cudaError_t launch_tridiag(R *A, int n, int ld, R *Q, int ldq, R *ws, cudaStream_t s);
+
+// Eigen-decomposition of the symmetric tridiagonal matrix held on the
+// diagonal / first subdiagonal of A (FP64 arithmetic): lam (ascending) and
+// ZT (row j = unit eigenvector j, n x n, ld n).  scratch: 2 n * chunk doubles
+// plus 2 n + 8.
+template <class R>
+cudaError_t launch_tridiag_eig(const R *A, int n, int ld, double *lam, double *ZT,
+                               double *scratch, int chunk, cudaStream_t s);
+
+}  // namespace sqm

@@ -1,0 +1,202 @@
+// steps.cu -- step-level C entry points (sqrtm_mp_steps.h): each runs one
+// stage of the method on caller-provided device buffers, with the same
+// kernels the drivers chain.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "handle.h"
+
+using namespace sqm;
+
+namespace {
+
+struct StepScratch {
+    double *dscal;   // [0] norm, [1] rnorm, [2..] partials
+    int *iscal;      // [0] e, [1] status
+};
+
+int step_scratch(sqrtm_handle_t h, int64_t n, size_t extra, StepScratch *ss, void **extra_p)
+{
+    int64_t nb = (n + 63) / 64;
+    size_t np = (size_t)std::max<int64_t>(nb * nb, 2048) + 8;
+    size_t need = Carve::round(np * sizeof(double)) + 256 + Carve::round(extra) + 1024;
+    if (ensure(h->ws, need)) return 7;
+    Carve c(h->ws.p);
+    ss->dscal = c.take<double>(np);
+    ss->iscal = c.take<int>(8);
+    *extra_p = extra ? c.take<char>(extra) : nullptr;
+    if (cudaMemsetAsync(ss->iscal, 0, 8 * sizeof(int), h->stream) != cudaSuccess) return 7;
+    return 0;
+}
+
+int fetch(sqrtm_handle_t h, void *dst, const void *src, size_t bytes)
+{
+    if (cudaMemcpyAsync(h->staging.p, src, bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) return 7;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return 7;
+    memcpy(dst, h->staging.p, bytes);
+    return 0;
+}
+
+}  // namespace
+
+extern "C" int sqrtm_step_scale(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda,
+                                void *dAs, int fp64, int *e_host, double *norm_host)
+{
+    if (!h) return -1;
+    if (n < 0) return -3;
+    if (lda < std::max<int64_t>(1, n)) return -4;
+    if (n == 0) { if (e_host) *e_host = 0; if (norm_host) *norm_host = 0; return 0; }
+    StepScratch ss; void *ex;
+    if (int rc = step_scratch(h, n, 0, &ss, &ex)) return rc;
+    if (launch_norm_scale(dA, n, lda, ss.dscal + 2, (int)std::min<int64_t>(n, 1024), ss.dscal, ss.iscal, h->stream)) return 7;
+    cudaError_t err = fp64 ? launch_cast_scaled<double>(dA, n, lda, ss.iscal, (cplx<double> *)dAs, n, h->stream)
+                           : launch_cast_scaled<float>(dA, n, lda, ss.iscal, (cplx<float> *)dAs, n, h->stream);
+    if (err) return 7;
+    double nrm; int e;
+    if (fetch(h, &nrm, ss.dscal, sizeof(double)) || fetch(h, &e, ss.iscal, sizeof(int))) return 7;
+    if (e_host) *e_host = e;
+    if (norm_host) *norm_host = nrm;
+    return 0;
+}
+
+template <class R>
+static int schur_step(sqrtm_handle_t h, cplx<R> *T, cplx<R> *Q, int64_t n)
+{
+    StepScratch ss; void *ex;
+    size_t extra = Carve::round((n + 8) * sizeof(cplx<R>)) + Carve::round(8 * sizeof(R)) + Carve::round(sizeof(SchurDesc<R>));
+    if (int rc = step_scratch(h, n, extra, &ss, &ex)) return rc;
+    Carve c(ex);
+    cplx<R> *v = c.take<cplx<R>>(n + 8);
+    R *beta = c.take<R>(8);
+    SchurDesc<R> *dd = c.take<SchurDesc<R>>(1);
+    SchurDesc<R> hd;
+    hd.T = T; hd.Q = Q; hd.v = v; hd.beta = beta; hd.status = ss.iscal + 1; hd.n = (int)n; hd.ld = (int)n;
+    hd.counters = nullptr;
+    memcpy(h->staging.p, &hd, sizeof(hd));
+    if (cudaMemcpyAsync(dd, h->staging.p, sizeof(hd), cudaMemcpyHostToDevice, h->stream)) return 7;
+    if (cudaStreamSynchronize(h->stream)) return 7;
+    if (launch_hessenberg<R>(dd, 1, (int)n, 64, h->stream)) return 7;
+    if (launch_qr_sweeps<R>(dd, 1, h->stream)) return 7;
+    int st = 0;
+    if (fetch(h, &st, ss.iscal + 1, sizeof(int))) return 7;
+    return st;
+}
+
+extern "C" int sqrtm_step_schur(sqrtm_handle_t h, void *dT, void *dQ, int64_t n, int fp64)
+{
+    if (!h) return -1;
+    if (n < 0) return -4;
+    if (n == 0) return 0;
+    return fp64 ? schur_step<double>(h, (cplx<double> *)dT, (cplx<double> *)dQ, n)
+                : schur_step<float>(h, (cplx<float> *)dT, (cplx<float> *)dQ, n);
+}
+
+extern "C" int sqrtm_step_trisqrt(sqrtm_handle_t h, const void *dT, void *dS, int64_t n, int blks,
+                                  int fp64)
+{
+    if (!h) return -1;
+    if (n < 0) return -4;
+    if (blks < 1) return -5;
+    if (n == 0) return 0;
+    StepScratch ss; void *ex;
+    if (int rc = step_scratch(h, n, 0, &ss, &ex)) return rc;
+    cudaError_t err = fp64 ? launch_trisqrt<double>((const cplx<double> *)dT, (int)n, (cplx<double> *)dS, (int)n, (int)n, blks, ss.iscal + 1, h->stream)
+                           : launch_trisqrt<float>((const cplx<float> *)dT, (int)n, (cplx<float> *)dS, (int)n, (int)n, blks, ss.iscal + 1, h->stream);
+    if (err) return 7;
+    int st = 0;
+    if (fetch(h, &st, ss.iscal + 1, sizeof(int))) return 7;
+    return st;
+}
+
+template <class R>
+static int form_x0(sqrtm_handle_t h, const cplx<R> *Q, const cplx<R> *S, int64_t n, int e,
+                   double *dX, int64_t ldx)
+{
+    StepScratch ss; void *ex;
+    if (int rc = step_scratch(h, n, (size_t)n * n * sizeof(cplx<R>), &ss, &ex)) return rc;
+    cplx<R> *W = (cplx<R> *)ex;
+    if (launch_cgemm<R>(OP_N, OP_N, (int)n, (int)n, (int)n, Q, (int)n, false, S, (int)n, EPI_STORE, W, (int)n, nullptr, 0, 0.0, h->stream)) return 7;
+    if (launch_cgemm<R>(OP_N, OP_H, (int)n, (int)n, (int)n, W, (int)n, false, Q, (int)n, EPI_REAL_TO_F64, nullptr, 0, dX, ldx, ldexp(1.0, e), h->stream)) return 7;
+    return cudaStreamSynchronize(h->stream) ? 7 : 0;
+}
+
+extern "C" int sqrtm_step_form_x0(sqrtm_handle_t h, const void *dQ, const void *dS, int64_t n,
+                                  int e, double *dX, int64_t ldx, int fp64)
+{
+    if (!h) return -1;
+    if (n < 0) return -4;
+    if (ldx < std::max<int64_t>(1, n)) return -7;
+    if (n == 0) return 0;
+    if (fp64) return form_x0<double>(h, (const cplx<double> *)dQ, (const cplx<double> *)dS, n, e, dX, ldx);
+    return form_x0<float>(h, (const cplx<float> *)dQ, (const cplx<float> *)dS, n, e, dX, ldx);
+}
+
+extern "C" int sqrtm_step_residual(sqrtm_handle_t h, const double *dA, int64_t lda,
+                                   const double *dX, int64_t ldx, int64_t n, int e, float *dRhat,
+                                   double *norm_host)
+{
+    if (!h) return -1;
+    if (n < 0) return -6;
+    if (lda < std::max<int64_t>(1, n)) return -3;
+    if (ldx < std::max<int64_t>(1, n)) return -5;
+    if (n == 0) { if (norm_host) *norm_host = 0; return 0; }
+    StepScratch ss; void *ex;
+    if (int rc = step_scratch(h, n, 0, &ss, &ex)) return rc;
+    int np = 0;
+    if (launch_residual_f64(dA, lda, dX, ldx, (int)n, e, dRhat, (int)n, ss.dscal + 2, &np, h->stream)) return 7;
+    if (launch_sum_partials(ss.dscal + 2, np, ss.dscal + 1, h->stream)) return 7;
+    double rn;
+    if (fetch(h, &rn, ss.dscal + 1, sizeof(double))) return 7;
+    if (norm_host) *norm_host = rn;
+    return 0;
+}
+
+extern "C" int sqrtm_step_transform_in(sqrtm_handle_t h, const void *dQ, const float *dRhat,
+                                       void *dRt, int64_t n)
+{
+    if (!h) return -1;
+    if (n < 0) return -5;
+    if (n == 0) return 0;
+    StepScratch ss; void *ex;
+    if (int rc = step_scratch(h, n, (size_t)n * n * sizeof(cplx<float>), &ss, &ex)) return rc;
+    cplx<float> *W = (cplx<float> *)ex;
+    const cplx<float> *Q = (const cplx<float> *)dQ;
+    if (launch_cgemm<float>(OP_N, OP_N, (int)n, (int)n, (int)n, dRhat, (int)n, true, Q, (int)n, EPI_STORE, W, (int)n, nullptr, 0, 0.0, h->stream)) return 7;
+    if (launch_cgemm<float>(OP_H, OP_N, (int)n, (int)n, (int)n, Q, (int)n, false, W, (int)n, EPI_STORE, (cplx<float> *)dRt, (int)n, nullptr, 0, 0.0, h->stream)) return 7;
+    return cudaStreamSynchronize(h->stream) ? 7 : 0;
+}
+
+extern "C" int sqrtm_step_rtrsyl(sqrtm_handle_t h, const void *dS, int64_t m, const void *dSt,
+                                 int64_t nn, void *dC, int blks)
+{
+    if (!h) return -1;
+    if (m < 0) return -3;
+    if (nn < 0) return -5;
+    if (blks < 1) return -7;
+    if (m == 0 || nn == 0) return 0;
+    StepScratch ss; void *ex;
+    if (int rc = step_scratch(h, std::max(m, nn), 0, &ss, &ex)) return rc;
+    if (launch_rtrsyl<float>((const cplx<float> *)dS, (int)m, (int)m, (const cplx<float> *)dSt, (int)nn, (int)nn,
+                             (cplx<float> *)dC, (int)m, blks, ss.iscal + 1, h->stream)) return 7;
+    int st = 0;
+    if (fetch(h, &st, ss.iscal + 1, sizeof(int))) return 7;
+    return st;
+}
+
+extern "C" int sqrtm_step_transform_out_update(sqrtm_handle_t h, const void *dQ, const void *dY,
+                                               int64_t n, int e, double *dX, int64_t ldx)
+{
+    if (!h) return -1;
+    if (n < 0) return -4;
+    if (ldx < std::max<int64_t>(1, n)) return -7;
+    if (n == 0) return 0;
+    StepScratch ss; void *ex;
+    if (int rc = step_scratch(h, n, (size_t)n * n * sizeof(cplx<float>), &ss, &ex)) return rc;
+    cplx<float> *W = (cplx<float> *)ex;
+    const cplx<float> *Q = (const cplx<float> *)dQ;
+    if (launch_cgemm<float>(OP_N, OP_N, (int)n, (int)n, (int)n, Q, (int)n, false, (const cplx<float> *)dY, (int)n, EPI_STORE, W, (int)n, nullptr, 0, 0.0, h->stream)) return 7;
+    if (launch_cgemm<float>(OP_N, OP_H, (int)n, (int)n, (int)n, W, (int)n, false, Q, (int)n, EPI_REAL_ADD_F64, nullptr, 0, dX, ldx, ldexp(1.0, e), h->stream)) return 7;
+    return cudaStreamSynchronize(h->stream) ? 7 : 0;
+}

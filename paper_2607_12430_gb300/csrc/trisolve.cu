@@ -1,0 +1,288 @@
+// trisolve.cu -- blocked triangular square root and triangular Sylvester
+// solver, in the storage precision R.
+//
+// Both solvers partition their matrices into b x b blocks (b = blks <= 32)
+// and solve one block equation per CTA:
+//   trisqrt (Sec. 2.2.1, block method):  S_II S_IJ + S_IJ S_JJ =
+//       T_IJ - sum_{I<K<J} S_IK S_KJ, diagonal blocks by Eq. (subst);
+//   Sylvester (Sec. 2.2.2, the block equations of Eq. (partition) down to
+//   b x b leaves):  S_II Y_IJ + Y_IJ St_JJ =
+//       C_IJ - sum_{K>I} S_IK Y_KJ - sum_{K<J} Y_IK St_KJ.
+// Block (I, J) needs only blocks on earlier wavefronts (J - I smaller for
+// trisqrt; larger I or smaller J for the Sylvester solve), so each wavefront
+// is one launch whose CTAs are independent.  Inside a CTA the sums are tile
+// products in shared memory and the leaf equation is solved by point
+// Bartels-Stewart substitution along anti-diagonals (4 threads per entry).
+// The recursion of Algorithm 1 computes the same block equations; only the
+// grouping of the update sums differs.
+#include "internal.h"
+
+namespace sqm {
+
+static constexpr int TB = 32;       // maximum block edge
+static constexpr int TLD = TB + 1;  // padded leading dimension in shared memory
+static constexpr int kTriThreads = 128;
+
+template <class R>
+__device__ void load_tile(cplx<R> *dst, const cplx<R> *__restrict__ src, int ld, int rows,
+                          int cols)
+{
+    for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+        int i = e % TB, j = e / TB;
+        dst[i + j * TLD] = (i < rows && j < cols) ? src[i + (int64_t)j * ld] : cplx<R>{0, 0};
+    }
+}
+
+// acc(r, c_q) -= sum_k A(r, k) B(k, c_q) for the 8 outputs a thread owns
+// (row r = tid % 32, columns c_q = tid / 32 + 4 q).
+template <class R>
+__device__ __forceinline__ void tile_mms(cplx<R> (&acc)[8], const cplx<R> *A, const cplx<R> *B,
+                                         int kk)
+{
+    const int r = threadIdx.x & 31, c0 = threadIdx.x >> 5;
+    for (int k = 0; k < kk; ++k) {
+        cplx<R> a = A[r + k * TLD];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) cfms(acc[q], a, B[k + (c0 + 4 * q) * TLD]);
+    }
+}
+
+// Point Bartels-Stewart on a leaf: A (ma x ma) and B (nb x nb) upper
+// triangular, C (ma x nb) overwritten by Y with A Y + Y B = C.  Anti-diagonal
+// w holds the entries with j - i = w - (ma - 1); each entry depends on
+// entries below it in its column and left of it in its row, all on earlier
+// anti-diagonals.
+template <class R>
+__device__ void leaf_sylvester(const cplx<R> *A, const cplx<R> *B, cplx<R> *C, int ma, int nb,
+                               int *bad)
+{
+    const int e = threadIdx.x >> 2, p = threadIdx.x & 3;
+    for (int w = 0; w <= ma + nb - 2; ++w) {
+        const int ioff = ma - 1 - w;  // j = i - ioff
+        const int ilo = max(0, ioff), ihi = min(ma - 1, ioff + nb - 1);
+        const int i = ilo + e;
+        const bool act = i <= ihi;
+        cplx<R> acc{0, 0};
+        int j = i - ioff;
+        if (act) {
+            const int la = ma - 1 - i;  // terms A(i, k) C(k, j), k = i+1 .. ma-1
+            const int L = la + j;       // plus C(i, k) B(k, j), k = 0 .. j-1
+            for (int t = p; t < L; t += 4) {
+                if (t < la) cfma(acc, A[i + (i + 1 + t) * TLD], C[(i + 1 + t) + j * TLD]);
+                else { int k = t - la; cfma(acc, C[i + k * TLD], B[k + j * TLD]); }
+            }
+        }
+        acc += shfl_xor(acc, 1);
+        acc += shfl_xor(acc, 2);
+        if (act && p == 0) {
+            cplx<R> den = A[i + i * TLD] + B[j + j * TLD];
+            if (den.x == R(0) && den.y == R(0)) { *bad = 1; den = cplx<R>{R(1), R(0)}; }
+            C[i + j * TLD] = cdiv(C[i + j * TLD] - acc, den);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Sylvester wavefront: blocks (I, J) with J - I = w - (Mb - 1)
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void __launch_bounds__(kTriThreads)
+rtrsyl_wave_kernel(const cplx<R> *__restrict__ S, int lds, int m, const cplx<R> *__restrict__ St,
+                   int ldst, int nn, cplx<R> *C, int ldc, int b, int w, int *status)
+{
+    extern __shared__ unsigned char smraw[];
+    cplx<R> *tc = reinterpret_cast<cplx<R> *>(smraw);
+    cplx<R> *ta = tc + TB * TLD;
+    cplx<R> *tb = ta + TB * TLD;
+    __shared__ int bad;
+    const int Mb = (m + b - 1) / b, Nb = (nn + b - 1) / b;
+    const int I = max(0, (Mb - 1) - w) + blockIdx.x;
+    const int J = I + w - (Mb - 1);
+    if (I >= Mb || J >= Nb || J < 0) return;
+    if (threadIdx.x == 0) bad = 0;
+    const int i0 = I * b, j0 = J * b;
+    const int bm = min(b, m - i0), bn = min(b, nn - j0);
+    load_tile(tc, C + i0 + (int64_t)j0 * ldc, ldc, bm, bn);
+    __syncthreads();
+    cplx<R> acc[8];
+    const int r = threadIdx.x & 31, c0 = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = tc[r + (c0 + 4 * q) * TLD];
+    for (int K = I + 1; K < Mb; ++K) {        // - S_IK Y_KJ
+        const int k0 = K * b, bk = min(b, m - k0);
+        load_tile(ta, S + i0 + (int64_t)k0 * lds, lds, bm, bk);
+        load_tile(tb, C + k0 + (int64_t)j0 * ldc, ldc, bk, bn);
+        __syncthreads();
+        tile_mms(acc, ta, tb, bk);
+        __syncthreads();
+    }
+    for (int K = 0; K < J; ++K) {             // - Y_IK St_KJ
+        const int k0 = K * b, bk = min(b, nn - k0);
+        load_tile(ta, C + i0 + (int64_t)k0 * ldc, ldc, bm, bk);
+        load_tile(tb, St + k0 + (int64_t)j0 * ldst, ldst, bk, bn);
+        __syncthreads();
+        tile_mms(acc, ta, tb, bk);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) tc[r + (c0 + 4 * q) * TLD] = acc[q];
+    load_tile(ta, S + i0 + (int64_t)i0 * lds, lds, bm, bm);
+    load_tile(tb, St + j0 + (int64_t)j0 * ldst, ldst, bn, bn);
+    __syncthreads();
+    leaf_sylvester(ta, tb, tc, bm, bn, &bad);
+    for (int e = threadIdx.x; e < bm * bn; e += blockDim.x) {
+        int i = e % bm, j = e / bm;
+        C[(i0 + i) + (int64_t)(j0 + j) * ldc] = tc[i + j * TLD];
+    }
+    if (threadIdx.x == 0 && bad) atomicExch(status, 2);
+}
+
+// ---------------------------------------------------------------------------
+// Triangular square root, block superdiagonal d
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void __launch_bounds__(kTriThreads)
+trisqrt_diag_kernel(const cplx<R> *__restrict__ T, int ldt, cplx<R> *S, int lds, int n, int b,
+                    int *status)
+{
+    extern __shared__ unsigned char smraw[];
+    cplx<R> *ts = reinterpret_cast<cplx<R> *>(smraw);  // T block, overwritten by S
+    __shared__ int bad;
+    const int I = blockIdx.x;
+    const int i0 = I * b, bm = min(b, n - i0);
+    if (threadIdx.x == 0) bad = 0;
+    load_tile(ts, T + i0 + (int64_t)i0 * ldt, ldt, bm, bm);
+    __syncthreads();
+    const R eps = num<R>::eps;
+    if (threadIdx.x < bm) {
+        int i = threadIdx.x;
+        cplx<R> t = ts[i + i * TLD];
+        R at = hypot(t.x, t.y);
+        // eigenvalue on (or within rounding of) the closed negative real axis
+        if (t.x <= R(0) && fabs(t.y) <= R(10) * eps * at) bad = 1;
+        ts[i + i * TLD] = csqrt_(t);
+    }
+    __syncthreads();
+    // Eq. (subst) by superdiagonals: s_ij, j - i = dd, from entries with
+    // smaller j - i; 4 threads per entry share the inner sum
+    const int e = threadIdx.x >> 2, p = threadIdx.x & 3;
+    for (int dd = 1; dd < bm; ++dd) {
+        const int i = e, j = e + dd;
+        const bool act = j < bm;
+        cplx<R> acc{0, 0};
+        if (act)
+            for (int k = i + 1 + p; k < j; k += 4) cfma(acc, ts[i + k * TLD], ts[k + j * TLD]);
+        acc += shfl_xor(acc, 1);
+        acc += shfl_xor(acc, 2);
+        if (act && p == 0) {
+            cplx<R> den = ts[i + i * TLD] + ts[j + j * TLD];
+            if (den.x == R(0) && den.y == R(0)) { bad = 1; den = cplx<R>{R(1), R(0)}; }
+            ts[i + j * TLD] = cdiv(ts[i + j * TLD] - acc, den);
+        }
+        __syncthreads();
+    }
+    for (int q = threadIdx.x; q < bm * bm; q += blockDim.x) {
+        int i = q % bm, j = q / bm;
+        S[(i0 + i) + (int64_t)(i0 + j) * lds] = (i <= j) ? ts[i + j * TLD] : cplx<R>{0, 0};
+    }
+    if (threadIdx.x == 0 && bad) atomicExch(status, 2);
+}
+
+template <class R>
+__global__ void __launch_bounds__(kTriThreads)
+trisqrt_off_kernel(const cplx<R> *__restrict__ T, int ldt, cplx<R> *S, int lds, int n, int b,
+                   int dblk, int *status)
+{
+    extern __shared__ unsigned char smraw[];
+    cplx<R> *tc = reinterpret_cast<cplx<R> *>(smraw);
+    cplx<R> *ta = tc + TB * TLD;
+    cplx<R> *tb = ta + TB * TLD;
+    __shared__ int bad;
+    const int Nb = (n + b - 1) / b;
+    const int I = blockIdx.x, J = I + dblk;
+    if (J >= Nb) return;
+    if (threadIdx.x == 0) bad = 0;
+    const int i0 = I * b, j0 = J * b;
+    const int bm = min(b, n - i0), bn = min(b, n - j0);
+    load_tile(tc, T + i0 + (int64_t)j0 * ldt, ldt, bm, bn);
+    __syncthreads();
+    cplx<R> acc[8];
+    const int r = threadIdx.x & 31, c0 = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = tc[r + (c0 + 4 * q) * TLD];
+    for (int K = I + 1; K < J; ++K) {
+        const int k0 = K * b, bk = min(b, n - k0);
+        load_tile(ta, S + i0 + (int64_t)k0 * lds, lds, bm, bk);
+        load_tile(tb, S + k0 + (int64_t)j0 * lds, lds, bk, bn);
+        __syncthreads();
+        tile_mms(acc, ta, tb, bk);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) tc[r + (c0 + 4 * q) * TLD] = acc[q];
+    load_tile(ta, S + i0 + (int64_t)i0 * lds, lds, bm, bm);
+    load_tile(tb, S + j0 + (int64_t)j0 * lds, lds, bn, bn);
+    __syncthreads();
+    leaf_sylvester(ta, tb, tc, bm, bn, &bad);
+    for (int q = threadIdx.x; q < bm * bn; q += blockDim.x) {
+        int i = q % bm, j = q / bm;
+        S[(i0 + i) + (int64_t)(j0 + j) * lds] = tc[i + j * TLD];
+    }
+    // the mirrored block below the diagonal is zero
+    for (int q = threadIdx.x; q < bn * bm; q += blockDim.x) {
+        int i = q % bn, j = q / bn;
+        S[(j0 + i) + (int64_t)(i0 + j) * lds] = cplx<R>{0, 0};
+    }
+    if (threadIdx.x == 0 && bad) atomicExch(status, 2);
+}
+
+template <class R>
+static cudaError_t set_smem(const void *fn, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <class R>
+cudaError_t launch_trisqrt(const cplx<R> *T, int ldt, cplx<R> *S, int lds, int n, int blks,
+                           int *d_status, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    int b = blks < 1 ? 1 : (blks > TB ? TB : blks);
+    int Nb = (n + b - 1) / b;
+    size_t sm1 = TB * TLD * sizeof(cplx<R>), sm3 = 3 * sm1;
+    cudaError_t err;
+    if ((err = set_smem<R>((const void *)trisqrt_off_kernel<R>, sm3))) return err;
+    trisqrt_diag_kernel<R><<<Nb, kTriThreads, sm1, s>>>(T, ldt, S, lds, n, b, d_status);
+    for (int dblk = 1; dblk < Nb; ++dblk)
+        trisqrt_off_kernel<R><<<Nb - dblk, kTriThreads, sm3, s>>>(T, ldt, S, lds, n, b, dblk, d_status);
+    return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_rtrsyl(const cplx<R> *S, int lds, int m, const cplx<R> *St, int ldst, int nn,
+                          cplx<R> *C, int ldc, int blks, int *d_status, cudaStream_t s)
+{
+    if (m <= 0 || nn <= 0) return cudaSuccess;
+    int b = blks < 1 ? 1 : (blks > TB ? TB : blks);
+    int Mb = (m + b - 1) / b, Nb = (nn + b - 1) / b;
+    size_t sm3 = 3 * TB * TLD * sizeof(cplx<R>);
+    cudaError_t err;
+    if ((err = set_smem<R>((const void *)rtrsyl_wave_kernel<R>, sm3))) return err;
+    for (int w = 0; w <= Mb + Nb - 2; ++w) {
+        int ilo = max(0, (Mb - 1) - w);
+        int ihi = min(Mb - 1, (Mb - 1) - w + (Nb - 1));
+        int cnt = ihi - ilo + 1;
+        if (cnt <= 0) continue;
+        rtrsyl_wave_kernel<R><<<cnt, kTriThreads, sm3, s>>>(S, lds, m, St, ldst, nn, C, ldc, b, w, d_status);
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_trisqrt<float>(const cplx<float> *, int, cplx<float> *, int, int, int, int *, cudaStream_t);
+template cudaError_t launch_trisqrt<double>(const cplx<double> *, int, cplx<double> *, int, int, int, int *, cudaStream_t);
+template cudaError_t launch_rtrsyl<float>(const cplx<float> *, int, int, const cplx<float> *, int, int, cplx<float> *, int, int, int *, cudaStream_t);
+template cudaError_t launch_rtrsyl<double>(const cplx<double> *, int, int, const cplx<double> *, int, int, cplx<double> *, int, int, int *, cudaStream_t);
+
+}  // namespace sqm
