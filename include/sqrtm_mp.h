@@ -153,6 +153,10 @@ SQRTM_API int sqrtm_mixed_batched(sqrtm_handle_t handle, int batch, const double
                         double *const *dX, const int64_t *ldx, const sqrtm_opts *opts,
                         int *status);
 
+/* Number of CUDA kernel launches this library has issued in the process so
+ * far (all handles, all threads).  Diagnostic; never resets. */
+SQRTM_API int64_t sqrtm_kernel_launches(void);
+
 /* Human-readable text for a status code (static storage). */
 SQRTM_API const char *sqrtm_status_string(int code);
 

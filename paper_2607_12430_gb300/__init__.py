@@ -79,6 +79,7 @@ _SIGS = {
     "sqrtm_backward": ([_P, _P, _L, _L, _D, _P, _L, ctypes.POINTER(Info)], _I),
     "sqrtm_mixed_batched": ([_P, _I, _P, _P, _P, _D, _P, _P, ctypes.POINTER(Opts), _P], _I),
     "sqrtm_status_string": ([_I], ctypes.c_char_p),
+    "sqrtm_kernel_launches": ([], _L),
     "sqrtm_step_scale": ([_P, _P, _L, _L, _P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
     "sqrtm_step_schur": ([_P, _P, _P, _L, _I], _I),
     "sqrtm_step_syevd": ([_P, _P, _P, _P, _L, _I], _I),
@@ -99,7 +100,7 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run build_library())")
         L = ctypes.CDLL(LIB_PATH)
         for name, (args, res) in _SIGS.items():
             fn = getattr(L, name)
@@ -109,7 +110,13 @@ def lib():
     return _lib
 
 
-def build(force: bool = False) -> str:
+def kernel_launches() -> int:
+    """Kernel launches the library has issued in this process."""
+    return int(lib().sqrtm_kernel_launches())
+
+
+def build_library(force: bool = False) -> str:
+    """Compile the CUDA library (no-op when it is up to date); returns its path."""
     return _build_mod.build(force=force)
 
 

@@ -44,7 +44,7 @@ extern "C" int sqrtm_backward(sqrtm_handle_t h, const double *dG, int64_t n, int
     size_t np_cap = (size_t)std::max<int64_t>(nb * nb, 2048) + 8;
     size_t need = Carve::round(np_cap * sizeof(double)) + 256 + Carve::round(nn * sizeof(float)) +
                   2 * Carve::round(nn * sizeof(cplx<float>)) + 4096;
-    if (ensure(h->ws, need)) return 7;
+    if (ensure(h->ws, need, h)) return 7;
     Carve c(h->ws.p);
     double *dscal = c.take<double>(np_cap);
     int *iscal = c.take<int>(8);

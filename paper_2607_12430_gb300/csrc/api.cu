@@ -6,11 +6,68 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <vector>
 
 #include "handle.h"
 
 using namespace sqm;
+
+#include <atomic>
+static std::atomic<long long> g_launches{0};
+void sqm::count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+extern "C" int64_t sqrtm_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+// ---------------------------------------------------------------------------
+// captured launch sequences
+// ---------------------------------------------------------------------------
+int run_graph(sqrtm_handle_t h, int tag, const void *key, int64_t n, int batch,
+              cudaError_t (*enqueue)(void *ctx, cudaStream_t s), void *ctx)
+{
+    for (auto &g : h->graphs) {
+        if (g.tag == tag && g.key == key && g.n == n && g.batch == batch) {
+            if (cudaGraphLaunch(g.exec, h->stream) != cudaSuccess) return 7;
+            g_launches.fetch_add(g.launches, std::memory_order_relaxed);
+            return 0;
+        }
+    }
+    if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return 7;
+    long long before = g_launches.load();
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) return 7;
+    cudaError_t err = enqueue(ctx, h->cap_stream);
+    cudaError_t err2 = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (err != cudaSuccess || err2 != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return 7;
+    }
+    long long nl = g_launches.load() - before;
+    g_launches.fetch_sub(nl, std::memory_order_relaxed);  // counted when the graph runs
+    cudaGraphExec_t exec = nullptr;
+    err = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (err != cudaSuccess) return 7;
+    h->graphs.push_back({tag, key, n, batch, exec, nl});
+    if (cudaGraphLaunch(exec, h->stream) != cudaSuccess) return 7;
+    g_launches.fetch_add(nl, std::memory_order_relaxed);
+    return 0;
+}
+
+void drop_graphs(sqrtm_handle_t h, const void *lo, const void *hi)
+{
+    for (size_t i = 0; i < h->graphs.size();) {
+        const char *k = (const char *)h->graphs[i].key;
+        if (k >= (const char *)lo && k < (const char *)hi) {
+            cudaGraphExecDestroy(h->graphs[i].exec);
+            h->graphs.erase(h->graphs.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+}
 
 extern "C" int sqrtm_create(sqrtm_handle_t *handle, void *stream)
 {
@@ -30,6 +87,13 @@ extern "C" int sqrtm_destroy(sqrtm_handle_t h)
     if (!h) return 0;
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
+    for (size_t w = 0; w < h->workers.size(); ++w) {
+        sqrtm_destroy(h->workers[w]);
+        cudaStreamDestroy(h->worker_streams[w]);
+    }
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->ws.p) cudaFree(h->ws.p);
     if (h->fact.p) cudaFree(h->fact.p);
     if (h->staging.p) cudaFreeHost(h->staging.p);
@@ -157,8 +221,9 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     size_t fbytes = 2 * Carve::round(nn * cb) + Carve::round(nn * sizeof(double)) + 1024;
     size_t wbytes = scalars_bytes(n) + 3 * Carve::round(nn * cb) + Carve::round(nn * sizeof(float)) +
                     Carve::round((n + 8) * cb) + Carve::round(8 * sizeof(R)) +
-                    Carve::round(sizeof(SchurDesc<R>)) + 4096;
-    if (ensure(h->fact, fbytes) || ensure(h->ws, wbytes)) return 7;
+                    Carve::round(sizeof(SchurDesc<R>)) + Carve::round(qr_log_capacity(n) * sizeof(RotLog<R>)) +
+                    Carve::round(8 * sizeof(int)) + 4096;
+    if (ensure(h->fact, fbytes, h) || ensure(h->ws, wbytes, h)) return 7;
     Carve cf(h->fact.p);
     cplx<R> *Q = cf.take<cplx<R>>(nn);
     cplx<R> *S = cf.take<cplx<R>>(nn);
@@ -172,6 +237,8 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     cplx<R> *v = cw.take<cplx<R>>(n + 8);
     R *beta = cw.take<R>(8);
     SchurDesc<R> *ddesc = cw.take<SchurDesc<R>>(1);
+    RotLog<R> *rlog = cw.take<RotLog<R>>(qr_log_capacity(n));
+    int *qstate = cw.take<int>(8);
     h->fact_n = -1;
 
     SQM_CU(cudaMemsetAsync(sc.e, 0, 8 * sizeof(int), s));
@@ -188,14 +255,22 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     SchurDesc<R> hd;
     hd.T = T; hd.Q = Q; hd.v = v; hd.beta = beta; hd.status = sc.st_schur; hd.n = (int)n; hd.ld = (int)n;
     hd.counters = sc.st_schur + 3;
+    hd.log = rlog; hd.state = qstate; hd.log_cap = (int)std::min<int64_t>(qr_log_capacity(n), INT32_MAX);
     memcpy(h->staging.p, &hd, sizeof(hd));
     SQM_CU(cudaMemcpyAsync(ddesc, h->staging.p, sizeof(hd), cudaMemcpyHostToDevice, s));
     SQM_CU(cudaStreamSynchronize(s));
-    SQM_CU(launch_hessenberg<R>(ddesc, 1, (int)n, 64, s));
+    {
+        struct Ctx { SchurDesc<R> *d; int n; } ctx{ddesc, (int)n};
+        auto enq = [](void *p, cudaStream_t st) -> cudaError_t {
+            Ctx *c = (Ctx *)p;
+            return launch_hessenberg<R>(c->d, 1, c->n, 64, st);
+        };
+        if (run_graph(h, 100 + (int)sizeof(R), ddesc, n, 1, enq, &ctx)) return 7;
+    }
     cudaEvent_t ev_red;
     SQM_CU(cudaEventCreate(&ev_red));
     SQM_CU(cudaEventRecord(ev_red, s));
-    SQM_CU(launch_qr_sweeps<R>(ddesc, 1, s));
+    SQM_CU(launch_qr_sweeps<R>(ddesc, 1, (int)n, (int *)h->staging.p + 512, qstate, s));
     SQM_CU(cudaEventRecord(h->ev[1], s));
     SQM_CU(launch_trisqrt<R>(T, (int)n, S, (int)n, (int)n, o.blks, sc.st_solve, s));
     // X_0 = Re(Q S Q^H), rounded to R, times 2^e
@@ -293,7 +368,7 @@ extern "C" int sqrtm_mixed(sqrtm_handle_t h, const double *dA, int64_t n, int64_
     int kind = o.kind;
     if (kind == SQRTM_KIND_AUTO) {
         int rc = 0;
-        if (ensure(h->ws, 4096)) return 7;
+        if (ensure(h->ws, 4096, h)) return 7;
         bool sym = is_bitwise_symmetric(h, dA, n, lda, (int *)h->ws.p, &rc);
         if (rc) return rc;
         kind = sym ? SQRTM_KIND_SPD : SQRTM_KIND_GENERAL;
@@ -319,7 +394,7 @@ extern "C" int sqrtm_schur_fp64(sqrtm_handle_t h, const double *dA, int64_t n, i
     int kind = o.kind;
     if (kind == SQRTM_KIND_AUTO) {
         int rc = 0;
-        if (ensure(h->ws, 4096)) return 7;
+        if (ensure(h->ws, 4096, h)) return 7;
         bool sym = is_bitwise_symmetric(h, dA, n, lda, (int *)h->ws.p, &rc);
         if (rc) return rc;
         kind = sym ? SQRTM_KIND_SPD : SQRTM_KIND_GENERAL;
@@ -354,11 +429,32 @@ static bool is_bitwise_symmetric(sqrtm_handle_t h, const double *dA, int64_t n, 
     int one = 1;
     if (cudaMemcpyAsync(flag_dev, &one, sizeof(int), cudaMemcpyHostToDevice, h->stream) != cudaSuccess) { *rc = 7; return false; }
     int grid = (int)std::min<int64_t>(std::max<int64_t>(1, (n * n + 255) / 256), 152 * 8);
-    symmetric_kernel<<<grid, 256, 0, h->stream>>>(dA, n, lda, flag_dev);
+    symmetric_kernel<<<grid, 256, 0, h->stream>>>(dA, n, lda, flag_dev); count_launch();
     int flag = 0;
     if (cudaMemcpyAsync(&flag, flag_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess) { *rc = 7; return false; }
     return flag != 0;
+}
+
+// ---------------------------------------------------------------------------
+// batched entry point: a host-side scheduler.  Matrices are sorted by size
+// (largest first) and handed out dynamically to worker threads; each worker
+// owns a handle on its own non-blocking stream, so the kernels of different
+// matrices overlap on the GPU.  The caller's stream is fenced on entry (the
+// workers wait for work already queued on it) and on exit (it waits for all
+// workers).
+// ---------------------------------------------------------------------------
+static int ensure_workers(sqrtm_handle_t h, int count)
+{
+    while ((int)h->workers.size() < count) {
+        cudaStream_t st;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return 7;
+        sqrtm_handle_t w = nullptr;
+        if (int rc = sqrtm_create(&w, (void *)st)) { cudaStreamDestroy(st); return rc; }
+        h->workers.push_back(w);
+        h->worker_streams.push_back(st);
+    }
+    return 0;
 }
 
 extern "C" int sqrtm_mixed_batched(sqrtm_handle_t h, int batch, const double *const *dA,
@@ -368,11 +464,48 @@ extern "C" int sqrtm_mixed_batched(sqrtm_handle_t h, int batch, const double *co
 {
     if (!h) return -1;
     if (batch < 0) return -2;
+    if (batch == 0) return 0;
+    if (!dA || !n || !lda || !dX || !ldx) return -3;
+    for (int i = 0; i < batch; ++i)
+        if (int rc = check_args(dA[i], n[i], lda[i], dX[i], ldx[i])) return rc;
+    int nw = std::min(batch, 12);
+    if (const char *env = getenv("SQRTM_BATCH_WORKERS")) nw = std::max(1, std::min(batch, atoi(env)));
+    if (int rc = ensure_workers(h, nw)) return rc;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 7;
+    // fence: workers start after the work already on the caller's stream
+    cudaEvent_t start;
+    if (cudaEventCreateWithFlags(&start, cudaEventDisableTiming) != cudaSuccess) return 7;
+    cudaEventRecord(start, h->stream);
+    for (int w = 0; w < nw; ++w) cudaStreamWaitEvent(h->worker_streams[w], start, 0);
+    std::vector<int> order(batch);
+    for (int i = 0; i < batch; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
+    std::vector<int> st(batch, 0);
+    std::atomic<int> next{0};
+    auto work = [&](int w) {
+        cudaSetDevice(dev);
+        for (;;) {
+            int q = next.fetch_add(1);
+            if (q >= batch) break;
+            int i = order[q];
+            st[i] = sqrtm_mixed(h->workers[w], dA[i], n[i], lda[i], tol, dX[i], ldx[i], opts, nullptr);
+        }
+    };
+    std::vector<std::thread> threads;
+    for (int w = 1; w < nw; ++w) threads.emplace_back(work, w);
+    work(0);
+    for (auto &t : threads) t.join();
+    // fence: the caller's stream waits for every worker
+    for (int w = 0; w < nw; ++w) {
+        cudaEventRecord(start, h->worker_streams[w]);
+        cudaStreamWaitEvent(h->stream, start, 0);
+    }
+    cudaEventDestroy(start);
     int first = 0;
     for (int i = 0; i < batch; ++i) {
-        int rc = sqrtm_mixed(h, dA[i], n[i], lda[i], tol, dX[i], ldx[i], opts, nullptr);
-        if (status) status[i] = rc;
-        if (rc && !first) first = rc;
+        if (status) status[i] = st[i];
+        if (st[i] && !first) first = st[i];
     }
     return first;
 }

@@ -113,16 +113,16 @@ static cudaError_t dispatch_epi(int epi, dim3 g, cudaStream_t s, int m, int n, i
 {
     switch (epi) {
     case EPI_STORE:
-        cgemm_kernel<R, OPA, OPB, AREAL, EPI_STORE><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale);
+        cgemm_kernel<R, OPA, OPB, AREAL, EPI_STORE><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale); count_launch();
         break;
     case EPI_REAL_TO_F64:
-        cgemm_kernel<R, OPA, OPB, AREAL, EPI_REAL_TO_F64><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale);
+        cgemm_kernel<R, OPA, OPB, AREAL, EPI_REAL_TO_F64><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale); count_launch();
         break;
     case EPI_REAL_ADD_F64:
-        cgemm_kernel<R, OPA, OPB, AREAL, EPI_REAL_ADD_F64><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale);
+        cgemm_kernel<R, OPA, OPB, AREAL, EPI_REAL_ADD_F64><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale); count_launch();
         break;
     default:
-        cgemm_kernel<R, OPA, OPB, AREAL, EPI_REAL_ADD_F64_T><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale);
+        cgemm_kernel<R, OPA, OPB, AREAL, EPI_REAL_ADD_F64_T><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale); count_launch();
     }
     return cudaGetLastError();
 }
@@ -229,7 +229,7 @@ cudaError_t launch_residual_f64(const double *A, int64_t lda, const double *X, i
     dim3 g((unsigned)cdiv_i(n, GB_M), (unsigned)cdiv_i(n, GB_N));
     *nparts = (int)(g.x * g.y);
     if (n <= 0) return cudaSuccess;
-    residual_f64_kernel<<<g, G_THREADS, 0, s>>>(A, lda, X, ldx, n, ldexp(1.0, -2 * e), Rhat, ldr, partials);
+    residual_f64_kernel<<<g, G_THREADS, 0, s>>>(A, lda, X, ldx, n, ldexp(1.0, -2 * e), Rhat, ldr, partials); count_launch();
     return cudaGetLastError();
 }
 
@@ -315,7 +315,7 @@ cudaError_t launch_adjoint_residual_f64(const double *G, int64_t ldg, const doub
     dim3 g((unsigned)cdiv_i(n, GB_M), (unsigned)cdiv_i(n, GB_N));
     *nparts = (int)(g.x * g.y);
     if (n <= 0) return cudaSuccess;
-    adjoint_residual_f64_kernel<<<g, G_THREADS, 0, s>>>(G, ldg, X, ldx, Y, ldy, n, Rhat, ldr, partials);
+    adjoint_residual_f64_kernel<<<g, G_THREADS, 0, s>>>(G, ldg, X, ldx, Y, ldy, n, Rhat, ldr, partials); count_launch();
     return cudaGetLastError();
 }
 
@@ -330,7 +330,7 @@ __global__ void sum_partials_kernel(const double *__restrict__ p, int np, double
 
 cudaError_t launch_sum_partials(const double *partials, int np, double *d_out, cudaStream_t s)
 {
-    sum_partials_kernel<<<1, 32, 0, s>>>(partials, np, d_out);
+    sum_partials_kernel<<<1, 32, 0, s>>>(partials, np, d_out); count_launch();
     return cudaGetLastError();
 }
 

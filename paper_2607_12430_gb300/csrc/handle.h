@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "internal.h"
 #include "../../include/sqrtm_mp.h"
 #include "../../include/sqrtm_mp_steps.h"
@@ -30,11 +32,28 @@ struct sqrtm_handle_s {
     int fact_e = 0;
     double fact_norm = 0.0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // captured launch sequences (CUDA graphs), keyed by what they depend on
+    struct Graph {
+        int tag;
+        const void *key;
+        int64_t n;
+        int batch;
+        cudaGraphExec_t exec;
+        long long launches;
+    };
+    std::vector<Graph> graphs;
+    cudaStream_t cap_stream = nullptr;
+    // batched calls: worker handles, each on its own non-blocking stream
+    std::vector<sqrtm_handle_s *> workers;
+    std::vector<cudaStream_t> worker_streams;
 };
 
-inline int ensure(Buf &b, size_t bytes)
+void drop_graphs(sqrtm_handle_t h, const void *lo, const void *hi);
+
+inline int ensure(Buf &b, size_t bytes, sqrtm_handle_t owner = nullptr)
 {
     if (b.bytes >= bytes) return 0;
+    if (owner && b.p) drop_graphs(owner, b.p, (const char *)b.p + b.bytes);
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
     b.bytes = 0;
@@ -71,3 +90,14 @@ int spd_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, double 
 int spd_schur_fp64(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, double *dX,
                    int64_t ldx, const sqrtm_opts &o, sqrtm_info *info);
 inline bool spd_enabled() { return true; }
+
+// Enqueue `enqueue(stream)` on the handle's stream through a cached CUDA graph:
+// the first call with a given (tag, key, n, batch) captures the launches on a
+// private stream and instantiates them; later calls replay the executable
+// graph.  The captured kernels must take all data-dependent arguments from
+// device memory (descriptors), so a replay stays valid while `key` (the
+// descriptor buffer) is the same allocation.  Returns 0 or 7.
+int run_graph(sqrtm_handle_t h, int tag, const void *key, int64_t n, int batch,
+              cudaError_t (*enqueue)(void *ctx, cudaStream_t s), void *ctx);
+// drop cached graphs whose key lies in [lo, hi) (a buffer being released)
+void drop_graphs(sqrtm_handle_t h, const void *lo, const void *hi);

@@ -6,14 +6,32 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace sqm {
+
+// Process-wide count of kernel launches issued by this library (diagnostic;
+// reported by sqrtm_kernel_launches).
+void count_launch();
+
+// One logged Givens rotation of the QR iteration: position k (acts on
+// indices k, k+1), the active block [lo, hi] of its sweep, G = [c s; -conj(s) c].
+template <class R>
+struct RotLog {
+    int k, lo, hi, pad;
+    R c, pad2;
+    cplx<R> s;
+};
 
 // One matrix of a (possibly batched) Schur stage.  All arrays are device
 // memory, column-major with leading dimension ld.
 template <class R>
 struct SchurDesc {
+    RotLog<R> *log;  // scratch: rotation log (log_cap entries)
+    int *state;      // scratch: 8 ints of QR iteration state
+    int log_cap;
     cplx<R> *T;      // in: A_s, out: upper triangular T (n x n)
     cplx<R> *Q;      // out: unitary Schur vectors (n x n)
     cplx<R> *v;      // scratch: Householder vector (>= n entries)
@@ -39,8 +57,13 @@ cudaError_t launch_cast_scaled_real(const double *A, int64_t n, int64_t lda, con
 template <class R>
 cudaError_t launch_hessenberg(const SchurDesc<R> *d_desc, int batch, int nmax,
                               int ctas_per_matrix, cudaStream_t s);
+// d_state_all: the 8-int state blocks of all matrices, contiguous (descs[b].
+// state == d_state_all + 8 b); h_state: pinned host buffer of 8 * batch ints.
 template <class R>
-cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, cudaStream_t s);
+cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, int *h_state,
+                             const int *d_state_all, cudaStream_t s);
+// log entries to allocate per matrix of size n
+inline int64_t qr_log_capacity(int64_t n) { return n <= 1 ? 64 : std::max<int64_t>(4 * n * n, 256 * n); }
 
 // ---- triangular solvers (trisolve.cu) ----
 // S = T^{1/2}, blocked; status receives 2 on a zero denominator or an

@@ -121,11 +121,11 @@ static cudaError_t rg_epi(int epi, dim3 g, cudaStream_t st, int m, int n, int k,
                           int64_t ldx, double scale)
 {
     switch (epi) {
-    case RG_STORE: rgemm_kernel<R, OPA, OPB, RG_STORE><<<g, R_THREADS, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, s, X, ldx, scale); break;
-    case RG_DIAG_SOLVE: rgemm_kernel<R, OPA, OPB, RG_DIAG_SOLVE><<<g, R_THREADS, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, s, X, ldx, scale); break;
-    case RG_SYM_TO_F64: rgemm_kernel<R, OPA, OPB, RG_SYM_TO_F64><<<g, R_THREADS, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, s, X, ldx, scale); break;
-    case RG_SYM_ADD_F64: rgemm_kernel<R, OPA, OPB, RG_SYM_ADD_F64><<<g, R_THREADS, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, s, X, ldx, scale); break;
-    default: rgemm_kernel<R, OPA, OPB, RG_ADD_F64><<<g, R_THREADS, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, s, X, ldx, scale);
+    case RG_STORE: rgemm_kernel<R, OPA, OPB, RG_STORE><<<g, R_THREADS, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, s, X, ldx, scale); count_launch(); break;
+    case RG_DIAG_SOLVE: rgemm_kernel<R, OPA, OPB, RG_DIAG_SOLVE><<<g, R_THREADS, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, s, X, ldx, scale); count_launch(); break;
+    case RG_SYM_TO_F64: rgemm_kernel<R, OPA, OPB, RG_SYM_TO_F64><<<g, R_THREADS, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, s, X, ldx, scale); count_launch(); break;
+    case RG_SYM_ADD_F64: rgemm_kernel<R, OPA, OPB, RG_SYM_ADD_F64><<<g, R_THREADS, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, s, X, ldx, scale); count_launch(); break;
+    default: rgemm_kernel<R, OPA, OPB, RG_ADD_F64><<<g, R_THREADS, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, s, X, ldx, scale); count_launch();
     }
     return cudaGetLastError();
 }
@@ -234,7 +234,7 @@ cudaError_t launch_residual_sym_f64(const double *A, int64_t lda, const double *
     dim3 g((unsigned)cdiv_i(n, RB_M), (unsigned)cdiv_i(n, RB_N));
     *nparts = (int)(g.x * g.y);
     if (n <= 0) return cudaSuccess;
-    residual_sym_f64_kernel<<<g, R_THREADS, 0, s>>>(A, lda, X, ldx, n, ldexp(1.0, -2 * e), Rhat, ldr, partials);
+    residual_sym_f64_kernel<<<g, R_THREADS, 0, s>>>(A, lda, X, ldx, n, ldexp(1.0, -2 * e), Rhat, ldr, partials); count_launch();
     return cudaGetLastError();
 }
 

@@ -58,8 +58,8 @@ cudaError_t launch_norm_scale(const double *A, int64_t n, int64_t lda, double *p
                               int nblk, double *d_norm, int *d_e, cudaStream_t s)
 {
     if (nblk < 1) nblk = 1;
-    norm_partials_kernel<<<nblk, kNormThreads, 0, s>>>(A, n, lda, partials);
-    norm_finalize_kernel<<<1, 32, 0, s>>>(partials, nblk, n, d_norm, d_e);
+    norm_partials_kernel<<<nblk, kNormThreads, 0, s>>>(A, n, lda, partials); count_launch();
+    norm_finalize_kernel<<<1, 32, 0, s>>>(partials, nblk, n, d_norm, d_e); count_launch();
     return cudaGetLastError();
 }
 
@@ -103,7 +103,7 @@ template <class R>
 cudaError_t launch_cast_scaled(const double *A, int64_t n, int64_t lda, const int *d_e,
                                cplx<R> *As, int64_t ldas, cudaStream_t s)
 {
-    cast_scaled_kernel<R><<<grid_for(n * n), 256, 0, s>>>(A, n, lda, d_e, As, ldas);
+    cast_scaled_kernel<R><<<grid_for(n * n), 256, 0, s>>>(A, n, lda, d_e, As, ldas); count_launch();
     return cudaGetLastError();
 }
 
@@ -111,7 +111,7 @@ template <class R>
 cudaError_t launch_cast_scaled_real(const double *A, int64_t n, int64_t lda, const int *d_e,
                                     R *As, int64_t ldas, cudaStream_t s)
 {
-    cast_scaled_real_kernel<R><<<grid_for(n * n), 256, 0, s>>>(A, n, lda, d_e, As, ldas);
+    cast_scaled_real_kernel<R><<<grid_for(n * n), 256, 0, s>>>(A, n, lda, d_e, As, ldas); count_launch();
     return cudaGetLastError();
 }
 

@@ -202,13 +202,13 @@ cudaError_t launch_tridiag(R *A, int n, int ld, R *Q, int ldq, R *ws, cudaStream
         if ((err = cudaFuncSetAttribute(tri_update_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2))) return err;
         if ((err = cudaFuncSetAttribute(tri_q_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1))) return err;
     }
-    eye_real_kernel<R><<<(int)std::min<int64_t>(cdiv_i((int64_t)n * n, 256), 152 * 8), 256, 0, s>>>(Q, n, ldq);
+    eye_real_kernel<R><<<(int)std::min<int64_t>(cdiv_i((int64_t)n * n, 256), 152 * 8), 256, 0, s>>>(Q, n, ldq); count_launch();
     for (int k = 0; k + 2 < n; ++k) {
         int m = n - k - 1;
         int ctas = (int)std::min<int64_t>(cdiv_i(m, kTriThreads2 / 32), 304);
-        tri_symv_kernel<R><<<ctas, kTriThreads2, sm1, s>>>(A, n, ld, k, wsv, wsp, wss);
-        tri_update_kernel<R><<<ctas, kTriThreads2, sm2, s>>>(A, n, ld, k, wsv, wsp, wss);
-        tri_q_kernel<R><<<(int)cdiv_i(n, 32), dim3(32, 8), sm1, s>>>(Q, n, ldq, k, wsv, wss);
+        tri_symv_kernel<R><<<ctas, kTriThreads2, sm1, s>>>(A, n, ld, k, wsv, wsp, wss); count_launch();
+        tri_update_kernel<R><<<ctas, kTriThreads2, sm2, s>>>(A, n, ld, k, wsv, wsp, wss); count_launch();
+        tri_q_kernel<R><<<(int)cdiv_i(n, 32), dim3(32, 8), sm1, s>>>(Q, n, ldq, k, wsv, wss); count_launch();
     }
     return cudaGetLastError();
 }
@@ -342,11 +342,11 @@ cudaError_t launch_tridiag_eig(const R *A, int n, int ld, double *lam, double *Z
     double *d = scratch, *e = d + n, *e2 = e + n, *bounds = e2 + n;
     double *Dp = bounds + 8;
     double *Dm = Dp + (size_t)n * chunk;
-    tri_extract_kernel<R><<<1, 256, 0, s>>>(A, n, ld, d, e, e2, bounds);
-    bisect_kernel<<<(int)cdiv_i(n, 64), 64, 0, s>>>(d, e2, n, bounds, lam);
+    tri_extract_kernel<R><<<1, 256, 0, s>>>(A, n, ld, d, e, e2, bounds); count_launch();
+    bisect_kernel<<<(int)cdiv_i(n, 64), 64, 0, s>>>(d, e2, n, bounds, lam); count_launch();
     for (int j0 = 0; j0 < n; j0 += chunk) {
         int cnt = std::min(chunk, n - j0);
-        twisted_kernel<<<(int)cdiv_i(cnt, 64), 64, 0, s>>>(d, e, e2, n, bounds, lam, j0, cnt, Dp, Dm, ZT);
+        twisted_kernel<<<(int)cdiv_i(cnt, 64), 64, 0, s>>>(d, e, e2, n, bounds, lam, j0, cnt, Dp, Dm, ZT); count_launch();
     }
     return cudaGetLastError();
 }
@@ -437,7 +437,7 @@ int spd_carve(sqrtm_handle_t h, int64_t n, SpdWork<R> *w)
     // factors V, lamr, s persist for the adjoint / reuse
     size_t fbytes = Carve::round(nn * sizeof(R)) + 2 * Carve::round(n * sizeof(R)) +
                     Carve::round(nn * sizeof(double)) + 1024;
-    if (ensure(h->fact, fbytes) || ensure(h->ws, spd_bytes<R>(n, chunk))) return 7;
+    if (ensure(h->fact, fbytes, h) || ensure(h->ws, spd_bytes<R>(n, chunk), h)) return 7;
     Carve cf(h->fact.p);
     w->V = cf.take<R>(nn);
     w->lamr = cf.take<R>(n);
@@ -467,7 +467,14 @@ int spd_decompose(sqrtm_handle_t h, int64_t n, SpdWork<R> &w)
 {
     cudaStream_t s = h->stream;
     const int ni = (int)n;
-    if (launch_tridiag<R>(w.As, ni, ni, w.Qh, ni, w.vecws, s)) return 7;
+    {
+        struct Ctx { R *A, *Q, *ws; int n; } ctx{w.As, w.Qh, w.vecws, ni};
+        auto enq = [](void *p, cudaStream_t st) -> cudaError_t {
+            Ctx *c = (Ctx *)p;
+            return launch_tridiag<R>(c->A, c->n, c->n, c->Q, c->n, c->ws, st);
+        };
+        if (run_graph(h, 200 + (int)sizeof(R), w.As, n, 1, enq, &ctx)) return 7;
+    }
     if (launch_tridiag_eig<R>(w.As, ni, ni, w.lam, w.ZT, w.eigscratch, w.chunk, s)) return 7;
     if (sizeof(R) == sizeof(double)) {
         // Eigenvectors of close eigenvalues from independent twisted
@@ -479,13 +486,13 @@ int spd_decompose(sqrtm_handle_t h, int64_t n, SpdWork<R> &w)
         double *M = (double *)w.W, *P = (double *)w.As;
         if (launch_rgemm<double>(0, 1, ni, ni, ni, w.ZT, ni, w.ZT, ni, RG_STORE, M, ni, nullptr, nullptr, 0, 0.0, s)) return 7;
         if (launch_rgemm<double>(0, 0, ni, ni, ni, M, ni, w.ZT, ni, RG_STORE, P, ni, nullptr, nullptr, 0, 0.0, s)) return 7;
-        newton_schulz_combine_kernel<<<grid1((int64_t)n * n), 256, 0, s>>>(w.ZT, P, (int64_t)n * n);
+        newton_schulz_combine_kernel<<<grid1((int64_t)n * n), 256, 0, s>>>(w.ZT, P, (int64_t)n * n); count_launch();
     }
     // V = Qh Z = Qh (ZT)^T
     R *ZTr = w.W;
-    cast_from_f64_kernel<R><<<grid1((int64_t)n * n), 256, 0, s>>>(w.ZT, ZTr, (int64_t)n * n);
+    cast_from_f64_kernel<R><<<grid1((int64_t)n * n), 256, 0, s>>>(w.ZT, ZTr, (int64_t)n * n); count_launch();
     if (launch_rgemm<R>(0, 1, ni, ni, ni, w.Qh, ni, ZTr, ni, RG_STORE, w.V, ni, nullptr, nullptr, 0, 0.0, s)) return 7;
-    sqrt_eig_kernel<R><<<grid1(n), 256, 0, s>>>(w.lam, w.lamr, w.s, ni, w.iscal + 1);
+    sqrt_eig_kernel<R><<<grid1(n), 256, 0, s>>>(w.lam, w.lamr, w.s, ni, w.iscal + 1); count_launch();
     return cudaGetLastError() ? 7 : 0;
 }
 
@@ -520,7 +527,7 @@ int spd_common(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, doubl
     if (int rc = spd_decompose<R>(h, n, w)) return rc;
     if (cudaEventRecord(h->ev[1], s)) return 7;
     // X_0 = V diag(s) V^T, rounded to R, times 2^e (mirrored)
-    scale_cols_kernel<R><<<grid1((int64_t)n * n), 256, 0, s>>>(w.V, w.s, w.W, ni);
+    scale_cols_kernel<R><<<grid1((int64_t)n * n), 256, 0, s>>>(w.V, w.s, w.W, ni); count_launch();
     if (launch_rgemm<R>(0, 1, ni, ni, ni, w.W, ni, w.V, ni, RG_SYM_TO_F64, nullptr, 0, nullptr, dX, ldx, ldexp(1.0, e), s)) return 7;
     if (cudaEventRecord(h->ev[2], s)) return 7;
     int st = 0;
@@ -633,13 +640,13 @@ extern "C" int sqrtm_step_transform_in_spd(sqrtm_handle_t h, const float *dV, co
     if (n < 0) return -6;
     if (n == 0) return 0;
     const size_t nn = (size_t)n * n;
-    if (ensure(h->ws, Carve::round(nn * sizeof(float)) + Carve::round(n * sizeof(float)) + 1024)) return 7;
+    if (ensure(h->ws, Carve::round(nn * sizeof(float)) + Carve::round(n * sizeof(float)) + 1024, h)) return 7;
     Carve c(h->ws.p);
     float *W = c.take<float>(nn);
     float *sv = c.take<float>(n);
     const int ni = (int)n;
     cudaStream_t st = h->stream;
-    sqrt_vec_kernel<<<grid1(n), 256, 0, st>>>(dlam, sv, ni);
+    sqrt_vec_kernel<<<grid1(n), 256, 0, st>>>(dlam, sv, ni); count_launch();
     if (launch_rgemm<float>(0, 0, ni, ni, ni, dRhat, ni, dV, ni, RG_STORE, W, ni, nullptr, nullptr, 0, 0.0, st)) return 7;
     if (launch_rgemm<float>(1, 0, ni, ni, ni, dV, ni, W, ni, RG_DIAG_SOLVE, dY, ni, sv, nullptr, 0, 0.0, st)) return 7;
     return cudaStreamSynchronize(st) ? 7 : 0;
@@ -654,7 +661,7 @@ extern "C" int sqrtm_step_transform_out_update_spd(sqrtm_handle_t h, const float
     if (ldx < std::max<int64_t>(1, n)) return -7;
     if (n == 0) return 0;
     const size_t nn = (size_t)n * n;
-    if (ensure(h->ws, Carve::round(nn * sizeof(float)) + 1024)) return 7;
+    if (ensure(h->ws, Carve::round(nn * sizeof(float)) + 1024, h)) return 7;
     Carve c(h->ws.p);
     float *W = c.take<float>(nn);
     const int ni = (int)n;

@@ -22,7 +22,7 @@ int step_scratch(sqrtm_handle_t h, int64_t n, size_t extra, StepScratch *ss, voi
     int64_t nb = (n + 63) / 64;
     size_t np = (size_t)std::max<int64_t>(nb * nb, 2048) + 8;
     size_t need = Carve::round(np * sizeof(double)) + 256 + Carve::round(extra) + 1024;
-    if (ensure(h->ws, need)) return 7;
+    if (ensure(h->ws, need, h)) return 7;
     Carve c(h->ws.p);
     ss->dscal = c.take<double>(np);
     ss->iscal = c.take<int>(8);
@@ -65,20 +65,24 @@ template <class R>
 static int schur_step(sqrtm_handle_t h, cplx<R> *T, cplx<R> *Q, int64_t n)
 {
     StepScratch ss; void *ex;
-    size_t extra = Carve::round((n + 8) * sizeof(cplx<R>)) + Carve::round(8 * sizeof(R)) + Carve::round(sizeof(SchurDesc<R>));
+    size_t extra = Carve::round((n + 8) * sizeof(cplx<R>)) + Carve::round(8 * sizeof(R)) + Carve::round(sizeof(SchurDesc<R>)) +
+                   Carve::round(qr_log_capacity(n) * sizeof(RotLog<R>)) + Carve::round(8 * sizeof(int));
     if (int rc = step_scratch(h, n, extra, &ss, &ex)) return rc;
     Carve c(ex);
     cplx<R> *v = c.take<cplx<R>>(n + 8);
     R *beta = c.take<R>(8);
     SchurDesc<R> *dd = c.take<SchurDesc<R>>(1);
+    RotLog<R> *rlog = c.take<RotLog<R>>(qr_log_capacity(n));
+    int *qstate = c.take<int>(8);
     SchurDesc<R> hd;
     hd.T = T; hd.Q = Q; hd.v = v; hd.beta = beta; hd.status = ss.iscal + 1; hd.n = (int)n; hd.ld = (int)n;
     hd.counters = nullptr;
+    hd.log = rlog; hd.state = qstate; hd.log_cap = (int)std::min<int64_t>(qr_log_capacity(n), INT32_MAX);
     memcpy(h->staging.p, &hd, sizeof(hd));
     if (cudaMemcpyAsync(dd, h->staging.p, sizeof(hd), cudaMemcpyHostToDevice, h->stream)) return 7;
     if (cudaStreamSynchronize(h->stream)) return 7;
     if (launch_hessenberg<R>(dd, 1, (int)n, 64, h->stream)) return 7;
-    if (launch_qr_sweeps<R>(dd, 1, h->stream)) return 7;
+    if (launch_qr_sweeps<R>(dd, 1, (int)n, (int *)h->staging.p + 512, qstate, h->stream)) return 7;
     int st = 0;
     if (fetch(h, &st, ss.iscal + 1, sizeof(int))) return 7;
     return st;

@@ -254,9 +254,9 @@ cudaError_t launch_trisqrt(const cplx<R> *T, int ldt, cplx<R> *S, int lds, int n
     size_t sm1 = TB * TLD * sizeof(cplx<R>), sm3 = 3 * sm1;
     cudaError_t err;
     if ((err = set_smem<R>((const void *)trisqrt_off_kernel<R>, sm3))) return err;
-    trisqrt_diag_kernel<R><<<Nb, kTriThreads, sm1, s>>>(T, ldt, S, lds, n, b, d_status);
+    trisqrt_diag_kernel<R><<<Nb, kTriThreads, sm1, s>>>(T, ldt, S, lds, n, b, d_status); count_launch();
     for (int dblk = 1; dblk < Nb; ++dblk)
-        trisqrt_off_kernel<R><<<Nb - dblk, kTriThreads, sm3, s>>>(T, ldt, S, lds, n, b, dblk, d_status);
+        trisqrt_off_kernel<R><<<Nb - dblk, kTriThreads, sm3, s>>>(T, ldt, S, lds, n, b, dblk, d_status); count_launch();
     return cudaGetLastError();
 }
 
@@ -275,7 +275,7 @@ cudaError_t launch_rtrsyl(const cplx<R> *S, int lds, int m, const cplx<R> *St, i
         int ihi = min(Mb - 1, (Mb - 1) - w + (Nb - 1));
         int cnt = ihi - ilo + 1;
         if (cnt <= 0) continue;
-        rtrsyl_wave_kernel<R><<<cnt, kTriThreads, sm3, s>>>(S, lds, m, St, ldst, nn, C, ldc, b, w, d_status);
+        rtrsyl_wave_kernel<R><<<cnt, kTriThreads, sm3, s>>>(S, lds, m, St, ldst, nn, C, ldc, b, w, d_status); count_launch();
     }
     return cudaGetLastError();
 }

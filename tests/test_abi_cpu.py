@@ -27,7 +27,7 @@ def test_headers_declare_entry_points():
 
 def test_library_exports_every_declared_symbol():
     import paper_2607_12430_gb300 as pkg
-    path = pkg.build()
+    path = pkg.build_library()
     L = ctypes.CDLL(path)
     missing = [n for n in _declared() if not hasattr(L, n)]
     assert missing == []

@@ -56,7 +56,7 @@ def _match(got, expect):
 
 
 @pytest.mark.parametrize("fp64", [False, True])
-@pytest.mark.parametrize("n", [1, 2, 5, 33, 100, 257])
+@pytest.mark.parametrize("n", [1, 2, 5, 33, 100, 257, 512])
 def test_schur(n, fp64):
     A = synth.shifted_gaussian(n, 3.0, seed=20 + n)
     u = U64 if fp64 else U32
@@ -201,7 +201,7 @@ def test_sqrtm_mixed_general(n):
     assert oracle.rel_residual(X2.cpu().numpy(), A) <= 5 * n * U64
 
 
-@pytest.mark.parametrize("n", [1, 3, 64, 201])
+@pytest.mark.parametrize("n", [1, 3, 64, 201, 512])
 def test_sqrtm_schur_fp64(n):
     A = synth.shifted_gaussian(n, 3.0, seed=95 + n)
     X, info = mp.sqrtm_schur_fp64(torch.from_numpy(A).cuda(), kind=mp.KIND_GENERAL)
