@@ -152,7 +152,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     mp.lib()
     dev = torch.device("cuda", local)
-    A_np = synth.config_general512(n=N)
+    A_np = np.ascontiguousarray(synth.config_general512(n=N))
     A = torch.from_numpy(A_np).to(dev)
     n = N
 
@@ -312,7 +312,7 @@ def run_profile_mode(args):
     import torch
     import paper_2607_12430_gb300 as mp
     mp.lib()
-    A = torch.from_numpy(synth.config_general512(n=N)).cuda()
+    A = torch.from_numpy(np.ascontiguousarray(synth.config_general512(n=N))).cuda()
     X = torch.empty_like(A)
     t0 = time.perf_counter()
     for _ in range(args.warmup + args.steps):

@@ -157,6 +157,11 @@ SQRTM_API int sqrtm_mixed_batched(sqrtm_handle_t handle, int batch, const double
  * far (all handles, all threads).  Diagnostic; never resets. */
 SQRTM_API int64_t sqrtm_kernel_launches(void);
 
+/* Text describing the first CUDA failure (status 7) recorded on the handle
+ * since it was created: the CUDA error name and where it happened; "" if
+ * none.  Owned by the handle. */
+SQRTM_API const char *sqrtm_last_error(sqrtm_handle_t handle);
+
 /* Human-readable text for a status code (static storage). */
 SQRTM_API const char *sqrtm_status_string(int code);
 

@@ -87,6 +87,18 @@ SQRTM_API int sqrtm_step_transform_in_spd(sqrtm_handle_t h, const float *dV, con
 SQRTM_API int sqrtm_step_transform_out_update_spd(sqrtm_handle_t h, const float *dV, const float *dY,
                                         int64_t n, int e, double *dX, int64_t ldx);
 
+/* Low-precision dense product on the tensor cores (the transforms of
+ * Algorithm 3, steps 8 and 10, in split-TF32): C = A B in FP32 with
+ * A(i, k) = dA[k + i*lda] (M x K, rows contiguous) and B(k, j) = dB[k + j*ldb]
+ * (K x N, columns contiguous); dC column-major (ldc).  Each operand is split
+ * into two TF32 terms and C = A_hi B_hi + A_hi B_lo + A_lo B_hi is accumulated
+ * in FP32 (tcgen05, sm_103a).  lda and ldb must be multiples of 4 and the
+ * bases 16-byte aligned (TMA rules); returns -4 otherwise, 6 if a device-side
+ * bounded wait gave up. */
+SQRTM_API int sqrtm_step_gemm_tf32x3(sqrtm_handle_t h, int64_t M, int64_t N, int64_t K,
+                                     const float *dA, int64_t lda, const float *dB, int64_t ldb,
+                                     float *dC, int64_t ldc);
+
 #ifdef __cplusplus
 }
 #endif

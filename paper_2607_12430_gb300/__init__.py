@@ -36,7 +36,13 @@ MAX_HISTORY = 64
 
 class SqrtmError(RuntimeError):
     def __init__(self, code, what):
-        super().__init__(f"{what} failed with status {code} ({STATUS.get(code, 'invalid argument')})")
+        msg = f"{what} failed with status {code} ({STATUS.get(code, 'invalid argument')})"
+        if code == 7 and _lib is not None:
+            try:
+                msg += ": " + last_error()
+            except Exception:
+                pass
+        super().__init__(msg)
         self.code = code
 
 
@@ -80,6 +86,7 @@ _SIGS = {
     "sqrtm_mixed_batched": ([_P, _I, _P, _P, _P, _D, _P, _P, ctypes.POINTER(Opts), _P], _I),
     "sqrtm_status_string": ([_I], ctypes.c_char_p),
     "sqrtm_kernel_launches": ([], _L),
+    "sqrtm_last_error": ([_P], ctypes.c_char_p),
     "sqrtm_step_scale": ([_P, _P, _L, _L, _P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
     "sqrtm_step_schur": ([_P, _P, _P, _L, _I], _I),
     "sqrtm_step_syevd": ([_P, _P, _P, _P, _L, _I], _I),
@@ -91,6 +98,7 @@ _SIGS = {
     "sqrtm_step_transform_out_update": ([_P, _P, _P, _L, _I, _P, _L], _I),
     "sqrtm_step_transform_in_spd": ([_P, _P, _P, _P, _P, _L], _I),
     "sqrtm_step_transform_out_update_spd": ([_P, _P, _P, _L, _I, _P, _L], _I),
+    "sqrtm_step_gemm_tf32x3": ([_P, _L, _L, _L, _P, _L, _P, _L, _P, _L], _I),
 }
 
 
@@ -108,6 +116,11 @@ def lib():
             fn.restype = res
         _lib = L
     return _lib
+
+
+def last_error() -> str:
+    """First CUDA failure recorded on this stream's handle ("" if none)."""
+    return lib().sqrtm_last_error(handle()).decode()
 
 
 def kernel_launches() -> int:
@@ -157,6 +170,17 @@ def _check_square(A, name="A"):
     return A
 
 
+def _out_like(out, A, name="out"):
+    """The caller's output buffer (must be a contiguous float64 CUDA tensor of
+    A's shape) or a new one."""
+    if out is None:
+        return torch.empty(A.shape, dtype=A.dtype, device=A.device)
+    if (not isinstance(out, torch.Tensor) or out.shape != A.shape or out.dtype != A.dtype
+            or out.device != A.device or not out.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous {A.dtype} tensor of shape {tuple(A.shape)} on {A.device}")
+    return out
+
+
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else ctypes.c_void_p(0)
 
@@ -176,7 +200,7 @@ def sqrtm_mixed(A, tol=1e-12, out=None, raise_on_error=True, **kw):
     ``(X, info_dict)``."""
     A = _check_square(A)
     n = A.shape[0]
-    X = out if out is not None else torch.empty_like(A)
+    X = _out_like(out, A)
     o = make_opts(tol=tol, **kw)
     info = Info()
     ld = max(1, n)
@@ -192,7 +216,7 @@ def sqrtm_schur_fp64(A, out=None, raise_on_error=True, **kw):
     """Plain FP64 Schur method on the GPU.  Returns ``(X, info_dict)``."""
     A = _check_square(A)
     n = A.shape[0]
-    X = out if out is not None else torch.empty_like(A)
+    X = _out_like(out, A)
     o = make_opts(**kw)
     info = Info()
     ld = max(1, n)
@@ -209,7 +233,7 @@ def sqrtm_backward(G, tol=1e-12, out=None, raise_on_error=True):
     stream's handle: Y with X^T Y + Y X^T = G."""
     G = _check_square(G, "G")
     n = G.shape[0]
-    Y = out if out is not None else torch.empty_like(G)
+    Y = _out_like(out, G)
     info = Info()
     ld = max(1, n)
     rc = lib().sqrtm_backward(handle(), _ptr(G), n, ld, tol, _ptr(Y), ld, ctypes.byref(info))
@@ -224,7 +248,7 @@ def sqrtm_mixed_batched(As, tol=1e-12, outs=None, **kw):
     """Square roots of a list of square float64 CUDA tensors of any sizes.
     Returns ``(list_of_X, list_of_status)``."""
     As = [_check_square(A) for A in As]
-    Xs = outs if outs is not None else [torch.empty_like(A) for A in As]
+    Xs = [_out_like(o, A) for o, A in zip(outs, As)] if outs is not None else [_out_like(None, A) for A in As]
     b = len(As)
     pa = (ctypes.c_void_p * b)(*[A.data_ptr() for A in As])
     px = (ctypes.c_void_p * b)(*[X.data_ptr() for X in Xs])
@@ -348,3 +372,13 @@ def step_transform_in_spd(V_cm, lam, Rhat_cm, n):
 def step_transform_out_update_spd(V_cm, Y_cm, n, X_cm, e=0):
     _rc(lib().sqrtm_step_transform_out_update_spd(handle(), _ptr(V_cm), _ptr(Y_cm), n, e, _ptr(X_cm), n), "transform_out_update_spd")
     return X_cm
+
+
+def step_gemm_tf32x3(A_rows, B_cols, M, N, K):
+    """C = A B on the tensor cores (split TF32).  A_rows: float32 tensor whose
+    storage holds A row by row (row i = A_rows[i*K:(i+1)*K]); B_cols: B column
+    by column.  Returns C column-major (M*N)."""
+    C = torch.empty(M * N, dtype=torch.float32, device=A_rows.device)
+    _rc(lib().sqrtm_step_gemm_tf32x3(handle(), M, N, K, _ptr(A_rows), K, _ptr(B_cols), K, _ptr(C), M),
+        "gemm_tf32x3")
+    return C

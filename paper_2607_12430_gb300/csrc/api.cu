@@ -20,6 +20,19 @@ void sqm::count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 extern "C" int64_t sqrtm_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
+cudaError_t sqm::allow_max_smem(const void *kernel)
+{
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, kernel)) != cudaSuccess) return e;
+    // the dynamic part may use what the kernel's static shared memory leaves
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)fa.sharedSizeBytes);
+}
+
 // ---------------------------------------------------------------------------
 // captured launch sequences
 // ---------------------------------------------------------------------------
@@ -36,10 +49,12 @@ int run_graph(sqrtm_handle_t h, int tag, const void *key, int64_t n, int batch,
     if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return 7;
     long long before = g_launches.load();
     cudaGraph_t graph = nullptr;
-    if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) return 7;
+    cudaError_t e0 = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed);
+    if (e0 != cudaSuccess) { note_error(h, cudaGetErrorName(e0), __LINE__, 7); return 7; }
     cudaError_t err = enqueue(ctx, h->cap_stream);
     cudaError_t err2 = cudaStreamEndCapture(h->cap_stream, &graph);
     if (err != cudaSuccess || err2 != cudaSuccess || !graph) {
+        note_error(h, cudaGetErrorName(err != cudaSuccess ? err : err2), __LINE__, 7);
         if (graph) cudaGraphDestroy(graph);
         cudaGetLastError();
         return 7;
@@ -49,11 +64,23 @@ int run_graph(sqrtm_handle_t h, int tag, const void *key, int64_t n, int batch,
     cudaGraphExec_t exec = nullptr;
     err = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
-    if (err != cudaSuccess) return 7;
+    if (err != cudaSuccess) { note_error(h, cudaGetErrorName(err), __LINE__, 7); return 7; }
     h->graphs.push_back({tag, key, n, batch, exec, nl});
     if (cudaGraphLaunch(exec, h->stream) != cudaSuccess) return 7;
     g_launches.fetch_add(nl, std::memory_order_relaxed);
     return 0;
+}
+
+void note_error(sqrtm_handle_t h, const char *what, int line, int code)
+{
+    if (!h || h->last_error[0]) return;
+    snprintf(h->last_error, sizeof(h->last_error), "status %d: %s (api.cu/qr/spd line %d)", code, what, line);
+}
+
+extern "C" const char *sqrtm_last_error(sqrtm_handle_t h)
+{
+    if (!h) return "";
+    return h->last_error;
 }
 
 void drop_graphs(sqrtm_handle_t h, const void *lo, const void *hi)
@@ -222,6 +249,7 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     size_t wbytes = scalars_bytes(n) + 3 * Carve::round(nn * cb) + Carve::round(nn * sizeof(float)) +
                     Carve::round((n + 8) * cb) + Carve::round(8 * sizeof(R)) +
                     Carve::round(sizeof(SchurDesc<R>)) + Carve::round(qr_log_capacity(n) * sizeof(RotLog<R>)) +
+                    Carve::round(qr_win_capacity(n) * sizeof(WinRec)) + Carve::round(qr_u_capacity(n) * cb) +
                     Carve::round(8 * sizeof(int)) + 4096;
     if (ensure(h->fact, fbytes, h) || ensure(h->ws, wbytes, h)) return 7;
     Carve cf(h->fact.p);
@@ -238,6 +266,8 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     R *beta = cw.take<R>(8);
     SchurDesc<R> *ddesc = cw.take<SchurDesc<R>>(1);
     RotLog<R> *rlog = cw.take<RotLog<R>>(qr_log_capacity(n));
+    WinRec *wrec = cw.take<WinRec>(qr_win_capacity(n));
+    cplx<R> *ubuf = cw.take<cplx<R>>(qr_u_capacity(n));
     int *qstate = cw.take<int>(8);
     h->fact_n = -1;
 
@@ -256,6 +286,8 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     hd.T = T; hd.Q = Q; hd.v = v; hd.beta = beta; hd.status = sc.st_schur; hd.n = (int)n; hd.ld = (int)n;
     hd.counters = sc.st_schur + 3;
     hd.log = rlog; hd.state = qstate; hd.log_cap = (int)std::min<int64_t>(qr_log_capacity(n), INT32_MAX);
+    hd.win = wrec; hd.win_cap = (int)std::min<int64_t>(qr_win_capacity(n), INT32_MAX);
+    hd.ubuf = ubuf; hd.u_cap = qr_u_capacity(n);
     memcpy(h->staging.p, &hd, sizeof(hd));
     SQM_CU(cudaMemcpyAsync(ddesc, h->staging.p, sizeof(hd), cudaMemcpyHostToDevice, s));
     SQM_CU(cudaStreamSynchronize(s));
@@ -290,6 +322,7 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
         info->schur_rotations = (int64_t)cnt[1] + ((int64_t)cnt[2] << 31);
     }
     cudaEventDestroy(ev_red);
+    if (st_schur == 7) note_error(h, "malformed QR rotation log entry", __LINE__, 7);
     if (st_schur) return st_schur;
     if (st_solve) return st_solve;
     if (!refine) return 0;
@@ -490,6 +523,7 @@ extern "C" int sqrtm_mixed_batched(sqrtm_handle_t h, int batch, const double *co
             if (q >= batch) break;
             int i = order[q];
             st[i] = sqrtm_mixed(h->workers[w], dA[i], n[i], lda[i], tol, dX[i], ldx[i], opts, nullptr);
+
         }
     };
     std::vector<std::thread> threads;
@@ -507,5 +541,10 @@ extern "C" int sqrtm_mixed_batched(sqrtm_handle_t h, int batch, const double *co
         if (status) status[i] = st[i];
         if (st[i] && !first) first = st[i];
     }
+    for (int w = 0; w < nw && !h->last_error[0]; ++w)
+        if (h->workers[w]->last_error[0]) {
+            snprintf(h->last_error, sizeof(h->last_error), "worker %d: %s", w, h->workers[w]->last_error);
+            h->workers[w]->last_error[0] = 0;
+        }
     return first;
 }

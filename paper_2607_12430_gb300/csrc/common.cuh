@@ -72,6 +72,22 @@ template <> struct num<double> {
     static constexpr double eps = 1.1102230246251565e-16;  // 2^-53
 };
 
+// Asynchronous global -> shared copy of one complex element (Ampere-style
+// cp.async; the thread does not wait for the load).  Complete with
+// cp_async_wait_all() followed by a barrier.
+template <class R> __device__ __forceinline__ void cp_async_elem(cplx<R> *smem, const cplx<R> *gmem);
+template <> __device__ __forceinline__ void cp_async_elem<float>(cplx<float> *smem, const cplx<float> *gmem)
+{
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+template <> __device__ __forceinline__ void cp_async_elem<double>(cplx<double> *smem, const cplx<double> *gmem)
+{
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <class T> __device__ __forceinline__ T shfl_xor(T v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
 template <class R> __device__ __forceinline__ cplx<R> shfl_xor(cplx<R> v, int m) {
     return {__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m)};

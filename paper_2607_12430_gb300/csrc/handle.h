@@ -44,6 +44,7 @@ struct sqrtm_handle_s {
     std::vector<Graph> graphs;
     cudaStream_t cap_stream = nullptr;
     // batched calls: worker handles, each on its own non-blocking stream
+    char last_error[160] = {0};
     std::vector<sqrtm_handle_s *> workers;
     std::vector<cudaStream_t> worker_streams;
 };
@@ -77,10 +78,16 @@ struct Carve {
     static size_t round(size_t bytes) { return (bytes + 255) & ~(size_t)255; }
 };
 
-#define SQM_CU(call)                              \
-    do {                                          \
-        cudaError_t _e = (call);                  \
-        if (_e != cudaSuccess) return 7;          \
+// record the first failure of a call on the handle (for sqrtm_last_error)
+void note_error(sqrtm_handle_t h, const char *what, int line, int code);
+
+#define SQM_CU(call)                                          \
+    do {                                                      \
+        cudaError_t _e = (call);                              \
+        if (_e != cudaSuccess) {                              \
+            note_error(h, cudaGetErrorName(_e), __LINE__, 7); \
+            return 7;                                         \
+        }                                                     \
     } while (0)
 
 

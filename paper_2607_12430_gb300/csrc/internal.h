@@ -16,6 +16,12 @@ namespace sqm {
 // reported by sqrtm_kernel_launches).
 void count_launch();
 
+// Allow a kernel the device's full opt-in dynamic shared memory.  The
+// attribute is process-wide per kernel, so every caller sets the same value
+// (a per-call size would race between threads launching the same kernel with
+// different sizes).
+cudaError_t allow_max_smem(const void *kernel);
+
 // One logged Givens rotation of the QR iteration: position k (acts on
 // indices k, k+1), the active block [lo, hi] of its sweep, G = [c s; -conj(s) c].
 template <class R>
@@ -25,13 +31,26 @@ struct RotLog {
     cplx<R> s;
 };
 
+// One chase window of the QR iteration: its rotations are log entries
+// [start, start + count), they act on indices kmin .. kmin + rr - 1, the
+// sweep's active block is [lo, hi], and the window's accumulated rotation
+// product U (rr x rr) is stored at ubuf + uoff.
+struct WinRec {
+    int start, count, kmin, rr, lo, hi;
+    long long uoff;
+};
+
 // One matrix of a (possibly batched) Schur stage.  All arrays are device
 // memory, column-major with leading dimension ld.
 template <class R>
 struct SchurDesc {
     RotLog<R> *log;  // scratch: rotation log (log_cap entries)
+    WinRec *win;     // scratch: window records (win_cap entries)
+    cplx<R> *ubuf;   // scratch: accumulated window rotations (u_cap elements)
+    long long u_cap;
     int *state;      // scratch: 8 ints of QR iteration state
     int log_cap;
+    int win_cap;
     cplx<R> *T;      // in: A_s, out: upper triangular T (n x n)
     cplx<R> *Q;      // out: unitary Schur vectors (n x n)
     cplx<R> *v;      // scratch: Householder vector (>= n entries)
@@ -62,8 +81,12 @@ cudaError_t launch_hessenberg(const SchurDesc<R> *d_desc, int batch, int nmax,
 template <class R>
 cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, int *h_state,
                              const int *d_state_all, cudaStream_t s);
-// log entries to allocate per matrix of size n
+// scratch sizes per matrix of size n: rotation log entries, window records,
+// elements of accumulated window products (one round of the QR iteration
+// stops at a sweep boundary before any of them would overflow)
 inline int64_t qr_log_capacity(int64_t n) { return n <= 1 ? 64 : std::max<int64_t>(4 * n * n, 256 * n); }
+inline int64_t qr_win_capacity(int64_t n) { return std::max<int64_t>(n * n / 2, 1024); }
+inline int64_t qr_u_capacity(int64_t n) { return std::max<int64_t>(24 * n * n, 64 * 64 * 64); }
 
 // ---- triangular solvers (trisolve.cu) ----
 // S = T^{1/2}, blocked; status receives 2 on a zero denominator or an

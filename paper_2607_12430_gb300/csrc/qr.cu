@@ -134,10 +134,12 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
     __shared__ cplx<R> ws[NB][W];
     __shared__ cplx<R> s_r[NB];
     __shared__ cplx<R> s_mu[NB];
-    __shared__ int s_lo, s_hi, s_iter, s_status, s_done, s_nb, s_nlog, s_sweeps, s_stop;
+    __shared__ int s_lo, s_hi, s_iter, s_status, s_done, s_nb, s_nlog, s_sweeps, s_stop, s_nwin;
+    __shared__ long long s_uoff;
     __shared__ long long s_rots;
     __shared__ int s_off[NB + 1];
     __shared__ int s_goff[W];
+    __shared__ int s_first[NB], s_cnt[NB];
 
     const SchurDesc<R> d = descs[blockIdx.x];
     const int n = d.n, ld = d.ld;
@@ -147,7 +149,7 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
     const R eps = num<R>::eps;
     int *st = d.state;
     if (st[2]) {  // already finished: nothing new in the log
-        if (tid == 0) st[3] = 0;
+        if (tid == 0) { st[3] = 0; st[7] = 0; }
         return;
     }
     if (tid == 0) {
@@ -156,6 +158,8 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
         s_status = 0;
         s_done = 0;
         s_nlog = 0;
+        s_nwin = 0;
+        s_uoff = 0;
         s_sweeps = st[4];
         s_rots = (long long)st[5] + ((long long)st[6] << 31);
         s_stop = 0;
@@ -187,7 +191,9 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
         if (tid == 0) {
             const int m = hi - lo + 1;
             int nb = (m >= 4 * NB + 2) ? NB : 1;
-            if (s_nlog + (long long)(hi - lo) * nb > d.log_cap) {
+            const long long nwin_sweep = ((hi - lo) + 3 * (nb - 1) + W - 1) / W;
+            if (s_nlog + (long long)(hi - lo) * nb > d.log_cap || s_nwin + nwin_sweep > d.win_cap ||
+                s_uoff + nwin_sweep * (long long)(RRMAX * RRMAX) > d.u_cap) {
                 s_stop = 1;  // drain the log first
             } else {
                 if (lo > 0) T[lo + (int64_t)(lo - 1) * ld] = cplx<R>{0, 0};
@@ -231,16 +237,25 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
             const int bw = r1 - r0 + 1;
             for (int e = tid; e < bw * bw; e += nt) {
                 int a = e % bw, b = e / bw;
-                blk[a + b * BWMAX] = T[(r0 + a) + (int64_t)(r0 + b) * ld];
+                cp_async_elem<R>(&blk[a + b * BWMAX], &T[(r0 + a) + (int64_t)(r0 + b) * ld]);
             }
             if (tid < NB * W) wk[tid / W][tid % W] = -1;
+            cp_async_wait_all();
             __syncthreads();
-            for (int t = t0; t < t1; ++t) {
-                // rotation parameters, one lane per bulge
-                if (lane == 0 && warp < nb) {
+            // the chase: warp g moves bulge g; only the NB chase warps take part
+            // (named barrier 1, NB * 32 threads).  Each warp's rotation depends
+            // only on entries its own previous step wrote, so all its lanes
+            // compute it redundantly; left rotations of one step touch disjoint
+            // rows and right rotations disjoint columns, so one barrier after
+            // each phase orders the warps.
+            if (warp < NB) {
+                for (int t = t0; t < t1; ++t) {
                     const int g = warp, k = lo + t - 3 * g;
-                    if (k >= lo && k < hi) {
-                        const int kk = k - r0;
+                    const bool act = warp < nb && k >= lo && k < hi;
+                    const int kk = k - r0;
+                    R c = R(1);
+                    cplx<R> s{0, 0}, r{0, 0};
+                    if (act) {
                         cplx<R> x, y;
                         if (k == lo) {
                             x = blk[kk + kk * BWMAX] - s_mu[g];
@@ -249,22 +264,14 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
                             x = blk[kk + (kk - 1) * BWMAX];
                             y = blk[(kk + 1) + (kk - 1) * BWMAX];
                         }
-                        R c; cplx<R> s, r;
                         givens(x, y, c, s, r);
-                        wk[g][t - t0] = k;
-                        wc[g][t - t0] = c;
-                        ws[g][t - t0] = s;
-                        s_r[g] = r;
-                    }
-                }
-                __syncthreads();
-                // left rotations: rows kk, kk+1 of the block
-                if (warp < nb) {
-                    const int g = warp, k = wk[g][t - t0];
-                    if (k >= 0) {
-                        const int kk = k - r0;
-                        const R c = wc[g][t - t0];
-                        const cplx<R> s = ws[g][t - t0];
+                        if (lane == 0) {
+                            wk[g][t - t0] = k;
+                            wc[g][t - t0] = c;
+                            ws[g][t - t0] = s;
+                        }
+                        __syncwarp();
+                        // left rotation: rows kk, kk+1 of the block
                         const int cstart = (k == lo) ? kk : kk - 1;
                         for (int b = cstart + lane; b < bw; b += 32) {
                             cplx<R> p = blk[kk + b * BWMAX], q = blk[(kk + 1) + b * BWMAX];
@@ -273,19 +280,13 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
                         }
                         __syncwarp();
                         if (lane == 0 && k > lo) {
-                            blk[kk + (kk - 1) * BWMAX] = s_r[g];
+                            blk[kk + (kk - 1) * BWMAX] = r;
                             blk[(kk + 1) + (kk - 1) * BWMAX] = cplx<R>{0, 0};
                         }
                     }
-                }
-                __syncthreads();
-                // right rotations: columns kk, kk+1 of the block, rows up to kk+2
-                if (warp < nb) {
-                    const int g = warp, k = wk[g][t - t0];
-                    if (k >= 0) {
-                        const int kk = k - r0;
-                        const R c = wc[g][t - t0];
-                        const cplx<R> s = ws[g][t - t0];
+                    asm volatile("bar.sync 1, %0;" ::"r"(NB * 32) : "memory");
+                    if (act) {
+                        // right rotation: columns kk, kk+1, block rows up to kk+2
                         const int rend = min(kk + 2, bw - 1);
                         for (int a = lane; a <= rend; a += 32) {
                             cplx<R> p = blk[a + kk * BWMAX], q = blk[a + (kk + 1) * BWMAX];
@@ -293,9 +294,10 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
                             blk[a + (kk + 1) * BWMAX] = c * q - s * p;
                         }
                     }
+                    asm volatile("bar.sync 1, %0;" ::"r"(NB * 32) : "memory");
                 }
-                __syncthreads();
             }
+            __syncthreads();
             for (int e = tid; e < bw * bw; e += nt) {
                 int a = e % bw, b = e / bw;
                 T[(r0 + a) + (int64_t)(r0 + b) * ld] = blk[a + b * BWMAX];
@@ -310,9 +312,20 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
                     for (int g = 0; g < nb; ++g) off += (wk[g][q] >= 0);
                 }
                 s_off[NB] = off;
+                for (int g = 0; g < NB; ++g) {
+                    int first = -1, cnt = 0;
+                    if (g < nb)
+                        for (int q = 0; q < t1 - t0; ++q)
+                            if (wk[g][q] >= 0) {
+                                if (first < 0) first = q;
+                                ++cnt;
+                            }
+                    s_first[g] = first;
+                    s_cnt[g] = cnt;
+                }
             }
             __syncthreads();
-            for (int e = tid; e < nb * W; e += nt) {
+            for (int e = tid; e < NB * W; e += nt) {
                 const int q = e / NB, g = e % NB;
                 if (g < nb && q < t1 - t0 && wk[g][q] >= 0) {
                     int pos = s_goff[q], gsz = 0;
@@ -335,21 +348,31 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
                 const int cn = min(CH, hi - c0 + 1);
                 for (int e = tid; e < rr * cn; e += nt) {
                     int a = e % rr, b = e / rr;
-                    tile[a + b * (RRMAX + 1)] = T[(kmin + a) + (int64_t)(c0 + b) * ld];
+                    cp_async_elem<R>(&tile[a + b * (RRMAX + 1)], &T[(kmin + a) + (int64_t)(c0 + b) * ld]);
                 }
+                cp_async_wait_all();
                 __syncthreads();
                 if (tid < cn) {
+                    // each bulge's rotations in this window are consecutive
+                    // positions k0, k0+1, ...: carry the running element in
+                    // registers and load the next one ahead of the update
                     cplx<R> *col = tile + tid * (RRMAX + 1) - kmin;
-                    for (int g = 0; g < nb; ++g)
-                        for (int q = 0; q < t1 - t0; ++q) {
-                            const int k = wk[g][q];
-                            if (k < 0) continue;
-                            const R c = wc[g][q];
-                            const cplx<R> s = ws[g][q];
-                            cplx<R> p = col[k], w2 = col[k + 1];
-                            col[k] = c * p + s * w2;
-                            col[k + 1] = c * w2 - conj(s) * p;
+                    for (int g = 0; g < nb; ++g) {
+                        const int q0 = s_first[g], cnt = s_cnt[g];
+                        if (cnt <= 0) continue;
+                        const int k0 = wk[g][q0];
+                        cplx<R> carry = col[k0];
+                        cplx<R> nxt = col[k0 + 1];
+                        for (int i = 0; i < cnt; ++i) {
+                            const R c = wc[g][q0 + i];
+                            const cplx<R> s = ws[g][q0 + i];
+                            const cplx<R> after = (i + 1 < cnt) ? col[k0 + i + 2] : cplx<R>{0, 0};
+                            col[k0 + i] = c * carry + s * nxt;
+                            carry = c * nxt - conj(s) * carry;
+                            nxt = after;
                         }
+                        col[k0 + cnt] = carry;
+                    }
                 }
                 __syncthreads();
                 for (int e = tid; e < rr * cn; e += nt) {
@@ -363,21 +386,28 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
                 const int rn = min(CH, r0 - i0);
                 for (int e = tid; e < rn * rr; e += nt) {
                     int a = e % rn, b = e / rn;
-                    tile[a + b * (CH + 1)] = T[(i0 + a) + (int64_t)(kmin + b) * ld];
+                    cp_async_elem<R>(&tile[a + b * (CH + 1)], &T[(i0 + a) + (int64_t)(kmin + b) * ld]);
                 }
+                cp_async_wait_all();
                 __syncthreads();
                 if (tid < rn) {
                     cplx<R> *row = tile + tid;
-                    for (int g = 0; g < nb; ++g)
-                        for (int q = 0; q < t1 - t0; ++q) {
-                            const int k = wk[g][q];
-                            if (k < 0) continue;
-                            const R c = wc[g][q];
-                            const cplx<R> s = ws[g][q];
-                            cplx<R> p = row[(k - kmin) * (CH + 1)], w2 = row[(k + 1 - kmin) * (CH + 1)];
-                            row[(k - kmin) * (CH + 1)] = c * p + conj(s) * w2;
-                            row[(k + 1 - kmin) * (CH + 1)] = c * w2 - s * p;
+                    for (int g = 0; g < nb; ++g) {
+                        const int q0 = s_first[g], cnt = s_cnt[g];
+                        if (cnt <= 0) continue;
+                        const int k0 = wk[g][q0] - kmin;
+                        cplx<R> carry = row[k0 * (CH + 1)];
+                        cplx<R> nxt = row[(k0 + 1) * (CH + 1)];
+                        for (int i = 0; i < cnt; ++i) {
+                            const R c = wc[g][q0 + i];
+                            const cplx<R> s = ws[g][q0 + i];
+                            const cplx<R> after = (i + 1 < cnt) ? row[(k0 + i + 2) * (CH + 1)] : cplx<R>{0, 0};
+                            row[(k0 + i) * (CH + 1)] = c * carry + conj(s) * nxt;
+                            carry = c * nxt - s * carry;
+                            nxt = after;
                         }
+                        row[(k0 + cnt) * (CH + 1)] = carry;
+                    }
                 }
                 __syncthreads();
                 for (int e = tid; e < rn * rr; e += nt) {
@@ -386,7 +416,20 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
                 }
                 __syncthreads();
             }
-            if (tid == 0) s_nlog = s_off[NB];
+            if (tid == 0) {
+                WinRec wr;
+                wr.start = s_nlog;
+                wr.count = s_off[NB] - s_nlog;
+                wr.kmin = kmin;
+                wr.rr = rr;
+                wr.lo = lo;
+                wr.hi = hi;
+                wr.uoff = s_uoff;
+                d.win[s_nwin] = wr;
+                s_nwin += 1;
+                s_uoff += (long long)rr * rr;
+                s_nlog = s_off[NB];
+            }
             __syncthreads();
         }
     }
@@ -396,6 +439,7 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
         st[1] = s_iter;
         st[2] = (s_done || s_status) ? 1 : 0;
         st[3] = s_nlog;
+        st[7] = s_nwin;
         st[4] = s_sweeps;
         st[5] = (int)(s_rots & 0x7fffffff);
         st[6] = (int)(s_rots >> 31);
@@ -408,122 +452,205 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
     }
 }
 
-// Deferred right rotations on rows: Schur vectors Z (every logged rotation)
-// and rows of T above the active block of the rotation's sweep (i < lo).
-// One thread per row, the CTA's rows staged in shared memory.
+// Accumulated product of one window's rotations: U = I G_1^H G_2^H ... (the
+// right rotations in log order applied to the rows of I).  Then a row
+// segment x (indices kmin .. kmin+rr-1) receiving the window's right
+// rotations becomes x U, and a column segment y receiving its left rotations
+// becomes U^H y.  One CTA per window, thread r owns row r of U.
 template <class R>
-__global__ void qr_defer_rows_kernel(const SchurDesc<R> *__restrict__ descs, int rows_per_cta,
-                                     int ctas_t)
+__global__ void qr_build_u_kernel(const SchurDesc<R> *__restrict__ descs)
 {
-    extern __shared__ unsigned char smraw[];
+    constexpr int RRMAX = QrCfg<R>::W + 3 * QrCfg<R>::NB;
+    __shared__ cplx<R> u[RRMAX * (RRMAX + 1)];
+    __shared__ RotLog<R> lg[64];
     const SchurDesc<R> d = descs[blockIdx.y];
-    const int n = d.n, ld = d.ld;
-    const int nlog = d.state[3];
-    if (nlog == 0) return;
-    const bool isT = blockIdx.x < ctas_t;
-    const int cb = isT ? blockIdx.x : blockIdx.x - ctas_t;
-    const int i0 = cb * rows_per_cta;
-    if (i0 >= n) return;
-    const int rn = min(rows_per_cta, n - i0);
-    cplx<R> *M = isT ? d.T : d.Q;
-    const int rp = rows_per_cta;  // row stride in shared memory (rows are interleaved)
-    cplx<R> *buf = reinterpret_cast<cplx<R> *>(smraw);
-    RotLog<R> *lg = reinterpret_cast<RotLog<R> *>(buf + (size_t)rp * n);
-    constexpr int LCH = 128;
-    for (int e = threadIdx.x; e < rn * n; e += blockDim.x) {
-        int a = e % rn, b = e / rn;
-        buf[a + b * rp] = M[(i0 + a) + (int64_t)b * ld];
-    }
-    const int i = i0 + threadIdx.x;
-    const bool act = threadIdx.x < rn;
-    cplx<R> *row = buf + threadIdx.x;
-    for (int e0 = 0; e0 < nlog; e0 += LCH) {
-        const int en = min(LCH, nlog - e0);
+    const int nwin = d.state[7];
+    if ((int)blockIdx.x >= nwin) return;
+    const WinRec w = d.win[blockIdx.x];
+    const int rr = w.rr, r = threadIdx.x;
+    const int ld = RRMAX + 1;
+    if (r < rr)
+        for (int c = 0; c < rr; ++c) u[r * ld + c] = cplx<R>{(R)(r == c), R(0)};
+    for (int e0 = 0; e0 < w.count; e0 += 64) {
+        const int en = min(64, w.count - e0);
         __syncthreads();
-        for (int e = threadIdx.x; e < en; e += blockDim.x) lg[e] = d.log[e0 + e];
+        if (threadIdx.x < en) lg[threadIdx.x] = d.log[w.start + e0 + threadIdx.x];
         __syncthreads();
-        if (act) {
-            // groups of rotations on disjoint index pairs: load all, rotate,
-            // store all (independent chains)
-            for (int e = 0; e < en;) {
-                const int gsz = max(1, min(lg[e].pad, en - e));
-                if (isT && i >= lg[e].lo) { e += gsz; continue; }
-                cplx<R> p[4], q[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (u < gsz) { p[u] = row[lg[e + u].k * rp]; q[u] = row[(lg[e + u].k + 1) * rp]; }
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (u < gsz) {
-                        const R c = lg[e + u].c;
-                        const cplx<R> s = lg[e + u].s;
-                        row[lg[e + u].k * rp] = c * p[u] + conj(s) * q[u];
-                        row[(lg[e + u].k + 1) * rp] = c * q[u] - s * p[u];
-                    }
-                e += gsz;
+        if (r < rr) {
+            cplx<R> *row = u + r * ld;
+            for (int e = 0; e < en; ++e) {
+                const int a = lg[e].k - w.kmin;
+                if ((unsigned)a > (unsigned)(rr - 2)) { atomicExch(d.status, 7); continue; }
+                const R c = lg[e].c;
+                const cplx<R> s = lg[e].s;
+                cplx<R> p = row[a], q = row[a + 1];
+                row[a] = c * p + conj(s) * q;
+                row[a + 1] = c * q - s * p;
             }
         }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < rn * n; e += blockDim.x) {
-        int a = e % rn, b = e / rn;
-        M[(i0 + a) + (int64_t)b * ld] = buf[a + b * rp];
+    cplx<R> *U = d.ubuf + w.uoff;
+    for (int e = threadIdx.x; e < rr * rr; e += blockDim.x) {
+        const int q = e % rr, c = e / rr;  // U(q, c), column-major
+        U[e] = u[q * ld + c];
     }
 }
 
-// Deferred left rotations on columns of T right of the active block of the
-// rotation's sweep (j > hi).  Runs after the rows pass.
+// Deferred right rotations on rows (Schur vectors Z: every window; rows of T
+// above the window's active block: i < lo): x <- x U_w for each window in
+// order.  A CTA holds rpc rows in shared memory.
 template <class R>
-__global__ void qr_defer_cols_kernel(const SchurDesc<R> *__restrict__ descs, int cols_per_cta)
+__global__ void __launch_bounds__(256)
+qr_apply_rows_kernel(const SchurDesc<R> *__restrict__ descs, int rpc, int ctas_t)
 {
+    constexpr int RRMAX = QrCfg<R>::W + 3 * QrCfg<R>::NB;
     extern __shared__ unsigned char smraw[];
     const SchurDesc<R> d = descs[blockIdx.y];
     const int n = d.n, ld = d.ld;
-    const int nlog = d.state[3];
-    if (nlog == 0) return;
-    const int j0 = blockIdx.x * cols_per_cta;
-    if (j0 >= n) return;
-    const int cn = min(cols_per_cta, n - j0);
-    const int cs = n + 1;  // column stride in shared memory
-    cplx<R> *buf = reinterpret_cast<cplx<R> *>(smraw);
-    RotLog<R> *lg = reinterpret_cast<RotLog<R> *>(buf + (size_t)cs * cols_per_cta);
-    constexpr int LCH = 128;
-    for (int e = threadIdx.x; e < cn * n; e += blockDim.x) {
-        int a = e % n, b = e / n;
-        buf[a + b * cs] = d.T[a + (int64_t)(j0 + b) * ld];
+    const int nwin = d.state[7];
+    if (nwin == 0) return;
+    const bool isT = blockIdx.x < ctas_t;
+    const int cb = isT ? blockIdx.x : blockIdx.x - ctas_t;
+    const int i0 = cb * rpc;
+    if (i0 >= n) return;
+    const int rn = min(rpc, n - i0);
+    cplx<R> *M = isT ? d.T : d.Q;
+    cplx<R> *buf = reinterpret_cast<cplx<R> *>(smraw);          // rpc x n, buf[r + c rpc]
+    cplx<R> *ub[2] = {buf + (size_t)rpc * n, buf + (size_t)rpc * n + RRMAX * RRMAX};
+    for (int e = threadIdx.x; e < rn * n; e += blockDim.x) {
+        const int a = e % rn, b = e / rn;
+        cp_async_elem<R>(&buf[a + b * rpc], &M[(i0 + a) + (int64_t)b * ld]);
     }
-    const int j = j0 + threadIdx.x;
-    const bool act = threadIdx.x < cn;
-    cplx<R> *col = buf + threadIdx.x * cs;
-    for (int e0 = 0; e0 < nlog; e0 += LCH) {
-        const int en = min(LCH, nlog - e0);
+    // windows that touch this CTA's rows, in order; U of the next one is
+    // fetched while the current one is applied
+    auto next_win = [&](int wi) {
+        while (wi < nwin && isT && i0 >= d.win[wi].lo) ++wi;
+        return wi;
+    };
+    auto fetch_u = [&](int wi, cplx<R> *dst) {
+        const WinRec w = d.win[wi];
+        for (int e = threadIdx.x; e < w.rr * w.rr; e += blockDim.x) cp_async_elem<R>(&dst[e], &d.ubuf[w.uoff + e]);
+    };
+    constexpr int MAXO = (32 * RRMAX + 255) / 256;
+    int wi = next_win(0), par = 0;
+    if (wi < nwin) fetch_u(wi, ub[0]);
+    while (wi < nwin) {
+        const WinRec w = d.win[wi];
+        const int rr = w.rr;
+        cp_async_wait_all();
         __syncthreads();
-        for (int e = threadIdx.x; e < en; e += blockDim.x) lg[e] = d.log[e0 + e];
-        __syncthreads();
-        if (act) {
-            for (int e = 0; e < en;) {
-                const int gsz = max(1, min(lg[e].pad, en - e));
-                if (j <= lg[e].hi) { e += gsz; continue; }
-                cplx<R> p[4], q[4];
+        const int wn = next_win(wi + 1);
+        if (wn < nwin) fetch_u(wn, ub[par ^ 1]);
+        const cplx<R> *us = ub[par];
+        cplx<R> out[MAXO];
+        const int no = rn * rr;
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (u < gsz) { p[u] = col[lg[e + u].k]; q[u] = col[lg[e + u].k + 1]; }
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (u < gsz) {
-                        const R c = lg[e + u].c;
-                        const cplx<R> s = lg[e + u].s;
-                        col[lg[e + u].k] = c * p[u] + s * q[u];
-                        col[lg[e + u].k + 1] = c * q[u] - conj(s) * p[u];
-                    }
-                e += gsz;
+        for (int j = 0; j < MAXO; ++j) {
+            const int o = threadIdx.x + j * 256;
+            out[j] = cplx<R>{0, 0};
+            if (o < no) {
+                const int r = o % rn, c = o / rn;
+                const cplx<R> *x = buf + r + (size_t)w.kmin * rpc;
+                const cplx<R> *uc = us + (size_t)c * rr;
+                cplx<R> acc{0, 0};
+                for (int q = 0; q < rr; ++q) cfma(acc, x[(size_t)q * rpc], uc[q]);
+                out[j] = acc;
             }
         }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < MAXO; ++j) {
+            const int o = threadIdx.x + j * 256;
+            if (o < no) {
+                const int r = o % rn, c = o / rn;
+                if (!isT || i0 + r < w.lo) buf[r + (size_t)(w.kmin + c) * rpc] = out[j];
+            }
+        }
+        wi = wn;
+        par ^= 1;
     }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int e = threadIdx.x; e < rn * n; e += blockDim.x) {
+        const int a = e % rn, b = e / rn;
+        M[(i0 + a) + (int64_t)b * ld] = buf[a + b * rpc];
+    }
+}
+
+// Deferred left rotations on columns of T right of the window's active block
+// (j > hi): y <- U_w^H y for each window in order.  Runs after the rows pass.
+template <class R>
+__global__ void __launch_bounds__(256)
+qr_apply_cols_kernel(const SchurDesc<R> *__restrict__ descs, int cpc)
+{
+    constexpr int RRMAX = QrCfg<R>::W + 3 * QrCfg<R>::NB;
+    extern __shared__ unsigned char smraw[];
+    const SchurDesc<R> d = descs[blockIdx.y];
+    const int n = d.n, ld = d.ld;
+    const int nwin = d.state[7];
+    if (nwin == 0) return;
+    const int j0 = blockIdx.x * cpc;
+    if (j0 >= n) return;
+    const int cn = min(cpc, n - j0);
+    const int cs = n + 1;
+    cplx<R> *buf = reinterpret_cast<cplx<R> *>(smraw);           // column jl at buf + jl cs
+    cplx<R> *ub[2] = {buf + (size_t)cs * cpc, buf + (size_t)cs * cpc + RRMAX * RRMAX};
+    for (int e = threadIdx.x; e < cn * n; e += blockDim.x) {
+        const int a = e % n, b = e / n;
+        cp_async_elem<R>(&buf[a + (size_t)b * cs], &d.T[a + (int64_t)(j0 + b) * ld]);
+    }
+    auto next_win = [&](int wi) {
+        while (wi < nwin && j0 + cn - 1 <= d.win[wi].hi) ++wi;
+        return wi;
+    };
+    auto fetch_u = [&](int wi, cplx<R> *dst) {
+        const WinRec w = d.win[wi];
+        for (int e = threadIdx.x; e < w.rr * w.rr; e += blockDim.x) cp_async_elem<R>(&dst[e], &d.ubuf[w.uoff + e]);
+    };
+    constexpr int MAXO = (32 * RRMAX + 255) / 256;
+    int wi = next_win(0), par = 0;
+    if (wi < nwin) fetch_u(wi, ub[0]);
+    while (wi < nwin) {
+        const WinRec w = d.win[wi];
+        const int rr = w.rr;
+        cp_async_wait_all();
+        __syncthreads();
+        const int wn = next_win(wi + 1);
+        if (wn < nwin) fetch_u(wn, ub[par ^ 1]);
+        const cplx<R> *us = ub[par];
+        cplx<R> out[MAXO];
+        const int no = cn * rr;
+#pragma unroll
+        for (int j = 0; j < MAXO; ++j) {
+            const int o = threadIdx.x + j * 256;
+            out[j] = cplx<R>{0, 0};
+            if (o < no) {
+                const int jl = o % cn, c = o / cn;
+                const cplx<R> *y = buf + (size_t)jl * cs + w.kmin;
+                const cplx<R> *uc = us + (size_t)c * rr;
+                cplx<R> acc{0, 0};
+                for (int q = 0; q < rr; ++q) cfma(acc, conj(uc[q]), y[q]);
+                out[j] = acc;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < MAXO; ++j) {
+            const int o = threadIdx.x + j * 256;
+            if (o < no) {
+                const int jl = o % cn, c = o / cn;
+                if (j0 + jl > w.hi) buf[(size_t)jl * cs + w.kmin + c] = out[j];
+            }
+        }
+        wi = wn;
+        par ^= 1;
+    }
+    cp_async_wait_all();
     __syncthreads();
     for (int e = threadIdx.x; e < cn * n; e += blockDim.x) {
-        int a = e % n, b = e / n;
-        d.T[a + (int64_t)(j0 + b) * ld] = buf[a + b * cs];
+        const int a = e % n, b = e / n;
+        d.T[a + (int64_t)(j0 + b) * ld] = buf[a + (size_t)b * cs];
     }
 }
 
@@ -550,11 +677,13 @@ __global__ void qr_state_init_kernel(const SchurDesc<R> *__restrict__ descs, int
 }
 
 template <class R>
-size_t qr_rows_per_cta(int nmax)
+int qr_rows_per_cta(int nmax)
 {
-    size_t per = (size_t)std::max(nmax, 1) * sizeof(cplx<R>);
-    size_t r = (150 * 1024) / per;
-    return std::max<size_t>(1, std::min<size_t>(32, r));
+    constexpr int RRMAX = QrCfg<R>::W + 3 * QrCfg<R>::NB;
+    size_t per = (size_t)(std::max(nmax, 1) + 1) * sizeof(cplx<R>);
+    size_t avail = 200 * 1024 - 2 * (size_t)RRMAX * RRMAX * sizeof(cplx<R>);
+    size_t r = avail / per;
+    return (int)std::max<size_t>(1, std::min<size_t>(32, r));
 }
 
 template <class R>
@@ -563,25 +692,32 @@ cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, in
 {
     constexpr int RRMAX = QrCfg<R>::W + 3 * QrCfg<R>::NB, CH = QrCfg<R>::CH;
     const size_t tile_bytes = std::max((size_t)(RRMAX + 1) * CH, (size_t)(CH + 1) * RRMAX) * sizeof(cplx<R>);
-    const int rpc = (int)qr_rows_per_cta<R>(nmax);
-    const size_t rows_bytes = (size_t)rpc * nmax * sizeof(cplx<R>) + 128 * sizeof(RotLog<R>);
-    const size_t cols_bytes = (size_t)rpc * (nmax + 1) * sizeof(cplx<R>) + 128 * sizeof(RotLog<R>);
+    const int rpc = qr_rows_per_cta<R>(nmax);
+    const size_t ubytes = 2 * (size_t)RRMAX * RRMAX * sizeof(cplx<R>);
+    const size_t rows_bytes = (size_t)rpc * nmax * sizeof(cplx<R>) + ubytes;
+    const size_t cols_bytes = (size_t)rpc * (nmax + 1) * sizeof(cplx<R>) + ubytes;
     cudaError_t err;
-    if ((err = cudaFuncSetAttribute(qr_chase_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_bytes))) return err;
-    if ((err = cudaFuncSetAttribute(qr_defer_rows_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_bytes))) return err;
-    if ((err = cudaFuncSetAttribute(qr_defer_cols_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cols_bytes))) return err;
+    if ((err = allow_max_smem((const void *)qr_chase_kernel<R>))) return err;
+    if ((err = allow_max_smem((const void *)qr_apply_rows_kernel<R>))) return err;
+    if ((err = allow_max_smem((const void *)qr_apply_cols_kernel<R>))) return err;
     qr_state_init_kernel<R><<<1, 256, 0, s>>>(d_desc, batch); count_launch();
     const int ctas = (int)cdiv_i(nmax, rpc);
-    for (int round = 0; round < 64; ++round) {
+    bool all = false;
+    for (int round = 0; round < 256 && !all; ++round) {
         qr_chase_kernel<R><<<batch, kQrThreads, tile_bytes, s>>>(d_desc); count_launch();
-        qr_defer_rows_kernel<R><<<dim3(2 * ctas, batch), rpc, rows_bytes, s>>>(d_desc, rpc, ctas); count_launch();
-        qr_defer_cols_kernel<R><<<dim3(ctas, batch), rpc, cols_bytes, s>>>(d_desc, rpc); count_launch();
-        // all matrices finished?
         if ((err = cudaMemcpyAsync(h_state, d_state_all, sizeof(int) * 8 * batch, cudaMemcpyDeviceToHost, s))) return err;
         if ((err = cudaStreamSynchronize(s))) return err;
-        bool all = true;
-        for (int b = 0; b < batch; ++b) all = all && h_state[8 * b + 2];
-        if (all) break;
+        int maxwin = 0;
+        all = true;
+        for (int b = 0; b < batch; ++b) {
+            all = all && h_state[8 * b + 2];
+            maxwin = std::max(maxwin, h_state[8 * b + 7]);
+        }
+        if (maxwin > 0) {
+            qr_build_u_kernel<R><<<dim3(maxwin, batch), 64, 0, s>>>(d_desc); count_launch();
+            qr_apply_rows_kernel<R><<<dim3(2 * ctas, batch), 256, rows_bytes, s>>>(d_desc, rpc, ctas); count_launch();
+            qr_apply_cols_kernel<R><<<dim3(ctas, batch), 256, cols_bytes, s>>>(d_desc, rpc); count_launch();
+        }
     }
     qr_finish_kernel<R><<<dim3(64, batch), 256, 0, s>>>(d_desc); count_launch();
     return cudaGetLastError();

@@ -87,56 +87,70 @@ hess_left_kernel(const SchurDesc<R> *__restrict__ descs, int k)
     for (int j = k + 1 + gw; j < n; j += nw) {
         cplx<R> *c = H + (k + 1) + (int64_t)j * ld;
         cplx<R> acc{0, 0};
+#pragma unroll 8
         for (int i = lane; i < m; i += 32) cfma(acc, conj(vsh[i]), c[i]);
         acc = warp_sum(acc);
         cplx<R> w = beta * acc;
+#pragma unroll 8
         for (int i = lane; i < m; i += 32) cfms(c[i], vsh[i], w);
     }
 }
 
-// Rows of H (t < n) and of Q (t >= n); blockDim = (32, 8): x = row in tile,
-// y = column segment.
+// Rows of H (t < n) and of Q (t >= n); blockDim = (HR_ROWS, HR_SEGS): x = row
+// in the tile, y = column segment (partial dot products reduced in shared
+// memory).
+static constexpr int HR_ROWS = 16, HR_SEGS = 16;
+
 template <class R>
 __global__ void __launch_bounds__(kHessThreads)
 hess_right_kernel(const SchurDesc<R> *__restrict__ descs, int k)
 {
     extern __shared__ unsigned char smraw[];
     cplx<R> *vsh = reinterpret_cast<cplx<R> *>(smraw);
-    __shared__ cplx<R> part[8][33];
+    __shared__ cplx<R> part[HR_SEGS][HR_ROWS + 1];
     const SchurDesc<R> d = descs[blockIdx.y];
     const int n = d.n, ld = d.ld;
     if (k + 2 >= n) return;
     const int m = n - k - 1;
     const R beta = d.beta[0];
-    const int tid = threadIdx.y * 32 + threadIdx.x;
-    for (int i = tid; i < m; i += 256) vsh[i] = d.v[i];
+    const int tid = threadIdx.y * HR_ROWS + threadIdx.x;
+    for (int i = tid; i < m; i += HR_ROWS * HR_SEGS) vsh[i] = d.v[i];
     if (blockIdx.x == 0 && beta != R(0)) {
         // column k of H becomes [.., -phase ||x||, 0, ..., 0]
         cplx<R> *col = d.T + (k + 1) + (int64_t)k * ld;
         const R xn = d.beta[1];
-        for (int i = tid; i < m; i += 256)
+        for (int i = tid; i < m; i += HR_ROWS * HR_SEGS)
             col[i] = (i == 0) ? cplx<R>{-d.beta[2] * xn, -d.beta[3] * xn} : cplx<R>{0, 0};
     }
     __syncthreads();
     if (beta == R(0)) return;
-    const int row0 = blockIdx.x * 32;
+    const int row0 = blockIdx.x * HR_ROWS;
     if (row0 >= 2 * n) return;
     const int t = row0 + threadIdx.x;
     const bool valid = t < 2 * n;
     cplx<R> *M = (t < n) ? d.T : d.Q;
     const int i = (t < n) ? t : t - n;
-    cplx<R> acc{0, 0};
+    cplx<R> acc{0, 0}, acc2{0, 0};
     if (valid) {
-        for (int l = threadIdx.y; l < m; l += 8) cfma(acc, M[i + (int64_t)(k + 1 + l) * ld], vsh[l]);
+        const cplx<R> *base = M + i + (int64_t)(k + 1) * ld;
+        int l = threadIdx.y;
+#pragma unroll 4
+        for (; l + HR_SEGS < m; l += 2 * HR_SEGS) {
+            cfma(acc, base[(int64_t)l * ld], vsh[l]);
+            cfma(acc2, base[(int64_t)(l + HR_SEGS) * ld], vsh[l + HR_SEGS]);
+        }
+        if (l < m) cfma(acc, base[(int64_t)l * ld], vsh[l]);
+        acc += acc2;
     }
     part[threadIdx.y][threadIdx.x] = acc;
     __syncthreads();
     cplx<R> u{0, 0};
 #pragma unroll
-    for (int q = 0; q < 8; ++q) u += part[q][threadIdx.x];
+    for (int q = 0; q < HR_SEGS; ++q) u += part[q][threadIdx.x];
     u = beta * u;
     if (valid) {
-        for (int l = threadIdx.y; l < m; l += 8) {
+#pragma unroll 8
+        for (int l = threadIdx.y; l < m; l += HR_SEGS) {
             cplx<R> &e = M[i + (int64_t)(k + 1 + l) * ld];
             cfms(e, u, conj(vsh[l]));
         }
@@ -162,9 +176,9 @@ cudaError_t launch_hessenberg(const SchurDesc<R> *d_desc, int batch, int nmax,
     size_t smem = (size_t)(nmax > 0 ? nmax : 1) * sizeof(cplx<R>);
     cudaError_t err;
     if (smem > 48 * 1024) {
-        if ((err = cudaFuncSetAttribute(hess_left_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+        if ((err = allow_max_smem((const void *)hess_left_kernel<R>)))
             return err;
-        if ((err = cudaFuncSetAttribute(hess_right_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+        if ((err = allow_max_smem((const void *)hess_right_kernel<R>)))
             return err;
     }
     eye_kernel<R><<<dim3(64, batch), 256, 0, s>>>(d_desc); count_launch();
@@ -173,8 +187,8 @@ cudaError_t launch_hessenberg(const SchurDesc<R> *d_desc, int batch, int nmax,
         int left_ctas = (int)cdiv_i(m, kHessThreads / 32);
         if (left_ctas > ctas_per_matrix) left_ctas = ctas_per_matrix;
         hess_left_kernel<R><<<dim3(left_ctas, batch), kHessThreads, smem, s>>>(d_desc, k); count_launch();
-        int right_ctas = (int)cdiv_i(2 * nmax, 32);
-        hess_right_kernel<R><<<dim3(right_ctas, batch), dim3(32, 8), smem, s>>>(d_desc, k); count_launch();
+        int right_ctas = (int)cdiv_i(2 * nmax, HR_ROWS);
+        hess_right_kernel<R><<<dim3(right_ctas, batch), dim3(HR_ROWS, HR_SEGS), smem, s>>>(d_desc, k); count_launch();
     }
     return cudaGetLastError();
 }

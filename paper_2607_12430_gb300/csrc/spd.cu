@@ -27,6 +27,7 @@
 
 #include "handle.h"
 #include "spd_internal.h"
+#include "tc_gemm.h"
 
 namespace sqm {
 
@@ -91,6 +92,7 @@ tri_symv_kernel(const R *__restrict__ A, int n, int ld, int k, R *__restrict__ w
     for (int j = gw; j < m; j += nw) {
         const R *c = A + (k + 1) + (int64_t)(k + 1 + j) * ld;
         R acc = 0;
+#pragma unroll 8
         for (int i = lane; i < m; i += 32) acc = fma(c[i], vsh[i], acc);
         acc = warp_sum(acc);
         if (lane == 0) wsp[j] = beta * acc;
@@ -143,6 +145,7 @@ tri_update_kernel(R *__restrict__ A, int n, int ld, int k, const R *__restrict__
     for (int j = gw; j < m; j += nw) {
         R *c = A + (k + 1) + (int64_t)(k + 1 + j) * ld;
         const R vj = vsh[j], wj = wsh[j];
+#pragma unroll 8
         for (int i = lane; i < m; i += 32) c[i] = fma(-vsh[i], wj, fma(-wsh[i], vj, c[i]));
     }
 }
@@ -165,19 +168,30 @@ tri_q_kernel(R *__restrict__ Q, int n, int ldq, int k, const R *__restrict__ wsv
     const int i = blockIdx.x * 32 + threadIdx.x;
     const bool valid = i < n;
     R acc = 0;
-    if (valid)
-        for (int l = threadIdx.y; l < m; l += 8) acc = fma(Q[i + (int64_t)(k + 1 + l) * ldq], vsh[l], acc);
+    if (valid) {
+        R acc2 = 0;
+        int l = threadIdx.y;
+#pragma unroll 4
+        for (; l + 8 < m; l += 16) {
+            acc = fma(Q[i + (int64_t)(k + 1 + l) * ldq], vsh[l], acc);
+            acc2 = fma(Q[i + (int64_t)(k + 1 + l + 8) * ldq], vsh[l + 8], acc2);
+        }
+        if (l < m) acc = fma(Q[i + (int64_t)(k + 1 + l) * ldq], vsh[l], acc);
+        acc += acc2;
+    }
     part[threadIdx.y][threadIdx.x] = acc;
     __syncthreads();
     R u = 0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) u += part[q][threadIdx.x];
     u *= beta;
-    if (valid)
+    if (valid) {
+#pragma unroll 8
         for (int l = threadIdx.y; l < m; l += 8) {
             R &e = Q[i + (int64_t)(k + 1 + l) * ldq];
             e = fma(-u, vsh[l], e);
         }
+    }
 }
 
 template <class R>
@@ -198,9 +212,9 @@ cudaError_t launch_tridiag(R *A, int n, int ld, R *Q, int ldq, R *ws, cudaStream
     size_t sm2 = 2 * sm1;
     cudaError_t err;
     if (sm2 > 48 * 1024) {
-        if ((err = cudaFuncSetAttribute(tri_symv_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1))) return err;
-        if ((err = cudaFuncSetAttribute(tri_update_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2))) return err;
-        if ((err = cudaFuncSetAttribute(tri_q_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1))) return err;
+        if ((err = allow_max_smem((const void *)tri_symv_kernel<R>))) return err;
+        if ((err = allow_max_smem((const void *)tri_update_kernel<R>))) return err;
+        if ((err = allow_max_smem((const void *)tri_q_kernel<R>))) return err;
     }
     eye_real_kernel<R><<<(int)std::min<int64_t>(cdiv_i((int64_t)n * n, 256), 152 * 8), 256, 0, s>>>(Q, n, ldq); count_launch();
     for (int k = 0; k + 2 < n; ++k) {
@@ -354,6 +368,23 @@ cudaError_t launch_tridiag_eig(const R *A, int n, int ld, double *lam, double *Z
 template cudaError_t launch_tridiag_eig<float>(const float *, int, int, double *, double *, double *, int, cudaStream_t);
 template cudaError_t launch_tridiag_eig<double>(const double *, int, int, double *, double *, double *, int, cudaStream_t);
 
+// B = A^T for a square n x n matrix (32 x 32 tiles through shared memory)
+template <class R>
+__global__ void transpose_kernel(const R *__restrict__ A, R *__restrict__ B, int n)
+{
+    __shared__ R t[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int r = bx + threadIdx.x, c = by + j;
+        if (r < n && c < n) t[j][threadIdx.x] = A[r + (int64_t)c * n];
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int r = by + threadIdx.x, c = bx + j;
+        if (r < n && c < n) B[r + (int64_t)c * n] = t[threadIdx.x][j];
+    }
+}
+
 // small elementwise helpers
 // ZT <- 1.5 ZT - 0.5 P  (one Newton-Schulz step towards orthogonality:
 // Z <- Z (3 I - Z^T Z) / 2, written for Z^T)
@@ -463,7 +494,7 @@ int spd_carve(sqrtm_handle_t h, int64_t n, SpdWork<R> *w)
 
 // A_s (already in w->As) -> V, lamr, s; returns status
 template <class R>
-int spd_decompose(sqrtm_handle_t h, int64_t n, SpdWork<R> &w)
+int spd_decompose(sqrtm_handle_t h, int64_t n, SpdWork<R> &w, sqrtm_info *info = nullptr)
 {
     cudaStream_t s = h->stream;
     const int ni = (int)n;
@@ -474,6 +505,11 @@ int spd_decompose(sqrtm_handle_t h, int64_t n, SpdWork<R> &w)
             return launch_tridiag<R>(c->A, c->n, c->n, c->Q, c->n, c->ws, st);
         };
         if (run_graph(h, 200 + (int)sizeof(R), w.As, n, 1, enq, &ctx)) return 7;
+    }
+    cudaEvent_t ev_red = nullptr;
+    if (info) {
+        if (cudaEventCreate(&ev_red)) return 7;
+        if (cudaEventRecord(ev_red, s)) return 7;
     }
     if (launch_tridiag_eig<R>(w.As, ni, ni, w.lam, w.ZT, w.eigscratch, w.chunk, s)) return 7;
     if (sizeof(R) == sizeof(double)) {
@@ -493,6 +529,12 @@ int spd_decompose(sqrtm_handle_t h, int64_t n, SpdWork<R> &w)
     cast_from_f64_kernel<R><<<grid1((int64_t)n * n), 256, 0, s>>>(w.ZT, ZTr, (int64_t)n * n); count_launch();
     if (launch_rgemm<R>(0, 1, ni, ni, ni, w.Qh, ni, ZTr, ni, RG_STORE, w.V, ni, nullptr, nullptr, 0, 0.0, s)) return 7;
     sqrt_eig_kernel<R><<<grid1(n), 256, 0, s>>>(w.lam, w.lamr, w.s, ni, w.iscal + 1); count_launch();
+    if (info && ev_red) {
+        float ms = 0;
+        if (cudaEventSynchronize(ev_red) == cudaSuccess && cudaEventElapsedTime(&ms, h->ev[0], ev_red) == cudaSuccess)
+            info->ms_reduction = ms;
+        cudaEventDestroy(ev_red);
+    }
     return cudaGetLastError() ? 7 : 0;
 }
 
@@ -524,7 +566,7 @@ int spd_common(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, doubl
     if (info) { info->norm_a = norm_a; info->scale_exponent = e; info->kind_used = SQRTM_KIND_SPD; }
     if (!isfinite(norm_a)) return 5;
     if (norm_a == 0.0) return 2;
-    if (int rc = spd_decompose<R>(h, n, w)) return rc;
+    if (int rc = spd_decompose<R>(h, n, w, info)) return rc;
     if (cudaEventRecord(h->ev[1], s)) return 7;
     // X_0 = V diag(s) V^T, rounded to R, times 2^e (mirrored)
     scale_cols_kernel<R><<<grid1((int64_t)n * n), 256, 0, s>>>(w.V, w.s, w.W, ni); count_launch();
@@ -540,6 +582,13 @@ int spd_common(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, doubl
     if (st) return st;
     if (!refine) return 0;
     const double norm_as = ldexp(norm_a, -2 * e);
+    // split-TF32 tensor-core transforms when asked for and the TMA rules hold
+    const bool use_tc = sizeof(R) == sizeof(float) && o.precision == SQRTM_PREC_TF32X3 &&
+                        tc_gemm_supported(n, n, n, n, n, w.V, w.Rhat);
+    if (use_tc) {
+        // V^T into the (now free) Householder-vector buffer
+        transpose_kernel<R><<<dim3((unsigned)cdiv_i(n, 32), (unsigned)cdiv_i(n, 32)), dim3(32, 8), 0, s>>>(w.V, w.Qh, ni); count_launch();
+    }
     const bool fixed = o.steps >= 0;
     const int max_corr = fixed ? o.steps : o.maxit + 1;
     int status = 0, applied = 0, grew = 0;
@@ -562,13 +611,35 @@ int spd_common(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, doubl
             prev = rn;
         }
         // Y = (V^T Rhat V) ./ (s_i + s_j);  X += 2^e V Y V^T
-        if (launch_rgemm<float>(0, 0, ni, ni, ni, w.Rhat, ni, (const float *)w.V, ni, RG_STORE, (float *)w.W, ni, nullptr, nullptr, 0, 0.0, s)) return 7;
-        if (launch_rgemm<float>(1, 0, ni, ni, ni, (const float *)w.V, ni, (const float *)w.W, ni, RG_DIAG_SOLVE, (float *)w.Y, ni, (const float *)w.s, nullptr, 0, 0.0, s)) return 7;
-        if (launch_rgemm<float>(0, 0, ni, ni, ni, (const float *)w.V, ni, (const float *)w.Y, ni, RG_STORE, (float *)w.W, ni, nullptr, nullptr, 0, 0.0, s)) return 7;
-        if (launch_rgemm<float>(0, 1, ni, ni, ni, (const float *)w.W, ni, (const float *)w.V, ni, RG_SYM_ADD_F64, nullptr, 0, nullptr, dX, ldx, ldexp(1.0, e), s)) return 7;
+        if (use_tc) {
+            // tensor cores, split TF32; every operand K-contiguous:
+            //   W1 = Rhat^T V (= Rhat V, Rhat exactly symmetric),
+            //   Y = (V^T W1) ./ (s_i + s_j), W2^T = Y^T V^T, X += W2 V^T
+            float *Vf = (float *)w.V, *VT = (float *)w.Qh, *Wf = (float *)w.W, *Yf = (float *)w.Y;
+            TcEpilogue ep{};
+            ep.C = Wf; ep.ldc = ni;
+            if (launch_tc3_gemm(ni, ni, ni, w.Rhat, ni, Vf, ni, TC_EPI_STORE, ep, w.iscal + 2, s)) return 7;
+            ep.C = Yf; ep.s = (const float *)w.s;
+            if (launch_tc3_gemm(ni, ni, ni, Vf, ni, Wf, ni, TC_EPI_DIAG_SOLVE, ep, w.iscal + 2, s)) return 7;
+            ep.C = Wf; ep.s = nullptr;
+            if (launch_tc3_gemm(ni, ni, ni, Yf, ni, VT, ni, TC_EPI_STORE, ep, w.iscal + 2, s)) return 7;
+            TcEpilogue ex{};
+            ex.X = dX; ex.ldx = ldx; ex.scale = ldexp(1.0, e);
+            if (launch_tc3_gemm(ni, ni, ni, Wf, ni, VT, ni, TC_EPI_SYM_ADD_F64, ex, w.iscal + 2, s)) return 7;
+        } else {
+            if (launch_rgemm<float>(0, 0, ni, ni, ni, w.Rhat, ni, (const float *)w.V, ni, RG_STORE, (float *)w.W, ni, nullptr, nullptr, 0, 0.0, s)) return 7;
+            if (launch_rgemm<float>(1, 0, ni, ni, ni, (const float *)w.V, ni, (const float *)w.W, ni, RG_DIAG_SOLVE, (float *)w.Y, ni, (const float *)w.s, nullptr, 0, 0.0, s)) return 7;
+            if (launch_rgemm<float>(0, 0, ni, ni, ni, (const float *)w.V, ni, (const float *)w.Y, ni, RG_STORE, (float *)w.W, ni, nullptr, nullptr, 0, 0.0, s)) return 7;
+            if (launch_rgemm<float>(0, 1, ni, ni, ni, (const float *)w.W, ni, (const float *)w.V, ni, RG_SYM_ADD_F64, nullptr, 0, nullptr, dX, ldx, ldexp(1.0, e), s)) return 7;
+        }
         ++applied;
     }
     if (cudaEventRecord(h->ev[3], s)) return 7;
+    if (use_tc) {
+        int tcst = 0;
+        if (fetch_scalar<R>(h, &tcst, w.iscal + 2, sizeof(int))) return 7;
+        if (tcst) return tcst;
+    }
     if (status == 0 || status == 1) {
         if (cudaMemcpy2DAsync(w.xsave, n * sizeof(double), dX, ldx * sizeof(double), n * sizeof(double), n,
                               cudaMemcpyDeviceToDevice, s)) return 7;

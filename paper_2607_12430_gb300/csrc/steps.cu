@@ -7,6 +7,7 @@
 #include <algorithm>
 
 #include "handle.h"
+#include "tc_gemm.h"
 
 using namespace sqm;
 
@@ -66,7 +67,8 @@ static int schur_step(sqrtm_handle_t h, cplx<R> *T, cplx<R> *Q, int64_t n)
 {
     StepScratch ss; void *ex;
     size_t extra = Carve::round((n + 8) * sizeof(cplx<R>)) + Carve::round(8 * sizeof(R)) + Carve::round(sizeof(SchurDesc<R>)) +
-                   Carve::round(qr_log_capacity(n) * sizeof(RotLog<R>)) + Carve::round(8 * sizeof(int));
+                   Carve::round(qr_log_capacity(n) * sizeof(RotLog<R>)) + Carve::round(8 * sizeof(int)) +
+                   Carve::round(qr_win_capacity(n) * sizeof(WinRec)) + Carve::round(qr_u_capacity(n) * sizeof(cplx<R>));
     if (int rc = step_scratch(h, n, extra, &ss, &ex)) return rc;
     Carve c(ex);
     cplx<R> *v = c.take<cplx<R>>(n + 8);
@@ -74,10 +76,14 @@ static int schur_step(sqrtm_handle_t h, cplx<R> *T, cplx<R> *Q, int64_t n)
     SchurDesc<R> *dd = c.take<SchurDesc<R>>(1);
     RotLog<R> *rlog = c.take<RotLog<R>>(qr_log_capacity(n));
     int *qstate = c.take<int>(8);
+    WinRec *wrec = c.take<WinRec>(qr_win_capacity(n));
+    cplx<R> *ubuf = c.take<cplx<R>>(qr_u_capacity(n));
     SchurDesc<R> hd;
     hd.T = T; hd.Q = Q; hd.v = v; hd.beta = beta; hd.status = ss.iscal + 1; hd.n = (int)n; hd.ld = (int)n;
     hd.counters = nullptr;
     hd.log = rlog; hd.state = qstate; hd.log_cap = (int)std::min<int64_t>(qr_log_capacity(n), INT32_MAX);
+    hd.win = wrec; hd.win_cap = (int)std::min<int64_t>(qr_win_capacity(n), INT32_MAX);
+    hd.ubuf = ubuf; hd.u_cap = qr_u_capacity(n);
     memcpy(h->staging.p, &hd, sizeof(hd));
     if (cudaMemcpyAsync(dd, h->staging.p, sizeof(hd), cudaMemcpyHostToDevice, h->stream)) return 7;
     if (cudaStreamSynchronize(h->stream)) return 7;
@@ -203,4 +209,22 @@ extern "C" int sqrtm_step_transform_out_update(sqrtm_handle_t h, const void *dQ,
     if (launch_cgemm<float>(OP_N, OP_N, (int)n, (int)n, (int)n, Q, (int)n, false, (const cplx<float> *)dY, (int)n, EPI_STORE, W, (int)n, nullptr, 0, 0.0, h->stream)) return 7;
     if (launch_cgemm<float>(OP_N, OP_H, (int)n, (int)n, (int)n, W, (int)n, false, Q, (int)n, EPI_REAL_ADD_F64, nullptr, 0, dX, ldx, ldexp(1.0, e), h->stream)) return 7;
     return cudaStreamSynchronize(h->stream) ? 7 : 0;
+}
+
+extern "C" int sqrtm_step_gemm_tf32x3(sqrtm_handle_t h, int64_t M, int64_t N, int64_t K,
+                                      const float *dA, int64_t lda, const float *dB, int64_t ldb,
+                                      float *dC, int64_t ldc)
+{
+    if (!h) return -1;
+    if (M < 0 || N < 0 || K < 0) return -2;
+    if (M == 0 || N == 0) return 0;
+    if (K == 0 || !tc_gemm_supported(M, N, K, lda, ldb, dA, dB) || ldc < M) return -4;
+    StepScratch ss; void *ex;
+    if (int rc = step_scratch(h, 1, 0, &ss, &ex)) return rc;
+    TcEpilogue ep{};
+    ep.C = dC; ep.ldc = ldc;
+    if (launch_tc3_gemm((int)M, (int)N, (int)K, dA, (int)lda, dB, (int)ldb, TC_EPI_STORE, ep, ss.iscal + 1, h->stream)) return 7;
+    int st = 0;
+    if (fetch(h, &st, ss.iscal + 1, sizeof(int))) return 7;
+    return st;
 }

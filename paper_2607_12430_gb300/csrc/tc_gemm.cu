@@ -1,0 +1,362 @@
+// tc_gemm.cu -- split-TF32 ("3xTF32") dense products on the 5th-generation
+// tensor cores (tcgen05) for the low-precision transforms of Algorithm 3
+// (steps 8 and 10: V^T R V and V Y V^T).
+//
+// C (M x N) = A B with both operands given K-contiguous ("K-major"):
+//   A(i, k) = a[k + i * lda]   (row i of A is contiguous),
+//   B(k, j) = b[k + j * ldb]   (column j of B is contiguous),
+// FP32 in global memory.  Each operand x is split on the fly into
+// hi = tf32(x) (round to nearest, 10 explicit mantissa bits) and
+// lo = tf32(x - hi); C = A_hi B_hi + A_hi B_lo + A_lo B_hi is accumulated in
+// FP32 in tensor memory (relative error about 2^-21, close to FP32).
+//
+// Per CTA: a 128 x 128 tile of C, K in steps of 32.  TMA loads the FP32 tiles
+// (128 rows x 128 bytes, 128-byte swizzle) into a 3-stage ring; all threads
+// split them in shared memory (hi in place, lo beside it); one thread issues
+// 3 x 4 tcgen05.mma (M = 128, N = 128, K = 8) per stage and commits them to
+// the stage's mbarrier; the accumulator (128 TMEM columns) is read back with
+// tcgen05.ld for a fused epilogue.  Every mbarrier wait is bounded (about
+// 2 s of globaltimer); on timeout the kernel records status 6, drains its
+// outstanding copies (bounded too), frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+#include "internal.h"
+#include "tc_gemm.h"
+
+namespace sqm {
+
+static constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 32, TC_STAGES = 3, TC_THREADS = 128;
+static constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 4;          // 16 KB
+static constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;          // A, A_lo, B, B_lo
+static constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 256;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait on an mbarrier phase; false after ~2 s
+__device__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (globaltimer_ns() - t0 > 2000000000ull) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row groups 1024 bytes apart
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+    d |= (uint64_t)1 << 16;                     // leading byte offset (unused with swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset
+    d |= (uint64_t)1 << 46;                     // descriptor version
+    d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+    return d;
+}
+
+// instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = 128
+__host__ __device__ constexpr uint32_t idesc_tf32_128x128()
+{
+    return (1u << 4)                    // D format F32
+           | (2u << 7) | (2u << 10)     // A, B format TF32
+           | ((128u >> 3) << 17)        // N / 8
+           | ((128u >> 4) << 24);       // M / 16
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15,"
+        " %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// round an FP32 value to TF32 (nearest, ties away from zero on the bit
+// pattern); the result keeps 10 explicit mantissa bits
+__device__ __forceinline__ float to_tf32(float x)
+{
+    uint32_t b = __float_as_uint(x);
+    b = (b + 0x1000u) & 0xFFFFE000u;
+    return __uint_as_float(b);
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+tc3_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
+                int K, TcEpilogue ep, int *err)
+{
+    extern __shared__ unsigned char smraw[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_BN;
+    if ((EPI == TC_EPI_SYM_ADD_F64) && m0 > n0) return;  // mirrored epilogue: upper block triangle only
+
+    // 1024-aligned stage ring, then barriers and the TMEM address slot
+    unsigned char *base = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(base + TC_STAGES * TC_STAGE_BYTES);
+    uint64_t *done = full + TC_STAGES;
+    uint32_t *tmem_slot = (uint32_t *)(done + TC_STAGES);
+    __shared__ int s_fail;
+
+    if (tid == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&done[s], 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(128)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int KT = (K + TC_BK - 1) / TC_BK;
+    auto stage_ptr = [&](int s, int which) { return base + s * TC_STAGE_BYTES + which * TC_TILE_BYTES; };
+    auto issue_load = [&](int t) {
+        const int s = t % TC_STAGES;
+        mbar_arrive_expect_tx(&full[s], 2 * TC_TILE_BYTES);
+        tma_load_2d(stage_ptr(s, 0), &mapA, &full[s], t * TC_BK, m0);
+        tma_load_2d(stage_ptr(s, 2), &mapB, &full[s], t * TC_BK, n0);
+    };
+    int issued = 0;  // TMA loads issued (thread 0's count)
+    if (tid == 0)
+        for (; issued < std::min(TC_STAGES - 1, KT); ++issued) issue_load(issued);
+
+    constexpr uint32_t IDESC = idesc_tf32_128x128();
+    bool fail = false;
+    int consumed = 0;   // tiles whose TMA completion every thread has observed
+    int committed = 0;  // tiles whose MMAs thread 0 has committed
+    for (int t = 0; t < KT && !fail; ++t) {
+        const int s = t % TC_STAGES;
+        // producer: refill the stage that tile t-1 used, once its MMAs are done
+        if (tid == 0 && issued < KT) {
+            if (t >= 1) {
+                const int sp = (t - 1) % TC_STAGES;
+                if (!mbar_wait(&done[sp], ((t - 1) / TC_STAGES) & 1)) s_fail = 1;
+            }
+            if (!s_fail) { issue_load(issued); ++issued; }
+        }
+        // everyone: wait for tile t
+        if (!mbar_wait(&full[s], (t / TC_STAGES) & 1)) s_fail = 1;
+        __syncthreads();
+        if (s_fail) { fail = true; break; }
+        consumed = t + 1;
+        // split A and B into hi (in place) and lo (beside)
+        {
+            float4 *a = (float4 *)stage_ptr(s, 0), *alo = (float4 *)stage_ptr(s, 1);
+            float4 *b = (float4 *)stage_ptr(s, 2), *blo = (float4 *)stage_ptr(s, 3);
+            constexpr int NV = TC_TILE_BYTES / 16;
+            for (int v = tid; v < NV; v += TC_THREADS) {
+                float4 x = a[v], h, l;
+                h.x = to_tf32(x.x); h.y = to_tf32(x.y); h.z = to_tf32(x.z); h.w = to_tf32(x.w);
+                l.x = to_tf32(x.x - h.x); l.y = to_tf32(x.y - h.y); l.z = to_tf32(x.z - h.z); l.w = to_tf32(x.w - h.w);
+                a[v] = h; alo[v] = l;
+                x = b[v];
+                h.x = to_tf32(x.x); h.y = to_tf32(x.y); h.z = to_tf32(x.z); h.w = to_tf32(x.w);
+                l.x = to_tf32(x.x - h.x); l.y = to_tf32(x.y - h.y); l.z = to_tf32(x.z - h.z); l.w = to_tf32(x.w - h.w);
+                b[v] = h; blo[v] = l;
+            }
+        }
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(stage_ptr(s, 0)), al = smem_u32(stage_ptr(s, 1));
+            const uint32_t b0 = smem_u32(stage_ptr(s, 2)), bl = smem_u32(stage_ptr(s, 3));
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 8; ++kk) {
+                const uint32_t off = kk * 32;  // 8 TF32 values = 32 bytes along K
+                const uint32_t acc0 = (t > 0 || kk > 0) ? 1u : 0u;
+                mma_tf32(tmem, smem_desc_sw128(a0 + off), smem_desc_sw128(b0 + off), IDESC, acc0);
+                mma_tf32(tmem, smem_desc_sw128(a0 + off), smem_desc_sw128(bl + off), IDESC, 1u);
+                mma_tf32(tmem, smem_desc_sw128(al + off), smem_desc_sw128(b0 + off), IDESC, 1u);
+            }
+            mma_commit(&done[s]);
+        }
+        committed = t + 1;
+    }
+    // wait for the last tile's MMAs (commits complete in issue order)
+    if (!fail && KT > 0) {
+        const int tl = KT - 1;
+        if (!mbar_wait(&done[tl % TC_STAGES], (tl / TC_STAGES) & 1)) s_fail = 1;
+    }
+    __syncthreads();
+    fail = s_fail != 0;
+    if (fail) {
+        if (tid == 0) {
+            atomicExch(err, 6);
+            // drain what is still in flight (bounded) before shared and tensor
+            // memory are released: TMA copies not yet observed, committed MMAs
+            for (int t = consumed; t < issued; ++t) mbar_wait(&full[t % TC_STAGES], (t / TC_STAGES) & 1);
+            if (committed > 0) mbar_wait(&done[(committed - 1) % TC_STAGES], ((committed - 1) / TC_STAGES) & 1);
+        }
+        __syncthreads();
+    } else {
+        tc_fence_after();
+        // epilogue: warp w owns rows 32w .. 32w+31 of the tile (TMEM lanes)
+        const int row = m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+            uint32_t r[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+            if (row < M) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int col = n0 + c0 + j;
+                    if (col >= N) continue;
+                    const float v = __uint_as_float(r[j]);
+                    if (EPI == TC_EPI_STORE) {
+                        ep.C[row + (int64_t)col * ep.ldc] = v;
+                    } else if (EPI == TC_EPI_DIAG_SOLVE) {
+                        ep.C[row + (int64_t)col * ep.ldc] = v / (ep.s[row] + ep.s[col]);
+                    } else {  // TC_EPI_SYM_ADD_F64
+                        if (row <= col) {
+                            const double x = ep.X[row + (int64_t)col * ep.ldx] + (double)v * ep.scale;
+                            ep.X[row + (int64_t)col * ep.ldx] = x;
+                            ep.X[col + (int64_t)row * ep.ldx] = x;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 2-D map over a K-contiguous operand: dim0 = K (contiguous), dim1 = rows
+static bool make_map(CUtensorMap *m, const float *ptr, int64_t kdim, int64_t rows, int64_t ld)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)kdim, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    cuuint32_t box[2] = {TC_BK, TC_BM};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)ptr, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+bool tc_gemm_supported(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, const void *A, const void *B)
+{
+    if (M <= 0 || N <= 0 || K <= 0) return false;
+    if ((lda * 4) % 16 || (ldb * 4) % 16) return false;           // TMA global stride rule
+    if (((uintptr_t)A) % 16 || ((uintptr_t)B) % 16) return false;  // TMA base alignment
+    return encode_fn() != nullptr;
+}
+
+cudaError_t launch_tc3_gemm(int M, int N, int K, const float *A, int lda, const float *B, int ldb, int epi,
+                            const TcEpilogue &ep, int *err, cudaStream_t s)
+{
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, A, K, M, lda) || !make_map(&mb, B, K, N, ldb)) return cudaErrorInvalidValue;
+    dim3 g((unsigned)cdiv_i(M, TC_BM), (unsigned)cdiv_i(N, TC_BN));
+    cudaError_t e;
+    switch (epi) {
+    case TC_EPI_STORE:
+        if ((e = allow_max_smem((const void *)tc3_gemm_kernel<TC_EPI_STORE>))) return e;
+        tc3_gemm_kernel<TC_EPI_STORE><<<g, TC_THREADS, TC_SMEM, s>>>(ma, mb, M, N, K, ep, err); count_launch();
+        break;
+    case TC_EPI_DIAG_SOLVE:
+        if ((e = allow_max_smem((const void *)tc3_gemm_kernel<TC_EPI_DIAG_SOLVE>))) return e;
+        tc3_gemm_kernel<TC_EPI_DIAG_SOLVE><<<g, TC_THREADS, TC_SMEM, s>>>(ma, mb, M, N, K, ep, err); count_launch();
+        break;
+    default:
+        if ((e = allow_max_smem((const void *)tc3_gemm_kernel<TC_EPI_SYM_ADD_F64>))) return e;
+        tc3_gemm_kernel<TC_EPI_SYM_ADD_F64><<<g, TC_THREADS, TC_SMEM, s>>>(ma, mb, M, N, K, ep, err); count_launch();
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace sqm

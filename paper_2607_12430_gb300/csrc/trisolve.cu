@@ -33,6 +33,19 @@ __device__ void load_tile(cplx<R> *dst, const cplx<R> *__restrict__ src, int ld,
     }
 }
 
+// Same tile with cp.async for the in-range part (zero padding written
+// directly); complete with cp_async_wait_all() and a barrier.
+template <class R>
+__device__ void load_tile_async(cplx<R> *dst, const cplx<R> *__restrict__ src, int ld, int rows,
+                                int cols)
+{
+    for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+        int i = e % TB, j = e / TB;
+        if (i < rows && j < cols) cp_async_elem<R>(&dst[i + j * TLD], &src[i + (int64_t)j * ld]);
+        else dst[i + j * TLD] = cplx<R>{0, 0};
+    }
+}
+
 // acc(r, c_q) -= sum_k A(r, k) B(k, c_q) for the 8 outputs a thread owns
 // (row r = tid % 32, columns c_q = tid / 32 + 4 q).
 template <class R>
@@ -95,6 +108,8 @@ rtrsyl_wave_kernel(const cplx<R> *__restrict__ S, int lds, int m, const cplx<R> 
     cplx<R> *tc = reinterpret_cast<cplx<R> *>(smraw);
     cplx<R> *ta = tc + TB * TLD;
     cplx<R> *tb = ta + TB * TLD;
+    cplx<R> *ta2 = tb + TB * TLD;
+    cplx<R> *tb2 = ta2 + TB * TLD;
     __shared__ int bad;
     const int Mb = (m + b - 1) / b, Nb = (nn + b - 1) / b;
     const int I = max(0, (Mb - 1) - w) + blockIdx.x;
@@ -109,22 +124,32 @@ rtrsyl_wave_kernel(const cplx<R> *__restrict__ S, int lds, int m, const cplx<R> 
     const int r = threadIdx.x & 31, c0 = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = tc[r + (c0 + 4 * q) * TLD];
-    for (int K = I + 1; K < Mb; ++K) {        // - S_IK Y_KJ
-        const int k0 = K * b, bk = min(b, m - k0);
-        load_tile(ta, S + i0 + (int64_t)k0 * lds, lds, bm, bk);
-        load_tile(tb, C + k0 + (int64_t)j0 * ldc, ldc, bk, bn);
+    // update terms: K = I+1..Mb-1 (S_IK Y_KJ), then K = 0..J-1 (Y_IK St_KJ);
+    // tiles of term t+1 are fetched asynchronously while term t is multiplied
+    const int nterm = (Mb - 1 - I) + J;
+    auto issue = [&](int t, cplx<R> *da, cplx<R> *db) {
+        if (t < Mb - 1 - I) {
+            const int k0 = (I + 1 + t) * b, bk = min(b, m - k0);
+            load_tile_async(da, S + i0 + (int64_t)k0 * lds, lds, bm, bk);
+            load_tile_async(db, C + k0 + (int64_t)j0 * ldc, ldc, bk, bn);
+        } else {
+            const int k0 = (t - (Mb - 1 - I)) * b, bk = min(b, nn - k0);
+            load_tile_async(da, C + i0 + (int64_t)k0 * ldc, ldc, bm, bk);
+            load_tile_async(db, St + k0 + (int64_t)j0 * ldst, ldst, bk, bn);
+        }
+    };
+    auto kdim = [&](int t) {
+        return (t < Mb - 1 - I) ? min(b, m - (I + 1 + t) * b) : min(b, nn - (t - (Mb - 1 - I)) * b);
+    };
+    if (nterm > 0) issue(0, ta, tb);
+    for (int t = 0; t < nterm; ++t) {
+        cplx<R> *ca = (t & 1) ? ta2 : ta, *cb = (t & 1) ? tb2 : tb;
+        cp_async_wait_all();
         __syncthreads();
-        tile_mms(acc, ta, tb, bk);
-        __syncthreads();
+        if (t + 1 < nterm) issue(t + 1, (t & 1) ? ta : ta2, (t & 1) ? tb : tb2);
+        tile_mms(acc, ca, cb, kdim(t));
     }
-    for (int K = 0; K < J; ++K) {             // - Y_IK St_KJ
-        const int k0 = K * b, bk = min(b, nn - k0);
-        load_tile(ta, C + i0 + (int64_t)k0 * ldc, ldc, bm, bk);
-        load_tile(tb, St + k0 + (int64_t)j0 * ldst, ldst, bk, bn);
-        __syncthreads();
-        tile_mms(acc, ta, tb, bk);
-        __syncthreads();
-    }
+    __syncthreads();
 #pragma unroll
     for (int q = 0; q < 8; ++q) tc[r + (c0 + 4 * q) * TLD] = acc[q];
     load_tile(ta, S + i0 + (int64_t)i0 * lds, lds, bm, bm);
@@ -198,6 +223,8 @@ trisqrt_off_kernel(const cplx<R> *__restrict__ T, int ldt, cplx<R> *S, int lds, 
     cplx<R> *tc = reinterpret_cast<cplx<R> *>(smraw);
     cplx<R> *ta = tc + TB * TLD;
     cplx<R> *tb = ta + TB * TLD;
+    cplx<R> *ta2 = tb + TB * TLD;
+    cplx<R> *tb2 = ta2 + TB * TLD;
     __shared__ int bad;
     const int Nb = (n + b - 1) / b;
     const int I = blockIdx.x, J = I + dblk;
@@ -211,14 +238,21 @@ trisqrt_off_kernel(const cplx<R> *__restrict__ T, int ldt, cplx<R> *S, int lds, 
     const int r = threadIdx.x & 31, c0 = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = tc[r + (c0 + 4 * q) * TLD];
-    for (int K = I + 1; K < J; ++K) {
-        const int k0 = K * b, bk = min(b, n - k0);
-        load_tile(ta, S + i0 + (int64_t)k0 * lds, lds, bm, bk);
-        load_tile(tb, S + k0 + (int64_t)j0 * lds, lds, bk, bn);
+    const int nterm = J - I - 1;  // K = I+1 .. J-1
+    auto issue = [&](int t, cplx<R> *da, cplx<R> *db) {
+        const int k0 = (I + 1 + t) * b, bk = min(b, n - k0);
+        load_tile_async(da, S + i0 + (int64_t)k0 * lds, lds, bm, bk);
+        load_tile_async(db, S + k0 + (int64_t)j0 * lds, lds, bk, bn);
+    };
+    if (nterm > 0) issue(0, ta, tb);
+    for (int t = 0; t < nterm; ++t) {
+        cplx<R> *ca = (t & 1) ? ta2 : ta, *cb = (t & 1) ? tb2 : tb;
+        cp_async_wait_all();
         __syncthreads();
-        tile_mms(acc, ta, tb, bk);
-        __syncthreads();
+        if (t + 1 < nterm) issue(t + 1, (t & 1) ? ta : ta2, (t & 1) ? tb : tb2);
+        tile_mms(acc, ca, cb, min(b, n - (I + 1 + t) * b));
     }
+    __syncthreads();
 #pragma unroll
     for (int q = 0; q < 8; ++q) tc[r + (c0 + 4 * q) * TLD] = acc[q];
     load_tile(ta, S + i0 + (int64_t)i0 * lds, lds, bm, bm);
@@ -241,7 +275,7 @@ template <class R>
 static cudaError_t set_smem(const void *fn, size_t bytes)
 {
     if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return allow_max_smem(fn);
 }
 
 template <class R>
@@ -251,7 +285,7 @@ cudaError_t launch_trisqrt(const cplx<R> *T, int ldt, cplx<R> *S, int lds, int n
     if (n <= 0) return cudaSuccess;
     int b = blks < 1 ? 1 : (blks > TB ? TB : blks);
     int Nb = (n + b - 1) / b;
-    size_t sm1 = TB * TLD * sizeof(cplx<R>), sm3 = 3 * sm1;
+    size_t sm1 = TB * TLD * sizeof(cplx<R>), sm3 = 5 * sm1;
     cudaError_t err;
     if ((err = set_smem<R>((const void *)trisqrt_off_kernel<R>, sm3))) return err;
     trisqrt_diag_kernel<R><<<Nb, kTriThreads, sm1, s>>>(T, ldt, S, lds, n, b, d_status); count_launch();
@@ -267,7 +301,7 @@ cudaError_t launch_rtrsyl(const cplx<R> *S, int lds, int m, const cplx<R> *St, i
     if (m <= 0 || nn <= 0) return cudaSuccess;
     int b = blks < 1 ? 1 : (blks > TB ? TB : blks);
     int Mb = (m + b - 1) / b, Nb = (nn + b - 1) / b;
-    size_t sm3 = 3 * TB * TLD * sizeof(cplx<R>);
+    size_t sm3 = 5 * TB * TLD * sizeof(cplx<R>);
     cudaError_t err;
     if ((err = set_smem<R>((const void *)rtrsyl_wave_kernel<R>, sm3))) return err;
     for (int w = 0; w <= Mb + Nb - 2; ++w) {

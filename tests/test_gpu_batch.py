@@ -31,7 +31,7 @@ def test_batched_matches_oracle():
     items = synth.batch_case(count=24, seed=synth.BASE_SEED + 3)
     As = [torch.from_numpy(it[1]).cuda() for it in items]
     Xs, st = mp.sqrtm_mixed_batched(As, steps=4)
-    assert st == [0] * len(items)
+    assert st == [0] * len(items), (st, mp.last_error())
     for it, X in zip(items, Xs):
         Xo = _reference(it)
         tol = 1e-13 if it[0] == "spd" else 1e-12
