@@ -99,6 +99,24 @@ SQRTM_API int sqrtm_step_gemm_tf32x3(sqrtm_handle_t h, int64_t M, int64_t N, int
                                      const float *dA, int64_t lda, const float *dB, int64_t ldb,
                                      float *dC, int64_t ldc);
 
+/* The residual above for callers that cannot allocate device memory.  The
+ * paper has no counterpart: this is a library service.  It takes no handle
+ * (a handle allocates its workspace on first use); its scratch -- the norm's
+ * per-block partial sums -- is a fixed array inside this library, held on
+ * every GPU that loads the library until the process exits.
+ *   dA, dX: n x n FP64 (lda, ldx); dRhat: n x n FP32 output (ld n) receiving
+ *   fl32((4^-e A - (2^-e X)^2)); norm_host: optional host pointer receiving
+ *   ||R||_F (when given the call waits for the GPU); stream: cudaStream_t.
+ * Limits: n <= 4096, otherwise -5.  Calls no cudaMalloc or cudaFree and no
+ * allocating library routine.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  All calls share the one array: calls that overlap on
+ * the GPU race on it.  Nothing in it needs to start at zero: each call writes
+ * every partial it later reads. */
+SQRTM_API int sqrtm_step_residual_noalloc(const double *dA, int64_t lda, const double *dX,
+                                          int64_t ldx, int64_t n, int e, float *dRhat,
+                                          double *norm_host, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -99,6 +99,7 @@ _SIGS = {
     "sqrtm_step_transform_in_spd": ([_P, _P, _P, _P, _P, _L], _I),
     "sqrtm_step_transform_out_update_spd": ([_P, _P, _P, _L, _I, _P, _L], _I),
     "sqrtm_step_gemm_tf32x3": ([_P, _L, _L, _L, _P, _L, _P, _L, _P, _L], _I),
+    "sqrtm_step_residual_noalloc": ([_P, _L, _P, _L, _L, _I, _P, ctypes.POINTER(_D), _P], _I),
 }
 
 
@@ -343,6 +344,17 @@ def step_residual(A_cm, X_cm, n, e=0):
     Rhat = torch.empty(n * n, dtype=torch.float32, device=A_cm.device)
     nrm = ctypes.c_double()
     _rc(lib().sqrtm_step_residual(handle(), _ptr(A_cm), n, _ptr(X_cm), n, n, e, _ptr(Rhat), ctypes.byref(nrm)), "residual")
+    return Rhat, nrm.value
+
+
+def step_residual_noalloc(A_cm, X_cm, n, e=0, out=None):
+    """The FP64 residual without any device allocation inside the library
+    (for callers that cannot allocate); ``out`` may supply the FP32 output
+    buffer so that this call allocates nothing at all."""
+    Rhat = out if out is not None else torch.empty(n * n, dtype=torch.float32, device=A_cm.device)
+    nrm = ctypes.c_double()
+    _rc(lib().sqrtm_step_residual_noalloc(_ptr(A_cm), n, _ptr(X_cm), n, n, e, _ptr(Rhat),
+                                          ctypes.byref(nrm), _stream_ptr()), "residual_noalloc")
     return Rhat, nrm.value
 
 
