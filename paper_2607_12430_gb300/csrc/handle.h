@@ -8,8 +8,8 @@
 #include <vector>
 
 #include "internal.h"
-#include "../../include/sqrtm_mp.h"
-#include "../../include/sqrtm_mp_steps.h"
+#include "sqrtm_mp.h"
+#include "sqrtm_mp_steps.h"
 
 // ---------------------------------------------------------------------------
 // handle

@@ -22,21 +22,21 @@ void count_launch();
 // different sizes).
 cudaError_t allow_max_smem(const void *kernel);
 
-// One logged Givens rotation of the QR iteration: position k (acts on
-// indices k, k+1), the active block [lo, hi] of its sweep, G = [c s; -conj(s) c].
+// One entry of a chase window's rotation table: G = [c s; -conj(s) c] with
+// s = sx + i sy; act = 0 marks a step in which the bulge did not move.
 template <class R>
-struct RotLog {
-    int k, lo, hi, pad;
-    R c, pad2;
-    cplx<R> s;
+struct alignas(16) RotLog {
+    R c, sx, sy, act;
 };
 
-// One chase window of the QR iteration: its rotations are log entries
-// [start, start + count), they act on indices kmin .. kmin + rr - 1, the
-// sweep's active block is [lo, hi], and the window's accumulated rotation
-// product U (rr x rr) is stored at ubuf + uoff.
+// One chase window of the QR iteration: its rotation table is log entries
+// [start, start + W NB) (step q, bulge g at start + q NB + g; that rotation
+// acts on indices kbase + q + 3 (NB - 1 - g) and the next one), nsteps steps
+// are used, all rotations act on indices kmin .. kmin + rr - 1, the sweep's
+// active block is [lo, hi], and the window's accumulated rotation product U
+// (rr x rr) is stored at ubuf + uoff.
 struct WinRec {
-    int start, count, kmin, rr, lo, hi;
+    int start, kbase, nsteps, kmin, rr, lo, hi, pad;
     long long uoff;
 };
 
@@ -84,7 +84,7 @@ cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, in
 // scratch sizes per matrix of size n: rotation log entries, window records,
 // elements of accumulated window products (one round of the QR iteration
 // stops at a sweep boundary before any of them would overflow)
-inline int64_t qr_log_capacity(int64_t n) { return n <= 1 ? 64 : std::max<int64_t>(4 * n * n, 256 * n); }
+inline int64_t qr_log_capacity(int64_t n) { return n <= 1 ? 64 : std::max<int64_t>(std::max<int64_t>(4 * n * n, 256 * n), 8192); }
 inline int64_t qr_win_capacity(int64_t n) { return std::max<int64_t>(n * n / 2, 1024); }
 inline int64_t qr_u_capacity(int64_t n) { return std::max<int64_t>(24 * n * n, 64 * 64 * 64); }
 

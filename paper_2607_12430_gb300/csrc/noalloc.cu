@@ -17,7 +17,7 @@
 #include <mutex>
 
 #include "internal.h"
-#include "../../include/sqrtm_mp_steps.h"
+#include "sqrtm_mp_steps.h"
 
 namespace {
 

@@ -2,23 +2,30 @@
 // upper triangular Schur factor T (Algorithm 2, step 1), accumulating the
 // Givens rotations into the Schur vectors Z.
 //
-// Organisation (one CTA per matrix for the chase, many CTAs for the rest):
+// Organisation (one CTA of 512 threads per matrix for the chase, many CTAs
+// for the rest):
 //
-//  * Each sweep applies nb single shifts at once (nb = NB when the active
-//    block [lo, hi] is large, the eigenvalues of its trailing nb x nb block;
-//    nb = 1 with the Wilkinson shift otherwise).  Bulge g starts 3 positions
-//    behind bulge g-1 and all bulges advance one position per step, so the
-//    rotations of one step act on disjoint row pairs (left) and disjoint
-//    column pairs (right) and are applied by different warps at once.  The
-//    result equals nb consecutive single-shift sweeps.
-//  * The chase runs in windows of W steps on the (W + 3 nb + 3)^2 block
-//    around the bulges in shared memory.  After a window its rotations are
-//    applied at once to the rest of the ACTIVE block only (rows to the right
-//    of the window, columns above it) and appended to a rotation log.
+//  * Each sweep applies nb single shifts at once: nb = min(NB, (m - 2) / 4)
+//    for an active block [lo, hi] of size m, the shifts being the eigenvalues
+//    of its trailing nb x nb block (one warp computes them by single-shift QR
+//    in shared memory); nb = 1 uses the Wilkinson shift.  Bulge g starts 3
+//    positions behind bulge g-1 and all bulges advance one position per step,
+//    so the rotations of one step act on disjoint row pairs (left) and
+//    disjoint column pairs (right); warp g moves bulge g.  The result equals
+//    nb consecutive single-shift sweeps.
+//  * The chase runs in windows of W steps on the (W + 3 NB)^2 block around
+//    the bulges in shared memory.  A window's rotations form a dense W x NB
+//    table (step-major, inactive entries marked), which is the rotation log.
+//    After a window its rotations are applied to the rest of the ACTIVE block
+//    (rows to the right of the window, columns above it) by all threads:
+//    each row or column segment is shared by 4 threads, which take the
+//    bulges g = sub, sub + 4, ... of every step in lock-step (a rotation of
+//    bulge g at step q needs bulge g-1's rotation of step q-2 only).
 //  * Entries outside the active block are never read again by the iteration,
 //    so their updates (columns right of hi, rows above lo) and all updates of
-//    Z are deferred and applied from the log afterwards: first a pass over
-//    rows (right rotations), then a pass over columns (left rotations).  For
+//    Z are deferred: each window's rotations are multiplied into a small
+//    unitary U_w (one CTA per window), then a pass over rows applies
+//    x <- x U_w and a pass over columns y <- U_w^H y, window by window.  For
 //    any entry every deferred right rotation precedes every deferred left one
 //    (the active block only shrinks from below or moves up), so that order
 //    is exact.
@@ -33,12 +40,31 @@
 
 namespace sqm {
 
-static constexpr int kQrThreads = 256;
 static constexpr int kItMax = 60;
+static constexpr int kQrThreads = 512;           // chase CTA
+static constexpr int kQrTpc = 4;                 // threads per row/column segment in the updates
+static constexpr int kQrCh = kQrThreads / kQrTpc;  // segments per update chunk
 
 template <class R> struct QrCfg;
-template <> struct QrCfg<float> { static constexpr int W = 32, NB = 4, CH = 256; };
-template <> struct QrCfg<double> { static constexpr int W = 16, NB = 4, CH = 128; };
+template <> struct QrCfg<float> { static constexpr int W = 32, NB = 16; };
+template <> struct QrCfg<double> { static constexpr int W = 16, NB = 8; };
+
+// Shared-memory geometry of the chase kernel.
+template <class R>
+struct QrDims {
+    static constexpr int W = QrCfg<R>::W, NB = QrCfg<R>::NB;
+    static constexpr int BW = W + 3 * NB;       // largest window block
+    static constexpr int BLD = BW + 1;          // its leading dimension (odd: no bank conflicts)
+    static constexpr int RR = W + 3 * NB - 2;   // largest index range of a window's rotations
+    static constexpr int RLD = RR + 1;          // column tile leading dimension
+    static constexpr int CLD = kQrCh + 1;       // row tile leading dimension
+    static constexpr int TILE = (kQrCh * RLD > RR * CLD) ? kQrCh * RLD : RR * CLD;
+    static constexpr size_t chase_smem =
+        (size_t)(BW * BLD + TILE) * sizeof(cplx<R>) + (size_t)W * NB * sizeof(RotLog<R>);
+    static constexpr size_t build_smem = (size_t)RR * (RR + 1) * sizeof(cplx<R>) + (size_t)W * NB * sizeof(RotLog<R>);
+    static_assert(NB % kQrTpc == 0, "bulges per thread");
+    static_assert(NB * 16 <= kQrThreads && NB % 2 == 0, "one half-warp per bulge");
+};
 
 // Complex Givens G = [c s; -conj(s) c] with c real and G [x; y] = [r; 0].
 template <class R>
@@ -74,78 +100,265 @@ __device__ cplx<R> wilkinson(cplx<R> a, cplx<R> b, cplx<R> c, cplx<R> d)
     return d;
 }
 
-// Eigenvalues of a small upper Hessenberg matrix M (nb x nb, column-major,
-// ld NBMAX) by single-shift QR without vectors; one thread.  M is destroyed.
-template <class R, int NBMAX>
-__device__ void small_eigvals(cplx<R> *M, int nb, cplx<R> *out)
+// The same rotation for FP32 from |x|^2 and |y|^2 with two square roots and
+// two divisions instead of three hypot calls and six divisions (the chase's
+// critical path).  All four are correctly rounded, so c^2 + |s|^2 - 1 has no
+// systematic part (approximate reciprocal square roots do, and the bias
+// accumulates over the thousands of rotations applied to each Schur
+// vector).  Tiny or huge arguments take the scaled path.
+template <class R>
+__device__ __forceinline__ void givens_fast(cplx<R> x, cplx<R> y, R &c, cplx<R> &s, cplx<R> &r)
 {
+    givens(x, y, c, s, r);
+}
+template <>
+__device__ __forceinline__ void givens_fast<float>(cplx<float> x, cplx<float> y, float &c, cplx<float> &s,
+                                                   cplx<float> &r)
+{
+    const float ax2 = fmaf(x.x, x.x, x.y * x.y), ay2 = fmaf(y.x, y.x, y.y * y.y);
+    const float nrm2 = ax2 + ay2;
+    if (!(ax2 >= 1e-30f) || !(nrm2 <= 1e30f)) {
+        givens(x, y, c, s, r);
+        return;
+    }
+    const float ax = sqrtf(ax2), nrm = sqrtf(nrm2);
+    c = ax / nrm;
+    const float f = 1.0f / (ax * nrm);
+    s = cplx<float>{(x.x * y.x + x.y * y.y) * f, (x.y * y.x - x.x * y.y) * f};  // x conj(y) / (|x| ||(x, y)||)
+    const float gsc = nrm / ax;
+    r = cplx<float>{x.x * gsc, x.y * gsc};
+}
+
+// Cheaper rotation for the shift computation only (eigenvalue estimates,
+// never applied to T or Z): reciprocal square roots instead of correctly
+// rounded square roots and divisions.
+template <class R>
+__device__ __forceinline__ void givens_approx(cplx<R> x, cplx<R> y, R &c, cplx<R> &s, cplx<R> &r)
+{
+    givens(x, y, c, s, r);
+}
+template <>
+__device__ __forceinline__ void givens_approx<float>(cplx<float> x, cplx<float> y, float &c, cplx<float> &s,
+                                                     cplx<float> &r)
+{
+    const float ax2 = fmaf(x.x, x.x, x.y * x.y), ay2 = fmaf(y.x, y.x, y.y * y.y);
+    const float nrm2 = ax2 + ay2;
+    if (!(ax2 >= 1e-30f) || !(nrm2 <= 1e30f)) {
+        givens(x, y, c, s, r);
+        return;
+    }
+    const float inv = rsqrtf(nrm2), invx = rsqrtf(ax2);
+    const float f = invx * inv;
+    c = ax2 * f;
+    s = cplx<float>{(x.x * y.x + x.y * y.y) * f, (x.y * y.x - x.x * y.y) * f};
+    const float gsc = nrm2 * f;
+    r = cplx<float>{x.x * gsc, x.y * gsc};
+}
+
+// Eigenvalues of a small upper Hessenberg matrix M (nb x nb, nb <= 32,
+// column-major, leading dimension LDM) by single-shift QR without vectors,
+// one warp: lane j updates column j of a row rotation and row j of a column
+// rotation.  Only the active block is updated.  M is destroyed; out[0..nb-1]
+// receives the eigenvalues.
+template <class R, int LDM>
+__device__ void warp_small_eigvals(cplx<R> *M, int nb, cplx<R> *out)
+{
+    const int lane = threadIdx.x & 31;
     const R eps = num<R>::eps;
     int hi = nb - 1, it = 0;
     while (hi > 0) {
-        int lo = hi;
-        while (lo > 0) {
-            cplx<R> sub = M[lo + (lo - 1) * NBMAX];
-            R as = hypot(sub.x, sub.y);
-            cplx<R> a = M[lo + lo * NBMAX], b = M[(lo - 1) + (lo - 1) * NBMAX];
-            if (as == R(0) || as <= eps * (hypot(a.x, a.y) + hypot(b.x, b.y))) break;
-            --lo;
+        bool small = false;
+        if (lane >= 1 && lane <= hi) {
+            const cplx<R> sub = M[lane + (lane - 1) * LDM];
+            const R as = hypot(sub.x, sub.y);
+            const cplx<R> a = M[lane + lane * LDM], b = M[(lane - 1) + (lane - 1) * LDM];
+            small = as == R(0) || as <= eps * (hypot(a.x, a.y) + hypot(b.x, b.y));
         }
-        if (lo == hi) { out[hi] = M[hi + hi * NBMAX]; --hi; it = 0; continue; }
-        if (++it > 40) {  // give up: use the diagonal of the unreduced block
-            for (int i = lo; i <= hi; ++i) out[i] = M[i + i * NBMAX];
-            hi = lo - 1;
+        const unsigned bal = __ballot_sync(0xffffffffu, small);
+        const int lo = bal ? 31 - __clz(bal) : 0;
+        if (lo == hi) {
+            if (lane == 0) out[hi] = M[hi + hi * LDM];
+            --hi;
             it = 0;
+            __syncwarp();
             continue;
         }
-        cplx<R> mu = wilkinson(M[(hi - 1) + (hi - 1) * NBMAX], M[(hi - 1) + hi * NBMAX],
-                               M[hi + (hi - 1) * NBMAX], M[hi + hi * NBMAX]);
-        R c; cplx<R> s, r;
+        if (++it > 40) {  // give up: the diagonal of the unreduced block
+            for (int i = lo + lane; i <= hi; i += 32) out[i] = M[i + i * LDM];
+            hi = lo - 1;
+            it = 0;
+            __syncwarp();
+            continue;
+        }
+        const cplx<R> mu = wilkinson(M[(hi - 1) + (hi - 1) * LDM], M[(hi - 1) + hi * LDM],
+                                     M[hi + (hi - 1) * LDM], M[hi + hi * LDM]);
         for (int k = lo; k < hi; ++k) {
-            if (k == lo) givens(M[lo + lo * NBMAX] - mu, M[(lo + 1) + lo * NBMAX], c, s, r);
-            else givens(M[k + (k - 1) * NBMAX], M[(k + 1) + (k - 1) * NBMAX], c, s, r);
-            for (int j = (k == lo ? k : k - 1); j < nb; ++j) {
-                cplx<R> p = M[k + j * NBMAX], q = M[(k + 1) + j * NBMAX];
-                M[k + j * NBMAX] = c * p + s * q;
-                M[(k + 1) + j * NBMAX] = c * q - conj(s) * p;
+            // lane j < 32 owns column j of the row pair; x, y sit in column js
+            const int js = (k == lo) ? k : k - 1;
+            const bool lj = lane >= js && lane <= hi;
+            cplx<R> p{0, 0}, q{0, 0};
+            if (lj) {
+                p = M[k + lane * LDM];
+                q = M[(k + 1) + lane * LDM];
             }
-            if (k > lo) M[(k + 1) + (k - 1) * NBMAX] = cplx<R>{0, 0};
-            for (int i = 0; i <= min(k + 2, hi); ++i) {
-                cplx<R> p = M[i + k * NBMAX], q = M[i + (k + 1) * NBMAX];
-                M[i + k * NBMAX] = c * p + conj(s) * q;
-                M[i + (k + 1) * NBMAX] = c * q - s * p;
+            cplx<R> x{__shfl_sync(0xffffffffu, p.x, js), __shfl_sync(0xffffffffu, p.y, js)};
+            const cplx<R> y{__shfl_sync(0xffffffffu, q.x, js), __shfl_sync(0xffffffffu, q.y, js)};
+            if (k == lo) x = x - mu;
+            R c;
+            cplx<R> s, r;
+            givens_approx(x, y, c, s, r);
+            if (lj) {
+                cplx<R> np = c * p + s * q, nq = c * q - conj(s) * p;
+                if (lane == js && k > lo) {
+                    np = r;
+                    nq = cplx<R>{0, 0};
+                }
+                M[k + lane * LDM] = np;
+                M[(k + 1) + lane * LDM] = nq;
+            }
+            __syncwarp();
+            if (lane >= lo && lane <= min(k + 2, hi)) {
+                const cplx<R> pp = M[lane + k * LDM], qq = M[lane + (k + 1) * LDM];
+                M[lane + k * LDM] = c * pp + conj(s) * qq;
+                M[lane + (k + 1) * LDM] = c * qq - s * pp;
+            }
+            __syncwarp();
+        }
+    }
+    if (hi == 0 && lane == 0) out[0] = M[0];
+    __syncwarp();
+}
+
+// Barrier among the NTH threads of the chase warps.
+template <int NTH>
+__device__ __forceinline__ void chase_bar()
+{
+    if constexpr (NTH == kQrThreads) __syncthreads();
+    else asm volatile("bar.sync 1, %0;" ::"n"(NTH) : "memory");
+}
+
+// Slot of bulge g in one step's row of the rotation table: the bulges are
+// split into kQrTpc runs of NB / kQrTpc consecutive bulges (one run per
+// updating thread), and the table stores run position j = g mod run length
+// major, so the kQrTpc threads of a segment read adjacent entries.
+template <int NB>
+__host__ __device__ __forceinline__ int rt_slot(int g)
+{
+    constexpr int NG = NB / kQrTpc;
+    return (g % NG) * kQrTpc + g / NG;
+}
+
+// Apply one window's rotations (table rt, steps 0..ns-1) to a segment of
+// indices kmin .. kmin + rr - 1 held at vec[i * STRIDE]; the rotation of
+// step q, bulge g acts on i = off + q + 3 (NB - 1 - g) and i + 1, with
+// off = kbase - kmin.  Bulge g moves in the steps q with
+// t0 + q in [3 g, span - 1 + 3 g] (and g < nb).  LEFT: rows of a column
+// (G [p; q]); otherwise columns of a row ([p q] G^H).
+//
+// The kQrTpc threads of a segment are consecutive lanes; thread sub takes
+// the NG = NB / kQrTpc consecutive bulges g = sub NG + j.  At step q they
+// span the L = 3 NG - 1 indices A(q) .. A(q) + L - 1, A(q) = A0 + q, which
+// the thread keeps in a register ring (index i at ring[(i - A0) mod L]; the
+// step loop is unrolled, so every ring index is a constant).  Each step the
+// thread loads the one new index A(q) + L - 1 -- written by the thread with
+// the bulges ahead at step q - 2 -- and stores A(q), which it no longer
+// touches and the thread behind reads at step q + 2; one __syncwarp per
+// step orders them.  All threads of the warp call this (on = false: no
+// segment).  Returns false if a bulge's index range leaves [0, rr) (a
+// malformed window: nothing is applied for that bulge).
+template <class R, int NB, int STRIDE, bool LEFT>
+__device__ __noinline__ bool apply_window(cplx<R> *vec, bool on, const RotLog<R> *rt, int ns, int off, int rr,
+                                          int sub, int t0, int span, int nb)
+{
+    constexpr int NG = NB / kQrTpc, L = 3 * NG - 1, W = QrCfg<R>::W;
+    const int A0 = off + 3 * (NB - NG * (sub + 1));
+    int qa[NG], len[NG];
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < NG; ++j) {
+        const int g = sub * NG + j;
+        const int a0 = max(0, 3 * g - t0), a1 = min(ns - 1, span - 1 + 3 * g - t0);
+        qa[j] = a0;
+        len[j] = (g < nb && a1 >= a0) ? a1 - a0 + 1 : 0;
+        if (len[j]) {
+            const int ia = off + a0 + 3 * (NB - 1 - g), ib = off + a1 + 3 * (NB - 1 - g);
+            if (ia < 0 || ib > rr - 2) {
+                len[j] = 0;
+                ok = false;
             }
         }
     }
-    if (hi == 0) out[0] = M[0];
+    cplx<R> ring[L];
+#pragma unroll
+    for (int i = 0; i < L - 1; ++i) {
+        const int r = A0 + i;
+        ring[i] = (on && r >= 0 && r < rr) ? vec[r * STRIDE] : cplx<R>{0, 0};
+    }
+    const RotLog<R> *rs = rt + sub;
+#pragma unroll 32
+    for (int q = 0; q < W; ++q) {
+        if (q < ns) {
+            if (on) {
+                {  // the new bottom index A(q) + L - 1
+                    const int r = A0 + q + L - 1;
+                    ring[(q + L - 1) % L] = (r >= 0 && r < rr) ? vec[r * STRIDE] : cplx<R>{0, 0};
+                }
+#pragma unroll
+                for (int j = 0; j < NG; ++j) {
+                    if ((unsigned)(q - qa[j]) < (unsigned)len[j]) {
+                        const RotLog<R> e = rs[q * NB + j * kQrTpc];
+                        const cplx<R> sv{e.sx, e.sy};
+                        cplx<R> &p = ring[(q + 3 * (NG - 1 - j)) % L];
+                        cplx<R> &w = ring[(q + 3 * (NG - 1 - j) + 1) % L];
+                        const cplx<R> p0 = p, w0 = w;
+                        if (LEFT) {
+                            p = e.c * p0 + sv * w0;
+                            w = e.c * w0 - conj(sv) * p0;
+                        } else {
+                            p = e.c * p0 + conj(sv) * w0;
+                            w = e.c * w0 - sv * p0;
+                        }
+                    }
+                }
+                {  // A(q) is final for this thread
+                    const int r = A0 + q;
+                    if (r >= 0 && r < rr) vec[r * STRIDE] = ring[q % L];
+                }
+                if (q == ns - 1) {  // last step: the rest of the ring
+#pragma unroll
+                    for (int i = 1; i < L; ++i) {
+                        const int r = A0 + q + i;
+                        if (r >= 0 && r < rr) vec[r * STRIDE] = ring[(q + i) % L];
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    return ok;
 }
 
 template <class R>
-__global__ void __launch_bounds__(kQrThreads)
+__global__ void __launch_bounds__(kQrThreads, 1)
 qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
 {
-    constexpr int W = QrCfg<R>::W, NB = QrCfg<R>::NB, CH = QrCfg<R>::CH;
-    constexpr int BWMAX = W + 3 * NB + 3;
-    constexpr int RRMAX = W + 3 * NB;  // rows touched by a window's rotations
-    extern __shared__ unsigned char smraw[];
-    cplx<R> *tile = reinterpret_cast<cplx<R> *>(smraw);  // (a')/(b') staging
-    __shared__ cplx<R> blk[BWMAX * BWMAX];
-    __shared__ int wk[NB][W];          // rotation positions of the window (-1: none)
-    __shared__ R wc[NB][W];
-    __shared__ cplx<R> ws[NB][W];
-    __shared__ cplx<R> s_r[NB];
+    using D = QrDims<R>;
+    constexpr int W = D::W, NB = D::NB, BLD = D::BLD, RLD = D::RLD, CLD = D::CLD;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cplx<R> *blk = reinterpret_cast<cplx<R> *>(smraw);   // window block, blk[a + b BLD]
+    cplx<R> *tile = blk + D::BW * BLD;                     // (a')/(b') staging
+    RotLog<R> *rt = reinterpret_cast<RotLog<R> *>(tile + D::TILE);  // rt[q NB + g]
     __shared__ cplx<R> s_mu[NB];
-    __shared__ int s_lo, s_hi, s_iter, s_status, s_done, s_nb, s_nlog, s_sweeps, s_stop, s_nwin;
-    __shared__ long long s_uoff;
-    __shared__ long long s_rots;
-    __shared__ int s_off[NB + 1];
-    __shared__ int s_goff[W];
-    __shared__ int s_first[NB], s_cnt[NB];
+    __shared__ cplx<R> s_m[NB * (NB + 1)];
+    __shared__ int s_lo, s_hi, s_iter, s_status, s_done, s_nb, s_sweeps, s_stop, s_nwin, s_nlog, s_small, s_bad;
+    __shared__ long long s_uoff, s_rots;
 
     const SchurDesc<R> d = descs[blockIdx.x];
     const int n = d.n, ld = d.ld;
     cplx<R> *T = d.T;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nt = blockDim.x;
+    constexpr int nt = kQrThreads;
+    const int sub = tid % kQrTpc, seg = tid / kQrTpc;
     const R eps = num<R>::eps;
     int *st = d.state;
     if (st[2]) {  // already finished: nothing new in the log
@@ -163,6 +376,7 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
         s_sweeps = st[4];
         s_rots = (long long)st[5] + ((long long)st[6] << 31);
         s_stop = 0;
+        s_bad = 0;
     }
     __syncthreads();
 
@@ -172,8 +386,8 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
         if (tid == 0) s_lo = 0;
         __syncthreads();
         for (int k = 1 + tid; k <= hi; k += nt) {
-            cplx<R> sub = T[k + (int64_t)(k - 1) * ld];
-            R as = hypot(sub.x, sub.y);
+            cplx<R> sub_ = T[k + (int64_t)(k - 1) * ld];
+            R as = hypot(sub_.x, sub_.y);
             cplx<R> a = T[k + (int64_t)k * ld], b = T[(k - 1) + (int64_t)(k - 1) * ld];
             if (as == R(0) || as <= eps * (hypot(a.x, a.y) + hypot(b.x, b.y))) atomicMax(&s_lo, k);
         }
@@ -190,11 +404,14 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
         }
         if (tid == 0) {
             const int m = hi - lo + 1;
-            int nb = (m >= 4 * NB + 2) ? NB : 1;
+            int nb = min(NB, max(1, (m - 2) / 4));
             const long long nwin_sweep = ((hi - lo) + 3 * (nb - 1) + W - 1) / W;
-            if (s_nlog + (long long)(hi - lo) * nb > d.log_cap || s_nwin + nwin_sweep > d.win_cap ||
-                s_uoff + nwin_sweep * (long long)(RRMAX * RRMAX) > d.u_cap) {
+            const bool fits = s_nlog + nwin_sweep * (W * NB) <= d.log_cap && s_nwin + nwin_sweep <= d.win_cap &&
+                              s_uoff + nwin_sweep * (long long)(D::RR * D::RR) <= d.u_cap;
+            s_small = 0;
+            if (!fits) {
                 s_stop = 1;  // drain the log first
+                if (s_nlog == 0 && s_nwin == 0 && s_uoff == 0) s_status = 7;  // can never fit
             } else {
                 if (lo > 0) T[lo + (int64_t)(lo - 1) * ld] = cplx<R>{0, 0};
                 int it = ++s_iter;
@@ -202,22 +419,15 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
                 if (it > kItMax) s_status = 3;
                 if (it % 10 == 0) {
                     nb = 1;
-                    cplx<R> sub = T[hi + (int64_t)(hi - 1) * ld];
+                    cplx<R> sb = T[hi + (int64_t)(hi - 1) * ld];
                     cplx<R> mu = T[hi + (int64_t)hi * ld];
-                    mu.x += R(0.75) * hypot(sub.x, sub.y);
+                    mu.x += R(0.75) * hypot(sb.x, sb.y);
                     s_mu[0] = mu;
                 } else if (nb == 1) {
                     s_mu[0] = wilkinson(T[(hi - 1) + (int64_t)(hi - 1) * ld], T[(hi - 1) + (int64_t)hi * ld],
                                         T[hi + (int64_t)(hi - 1) * ld], T[hi + (int64_t)hi * ld]);
                 } else {
-                    cplx<R> M[NB * NB];
-                    const int b0 = hi - nb + 1;
-                    for (int j = 0; j < nb; ++j)
-                        for (int i = 0; i < nb; ++i)
-                            M[i + j * NB] = (i <= j + 1) ? T[(b0 + i) + (int64_t)(b0 + j) * ld] : cplx<R>{0, 0};
-                    cplx<R> ev[NB];
-                    small_eigvals<R, NB>(M, nb, ev);
-                    for (int g = 0; g < nb; ++g) s_mu[g] = ev[g];
+                    s_small = 1;
                 }
                 s_nb = nb;
                 s_rots += (long long)(hi - lo) * nb;
@@ -226,212 +436,179 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
         __syncthreads();
         if (s_stop || s_status) break;
         const int nb = s_nb;
+        if (s_small) {  // shifts: eigenvalues of the trailing nb x nb block
+            if (warp == 0) {
+                const int b0 = hi - nb + 1;
+                for (int e = lane; e < nb * nb; e += 32) {
+                    const int i = e % nb, j = e / nb;
+                    s_m[i + j * (NB + 1)] = (i <= j + 1) ? T[(b0 + i) + (int64_t)(b0 + j) * ld] : cplx<R>{0, 0};
+                }
+                __syncwarp();
+                warp_small_eigvals<R, NB + 1>(s_m, nb, s_mu);
+            }
+            __syncthreads();
+        }
         const int nsteps = (hi - lo) + 3 * (nb - 1);
 
         for (int t0 = 0; t0 < nsteps; t0 += W) {
-            const int t1 = min(t0 + W, nsteps);
+            const int t1 = min(t0 + W, nsteps), ns = t1 - t0;
             const int kmin = max(lo, lo + t0 - 3 * (nb - 1));
             const int kmax = min(hi - 1, lo + t1 - 1);
             const int r0 = max(lo, kmin - 1);
             const int r1 = min(hi, kmax + 2);
-            const int bw = r1 - r0 + 1;
-            for (int e = tid; e < bw * bw; e += nt) {
-                int a = e % bw, b = e / bw;
-                cp_async_elem<R>(&blk[a + b * BWMAX], &T[(r0 + a) + (int64_t)(r0 + b) * ld]);
+            const int bw = r1 - r0 + 1, rr = kmax + 2 - kmin;
+            const int kbase = lo + t0 - 3 * (NB - 1);
+            if (bw > D::BW || rr > D::RR) {  // cannot happen; guards the shared-memory bounds
+                if (tid == 0) s_status = 7;
+                __syncthreads();
+                break;
             }
-            if (tid < NB * W) wk[tid / W][tid % W] = -1;
+            for (int e = tid; e < bw * bw; e += nt) {
+                const int a = e % bw, b = e / bw;
+                cp_async_elem<R>(&blk[a + b * BLD], &T[(r0 + a) + (int64_t)(r0 + b) * ld]);
+            }
+            for (int e = tid; e < W * NB; e += nt) rt[e] = RotLog<R>{R(1), R(0), R(0), R(0)};
             cp_async_wait_all();
             __syncthreads();
-            // the chase: warp g moves bulge g; only the NB chase warps take part
-            // (named barrier 1, NB * 32 threads).  Each warp's rotation depends
-            // only on entries its own previous step wrote, so all its lanes
-            // compute it redundantly; left rotations of one step touch disjoint
-            // rows and right rotations disjoint columns, so one barrier after
-            // each phase orders the warps.
-            if (warp < NB) {
+            // the chase: half-warp h of warp w moves bulge g = 2 w + h.  Each
+            // bulge's rotation depends only on entries its own previous step
+            // wrote, so all 16 lanes compute it redundantly; left rotations of
+            // one step touch disjoint rows and right rotations disjoint
+            // columns, so one barrier after each phase orders the bulges.
+            if (warp < NB / 2) {
+                constexpr int NI = (D::BW + 15) / 16;
+                const int hl = lane & 15;
+                const int g = 2 * warp + (lane >> 4);
                 for (int t = t0; t < t1; ++t) {
-                    const int g = warp, k = lo + t - 3 * g;
-                    const bool act = warp < nb && k >= lo && k < hi;
+                    const int k = lo + t - 3 * g;
+                    const bool act = g < nb && k >= lo && k < hi;  // uniform per half-warp
                     const int kk = k - r0;
+                    // left rotation of rows kk, kk+1 from column cstart on; the
+                    // half's lane 0 holds x and y in its first column
+                    const int cstart = (k == lo) ? kk : kk - 1;
+                    const int ni = act ? (bw - cstart + 15) >> 4 : 0;
+                    cplx<R> p[NI], q[NI];
+#pragma unroll
+                    for (int i = 0; i < NI; ++i) {
+                        const int b = cstart + hl + 16 * i;
+                        if (i < ni && b < bw) {
+                            p[i] = blk[kk + b * BLD];
+                            q[i] = blk[(kk + 1) + b * BLD];
+                        } else {
+                            p[i] = cplx<R>{1, 0};
+                            q[i] = cplx<R>{0, 0};
+                        }
+                    }
+                    cplx<R> x{__shfl_sync(0xffffffffu, p[0].x, 0, 16), __shfl_sync(0xffffffffu, p[0].y, 0, 16)};
+                    const cplx<R> y{__shfl_sync(0xffffffffu, q[0].x, 0, 16), __shfl_sync(0xffffffffu, q[0].y, 0, 16)};
+                    if (act && k == lo) x = x - s_mu[g];
                     R c = R(1);
                     cplx<R> s{0, 0}, r{0, 0};
-                    if (act) {
-                        cplx<R> x, y;
-                        if (k == lo) {
-                            x = blk[kk + kk * BWMAX] - s_mu[g];
-                            y = blk[(kk + 1) + kk * BWMAX];
-                        } else {
-                            x = blk[kk + (kk - 1) * BWMAX];
-                            y = blk[(kk + 1) + (kk - 1) * BWMAX];
-                        }
-                        givens(x, y, c, s, r);
-                        if (lane == 0) {
-                            wk[g][t - t0] = k;
-                            wc[g][t - t0] = c;
-                            ws[g][t - t0] = s;
-                        }
-                        __syncwarp();
-                        // left rotation: rows kk, kk+1 of the block
-                        const int cstart = (k == lo) ? kk : kk - 1;
-                        for (int b = cstart + lane; b < bw; b += 32) {
-                            cplx<R> p = blk[kk + b * BWMAX], q = blk[(kk + 1) + b * BWMAX];
-                            blk[kk + b * BWMAX] = c * p + s * q;
-                            blk[(kk + 1) + b * BWMAX] = c * q - conj(s) * p;
-                        }
-                        __syncwarp();
-                        if (lane == 0 && k > lo) {
-                            blk[kk + (kk - 1) * BWMAX] = r;
-                            blk[(kk + 1) + (kk - 1) * BWMAX] = cplx<R>{0, 0};
+                    if (act) givens_fast(x, y, c, s, r);
+#pragma unroll
+                    for (int i = 0; i < NI; ++i) {
+                        const int b = cstart + hl + 16 * i;
+                        if (i < ni && b < bw) {
+                            cplx<R> np = c * p[i] + s * q[i], nq = c * q[i] - conj(s) * p[i];
+                            if (i == 0 && hl == 0 && k > lo) {  // the annihilated bulge entry
+                                np = r;
+                                nq = cplx<R>{0, 0};
+                            }
+                            blk[kk + b * BLD] = np;
+                            blk[(kk + 1) + b * BLD] = nq;
                         }
                     }
-                    asm volatile("bar.sync 1, %0;" ::"r"(NB * 32) : "memory");
-                    if (act) {
-                        // right rotation: columns kk, kk+1, block rows up to kk+2
-                        const int rend = min(kk + 2, bw - 1);
-                        for (int a = lane; a <= rend; a += 32) {
-                            cplx<R> p = blk[a + kk * BWMAX], q = blk[a + (kk + 1) * BWMAX];
-                            blk[a + kk * BWMAX] = c * p + conj(s) * q;
-                            blk[a + (kk + 1) * BWMAX] = c * q - s * p;
+                    if (act && hl == 0) rt[(t - t0) * NB + rt_slot<NB>(g)] = RotLog<R>{c, s.x, s.y, R(1)};
+                    chase_bar<NB * 16>();
+                    // right rotation: columns kk, kk+1, block rows up to kk+2
+                    const int rend = min(kk + 2, bw - 1);
+                    const int nr = act ? (rend + 16) >> 4 : 0;
+#pragma unroll
+                    for (int i = 0; i < NI; ++i) {
+                        const int a = hl + 16 * i;
+                        if (i < nr && a <= rend) {
+                            p[i] = blk[a + kk * BLD];
+                            q[i] = blk[a + (kk + 1) * BLD];
                         }
                     }
-                    asm volatile("bar.sync 1, %0;" ::"r"(NB * 32) : "memory");
+#pragma unroll
+                    for (int i = 0; i < NI; ++i) {
+                        const int a = hl + 16 * i;
+                        if (i < nr && a <= rend) {
+                            blk[a + kk * BLD] = c * p[i] + conj(s) * q[i];
+                            blk[a + (kk + 1) * BLD] = c * q[i] - s * p[i];
+                        }
+                    }
+                    chase_bar<NB * 16>();
                 }
             }
             __syncthreads();
             for (int e = tid; e < bw * bw; e += nt) {
-                int a = e % bw, b = e / bw;
-                T[(r0 + a) + (int64_t)(r0 + b) * ld] = blk[a + b * BWMAX];
+                const int a = e % bw, b = e / bw;
+                T[(r0 + a) + (int64_t)(r0 + b) * ld] = blk[a + b * BLD];
             }
-            // log the window's rotations step by step: the (up to nb) rotations of
-            // one step act on disjoint index pairs and form one group; the first
-            // entry of a group carries the group size (pad), the others 0
-            if (tid == 0) {
-                int off = s_nlog;
-                for (int q = 0; q < t1 - t0; ++q) {
-                    s_goff[q] = off;
-                    for (int g = 0; g < nb; ++g) off += (wk[g][q] >= 0);
-                }
-                s_off[NB] = off;
-                for (int g = 0; g < NB; ++g) {
-                    int first = -1, cnt = 0;
-                    if (g < nb)
-                        for (int q = 0; q < t1 - t0; ++q)
-                            if (wk[g][q] >= 0) {
-                                if (first < 0) first = q;
-                                ++cnt;
-                            }
-                    s_first[g] = first;
-                    s_cnt[g] = cnt;
-                }
+            {
+                RotLog<R> *dst = d.log + s_nlog;
+                for (int e = tid; e < W * NB; e += nt) dst[e] = rt[e];
             }
-            __syncthreads();
-            for (int e = tid; e < NB * W; e += nt) {
-                const int q = e / NB, g = e % NB;
-                if (g < nb && q < t1 - t0 && wk[g][q] >= 0) {
-                    int pos = s_goff[q], gsz = 0;
-                    for (int u = 0; u < nb; ++u) {
-                        if (wk[u][q] >= 0) {
-                            if (u < g) ++pos;
-                            ++gsz;
-                        }
-                    }
-                    RotLog<R> L;
-                    L.k = wk[g][q]; L.lo = lo; L.hi = hi;
-                    L.pad = (pos == s_goff[q]) ? gsz : 0;
-                    L.c = wc[g][q]; L.pad2 = R(0); L.s = ws[g][q];
-                    d.log[pos] = L;
-                }
-            }
-            // (a') columns r1+1 .. hi, rows kmin .. kmax+1: left rotations
-            const int rr = kmax + 2 - kmin;
-            for (int c0 = r1 + 1; c0 <= hi; c0 += CH) {
-                const int cn = min(CH, hi - c0 + 1);
+            const int off = kbase - kmin;
+            // (a') columns r1+1 .. hi, rows kmin .. kmin+rr-1: left rotations
+            for (int c0 = r1 + 1; c0 <= hi; c0 += kQrCh) {
+                const int cn = min(kQrCh, hi - c0 + 1);
                 for (int e = tid; e < rr * cn; e += nt) {
-                    int a = e % rr, b = e / rr;
-                    cp_async_elem<R>(&tile[a + b * (RRMAX + 1)], &T[(kmin + a) + (int64_t)(c0 + b) * ld]);
+                    const int v = e % rr, j = e / rr;
+                    cp_async_elem<R>(&tile[v + j * RLD], &T[(kmin + v) + (int64_t)(c0 + j) * ld]);
                 }
                 cp_async_wait_all();
                 __syncthreads();
-                if (tid < cn) {
-                    // each bulge's rotations in this window are consecutive
-                    // positions k0, k0+1, ...: carry the running element in
-                    // registers and load the next one ahead of the update
-                    cplx<R> *col = tile + tid * (RRMAX + 1) - kmin;
-                    for (int g = 0; g < nb; ++g) {
-                        const int q0 = s_first[g], cnt = s_cnt[g];
-                        if (cnt <= 0) continue;
-                        const int k0 = wk[g][q0];
-                        cplx<R> carry = col[k0];
-                        cplx<R> nxt = col[k0 + 1];
-                        for (int i = 0; i < cnt; ++i) {
-                            const R c = wc[g][q0 + i];
-                            const cplx<R> s = ws[g][q0 + i];
-                            const cplx<R> after = (i + 1 < cnt) ? col[k0 + i + 2] : cplx<R>{0, 0};
-                            col[k0 + i] = c * carry + s * nxt;
-                            carry = c * nxt - conj(s) * carry;
-                            nxt = after;
-                        }
-                        col[k0 + cnt] = carry;
-                    }
-                }
+                if (!apply_window<R, NB, 1, true>(tile + seg * RLD, seg < cn, rt, ns, off, rr, sub, t0, hi - lo, nb))
+                    s_bad = 1;
                 __syncthreads();
                 for (int e = tid; e < rr * cn; e += nt) {
-                    int a = e % rr, b = e / rr;
-                    T[(kmin + a) + (int64_t)(c0 + b) * ld] = tile[a + b * (RRMAX + 1)];
+                    const int v = e % rr, j = e / rr;
+                    T[(kmin + v) + (int64_t)(c0 + j) * ld] = tile[v + j * RLD];
                 }
                 __syncthreads();
             }
-            // (b') rows lo .. r0-1, columns kmin .. kmax+1: right rotations
-            for (int i0 = lo; i0 < r0; i0 += CH) {
-                const int rn = min(CH, r0 - i0);
+            // (b') rows lo .. r0-1, columns kmin .. kmin+rr-1: right rotations
+            for (int i0 = lo; i0 < r0; i0 += kQrCh) {
+                const int rn = min(kQrCh, r0 - i0);
                 for (int e = tid; e < rn * rr; e += nt) {
-                    int a = e % rn, b = e / rn;
-                    cp_async_elem<R>(&tile[a + b * (CH + 1)], &T[(i0 + a) + (int64_t)(kmin + b) * ld]);
+                    const int a = e % rn, v = e / rn;
+                    cp_async_elem<R>(&tile[a + v * CLD], &T[(i0 + a) + (int64_t)(kmin + v) * ld]);
                 }
                 cp_async_wait_all();
                 __syncthreads();
-                if (tid < rn) {
-                    cplx<R> *row = tile + tid;
-                    for (int g = 0; g < nb; ++g) {
-                        const int q0 = s_first[g], cnt = s_cnt[g];
-                        if (cnt <= 0) continue;
-                        const int k0 = wk[g][q0] - kmin;
-                        cplx<R> carry = row[k0 * (CH + 1)];
-                        cplx<R> nxt = row[(k0 + 1) * (CH + 1)];
-                        for (int i = 0; i < cnt; ++i) {
-                            const R c = wc[g][q0 + i];
-                            const cplx<R> s = ws[g][q0 + i];
-                            const cplx<R> after = (i + 1 < cnt) ? row[(k0 + i + 2) * (CH + 1)] : cplx<R>{0, 0};
-                            row[(k0 + i) * (CH + 1)] = c * carry + conj(s) * nxt;
-                            carry = c * nxt - s * carry;
-                            nxt = after;
-                        }
-                        row[(k0 + cnt) * (CH + 1)] = carry;
-                    }
-                }
+                if (!apply_window<R, NB, CLD, false>(tile + seg, seg < rn, rt, ns, off, rr, sub, t0, hi - lo, nb))
+                    s_bad = 1;
                 __syncthreads();
                 for (int e = tid; e < rn * rr; e += nt) {
-                    int a = e % rn, b = e / rn;
-                    T[(i0 + a) + (int64_t)(kmin + b) * ld] = tile[a + b * (CH + 1)];
+                    const int a = e % rn, v = e / rn;
+                    T[(i0 + a) + (int64_t)(kmin + v) * ld] = tile[a + v * CLD];
                 }
                 __syncthreads();
             }
             if (tid == 0) {
                 WinRec wr;
                 wr.start = s_nlog;
-                wr.count = s_off[NB] - s_nlog;
+                wr.kbase = kbase;
+                wr.nsteps = ns;
                 wr.kmin = kmin;
                 wr.rr = rr;
                 wr.lo = lo;
                 wr.hi = hi;
+                wr.pad = 0;
                 wr.uoff = s_uoff;
                 d.win[s_nwin] = wr;
                 s_nwin += 1;
                 s_uoff += (long long)rr * rr;
-                s_nlog = s_off[NB];
+                s_nlog += W * NB;
+                if (s_bad) s_status = 7;
             }
             __syncthreads();
         }
+        __syncthreads();
+        if (s_status) break;
     }
     __syncthreads();
     if (tid == 0) {
@@ -458,42 +635,50 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
 // rotations becomes x U, and a column segment y receiving its left rotations
 // becomes U^H y.  One CTA per window, thread r owns row r of U.
 template <class R>
-__global__ void qr_build_u_kernel(const SchurDesc<R> *__restrict__ descs)
+__global__ void __launch_bounds__(128) qr_build_u_kernel(const SchurDesc<R> *__restrict__ descs)
 {
-    constexpr int RRMAX = QrCfg<R>::W + 3 * QrCfg<R>::NB;
-    __shared__ cplx<R> u[RRMAX * (RRMAX + 1)];
-    __shared__ RotLog<R> lg[64];
+    using D = QrDims<R>;
+    constexpr int W = D::W, NB = D::NB, ULD = D::RR + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    RotLog<R> *lg = reinterpret_cast<RotLog<R> *>(smraw);
+    cplx<R> *u = reinterpret_cast<cplx<R> *>(lg + W * NB);
     const SchurDesc<R> d = descs[blockIdx.y];
     const int nwin = d.state[7];
     if ((int)blockIdx.x >= nwin) return;
     const WinRec w = d.win[blockIdx.x];
     const int rr = w.rr, r = threadIdx.x;
-    const int ld = RRMAX + 1;
+    if (rr > D::RR || rr < 2) {
+        if (r == 0) atomicExch(d.status, 7);
+        return;
+    }
+    for (int e = threadIdx.x; e < W * NB; e += blockDim.x) lg[e] = d.log[w.start + e];
     if (r < rr)
-        for (int c = 0; c < rr; ++c) u[r * ld + c] = cplx<R>{(R)(r == c), R(0)};
-    for (int e0 = 0; e0 < w.count; e0 += 64) {
-        const int en = min(64, w.count - e0);
-        __syncthreads();
-        if (threadIdx.x < en) lg[threadIdx.x] = d.log[w.start + e0 + threadIdx.x];
-        __syncthreads();
-        if (r < rr) {
-            cplx<R> *row = u + r * ld;
-            for (int e = 0; e < en; ++e) {
-                const int a = lg[e].k - w.kmin;
-                if ((unsigned)a > (unsigned)(rr - 2)) { atomicExch(d.status, 7); continue; }
-                const R c = lg[e].c;
-                const cplx<R> s = lg[e].s;
-                cplx<R> p = row[a], q = row[a + 1];
-                row[a] = c * p + conj(s) * q;
-                row[a + 1] = c * q - s * p;
+        for (int c = 0; c < rr; ++c) u[r * ULD + c] = cplx<R>{(R)(r == c), R(0)};
+    __syncthreads();
+    if (r < rr) {
+        cplx<R> *row = u + r * ULD;
+        const int off = w.kbase - w.kmin;
+        bool bad = false;
+        for (int q = 0; q < w.nsteps; ++q) {
+#pragma unroll
+            for (int g = 0; g < NB; ++g) {
+                const RotLog<R> e = lg[q * NB + rt_slot<NB>(g)];
+                if (e.act == R(0)) continue;
+                const int a = off + q + 3 * (NB - 1 - g);
+                if ((unsigned)a > (unsigned)(rr - 2)) { bad = true; continue; }
+                const cplx<R> sv{e.sx, e.sy};
+                const cplx<R> p = row[a], qv = row[a + 1];
+                row[a] = e.c * p + conj(sv) * qv;
+                row[a + 1] = e.c * qv - sv * p;
             }
         }
+        if (bad) atomicExch(d.status, 7);
     }
     __syncthreads();
     cplx<R> *U = d.ubuf + w.uoff;
     for (int e = threadIdx.x; e < rr * rr; e += blockDim.x) {
         const int q = e % rr, c = e / rr;  // U(q, c), column-major
-        U[e] = u[q * ld + c];
+        U[e] = u[q * ULD + c];
     }
 }
 
@@ -504,7 +689,7 @@ template <class R>
 __global__ void __launch_bounds__(256)
 qr_apply_rows_kernel(const SchurDesc<R> *__restrict__ descs, int rpc, int ctas_t)
 {
-    constexpr int RRMAX = QrCfg<R>::W + 3 * QrCfg<R>::NB;
+    constexpr int RRMAX = QrDims<R>::RR;
     extern __shared__ unsigned char smraw[];
     const SchurDesc<R> d = descs[blockIdx.y];
     const int n = d.n, ld = d.ld;
@@ -584,7 +769,7 @@ template <class R>
 __global__ void __launch_bounds__(256)
 qr_apply_cols_kernel(const SchurDesc<R> *__restrict__ descs, int cpc)
 {
-    constexpr int RRMAX = QrCfg<R>::W + 3 * QrCfg<R>::NB;
+    constexpr int RRMAX = QrDims<R>::RR;
     extern __shared__ unsigned char smraw[];
     const SchurDesc<R> d = descs[blockIdx.y];
     const int n = d.n, ld = d.ld;
@@ -676,10 +861,19 @@ __global__ void qr_state_init_kernel(const SchurDesc<R> *__restrict__ descs, int
     }
 }
 
+// A matrix whose iteration did not finish within the round limit gets the
+// iteration-cap status.
+template <class R>
+__global__ void qr_mark_unfinished_kernel(const SchurDesc<R> *__restrict__ descs, int batch)
+{
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < batch; b += gridDim.x * blockDim.x)
+        if (!descs[b].state[2]) atomicExch(descs[b].status, 3);
+}
+
 template <class R>
 int qr_rows_per_cta(int nmax)
 {
-    constexpr int RRMAX = QrCfg<R>::W + 3 * QrCfg<R>::NB;
+    constexpr int RRMAX = QrDims<R>::RR;
     size_t per = (size_t)(std::max(nmax, 1) + 1) * sizeof(cplx<R>);
     size_t avail = 200 * 1024 - 2 * (size_t)RRMAX * RRMAX * sizeof(cplx<R>);
     size_t r = avail / per;
@@ -690,21 +884,21 @@ template <class R>
 cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, int *h_state,
                              const int *d_state_all, cudaStream_t s)
 {
-    constexpr int RRMAX = QrCfg<R>::W + 3 * QrCfg<R>::NB, CH = QrCfg<R>::CH;
-    const size_t tile_bytes = std::max((size_t)(RRMAX + 1) * CH, (size_t)(CH + 1) * RRMAX) * sizeof(cplx<R>);
+    constexpr int RRMAX = QrDims<R>::RR;
     const int rpc = qr_rows_per_cta<R>(nmax);
     const size_t ubytes = 2 * (size_t)RRMAX * RRMAX * sizeof(cplx<R>);
     const size_t rows_bytes = (size_t)rpc * nmax * sizeof(cplx<R>) + ubytes;
     const size_t cols_bytes = (size_t)rpc * (nmax + 1) * sizeof(cplx<R>) + ubytes;
     cudaError_t err;
     if ((err = allow_max_smem((const void *)qr_chase_kernel<R>))) return err;
+    if ((err = allow_max_smem((const void *)qr_build_u_kernel<R>))) return err;
     if ((err = allow_max_smem((const void *)qr_apply_rows_kernel<R>))) return err;
     if ((err = allow_max_smem((const void *)qr_apply_cols_kernel<R>))) return err;
     qr_state_init_kernel<R><<<1, 256, 0, s>>>(d_desc, batch); count_launch();
     const int ctas = (int)cdiv_i(nmax, rpc);
     bool all = false;
     for (int round = 0; round < 256 && !all; ++round) {
-        qr_chase_kernel<R><<<batch, kQrThreads, tile_bytes, s>>>(d_desc); count_launch();
+        qr_chase_kernel<R><<<batch, kQrThreads, QrDims<R>::chase_smem, s>>>(d_desc); count_launch();
         if ((err = cudaMemcpyAsync(h_state, d_state_all, sizeof(int) * 8 * batch, cudaMemcpyDeviceToHost, s))) return err;
         if ((err = cudaStreamSynchronize(s))) return err;
         int maxwin = 0;
@@ -714,11 +908,12 @@ cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, in
             maxwin = std::max(maxwin, h_state[8 * b + 7]);
         }
         if (maxwin > 0) {
-            qr_build_u_kernel<R><<<dim3(maxwin, batch), 64, 0, s>>>(d_desc); count_launch();
+            qr_build_u_kernel<R><<<dim3(maxwin, batch), 128, QrDims<R>::build_smem, s>>>(d_desc); count_launch();
             qr_apply_rows_kernel<R><<<dim3(2 * ctas, batch), 256, rows_bytes, s>>>(d_desc, rpc, ctas); count_launch();
             qr_apply_cols_kernel<R><<<dim3(ctas, batch), 256, cols_bytes, s>>>(d_desc, rpc); count_launch();
         }
     }
+    if (!all) { qr_mark_unfinished_kernel<R><<<1, 256, 0, s>>>(d_desc, batch); count_launch(); }
     qr_finish_kernel<R><<<dim3(64, batch), 256, 0, s>>>(d_desc); count_launch();
     return cudaGetLastError();
 }
