@@ -7,6 +7,7 @@
 //     RG_SYM_TO_F64  X_ij = X_ji = double(R(result_ij)) * scale   (X_0)
 //     RG_SYM_ADD_F64 X_ij = X_ji = X_ij + double(result_ij) * scale (update)
 //     RG_ADD_F64     X_ij += double(result_ij) * scale (no mirroring)
+//     RG_SUB         C = C - result
 //   The two symmetric epilogues evaluate only tiles on or above the block
 //   diagonal and mirror each value, so the FP64 iterate stays exactly
 //   symmetric and half of the product is skipped.
@@ -104,6 +105,8 @@ rgemm_kernel(int m, int n, int k, const R *__restrict__ A, int lda, const R *__r
                 }
             } else if (EPI == RG_ADD_F64) {
                 X[gi + gj * ldx] += (double)v * scale;
+            } else if (EPI == RG_SUB) {
+                C[gi + (int64_t)gj * ldc] -= v;
             } else {
                 if (gi <= gj) {
                     double x = X[gi + gj * ldx] + (double)v * scale;
@@ -125,6 +128,7 @@ static cudaError_t rg_epi(int epi, dim3 g, cudaStream_t st, int m, int n, int k,
     case RG_DIAG_SOLVE: rgemm_kernel<R, OPA, OPB, RG_DIAG_SOLVE><<<g, R_THREADS, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, s, X, ldx, scale); count_launch(); break;
     case RG_SYM_TO_F64: rgemm_kernel<R, OPA, OPB, RG_SYM_TO_F64><<<g, R_THREADS, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, s, X, ldx, scale); count_launch(); break;
     case RG_SYM_ADD_F64: rgemm_kernel<R, OPA, OPB, RG_SYM_ADD_F64><<<g, R_THREADS, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, s, X, ldx, scale); count_launch(); break;
+    case RG_SUB: rgemm_kernel<R, OPA, OPB, RG_SUB><<<g, R_THREADS, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, s, X, ldx, scale); count_launch(); break;
     default: rgemm_kernel<R, OPA, OPB, RG_ADD_F64><<<g, R_THREADS, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, s, X, ldx, scale); count_launch();
     }
     return cudaGetLastError();

@@ -2,18 +2,21 @@
 //
 // Spectral decomposition A_s = V diag(lam) V^T (Algorithm 3, step 1):
 //   1. Householder tridiagonalisation in the storage precision R (FP32 for
-//      the mixed method): three launches per column -- reflector + product
-//      p = beta A v (one warp per column of the trailing block), the
+//      the mixed method): two launches per column -- reflector + product
+//      p = beta A v (one warp per column of the trailing block), and the
 //      symmetric rank-2 update A -= v w^T + w v^T with w = p - (beta/2)(v.p)
-//      v, and Q <- Q (I - beta v v^T);
-//   2. eigenvalues of the tridiagonal matrix by bisection on Sturm counts,
-//      one thread per eigenvalue, in FP64;
+//      v.  The reflectors are kept (one column each) for step 4;
+//   2. eigenvalues of the tridiagonal matrix: FP32 multisection (one warp
+//      per eigenvalue, 32 Sturm counts per round) to a bracket of FP32
+//      width, checked and finished by FP64 bisection (one thread per
+//      eigenvalue);
 //   3. eigenvectors of the tridiagonal matrix from twisted factorisations
 //      T - lam I = L D+ L^T = U D- U^T (one thread per eigenvalue, FP64):
 //      with r = argmin |D+_r + D-_r - (d_r - lam)|, z_r = 1,
 //      z_i = -(e_i / D+_i) z_{i+1} above r, z_{i+1} = -(e_i / D-_{i+1}) z_i
 //      below r, normalised;
-//   4. V = Q Z in R.
+//   4. V = Q Z: the reflectors applied to Z in blocks of 64 in compact WY
+//      form (three products per block).
 // Steps 2-3 are O(n^2) work; the O(n^3) steps 1 and 4 run in R.
 //
 // Refinement (Algorithm 3, steps 4-12): FP64 symmetric residual, then
@@ -72,7 +75,8 @@ __device__ void real_reflector(const R *__restrict__ col, int m, R *vsh, R *scal
 template <class R>
 __global__ void __launch_bounds__(kTriThreads2)
 tri_symv_kernel(const R *__restrict__ A, int n, int ld, int k, R *__restrict__ wsv,
-                R *__restrict__ wsp, R *__restrict__ wss)
+                R *__restrict__ wsp, R *__restrict__ wss, R *__restrict__ Y, int ldy,
+                R *__restrict__ betas)
 {
     extern __shared__ unsigned char smraw[];
     R *vsh = reinterpret_cast<R *>(smraw);
@@ -81,8 +85,13 @@ tri_symv_kernel(const R *__restrict__ A, int n, int ld, int k, R *__restrict__ w
     real_reflector<R>(A + (k + 1) + (int64_t)k * ld, m, vsh, scal);
     const R beta = scal[0];
     if (blockIdx.x == 0) {
-        for (int i = threadIdx.x; i < m; i += blockDim.x) wsv[i] = vsh[i];
+        R *yk = Y + (k + 1) + (int64_t)k * ldy;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            wsv[i] = vsh[i];
+            yk[i] = vsh[i];
+        }
         if (threadIdx.x < 3) wss[threadIdx.x] = scal[threadIdx.x];
+        if (threadIdx.x == 0) betas[k] = beta;
     }
     if (beta == R(0)) return;
     const int lane = threadIdx.x & 31;
@@ -150,62 +159,8 @@ tri_update_kernel(R *__restrict__ A, int n, int ld, int k, const R *__restrict__
     }
 }
 
-// Q(:, k+1:n) <- Q(:, k+1:n) - beta (Q v) v^T ; blockDim (32, 8)
 template <class R>
-__global__ void __launch_bounds__(kTriThreads2)
-tri_q_kernel(R *__restrict__ Q, int n, int ldq, int k, const R *__restrict__ wsv,
-             const R *__restrict__ wss)
-{
-    extern __shared__ unsigned char smraw[];
-    R *vsh = reinterpret_cast<R *>(smraw);
-    __shared__ R part[8][33];
-    const int m = n - k - 1;
-    const R beta = wss[0];
-    if (beta == R(0)) return;
-    const int tid = threadIdx.y * 32 + threadIdx.x;
-    for (int i = tid; i < m; i += 256) vsh[i] = wsv[i];
-    __syncthreads();
-    const int i = blockIdx.x * 32 + threadIdx.x;
-    const bool valid = i < n;
-    R acc = 0;
-    if (valid) {
-        R acc2 = 0;
-        int l = threadIdx.y;
-#pragma unroll 4
-        for (; l + 8 < m; l += 16) {
-            acc = fma(Q[i + (int64_t)(k + 1 + l) * ldq], vsh[l], acc);
-            acc2 = fma(Q[i + (int64_t)(k + 1 + l + 8) * ldq], vsh[l + 8], acc2);
-        }
-        if (l < m) acc = fma(Q[i + (int64_t)(k + 1 + l) * ldq], vsh[l], acc);
-        acc += acc2;
-    }
-    part[threadIdx.y][threadIdx.x] = acc;
-    __syncthreads();
-    R u = 0;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) u += part[q][threadIdx.x];
-    u *= beta;
-    if (valid) {
-#pragma unroll 8
-        for (int l = threadIdx.y; l < m; l += 8) {
-            R &e = Q[i + (int64_t)(k + 1 + l) * ldq];
-            e = fma(-u, vsh[l], e);
-        }
-    }
-}
-
-template <class R>
-__global__ void eye_real_kernel(R *Q, int n, int ldq)
-{
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)n * n;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        int i = (int)(t % n), j = (int)(t / n);
-        Q[i + (int64_t)j * ldq] = (R)(i == j);
-    }
-}
-
-template <class R>
-cudaError_t launch_tridiag(R *A, int n, int ld, R *Q, int ldq, R *ws, cudaStream_t s)
+cudaError_t launch_tridiag(R *A, int n, int ld, R *Y, int ldy, R *betas, R *ws, cudaStream_t s)
 {
     R *wsv = ws, *wsp = ws + n, *wss = ws + 2 * n;
     size_t sm1 = (size_t)std::max(n, 1) * sizeof(R);
@@ -214,21 +169,67 @@ cudaError_t launch_tridiag(R *A, int n, int ld, R *Q, int ldq, R *ws, cudaStream
     if (sm2 > 48 * 1024) {
         if ((err = allow_max_smem((const void *)tri_symv_kernel<R>))) return err;
         if ((err = allow_max_smem((const void *)tri_update_kernel<R>))) return err;
-        if ((err = allow_max_smem((const void *)tri_q_kernel<R>))) return err;
     }
-    eye_real_kernel<R><<<(int)std::min<int64_t>(cdiv_i((int64_t)n * n, 256), 152 * 8), 256, 0, s>>>(Q, n, ldq); count_launch();
     for (int k = 0; k + 2 < n; ++k) {
         int m = n - k - 1;
         int ctas = (int)std::min<int64_t>(cdiv_i(m, kTriThreads2 / 32), 304);
-        tri_symv_kernel<R><<<ctas, kTriThreads2, sm1, s>>>(A, n, ld, k, wsv, wsp, wss); count_launch();
+        tri_symv_kernel<R><<<ctas, kTriThreads2, sm1, s>>>(A, n, ld, k, wsv, wsp, wss, Y, ldy, betas); count_launch();
         tri_update_kernel<R><<<ctas, kTriThreads2, sm2, s>>>(A, n, ld, k, wsv, wsp, wss); count_launch();
-        tri_q_kernel<R><<<(int)cdiv_i(n, 32), dim3(32, 8), sm1, s>>>(Q, n, ldq, k, wsv, wss); count_launch();
     }
     return cudaGetLastError();
 }
 
-template cudaError_t launch_tridiag<float>(float *, int, int, float *, int, float *, cudaStream_t);
-template cudaError_t launch_tridiag<double>(double *, int, int, double *, int, double *, cudaStream_t);
+template cudaError_t launch_tridiag<float>(float *, int, int, float *, int, float *, float *, cudaStream_t);
+template cudaError_t launch_tridiag<double>(double *, int, int, double *, int, double *, double *, cudaStream_t);
+
+// T of the compact WY form of one block of nb reflectors: Q_b = H_0 ... H_{nb-1}
+// = I - Y T Y^T with T upper triangular, T(i,i) = beta_i and
+// T(0:i, i) = -beta_i T(0:i, 0:i) G(0:i, i), G = Y^T Y (one CTA; column by
+// column since column i needs the columns before it).
+template <class R>
+__global__ void larft_kernel(const R *__restrict__ G, int ldg, const R *__restrict__ beta, int nb,
+                             R *__restrict__ Tm, int ldt)
+{
+    __shared__ R g[kBackNb];
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) Tm[(e % nb) + (int64_t)(e / nb) * ldt] = R(0);
+    __syncthreads();
+    for (int i = 0; i < nb; ++i) {
+        const R bi = beta[i];
+        for (int c = threadIdx.x; c < i; c += blockDim.x) g[c] = G[c + (int64_t)i * ldg];
+        __syncthreads();
+        for (int r = threadIdx.x; r < i; r += blockDim.x) {
+            R acc = 0;
+            for (int c = r; c < i; ++c) acc = fma(Tm[r + (int64_t)c * ldt], g[c], acc);
+            Tm[r + (int64_t)i * ldt] = -bi * acc;
+        }
+        if (threadIdx.x == 0) Tm[i + (int64_t)i * ldt] = bi;
+        __syncthreads();
+    }
+}
+
+template <class R>
+cudaError_t launch_back_transform(const R *Y, int ldy, const R *betas, R *Z, int n, int ldz, R *scratch,
+                                  cudaStream_t s)
+{
+    const int nref = std::max(0, n - 2);
+    R *G = scratch, *Tm = G + kBackNb * kBackNb, *W = Tm + kBackNb * kBackNb, *W2 = W + (size_t)kBackNb * n;
+    const int nblk = (int)cdiv_i(nref, kBackNb);
+    for (int b = nblk - 1; b >= 0; --b) {
+        const int k0 = b * kBackNb, nb = std::min(kBackNb, nref - k0);
+        const int r0 = k0 + 1, mb = n - r0;
+        const R *Yb = Y + r0 + (int64_t)k0 * ldy;
+        cudaError_t err;
+        if ((err = launch_rgemm<R>(1, 0, nb, nb, mb, Yb, ldy, Yb, ldy, RG_STORE, G, nb, nullptr, nullptr, 0, 0.0, s))) return err;
+        larft_kernel<R><<<1, 64, 0, s>>>(G, nb, betas + k0, nb, Tm, nb); count_launch();
+        if ((err = launch_rgemm<R>(1, 0, nb, n, mb, Yb, ldy, Z + r0, ldz, RG_STORE, W, nb, nullptr, nullptr, 0, 0.0, s))) return err;
+        if ((err = launch_rgemm<R>(0, 0, nb, n, nb, Tm, nb, W, nb, RG_STORE, W2, nb, nullptr, nullptr, 0, 0.0, s))) return err;
+        if ((err = launch_rgemm<R>(0, 0, mb, n, nb, Yb, ldy, W2, nb, RG_SUB, Z + r0, ldz, nullptr, nullptr, 0, 0.0, s))) return err;
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_back_transform<float>(const float *, int, const float *, float *, int, int, float *, cudaStream_t);
+template cudaError_t launch_back_transform<double>(const double *, int, const double *, double *, int, int, double *, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // tridiagonal eigensolver in FP64
@@ -236,13 +237,15 @@ template cudaError_t launch_tridiag<double>(double *, int, int, double *, int, d
 // d, e, e^2, Gershgorin interval [gl, gu] and the pivot floor
 template <class R>
 __global__ void tri_extract_kernel(const R *__restrict__ A, int n, int ld, double *d, double *e,
-                                   double *e2, double *bounds)
+                                   double *e2, double *bounds, float *df, float *e2f)
 {
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         d[i] = (double)A[i + (int64_t)i * ld];
         double ei = (i + 1 < n) ? (double)A[(i + 1) + (int64_t)i * ld] : 0.0;
         e[i] = ei;
         e2[i] = ei * ei;
+        df[i] = (float)d[i];
+        e2f[i] = (float)e2[i];
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -257,6 +260,7 @@ __global__ void tri_extract_kernel(const R *__restrict__ A, int n, int ld, doubl
         bounds[0] = gl - 4.0 * 1.1102230246251565e-16 * w * n - 1e-300;
         bounds[1] = gu + 4.0 * 1.1102230246251565e-16 * w * n + 1e-300;
         bounds[2] = 2.2250738585072014e-308 * fmax(1.0, emax2);
+        bounds[3] = 1.1754943508222875e-38 * fmax(1.0, emax2);  // FP32 pivot floor
     }
 }
 
@@ -275,17 +279,78 @@ __device__ __forceinline__ int sturm_count(const double *__restrict__ d, const d
     return c;
 }
 
-__global__ void bisect_kernel(const double *__restrict__ d, const double *__restrict__ e2, int n,
-                              const double *__restrict__ bounds, double *__restrict__ lam)
+__device__ __forceinline__ int sturm_count_f32(const float *__restrict__ d, const float *__restrict__ e2, int n,
+                                               float x, float pivmin)
+{
+    float q = d[0] - x;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    int c = q < 0.0f;
+    for (int i = 1; i < n; ++i) {
+        q = (d[i] - x) - __fdividef(e2[i - 1], q);
+        if (fabsf(q) < pivmin) q = -pivmin;
+        c += q < 0.0f;
+    }
+    return c;
+}
+
+// FP32 multisection, one warp per eigenvalue j: each round the 32 lanes
+// count at 32 equally spaced points of the bracket and the bracket shrinks
+// to the subinterval where the count passes j (five rounds: 2^-25 of the
+// Gershgorin width).  The FP32 counts are those of a matrix within a few
+// FP32 units of T, so the bracket is widened before the FP64 stage checks it.
+__global__ void __launch_bounds__(256) multisect_f32_kernel(const float *__restrict__ d, const float *__restrict__ e2,
+                                                            int n, const double *__restrict__ bounds,
+                                                            double *__restrict__ blo, double *__restrict__ bhi)
+{
+    const int lane = threadIdx.x & 31;
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (j >= n) return;  // whole warps leave together
+    float lo = (float)bounds[0], hi = (float)bounds[1];
+    const float pivmin = (float)bounds[3];
+    for (int round = 0; round < 5; ++round) {
+        const float h = (hi - lo) * (1.0f / 32.0f);
+        const float x = (lane == 31) ? hi : lo + h * (float)(lane + 1);
+        const int c = sturm_count_f32(d, e2, n, x, pivmin);
+        const unsigned above = __ballot_sync(0xffffffffu, c > j);
+        const int first = above ? __ffs(above) - 1 : 31;
+        const float xf = __shfl_sync(0xffffffffu, x, first);
+        const float xp = __shfl_sync(0xffffffffu, x, first > 0 ? first - 1 : 0);
+        const float nlo = first > 0 ? xp : lo, nhi = xf;
+        if (!(nlo < nhi)) break;
+        lo = nlo;
+        hi = nhi;
+    }
+    if (lane == 0) {
+        blo[j] = lo;
+        bhi[j] = hi;
+    }
+}
+
+// FP64 bisection of eigenvalue j from the FP32 bracket, widened by a few
+// FP32 units of the spectrum's scale; if the FP64 counts at its ends do not
+// enclose j, from the Gershgorin interval instead.  Stops at a bracket of
+// width reltol |lam| + 2u ||T|| (plus the pivot floor).  One thread per
+// eigenvalue, 32-thread blocks so that all SMs take part.
+__global__ void __launch_bounds__(32) bisect_f64_kernel(const double *__restrict__ d, const double *__restrict__ e2,
+                                                        int n, const double *__restrict__ bounds,
+                                                        const double *__restrict__ blo,
+                                                        const double *__restrict__ bhi, double reltol,
+                                                        double *__restrict__ lam)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
-    double lo = bounds[0], hi = bounds[1];
-    const double pivmin = bounds[2];
+    const double gl = bounds[0], gu = bounds[1], pivmin = bounds[2];
+    const double widen = 16.0 * 5.9604644775390625e-08 * fmax(fabs(gl), fabs(gu)) + pivmin;
+    double lo = fmax(gl, blo[j] - widen), hi = fmin(gu, bhi[j] + widen);
+    if (!(lo < hi) || sturm_count(d, e2, n, lo, pivmin) > j || sturm_count(d, e2, n, hi, pivmin) <= j) {
+        lo = gl;
+        hi = gu;
+    }
+    const double atol = 2.0 * 1.1102230246251565e-16 * fmax(fabs(gl), fabs(gu)) + pivmin;
     for (int it = 0; it < 160; ++it) {
         double mid = 0.5 * (lo + hi);
         if (mid <= lo || mid >= hi) break;
-        if (hi - lo <= 2.0 * 1.1102230246251565e-16 * fmax(fabs(lo), fabs(hi)) + pivmin) break;
+        if (hi - lo <= reltol * fmax(fabs(lo), fabs(hi)) + atol) break;
         if (sturm_count(d, e2, n, mid, pivmin) > j) hi = mid;
         else lo = mid;
     }
@@ -356,11 +421,20 @@ cudaError_t launch_tridiag_eig(const R *A, int n, int ld, double *lam, double *Z
     double *d = scratch, *e = d + n, *e2 = e + n, *bounds = e2 + n;
     double *Dp = bounds + 8;
     double *Dm = Dp + (size_t)n * chunk;
-    tri_extract_kernel<R><<<1, 256, 0, s>>>(A, n, ld, d, e, e2, bounds); count_launch();
-    bisect_kernel<<<(int)cdiv_i(n, 64), 64, 0, s>>>(d, e2, n, bounds, lam); count_launch();
+    // the bisection stage's scratch lives in Dp (free until the vectors)
+    double *blo = Dp, *bhi = Dp + n;
+    float *df = (float *)(Dp + 2 * (size_t)n), *e2f = df + n;
+    tri_extract_kernel<R><<<1, 256, 0, s>>>(A, n, ld, d, e, e2, bounds, df, e2f); count_launch();
+    multisect_f32_kernel<<<(int)cdiv_i((int64_t)n * 32, 256), 256, 0, s>>>(df, e2f, n, bounds, blo, bhi); count_launch();
+    // The FP32 factorisation needs eigenvectors orthogonal to FP32 working
+    // precision only: |dlam| / gap well below 2^-24 takes eigenvalues to
+    // about 1e-10 relative for any gap above 1e-3 |lam|.  The FP64 method
+    // takes them to FP64 precision.
+    const double reltol = sizeof(R) == sizeof(float) ? 1e-10 : 2.0 * 1.1102230246251565e-16;
+    bisect_f64_kernel<<<(int)cdiv_i(n, 32), 32, 0, s>>>(d, e2, n, bounds, blo, bhi, reltol, lam); count_launch();
     for (int j0 = 0; j0 < n; j0 += chunk) {
         int cnt = std::min(chunk, n - j0);
-        twisted_kernel<<<(int)cdiv_i(cnt, 64), 64, 0, s>>>(d, e, e2, n, bounds, lam, j0, cnt, Dp, Dm, ZT); count_launch();
+        twisted_kernel<<<(int)cdiv_i(cnt, 32), 32, 0, s>>>(d, e, e2, n, bounds, lam, j0, cnt, Dp, Dm, ZT); count_launch();
     }
     return cudaGetLastError();
 }
@@ -394,11 +468,21 @@ __global__ void newton_schulz_combine_kernel(double *__restrict__ ZT, const doub
         ZT[t] = fma(-0.5, P[t], 1.5 * ZT[t]);
 }
 
+// Z(i, j) = R(ZT(j, i)): ZT holds Z^T (row j = eigenvector j), n x n, ld n
 template <class R>
-__global__ void cast_from_f64_kernel(const double *__restrict__ src, R *__restrict__ dst, int64_t count)
+__global__ void cast_transpose_kernel(const double *__restrict__ ZT, R *__restrict__ Z, int n)
 {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
-        dst[t] = (R)src[t];
+    __shared__ double t[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int r = bx + threadIdx.x, c = by + j;
+        if (r < n && c < n) t[j][threadIdx.x] = ZT[r + (int64_t)c * n];
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int r = by + threadIdx.x, c = bx + j;
+        if (r < n && c < n) Z[r + (int64_t)c * n] = (R)t[threadIdx.x][j];
+    }
 }
 
 // s_i = sqrt(lam_i) (lam rounded to R first); status 2 for lam_i <= 0
@@ -438,7 +522,7 @@ namespace {
 
 template <class R>
 struct SpdWork {
-    R *As, *V, *lamr, *s, *W, *Y, *Qh, *vecws;
+    R *As, *V, *lamr, *s, *W, *Y, *Qh, *vecws, *betas, *btws;
     double *lam, *ZT, *eigscratch;
     float *Rhat;
     double *xsave;   // FP64 copy of X for the adjoint
@@ -457,7 +541,9 @@ size_t spd_bytes(int64_t n, int chunk)
            Carve::round(nn * sizeof(float)) + Carve::round(nn * sizeof(double)) +
            Carve::round((2 * (size_t)n * chunk + 3 * n + 8) * sizeof(double)) +
            Carve::round(n * sizeof(double)) + 2 * Carve::round(n * sizeof(R)) +
-           Carve::round((2 * n + 8) * sizeof(R)) + 8192;
+           Carve::round((2 * n + 8) * sizeof(R)) + Carve::round((n + 8) * sizeof(R)) +
+           Carve::round(((size_t)2 * kBackNb * kBackNb + (size_t)2 * kBackNb * n) * sizeof(R)) +
+           Carve::round((size_t)(4 * n + 8) * sizeof(double)) + 8192;
 }
 
 template <class R>
@@ -485,9 +571,11 @@ int spd_carve(sqrtm_handle_t h, int64_t n, SpdWork<R> *w)
     w->Y = w->As;  // As is dead after the tridiagonalisation
     w->Rhat = c.take<float>(nn);
     w->ZT = c.take<double>(nn);
-    w->eigscratch = c.take<double>(2 * (size_t)n * chunk + 3 * n + 8);
+    w->eigscratch = c.take<double>(2 * (size_t)n * chunk + 3 * n + 8 + (4 * n + 8));
     w->lam = c.take<double>(n);
     w->vecws = c.take<R>(2 * n + 8);
+    w->betas = c.take<R>(n + 8);
+    w->btws = c.take<R>((size_t)2 * kBackNb * kBackNb + (size_t)2 * kBackNb * n);
     w->chunk = chunk;
     return 0;
 }
@@ -498,11 +586,13 @@ int spd_decompose(sqrtm_handle_t h, int64_t n, SpdWork<R> &w, sqrtm_info *info =
 {
     cudaStream_t s = h->stream;
     const int ni = (int)n;
+    // reflectors go to Qh (zero outside their support)
+    if (cudaMemsetAsync(w.Qh, 0, (size_t)n * n * sizeof(R), s)) return 7;
     {
-        struct Ctx { R *A, *Q, *ws; int n; } ctx{w.As, w.Qh, w.vecws, ni};
+        struct Ctx { R *A, *Y, *betas, *ws; int n; } ctx{w.As, w.Qh, w.betas, w.vecws, ni};
         auto enq = [](void *p, cudaStream_t st) -> cudaError_t {
             Ctx *c = (Ctx *)p;
-            return launch_tridiag<R>(c->A, c->n, c->n, c->Q, c->n, c->ws, st);
+            return launch_tridiag<R>(c->A, c->n, c->n, c->Y, c->n, c->betas, c->ws, st);
         };
         if (run_graph(h, 200 + (int)sizeof(R), w.As, n, 1, enq, &ctx)) return 7;
     }
@@ -524,10 +614,10 @@ int spd_decompose(sqrtm_handle_t h, int64_t n, SpdWork<R> &w, sqrtm_info *info =
         if (launch_rgemm<double>(0, 0, ni, ni, ni, M, ni, w.ZT, ni, RG_STORE, P, ni, nullptr, nullptr, 0, 0.0, s)) return 7;
         newton_schulz_combine_kernel<<<grid1((int64_t)n * n), 256, 0, s>>>(w.ZT, P, (int64_t)n * n); count_launch();
     }
-    // V = Qh Z = Qh (ZT)^T
-    R *ZTr = w.W;
-    cast_from_f64_kernel<R><<<grid1((int64_t)n * n), 256, 0, s>>>(w.ZT, ZTr, (int64_t)n * n); count_launch();
-    if (launch_rgemm<R>(0, 1, ni, ni, ni, w.Qh, ni, ZTr, ni, RG_STORE, w.V, ni, nullptr, nullptr, 0, 0.0, s)) return 7;
+    // V = Q Z: Z (rounded to R) into V, then the reflectors applied to it
+    cast_transpose_kernel<R><<<dim3((unsigned)cdiv_i(n, 32), (unsigned)cdiv_i(n, 32)), dim3(32, 8), 0, s>>>(w.ZT, w.V, ni);
+    count_launch();
+    if (launch_back_transform<R>(w.Qh, ni, w.betas, w.V, ni, ni, w.btws, s)) return 7;
     sqrt_eig_kernel<R><<<grid1(n), 256, 0, s>>>(w.lam, w.lamr, w.s, ni, w.iscal + 1); count_launch();
     if (info && ev_red) {
         float ms = 0;

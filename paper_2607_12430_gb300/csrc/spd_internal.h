@@ -7,7 +7,7 @@
 
 namespace sqm {
 
-enum { RG_STORE = 0, RG_DIAG_SOLVE = 1, RG_SYM_TO_F64 = 2, RG_SYM_ADD_F64 = 3, RG_ADD_F64 = 4 };
+enum { RG_STORE = 0, RG_DIAG_SOLVE = 1, RG_SYM_TO_F64 = 2, RG_SYM_ADD_F64 = 3, RG_ADD_F64 = 4, RG_SUB = 5 };
 
 // C = op(A) op(B), op 0 = N, 1 = T; see rgemm.cu for the epilogues.
 template <class R>
@@ -20,10 +20,22 @@ cudaError_t launch_residual_sym_f64(const double *A, int64_t lda, const double *
                                     int n, int e, float *Rhat, int ldr, double *partials,
                                     int *nparts, cudaStream_t s);
 
-// Householder tridiagonalisation A = Q Tri Q^T (A overwritten; Q out).
-// ws: >= 2 n + 8 elements of R.
+// Householder tridiagonalisation A = Q Tri Q^T (A overwritten: the
+// tridiagonal on its diagonal and first subdiagonal).  Reflector k,
+// H_k = I - beta_k y_k y_k^T, is stored as column k of Y (y_k(i) = 0 for
+// i <= k; Y must be zero on entry) and beta_k in betas[k]; Q = H_0 H_1 ...
+// H_{n-3}.  ws: >= 2 n + 8 elements of R.
 template <class R>
-cudaError_t launch_tridiag(R *A, int n, int ld, R *Q, int ldq, R *ws, cudaStream_t s);
+cudaError_t launch_tridiag(R *A, int n, int ld, R *Y, int ldy, R *betas, R *ws, cudaStream_t s);
+
+// Z <- Q Z for Q = H_0 ... H_{n-3} from launch_tridiag, applied in blocks of
+// kBackNb reflectors in compact WY form (Q_b = I - Y_b T_b Y_b^T, T_b upper
+// triangular), last block first: three products per block.
+// scratch: >= kBackNb * (kBackNb + 2 n) + kBackNb^2 elements of R.
+constexpr int kBackNb = 64;
+template <class R>
+cudaError_t launch_back_transform(const R *Y, int ldy, const R *betas, R *Z, int n, int ldz, R *scratch,
+                                  cudaStream_t s);
 
 // Eigen-decomposition of the symmetric tridiagonal matrix held on the
 // diagonal / first subdiagonal of A (FP64 arithmetic): lam (ascending) and
