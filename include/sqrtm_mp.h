@@ -57,12 +57,20 @@ typedef struct sqrtm_handle_s *sqrtm_handle_t;
  * when A is bitwise symmetric, the general path (Algorithm 2) otherwise. */
 enum { SQRTM_KIND_AUTO = 0, SQRTM_KIND_GENERAL = 1, SQRTM_KIND_SPD = 2 };
 
-/* Precision of the low-precision dense products (transforms of Algorithm 2/3
- * steps 3, 8 and 10 and the GEMM updates inside the Sylvester and triangular
- * square root solvers).  FP32 is IEEE single on the CUDA cores; TF32X3 is a
+/* Precision options (bit flags).
+ * Low-precision dense products (transforms of Algorithm 2/3 steps 3, 8 and
+ * 10 and the GEMM updates inside the Sylvester and triangular square root
+ * solvers): FP32 (0) is IEEE single on the CUDA cores; TF32X3 is a
  * three-term split-TF32 product on the tensor cores with FP32 accumulation
- * (error comparable to FP32). */
-enum { SQRTM_PREC_FP32 = 0, SQRTM_PREC_TF32X3 = 1 };
+ * (error comparable to FP32).
+ * FP64 residual of the symmetric positive definite path (Algorithm 3,
+ * step 5): by default, for 256 <= n <= 46340, X X is formed from exact
+ * products of 5- to 8-bit digit slices of X on the BF16 tensor cores and
+ * summed in FP64 (error-free splitting; the terms left out are below
+ * n 2^(rho_i + rho_j - 56), 2^rho_i bounding row i of X, i.e. within the
+ * FP64 product's own error bound); RESID_FP64 forces the FP64 product on
+ * the CUDA cores. */
+enum { SQRTM_PREC_FP32 = 0, SQRTM_PREC_TF32X3 = 1, SQRTM_PREC_RESID_FP64 = 2 };
 
 typedef struct {
     double tol;      /* stop when ||A - X^2||_F <= tol ||A||_F (Algorithm 2,
@@ -72,7 +80,7 @@ typedef struct {
     int blks;        /* block size of the Sylvester and triangular square
                         root solvers (Algorithm 1); default 32 (Sec. 5) */
     int kind;        /* SQRTM_KIND_* */
-    int precision;   /* SQRTM_PREC_* */
+    int precision;   /* SQRTM_PREC_* flags */
     int steps;       /* >= 0: apply exactly this many corrections with the
                         stopping test nullified (the accuracy-run protocol of
                         Sec. 5.1); -1 (default): use tol / maxit */

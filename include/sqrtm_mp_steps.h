@@ -99,6 +99,19 @@ SQRTM_API int sqrtm_step_gemm_tf32x3(sqrtm_handle_t h, int64_t M, int64_t N, int
                                      const float *dA, int64_t lda, const float *dB, int64_t ldb,
                                      float *dC, int64_t ldc);
 
+/* Residual of the symmetric positive definite path (Algorithm 3, step 5)
+ * for symmetric X: R = 4^-e A - X_s X_s with X_s = 2^-e X, FP64 accuracy;
+ * writes fl32(R) (mirrored) into dRhat (float n x n) and ||R||_F into
+ * *norm_host.  split = 0: X X by FP64 products on the CUDA cores;
+ * split = 1: X X from exact BF16 tensor-core products of digit slices of X
+ * summed in FP64 (error-free splitting; terms left out below
+ * n 2^(rho_i + rho_j - 56), 2^rho_i bounding row i of X); returns -10 when
+ * the splitting does not apply to n.  Status 6: a bounded wait inside a
+ * tensor-core kernel gave up. */
+SQRTM_API int sqrtm_step_residual_sym(sqrtm_handle_t h, const double *dA, int64_t lda, const double *dX,
+                                      int64_t ldx, int64_t n, int e, float *dRhat, double *norm_host,
+                                      int split);
+
 /* The residual above for callers that cannot allocate device memory.  The
  * paper has no counterpart: this is a library service.  It takes no handle
  * (a handle allocates its workspace on first use); its scratch -- the norm's

@@ -30,7 +30,7 @@ STATUS = {
 }
 
 KIND_AUTO, KIND_GENERAL, KIND_SPD = 0, 1, 2
-PREC_FP32, PREC_TF32X3 = 0, 1
+PREC_FP32, PREC_TF32X3, PREC_RESID_FP64 = 0, 1, 2
 MAX_HISTORY = 64
 
 
@@ -99,6 +99,7 @@ _SIGS = {
     "sqrtm_step_transform_in_spd": ([_P, _P, _P, _P, _P, _L], _I),
     "sqrtm_step_transform_out_update_spd": ([_P, _P, _P, _L, _I, _P, _L], _I),
     "sqrtm_step_gemm_tf32x3": ([_P, _L, _L, _L, _P, _L, _P, _L, _P, _L], _I),
+    "sqrtm_step_residual_sym": ([_P, _P, _L, _P, _L, _L, _I, _P, ctypes.POINTER(_D), _I], _I),
     "sqrtm_step_residual_noalloc": ([_P, _L, _P, _L, _L, _I, _P, ctypes.POINTER(_D), _P], _I),
 }
 
@@ -344,6 +345,16 @@ def step_residual(A_cm, X_cm, n, e=0):
     Rhat = torch.empty(n * n, dtype=torch.float32, device=A_cm.device)
     nrm = ctypes.c_double()
     _rc(lib().sqrtm_step_residual(handle(), _ptr(A_cm), n, _ptr(X_cm), n, n, e, _ptr(Rhat), ctypes.byref(nrm)), "residual")
+    return Rhat, nrm.value
+
+
+def step_residual_sym(A_cm, X_cm, n, e=0, split=False):
+    """Symmetric FP64 residual of the SPD path; split=True forms X X from
+    exact BF16 tensor-core digit products summed in FP64."""
+    Rhat = torch.empty(n * n, dtype=torch.float32, device=A_cm.device)
+    nrm = ctypes.c_double()
+    _rc(lib().sqrtm_step_residual_sym(handle(), _ptr(A_cm), n, _ptr(X_cm), n, n, e, _ptr(Rhat),
+                                      ctypes.byref(nrm), int(split)), "residual_sym")
     return Rhat, nrm.value
 
 

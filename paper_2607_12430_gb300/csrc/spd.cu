@@ -523,6 +523,8 @@ namespace {
 template <class R>
 struct SpdWork {
     R *As, *V, *lamr, *s, *W, *Y, *Qh, *vecws, *betas, *btws;
+    void *digits;    // BF16 digit slices of X for the split residual (FP32 method)
+    int *rho;        // their row exponents
     double *lam, *ZT, *eigscratch;
     float *Rhat;
     double *xsave;   // FP64 copy of X for the adjoint
@@ -543,7 +545,9 @@ size_t spd_bytes(int64_t n, int chunk)
            Carve::round(n * sizeof(double)) + 2 * Carve::round(n * sizeof(R)) +
            Carve::round((2 * n + 8) * sizeof(R)) + Carve::round((n + 8) * sizeof(R)) +
            Carve::round(((size_t)2 * kBackNb * kBackNb + (size_t)2 * kBackNb * n) * sizeof(R)) +
-           Carve::round((size_t)(4 * n + 8) * sizeof(double)) + 8192;
+           Carve::round((size_t)(4 * n + 8) * sizeof(double)) +
+           (sizeof(R) == sizeof(float) ? Carve::round(split_digit_elems((int)n) * 2) + Carve::round(n * sizeof(int)) : 0) +
+           8192;
 }
 
 template <class R>
@@ -576,6 +580,12 @@ int spd_carve(sqrtm_handle_t h, int64_t n, SpdWork<R> *w)
     w->vecws = c.take<R>(2 * n + 8);
     w->betas = c.take<R>(n + 8);
     w->btws = c.take<R>((size_t)2 * kBackNb * kBackNb + (size_t)2 * kBackNb * n);
+    w->digits = nullptr;
+    w->rho = nullptr;
+    if (sizeof(R) == sizeof(float)) {
+        w->digits = c.take<uint16_t>(split_digit_elems((int)n));
+        w->rho = c.take<int>(n);
+    }
     w->chunk = chunk;
     return 0;
 }
@@ -673,8 +683,12 @@ int spd_common(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, doubl
     if (!refine) return 0;
     const double norm_as = ldexp(norm_a, -2 * e);
     // split-TF32 tensor-core transforms when asked for and the TMA rules hold
-    const bool use_tc = sizeof(R) == sizeof(float) && o.precision == SQRTM_PREC_TF32X3 &&
+    const bool use_tc = sizeof(R) == sizeof(float) && (o.precision & SQRTM_PREC_TF32X3) &&
                         tc_gemm_supported(n, n, n, n, n, w.V, w.Rhat);
+    // FP64 residual from BF16 digit products (the FP64 accumulator reuses
+    // ZT, free once V is formed)
+    const bool use_split = sizeof(R) == sizeof(float) && !(o.precision & SQRTM_PREC_RESID_FP64) && n >= 256 &&
+                           split_residual_supported(ni);
     if (use_tc) {
         // V^T into the (now free) Householder-vector buffer
         transpose_kernel<R><<<dim3((unsigned)cdiv_i(n, 32), (unsigned)cdiv_i(n, 32)), dim3(32, 8), 0, s>>>(w.V, w.Qh, ni); count_launch();
@@ -686,7 +700,12 @@ int spd_common(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, doubl
     for (int k = 0;; ++k) {
         if (fixed && k >= max_corr) break;
         int np = 0;
-        if (launch_residual_sym_f64(dA, lda, dX, ldx, ni, e, w.Rhat, ni, w.dscal + 2, &np, s)) return 7;
+        if (use_split) {
+            if (launch_residual_sym_split(dA, lda, dX, ldx, ni, e, w.Rhat, ni, w.ZT, w.digits, w.rho, w.dscal + 2,
+                                          &np, w.iscal + 2, s)) return 7;
+        } else if (launch_residual_sym_f64(dA, lda, dX, ldx, ni, e, w.Rhat, ni, w.dscal + 2, &np, s)) {
+            return 7;
+        }
         if (launch_sum_partials(w.dscal + 2, np, w.dscal + 1, s)) return 7;
         if (!fixed) {
             double rn = 0.0;
@@ -725,7 +744,7 @@ int spd_common(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, doubl
         ++applied;
     }
     if (cudaEventRecord(h->ev[3], s)) return 7;
-    if (use_tc) {
+    if (use_tc || use_split) {
         int tcst = 0;
         if (fetch_scalar<R>(h, &tcst, w.iscal + 2, sizeof(int))) return 7;
         if (tcst) return tcst;

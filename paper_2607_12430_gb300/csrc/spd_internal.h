@@ -20,6 +20,16 @@ cudaError_t launch_residual_sym_f64(const double *A, int64_t lda, const double *
                                     int n, int e, float *Rhat, int ldr, double *partials,
                                     int *nparts, cudaStream_t s);
 
+// The same residual with X X from exact BF16 tensor-core products of digit
+// slices of X, summed in FP64 (tc_split.cu).  Racc: n x n doubles (ld n)
+// of scratch; digits: split_digit_elems(n) BF16 values; rho: n ints; err
+// receives 6 if a bounded wait gives up.
+bool split_residual_supported(int n);
+size_t split_digit_elems(int n);
+cudaError_t launch_residual_sym_split(const double *A, int64_t lda, const double *X, int64_t ldx, int n, int e,
+                                      float *Rhat, int ldr, double *Racc, void *digits, int *rho,
+                                      double *partials, int *nparts, int *err, cudaStream_t s);
+
 // Householder tridiagonalisation A = Q Tri Q^T (A overwritten: the
 // tridiagonal on its diagonal and first subdiagonal).  Reflector k,
 // H_k = I - beta_k y_k y_k^T, is stored as column k of Y (y_k(i) = 0 for

@@ -1,0 +1,304 @@
+// tc_split.cu -- the FP64 residual of the SPD refinement (Algorithm 3,
+// steps 4-5), R = (A - X X) 4^-e for symmetric X, with the product X X
+// formed on the BF16 tensor cores by error-free splitting (the scheme of
+// Ozaki, Ogita, Oishi and Rump, Numer. Algorithms 59 (2012)).
+//
+// Splitting.  Row i of X (= column i) is scaled by 2^-rho_i, the smallest
+// power of two above its largest magnitude, and cut into S balanced digits
+// of b bits, each rounded to nearest:
+//   X(i, k) = 2^rho_i sum_s m_s(i, k) 2^(-b (s + 1)) + r(i, k),
+//   m_s integers with |m_s| <= 2^b,  |r(i, k)| <= 2^(rho_i - b S - 1).
+// Rounding (not truncation toward zero) leaves remainders of either sign,
+// so the left-out parts of a length-n sum do not all pull one way.  Each
+// m_s is exact in BF16 (b <= 8).  A product of two digit matrices,
+//   P_st(i, j) = sum_k m_s(i, k) m_t(j, k),
+// is a sum of n integers of magnitude <= 2^(2b); with n 2^(2b) <= 2^24 every
+// partial sum is an integer of at most 24 bits, so the tensor core's FP32
+// accumulation is exact whatever its internal order or rounding.  Then
+//   (X X)(i, j) = 2^(rho_i + rho_j) sum_{s,t} 2^(-b (s + t + 2)) P_st(i, j)
+// up to the terms left out: digits beyond S and pairs with s + t > D.  With
+// b (D + 1) >= 56 + log2(D + 2) and S = D + 1 their sum is below
+// n 2^(rho_i + rho_j - 56), within the FP64 product's own error bound
+// n u sum_k |X(i,k)| |X(k,j)| for u = 2^-53 when one term dominates, and
+// far below it otherwise.  The P_st are scaled exactly (powers of two) and
+// summed in FP64.
+//
+// Products.  One launch per pair (s, t): 128 x 128 output tiles of the upper
+// block triangle only (R is symmetric), K in steps of 64 BF16 values; TMA
+// loads both digit tiles (128 rows x 128 bytes, 128-byte swizzle) into a
+// 4-stage ring, one thread issues 4 tcgen05.mma (M = N = 128, K = 16) per
+// stage into a 128-column TMEM accumulator, and the epilogue adds the scaled
+// tile into the FP64 accumulator (the first pair starts it from A, the last
+// one writes Rhat = fl32(R 4^-e), mirrored, and per-tile partial sums of
+// |R|^2).  Every mbarrier wait is bounded (status 6 on timeout).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "internal.h"
+#include "spd_internal.h"
+#include "tc_common.cuh"
+
+namespace sqm {
+
+static constexpr int SP_BM = 128, SP_BN = 128, SP_BK = 64, SP_STAGES = 4, SP_THREADS = 128;
+static constexpr int SP_TILE_BYTES = SP_BM * SP_BK * 2;  // 16 KB
+static constexpr int SP_STAGE_BYTES = 2 * SP_TILE_BYTES;
+static constexpr int SP_SMEM = SP_STAGES * SP_STAGE_BYTES + 1024 + 256;
+enum { SP_FIRST = 1, SP_LAST = 2 };
+
+// digit width b and pair bound D for an inner dimension n (see above)
+void split_plan(int n, int *b, int *D)
+{
+    int lg = 0;
+    while ((1 << lg) < std::max(n, 1)) ++lg;
+    int bb = std::max(1, std::min(8, (24 - lg) / 2));
+    int dd = 0;
+    while (bb * (dd + 1) < 56 + 4) ++dd;  // log2(D + 2) <= 4 for D <= 14
+    *b = bb;
+    *D = dd;
+}
+
+// one warp per row i of X (X symmetric: row i is column i, contiguous)
+__global__ void __launch_bounds__(256) split_rows_kernel(const double *__restrict__ X, int64_t ldx, int n, int lds,
+                                                         int b, int S, __nv_bfloat16 *__restrict__ Xs,
+                                                         int *__restrict__ rho)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;  // whole warps
+    const double *col = X + (int64_t)i * ldx;
+    double mx = 0.0;
+    for (int k = lane; k < n; k += 32) mx = fmax(mx, fabs(col[k]));
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, m));
+    int r = 0;
+    if (mx > 0.0) frexp(mx, &r);  // mx < 2^r
+    if (lane == 0) rho[i] = r;
+    const double scale_b = ldexp(1.0, b);
+    for (int k = lane; k < lds; k += 32) {
+        double x = (k < n) ? ldexp(col[k], -r) : 0.0;  // |x| < 1, exact
+        for (int s = 0; s < S; ++s) {
+            const double t = x * scale_b;  // exact
+            const double m = rint(t);      // |m| <= 2^b
+            x = t - m;  // exact (|t - m| <= 1/2, m within a factor 2 of t or 0)
+            Xs[((int64_t)s * n + i) * lds + k] = __float2bfloat16_rn((float)m);  // |m| <= 2^b: exact
+        }
+    }
+}
+
+struct SplitEpi {
+    const double *A;
+    int64_t lda;
+    double *Racc;
+    int64_t ldr;
+    const int *rho;
+    int shift;      // b (s + t + 2)
+    float *Rhat;
+    int64_t ldh;
+    double sc;      // 4^-e
+    double *partials;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(SP_THREADS, 1)
+split_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int n, int KT,
+                  int T, SplitEpi ep, int *err)
+{
+    extern __shared__ unsigned char smraw[];
+    __shared__ int s_fail;
+    __shared__ double s_red[SP_THREADS / 32];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // upper block triangle: tile q -> (I, J), I <= J, row-major over I
+    int q = blockIdx.x, I = 0;
+    while (q >= T - I) { q -= T - I; ++I; }
+    const int J = I + q;
+    const int m0 = I * SP_BM, n0 = J * SP_BN;
+
+    unsigned char *base = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(base + SP_STAGES * SP_STAGE_BYTES);
+    uint64_t *done = full + SP_STAGES;
+    uint32_t *tmem_slot = (uint32_t *)(done + SP_STAGES);
+    if (tid == 0) {
+        for (int s = 0; s < SP_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&done[s], 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(128)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    auto stage_ptr = [&](int s, int which) { return base + s * SP_STAGE_BYTES + which * SP_TILE_BYTES; };
+    int issued = 0, consumed = 0, committed = 0;
+    if (tid == 0) {
+        auto issue_load = [&](int t) {
+            const int s = t % SP_STAGES;
+            mbar_arrive_expect_tx(&full[s], 2 * SP_TILE_BYTES);
+            tma_load_2d(stage_ptr(s, 0), &mapA, &full[s], t * SP_BK, m0);
+            tma_load_2d(stage_ptr(s, 1), &mapB, &full[s], t * SP_BK, n0);
+        };
+        for (; issued < min(SP_STAGES + 0, KT); ++issued) issue_load(issued);
+        constexpr uint32_t IDESC = idesc_bf16_128x128();
+        for (int t = 0; t < KT; ++t) {
+            const int s = t % SP_STAGES;
+            if (!mbar_wait(&full[s], (t / SP_STAGES) & 1)) { s_fail = 1; break; }
+            consumed = t + 1;
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(stage_ptr(s, 0)), b0 = smem_u32(stage_ptr(s, 1));
+#pragma unroll
+            for (int kk = 0; kk < SP_BK / 16; ++kk) {
+                const uint32_t off = kk * 32;  // 16 BF16 values = 32 bytes along K
+                mma_bf16(tmem, smem_desc_sw128(a0 + off), smem_desc_sw128(b0 + off), IDESC, (t > 0 || kk > 0) ? 1u : 0u);
+            }
+            mma_commit(&done[s]);
+            committed = t + 1;
+            // refill the stage tile t-1 used once its products are done
+            if (t >= 1 && issued < KT) {
+                const int sp = (t - 1) % SP_STAGES;
+                if (!mbar_wait(&done[sp], ((t - 1) / SP_STAGES) & 1)) { s_fail = 1; break; }
+                issue_load(issued);
+                ++issued;
+            }
+        }
+    }
+    __syncthreads();
+    if (!s_fail && KT > 0) {
+        const int tl = KT - 1;
+        if (!mbar_wait(&done[tl % SP_STAGES], (tl / SP_STAGES) & 1)) s_fail = 1;
+    }
+    __syncthreads();
+    if (s_fail) {
+        if (tid == 0) {
+            atomicExch(err, 6);
+            for (int t = consumed; t < issued; ++t) mbar_wait(&full[t % SP_STAGES], (t / SP_STAGES) & 1);
+            if (committed > 0) mbar_wait(&done[(committed - 1) % SP_STAGES], ((committed - 1) / SP_STAGES) & 1);
+        }
+        __syncthreads();
+    } else {
+        tc_fence_after();
+        const int row = m0 + warp * 32 + lane;
+        const int rho_i = row < n ? ep.rho[row] : 0;
+        double ss = 0.0;
+        for (int c0 = 0; c0 < SP_BN; c0 += 32) {
+            uint32_t r[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+            if (row < n) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int col = n0 + c0 + j;
+                    if (col >= n || row > col) continue;
+                    const double p = ldexp((double)__uint_as_float(r[j]), rho_i + ep.rho[col] - ep.shift);
+                    double *acc = ep.Racc + row + (int64_t)col * ep.ldr;
+                    const double v = ((MODE & SP_FIRST) ? ep.A[row + (int64_t)col * ep.lda] : *acc) - p;
+                    if (MODE & SP_LAST) {
+                        const double rs = v * ep.sc;
+                        const float rf = (float)rs;
+                        ep.Rhat[row + (int64_t)col * ep.ldh] = rf;
+                        ep.Rhat[col + (int64_t)row * ep.ldh] = rf;
+                        ss = fma(rs, rs, ss);
+                        if (row != col) ss = fma(rs, rs, ss);  // mirrored entry
+                    } else {
+                        *acc = v;
+                    }
+                }
+            }
+        }
+        if (MODE & SP_LAST) {
+#pragma unroll
+            for (int m = 16; m > 0; m >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, m);
+            if (lane == 0) s_red[warp] = ss;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if ((MODE & SP_LAST) && tid == 0) {
+        double t = 0.0;
+        if (!s_fail)
+            for (int w = 0; w < SP_THREADS / 32; ++w) t += s_red[w];
+        ep.partials[blockIdx.x] = t;
+    }
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
+}
+
+static bool make_bf16_map(CUtensorMap *m, const void *ptr, int64_t kdim, int64_t rows, int64_t ld)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)kdim, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {SP_BK, SP_BM};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+int split_lds(int n) { return (int)cdiv_i(std::max(n, 1), SP_BK) * SP_BK; }
+
+size_t split_digit_elems(int n)
+{
+    int b, D;
+    split_plan(n, &b, &D);
+    return (size_t)(D + 1) * (size_t)n * (size_t)split_lds(n);
+}
+
+bool split_residual_supported(int n)
+{
+    int b, D;
+    split_plan(n, &b, &D);
+    return n >= 1 && (int64_t)n * (1 << (2 * b)) <= (1 << 24) && encode_fn() != nullptr;
+}
+
+cudaError_t launch_residual_sym_split(const double *A, int64_t lda, const double *X, int64_t ldx, int n, int e,
+                                      float *Rhat, int ldr, double *Racc, void *digits, int *rho,
+                                      double *partials, int *nparts, int *err, cudaStream_t s)
+{
+    if (n <= 0) { *nparts = 0; return cudaSuccess; }
+    int b, D;
+    split_plan(n, &b, &D);
+    const int S = D + 1, lds = split_lds(n);
+    __nv_bfloat16 *Xs = (__nv_bfloat16 *)digits;
+    split_rows_kernel<<<(unsigned)cdiv_i((int64_t)n * 32, 256), 256, 0, s>>>(X, ldx, n, lds, b, S, Xs, rho);
+    count_launch();
+    CUtensorMap maps[16];
+    if (S > 16) return cudaErrorInvalidValue;
+    for (int q = 0; q < S; ++q)
+        if (!make_bf16_map(&maps[q], Xs + (size_t)q * n * lds, lds, n, lds)) return cudaErrorInvalidValue;
+    const int T = (int)cdiv_i(n, SP_BM), ntiles = T * (T + 1) / 2, KT = lds / SP_BK;
+    cudaError_t er;
+    if ((er = allow_max_smem((const void *)split_gemm_kernel<0>))) return er;
+    if ((er = allow_max_smem((const void *)split_gemm_kernel<SP_FIRST>))) return er;
+    if ((er = allow_max_smem((const void *)split_gemm_kernel<SP_LAST>))) return er;
+    if ((er = allow_max_smem((const void *)split_gemm_kernel<SP_FIRST | SP_LAST>))) return er;
+    const int npairs = (D + 1) * (D + 2) / 2;
+    int idx = 0;
+    for (int d = 0; d <= D; ++d)
+        for (int si = 0; si <= d; ++si, ++idx) {
+            const int ti = d - si;
+            SplitEpi ep{A, lda, Racc, (int64_t)n, rho, b * (d + 2), Rhat, (int64_t)ldr, ldexp(1.0, -2 * e), partials};
+            const int mode = (idx == 0 ? SP_FIRST : 0) | (idx == npairs - 1 ? SP_LAST : 0);
+            switch (mode) {
+            case 0: split_gemm_kernel<0><<<ntiles, SP_THREADS, SP_SMEM, s>>>(maps[si], maps[ti], n, KT, T, ep, err); break;
+            case SP_FIRST: split_gemm_kernel<SP_FIRST><<<ntiles, SP_THREADS, SP_SMEM, s>>>(maps[si], maps[ti], n, KT, T, ep, err); break;
+            case SP_LAST: split_gemm_kernel<SP_LAST><<<ntiles, SP_THREADS, SP_SMEM, s>>>(maps[si], maps[ti], n, KT, T, ep, err); break;
+            default: split_gemm_kernel<SP_FIRST | SP_LAST><<<ntiles, SP_THREADS, SP_SMEM, s>>>(maps[si], maps[ti], n, KT, T, ep, err);
+            }
+            count_launch();
+        }
+    *nparts = ntiles;
+    return cudaGetLastError();
+}
+
+}  // namespace sqm
