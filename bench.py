@@ -108,6 +108,22 @@ def _peaks():
 # ---------------------------------------------------------------------------
 # reference arm: the CPU oracle as it stands
 # ---------------------------------------------------------------------------
+# DRAM bytes (read + write) of one qr_chase_kernel launch on this workload,
+# from the ncu capture summarised in profiles/qr_chase_general512.md; valid
+# only for the qr.cu it was taken with (SHA-256 below), else null.
+CHASE_TRAFFIC = {"sha256": "1d82153ce2cc09aa09e82f4760012fb9bf4e25ef44501d6a0b9464224ba595ee", "bytes": 2155264}
+
+
+def _chase_traffic():
+    import hashlib
+    p = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2607_12430_gb300", "csrc", "qr.cu")
+    try:
+        h = hashlib.sha256(open(p, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return CHASE_TRAFFIC["bytes"] if h == CHASE_TRAFFIC["sha256"] else None
+
+
 def run_reference(args):
     ws, rank = _dist()
     if rank != 0:
@@ -267,20 +283,28 @@ def run_ours(args):
         e2e_ms.append(s.elapsed_time(e))
     e2e = statistics.mean(e2e_ms)
 
-    # ---- roofline of the dominant kernel ----
+    # ---- roofline of the dominant kernel: the QR chase (one CTA per matrix) ----
     peaks = _peaks()
-    # Schur QR sweeps: each Givens rotation (wanted T and Z) updates two rows of
-    # T (n - k columns), two columns of T (k + 2 rows) and two columns of Z (n
-    # rows): about 2n complex 2-vectors, 16 real flops each (complex rotation
-    # of a pair: 2 x (real*complex + complex*complex + add)).
-    qr_flops = rots * 32.0 * n
+    # Algorithmic work, counted by the kernel: every rotation of a sweep on the
+    # active block [lo, hi] rotates about m = hi - lo + 1 pairs of complex
+    # entries of T (two rows right of it, two columns above it); a complex
+    # rotation of one pair, (c p + s q, c q - conj(s) p) with c real, costs 20
+    # real flops.  The duration is the sum of the chase kernel's launches,
+    # timed with CUDA events on the library's stream inside the timed steps.
+    work = statistics.mean([i["schur_work"] for i in infos])
+    chase_ms = statistics.mean([i["ms_qr_chase"] for i in infos])
+    chase_flops = 20.0 * work
     fp32_peak_tflops = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 FFMA lanes x 2 flops x max clock
-    achieved = qr_flops / (ph["ms_qr"] * 1e-3) / 1e12
-    roofline = {"kernel": "qr_sweeps_kernel<float>", "bound": "alu", "achieved": achieved,
+    one_sm_peak = fp32_peak_tflops / 152
+    achieved = chase_flops / (chase_ms * 1e-3) / 1e12
+    roofline = {"kernel": "qr_chase_kernel<float>", "bound": "alu", "achieved": achieved,
                 "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
-                "traffic": None,
-                "note": "peak = 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived, not measured); "
-                        "the sweep chase is latency-bound"}
+                "traffic": _chase_traffic(),
+                "kernel_ms_per_step": chase_ms, "flops_per_step": chase_flops,
+                "peak_one_sm": one_sm_peak, "frac_one_sm": achieved / one_sm_peak,
+                "note": "peak derived (152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz), not measured; the "
+                        "chase is one CTA per matrix (a serial bulge chain), so the one-SM fraction is "
+                        "the meaningful one; traffic = ncu dram bytes of one launch for this qr.cu"}
 
     line = {
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": ws, "steps": args.steps,
@@ -308,15 +332,22 @@ def run_ours(args):
 
 def run_profile_mode(args):
     """Only the timed sqrtm_mixed calls (no oracle, FP64 or e2e legs), for
-    profiler launch lists: warmup + steps calls with k* corrections each."""
+    profiler launch lists: warmup + steps calls with k* corrections each.
+    --workload spd runs the kappa = 1e6 SPD workload at size --n instead."""
     import torch
     import paper_2607_12430_gb300 as mp
     mp.lib()
-    A = torch.from_numpy(np.ascontiguousarray(synth.config_general512(n=N))).cuda()
+    if args.workload == "spd":
+        A_np, _, _ = synth.config_spd4096(n=args.n)
+        kind = mp.KIND_SPD
+    else:
+        A_np = synth.config_general512(n=N)
+        kind = mp.KIND_GENERAL
+    A = torch.from_numpy(np.ascontiguousarray(A_np)).cuda()
     X = torch.empty_like(A)
     t0 = time.perf_counter()
     for _ in range(args.warmup + args.steps):
-        _, info = mp.sqrtm_mixed(A, kind=mp.KIND_GENERAL, steps=args.kstar, out=X)
+        _, info = mp.sqrtm_mixed(A, kind=kind, steps=args.kstar, out=X)
     torch.cuda.synchronize()
     print(json.dumps({"profile_mode": True, "calls": args.warmup + args.steps, "kstar": args.kstar,
                       "wall_s": time.perf_counter() - t0, "status": info["status"]}), flush=True)
@@ -328,6 +359,9 @@ def main():
     p.add_argument("--profile-mode", action="store_true",
                    help="run only the timed calls (for ncu launch lists)")
     p.add_argument("--kstar", type=int, default=2, help="corrections per call in --profile-mode")
+    p.add_argument("--workload", choices=["general512", "spd"], default="general512",
+                   help="--profile-mode workload")
+    p.add_argument("--n", type=int, default=4096, help="--profile-mode SPD size")
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)

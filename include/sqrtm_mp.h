@@ -107,6 +107,11 @@ typedef struct {
     /* QR sweeps and Givens rotations of the Schur iteration (general path) */
     int schur_sweeps;
     int64_t schur_rotations;
+    /* general path: summed duration of the QR chase kernel's launches (ms)
+     * and its in-block work, sum over sweeps of rotations x active-block
+     * size (each such unit is one rotated pair of complex entries) */
+    double ms_qr_chase;
+    int64_t schur_work;
 } sqrtm_info;
 
 /* Create a handle bound to a CUDA stream (cudaStream_t passed as void*;

@@ -57,7 +57,8 @@ class Info(ctypes.Structure):
                 ("history_len", ctypes.c_int), ("history", ctypes.c_double * MAX_HISTORY),
                 ("ms_schur", ctypes.c_double), ("ms_trisqrt", ctypes.c_double),
                 ("ms_refine", ctypes.c_double), ("ms_reduction", ctypes.c_double),
-                ("schur_sweeps", ctypes.c_int), ("schur_rotations", ctypes.c_int64)]
+                ("schur_sweeps", ctypes.c_int), ("schur_rotations", ctypes.c_int64),
+                ("ms_qr_chase", ctypes.c_double), ("schur_work", ctypes.c_int64)]
 
     def as_dict(self):
         return {"status": self.status, "kind_used": self.kind_used, "iterations": self.iterations,
@@ -65,7 +66,8 @@ class Info(ctypes.Structure):
                 "history": [self.history[i] for i in range(self.history_len)],
                 "ms_schur": self.ms_schur, "ms_trisqrt": self.ms_trisqrt, "ms_refine": self.ms_refine,
                 "ms_reduction": self.ms_reduction, "schur_sweeps": self.schur_sweeps,
-                "schur_rotations": self.schur_rotations}
+                "schur_rotations": self.schur_rotations, "ms_qr_chase": self.ms_qr_chase,
+                "schur_work": self.schur_work}
 
 
 _lib = None

@@ -193,7 +193,7 @@ static Scalars carve_scalars(Carve &c, int64_t n)
     s.norm = c.take<double>(s.npart_cap + 8);
     s.rnorm = s.norm + 1;
     s.partials = s.norm + 2;
-    int *iv = c.take<int>(8);
+    int *iv = c.take<int>(16);
     s.e = iv;
     s.st_schur = iv + 1;
     s.st_solve = iv + 2;
@@ -268,10 +268,10 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     RotLog<R> *rlog = cw.take<RotLog<R>>(qr_log_capacity(n));
     WinRec *wrec = cw.take<WinRec>(qr_win_capacity(n));
     cplx<R> *ubuf = cw.take<cplx<R>>(qr_u_capacity(n));
-    int *qstate = cw.take<int>(8);
+    int *qstate = cw.take<int>(kQrStateInts);
     h->fact_n = -1;
 
-    SQM_CU(cudaMemsetAsync(sc.e, 0, 8 * sizeof(int), s));
+    SQM_CU(cudaMemsetAsync(sc.e, 0, 16 * sizeof(int), s));
     SQM_CU(cudaEventRecord(h->ev[0], s));
     SQM_CU(launch_norm_scale(dA, n, lda, sc.partials, (int)std::min<int64_t>(n, 1024), sc.norm, sc.e, s));
     SQM_CU(launch_cast_scaled<R>(dA, n, lda, sc.e, T, n, s));
@@ -302,7 +302,8 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     cudaEvent_t ev_red;
     SQM_CU(cudaEventCreate(&ev_red));
     SQM_CU(cudaEventRecord(ev_red, s));
-    SQM_CU(launch_qr_sweeps<R>(ddesc, 1, (int)n, (int *)h->staging.p + 512, qstate, s));
+    float ms_chase = 0.0f;
+    SQM_CU(launch_qr_sweeps<R>(ddesc, 1, (int)n, (int *)h->staging.p + 512, qstate, s, &ms_chase));
     SQM_CU(cudaEventRecord(h->ev[1], s));
     SQM_CU(launch_trisqrt<R>(T, (int)n, S, (int)n, (int)n, o.blks, sc.st_solve, s));
     // X_0 = Re(Q S Q^H), rounded to R, times 2^e
@@ -316,10 +317,12 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
         cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]); info->ms_schur = ms;
         cudaEventElapsedTime(&ms, h->ev[1], h->ev[2]); info->ms_trisqrt = ms;
         cudaEventElapsedTime(&ms, h->ev[0], ev_red); info->ms_reduction = ms;
-        int cnt[3];
+        int cnt[5];
         SQM_CU(cudaMemcpy(cnt, sc.st_schur + 3, sizeof(cnt), cudaMemcpyDeviceToHost));
         info->schur_sweeps = cnt[0];
         info->schur_rotations = (int64_t)cnt[1] + ((int64_t)cnt[2] << 31);
+        info->schur_work = (int64_t)cnt[3] + ((int64_t)cnt[4] << 31);
+        info->ms_qr_chase = ms_chase;
     }
     cudaEventDestroy(ev_red);
     if (st_schur == 7) note_error(h, "malformed QR rotation log entry", __LINE__, 7);

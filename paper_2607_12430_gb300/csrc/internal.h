@@ -56,7 +56,7 @@ struct SchurDesc {
     cplx<R> *v;      // scratch: Householder vector (>= n entries)
     R *beta;         // scratch: reflector scalars [beta, |x|, phase.x, phase.y]
     int *status;     // out: 0 / 3 (iteration cap)
-    int *counters;   // out: [0] sweeps, [1..2] rotations (int64 split lo/hi)
+    int *counters;   // out: [0] sweeps, [1..2] rotations, [3..4] in-block rotation work (int64s split lo/hi)
     int n;
     int ld;
 };
@@ -76,11 +76,14 @@ cudaError_t launch_cast_scaled_real(const double *A, int64_t n, int64_t lda, con
 template <class R>
 cudaError_t launch_hessenberg(const SchurDesc<R> *d_desc, int batch, int nmax,
                               int ctas_per_matrix, cudaStream_t s);
-// d_state_all: the 8-int state blocks of all matrices, contiguous (descs[b].
-// state == d_state_all + 8 b); h_state: pinned host buffer of 8 * batch ints.
+// d_state_all: the kQrStateInts-int state blocks of all matrices, contiguous
+// (descs[b].state == d_state_all + kQrStateInts b); h_state: pinned host
+// buffer of kQrStateInts * batch ints.  ms_chase (may be null) receives the
+// summed duration of the chase kernel's launches (CUDA events on s).
+constexpr int kQrStateInts = 16;
 template <class R>
 cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, int *h_state,
-                             const int *d_state_all, cudaStream_t s);
+                             const int *d_state_all, cudaStream_t s, float *ms_chase = nullptr);
 // scratch sizes per matrix of size n: rotation log entries, window records,
 // elements of accumulated window products (one round of the QR iteration
 // stops at a sweep boundary before any of them would overflow)

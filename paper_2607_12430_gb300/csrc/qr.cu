@@ -351,7 +351,7 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
     __shared__ cplx<R> s_mu[NB];
     __shared__ cplx<R> s_m[NB * (NB + 1)];
     __shared__ int s_lo, s_hi, s_iter, s_status, s_done, s_nb, s_sweeps, s_stop, s_nwin, s_nlog, s_small, s_bad;
-    __shared__ long long s_uoff, s_rots;
+    __shared__ long long s_uoff, s_rots, s_work;
 
     const SchurDesc<R> d = descs[blockIdx.x];
     const int n = d.n, ld = d.ld;
@@ -375,6 +375,7 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
         s_uoff = 0;
         s_sweeps = st[4];
         s_rots = (long long)st[5] + ((long long)st[6] << 31);
+        s_work = (long long)st[8] + ((long long)st[9] << 31);
         s_stop = 0;
         s_bad = 0;
     }
@@ -431,6 +432,9 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
                 }
                 s_nb = nb;
                 s_rots += (long long)(hi - lo) * nb;
+                // in-block work: each rotation of the sweep updates two rows and
+                // two columns of the active block, about m element pairs
+                s_work += (long long)(hi - lo) * nb * (long long)m;
             }
         }
         __syncthreads();
@@ -620,11 +624,15 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
         st[4] = s_sweeps;
         st[5] = (int)(s_rots & 0x7fffffff);
         st[6] = (int)(s_rots >> 31);
+        st[8] = (int)(s_work & 0x7fffffff);
+        st[9] = (int)(s_work >> 31);
         if (s_status) *d.status = s_status;
         if (d.counters) {
             d.counters[0] = s_sweeps;
             d.counters[1] = st[5];
             d.counters[2] = st[6];
+            d.counters[3] = st[8];
+            d.counters[4] = st[9];
         }
     }
 }
@@ -857,7 +865,7 @@ __global__ void qr_state_init_kernel(const SchurDesc<R> *__restrict__ descs, int
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < batch; b += gridDim.x * blockDim.x) {
         int *st = descs[b].state;
         st[0] = -2;  // fresh: start from hi = n - 1
-        for (int q = 1; q < 8; ++q) st[q] = 0;
+        for (int q = 1; q < kQrStateInts; ++q) st[q] = 0;
     }
 }
 
@@ -882,7 +890,7 @@ int qr_rows_per_cta(int nmax)
 
 template <class R>
 cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, int *h_state,
-                             const int *d_state_all, cudaStream_t s)
+                             const int *d_state_all, cudaStream_t s, float *ms_chase)
 {
     constexpr int RRMAX = QrDims<R>::RR;
     const int rpc = qr_rows_per_cta<R>(nmax);
@@ -897,15 +905,27 @@ cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, in
     qr_state_init_kernel<R><<<1, 256, 0, s>>>(d_desc, batch); count_launch();
     const int ctas = (int)cdiv_i(nmax, rpc);
     bool all = false;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (ms_chase) {
+        *ms_chase = 0.0f;
+        if ((err = cudaEventCreate(&ev[0])) || (err = cudaEventCreate(&ev[1]))) return err;
+    }
     for (int round = 0; round < 256 && !all; ++round) {
+        if (ms_chase && (err = cudaEventRecord(ev[0], s))) break;
         qr_chase_kernel<R><<<batch, kQrThreads, QrDims<R>::chase_smem, s>>>(d_desc); count_launch();
-        if ((err = cudaMemcpyAsync(h_state, d_state_all, sizeof(int) * 8 * batch, cudaMemcpyDeviceToHost, s))) return err;
-        if ((err = cudaStreamSynchronize(s))) return err;
+        if (ms_chase && (err = cudaEventRecord(ev[1], s))) break;
+        if ((err = cudaMemcpyAsync(h_state, d_state_all, sizeof(int) * kQrStateInts * batch, cudaMemcpyDeviceToHost, s))) break;
+        if ((err = cudaStreamSynchronize(s))) break;
+        if (ms_chase) {
+            float ms = 0.0f;
+            if ((err = cudaEventElapsedTime(&ms, ev[0], ev[1]))) break;
+            *ms_chase += ms;
+        }
         int maxwin = 0;
         all = true;
         for (int b = 0; b < batch; ++b) {
-            all = all && h_state[8 * b + 2];
-            maxwin = std::max(maxwin, h_state[8 * b + 7]);
+            all = all && h_state[kQrStateInts * b + 2];
+            maxwin = std::max(maxwin, h_state[kQrStateInts * b + 7]);
         }
         if (maxwin > 0) {
             qr_build_u_kernel<R><<<dim3(maxwin, batch), 128, QrDims<R>::build_smem, s>>>(d_desc); count_launch();
@@ -913,12 +933,15 @@ cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, in
             qr_apply_cols_kernel<R><<<dim3(ctas, batch), 256, cols_bytes, s>>>(d_desc, rpc); count_launch();
         }
     }
+    if (ev[0]) cudaEventDestroy(ev[0]);
+    if (ev[1]) cudaEventDestroy(ev[1]);
+    if (err) return err;
     if (!all) { qr_mark_unfinished_kernel<R><<<1, 256, 0, s>>>(d_desc, batch); count_launch(); }
     qr_finish_kernel<R><<<dim3(64, batch), 256, 0, s>>>(d_desc); count_launch();
     return cudaGetLastError();
 }
 
-template cudaError_t launch_qr_sweeps<float>(const SchurDesc<float> *, int, int, int *, const int *, cudaStream_t);
-template cudaError_t launch_qr_sweeps<double>(const SchurDesc<double> *, int, int, int *, const int *, cudaStream_t);
+template cudaError_t launch_qr_sweeps<float>(const SchurDesc<float> *, int, int, int *, const int *, cudaStream_t, float *);
+template cudaError_t launch_qr_sweeps<double>(const SchurDesc<double> *, int, int, int *, const int *, cudaStream_t, float *);
 
 }  // namespace sqm

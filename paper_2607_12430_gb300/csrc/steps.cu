@@ -76,7 +76,7 @@ static int schur_step(sqrtm_handle_t h, cplx<R> *T, cplx<R> *Q, int64_t n)
     R *beta = c.take<R>(8);
     SchurDesc<R> *dd = c.take<SchurDesc<R>>(1);
     RotLog<R> *rlog = c.take<RotLog<R>>(qr_log_capacity(n));
-    int *qstate = c.take<int>(8);
+    int *qstate = c.take<int>(kQrStateInts);
     WinRec *wrec = c.take<WinRec>(qr_win_capacity(n));
     cplx<R> *ubuf = c.take<cplx<R>>(qr_u_capacity(n));
     SchurDesc<R> hd;
