@@ -103,6 +103,9 @@ extern "C" int sqrtm_create(sqrtm_handle_t *handle, void *stream)
     h->stream = (cudaStream_t)stream;
     for (auto &e : h->ev)
         if (cudaEventCreate(&e) != cudaSuccess) { delete h; return 7; }
+    for (auto &e : h->qev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) { delete h; return 7; }
+    if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess) { delete h; return 7; }
     if (cudaMallocHost(&h->staging.p, 4096) != cudaSuccess) { delete h; return 7; }
     h->staging.bytes = 4096;
     *handle = h;
@@ -121,6 +124,12 @@ extern "C" int sqrtm_destroy(sqrtm_handle_t h)
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->side) {
+        cudaStreamSynchronize(h->side);
+        cudaStreamDestroy(h->side);
+    }
+    for (auto &e : h->qev)
+        if (e) cudaEventDestroy(e);
     if (h->ws.p) cudaFree(h->ws.p);
     if (h->fact.p) cudaFree(h->fact.p);
     if (h->staging.p) cudaFreeHost(h->staging.p);
@@ -248,9 +257,10 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     size_t fbytes = 2 * Carve::round(nn * cb) + Carve::round(nn * sizeof(double)) + 1024;
     size_t wbytes = scalars_bytes(n) + 3 * Carve::round(nn * cb) + Carve::round(nn * sizeof(float)) +
                     Carve::round((n + 8) * cb) + Carve::round(8 * sizeof(R)) +
-                    Carve::round(sizeof(SchurDesc<R>)) + Carve::round(qr_log_capacity(n) * sizeof(RotLog<R>)) +
-                    Carve::round(qr_win_capacity(n) * sizeof(WinRec)) + Carve::round(qr_u_capacity(n) * cb) +
-                    Carve::round(8 * sizeof(int)) + 4096;
+                    Carve::round(2 * sizeof(SchurDesc<R>)) +
+                    2 * (Carve::round(qr_log_capacity(n) * sizeof(RotLog<R>)) +
+                         Carve::round(qr_win_capacity(n) * sizeof(WinRec)) + Carve::round(qr_u_capacity(n) * cb)) +
+                    Carve::round(kQrStateInts * sizeof(int)) + Carve::round(4 * sizeof(int)) + 4096;
     if (ensure(h->fact, fbytes, h) || ensure(h->ws, wbytes, h)) return 7;
     Carve cf(h->fact.p);
     cplx<R> *Q = cf.take<cplx<R>>(nn);
@@ -264,11 +274,20 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     float *Rhat = cw.take<float>(nn);
     cplx<R> *v = cw.take<cplx<R>>(n + 8);
     R *beta = cw.take<R>(8);
-    SchurDesc<R> *ddesc = cw.take<SchurDesc<R>>(1);
-    RotLog<R> *rlog = cw.take<RotLog<R>>(qr_log_capacity(n));
-    WinRec *wrec = cw.take<WinRec>(qr_win_capacity(n));
-    cplx<R> *ubuf = cw.take<cplx<R>>(qr_u_capacity(n));
+    // two descriptors of the same matrix with separate log / window / U
+    // buffers: chase rounds alternate between them while the deferred passes
+    // of the previous round run on the side stream
+    SchurDesc<R> *ddesc = cw.take<SchurDesc<R>>(2);
+    RotLog<R> *rlog[2];
+    WinRec *wrec[2];
+    cplx<R> *ubuf[2];
+    for (int q = 0; q < 2; ++q) {
+        rlog[q] = cw.take<RotLog<R>>(qr_log_capacity(n));
+        wrec[q] = cw.take<WinRec>(qr_win_capacity(n));
+        ubuf[q] = cw.take<cplx<R>>(qr_u_capacity(n));
+    }
     int *qstate = cw.take<int>(kQrStateInts);
+    int *rstate = cw.take<int>(4);
     h->fact_n = -1;
 
     SQM_CU(cudaMemsetAsync(sc.e, 0, 16 * sizeof(int), s));
@@ -285,11 +304,20 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     SchurDesc<R> hd;
     hd.T = T; hd.Q = Q; hd.v = v; hd.beta = beta; hd.status = sc.st_schur; hd.n = (int)n; hd.ld = (int)n;
     hd.counters = sc.st_schur + 3;
-    hd.log = rlog; hd.state = qstate; hd.log_cap = (int)std::min<int64_t>(qr_log_capacity(n), INT32_MAX);
-    hd.win = wrec; hd.win_cap = (int)std::min<int64_t>(qr_win_capacity(n), INT32_MAX);
-    hd.ubuf = ubuf; hd.u_cap = qr_u_capacity(n);
-    memcpy(h->staging.p, &hd, sizeof(hd));
-    SQM_CU(cudaMemcpyAsync(ddesc, h->staging.p, sizeof(hd), cudaMemcpyHostToDevice, s));
+    hd.state = qstate; hd.log_cap = (int)std::min<int64_t>(qr_log_capacity(n), INT32_MAX);
+    // rounds of at most max(64, n/2) windows, so that several rounds overlap
+    // their deferred passes with the chase
+    hd.win_cap = (int)std::min<int64_t>(qr_win_capacity(n), std::max<int64_t>(64, n / 2));
+    hd.u_cap = qr_u_capacity(n);
+    SchurDesc<R> hd2[2] = {hd, hd};
+    for (int q = 0; q < 2; ++q) {
+        hd2[q].log = rlog[q];
+        hd2[q].win = wrec[q];
+        hd2[q].ubuf = ubuf[q];
+        hd2[q].rstate = rstate + 2 * q;
+    }
+    memcpy(h->staging.p, hd2, sizeof(hd2));
+    SQM_CU(cudaMemcpyAsync(ddesc, h->staging.p, sizeof(hd2), cudaMemcpyHostToDevice, s));
     SQM_CU(cudaStreamSynchronize(s));
     {
         struct Ctx { SchurDesc<R> *d; int n; } ctx{ddesc, (int)n};
@@ -303,7 +331,8 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     SQM_CU(cudaEventCreate(&ev_red));
     SQM_CU(cudaEventRecord(ev_red, s));
     float ms_chase = 0.0f;
-    SQM_CU(launch_qr_sweeps<R>(ddesc, 1, (int)n, (int *)h->staging.p + 512, qstate, s, &ms_chase));
+    SQM_CU(launch_qr_sweeps<R>(ddesc, 1, (int)n, (int *)h->staging.p + 512, qstate, s, &ms_chase, ddesc + 1, h->side,
+                               h->qev));
     SQM_CU(cudaEventRecord(h->ev[1], s));
     SQM_CU(launch_trisqrt<R>(T, (int)n, S, (int)n, (int)n, o.blks, sc.st_solve, s));
     // X_0 = Re(Q S Q^H), rounded to R, times 2^e

@@ -32,6 +32,11 @@ struct sqrtm_handle_s {
     int fact_e = 0;
     double fact_norm = 0.0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // QR iteration: a second stream for the deferred window products, which
+    // run while the next round of the chase does, and its ordering events
+    // (chase done / deferred passes done, one pair per log buffer)
+    cudaStream_t side = nullptr;
+    cudaEvent_t qev[4] = {nullptr, nullptr, nullptr, nullptr};
     // captured launch sequences (CUDA graphs), keyed by what they depend on
     struct Graph {
         int tag;

@@ -48,7 +48,8 @@ struct SchurDesc {
     WinRec *win;     // scratch: window records (win_cap entries)
     cplx<R> *ubuf;   // scratch: accumulated window rotations (u_cap elements)
     long long u_cap;
-    int *state;      // scratch: 8 ints of QR iteration state
+    int *state;      // scratch: kQrStateInts ints of QR iteration state
+    int *rstate;     // scratch: [0] windows in this descriptor's buffers after its last chase round
     int log_cap;
     int win_cap;
     cplx<R> *T;      // in: A_s, out: upper triangular T (n x n)
@@ -80,10 +81,18 @@ cudaError_t launch_hessenberg(const SchurDesc<R> *d_desc, int batch, int nmax,
 // (descs[b].state == d_state_all + kQrStateInts b); h_state: pinned host
 // buffer of kQrStateInts * batch ints.  ms_chase (may be null) receives the
 // summed duration of the chase kernel's launches (CUDA events on s).
+// d_desc_alt (may be null): the same matrices with a second set of log,
+// window and U buffers; then the chase rounds alternate between the two
+// sets and each round's deferred passes run on `side` (ordered by the four
+// events qev) while the next round's chase runs on s.  The deferred passes
+// touch only T entries outside every later active block and Z, which the
+// chase never reads.
 constexpr int kQrStateInts = 16;
 template <class R>
 cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, int *h_state,
-                             const int *d_state_all, cudaStream_t s, float *ms_chase = nullptr);
+                             const int *d_state_all, cudaStream_t s, float *ms_chase = nullptr,
+                             const SchurDesc<R> *d_desc_alt = nullptr, cudaStream_t side = nullptr,
+                             const cudaEvent_t *qev = nullptr);
 // scratch sizes per matrix of size n: rotation log entries, window records,
 // elements of accumulated window products (one round of the QR iteration
 // stops at a sweep boundary before any of them would overflow)

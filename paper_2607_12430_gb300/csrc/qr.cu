@@ -362,7 +362,7 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
     const R eps = num<R>::eps;
     int *st = d.state;
     if (st[2]) {  // already finished: nothing new in the log
-        if (tid == 0) { st[3] = 0; st[7] = 0; }
+        if (tid == 0) { st[3] = 0; st[7] = 0; d.rstate[0] = 0; }
         return;
     }
     if (tid == 0) {
@@ -621,6 +621,7 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
         st[2] = (s_done || s_status) ? 1 : 0;
         st[3] = s_nlog;
         st[7] = s_nwin;
+        d.rstate[0] = s_nwin;
         st[4] = s_sweeps;
         st[5] = (int)(s_rots & 0x7fffffff);
         st[6] = (int)(s_rots >> 31);
@@ -651,7 +652,7 @@ __global__ void __launch_bounds__(128) qr_build_u_kernel(const SchurDesc<R> *__r
     RotLog<R> *lg = reinterpret_cast<RotLog<R> *>(smraw);
     cplx<R> *u = reinterpret_cast<cplx<R> *>(lg + W * NB);
     const SchurDesc<R> d = descs[blockIdx.y];
-    const int nwin = d.state[7];
+    const int nwin = d.rstate[0];
     if ((int)blockIdx.x >= nwin) return;
     const WinRec w = d.win[blockIdx.x];
     const int rr = w.rr, r = threadIdx.x;
@@ -701,7 +702,7 @@ qr_apply_rows_kernel(const SchurDesc<R> *__restrict__ descs, int rpc, int ctas_t
     extern __shared__ unsigned char smraw[];
     const SchurDesc<R> d = descs[blockIdx.y];
     const int n = d.n, ld = d.ld;
-    const int nwin = d.state[7];
+    const int nwin = d.rstate[0];
     if (nwin == 0) return;
     const bool isT = blockIdx.x < ctas_t;
     const int cb = isT ? blockIdx.x : blockIdx.x - ctas_t;
@@ -711,6 +712,11 @@ qr_apply_rows_kernel(const SchurDesc<R> *__restrict__ descs, int rpc, int ctas_t
     cplx<R> *M = isT ? d.T : d.Q;
     cplx<R> *buf = reinterpret_cast<cplx<R> *>(smraw);          // rpc x n, buf[r + c rpc]
     cplx<R> *ub[2] = {buf + (size_t)rpc * n, buf + (size_t)rpc * n + RRMAX * RRMAX};
+    // T rows: column c was changed in rows i < lmax[c] (the windows' lo);
+    // only those entries are written back (the rest may belong to a later
+    // active block that the chase is updating meanwhile)
+    int *lmax = reinterpret_cast<int *>(ub[1] + RRMAX * RRMAX);
+    for (int c = threadIdx.x; c < n; c += blockDim.x) lmax[c] = 0;
     for (int e = threadIdx.x; e < rn * n; e += blockDim.x) {
         const int a = e % rn, b = e / rn;
         cp_async_elem<R>(&buf[a + b * rpc], &M[(i0 + a) + (int64_t)b * ld]);
@@ -758,6 +764,7 @@ qr_apply_rows_kernel(const SchurDesc<R> *__restrict__ descs, int rpc, int ctas_t
             if (o < no) {
                 const int r = o % rn, c = o / rn;
                 if (!isT || i0 + r < w.lo) buf[r + (size_t)(w.kmin + c) * rpc] = out[j];
+                if (r == 0) lmax[w.kmin + c] = max(lmax[w.kmin + c], w.lo);
             }
         }
         wi = wn;
@@ -767,7 +774,7 @@ qr_apply_rows_kernel(const SchurDesc<R> *__restrict__ descs, int rpc, int ctas_t
     __syncthreads();
     for (int e = threadIdx.x; e < rn * n; e += blockDim.x) {
         const int a = e % rn, b = e / rn;
-        M[(i0 + a) + (int64_t)b * ld] = buf[a + b * rpc];
+        if (!isT || i0 + a < lmax[b]) M[(i0 + a) + (int64_t)b * ld] = buf[a + b * rpc];
     }
 }
 
@@ -781,7 +788,7 @@ qr_apply_cols_kernel(const SchurDesc<R> *__restrict__ descs, int cpc)
     extern __shared__ unsigned char smraw[];
     const SchurDesc<R> d = descs[blockIdx.y];
     const int n = d.n, ld = d.ld;
-    const int nwin = d.state[7];
+    const int nwin = d.rstate[0];
     if (nwin == 0) return;
     const int j0 = blockIdx.x * cpc;
     if (j0 >= n) return;
@@ -789,6 +796,10 @@ qr_apply_cols_kernel(const SchurDesc<R> *__restrict__ descs, int cpc)
     const int cs = n + 1;
     cplx<R> *buf = reinterpret_cast<cplx<R> *>(smraw);           // column jl at buf + jl cs
     cplx<R> *ub[2] = {buf + (size_t)cs * cpc, buf + (size_t)cs * cpc + RRMAX * RRMAX};
+    // row i was changed in columns j > hmin[i] (the windows' hi); only those
+    // entries are written back
+    int *hmin = reinterpret_cast<int *>(ub[1] + RRMAX * RRMAX);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) hmin[i] = n;
     for (int e = threadIdx.x; e < cn * n; e += blockDim.x) {
         const int a = e % n, b = e / n;
         cp_async_elem<R>(&buf[a + (size_t)b * cs], &d.T[a + (int64_t)(j0 + b) * ld]);
@@ -834,6 +845,7 @@ qr_apply_cols_kernel(const SchurDesc<R> *__restrict__ descs, int cpc)
             if (o < no) {
                 const int jl = o % cn, c = o / cn;
                 if (j0 + jl > w.hi) buf[(size_t)jl * cs + w.kmin + c] = out[j];
+                if (jl == 0) hmin[w.kmin + c] = min(hmin[w.kmin + c], w.hi);
             }
         }
         wi = wn;
@@ -843,7 +855,7 @@ qr_apply_cols_kernel(const SchurDesc<R> *__restrict__ descs, int cpc)
     __syncthreads();
     for (int e = threadIdx.x; e < cn * n; e += blockDim.x) {
         const int a = e % n, b = e / n;
-        d.T[a + (int64_t)(j0 + b) * ld] = buf[a + (size_t)b * cs];
+        if (j0 + b > hmin[a]) d.T[a + (int64_t)(j0 + b) * ld] = buf[a + (size_t)b * cs];
     }
 }
 
@@ -883,20 +895,22 @@ int qr_rows_per_cta(int nmax)
 {
     constexpr int RRMAX = QrDims<R>::RR;
     size_t per = (size_t)(std::max(nmax, 1) + 1) * sizeof(cplx<R>);
-    size_t avail = 200 * 1024 - 2 * (size_t)RRMAX * RRMAX * sizeof(cplx<R>);
+    size_t avail = 200 * 1024 - 2 * (size_t)RRMAX * RRMAX * sizeof(cplx<R>) - (size_t)std::max(nmax, 1) * sizeof(int);
     size_t r = avail / per;
     return (int)std::max<size_t>(1, std::min<size_t>(32, r));
 }
 
 template <class R>
 cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, int *h_state,
-                             const int *d_state_all, cudaStream_t s, float *ms_chase)
+                             const int *d_state_all, cudaStream_t s, float *ms_chase,
+                             const SchurDesc<R> *d_desc_alt, cudaStream_t side, const cudaEvent_t *qev)
 {
     constexpr int RRMAX = QrDims<R>::RR;
     const int rpc = qr_rows_per_cta<R>(nmax);
     const size_t ubytes = 2 * (size_t)RRMAX * RRMAX * sizeof(cplx<R>);
-    const size_t rows_bytes = (size_t)rpc * nmax * sizeof(cplx<R>) + ubytes;
-    const size_t cols_bytes = (size_t)rpc * (nmax + 1) * sizeof(cplx<R>) + ubytes;
+    const size_t mbytes = (size_t)std::max(nmax, 1) * sizeof(int);  // write-back masks
+    const size_t rows_bytes = (size_t)rpc * nmax * sizeof(cplx<R>) + ubytes + mbytes;
+    const size_t cols_bytes = (size_t)rpc * (nmax + 1) * sizeof(cplx<R>) + ubytes + mbytes;
     cudaError_t err;
     if ((err = allow_max_smem((const void *)qr_chase_kernel<R>))) return err;
     if ((err = allow_max_smem((const void *)qr_build_u_kernel<R>))) return err;
@@ -910,9 +924,15 @@ cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, in
         *ms_chase = 0.0f;
         if ((err = cudaEventCreate(&ev[0])) || (err = cudaEventCreate(&ev[1]))) return err;
     }
+    const bool overlap = d_desc_alt && side && qev;
+    bool used[2] = {false, false};
     for (int round = 0; round < 256 && !all; ++round) {
+        const int par = overlap ? (round & 1) : 0;
+        const SchurDesc<R> *dd = par ? d_desc_alt : d_desc;
+        // this buffer set's deferred passes from two rounds ago must be done
+        if (used[par] && (err = cudaStreamWaitEvent(s, qev[2 + par], 0))) break;
         if (ms_chase && (err = cudaEventRecord(ev[0], s))) break;
-        qr_chase_kernel<R><<<batch, kQrThreads, QrDims<R>::chase_smem, s>>>(d_desc); count_launch();
+        qr_chase_kernel<R><<<batch, kQrThreads, QrDims<R>::chase_smem, s>>>(dd); count_launch();
         if (ms_chase && (err = cudaEventRecord(ev[1], s))) break;
         if ((err = cudaMemcpyAsync(h_state, d_state_all, sizeof(int) * kQrStateInts * batch, cudaMemcpyDeviceToHost, s))) break;
         if ((err = cudaStreamSynchronize(s))) break;
@@ -928,11 +948,26 @@ cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, in
             maxwin = std::max(maxwin, h_state[kQrStateInts * b + 7]);
         }
         if (maxwin > 0) {
-            qr_build_u_kernel<R><<<dim3(maxwin, batch), 128, QrDims<R>::build_smem, s>>>(d_desc); count_launch();
-            qr_apply_rows_kernel<R><<<dim3(2 * ctas, batch), 256, rows_bytes, s>>>(d_desc, rpc, ctas); count_launch();
-            qr_apply_cols_kernel<R><<<dim3(ctas, batch), 256, cols_bytes, s>>>(d_desc, rpc); count_launch();
+            cudaStream_t ds = s;
+            if (overlap) {
+                if ((err = cudaEventRecord(qev[par], s)) || (err = cudaStreamWaitEvent(side, qev[par], 0))) break;
+                ds = side;
+            }
+            qr_build_u_kernel<R><<<dim3(maxwin, batch), 128, QrDims<R>::build_smem, ds>>>(dd); count_launch();
+            qr_apply_rows_kernel<R><<<dim3(2 * ctas, batch), 256, rows_bytes, ds>>>(dd, rpc, ctas); count_launch();
+            qr_apply_cols_kernel<R><<<dim3(ctas, batch), 256, cols_bytes, ds>>>(dd, rpc); count_launch();
+            if (overlap) {
+                if ((err = cudaEventRecord(qev[2 + par], side))) break;
+                used[par] = true;
+            }
         }
     }
+    // every deferred pass finishes before T is read again
+    for (int q = 0; q < 2; ++q)
+        if (used[q]) {
+            cudaError_t e2 = cudaStreamWaitEvent(s, qev[2 + q], 0);
+            if (!err) err = e2;
+        }
     if (ev[0]) cudaEventDestroy(ev[0]);
     if (ev[1]) cudaEventDestroy(ev[1]);
     if (err) return err;
@@ -941,7 +976,9 @@ cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, in
     return cudaGetLastError();
 }
 
-template cudaError_t launch_qr_sweeps<float>(const SchurDesc<float> *, int, int, int *, const int *, cudaStream_t, float *);
-template cudaError_t launch_qr_sweeps<double>(const SchurDesc<double> *, int, int, int *, const int *, cudaStream_t, float *);
+template cudaError_t launch_qr_sweeps<float>(const SchurDesc<float> *, int, int, int *, const int *, cudaStream_t, float *,
+                                             const SchurDesc<float> *, cudaStream_t, const cudaEvent_t *);
+template cudaError_t launch_qr_sweeps<double>(const SchurDesc<double> *, int, int, int *, const int *, cudaStream_t, float *,
+                                              const SchurDesc<double> *, cudaStream_t, const cudaEvent_t *);
 
 }  // namespace sqm

@@ -68,7 +68,8 @@ static int schur_step(sqrtm_handle_t h, cplx<R> *T, cplx<R> *Q, int64_t n)
 {
     StepScratch ss; void *ex;
     size_t extra = Carve::round((n + 8) * sizeof(cplx<R>)) + Carve::round(8 * sizeof(R)) + Carve::round(sizeof(SchurDesc<R>)) +
-                   Carve::round(qr_log_capacity(n) * sizeof(RotLog<R>)) + Carve::round(8 * sizeof(int)) +
+                   Carve::round(qr_log_capacity(n) * sizeof(RotLog<R>)) + Carve::round(kQrStateInts * sizeof(int)) +
+                   Carve::round(4 * sizeof(int)) +
                    Carve::round(qr_win_capacity(n) * sizeof(WinRec)) + Carve::round(qr_u_capacity(n) * sizeof(cplx<R>));
     if (int rc = step_scratch(h, n, extra, &ss, &ex)) return rc;
     Carve c(ex);
@@ -79,7 +80,9 @@ static int schur_step(sqrtm_handle_t h, cplx<R> *T, cplx<R> *Q, int64_t n)
     int *qstate = c.take<int>(kQrStateInts);
     WinRec *wrec = c.take<WinRec>(qr_win_capacity(n));
     cplx<R> *ubuf = c.take<cplx<R>>(qr_u_capacity(n));
+    int *rstate = c.take<int>(4);
     SchurDesc<R> hd;
+    hd.rstate = rstate;
     hd.T = T; hd.Q = Q; hd.v = v; hd.beta = beta; hd.status = ss.iscal + 1; hd.n = (int)n; hd.ld = (int)n;
     hd.counters = nullptr;
     hd.log = rlog; hd.state = qstate; hd.log_cap = (int)std::min<int64_t>(qr_log_capacity(n), INT32_MAX);

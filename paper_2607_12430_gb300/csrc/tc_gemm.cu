@@ -168,21 +168,31 @@ tc3_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
             uint32_t r[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
             if (row < M) {
+                if (EPI == TC_EPI_SYM_ADD_F64) {
+                    // loads of the chunk first (the mirrored stores go to the
+                    // same array and would otherwise serialise every load)
+                    double old[32];
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int col = n0 + c0 + j;
-                    if (col >= N) continue;
-                    const float v = __uint_as_float(r[j]);
-                    if (EPI == TC_EPI_STORE) {
-                        ep.C[row + (int64_t)col * ep.ldc] = v;
-                    } else if (EPI == TC_EPI_DIAG_SOLVE) {
-                        ep.C[row + (int64_t)col * ep.ldc] = v / (ep.s[row] + ep.s[col]);
-                    } else {  // TC_EPI_SYM_ADD_F64
-                        if (row <= col) {
-                            const double x = ep.X[row + (int64_t)col * ep.ldx] + (double)v * ep.scale;
-                            ep.X[row + (int64_t)col * ep.ldx] = x;
-                            ep.X[col + (int64_t)row * ep.ldx] = x;
-                        }
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = n0 + c0 + j;
+                        old[j] = (col < N && row <= col) ? ep.X[row + (int64_t)col * ep.ldx] : 0.0;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = n0 + c0 + j;
+                        if (col >= N || row > col) continue;
+                        const double x = old[j] + (double)__uint_as_float(r[j]) * ep.scale;
+                        ep.X[row + (int64_t)col * ep.ldx] = x;
+                        ep.X[col + (int64_t)row * ep.ldx] = x;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = n0 + c0 + j;
+                        if (col >= N) continue;
+                        const float v = __uint_as_float(r[j]);
+                        if (EPI == TC_EPI_STORE) ep.C[row + (int64_t)col * ep.ldc] = v;
+                        else ep.C[row + (int64_t)col * ep.ldc] = v / (ep.s[row] + ep.s[col]);
                     }
                 }
             }

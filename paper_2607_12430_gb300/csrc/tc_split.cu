@@ -26,7 +26,7 @@
 // Products.  One launch per pair (s, t): 128 x 128 output tiles of the upper
 // block triangle only (R is symmetric), K in steps of 64 BF16 values; TMA
 // loads both digit tiles (128 rows x 128 bytes, 128-byte swizzle) into a
-// 4-stage ring, one thread issues 4 tcgen05.mma (M = N = 128, K = 16) per
+// 6-stage ring, one thread issues 4 tcgen05.mma (M = N = 128, K = 16) per
 // stage into a 128-column TMEM accumulator, and the epilogue adds the scaled
 // tile into the FP64 accumulator (the first pair starts it from A, the last
 // one writes Rhat = fl32(R 4^-e), mirrored, and per-tile partial sums of
@@ -41,7 +41,7 @@
 
 namespace sqm {
 
-static constexpr int SP_BM = 128, SP_BN = 128, SP_BK = 64, SP_STAGES = 4, SP_THREADS = 128;
+static constexpr int SP_BM = 128, SP_BN = 128, SP_BK = 64, SP_STAGES = 6, SP_THREADS = 128;
 static constexpr int SP_TILE_BYTES = SP_BM * SP_BK * 2;  // 16 KB
 static constexpr int SP_STAGE_BYTES = 2 * SP_TILE_BYTES;
 static constexpr int SP_SMEM = SP_STAGES * SP_STAGE_BYTES + 1024 + 256;
@@ -193,13 +193,26 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
             uint32_t r[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
             if (row < n) {
+                // all loads of the chunk first: the stores below go to the
+                // same arrays, so loads issued after them would each wait
+                // out a full memory round trip
+                double old[32];
+                int rj[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int col = n0 + c0 + j;
+                    const bool in = col < n && row <= col;
+                    old[j] = in ? ((MODE & SP_FIRST) ? ep.A[row + (int64_t)col * ep.lda]
+                                                      : ep.Racc[row + (int64_t)col * ep.ldr])
+                                : 0.0;
+                    rj[j] = col < n ? ep.rho[col] : 0;
+                }
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int col = n0 + c0 + j;
                     if (col >= n || row > col) continue;
-                    const double p = ldexp((double)__uint_as_float(r[j]), rho_i + ep.rho[col] - ep.shift);
-                    double *acc = ep.Racc + row + (int64_t)col * ep.ldr;
-                    const double v = ((MODE & SP_FIRST) ? ep.A[row + (int64_t)col * ep.lda] : *acc) - p;
+                    const double p = ldexp((double)__uint_as_float(r[j]), rho_i + rj[j] - ep.shift);
+                    const double v = old[j] - p;
                     if (MODE & SP_LAST) {
                         const double rs = v * ep.sc;
                         const float rf = (float)rs;
@@ -208,7 +221,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
                         ss = fma(rs, rs, ss);
                         if (row != col) ss = fma(rs, rs, ss);  // mirrored entry
                     } else {
-                        *acc = v;
+                        ep.Racc[row + (int64_t)col * ep.ldr] = v;
                     }
                 }
             }
