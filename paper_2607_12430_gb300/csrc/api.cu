@@ -260,7 +260,7 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
                     Carve::round(2 * sizeof(SchurDesc<R>)) +
                     2 * (Carve::round(qr_log_capacity(n) * sizeof(RotLog<R>)) +
                          Carve::round(qr_win_capacity(n) * sizeof(WinRec)) + Carve::round(qr_u_capacity(n) * cb)) +
-                    Carve::round(kQrStateInts * sizeof(int)) + Carve::round(4 * sizeof(int)) + 4096;
+                    Carve::round(kQrStateInts * sizeof(int)) + Carve::round(4 * sizeof(int)) + Carve::round(32 * sizeof(int)) + 4096;
     if (ensure(h->fact, fbytes, h) || ensure(h->ws, wbytes, h)) return 7;
     Carve cf(h->fact.p);
     cplx<R> *Q = cf.take<cplx<R>>(nn);
@@ -288,6 +288,7 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     }
     int *qstate = cw.take<int>(kQrStateInts);
     int *rstate = cw.take<int>(4);
+    int *qsync = cw.take<int>(32);
     h->fact_n = -1;
 
     SQM_CU(cudaMemsetAsync(sc.e, 0, 16 * sizeof(int), s));
@@ -315,6 +316,7 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
         hd2[q].win = wrec[q];
         hd2[q].ubuf = ubuf[q];
         hd2[q].rstate = rstate + 2 * q;
+        hd2[q].sync = qsync;
     }
     memcpy(h->staging.p, hd2, sizeof(hd2));
     SQM_CU(cudaMemcpyAsync(ddesc, h->staging.p, sizeof(hd2), cudaMemcpyHostToDevice, s));
@@ -332,7 +334,7 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     SQM_CU(cudaEventRecord(ev_red, s));
     float ms_chase = 0.0f;
     SQM_CU(launch_qr_sweeps<R>(ddesc, 1, (int)n, (int *)h->staging.p + 512, qstate, s, &ms_chase, ddesc + 1, h->side,
-                               h->qev));
+                               h->qev, qsync));
     SQM_CU(cudaEventRecord(h->ev[1], s));
     SQM_CU(launch_trisqrt<R>(T, (int)n, S, (int)n, (int)n, o.blks, sc.st_solve, s));
     // X_0 = Re(Q S Q^H), rounded to R, times 2^e

@@ -36,7 +36,10 @@ struct alignas(16) RotLog {
 // active block is [lo, hi], and the window's accumulated rotation product U
 // (rr x rr) is stored at ubuf + uoff.
 struct WinRec {
-    int start, kbase, nsteps, kmin, rr, lo, hi, pad;
+    int start, kbase, nsteps, kmin, rr, lo, hi;
+    int t0, nb;      // first step of the window within its sweep; bulges of the sweep
+    int r0, rnext;   // first row of the window block; last column of the next window's block
+    int pad;
     long long uoff;
 };
 
@@ -50,6 +53,7 @@ struct SchurDesc {
     long long u_cap;
     int *state;      // scratch: kQrStateInts ints of QR iteration state
     int *rstate;     // scratch: [0] windows in this descriptor's buffers after its last chase round
+    int *sync;       // scratch (cooperative chase): [0] windows posted, [1] quit, [2] failed, [4 + h] windows done by helper h
     int log_cap;
     int win_cap;
     cplx<R> *T;      // in: A_s, out: upper triangular T (n x n)
@@ -86,13 +90,16 @@ cudaError_t launch_hessenberg(const SchurDesc<R> *d_desc, int batch, int nmax,
 // sets and each round's deferred passes run on `side` (ordered by the four
 // events qev) while the next round's chase runs on s.  The deferred passes
 // touch only T entries outside every later active block and Z, which the
-// chase never reads.
+// chase never reads.  d_sync (may be null; >= 32 ints, the descriptors'
+// `sync`): with batch == 1 and a large enough n the chase runs as one
+// cooperative grid of a chase CTA and helper CTAs that take the
+// out-of-window updates of the active block.
 constexpr int kQrStateInts = 16;
 template <class R>
 cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, int *h_state,
                              const int *d_state_all, cudaStream_t s, float *ms_chase = nullptr,
                              const SchurDesc<R> *d_desc_alt = nullptr, cudaStream_t side = nullptr,
-                             const cudaEvent_t *qev = nullptr);
+                             const cudaEvent_t *qev = nullptr, int *d_sync = nullptr);
 // scratch sizes per matrix of size n: rotation log entries, window records,
 // elements of accumulated window products (one round of the QR iteration
 // stops at a sweep boundary before any of them would overflow)

@@ -37,10 +37,12 @@
 #include <algorithm>
 
 #include "internal.h"
+#include "tc_common.cuh"
 
 namespace sqm {
 
 static constexpr int kItMax = 60;
+static constexpr int kQrCoopMinN = 256;  // smallest n for the cooperative chase
 static constexpr int kQrThreads = 512;           // chase CTA
 static constexpr int kQrTpc = 4;                 // threads per row/column segment in the updates
 static constexpr int kQrCh = kQrThreads / kQrTpc;  // segments per update chunk
@@ -338,9 +340,171 @@ __device__ __noinline__ bool apply_window(cplx<R> *vec, bool on, const RotLog<R>
     return ok;
 }
 
+// Loads through L2 only (ld.global.cg): in the cooperative chase, T, the
+// rotation tables and the window records are written by other CTAs of the
+// same grid, and L1 is not coherent across SMs.
+template <class R> __device__ __forceinline__ cplx<R> ldcg_c(const cplx<R> *p);
+template <> __device__ __forceinline__ cplx<float> ldcg_c<float>(const cplx<float> *p)
+{
+    const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+    return cplx<float>{v.x, v.y};
+}
+template <> __device__ __forceinline__ cplx<double> ldcg_c<double>(const cplx<double> *p)
+{
+    const double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+    return cplx<double>{v.x, v.y};
+}
+template <class R> __device__ __forceinline__ RotLog<R> ldcg_rot(const RotLog<R> *p);
+template <> __device__ __forceinline__ RotLog<float> ldcg_rot<float>(const RotLog<float> *p)
+{
+    const float4 v = __ldcg(reinterpret_cast<const float4 *>(p));
+    return RotLog<float>{v.x, v.y, v.z, v.w};
+}
+template <> __device__ __forceinline__ RotLog<double> ldcg_rot<double>(const RotLog<double> *p)
+{
+    const double2 a = __ldcg(reinterpret_cast<const double2 *>(p)), b = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
+    return RotLog<double>{a.x, a.y, b.x, b.y};
+}
+// T element into shared memory: asynchronous copy through L1 in the
+// single-CTA chase, L2-coherent load in the cooperative one
+template <class R, bool HELP>
+__device__ __forceinline__ void load_t(cplx<R> *dst, const cplx<R> *src)
+{
+    if (HELP) *dst = ldcg_c<R>(src);
+    else cp_async_elem<R>(dst, src);
+}
+
+static constexpr uint64_t kQrWaitNs = 2000000000ull;  // bounded inter-CTA waits (~2 s)
+
+// Cooperative chase: every thread of the calling CTA waits until each of
+// the H helpers has finished `target` windows; false if a helper failed or
+// the wait gave up.
 template <class R>
+__device__ bool wait_helpers(const SchurDesc<R> &d, int H, int target)
+{
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        volatile int *sy = d.sync;
+        const uint64_t t0 = globaltimer_ns();
+        int ok = 1;
+        for (int h = 0; h < H && ok; ++h)
+            while (sy[4 + h] < target) {
+                if (sy[2] || globaltimer_ns() - t0 > kQrWaitNs) { ok = 0; break; }
+            }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    const bool ok = s_ok != 0;
+    __threadfence();
+    __syncthreads();
+    return ok;
+}
+
+// Helper CTA h of the cooperative chase: for every window the chase CTA
+// posts (in order), the left rotations on the columns right of the next
+// window's block and the right rotations on the rows above the window,
+// restricted to the index groups it owns (groups of 8 consecutive indices,
+// group g owned by helper g mod H; no other CTA writes them, so the windows
+// need no ordering between helpers).  Then it publishes its count.
+template <class R>
+__device__ void qr_helper(const SchurDesc<R> &d, int H, int h, cplx<R> *tile, RotLog<R> *rt)
+{
+    using D = QrDims<R>;
+    constexpr int W = D::W, NB = D::NB, RLD = D::RLD, CLD = D::CLD;
+    constexpr int nt = kQrThreads;
+    __shared__ int s_go, s_cnt, s_g, s_idx[kQrCh];
+    __shared__ int s_win[12];
+    const int tid = threadIdx.x, sub = tid % kQrTpc, seg = tid / kQrTpc;
+    cplx<R> *T = d.T;
+    const int ld = d.ld;
+    for (int w = 0;; ++w) {
+        if (tid == 0) {
+            volatile int *sy = d.sync;
+            const uint64_t t0 = globaltimer_ns();
+            int go = 0;
+            while (true) {
+                if (sy[0] > w) { go = 1; break; }
+                if (sy[1]) { go = 2; break; }
+                if (sy[2] || globaltimer_ns() - t0 > kQrWaitNs) { go = 3; break; }
+            }
+            __threadfence();
+            s_go = go;
+        }
+        __syncthreads();
+        const int go = s_go;
+        if (go != 1) {
+            if (go == 3 && tid == 0) atomicExch(&d.sync[2], 1);
+            return;
+        }
+        __threadfence();
+        if (tid < 12) s_win[tid] = __ldcg(reinterpret_cast<const int *>(&d.win[w]) + tid);
+        __syncthreads();
+        const int start = s_win[0], kbase = s_win[1], ns = s_win[2], kmin = s_win[3], rr = s_win[4];
+        const int lo = s_win[5], hi = s_win[6], t0w = s_win[7], nb = s_win[8], r0 = s_win[9], rnext = s_win[10];
+        for (int e = tid; e < W * NB; e += nt) rt[e] = ldcg_rot<R>(d.log + start + e);
+        const int off = kbase - kmin;
+        bool bad = false;
+        // two passes: left rotations on columns (rnext, hi], right rotations
+        // on rows [lo, r0); the owned indices are gathered 128 at a time
+        for (int pass = 0; pass < 2; ++pass) {
+            const int ilo = pass == 0 ? rnext + 1 : lo, ihi = pass == 0 ? hi : r0 - 1;
+            if (ihi < ilo) continue;
+            int g = ilo >> 3;
+            g += ((h - g % H) % H + H) % H;
+            while (g <= (ihi >> 3)) {
+                __syncthreads();
+                if (tid == 0) {
+                    int cnt = 0, gg = g;
+                    while (gg <= (ihi >> 3) && cnt + 8 <= kQrCh) {
+                        for (int c = max(ilo, 8 * gg); c <= min(ihi, 8 * gg + 7); ++c) s_idx[cnt++] = c;
+                        gg += H;
+                    }
+                    s_cnt = cnt;
+                    s_g = gg;
+                }
+                __syncthreads();
+                const int cn = s_cnt;
+                g = s_g;
+                if (pass == 0) {
+                    for (int e = tid; e < rr * cn; e += nt) {
+                        const int v = e % rr, j = e / rr;
+                        tile[v + j * RLD] = ldcg_c<R>(&T[(kmin + v) + (int64_t)s_idx[j] * ld]);
+                    }
+                    __syncthreads();
+                    if (!apply_window<R, NB, 1, true>(tile + seg * RLD, seg < cn, rt, ns, off, rr, sub, t0w, hi - lo, nb))
+                        bad = true;
+                    __syncthreads();
+                    for (int e = tid; e < rr * cn; e += nt) {
+                        const int v = e % rr, j = e / rr;
+                        T[(kmin + v) + (int64_t)s_idx[j] * ld] = tile[v + j * RLD];
+                    }
+                } else {
+                    for (int e = tid; e < cn * rr; e += nt) {
+                        const int a = e % cn, v = e / cn;
+                        tile[a + v * CLD] = ldcg_c<R>(&T[s_idx[a] + (int64_t)(kmin + v) * ld]);
+                    }
+                    __syncthreads();
+                    if (!apply_window<R, NB, CLD, false>(tile + seg, seg < cn, rt, ns, off, rr, sub, t0w, hi - lo, nb))
+                        bad = true;
+                    __syncthreads();
+                    for (int e = tid; e < cn * rr; e += nt) {
+                        const int a = e % cn, v = e / cn;
+                        T[s_idx[a] + (int64_t)(kmin + v) * ld] = tile[a + v * CLD];
+                    }
+                }
+            }
+        }
+        if (bad) atomicExch(d.status, 7);
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) atomicExch(&d.sync[4 + h], w + 1);
+    }
+}
+
+template <class R, bool HELP>
 __global__ void __launch_bounds__(kQrThreads, 1)
-qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
+qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
 {
     using D = QrDims<R>;
     constexpr int W = D::W, NB = D::NB, BLD = D::BLD, RLD = D::RLD, CLD = D::CLD;
@@ -353,7 +517,11 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
     __shared__ int s_lo, s_hi, s_iter, s_status, s_done, s_nb, s_sweeps, s_stop, s_nwin, s_nlog, s_small, s_bad;
     __shared__ long long s_uoff, s_rots, s_work;
 
-    const SchurDesc<R> d = descs[blockIdx.x];
+    const SchurDesc<R> d = descs[HELP ? 0 : blockIdx.x];
+    if (HELP && blockIdx.x > 0) {
+        qr_helper<R>(d, H, (int)blockIdx.x - 1, tile, rt);
+        return;
+    }
     const int n = d.n, ld = d.ld;
     cplx<R> *T = d.T;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -361,8 +529,12 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
     const int sub = tid % kQrTpc, seg = tid / kQrTpc;
     const R eps = num<R>::eps;
     int *st = d.state;
+    auto ldT = [&](int64_t idx) { return HELP ? ldcg_c<R>(T + idx) : T[idx]; };
     if (st[2]) {  // already finished: nothing new in the log
-        if (tid == 0) { st[3] = 0; st[7] = 0; d.rstate[0] = 0; }
+        if (tid == 0) {
+            st[3] = 0; st[7] = 0; d.rstate[0] = 0;
+            if (HELP) atomicExch(&d.sync[1], 1);
+        }
         return;
     }
     if (tid == 0) {
@@ -387,9 +559,9 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
         if (tid == 0) s_lo = 0;
         __syncthreads();
         for (int k = 1 + tid; k <= hi; k += nt) {
-            cplx<R> sub_ = T[k + (int64_t)(k - 1) * ld];
+            cplx<R> sub_ = ldT(k + (int64_t)(k - 1) * ld);
             R as = hypot(sub_.x, sub_.y);
-            cplx<R> a = T[k + (int64_t)k * ld], b = T[(k - 1) + (int64_t)(k - 1) * ld];
+            cplx<R> a = ldT(k + (int64_t)k * ld), b = ldT((k - 1) + (int64_t)(k - 1) * ld);
             if (as == R(0) || as <= eps * (hypot(a.x, a.y) + hypot(b.x, b.y))) atomicMax(&s_lo, k);
         }
         __syncthreads();
@@ -420,13 +592,13 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
                 if (it > kItMax) s_status = 3;
                 if (it % 10 == 0) {
                     nb = 1;
-                    cplx<R> sb = T[hi + (int64_t)(hi - 1) * ld];
-                    cplx<R> mu = T[hi + (int64_t)hi * ld];
+                    cplx<R> sb = ldT(hi + (int64_t)(hi - 1) * ld);
+                    cplx<R> mu = ldT(hi + (int64_t)hi * ld);
                     mu.x += R(0.75) * hypot(sb.x, sb.y);
                     s_mu[0] = mu;
                 } else if (nb == 1) {
-                    s_mu[0] = wilkinson(T[(hi - 1) + (int64_t)(hi - 1) * ld], T[(hi - 1) + (int64_t)hi * ld],
-                                        T[hi + (int64_t)(hi - 1) * ld], T[hi + (int64_t)hi * ld]);
+                    s_mu[0] = wilkinson(ldT((hi - 1) + (int64_t)(hi - 1) * ld), ldT((hi - 1) + (int64_t)hi * ld),
+                                        ldT(hi + (int64_t)(hi - 1) * ld), ldT(hi + (int64_t)hi * ld));
                 } else {
                     s_small = 1;
                 }
@@ -445,7 +617,7 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
                 const int b0 = hi - nb + 1;
                 for (int e = lane; e < nb * nb; e += 32) {
                     const int i = e % nb, j = e / nb;
-                    s_m[i + j * (NB + 1)] = (i <= j + 1) ? T[(b0 + i) + (int64_t)(b0 + j) * ld] : cplx<R>{0, 0};
+                    s_m[i + j * (NB + 1)] = (i <= j + 1) ? ldT((b0 + i) + (int64_t)(b0 + j) * ld) : cplx<R>{0, 0};
                 }
                 __syncwarp();
                 warp_small_eigvals<R, NB + 1>(s_m, nb, s_mu);
@@ -469,7 +641,7 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
             }
             for (int e = tid; e < bw * bw; e += nt) {
                 const int a = e % bw, b = e / bw;
-                cp_async_elem<R>(&blk[a + b * BLD], &T[(r0 + a) + (int64_t)(r0 + b) * ld]);
+                load_t<R, HELP>(&blk[a + b * BLD], &T[(r0 + a) + (int64_t)(r0 + b) * ld]);
             }
             for (int e = tid; e < W * NB; e += nt) rt[e] = RotLog<R>{R(1), R(0), R(0), R(0)};
             cp_async_wait_all();
@@ -556,12 +728,35 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
                 for (int e = tid; e < W * NB; e += nt) dst[e] = rt[e];
             }
             const int off = kbase - kmin;
-            // (a') columns r1+1 .. hi, rows kmin .. kmin+rr-1: left rotations
-            for (int c0 = r1 + 1; c0 <= hi; c0 += kQrCh) {
-                const int cn = min(kQrCh, hi - c0 + 1);
+            // last column of the next window's block (hi after the last window)
+            const int rnext = (t1 < nsteps) ? min(hi, min(hi - 1, lo + min(t1 + W, nsteps) - 1) + 2) : hi;
+            if (HELP) {
+                // post the window to the helpers, wait until they have finished
+                // the previous one, then update the next block's new columns
+                // (r1, rnext] here; the helpers take the rest
+                if (tid == 0) {
+                    WinRec wr;
+                    wr.start = s_nlog; wr.kbase = kbase; wr.nsteps = ns; wr.kmin = kmin; wr.rr = rr;
+                    wr.lo = lo; wr.hi = hi; wr.t0 = t0; wr.nb = nb; wr.r0 = r0; wr.rnext = rnext; wr.pad = 0;
+                    wr.uoff = s_uoff;
+                    d.win[s_nwin] = wr;
+                }
+                __threadfence();
+                __syncthreads();
+                if (tid == 0) atomicExch(&d.sync[0], s_nwin + 1);
+                if (!wait_helpers(d, H, s_nwin)) {
+                    if (tid == 0) s_status = 6;
+                    __syncthreads();
+                    break;
+                }
+            }
+            // (a') columns r1+1 .. hi (cooperative: .. rnext), rows kmin .. kmin+rr-1: left rotations
+            const int aend = HELP ? rnext : hi;
+            for (int c0 = r1 + 1; c0 <= aend; c0 += kQrCh) {
+                const int cn = min(kQrCh, aend - c0 + 1);
                 for (int e = tid; e < rr * cn; e += nt) {
                     const int v = e % rr, j = e / rr;
-                    cp_async_elem<R>(&tile[v + j * RLD], &T[(kmin + v) + (int64_t)(c0 + j) * ld]);
+                    load_t<R, HELP>(&tile[v + j * RLD], &T[(kmin + v) + (int64_t)(c0 + j) * ld]);
                 }
                 cp_async_wait_all();
                 __syncthreads();
@@ -575,11 +770,12 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
                 __syncthreads();
             }
             // (b') rows lo .. r0-1, columns kmin .. kmin+rr-1: right rotations
-            for (int i0 = lo; i0 < r0; i0 += kQrCh) {
+            // (the helpers' part in the cooperative chase)
+            for (int i0 = lo; i0 < (HELP ? lo : r0); i0 += kQrCh) {
                 const int rn = min(kQrCh, r0 - i0);
                 for (int e = tid; e < rn * rr; e += nt) {
                     const int a = e % rn, v = e / rn;
-                    cp_async_elem<R>(&tile[a + v * CLD], &T[(i0 + a) + (int64_t)(kmin + v) * ld]);
+                    load_t<R, HELP>(&tile[a + v * CLD], &T[(i0 + a) + (int64_t)(kmin + v) * ld]);
                 }
                 cp_async_wait_all();
                 __syncthreads();
@@ -593,25 +789,28 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
                 __syncthreads();
             }
             if (tid == 0) {
-                WinRec wr;
-                wr.start = s_nlog;
-                wr.kbase = kbase;
-                wr.nsteps = ns;
-                wr.kmin = kmin;
-                wr.rr = rr;
-                wr.lo = lo;
-                wr.hi = hi;
-                wr.pad = 0;
-                wr.uoff = s_uoff;
-                d.win[s_nwin] = wr;
+                if (!HELP) {
+                    WinRec wr;
+                    wr.start = s_nlog; wr.kbase = kbase; wr.nsteps = ns; wr.kmin = kmin; wr.rr = rr;
+                    wr.lo = lo; wr.hi = hi; wr.t0 = t0; wr.nb = nb; wr.r0 = r0; wr.rnext = rnext; wr.pad = 0;
+                    wr.uoff = s_uoff;
+                    d.win[s_nwin] = wr;
+                }
                 s_nwin += 1;
                 s_uoff += (long long)rr * rr;
                 s_nlog += W * NB;
                 if (s_bad) s_status = 7;
             }
+            if (HELP) __threadfence();  // the block and head columns, before the next block is read back
             __syncthreads();
         }
         __syncthreads();
+        // cooperative chase: the whole sweep's out-of-window updates are done
+        // before the next sweep reads T
+        if (HELP && !s_status && !wait_helpers(d, H, s_nwin)) {
+            if (tid == 0) s_status = 6;
+            __syncthreads();
+        }
         if (s_status) break;
     }
     __syncthreads();
@@ -628,6 +827,10 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs)
         st[8] = (int)(s_work & 0x7fffffff);
         st[9] = (int)(s_work >> 31);
         if (s_status) *d.status = s_status;
+        if (HELP) {
+            __threadfence();
+            atomicExch(&d.sync[1], 1);  // helpers leave once every posted window is done
+        }
         if (d.counters) {
             d.counters[0] = s_sweeps;
             d.counters[1] = st[5];
@@ -903,7 +1106,8 @@ int qr_rows_per_cta(int nmax)
 template <class R>
 cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, int *h_state,
                              const int *d_state_all, cudaStream_t s, float *ms_chase,
-                             const SchurDesc<R> *d_desc_alt, cudaStream_t side, const cudaEvent_t *qev)
+                             const SchurDesc<R> *d_desc_alt, cudaStream_t side, const cudaEvent_t *qev,
+                             int *d_sync)
 {
     constexpr int RRMAX = QrDims<R>::RR;
     const int rpc = qr_rows_per_cta<R>(nmax);
@@ -912,7 +1116,11 @@ cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, in
     const size_t rows_bytes = (size_t)rpc * nmax * sizeof(cplx<R>) + ubytes + mbytes;
     const size_t cols_bytes = (size_t)rpc * (nmax + 1) * sizeof(cplx<R>) + ubytes + mbytes;
     cudaError_t err;
-    if ((err = allow_max_smem((const void *)qr_chase_kernel<R>))) return err;
+    if ((err = allow_max_smem((const void *)qr_chase_kernel<R, false>))) return err;
+    if ((err = allow_max_smem((const void *)qr_chase_kernel<R, true>))) return err;
+    // cooperative chase (one chase CTA + H helper CTAs) for one large matrix
+    const bool coop = d_sync != nullptr && batch == 1 && nmax >= kQrCoopMinN;
+    int H = nmax >= 1024 ? 16 : 8;
     if ((err = allow_max_smem((const void *)qr_build_u_kernel<R>))) return err;
     if ((err = allow_max_smem((const void *)qr_apply_rows_kernel<R>))) return err;
     if ((err = allow_max_smem((const void *)qr_apply_cols_kernel<R>))) return err;
@@ -932,7 +1140,16 @@ cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, in
         // this buffer set's deferred passes from two rounds ago must be done
         if (used[par] && (err = cudaStreamWaitEvent(s, qev[2 + par], 0))) break;
         if (ms_chase && (err = cudaEventRecord(ev[0], s))) break;
-        qr_chase_kernel<R><<<batch, kQrThreads, QrDims<R>::chase_smem, s>>>(dd); count_launch();
+        if (coop) {
+            if ((err = cudaMemsetAsync(d_sync, 0, (4 + H) * sizeof(int), s))) break;
+            const SchurDesc<R> *arg0 = dd;
+            void *args[2] = {(void *)&arg0, (void *)&H};
+            if ((err = cudaLaunchCooperativeKernel((const void *)qr_chase_kernel<R, true>, dim3(1 + H), dim3(kQrThreads),
+                                                   args, QrDims<R>::chase_smem, s))) break;
+        } else {
+            qr_chase_kernel<R, false><<<batch, kQrThreads, QrDims<R>::chase_smem, s>>>(dd, 0);
+        }
+        count_launch();
         if (ms_chase && (err = cudaEventRecord(ev[1], s))) break;
         if ((err = cudaMemcpyAsync(h_state, d_state_all, sizeof(int) * kQrStateInts * batch, cudaMemcpyDeviceToHost, s))) break;
         if ((err = cudaStreamSynchronize(s))) break;
@@ -977,8 +1194,8 @@ cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, in
 }
 
 template cudaError_t launch_qr_sweeps<float>(const SchurDesc<float> *, int, int, int *, const int *, cudaStream_t, float *,
-                                             const SchurDesc<float> *, cudaStream_t, const cudaEvent_t *);
+                                             const SchurDesc<float> *, cudaStream_t, const cudaEvent_t *, int *);
 template cudaError_t launch_qr_sweeps<double>(const SchurDesc<double> *, int, int, int *, const int *, cudaStream_t, float *,
-                                              const SchurDesc<double> *, cudaStream_t, const cudaEvent_t *);
+                                              const SchurDesc<double> *, cudaStream_t, const cudaEvent_t *, int *);
 
 }  // namespace sqm
