@@ -260,7 +260,7 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
                     Carve::round(2 * sizeof(SchurDesc<R>)) +
                     2 * (Carve::round(qr_log_capacity(n) * sizeof(RotLog<R>)) +
                          Carve::round(qr_win_capacity(n) * sizeof(WinRec)) + Carve::round(qr_u_capacity(n) * cb)) +
-                    Carve::round(kQrStateInts * sizeof(int)) + Carve::round(4 * sizeof(int)) + Carve::round(32 * sizeof(int)) + 4096;
+                    Carve::round(kQrStateInts * sizeof(int)) + Carve::round(4 * sizeof(int)) + Carve::round(32 * sizeof(int)) + Carve::round(qr_win_capacity(n) * sizeof(int)) + 4096;
     if (ensure(h->fact, fbytes, h) || ensure(h->ws, wbytes, h)) return 7;
     Carve cf(h->fact.p);
     cplx<R> *Q = cf.take<cplx<R>>(nn);
@@ -289,6 +289,7 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     int *qstate = cw.take<int>(kQrStateInts);
     int *rstate = cw.take<int>(4);
     int *qsync = cw.take<int>(32);
+    int *qpost = cw.take<int>(qr_win_capacity(n));
     h->fact_n = -1;
 
     SQM_CU(cudaMemsetAsync(sc.e, 0, 16 * sizeof(int), s));
@@ -317,6 +318,7 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
         hd2[q].ubuf = ubuf[q];
         hd2[q].rstate = rstate + 2 * q;
         hd2[q].sync = qsync;
+        hd2[q].postlist = qpost;
     }
     memcpy(h->staging.p, hd2, sizeof(hd2));
     SQM_CU(cudaMemcpyAsync(ddesc, h->staging.p, sizeof(hd2), cudaMemcpyHostToDevice, s));

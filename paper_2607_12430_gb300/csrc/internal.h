@@ -54,6 +54,7 @@ struct SchurDesc {
     int *state;      // scratch: kQrStateInts ints of QR iteration state
     int *rstate;     // scratch: [0] windows in this descriptor's buffers after its last chase round
     int *sync;       // scratch (cooperative chase): [0] windows posted, [1] quit, [2] failed, [4 + h] windows done by helper h
+    int *postlist;   // scratch (cooperative chase): window record index of each posted window (win_cap entries)
     int log_cap;
     int win_cap;
     cplx<R> *T;      // in: A_s, out: upper triangular T (n x n)

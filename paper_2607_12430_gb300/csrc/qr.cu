@@ -43,6 +43,9 @@ namespace sqm {
 
 static constexpr int kItMax = 60;
 static constexpr int kQrCoopMinN = 256;  // smallest n for the cooperative chase
+static constexpr int kQrPostMin = 64;    // fewer out-of-window rows + columns: the chase CTA does them
+static constexpr int kQrTiny = 24;       // active blocks up to this size: one warp, dense U
+static constexpr int kQrTinyLd = 33;     // leading dimension of its shared-memory block and U
 static constexpr int kQrThreads = 512;           // chase CTA
 static constexpr int kQrTpc = 4;                 // threads per row/column segment in the updates
 static constexpr int kQrCh = kQrThreads / kQrTpc;  // segments per update chunk
@@ -229,6 +232,96 @@ __device__ void warp_small_eigvals(cplx<R> *M, int nb, cplx<R> *out)
     }
     if (hi == 0 && lane == 0) out[0] = M[0];
     __syncwarp();
+}
+
+// Complete Schur form of a small active block (m <= 32), one warp: single-
+// shift QR with Wilkinson shifts (an exceptional shift every 10 sweeps
+// without deflation) on the m x m block M in shared memory (leading
+// dimension LDM), every rotation applied to the whole block (rows k, k+1
+// from column k-1 on; columns k, k+1 down to row k+2) and accumulated into
+// U (U <- U G^H, U = I on entry), until every subdiagonal entry is
+// negligible (set to zero).  Then the rest of T needs only x <- x U (rows
+// above the block, Schur vectors) and y <- U^H y (columns right of it).
+// Returns false if some eigenvalue took more than kItMax sweeps.
+template <class R, int LDM>
+__device__ bool warp_tiny_schur(cplx<R> *M, cplx<R> *U, int m, int *sweeps, int *rots)
+{
+    const int lane = threadIdx.x & 31;
+    const R eps = num<R>::eps;
+    int hi = m - 1, it = 0, nsw = 0, nrot = 0;
+    bool ok = true;
+    while (hi > 0) {
+        bool small = false;
+        if (lane >= 1 && lane <= hi) {
+            const cplx<R> sub = M[lane + (lane - 1) * LDM];
+            const R as = hypot(sub.x, sub.y);
+            const cplx<R> a = M[lane + lane * LDM], b = M[(lane - 1) + (lane - 1) * LDM];
+            small = as == R(0) || as <= eps * (hypot(a.x, a.y) + hypot(b.x, b.y));
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, small);
+        const int lo = bal ? 31 - __clz(bal) : 0;
+        __syncwarp();
+        if (lo == hi) {
+            if (lane == 0) M[hi + (hi - 1) * LDM] = cplx<R>{0, 0};
+            --hi;
+            it = 0;
+            __syncwarp();
+            continue;
+        }
+        if (lo > 0 && lane == 0) M[lo + (lo - 1) * LDM] = cplx<R>{0, 0};
+        if (++it > kItMax) { ok = false; break; }
+        ++nsw;
+        cplx<R> mu;
+        if (it % 10 == 0) {
+            const cplx<R> sb = M[hi + (hi - 1) * LDM];
+            mu = M[hi + hi * LDM];
+            mu.x += R(0.75) * hypot(sb.x, sb.y);
+        } else {
+            mu = wilkinson(M[(hi - 1) + (hi - 1) * LDM], M[(hi - 1) + hi * LDM], M[hi + (hi - 1) * LDM],
+                           M[hi + hi * LDM]);
+        }
+        __syncwarp();
+        for (int k = lo; k < hi; ++k) {
+            const int js = (k == lo) ? k : k - 1;
+            const bool lj = lane >= js && lane < m;
+            cplx<R> p{0, 0}, q{0, 0};
+            if (lj) {
+                p = M[k + lane * LDM];
+                q = M[(k + 1) + lane * LDM];
+            }
+            cplx<R> x{__shfl_sync(0xffffffffu, p.x, js), __shfl_sync(0xffffffffu, p.y, js)};
+            const cplx<R> y{__shfl_sync(0xffffffffu, q.x, js), __shfl_sync(0xffffffffu, q.y, js)};
+            if (k == lo) x = x - mu;
+            R c;
+            cplx<R> s, r;
+            givens_fast(x, y, c, s, r);
+            if (lj) {
+                cplx<R> np = c * p + s * q, nq = c * q - conj(s) * p;
+                if (lane == js && k > lo) {
+                    np = r;
+                    nq = cplx<R>{0, 0};
+                }
+                M[k + lane * LDM] = np;
+                M[(k + 1) + lane * LDM] = nq;
+            }
+            __syncwarp();
+            if (lane <= min(k + 2, m - 1)) {
+                const cplx<R> pp = M[lane + k * LDM], qq = M[lane + (k + 1) * LDM];
+                M[lane + k * LDM] = c * pp + conj(s) * qq;
+                M[lane + (k + 1) * LDM] = c * qq - s * pp;
+            }
+            if (lane < m) {
+                const cplx<R> pp = U[lane + k * LDM], qq = U[lane + (k + 1) * LDM];
+                U[lane + k * LDM] = c * pp + conj(s) * qq;
+                U[lane + (k + 1) * LDM] = c * qq - s * pp;
+            }
+            __syncwarp();
+            ++nrot;
+        }
+    }
+    *sweeps = nsw;
+    *rots = nrot;
+    return ok;
 }
 
 // Barrier among the NTH threads of the chase warps.
@@ -438,7 +531,7 @@ __device__ void qr_helper(const SchurDesc<R> &d, int H, int h, cplx<R> *tile, Ro
             return;
         }
         __threadfence();
-        if (tid < 12) s_win[tid] = __ldcg(reinterpret_cast<const int *>(&d.win[w]) + tid);
+        if (tid < 12) s_win[tid] = __ldcg(reinterpret_cast<const int *>(&d.win[__ldcg(d.postlist + w)]) + tid);
         __syncthreads();
         const int start = s_win[0], kbase = s_win[1], ns = s_win[2], kmin = s_win[3], rr = s_win[4];
         const int lo = s_win[5], hi = s_win[6], t0w = s_win[7], nb = s_win[8], r0 = s_win[9], rnext = s_win[10];
@@ -514,7 +607,8 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
     RotLog<R> *rt = reinterpret_cast<RotLog<R> *>(tile + D::TILE);  // rt[q NB + g]
     __shared__ cplx<R> s_mu[NB];
     __shared__ cplx<R> s_m[NB * (NB + 1)];
-    __shared__ int s_lo, s_hi, s_iter, s_status, s_done, s_nb, s_sweeps, s_stop, s_nwin, s_nlog, s_small, s_bad;
+    __shared__ int s_lo, s_hi, s_iter, s_status, s_done, s_nb, s_sweeps, s_stop, s_nwin, s_nlog, s_small, s_bad, s_npost,
+        s_tiny;
     __shared__ long long s_uoff, s_rots, s_work;
 
     const SchurDesc<R> d = descs[HELP ? 0 : blockIdx.x];
@@ -550,6 +644,7 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
         s_work = (long long)st[8] + ((long long)st[9] << 31);
         s_stop = 0;
         s_bad = 0;
+        s_npost = 0;
     }
     __syncthreads();
 
@@ -578,7 +673,8 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
         if (tid == 0) {
             const int m = hi - lo + 1;
             int nb = min(NB, max(1, (m - 2) / 4));
-            const long long nwin_sweep = ((hi - lo) + 3 * (nb - 1) + W - 1) / W;
+            s_tiny = m <= kQrTiny;
+            const long long nwin_sweep = s_tiny ? 1 : ((hi - lo) + 3 * (nb - 1) + W - 1) / W;
             const bool fits = s_nlog + nwin_sweep * (W * NB) <= d.log_cap && s_nwin + nwin_sweep <= d.win_cap &&
                               s_uoff + nwin_sweep * (long long)(D::RR * D::RR) <= d.u_cap;
             s_small = 0;
@@ -587,6 +683,8 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
                 if (s_nlog == 0 && s_nwin == 0 && s_uoff == 0) s_status = 7;  // can never fit
             } else {
                 if (lo > 0) T[lo + (int64_t)(lo - 1) * ld] = cplx<R>{0, 0};
+            }
+            if (fits && !s_tiny) {
                 int it = ++s_iter;
                 ++s_sweeps;
                 if (it > kItMax) s_status = 3;
@@ -611,6 +709,50 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
         }
         __syncthreads();
         if (s_stop || s_status) break;
+        if (s_tiny) {
+            // a small active block: its whole Schur form by one warp, recorded
+            // as one window with a dense U
+            const int m = hi - lo + 1;
+            cplx<R> *Mb = blk, *Ub = tile;  // ld kQrTinyLd
+            for (int e = tid; e < m * m; e += nt) {
+                const int a = e % m, b = e / m;
+                Mb[a + b * kQrTinyLd] = ldT((lo + a) + (int64_t)(lo + b) * ld);
+                Ub[a + b * kQrTinyLd] = cplx<R>{(R)(a == b), R(0)};
+            }
+            __syncthreads();
+            if (warp == 0) {
+                int nsw = 0, nrot = 0;
+                const bool ok = warp_tiny_schur<R, kQrTinyLd>(Mb, Ub, m, &nsw, &nrot);
+                if (lane == 0) {
+                    if (!ok) s_status = 3;
+                    s_sweeps += nsw;
+                    s_rots += nrot;
+                    s_work += (long long)nrot * m;
+                }
+            }
+            __syncthreads();
+            cplx<R> *U = d.ubuf + s_uoff;
+            for (int e = tid; e < m * m; e += nt) {
+                const int a = e % m, b = e / m;
+                T[(lo + a) + (int64_t)(lo + b) * ld] = Mb[a + b * kQrTinyLd];
+                U[a + b * m] = Ub[a + b * kQrTinyLd];
+            }
+            if (tid == 0) {
+                WinRec wr;
+                wr.start = s_nlog; wr.kbase = lo; wr.nsteps = -1; wr.kmin = lo; wr.rr = m;
+                wr.lo = lo; wr.hi = hi; wr.t0 = 0; wr.nb = 0; wr.r0 = lo; wr.rnext = hi; wr.pad = 0;
+                wr.uoff = s_uoff;
+                d.win[s_nwin] = wr;
+                s_nwin += 1;
+                s_uoff += (long long)m * m;
+                s_hi = lo - 1;
+                s_iter = 0;
+            }
+            if (HELP) __threadfence();
+            __syncthreads();
+            if (s_status) break;
+            continue;
+        }
         const int nb = s_nb;
         if (s_small) {  // shifts: eigenvalues of the trailing nb x nb block
             if (warp == 0) {
@@ -730,28 +872,34 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
             const int off = kbase - kmin;
             // last column of the next window's block (hi after the last window)
             const int rnext = (t1 < nsteps) ? min(hi, min(hi - 1, lo + min(t1 + W, nsteps) - 1) + 2) : hi;
+            // cooperative chase: windows with more than kQrPostMin rows and
+            // columns outside the next block go to the helpers (the chase CTA
+            // then updates only the next block's new columns (r1, rnext]);
+            // smaller ones are done here after the helpers have finished every
+            // posted window, so each entry still sees the windows in order
+            const bool post = HELP && (hi - rnext) + (r0 - lo) > kQrPostMin;
             if (HELP) {
-                // post the window to the helpers, wait until they have finished
-                // the previous one, then update the next block's new columns
-                // (r1, rnext] here; the helpers take the rest
-                if (tid == 0) {
+                if (post && tid == 0) {
                     WinRec wr;
                     wr.start = s_nlog; wr.kbase = kbase; wr.nsteps = ns; wr.kmin = kmin; wr.rr = rr;
                     wr.lo = lo; wr.hi = hi; wr.t0 = t0; wr.nb = nb; wr.r0 = r0; wr.rnext = rnext; wr.pad = 0;
                     wr.uoff = s_uoff;
                     d.win[s_nwin] = wr;
+                    d.postlist[s_npost] = s_nwin;
                 }
                 __threadfence();
                 __syncthreads();
-                if (tid == 0) atomicExch(&d.sync[0], s_nwin + 1);
-                if (!wait_helpers(d, H, s_nwin)) {
+                if (post && tid == 0) atomicExch(&d.sync[0], s_npost + 1);
+                // helpers done with every window posted before this one (all of
+                // them if this one is done here)
+                if (!wait_helpers(d, H, s_npost)) {
                     if (tid == 0) s_status = 6;
                     __syncthreads();
                     break;
                 }
             }
-            // (a') columns r1+1 .. hi (cooperative: .. rnext), rows kmin .. kmin+rr-1: left rotations
-            const int aend = HELP ? rnext : hi;
+            // (a') columns r1+1 .. hi (cooperative, posted: .. rnext), rows kmin .. kmin+rr-1: left rotations
+            const int aend = post ? rnext : hi;
             for (int c0 = r1 + 1; c0 <= aend; c0 += kQrCh) {
                 const int cn = min(kQrCh, aend - c0 + 1);
                 for (int e = tid; e < rr * cn; e += nt) {
@@ -770,8 +918,8 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
                 __syncthreads();
             }
             // (b') rows lo .. r0-1, columns kmin .. kmin+rr-1: right rotations
-            // (the helpers' part in the cooperative chase)
-            for (int i0 = lo; i0 < (HELP ? lo : r0); i0 += kQrCh) {
+            // (the helpers' part for a posted window)
+            for (int i0 = lo; i0 < (post ? lo : r0); i0 += kQrCh) {
                 const int rn = min(kQrCh, r0 - i0);
                 for (int e = tid; e < rn * rr; e += nt) {
                     const int a = e % rn, v = e / rn;
@@ -789,7 +937,8 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
                 __syncthreads();
             }
             if (tid == 0) {
-                if (!HELP) {
+                if (post) ++s_npost;
+                if (!post) {
                     WinRec wr;
                     wr.start = s_nlog; wr.kbase = kbase; wr.nsteps = ns; wr.kmin = kmin; wr.rr = rr;
                     wr.lo = lo; wr.hi = hi; wr.t0 = t0; wr.nb = nb; wr.r0 = r0; wr.rnext = rnext; wr.pad = 0;
@@ -807,7 +956,7 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
         __syncthreads();
         // cooperative chase: the whole sweep's out-of-window updates are done
         // before the next sweep reads T
-        if (HELP && !s_status && !wait_helpers(d, H, s_nwin)) {
+        if (HELP && !s_status && !wait_helpers(d, H, s_npost)) {
             if (tid == 0) s_status = 6;
             __syncthreads();
         }
@@ -858,6 +1007,7 @@ __global__ void __launch_bounds__(128) qr_build_u_kernel(const SchurDesc<R> *__r
     const int nwin = d.rstate[0];
     if ((int)blockIdx.x >= nwin) return;
     const WinRec w = d.win[blockIdx.x];
+    if (w.nsteps < 0) return;  // dense window: U written by the chase
     const int rr = w.rr, r = threadIdx.x;
     if (rr > D::RR || rr < 2) {
         if (r == 0) atomicExch(d.status, 7);

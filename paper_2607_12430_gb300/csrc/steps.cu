@@ -84,6 +84,7 @@ static int schur_step(sqrtm_handle_t h, cplx<R> *T, cplx<R> *Q, int64_t n)
     SchurDesc<R> hd;
     hd.rstate = rstate;
     hd.sync = nullptr;
+    hd.postlist = nullptr;
     hd.T = T; hd.Q = Q; hd.v = v; hd.beta = beta; hd.status = ss.iscal + 1; hd.n = (int)n; hd.ld = (int)n;
     hd.counters = nullptr;
     hd.log = rlog; hd.state = qstate; hd.log_cap = (int)std::min<int64_t>(qr_log_capacity(n), INT32_MAX);
