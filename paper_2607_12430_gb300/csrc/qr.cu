@@ -105,12 +105,22 @@ __device__ cplx<R> wilkinson(cplx<R> a, cplx<R> b, cplx<R> c, cplx<R> d)
     return d;
 }
 
-// The same rotation for FP32 from |x|^2 and |y|^2 with two square roots and
-// two divisions instead of three hypot calls and six divisions (the chase's
-// critical path).  All four are correctly rounded, so c^2 + |s|^2 - 1 has no
-// systematic part (approximate reciprocal square roots do, and the bias
-// accumulates over the thousands of rotations applied to each Schur
-// vector).  Tiny or huge arguments take the scaled path.
+// The same rotation for FP32 from |x|^2 and |y|^2 and two reciprocal square
+// roots, each refined by one Newton step written with fused multiply-adds:
+// e = 1 - v y0^2 (one rounding), y1 = y0 + (y0 / 2) e (one rounding).  The
+// refinement squares away the systematic part of the hardware reciprocal
+// square root's error, which would otherwise accumulate over the thousands
+// of rotations applied to each Schur vector (an unrefined form measured ten
+// times worse orthogonality); the remaining error is rounding of either
+// sign, as with correctly rounded square roots and divisions, at a fraction
+// of their latency on the chase's critical path.  Tiny or huge arguments
+// take the scaled path.
+__device__ __forceinline__ float rsqrt_refined(float v)
+{
+    const float y0 = rsqrtf(v);
+    const float e = fmaf(-(v * y0), y0, 1.0f);
+    return fmaf(0.5f * y0, e, y0);
+}
 template <class R>
 __device__ __forceinline__ void givens_fast(cplx<R> x, cplx<R> y, R &c, cplx<R> &s, cplx<R> &r)
 {
@@ -126,11 +136,11 @@ __device__ __forceinline__ void givens_fast<float>(cplx<float> x, cplx<float> y,
         givens(x, y, c, s, r);
         return;
     }
-    const float ax = sqrtf(ax2), nrm = sqrtf(nrm2);
-    c = ax / nrm;
-    const float f = 1.0f / (ax * nrm);
-    s = cplx<float>{(x.x * y.x + x.y * y.y) * f, (x.y * y.x - x.x * y.y) * f};  // x conj(y) / (|x| ||(x, y)||)
-    const float gsc = nrm / ax;
+    const float inv = rsqrt_refined(nrm2), invx = rsqrt_refined(ax2);
+    const float f = invx * inv;  // 1 / (|x| ||(x, y)||)
+    c = ax2 * f;
+    s = cplx<float>{(x.x * y.x + x.y * y.y) * f, (x.y * y.x - x.x * y.y) * f};  // x conj(y) f
+    const float gsc = nrm2 * f;                                                // ||(x, y)|| / |x|
     r = cplx<float>{x.x * gsc, x.y * gsc};
 }
 
