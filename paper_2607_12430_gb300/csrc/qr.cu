@@ -371,17 +371,19 @@ __host__ __device__ __forceinline__ int rt_slot(int g)
 // step orders them.  All threads of the warp call this (on = false: no
 // segment).  Returns false if a bulge's index range leaves [0, rr) (a
 // malformed window: nothing is applied for that bulge).
-template <class R, int NB, int STRIDE, bool LEFT>
+template <class R, int NB, int STRIDE, bool LEFT, int TPC = kQrTpc>
 __device__ __noinline__ bool apply_window(cplx<R> *vec, bool on, const RotLog<R> *rt, int ns, int off, int rr,
                                           int sub, int t0, int span, int nb)
 {
-    constexpr int NG = NB / kQrTpc, L = 3 * NG - 1, W = QrCfg<R>::W;
+    static_assert(NB % TPC == 0 && 32 % TPC == 0, "a segment's threads share a warp");
+    constexpr int NG = NB / TPC, L = 3 * NG - 1 > 1 ? 3 * NG - 1 : 2, W = QrCfg<R>::W;
     const int A0 = off + 3 * (NB - NG * (sub + 1));
-    int qa[NG], len[NG];
+    int qa[NG], len[NG], slot[NG];
     bool ok = true;
 #pragma unroll
     for (int j = 0; j < NG; ++j) {
         const int g = sub * NG + j;
+        slot[j] = rt_slot<NB>(g);  // the table is written in the kQrTpc layout
         const int a0 = max(0, 3 * g - t0), a1 = min(ns - 1, span - 1 + 3 * g - t0);
         qa[j] = a0;
         len[j] = (g < nb && a1 >= a0) ? a1 - a0 + 1 : 0;
@@ -399,7 +401,6 @@ __device__ __noinline__ bool apply_window(cplx<R> *vec, bool on, const RotLog<R>
         const int r = A0 + i;
         ring[i] = (on && r >= 0 && r < rr) ? vec[r * STRIDE] : cplx<R>{0, 0};
     }
-    const RotLog<R> *rs = rt + sub;
 #pragma unroll 32
     for (int q = 0; q < W; ++q) {
         if (q < ns) {
@@ -411,7 +412,7 @@ __device__ __noinline__ bool apply_window(cplx<R> *vec, bool on, const RotLog<R>
 #pragma unroll
                 for (int j = 0; j < NG; ++j) {
                     if ((unsigned)(q - qa[j]) < (unsigned)len[j]) {
-                        const RotLog<R> e = rs[q * NB + j * kQrTpc];
+                        const RotLog<R> e = rt[q * NB + slot[j]];
                         const cplx<R> sv{e.sx, e.sy};
                         cplx<R> &p = ring[(q + 3 * (NG - 1 - j)) % L];
                         cplx<R> &w = ring[(q + 3 * (NG - 1 - j) + 1) % L];
@@ -918,8 +919,16 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
                 }
                 cp_async_wait_all();
                 __syncthreads();
-                if (!apply_window<R, NB, 1, true>(tile + seg * RLD, seg < cn, rt, ns, off, rr, sub, t0, hi - lo, nb))
+                if (post) {
+                    // at most W new columns: up to 16 threads (one bulge each) per column
+                    constexpr int HT = NB < 16 ? NB : 16;
+                    if (!apply_window<R, NB, 1, true, HT>(tile + (tid / HT) * RLD, (tid / HT) < cn, rt, ns, off, rr,
+                                                          tid % HT, t0, hi - lo, nb))
+                        s_bad = 1;
+                } else if (!apply_window<R, NB, 1, true>(tile + seg * RLD, seg < cn, rt, ns, off, rr, sub, t0, hi - lo,
+                                                         nb)) {
                     s_bad = 1;
+                }
                 __syncthreads();
                 for (int e = tid; e < rr * cn; e += nt) {
                     const int v = e % rr, j = e / rr;
