@@ -8,10 +8,10 @@
 //      v.  The reflectors are kept (one column each) for step 4;
 //   2. eigenvalues of the tridiagonal matrix: FP32 multisection (one warp
 //      per eigenvalue, 32 Sturm counts per round) to a bracket of FP32
-//      width, checked and finished by FP64 bisection (one thread per
-//      eigenvalue);
+//      width, checked and finished by FP64 multisection (a few lanes per
+//      eigenvalue, chosen to keep every SM sub-partition busy);
 //   3. eigenvectors of the tridiagonal matrix from twisted factorisations
-//      T - lam I = L D+ L^T = U D- U^T (one thread per eigenvalue, FP64):
+//      T - lam I = L D+ L^T = U D- U^T (two lanes per eigenvalue, FP64):
 //      with r = argmin |D+_r + D-_r - (d_r - lam)|, z_r = 1,
 //      z_i = -(e_i / D+_i) z_{i+1} above r, z_{i+1} = -(e_i / D-_{i+1}) z_i
 //      below r, normalised;
@@ -27,6 +27,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include "handle.h"
 #include "spd_internal.h"
@@ -326,92 +327,177 @@ __global__ void __launch_bounds__(256) multisect_f32_kernel(const float *__restr
     }
 }
 
-// FP64 bisection of eigenvalue j from the FP32 bracket, widened by a few
-// FP32 units of the spectrum's scale; if the FP64 counts at its ends do not
-// enclose j, from the Gershgorin interval instead.  Stops at a bracket of
-// width reltol |lam| + 2u ||T|| (plus the pivot floor).  One thread per
-// eigenvalue, 32-thread blocks so that all SMs take part.
-__global__ void __launch_bounds__(32) bisect_f64_kernel(const double *__restrict__ d, const double *__restrict__ e2,
-                                                        int n, const double *__restrict__ bounds,
-                                                        const double *__restrict__ blo,
-                                                        const double *__restrict__ bhi, double reltol,
-                                                        double *__restrict__ lam)
+// FP64 multisection of eigenvalue j from the FP32 bracket, widened by a
+// few FP32 units of the spectrum's scale; if the FP64 counts at its ends do
+// not enclose j, from the Gershgorin interval instead.  K lanes per
+// eigenvalue (K divides 32): each round they count at the K interior points
+// that cut the bracket into K + 1 equal parts, and the bracket shrinks to the
+// part where the count passes j (K = 1 is bisection).  Stops at a bracket of
+// width reltol |lam| + 2u ||T|| (plus the pivot floor).  A Sturm count is a
+// chain of dependent FP64 divisions; one eigenvalue per lane leaves most SM
+// sub-partitions idle for n of a few thousand, so the launcher trades extra
+// counts for more resident warps.
+template <int K>
+__global__ void __launch_bounds__(128) bisect_f64_kernel(const double *__restrict__ d, const double *__restrict__ e2,
+                                                         int n, const double *__restrict__ bounds,
+                                                         const double *__restrict__ blo,
+                                                         const double *__restrict__ bhi, double reltol,
+                                                         double *__restrict__ lam)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = gt / K, l = gt % K;
+    const int base = (threadIdx.x & 31) & ~(K - 1);  // first lane of this eigenvalue's group
+    const bool valid = j < n;                         // the rest of the last warp still shuffles
     const double gl = bounds[0], gu = bounds[1], pivmin = bounds[2];
     const double widen = 16.0 * 5.9604644775390625e-08 * fmax(fabs(gl), fabs(gu)) + pivmin;
-    double lo = fmax(gl, blo[j] - widen), hi = fmin(gu, bhi[j] + widen);
-    if (!(lo < hi) || sturm_count(d, e2, n, lo, pivmin) > j || sturm_count(d, e2, n, hi, pivmin) <= j) {
+    double lo = gl, hi = gu;
+    if (valid) {
+        lo = fmax(gl, blo[j] - widen);
+        hi = fmin(gu, bhi[j] + widen);
+    }
+    // counts at both ends (two lanes at once where K >= 2)
+    int c0 = 0, c1 = 0;
+    if (valid && (lo < hi)) {
+        if (K == 1) {
+            c0 = sturm_count(d, e2, n, lo, pivmin);
+            c1 = sturm_count(d, e2, n, hi, pivmin);
+        } else if (l < 2) {
+            c0 = sturm_count(d, e2, n, l == 0 ? lo : hi, pivmin);
+        }
+    }
+    if (K > 1) {
+        const int a = __shfl_sync(0xffffffffu, c0, base);
+        c1 = __shfl_sync(0xffffffffu, c0, base + 1);
+        c0 = a;
+    }
+    if (!(lo < hi) || c0 > j || c1 <= j) {
         lo = gl;
         hi = gu;
     }
     const double atol = 2.0 * 1.1102230246251565e-16 * fmax(fabs(gl), fabs(gu)) + pivmin;
+    const double step = 1.0 / (double)(K + 1);
     for (int it = 0; it < 160; ++it) {
-        double mid = 0.5 * (lo + hi);
-        if (mid <= lo || mid >= hi) break;
-        if (hi - lo <= reltol * fmax(fabs(lo), fabs(hi)) + atol) break;
-        if (sturm_count(d, e2, n, mid, pivmin) > j) hi = mid;
-        else lo = mid;
+        const double h = (hi - lo) * step;
+        const double x = lo + h * (double)(l + 1);
+        const double xfirst = lo + h, xlast = lo + h * (double)K;
+        const bool conv = !valid || !(xfirst > lo && xlast < hi) ||
+                          hi - lo <= reltol * fmax(fabs(lo), fabs(hi)) + atol;
+        if (__all_sync(0xffffffffu, conv)) break;
+        const int c = conv ? 0 : sturm_count(d, e2, n, x, pivmin);
+        unsigned above = __ballot_sync(0xffffffffu, c > j);
+        if (!conv) {
+            above = (K == 32) ? above : (above >> base) & ((1u << K) - 1u);
+            const int first = above ? __ffs(above) - 1 : K;  // part (x_{first-1}, x_first]
+            const double nlo = first > 0 ? lo + h * (double)first : lo;
+            const double nhi = first < K ? lo + h * (double)(first + 1) : hi;
+            lo = nlo;
+            hi = nhi;
+        }
     }
-    lam[j] = 0.5 * (lo + hi);
+    if (valid && l == 0) lam[j] = 0.5 * (lo + hi);
 }
 
-// twisted factorisation eigenvectors for eigenvalues [j0, j0 + cnt);
-// Dp, Dm: scratch [i * cnt + (j - j0)] (coalesced across threads);
-// ZT row j (ld n) receives eigenvector j
-__global__ void twisted_kernel(const double *__restrict__ d, const double *__restrict__ e,
-                               const double *__restrict__ e2, int n,
-                               const double *__restrict__ bounds, const double *__restrict__ lam,
-                               int j0, int cnt, double *__restrict__ Dp, double *__restrict__ Dm,
-                               double *__restrict__ ZT)
+// lanes per eigenvalue for bisect_f64_kernel: the K that minimises the
+// counts per bit of bracket per SM sub-partition in use, K / log2(K + 1)
+// counts for each of n eigenvalues spread over min(4 * SMs, n K / 32) warps
+static int bisect_lanes(int n)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= cnt) return;
-    const int j = j0 + t;
-    const double x = lam[j];
-    const double pivmin = bounds[2];
-    // backward: D-_{n-1} = d_{n-1} - x; D-_i = d_i - x - e_i^2 / D-_{i+1}
-    double q = d[n - 1] - x;
-    if (fabs(q) < pivmin) q = -pivmin;
-    Dm[(int64_t)(n - 1) * cnt + t] = q;
-    for (int i = n - 2; i >= 0; --i) {
-        q = (d[i] - x) - e2[i] / q;
-        if (fabs(q) < pivmin) q = -pivmin;
-        Dm[(int64_t)i * cnt + t] = q;
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int best = 1;
+    double best_cost = 1e300;
+    for (int K = 1; K <= 32; K *= 2) {
+        const double warps = std::min<double>(4.0 * sms, std::ceil((double)n * K / 32.0));
+        const double cost = (double)K / std::log2((double)K + 1.0) * (double)n / warps;
+        if (cost < best_cost * 0.999) { best_cost = cost; best = K; }
     }
-    // forward: D+_0 = d_0 - x; D+_i = d_i - x - e_{i-1}^2 / D+_{i-1};
-    // twist index r minimises |gamma_r| = |D+_r + D-_r - (d_r - x)|
-    double p = d[0] - x;
-    if (fabs(p) < pivmin) p = -pivmin;
-    Dp[t] = p;
-    int r = 0;
-    double gbest = fabs(p + Dm[t] - (d[0] - x));
-    for (int i = 1; i < n; ++i) {
-        p = (d[i] - x) - e2[i - 1] / p;
+    return best;
+}
+
+// twisted factorisation eigenvectors for eigenvalues [j0, j0 + cnt), two
+// lanes per eigenvalue: lane 0 of the pair runs the backward recurrence and
+// the part of the vector above the twist, lane 1 the forward recurrence and
+// the part below it (the two chains are independent).
+// Dp, Dm: scratch [i * cnt + (j - j0)]; ZT row j (ld n) receives
+// eigenvector j
+__global__ void __launch_bounds__(32) twisted_kernel(const double *__restrict__ d, const double *__restrict__ e,
+                                                     const double *__restrict__ e2, int n,
+                                                     const double *__restrict__ bounds,
+                                                     const double *__restrict__ lam, int j0, int cnt,
+                                                     double *__restrict__ Dp, double *__restrict__ Dm,
+                                                     double *__restrict__ ZT)
+{
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = gt >> 1, half = gt & 1;
+    const bool valid = t < cnt;  // the rest of the last warp still synchronises
+    const int j = j0 + t;
+    const double x = valid ? lam[j] : 0.0;
+    const double pivmin = bounds[2];
+    if (valid && half == 0) {
+        // backward: D-_{n-1} = d_{n-1} - x; D-_i = d_i - x - e_i^2 / D-_{i+1}
+        double q = d[n - 1] - x;
+        if (fabs(q) < pivmin) q = -pivmin;
+        Dm[(int64_t)(n - 1) * cnt + t] = q;
+        for (int i = n - 2; i >= 0; --i) {
+            q = (d[i] - x) - e2[i] / q;
+            if (fabs(q) < pivmin) q = -pivmin;
+            Dm[(int64_t)i * cnt + t] = q;
+        }
+    } else if (valid) {
+        // forward: D+_0 = d_0 - x; D+_i = d_i - x - e_{i-1}^2 / D+_{i-1}
+        double p = d[0] - x;
         if (fabs(p) < pivmin) p = -pivmin;
-        Dp[(int64_t)i * cnt + t] = p;
-        double g = fabs(p + Dm[(int64_t)i * cnt + t] - (d[i] - x));
-        if (g < gbest) { gbest = g; r = i; }
+        Dp[t] = p;
+        for (int i = 1; i < n; ++i) {
+            p = (d[i] - x) - e2[i - 1] / p;
+            if (fabs(p) < pivmin) p = -pivmin;
+            Dp[(int64_t)i * cnt + t] = p;
+        }
+    }
+    __syncwarp();
+    // twist index r: the first i minimising |gamma_i| = |D+_i + D-_i - (d_i - x)|
+    // (lane 0 scans the first half of the indices, lane 1 the second)
+    const int mid = n / 2;
+    int r = -1;
+    double gbest = 0.0;
+    if (valid) {
+        for (int i = half ? mid : 0; i < (half ? n : mid); ++i) {
+            const double g = fabs(Dp[(int64_t)i * cnt + t] + Dm[(int64_t)i * cnt + t] - (d[i] - x));
+            if (r < 0 || g < gbest) { gbest = g; r = i; }
+        }
+    }
+    {
+        const int ro = __shfl_xor_sync(0xffffffffu, r, 1);
+        const double go = __shfl_xor_sync(0xffffffffu, gbest, 1);
+        // the pair's first minimum: lane 0's indices come first
+        if (half == 0) { if (r < 0 || (ro >= 0 && go < gbest)) r = ro; }
+        else if (ro >= 0 && !(gbest < go)) r = ro;
     }
     // ZT holds Z^T column-major: component i of eigenvector j at ZT[j + i n],
-    // so the threads of a warp (consecutive j) write consecutive addresses
-    ZT[j + (int64_t)r * n] = 1.0;
-    double nrm2 = 1.0;
-    double zi = 1.0;
-    for (int i = r - 1; i >= 0; --i) {
-        zi = -(e[i] / Dp[(int64_t)i * cnt + t]) * zi;
-        ZT[j + (int64_t)i * n] = zi;
-        nrm2 = fma(zi, zi, nrm2);
+    // so the pairs of a warp (consecutive j) write neighbouring addresses
+    double nrm2 = 0.0;
+    if (valid && half == 0) {
+        ZT[j + (int64_t)r * n] = 1.0;
+        nrm2 = 1.0;
+        double zi = 1.0;
+        for (int i = r - 1; i >= 0; --i) {
+            zi = -(e[i] / Dp[(int64_t)i * cnt + t]) * zi;
+            ZT[j + (int64_t)i * n] = zi;
+            nrm2 = fma(zi, zi, nrm2);
+        }
+    } else if (valid) {
+        double zi = 1.0;
+        for (int i = r; i + 1 < n; ++i) {
+            zi = -(e[i] / Dm[(int64_t)(i + 1) * cnt + t]) * zi;
+            ZT[j + (int64_t)(i + 1) * n] = zi;
+            nrm2 = fma(zi, zi, nrm2);
+        }
     }
-    zi = 1.0;
-    for (int i = r; i + 1 < n; ++i) {
-        zi = -(e[i] / Dm[(int64_t)(i + 1) * cnt + t]) * zi;
-        ZT[j + (int64_t)(i + 1) * n] = zi;
-        nrm2 = fma(zi, zi, nrm2);
+    nrm2 += __shfl_xor_sync(0xffffffffu, nrm2, 1);
+    if (valid) {
+        const double inv = 1.0 / sqrt(nrm2);
+        for (int i = half ? r + 1 : 0; i < (half ? n : r + 1); ++i) ZT[j + (int64_t)i * n] *= inv;
     }
-    const double inv = 1.0 / sqrt(nrm2);
-    for (int i = 0; i < n; ++i) ZT[j + (int64_t)i * n] *= inv;
 }
 
 template <class R>
@@ -431,10 +517,23 @@ cudaError_t launch_tridiag_eig(const R *A, int n, int ld, double *lam, double *Z
     // about 1e-10 relative for any gap above 1e-3 |lam|.  The FP64 method
     // takes them to FP64 precision.
     const double reltol = sizeof(R) == sizeof(float) ? 1e-10 : 2.0 * 1.1102230246251565e-16;
-    bisect_f64_kernel<<<(int)cdiv_i(n, 32), 32, 0, s>>>(d, e2, n, bounds, blo, bhi, reltol, lam); count_launch();
+    {
+        const int K = bisect_lanes(n);
+        const int grid = (int)cdiv_i((int64_t)n * K, 128);
+        switch (K) {
+        case 1: bisect_f64_kernel<1><<<grid, 128, 0, s>>>(d, e2, n, bounds, blo, bhi, reltol, lam); break;
+        case 2: bisect_f64_kernel<2><<<grid, 128, 0, s>>>(d, e2, n, bounds, blo, bhi, reltol, lam); break;
+        case 4: bisect_f64_kernel<4><<<grid, 128, 0, s>>>(d, e2, n, bounds, blo, bhi, reltol, lam); break;
+        case 8: bisect_f64_kernel<8><<<grid, 128, 0, s>>>(d, e2, n, bounds, blo, bhi, reltol, lam); break;
+        case 16: bisect_f64_kernel<16><<<grid, 128, 0, s>>>(d, e2, n, bounds, blo, bhi, reltol, lam); break;
+        default: bisect_f64_kernel<32><<<grid, 128, 0, s>>>(d, e2, n, bounds, blo, bhi, reltol, lam); break;
+        }
+        count_launch();
+    }
     for (int j0 = 0; j0 < n; j0 += chunk) {
         int cnt = std::min(chunk, n - j0);
-        twisted_kernel<<<(int)cdiv_i(cnt, 32), 32, 0, s>>>(d, e, e2, n, bounds, lam, j0, cnt, Dp, Dm, ZT); count_launch();
+        twisted_kernel<<<(int)cdiv_i(2 * (int64_t)cnt, 32), 32, 0, s>>>(d, e, e2, n, bounds, lam, j0, cnt, Dp, Dm, ZT);
+        count_launch();
     }
     return cudaGetLastError();
 }
