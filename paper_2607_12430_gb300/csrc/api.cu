@@ -323,7 +323,11 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     memcpy(h->staging.p, hd2, sizeof(hd2));
     SQM_CU(cudaMemcpyAsync(ddesc, h->staging.p, sizeof(hd2), cudaMemcpyHostToDevice, s));
     SQM_CU(cudaStreamSynchronize(s));
-    {
+    if (hess_cluster_size<R>((int)n) > 0) {
+        // A is real: the cluster-resident real reduction (W and Rt are free
+        // until the Schur form is done)
+        SQM_CU(launch_hessenberg_cluster<R>(T, Q, (int)n, (int)n, (R *)W, (R *)Rt, s));
+    } else {
         struct Ctx { SchurDesc<R> *d; int n; } ctx{ddesc, (int)n};
         auto enq = [](void *p, cudaStream_t st) -> cudaError_t {
             Ctx *c = (Ctx *)p;

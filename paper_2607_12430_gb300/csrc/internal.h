@@ -82,6 +82,15 @@ cudaError_t launch_cast_scaled_real(const double *A, int64_t n, int64_t lda, con
 template <class R>
 cudaError_t launch_hessenberg(const SchurDesc<R> *d_desc, int batch, int nmax,
                               int ctas_per_matrix, cudaStream_t s);
+// Hessenberg reduction of a REAL matrix (T holds it with zero imaginary
+// parts) and Q, both written as complex n x n (ld) matrices, in one launch
+// of a thread-block cluster.  V: n x n scratch of R (ld n), betas: n of R.
+// hess_cluster_size returns the cluster size used for n, 0 if n is too large
+// for it (then launch_hessenberg_cluster returns cudaErrorNotSupported).
+template <class R>
+int hess_cluster_size(int n);
+template <class R>
+cudaError_t launch_hessenberg_cluster(cplx<R> *T, cplx<R> *Q, int n, int ld, R *V, R *betas, cudaStream_t s);
 // d_state_all: the kQrStateInts-int state blocks of all matrices, contiguous
 // (descs[b].state == d_state_all + kQrStateInts b); h_state: pinned host
 // buffer of kQrStateInts * batch ints.  ms_chase (may be null) receives the

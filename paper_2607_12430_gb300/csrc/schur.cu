@@ -9,7 +9,16 @@
 // split over 8 column segments).  Every CTA of hess_left recomputes the
 // reflector from column k, which no CTA writes during that launch.
 //
+// Real input (every matrix the library factors) of moderate size instead
+// takes hess_cluster_kernel: the whole reduction and the accumulation of Q
+// in one launch of a thread-block cluster that keeps the matrix in its
+// shared memory.
+//
 // The QR sweeps that follow the reduction are in qr.cu.
+#include <cooperative_groups.h>
+
+#include <atomic>
+
 #include "internal.h"
 
 namespace sqm {
@@ -156,6 +165,242 @@ hess_right_kernel(const SchurDesc<R> *__restrict__ descs, int k)
         }
     }
 }
+
+// ---------------------------------------------------------------------------
+// Real Householder Hessenberg reduction held in the shared memory of one
+// thread-block cluster of CL <= 8 CTAs; CTA c keeps the columns j = c (mod
+// CL) (the active columns stay spread evenly as k grows).  For column k the
+// owning CTA forms P_k = I - beta v v^T from x = H(k+1:n, k) with
+// v = x + sign(x_0) ||x|| e_1, beta = 2 / ||v||^2 (beta = 0 when the tail of
+// x is zero) and stores v in column k of V.  P_k H changes each column on
+// its own, so every CTA applies it to its columns; H P_k needs
+// u = H(:, k+1:n) v, whose per-CTA parts are summed through distributed
+// shared memory.  Two cluster barriers per column.  Then Q = P_0 P_1 ...
+// P_{n-3} by backward accumulation (Q <- P_k Q for k = n-3 .. 0, which
+// changes only columns > k), again column by column in the same shared
+// memory.  H and Q are written back as complex matrices with zero
+// imaginary parts.  No CTA waits on anything but the cluster's hardware
+// barriers, which every CTA reaches the same number of times.
+// ---------------------------------------------------------------------------
+namespace cg = cooperative_groups;
+
+static constexpr int kHessClThreads = 512;
+static constexpr int kHessClMax = 8;
+
+template <class R>
+__global__ void __launch_bounds__(kHessClThreads, 1)
+hess_cluster_kernel(cplx<R> *__restrict__ T, cplx<R> *__restrict__ Q, int n, int ld, R *__restrict__ Vg,
+                    R *__restrict__ betas)
+{
+    cg::cluster_group cl = cg::this_cluster();
+    const int CL = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int nt = kHessClThreads, nw = kHessClThreads / 32;
+    const int ncmax = (n + CL - 1) / CL;
+    const int ncl = rank < n ? (n - rank + CL - 1) / CL : 0;  // columns rank, rank + CL, ...
+    extern __shared__ __align__(16) unsigned char smraw[];
+    R *Hs = reinterpret_cast<R *>(smraw);  // Hs[i + jl n] = column rank + jl CL
+    R *vbuf = Hs + (size_t)n * ncmax;      // reflector of a column this CTA owns
+    R *pbuf = vbuf + n;                    // this CTA's part of u
+    R *vloc = pbuf + n;                    // the current reflector
+    __shared__ R s_scal[2];                // beta, new subdiagonal entry
+    __shared__ R s_red[2][nw];
+    auto first_col = [&](int k) {  // first local column with global index > k
+        const int d0 = k + 1 - rank;
+        return d0 > 0 ? (d0 + CL - 1) / CL : 0;
+    };
+    auto gcol = [&](int jl) { return rank + jl * CL; };
+
+    for (int e = tid; e < n * ncl; e += nt) {
+        const int i = e % n, jl = e / n;
+        Hs[i + (size_t)jl * n] = T[i + (int64_t)gcol(jl) * ld].x;
+    }
+    __syncthreads();
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1, o = k % CL;
+        if (rank == o) {
+            R *col = Hs + (size_t)(k / CL) * n + (k + 1);
+            R a = 0, t = 0;
+            for (int i = tid; i < m; i += nt) {
+                const R x = col[i];
+                a = fma(x, x, a);
+                if (i > 0) t = fma(x, x, t);
+            }
+            a = warp_sum(a);
+            t = warp_sum(t);
+            if (lane == 0) { s_red[0][warp] = a; s_red[1][warp] = t; }
+            __syncthreads();
+            if (tid == 0) {
+                R xn2 = 0, tail2 = 0;
+                for (int q = 0; q < nw; ++q) { xn2 += s_red[0][q]; tail2 += s_red[1][q]; }
+                const R x0 = col[0];
+                if (tail2 == R(0)) {
+                    s_scal[0] = 0;
+                    s_scal[1] = x0;
+                } else {
+                    const R xn = sqrt(xn2), sg = x0 < R(0) ? R(-1) : R(1);
+                    const R v0 = x0 + sg * xn;
+                    s_scal[0] = R(2) / (v0 * v0 + tail2);
+                    s_scal[1] = -sg * xn;
+                    vbuf[0] = v0;
+                }
+            }
+            for (int i = 1 + tid; i < m; i += nt) vbuf[i] = col[i];
+            __syncthreads();
+            const R beta = s_scal[0];
+            if (tid == 0) betas[k] = beta;
+            for (int i = tid; i < m; i += nt) Vg[(k + 1 + i) + (int64_t)k * n] = beta != R(0) ? vbuf[i] : R(0);
+            if (beta != R(0))
+                for (int i = tid; i < m; i += nt) col[i] = (i == 0) ? s_scal[1] : R(0);
+            __threadfence();
+        }
+        cl.sync();
+        const R beta = *cl.map_shared_rank(&s_scal[0], o);  // the same in every CTA
+        const int jl0 = first_col(k);
+        if (beta != R(0)) {
+            const R *rv = cl.map_shared_rank(vbuf, o);
+            for (int i = tid; i < m; i += nt) vloc[i] = rv[i];
+            __syncthreads();
+            // P_k H on this CTA's columns > k (rows k+1 .. n-1)
+            for (int jl = jl0 + warp; jl < ncl; jl += nw) {
+                R *c = Hs + (size_t)jl * n + (k + 1);
+                R acc = 0;
+                for (int i = lane; i < m; i += 32) acc = fma(vloc[i], c[i], acc);
+                acc = warp_sum(acc) * beta;
+                for (int i = lane; i < m; i += 32) c[i] = fma(-acc, vloc[i], c[i]);
+            }
+            __syncthreads();
+            // this CTA's part of u = H(:, k+1:n) v
+            for (int i = tid; i < n; i += nt) {
+                R acc0 = 0, acc1 = 0;
+                int jl = jl0;
+                for (; jl + 1 < ncl; jl += 2) {
+                    acc0 = fma(Hs[i + (size_t)jl * n], vloc[gcol(jl) - k - 1], acc0);
+                    acc1 = fma(Hs[i + (size_t)(jl + 1) * n], vloc[gcol(jl + 1) - k - 1], acc1);
+                }
+                if (jl < ncl) acc0 = fma(Hs[i + (size_t)jl * n], vloc[gcol(jl) - k - 1], acc0);
+                pbuf[i] = acc0 + acc1;
+            }
+        }
+        cl.sync();
+        if (beta != R(0)) {
+            // H P_k: every CTA sums the parts in the same order
+            for (int i = tid; i < n; i += nt) {
+                R u = 0;
+                for (int c = 0; c < CL; ++c) u += cl.map_shared_rank(pbuf, c)[i];
+                u *= beta;
+                for (int jl = jl0; jl < ncl; ++jl)
+                    Hs[i + (size_t)jl * n] = fma(-u, vloc[gcol(jl) - k - 1], Hs[i + (size_t)jl * n]);
+            }
+        }
+        __syncthreads();
+    }
+    cl.sync();  // no CTA reads another's shared memory after this point
+    for (int e = tid; e < n * ncl; e += nt) {
+        const int i = e % n, jl = e / n;
+        T[i + (int64_t)gcol(jl) * ld] = cplx<R>{Hs[i + (size_t)jl * n], R(0)};
+    }
+    __syncthreads();
+    for (int e = tid; e < n * ncl; e += nt) {
+        const int i = e % n, jl = e / n;
+        Hs[i + (size_t)jl * n] = (R)(i == gcol(jl));
+    }
+    __syncthreads();
+    for (int k = n - 3; k >= 0; --k) {
+        const R beta = __ldcg(betas + k);
+        if (beta == R(0)) continue;
+        const int m = n - k - 1, jl0 = first_col(k);
+        for (int i = tid; i < m; i += nt) vloc[i] = __ldcg(Vg + (k + 1 + i) + (int64_t)k * n);
+        __syncthreads();
+        for (int jl = jl0 + warp; jl < ncl; jl += nw) {
+            R *c = Hs + (size_t)jl * n + (k + 1);
+            R acc = 0;
+            for (int i = lane; i < m; i += 32) acc = fma(vloc[i], c[i], acc);
+            acc = warp_sum(acc) * beta;
+            for (int i = lane; i < m; i += 32) c[i] = fma(-acc, vloc[i], c[i]);
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < n * ncl; e += nt) {
+        const int i = e % n, jl = e / n;
+        Q[i + (int64_t)gcol(jl) * ld] = cplx<R>{Hs[i + (size_t)jl * n], R(0)};
+    }
+}
+
+static constexpr size_t kHessClSmemMax = 232448 - 1024;  // 227 KB opt-in per CTA, less the static arrays
+
+template <class R>
+static size_t hess_cluster_smem(int n, int CL)
+{
+    const size_t ncmax = (size_t)((n + CL - 1) / CL);
+    return ((size_t)n * ncmax + 3 * (size_t)n) * sizeof(R);
+}
+
+// cluster size for an n x n matrix: the smallest that leaves at most 64
+// columns per CTA, else the largest that fits; 0 = too large (or no such
+// cluster can be resident), use launch_hessenberg
+template <class R>
+int hess_cluster_size(int n)
+{
+    if (n < 3) return 0;
+    static std::atomic<int> resident[kHessClMax + 1];  // per CL: 0 unknown, 1 yes, -1 no
+    int pick = 0;
+    for (int CL = 1; CL <= kHessClMax; CL *= 2) {
+        if (hess_cluster_smem<R>(n, CL) > kHessClSmemMax) continue;
+        pick = CL;
+        if ((n + CL - 1) / CL <= 64) break;
+    }
+    if (!pick) return 0;
+    if (resident[pick].load() == 0) {
+        int ok = -1;
+        if (cudaFuncSetAttribute((const void *)hess_cluster_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kHessClSmemMax) == cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = pick; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(pick);
+            cfg.blockDim = dim3(kHessClThreads);
+            cfg.dynamicSmemBytes = kHessClSmemMax;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int nclusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&nclusters, (const void *)hess_cluster_kernel<R>, &cfg) == cudaSuccess &&
+                nclusters > 0)
+                ok = 1;
+        }
+        cudaGetLastError();
+        resident[pick].store(ok);
+    }
+    return resident[pick].load() > 0 ? pick : 0;
+}
+
+template <class R>
+cudaError_t launch_hessenberg_cluster(cplx<R> *T, cplx<R> *Q, int n, int ld, R *V, R *betas, cudaStream_t s)
+{
+    const int CL = hess_cluster_size<R>(n);
+    if (!CL) return cudaErrorNotSupported;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(kHessClThreads);
+    cfg.dynamicSmemBytes = hess_cluster_smem<R>(n, CL);
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t err = cudaLaunchKernelEx(&cfg, hess_cluster_kernel<R>, T, Q, n, ld, V, betas);
+    count_launch();
+    return err;
+}
+
+template int hess_cluster_size<float>(int);
+template int hess_cluster_size<double>(int);
+template cudaError_t launch_hessenberg_cluster<float>(cplx<float> *, cplx<float> *, int, int, float *, float *,
+                                                      cudaStream_t);
+template cudaError_t launch_hessenberg_cluster<double>(cplx<double> *, cplx<double> *, int, int, double *, double *,
+                                                       cudaStream_t);
 
 template <class R>
 __global__ void eye_kernel(const SchurDesc<R> *__restrict__ descs)
