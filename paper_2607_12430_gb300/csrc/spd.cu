@@ -2,10 +2,11 @@
 //
 // Spectral decomposition A_s = V diag(lam) V^T (Algorithm 3, step 1):
 //   1. Householder tridiagonalisation in the storage precision R (FP32 for
-//      the mixed method): two launches per column -- reflector + product
-//      p = beta A v (one warp per column of the trailing block), and the
-//      symmetric rank-2 update A -= v w^T + w v^T with w = p - (beta/2)(v.p)
-//      v.  The reflectors are kept (one column each) for step 4;
+//      the mixed method): one launch per column that applies the symmetric
+//      rank-2 update A -= v w^T + w v^T of step k (w = p - (beta/2)(v.p) v,
+//      p = beta A v) and in the same pass forms the reflector and p of step
+//      k+1 (one warp per column of the trailing block).  The reflectors are
+//      kept (one column each) for step 4;
 //   2. eigenvalues of the tridiagonal matrix: FP32 multisection (one warp
 //      per eigenvalue, 32 Sturm counts per round) to a bracket of FP32
 //      width, checked and finished by FP64 multisection (a few lanes per
@@ -109,74 +110,143 @@ tri_symv_kernel(const R *__restrict__ A, int n, int ld, int k, R *__restrict__ w
     }
 }
 
+// One step s of the tridiagonalisation in one launch: the rank-2 update of
+// step s on the trailing block A(s+1:n, s+1:n) <- A - v w^T - w v^T, with
+// w = p - (beta/2)(v.p) v from v, beta and p = beta A v of the previous
+// launch, and in the same pass the quantities of step s+1: every CTA updates
+// column s+1 of the block itself and forms its reflector (redundantly; the
+// column is read, never written, in this launch), and each warp, right after
+// updating a column of A(s+2:n, s+2:n), takes its product with the new
+// reflector, which gives p for step s+1.  One read and one write of the
+// trailing block per step instead of three passes.  Row s+1 of the block
+// (above the diagonal of columns > s+1) is not kept up to date: nothing
+// reads it again.  Column s receives its final entries (subdiagonal
+// -sign ||x||, zeros below) and its diagonal from the previous launch; the
+// values of the last column pair go to ns[4..5] (tri_finish_kernel).
+// cv, cp, cs: v, p and [beta, ||x||, sign, diagonal of column s] of step s;
+// nv, np, ns: the same for step s+1.
 template <class R>
 __global__ void __launch_bounds__(kTriThreads2)
-tri_update_kernel(R *__restrict__ A, int n, int ld, int k, const R *__restrict__ wsv,
-                  const R *__restrict__ wsp, const R *__restrict__ wss)
+tri_step_kernel(R *__restrict__ A, int n, int ld, int s, const R *__restrict__ cv, const R *__restrict__ cp,
+                const R *__restrict__ cs, R *__restrict__ nv, R *__restrict__ np, R *__restrict__ ns,
+                R *__restrict__ Y, int ldy, R *__restrict__ betas)
 {
     extern __shared__ unsigned char smraw[];
-    const int m = n - k - 1;
-    R *vsh = reinterpret_cast<R *>(smraw);
-    R *wsh = vsh + m;
+    const int m = n - s - 1;  // block rows / columns s+1 .. n-1
+    R *vs = reinterpret_cast<R *>(smraw), *wsm = vs + m, *cn = wsm + m, *vn = cn + m;
     __shared__ R red[kTriThreads2 / 32];
-    __shared__ R s_K;
-    const R beta = wss[0];
-    if (beta == R(0)) return;
+    __shared__ R s_K, s_scal[3];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const R beta = cs[0];
     R acc = 0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        R v = wsv[i], p = wsp[i];
-        vsh[i] = v;
-        wsh[i] = p;
-        acc = fma(v, p, acc);
+    for (int i = tid; i < m; i += blockDim.x) {
+        const R v = cv[i], pp = beta != R(0) ? cp[i] : R(0);
+        vs[i] = v;
+        wsm[i] = pp;
+        acc = fma(v, pp, acc);
     }
     acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    if (lane == 0) red[warp] = acc;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         R t = 0;
         for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
         s_K = R(0.5) * beta * t;
     }
     __syncthreads();
     const R K = s_K;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) wsh[i] = fma(-K, vsh[i], wsh[i]);
+    for (int i = tid; i < m; i += blockDim.x) wsm[i] = beta != R(0) ? fma(-K, vs[i], wsm[i]) : R(0);
     __syncthreads();
+    {
+        const R v0 = vs[0], w0 = wsm[0];
+        const R *c = A + (s + 1) + (int64_t)(s + 1) * ld;
+        for (int i = tid; i < m; i += blockDim.x) cn[i] = fma(-vs[i], w0, fma(-wsm[i], v0, c[i]));
+    }
+    __syncthreads();
+    const bool more = s + 4 <= n;  // column s+1 has a reflector
+    R bn = 0;
+    if (more) {
+        real_reflector<R>(cn + 1, m - 1, vn, s_scal);
+        bn = s_scal[0];
+    }
     if (blockIdx.x == 0) {
-        const R xn = wss[1], sg = wss[2];
-        for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            R val = (i == 0) ? -sg * xn : R(0);
-            A[(k + 1 + i) + (int64_t)k * ld] = val;
-            A[k + (int64_t)(k + 1 + i) * ld] = val;
+        if (beta != R(0))
+            for (int i = tid; i < m; i += blockDim.x) A[(s + 1 + i) + (int64_t)s * ld] = (i == 0) ? -cs[2] * cs[1] : R(0);
+        if (s >= 1 && tid == 0) A[s + (int64_t)s * ld] = cs[3];
+        if (more) {
+            R *yk = Y + (s + 2) + (int64_t)(s + 1) * ldy;
+            for (int i = tid; i < m - 1; i += blockDim.x) {
+                nv[i] = vn[i];
+                yk[i] = vn[i];
+            }
+            if (tid == 0) {
+                ns[0] = s_scal[0]; ns[1] = s_scal[1]; ns[2] = s_scal[2]; ns[3] = cn[0];
+                betas[s + 1] = bn;
+            }
+        } else if (tid == 0) {
+            ns[4] = cn[0];
+            ns[5] = cn[1];
         }
     }
-    const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int nw = gridDim.x * (blockDim.x >> 5);
-    for (int j = gw; j < m; j += nw) {
-        R *c = A + (k + 1) + (int64_t)(k + 1 + j) * ld;
-        const R vj = vsh[j], wj = wsh[j];
-#pragma unroll 8
-        for (int i = lane; i < m; i += 32) c[i] = fma(-vsh[i], wj, fma(-wsh[i], vj, c[i]));
+    const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
+    const int nwt = gridDim.x * (blockDim.x >> 5);
+    for (int j = 1 + gw; j < m; j += nwt) {
+        R *c = A + (s + 1) + (int64_t)(s + 1 + j) * ld;
+        const R vj = vs[j], wj = wsm[j];
+        if (more) {
+            R dot = 0;
+#pragma unroll 4
+            for (int i = 1 + lane; i < m; i += 32) {
+                const R cc = fma(-vs[i], wj, fma(-wsm[i], vj, c[i]));
+                c[i] = cc;
+                dot = fma(cc, vn[i - 1], dot);
+            }
+            dot = warp_sum(dot);
+            if (lane == 0) np[j - 1] = bn * dot;
+        } else {
+            for (int i = 1 + lane; i < m; i += 32) c[i] = fma(-vs[i], wj, fma(-wsm[i], vj, c[i]));
+        }
+    }
+}
+
+// the last two columns: diagonal and subdiagonal of column n-2 (n >= 3)
+template <class R>
+__global__ void tri_finish_kernel(R *__restrict__ A, int n, int ld, const R *__restrict__ ns)
+{
+    if (threadIdx.x == 0) {
+        A[(n - 2) + (int64_t)(n - 2) * ld] = ns[4];
+        A[(n - 1) + (int64_t)(n - 2) * ld] = ns[5];
     }
 }
 
 template <class R>
 cudaError_t launch_tridiag(R *A, int n, int ld, R *Y, int ldy, R *betas, R *ws, cudaStream_t s)
 {
-    R *wsv = ws, *wsp = ws + n, *wss = ws + 2 * n;
-    size_t sm1 = (size_t)std::max(n, 1) * sizeof(R);
-    size_t sm2 = 2 * sm1;
+    if (n < 3) return cudaSuccess;
+    // two sets of (v, p, scalars), alternating between steps
+    R *set[2] = {ws, ws + 2 * n + 8};
+    size_t sm1 = (size_t)n * sizeof(R);
+    size_t sm4 = 4 * sm1;
     cudaError_t err;
-    if (sm2 > 48 * 1024) {
-        if ((err = allow_max_smem((const void *)tri_symv_kernel<R>))) return err;
-        if ((err = allow_max_smem((const void *)tri_update_kernel<R>))) return err;
+    if (sm1 > 48 * 1024 && (err = allow_max_smem((const void *)tri_symv_kernel<R>))) return err;
+    if (sm4 > 48 * 1024 && (err = allow_max_smem((const void *)tri_step_kernel<R>))) return err;
+    {
+        const int m = n - 1;
+        const int ctas = (int)std::min<int64_t>(cdiv_i(m, kTriThreads2 / 32), 304);
+        tri_symv_kernel<R><<<ctas, kTriThreads2, sm1, s>>>(A, n, ld, 0, set[0], set[0] + n, set[0] + 2 * n, Y, ldy,
+                                                            betas);
+        count_launch();
     }
     for (int k = 0; k + 2 < n; ++k) {
-        int m = n - k - 1;
-        int ctas = (int)std::min<int64_t>(cdiv_i(m, kTriThreads2 / 32), 304);
-        tri_symv_kernel<R><<<ctas, kTriThreads2, sm1, s>>>(A, n, ld, k, wsv, wsp, wss, Y, ldy, betas); count_launch();
-        tri_update_kernel<R><<<ctas, kTriThreads2, sm2, s>>>(A, n, ld, k, wsv, wsp, wss); count_launch();
+        const int m = n - k - 1;
+        const int ctas = (int)std::min<int64_t>(std::max<int64_t>(1, cdiv_i(m - 1, kTriThreads2 / 32)), 304);
+        R *c = set[k & 1], *x = set[(k + 1) & 1];
+        tri_step_kernel<R><<<ctas, kTriThreads2, (size_t)4 * m * sizeof(R), s>>>(A, n, ld, k, c, c + n, c + 2 * n, x,
+                                                                                  x + n, x + 2 * n, Y, ldy, betas);
+        count_launch();
     }
+    tri_finish_kernel<R><<<1, 32, 0, s>>>(A, n, ld, set[(n - 2) & 1] + 2 * n);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -642,7 +712,7 @@ size_t spd_bytes(int64_t n, int chunk)
            Carve::round(nn * sizeof(float)) + Carve::round(nn * sizeof(double)) +
            Carve::round((2 * (size_t)n * chunk + 3 * n + 8) * sizeof(double)) +
            Carve::round(n * sizeof(double)) + 2 * Carve::round(n * sizeof(R)) +
-           Carve::round((2 * n + 8) * sizeof(R)) + Carve::round((n + 8) * sizeof(R)) +
+           Carve::round((4 * n + 16) * sizeof(R)) + Carve::round((n + 8) * sizeof(R)) +
            Carve::round(((size_t)2 * kBackNb * kBackNb + (size_t)2 * kBackNb * n) * sizeof(R)) +
            Carve::round((size_t)(4 * n + 8) * sizeof(double)) +
            (sizeof(R) == sizeof(float) ? Carve::round(split_digit_elems((int)n) * 2) + Carve::round(n * sizeof(int)) : 0) +
@@ -676,7 +746,7 @@ int spd_carve(sqrtm_handle_t h, int64_t n, SpdWork<R> *w)
     w->ZT = c.take<double>(nn);
     w->eigscratch = c.take<double>(2 * (size_t)n * chunk + 3 * n + 8 + (4 * n + 8));
     w->lam = c.take<double>(n);
-    w->vecws = c.take<R>(2 * n + 8);
+    w->vecws = c.take<R>(4 * n + 16);
     w->betas = c.take<R>(n + 8);
     w->btws = c.take<R>((size_t)2 * kBackNb * kBackNb + (size_t)2 * kBackNb * n);
     w->digits = nullptr;

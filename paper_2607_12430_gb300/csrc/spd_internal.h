@@ -34,7 +34,7 @@ cudaError_t launch_residual_sym_split(const double *A, int64_t lda, const double
 // tridiagonal on its diagonal and first subdiagonal).  Reflector k,
 // H_k = I - beta_k y_k y_k^T, is stored as column k of Y (y_k(i) = 0 for
 // i <= k; Y must be zero on entry) and beta_k in betas[k]; Q = H_0 H_1 ...
-// H_{n-3}.  ws: >= 2 n + 8 elements of R.
+// H_{n-3}.  ws: >= 4 n + 16 elements of R.
 template <class R>
 cudaError_t launch_tridiag(R *A, int n, int ld, R *Y, int ldy, R *betas, R *ws, cudaStream_t s);
 
