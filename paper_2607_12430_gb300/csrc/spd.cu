@@ -37,6 +37,7 @@
 namespace sqm {
 
 static constexpr int kTriThreads2 = 256;
+static constexpr int kTriBatch = 8;  // rows in flight per lane in tri_step_kernel
 
 // reflector for x = A(k+1:n, k) (real): v = x + sign(x0) ||x|| e1,
 // beta = 2 / ||v||^2, P x = -sign(x0) ||x|| e1
@@ -190,21 +191,32 @@ tri_step_kernel(R *__restrict__ A, int n, int ld, int s, const R *__restrict__ c
     }
     const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
     const int nwt = gridDim.x * (blockDim.x >> 5);
+    // columns of the block: the loads of a batch of kTriBatch rows per lane
+    // are issued before any is used (the pass is bound by L2 latency)
     for (int j = 1 + gw; j < m; j += nwt) {
         R *c = A + (s + 1) + (int64_t)(s + 1 + j) * ld;
         const R vj = vs[j], wj = wsm[j];
-        if (more) {
-            R dot = 0;
-#pragma unroll 4
-            for (int i = 1 + lane; i < m; i += 32) {
-                const R cc = fma(-vs[i], wj, fma(-wsm[i], vj, c[i]));
-                c[i] = cc;
-                dot = fma(cc, vn[i - 1], dot);
+        R dot = 0;
+        for (int i0 = 1 + lane; i0 < m; i0 += 32 * kTriBatch) {
+            R x[kTriBatch];
+#pragma unroll
+            for (int u = 0; u < kTriBatch; ++u) {
+                const int i = i0 + 32 * u;
+                x[u] = i < m ? c[i] : R(0);
             }
+#pragma unroll
+            for (int u = 0; u < kTriBatch; ++u) {
+                const int i = i0 + 32 * u;
+                if (i < m) {
+                    const R cc = fma(-vs[i], wj, fma(-wsm[i], vj, x[u]));
+                    c[i] = cc;
+                    if (more) dot = fma(cc, vn[i - 1], dot);
+                }
+            }
+        }
+        if (more) {
             dot = warp_sum(dot);
             if (lane == 0) np[j - 1] = bn * dot;
-        } else {
-            for (int i = 1 + lane; i < m; i += 32) c[i] = fma(-vs[i], wj, fma(-wsm[i], vj, c[i]));
         }
     }
 }
@@ -237,9 +249,13 @@ cudaError_t launch_tridiag(R *A, int n, int ld, R *Y, int ldy, R *betas, R *ws, 
                                                             betas);
         count_launch();
     }
+    // up to four resident CTAs per SM: more warps, more loads in flight
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t tri_ctas = 4 * (int64_t)sms;
     for (int k = 0; k + 2 < n; ++k) {
         const int m = n - k - 1;
-        const int ctas = (int)std::min<int64_t>(std::max<int64_t>(1, cdiv_i(m - 1, kTriThreads2 / 32)), 304);
+        const int ctas = (int)std::min<int64_t>(std::max<int64_t>(1, cdiv_i(m - 1, kTriThreads2 / 32)), tri_ctas);
         R *c = set[k & 1], *x = set[(k + 1) & 1];
         tri_step_kernel<R><<<ctas, kTriThreads2, (size_t)4 * m * sizeof(R), s>>>(A, n, ld, k, c, c + n, c + 2 * n, x,
                                                                                   x + n, x + 2 * n, Y, ldy, betas);
