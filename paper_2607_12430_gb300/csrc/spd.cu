@@ -139,11 +139,13 @@ tri_step_kernel(R *__restrict__ A, int n, int ld, int s, const R *__restrict__ c
     __shared__ R s_K, s_scal[3];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const R beta = cs[0];
+    const R *c1 = A + (s + 1) + (int64_t)(s + 1) * ld;  // column s+1 of the block
     R acc = 0;
-    for (int i = tid; i < m; i += blockDim.x) {
+    for (int i = tid; i < m; i += blockDim.x) {  // all global reads of the prologue in one pass
         const R v = cv[i], pp = beta != R(0) ? cp[i] : R(0);
         vs[i] = v;
         wsm[i] = pp;
+        cn[i] = c1[i];
         acc = fma(v, pp, acc);
     }
     acc = warp_sum(acc);
@@ -160,8 +162,7 @@ tri_step_kernel(R *__restrict__ A, int n, int ld, int s, const R *__restrict__ c
     __syncthreads();
     {
         const R v0 = vs[0], w0 = wsm[0];
-        const R *c = A + (s + 1) + (int64_t)(s + 1) * ld;
-        for (int i = tid; i < m; i += blockDim.x) cn[i] = fma(-vs[i], w0, fma(-wsm[i], v0, c[i]));
+        for (int i = tid; i < m; i += blockDim.x) cn[i] = fma(-vs[i], w0, fma(-wsm[i], v0, cn[i]));
     }
     __syncthreads();
     const bool more = s + 4 <= n;  // column s+1 has a reflector
@@ -423,8 +424,10 @@ __global__ void __launch_bounds__(256) multisect_f32_kernel(const float *__restr
 // chain of dependent FP64 divisions; one eigenvalue per lane leaves most SM
 // sub-partitions idle for n of a few thousand, so the launcher trades extra
 // counts for more resident warps.
+static constexpr int kBisectThreads = 64;  // two warps per CTA: the warps spread over every SM
+
 template <int K>
-__global__ void __launch_bounds__(128) bisect_f64_kernel(const double *__restrict__ d, const double *__restrict__ e2,
+__global__ void __launch_bounds__(kBisectThreads) bisect_f64_kernel(const double *__restrict__ d, const double *__restrict__ e2,
                                                          int n, const double *__restrict__ bounds,
                                                          const double *__restrict__ blo,
                                                          const double *__restrict__ bhi, double reltol,
@@ -605,14 +608,14 @@ cudaError_t launch_tridiag_eig(const R *A, int n, int ld, double *lam, double *Z
     const double reltol = sizeof(R) == sizeof(float) ? 1e-10 : 2.0 * 1.1102230246251565e-16;
     {
         const int K = bisect_lanes(n);
-        const int grid = (int)cdiv_i((int64_t)n * K, 128);
+        const int grid = (int)cdiv_i((int64_t)n * K, kBisectThreads);
         switch (K) {
-        case 1: bisect_f64_kernel<1><<<grid, 128, 0, s>>>(d, e2, n, bounds, blo, bhi, reltol, lam); break;
-        case 2: bisect_f64_kernel<2><<<grid, 128, 0, s>>>(d, e2, n, bounds, blo, bhi, reltol, lam); break;
-        case 4: bisect_f64_kernel<4><<<grid, 128, 0, s>>>(d, e2, n, bounds, blo, bhi, reltol, lam); break;
-        case 8: bisect_f64_kernel<8><<<grid, 128, 0, s>>>(d, e2, n, bounds, blo, bhi, reltol, lam); break;
-        case 16: bisect_f64_kernel<16><<<grid, 128, 0, s>>>(d, e2, n, bounds, blo, bhi, reltol, lam); break;
-        default: bisect_f64_kernel<32><<<grid, 128, 0, s>>>(d, e2, n, bounds, blo, bhi, reltol, lam); break;
+        case 1: bisect_f64_kernel<1><<<grid, kBisectThreads, 0, s>>>(d, e2, n, bounds, blo, bhi, reltol, lam); break;
+        case 2: bisect_f64_kernel<2><<<grid, kBisectThreads, 0, s>>>(d, e2, n, bounds, blo, bhi, reltol, lam); break;
+        case 4: bisect_f64_kernel<4><<<grid, kBisectThreads, 0, s>>>(d, e2, n, bounds, blo, bhi, reltol, lam); break;
+        case 8: bisect_f64_kernel<8><<<grid, kBisectThreads, 0, s>>>(d, e2, n, bounds, blo, bhi, reltol, lam); break;
+        case 16: bisect_f64_kernel<16><<<grid, kBisectThreads, 0, s>>>(d, e2, n, bounds, blo, bhi, reltol, lam); break;
+        default: bisect_f64_kernel<32><<<grid, kBisectThreads, 0, s>>>(d, e2, n, bounds, blo, bhi, reltol, lam); break;
         }
         count_launch();
     }
@@ -738,7 +741,7 @@ size_t spd_bytes(int64_t n, int chunk)
 template <class R>
 int spd_carve(sqrtm_handle_t h, int64_t n, SpdWork<R> *w)
 {
-    int chunk = (int)std::min<int64_t>(n, 2048);
+    int chunk = (int)std::min<int64_t>(n, 4096);  // eigenvectors per twisted_kernel launch
     size_t nn = (size_t)n * n;
     // factors V, lamr, s persist for the adjoint / reuse
     size_t fbytes = Carve::round(nn * sizeof(R)) + 2 * Carve::round(n * sizeof(R)) +
