@@ -23,13 +23,20 @@
 // far below it otherwise.  The P_st are scaled exactly (powers of two) and
 // summed in FP64.
 //
-// Products.  One launch per pair (s, t): 128 x 128 output tiles of the upper
-// block triangle only (R is symmetric), K in steps of 64 BF16 values; TMA
-// loads both digit tiles (128 rows x 128 bytes, 128-byte swizzle) into a
-// 6-stage ring, one thread issues 4 tcgen05.mma (M = N = 128, K = 16) per
-// stage into a 128-column TMEM accumulator, and the epilogue adds the scaled
-// tile into the FP64 accumulator (the first pair starts it from A, the last
-// one writes Rhat = fl32(R 4^-e), mirrored, and per-tile partial sums of
+// Products.  Pairs with the same s + t carry the same power of two, so
+// several of them can share one FP32 accumulator as long as the bounds of
+// their integer sums add up to at most 2^24 (|m_0| <= 2^b, |m_s| <= 2^(b-1)
+// for s >= 1, so |P_st| <= n 2^b_s 2^b_t): the accumulation stays exact
+// and the FP64 epilogue -- which costs as much as the tensor-core work on a
+// part with few FP64 units -- runs once per group instead of once per pair.
+// One launch per group: 128 x 128 output tiles of the upper block triangle
+// only (R is symmetric), K in steps of 64 BF16 values over each pair of the
+// group in turn; TMA loads both digit tiles (128 rows x 128 bytes, 128-byte
+// swizzle) from one map over all digit slices into a 6-stage ring, one
+// thread issues 4 tcgen05.mma (M = N = 128, K = 16) per stage into a
+// 128-column TMEM accumulator, and the epilogue adds the scaled tile into
+// the FP64 accumulator (the first group starts it from A, the last one
+// writes Rhat = fl32(R 4^-e), mirrored, and per-tile partial sums of
 // |R|^2).  Every mbarrier wait is bounded (status 6 on timeout).
 #include <cuda_bf16.h>
 
@@ -87,6 +94,14 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const double *__restric
     }
 }
 
+static constexpr int SP_MAXG = 16;  // pairs per group
+
+// digit-slice indices of the pairs of one group (all with the same s + t)
+struct SplitGroup {
+    int g;                 // pairs in the group
+    int s[SP_MAXG], t[SP_MAXG];
+};
+
 struct SplitEpi {
     const double *A;
     int64_t lda;
@@ -102,8 +117,8 @@ struct SplitEpi {
 
 template <int MODE>
 __global__ void __launch_bounds__(SP_THREADS, 1)
-split_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int n, int KT,
-                  int T, SplitEpi ep, int *err)
+split_gemm_kernel(const __grid_constant__ CUtensorMap mapX, const SplitGroup grp, int n, int KT, int T, SplitEpi ep,
+                  int *err)
 {
     extern __shared__ unsigned char smraw[];
     __shared__ int s_fail;
@@ -140,16 +155,20 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
 
     auto stage_ptr = [&](int s, int which) { return base + s * SP_STAGE_BYTES + which * SP_TILE_BYTES; };
     int issued = 0, consumed = 0, committed = 0;
+    const int KTG = KT * grp.g;  // K steps over every pair of the group
     if (tid == 0) {
+        // step t: pair t / KT, K block t % KT; digit slice q starts at row q n
+        // of the map (rows past n of a tile read the next slice or the zero
+        // fill; they only reach output rows / columns >= n, never stored)
         auto issue_load = [&](int t) {
-            const int s = t % SP_STAGES;
+            const int s = t % SP_STAGES, pr = t / KT, kb = t - pr * KT;
             mbar_arrive_expect_tx(&full[s], 2 * SP_TILE_BYTES);
-            tma_load_2d(stage_ptr(s, 0), &mapA, &full[s], t * SP_BK, m0);
-            tma_load_2d(stage_ptr(s, 1), &mapB, &full[s], t * SP_BK, n0);
+            tma_load_2d(stage_ptr(s, 0), &mapX, &full[s], kb * SP_BK, grp.s[pr] * n + m0);
+            tma_load_2d(stage_ptr(s, 1), &mapX, &full[s], kb * SP_BK, grp.t[pr] * n + n0);
         };
-        for (; issued < min(SP_STAGES + 0, KT); ++issued) issue_load(issued);
+        for (; issued < min(SP_STAGES + 0, KTG); ++issued) issue_load(issued);
         constexpr uint32_t IDESC = idesc_bf16_128x128();
-        for (int t = 0; t < KT; ++t) {
+        for (int t = 0; t < KTG; ++t) {
             const int s = t % SP_STAGES;
             if (!mbar_wait(&full[s], (t / SP_STAGES) & 1)) { s_fail = 1; break; }
             consumed = t + 1;
@@ -163,7 +182,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
             mma_commit(&done[s]);
             committed = t + 1;
             // refill the stage tile t-1 used once its products are done
-            if (t >= 1 && issued < KT) {
+            if (t >= 1 && issued < KTG) {
                 const int sp = (t - 1) % SP_STAGES;
                 if (!mbar_wait(&done[sp], ((t - 1) / SP_STAGES) & 1)) { s_fail = 1; break; }
                 issue_load(issued);
@@ -172,8 +191,8 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
         }
     }
     __syncthreads();
-    if (!s_fail && KT > 0) {
-        const int tl = KT - 1;
+    if (!s_fail && KTG > 0) {
+        const int tl = KTG - 1;
         if (!mbar_wait(&done[tl % SP_STAGES], (tl / SP_STAGES) & 1)) s_fail = 1;
     }
     __syncthreads();
@@ -285,31 +304,50 @@ cudaError_t launch_residual_sym_split(const double *A, int64_t lda, const double
     __nv_bfloat16 *Xs = (__nv_bfloat16 *)digits;
     split_rows_kernel<<<(unsigned)cdiv_i((int64_t)n * 32, 256), 256, 0, s>>>(X, ldx, n, lds, b, S, Xs, rho);
     count_launch();
-    CUtensorMap maps[16];
-    if (S > 16) return cudaErrorInvalidValue;
-    for (int q = 0; q < S; ++q)
-        if (!make_bf16_map(&maps[q], Xs + (size_t)q * n * lds, lds, n, lds)) return cudaErrorInvalidValue;
+    CUtensorMap mapX;
+    if (S > SP_MAXG) return cudaErrorInvalidValue;
+    if (!make_bf16_map(&mapX, Xs, lds, (int64_t)S * n, lds)) return cudaErrorInvalidValue;
     const int T = (int)cdiv_i(n, SP_BM), ntiles = T * (T + 1) / 2, KT = lds / SP_BK;
     cudaError_t er;
     if ((er = allow_max_smem((const void *)split_gemm_kernel<0>))) return er;
     if ((er = allow_max_smem((const void *)split_gemm_kernel<SP_FIRST>))) return er;
     if ((er = allow_max_smem((const void *)split_gemm_kernel<SP_LAST>))) return er;
     if ((er = allow_max_smem((const void *)split_gemm_kernel<SP_FIRST | SP_LAST>))) return er;
-    const int npairs = (D + 1) * (D + 2) / 2;
-    int idx = 0;
-    for (int d = 0; d <= D; ++d)
-        for (int si = 0; si <= d; ++si, ++idx) {
+    // groups of pairs with the same s + t whose integer bounds sum to <= 2^24
+    SplitGroup groups[(SP_MAXG * (SP_MAXG + 1)) / 2];
+    int shifts[(SP_MAXG * (SP_MAXG + 1)) / 2];
+    int ng = 0;
+    for (int d = 0; d <= D; ++d) {
+        double used = 0.0;
+        bool open = false;
+        for (int si = 0; si <= d; ++si) {
             const int ti = d - si;
-            SplitEpi ep{A, lda, Racc, (int64_t)n, rho, b * (d + 2), Rhat, (int64_t)ldr, ldexp(1.0, -2 * e), partials};
-            const int mode = (idx == 0 ? SP_FIRST : 0) | (idx == npairs - 1 ? SP_LAST : 0);
-            switch (mode) {
-            case 0: split_gemm_kernel<0><<<ntiles, SP_THREADS, SP_SMEM, s>>>(maps[si], maps[ti], n, KT, T, ep, err); break;
-            case SP_FIRST: split_gemm_kernel<SP_FIRST><<<ntiles, SP_THREADS, SP_SMEM, s>>>(maps[si], maps[ti], n, KT, T, ep, err); break;
-            case SP_LAST: split_gemm_kernel<SP_LAST><<<ntiles, SP_THREADS, SP_SMEM, s>>>(maps[si], maps[ti], n, KT, T, ep, err); break;
-            default: split_gemm_kernel<SP_FIRST | SP_LAST><<<ntiles, SP_THREADS, SP_SMEM, s>>>(maps[si], maps[ti], n, KT, T, ep, err);
+            const double pb = (double)n * ldexp(1.0, si == 0 ? b : b - 1) * ldexp(1.0, ti == 0 ? b : b - 1);
+            if (!open || used + pb > 16777216.0 || groups[ng - 1].g == SP_MAXG) {
+                groups[ng].g = 0;
+                shifts[ng] = b * (d + 2);
+                ++ng;
+                used = 0.0;
+                open = true;
             }
-            count_launch();
+            SplitGroup &gr = groups[ng - 1];
+            gr.s[gr.g] = si;
+            gr.t[gr.g] = ti;
+            ++gr.g;
+            used += pb;
         }
+    }
+    for (int q = 0; q < ng; ++q) {
+        SplitEpi ep{A, lda, Racc, (int64_t)n, rho, shifts[q], Rhat, (int64_t)ldr, ldexp(1.0, -2 * e), partials};
+        const int mode = (q == 0 ? SP_FIRST : 0) | (q == ng - 1 ? SP_LAST : 0);
+        switch (mode) {
+        case 0: split_gemm_kernel<0><<<ntiles, SP_THREADS, SP_SMEM, s>>>(mapX, groups[q], n, KT, T, ep, err); break;
+        case SP_FIRST: split_gemm_kernel<SP_FIRST><<<ntiles, SP_THREADS, SP_SMEM, s>>>(mapX, groups[q], n, KT, T, ep, err); break;
+        case SP_LAST: split_gemm_kernel<SP_LAST><<<ntiles, SP_THREADS, SP_SMEM, s>>>(mapX, groups[q], n, KT, T, ep, err); break;
+        default: split_gemm_kernel<SP_FIRST | SP_LAST><<<ntiles, SP_THREADS, SP_SMEM, s>>>(mapX, groups[q], n, KT, T, ep, err);
+        }
+        count_launch();
+    }
     *nparts = ntiles;
     return cudaGetLastError();
 }
