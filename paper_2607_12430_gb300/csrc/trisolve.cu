@@ -22,6 +22,9 @@ namespace sqm {
 static constexpr int TB = 32;       // maximum block edge
 static constexpr int TLD = TB + 1;  // padded leading dimension in shared memory
 static constexpr int kTriThreads = 128;
+// Sylvester: the update terms of a block split over groups of 128 threads
+// (4 for complex FP32, 2 for complex FP64: 4 tiles of shared memory each)
+template <class R> struct SylCfg { static constexpr int G = sizeof(R) == 4 ? 4 : 2, THREADS = kTriThreads * G; };
 
 template <class R>
 __device__ void load_tile(cplx<R> *dst, const cplx<R> *__restrict__ src, int ld, int rows,
@@ -46,13 +49,31 @@ __device__ void load_tile_async(cplx<R> *dst, const cplx<R> *__restrict__ src, i
     }
 }
 
+// The same for one 128-thread group: lt = thread index within the group.
+template <class R>
+__device__ void load_tile_async_g(cplx<R> *dst, const cplx<R> *__restrict__ src, int ld, int rows, int cols, int lt)
+{
+    for (int e = lt; e < TB * TB; e += kTriThreads) {
+        int i = e % TB, j = e / TB;
+        if (i < rows && j < cols) cp_async_elem<R>(&dst[i + j * TLD], &src[i + (int64_t)j * ld]);
+        else dst[i + j * TLD] = cplx<R>{0, 0};
+    }
+}
+
+// barrier of one 128-thread group (named barrier 1 + g)
+__device__ __forceinline__ void group_bar(int g)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kTriThreads) : "memory");
+}
+
 // acc(r, c_q) -= sum_k A(r, k) B(k, c_q) for the 8 outputs a thread owns
-// (row r = tid % 32, columns c_q = tid / 32 + 4 q).
+// (row r = lt % 32, columns c_q = lt / 32 + 4 q; lt = thread index within
+// its 128-thread group).
 template <class R>
 __device__ __forceinline__ void tile_mms(cplx<R> (&acc)[8], const cplx<R> *A, const cplx<R> *B,
-                                         int kk)
+                                         int kk, int lt)
 {
-    const int r = threadIdx.x & 31, c0 = threadIdx.x >> 5;
+    const int r = lt & 31, c0 = lt >> 5;
     for (int k = 0; k < kk; ++k) {
         cplx<R> a = A[r + k * TLD];
 #pragma unroll
@@ -97,65 +118,83 @@ __device__ void leaf_sylvester(const cplx<R> *A, const cplx<R> *B, cplx<R> *C, i
 }
 
 // ---------------------------------------------------------------------------
-// Sylvester wavefront: blocks (I, J) with J - I = w - (Mb - 1)
+// Sylvester wavefront: blocks (I, J) with J - I = w - (Mb - 1).  The update
+// terms of a block are dealt round-robin to SylCfg<R>::G groups of 128 threads
+// (each with its own double-buffered tiles and named barrier); the partial
+// sums are added in group order, then the leaf is solved.
 // ---------------------------------------------------------------------------
 template <class R>
-__global__ void __launch_bounds__(kTriThreads)
+__global__ void __launch_bounds__(SylCfg<R>::THREADS)
 rtrsyl_wave_kernel(const cplx<R> *__restrict__ S, int lds, int m, const cplx<R> *__restrict__ St,
                    int ldst, int nn, cplx<R> *C, int ldc, int b, int w, int *status)
 {
     extern __shared__ unsigned char smraw[];
+    constexpr int TT = TB * TLD, kSylGroups = SylCfg<R>::G;
     cplx<R> *tc = reinterpret_cast<cplx<R> *>(smraw);
-    cplx<R> *ta = tc + TB * TLD;
-    cplx<R> *tb = ta + TB * TLD;
-    cplx<R> *ta2 = tb + TB * TLD;
-    cplx<R> *tb2 = ta2 + TB * TLD;
     __shared__ int bad;
     const int Mb = (m + b - 1) / b, Nb = (nn + b - 1) / b;
     const int I = max(0, (Mb - 1) - w) + blockIdx.x;
     const int J = I + w - (Mb - 1);
     if (I >= Mb || J >= Nb || J < 0) return;
+    const int g = threadIdx.x / kTriThreads, lt = threadIdx.x % kTriThreads;
+    cplx<R> *ta = tc + TT * (1 + 4 * g), *tb = ta + TT, *ta2 = tb + TT, *tb2 = ta2 + TT;
     if (threadIdx.x == 0) bad = 0;
     const int i0 = I * b, j0 = J * b;
     const int bm = min(b, m - i0), bn = min(b, nn - j0);
     load_tile(tc, C + i0 + (int64_t)j0 * ldc, ldc, bm, bn);
     __syncthreads();
     cplx<R> acc[8];
-    const int r = threadIdx.x & 31, c0 = threadIdx.x >> 5;
+    const int r = lt & 31, c0 = lt >> 5;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = tc[r + (c0 + 4 * q) * TLD];
+    for (int q = 0; q < 8; ++q) acc[q] = g == 0 ? tc[r + (c0 + 4 * q) * TLD] : cplx<R>{0, 0};
     // update terms: K = I+1..Mb-1 (S_IK Y_KJ), then K = 0..J-1 (Y_IK St_KJ);
-    // tiles of term t+1 are fetched asynchronously while term t is multiplied
+    // group g takes terms g, g + G, ...; its tiles of the next term are
+    // fetched asynchronously while the current one is multiplied
     const int nterm = (Mb - 1 - I) + J;
     auto issue = [&](int t, cplx<R> *da, cplx<R> *db) {
         if (t < Mb - 1 - I) {
             const int k0 = (I + 1 + t) * b, bk = min(b, m - k0);
-            load_tile_async(da, S + i0 + (int64_t)k0 * lds, lds, bm, bk);
-            load_tile_async(db, C + k0 + (int64_t)j0 * ldc, ldc, bk, bn);
+            load_tile_async_g(da, S + i0 + (int64_t)k0 * lds, lds, bm, bk, lt);
+            load_tile_async_g(db, C + k0 + (int64_t)j0 * ldc, ldc, bk, bn, lt);
         } else {
             const int k0 = (t - (Mb - 1 - I)) * b, bk = min(b, nn - k0);
-            load_tile_async(da, C + i0 + (int64_t)k0 * ldc, ldc, bm, bk);
-            load_tile_async(db, St + k0 + (int64_t)j0 * ldst, ldst, bk, bn);
+            load_tile_async_g(da, C + i0 + (int64_t)k0 * ldc, ldc, bm, bk, lt);
+            load_tile_async_g(db, St + k0 + (int64_t)j0 * ldst, ldst, bk, bn, lt);
         }
     };
     auto kdim = [&](int t) {
         return (t < Mb - 1 - I) ? min(b, m - (I + 1 + t) * b) : min(b, nn - (t - (Mb - 1 - I)) * b);
     };
-    if (nterm > 0) issue(0, ta, tb);
-    for (int t = 0; t < nterm; ++t) {
-        cplx<R> *ca = (t & 1) ? ta2 : ta, *cb = (t & 1) ? tb2 : tb;
+    if (g < nterm) issue(g, ta, tb);
+    for (int t = g, it = 0; t < nterm; t += kSylGroups, ++it) {
+        cplx<R> *ca = (it & 1) ? ta2 : ta, *cb = (it & 1) ? tb2 : tb;
         cp_async_wait_all();
-        __syncthreads();
-        if (t + 1 < nterm) issue(t + 1, (t & 1) ? ta : ta2, (t & 1) ? tb : tb2);
-        tile_mms(acc, ca, cb, kdim(t));
+        group_bar(g);
+        if (t + kSylGroups < nterm) issue(t + kSylGroups, (it & 1) ? ta : ta2, (it & 1) ? tb : tb2);
+        tile_mms(acc, ca, cb, kdim(t), lt);
     }
     __syncthreads();
+    // partial sums of groups 1.. into their first tile, added to group 0's in order
+    if (g > 0) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) tc[r + (c0 + 4 * q) * TLD] = acc[q];
-    load_tile(ta, S + i0 + (int64_t)i0 * lds, lds, bm, bm);
-    load_tile(tb, St + j0 + (int64_t)j0 * ldst, ldst, bn, bn);
+        for (int q = 0; q < 8; ++q) ta[r + (c0 + 4 * q) * TLD] = acc[q];
+    }
     __syncthreads();
-    leaf_sylvester(ta, tb, tc, bm, bn, &bad);
+    if (g == 0) {
+        for (int h = 1; h < kSylGroups; ++h) {
+            const cplx<R> *ph = tc + TT * (1 + 4 * h);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q] += ph[r + (c0 + 4 * q) * TLD];
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) tc[r + (c0 + 4 * q) * TLD] = acc[q];
+    }
+    __syncthreads();
+    cplx<R> *la = tc + TT, *lb = la + TT;  // group 0's tiles, free now
+    load_tile(la, S + i0 + (int64_t)i0 * lds, lds, bm, bm);
+    load_tile(lb, St + j0 + (int64_t)j0 * ldst, ldst, bn, bn);
+    __syncthreads();
+    leaf_sylvester(la, lb, tc, bm, bn, &bad);
     for (int e = threadIdx.x; e < bm * bn; e += blockDim.x) {
         int i = e % bm, j = e / bm;
         C[(i0 + i) + (int64_t)(j0 + j) * ldc] = tc[i + j * TLD];
@@ -250,7 +289,7 @@ trisqrt_off_kernel(const cplx<R> *__restrict__ T, int ldt, cplx<R> *S, int lds, 
         cp_async_wait_all();
         __syncthreads();
         if (t + 1 < nterm) issue(t + 1, (t & 1) ? ta : ta2, (t & 1) ? tb : tb2);
-        tile_mms(acc, ca, cb, min(b, n - (I + 1 + t) * b));
+        tile_mms(acc, ca, cb, min(b, n - (I + 1 + t) * b), (int)threadIdx.x);
     }
     __syncthreads();
 #pragma unroll
@@ -301,7 +340,7 @@ cudaError_t launch_rtrsyl(const cplx<R> *S, int lds, int m, const cplx<R> *St, i
     if (m <= 0 || nn <= 0) return cudaSuccess;
     int b = blks < 1 ? 1 : (blks > TB ? TB : blks);
     int Mb = (m + b - 1) / b, Nb = (nn + b - 1) / b;
-    size_t sm3 = 5 * TB * TLD * sizeof(cplx<R>);
+    size_t sm3 = (1 + 4 * SylCfg<R>::G) * TB * TLD * sizeof(cplx<R>);
     cudaError_t err;
     if ((err = set_smem<R>((const void *)rtrsyl_wave_kernel<R>, sm3))) return err;
     for (int w = 0; w <= Mb + Nb - 2; ++w) {
@@ -309,7 +348,7 @@ cudaError_t launch_rtrsyl(const cplx<R> *S, int lds, int m, const cplx<R> *St, i
         int ihi = min(Mb - 1, (Mb - 1) - w + (Nb - 1));
         int cnt = ihi - ilo + 1;
         if (cnt <= 0) continue;
-        rtrsyl_wave_kernel<R><<<cnt, kTriThreads, sm3, s>>>(S, lds, m, St, ldst, nn, C, ldc, b, w, d_status); count_launch();
+        rtrsyl_wave_kernel<R><<<cnt, SylCfg<R>::THREADS, sm3, s>>>(S, lds, m, St, ldst, nn, C, ldc, b, w, d_status); count_launch();
     }
     return cudaGetLastError();
 }
