@@ -327,6 +327,211 @@ hess_cluster_kernel(cplx<R> *__restrict__ T, cplx<R> *__restrict__ Q, int n, int
     }
 }
 
+// The same reduction with the CTA's columns in registers (n <= 32 RPL <= 512,
+// at most 64 columns per CTA): lane l of warp w holds rows l + 32 q
+// (q < RPL) of the local columns w + 16 c (c < 4).  The owner of column k is
+// one warp, which forms the reflector with shuffles alone; the left
+// reflection is a warp dot product per column; the right one needs the
+// partial sums over the CTA's columns, reduced across the 16 warps in shared
+// memory and across the cluster through distributed shared memory.  Two
+// cluster barriers per column, as above, and the backward accumulation of Q
+// in the same registers.
+template <class R, int RPL>
+__global__ void __launch_bounds__(kHessClThreads, 1)
+hess_cluster_reg_kernel(cplx<R> *__restrict__ T, cplx<R> *__restrict__ Q, int n, int ld, R *__restrict__ Vg,
+                        R *__restrict__ betas)
+{
+    constexpr int NW = kHessClThreads / 32, CPW = 4, PLD = 32 * RPL + 1;
+    cg::cluster_group cl = cg::this_cluster();
+    const int CL = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ncl = rank < n ? (n - rank + CL - 1) / CL : 0;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    R *vbuf = reinterpret_cast<R *>(smraw);  // reflector of a column this CTA owns (32 RPL)
+    R *pbuf = vbuf + 32 * RPL;               // this CTA's part of u
+    R *ubuf = pbuf + 32 * RPL;               // u
+    R *vloc = ubuf + 32 * RPL;               // the current reflector
+    R *part = vloc + 32 * RPL;               // per-warp partial sums, NW x PLD
+    __shared__ R s_scal[2];
+    auto gcol = [&](int jl) { return rank + jl * CL; };
+    R h[CPW][RPL];
+#pragma unroll
+    for (int c = 0; c < CPW; ++c) {
+        const int jl = warp + NW * c;
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+            const int i = lane + 32 * q;
+            h[c][q] = (jl < ncl && i < n) ? T[i + (int64_t)gcol(jl) * ld].x : R(0);
+        }
+    }
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1, o = k % CL, jlk = k / CL;
+        if (rank == o && warp == jlk % NW) {
+            const int ck = jlk / NW;  // which of this warp's columns
+            auto colk = [&](int q) {  // row lane + 32 q of column k
+                R v = h[0][q];
+#pragma unroll
+                for (int c = 1; c < CPW; ++c) v = (ck == c) ? h[c][q] : v;
+                return v;
+            };
+            R a = 0, t = 0, x0 = 0;
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) {
+                const int i = lane + 32 * q;
+                const R xq = colk(q);
+                if (i >= k + 1) a = fma(xq, xq, a);
+                if (i >= k + 2) t = fma(xq, xq, t);
+                if (i == k + 1) x0 = xq;
+            }
+            a = warp_sum(a);
+            t = warp_sum(t);
+            x0 = __shfl_sync(0xffffffffu, x0, (k + 1) & 31);
+            R beta = 0, diag = x0, v0 = 0;
+            if (t != R(0)) {
+                const R xn = sqrt(a), sg = x0 < R(0) ? R(-1) : R(1);
+                v0 = x0 + sg * xn;
+                beta = R(2) / (v0 * v0 + t);
+                diag = -sg * xn;
+            }
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) {
+                const int i = lane + 32 * q;
+                if (i >= k + 1 && i < n) {
+                    const R vi = (i == k + 1) ? v0 : colk(q);
+                    vbuf[i - k - 1] = vi;
+                    Vg[i + (int64_t)k * n] = beta != R(0) ? vi : R(0);
+                    if (beta != R(0)) {
+                        const R nv = (i == k + 1) ? diag : R(0);
+#pragma unroll
+                        for (int c = 0; c < CPW; ++c)
+                            if (ck == c) h[c][q] = nv;
+                    }
+                }
+            }
+            if (lane == 0) {
+                s_scal[0] = beta;
+                betas[k] = beta;
+            }
+            __threadfence();
+        }
+        cl.sync();
+        const R beta = *cl.map_shared_rank(&s_scal[0], o);  // the same in every CTA
+        R vc[CPW];
+        if (beta != R(0)) {
+            const R *rv = cl.map_shared_rank(vbuf, o);
+            for (int i = tid; i < m; i += kHessClThreads) vloc[i] = rv[i];
+            __syncthreads();
+            R vr[RPL];
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) {
+                const int i = lane + 32 * q;
+                vr[q] = (i >= k + 1 && i < n) ? vloc[i - k - 1] : R(0);
+            }
+#pragma unroll
+            for (int c = 0; c < CPW; ++c) {
+                const int jl = warp + NW * c;
+                const bool act = jl < ncl && gcol(jl) > k;  // uniform per warp
+                vc[c] = act ? vloc[gcol(jl) - k - 1] : R(0);
+                if (act) {
+                    // P_k H: w = beta v^T h, h -= w v
+                    R d = 0;
+#pragma unroll
+                    for (int q = 0; q < RPL; ++q) d = fma(vr[q], h[c][q], d);
+                    d = warp_sum(d) * beta;
+#pragma unroll
+                    for (int q = 0; q < RPL; ++q) h[c][q] = fma(-d, vr[q], h[c][q]);
+                }
+            }
+            // this warp's part of u = H(:, k+1:n) v over its columns
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) {
+                R pq = 0;
+#pragma unroll
+                for (int c = 0; c < CPW; ++c) pq = fma(h[c][q], vc[c], pq);
+                part[warp * PLD + lane + 32 * q] = pq;
+            }
+            __syncthreads();
+            for (int i = tid; i < n; i += kHessClThreads) {
+                R sum = 0;
+#pragma unroll
+                for (int w2 = 0; w2 < NW; ++w2) sum += part[w2 * PLD + i];
+                pbuf[i] = sum;
+            }
+        }
+        cl.sync();
+        if (beta != R(0)) {
+            // H P_k: every CTA sums the parts in the same order
+            for (int i = tid; i < n; i += kHessClThreads) {
+                R u = 0;
+                for (int c = 0; c < CL; ++c) u += cl.map_shared_rank(pbuf, c)[i];
+                ubuf[i] = u * beta;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) {
+                const int i = lane + 32 * q;
+                const R uq = i < n ? ubuf[i] : R(0);
+#pragma unroll
+                for (int c = 0; c < CPW; ++c) h[c][q] = fma(-uq, vc[c], h[c][q]);
+            }
+        }
+        __syncthreads();
+    }
+    cl.sync();  // no CTA reads another's shared memory after this point
+#pragma unroll
+    for (int c = 0; c < CPW; ++c) {
+        const int jl = warp + NW * c;
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+            const int i = lane + 32 * q;
+            if (jl < ncl && i < n) T[i + (int64_t)gcol(jl) * ld] = cplx<R>{h[c][q], R(0)};
+            h[c][q] = (R)(i == gcol(jl));
+        }
+    }
+    // Q = P_0 ... P_{n-3}: Q <- P_k Q for k = n-3 .. 0
+    for (int k = n - 3; k >= 0; --k) {
+        const R beta = __ldcg(betas + k);
+        if (beta == R(0)) continue;
+        const int m = n - k - 1;
+        for (int i = tid; i < m; i += kHessClThreads) vloc[i] = __ldcg(Vg + (k + 1 + i) + (int64_t)k * n);
+        __syncthreads();
+        R vr[RPL];
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+            const int i = lane + 32 * q;
+            vr[q] = (i >= k + 1 && i < n) ? vloc[i - k - 1] : R(0);
+        }
+#pragma unroll
+        for (int c = 0; c < CPW; ++c) {
+            const int jl = warp + NW * c;
+            if (jl < ncl && gcol(jl) > k) {
+                R d = 0;
+#pragma unroll
+                for (int q = 0; q < RPL; ++q) d = fma(vr[q], h[c][q], d);
+                d = warp_sum(d) * beta;
+#pragma unroll
+                for (int q = 0; q < RPL; ++q) h[c][q] = fma(-d, vr[q], h[c][q]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int c = 0; c < CPW; ++c) {
+        const int jl = warp + NW * c;
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+            const int i = lane + 32 * q;
+            if (jl < ncl && i < n) Q[i + (int64_t)gcol(jl) * ld] = cplx<R>{h[c][q], R(0)};
+        }
+    }
+}
+
+template <class R, int RPL>
+static constexpr size_t hess_reg_smem()
+{
+    return ((size_t)4 * 32 * RPL + (size_t)(kHessClThreads / 32) * (32 * RPL + 1)) * sizeof(R);
+}
+
 static constexpr size_t kHessClSmemMax = 232448 - 1024;  // 227 KB opt-in per CTA, less the static arrays
 
 template <class R>
@@ -336,43 +541,100 @@ static size_t hess_cluster_smem(int n, int CL)
     return ((size_t)n * ncmax + 3 * (size_t)n) * sizeof(R);
 }
 
+// can a cluster of CL CTAs of `kernel` with `smem` bytes each be resident?
+static bool cluster_resident(const void *kernel, int CL, size_t smem)
+{
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(kHessClThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    const bool ok = cudaOccupancyMaxActiveClusters(&nclusters, kernel, &cfg) == cudaSuccess && nclusters > 0;
+    cudaGetLastError();
+    return ok;
+}
+
+// rows per lane of the register-resident kernel for n (0: not used; FP64
+// keeps at most 4 rows per lane in registers)
+template <class R>
+static int hess_reg_rpl(int n)
+{
+    const int r = n <= 64 ? 2 : n <= 128 ? 4 : n <= 256 ? 8 : n <= 512 ? 16 : 0;
+    return (sizeof(R) == sizeof(double) && r > 4) ? 0 : r;
+}
+
+template <class R>
+static const void *hess_reg_fn(int rpl)
+{
+    switch (rpl) {
+    case 2: return (const void *)hess_cluster_reg_kernel<R, 2>;
+    case 4: return (const void *)hess_cluster_reg_kernel<R, 4>;
+    case 8: return (const void *)hess_cluster_reg_kernel<R, sizeof(R) == sizeof(double) ? 4 : 8>;
+    default: return (const void *)hess_cluster_reg_kernel<R, sizeof(R) == sizeof(double) ? 4 : 16>;
+    }
+}
+
 // cluster size for an n x n matrix: the smallest that leaves at most 64
-// columns per CTA, else the largest that fits; 0 = too large (or no such
-// cluster can be resident), use launch_hessenberg
+// columns per CTA (register-resident kernel up to n = 512), else the largest
+// shared-memory layout that fits; 0 = too large (or no such cluster can be
+// resident), use launch_hessenberg
 template <class R>
 int hess_cluster_size(int n)
 {
     if (n < 3) return 0;
-    static std::atomic<int> resident[kHessClMax + 1];  // per CL: 0 unknown, 1 yes, -1 no
-    int pick = 0;
-    for (int CL = 1; CL <= kHessClMax; CL *= 2) {
-        if (hess_cluster_smem<R>(n, CL) > kHessClSmemMax) continue;
-        pick = CL;
-        if ((n + CL - 1) / CL <= 64) break;
+    // per kernel kind (0 = registers, 1 = shared memory) and CL: 0 unknown, 1 yes, -1 no
+    static std::atomic<int> resident[2][kHessClMax + 1];
+    const int rpl = hess_reg_rpl<R>(n);
+    int pick = 0, kind = 0;
+    if (rpl) {
+        for (int CL = 1; CL <= kHessClMax; CL *= 2)
+            if ((n + CL - 1) / CL <= 64) { pick = CL; break; }
+    } else {
+        kind = 1;
+        for (int CL = 1; CL <= kHessClMax; CL *= 2) {
+            if (hess_cluster_smem<R>(n, CL) > kHessClSmemMax) continue;
+            pick = CL;
+            if ((n + CL - 1) / CL <= 64) break;
+        }
     }
     if (!pick) return 0;
-    if (resident[pick].load() == 0) {
-        int ok = -1;
-        if (cudaFuncSetAttribute((const void *)hess_cluster_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kHessClSmemMax) == cudaSuccess) {
-            cudaLaunchConfig_t cfg = {};
-            cudaLaunchAttribute at[1];
-            at[0].id = cudaLaunchAttributeClusterDimension;
-            at[0].val.clusterDim.x = pick; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
-            cfg.gridDim = dim3(pick);
-            cfg.blockDim = dim3(kHessClThreads);
-            cfg.dynamicSmemBytes = kHessClSmemMax;
-            cfg.attrs = at;
-            cfg.numAttrs = 1;
-            int nclusters = 0;
-            if (cudaOccupancyMaxActiveClusters(&nclusters, (const void *)hess_cluster_kernel<R>, &cfg) == cudaSuccess &&
-                nclusters > 0)
-                ok = 1;
-        }
-        cudaGetLastError();
-        resident[pick].store(ok);
+    if (resident[kind][pick].load() == 0) {
+        const bool ok = kind == 0 ? cluster_resident(hess_reg_fn<R>(rpl), pick, hess_reg_smem<R, 16>())
+                                  : cluster_resident((const void *)hess_cluster_kernel<R>, pick, kHessClSmemMax);
+        resident[kind][pick].store(ok ? 1 : -1);
     }
-    return resident[pick].load() > 0 ? pick : 0;
+    return resident[kind][pick].load() > 0 ? pick : 0;
+}
+
+template <class R, int RPL>
+static cudaError_t launch_hess_reg(cplx<R> *T, cplx<R> *Q, int n, int ld, R *V, R *betas, int CL, cudaStream_t s)
+{
+    constexpr size_t smem = hess_reg_smem<R, RPL>();
+    cudaError_t err = cudaFuncSetAttribute((const void *)hess_cluster_reg_kernel<R, RPL>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err) return err;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(kHessClThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    err = cudaLaunchKernelEx(&cfg, hess_cluster_reg_kernel<R, RPL>, T, Q, n, ld, V, betas);
+    count_launch();
+    return err;
 }
 
 template <class R>
@@ -380,6 +642,13 @@ cudaError_t launch_hessenberg_cluster(cplx<R> *T, cplx<R> *Q, int n, int ld, R *
 {
     const int CL = hess_cluster_size<R>(n);
     if (!CL) return cudaErrorNotSupported;
+    switch (hess_reg_rpl<R>(n)) {
+    case 2: return launch_hess_reg<R, 2>(T, Q, n, ld, V, betas, CL, s);
+    case 4: return launch_hess_reg<R, 4>(T, Q, n, ld, V, betas, CL, s);
+    case 8: return launch_hess_reg<R, sizeof(R) == sizeof(double) ? 4 : 8>(T, Q, n, ld, V, betas, CL, s);
+    case 16: return launch_hess_reg<R, sizeof(R) == sizeof(double) ? 4 : 16>(T, Q, n, ld, V, betas, CL, s);
+    default: break;
+    }
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;

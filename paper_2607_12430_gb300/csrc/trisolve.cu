@@ -11,8 +11,10 @@
 // Block (I, J) needs only blocks on earlier wavefronts (J - I smaller for
 // trisqrt; larger I or smaller J for the Sylvester solve), so each wavefront
 // is one launch whose CTAs are independent.  Inside a CTA the sums are tile
-// products in shared memory and the leaf equation is solved by point
-// Bartels-Stewart substitution along anti-diagonals (4 threads per entry).
+// products in shared memory, dealt round-robin to groups of 128 threads
+// (partial sums added in group order), and the leaf equation is solved by
+// point Bartels-Stewart substitution along anti-diagonals (4 threads per
+// entry).
 // The recursion of Algorithm 1 computes the same block equations; only the
 // grouping of the update sums differs.
 #include "internal.h"
@@ -37,19 +39,8 @@ __device__ void load_tile(cplx<R> *dst, const cplx<R> *__restrict__ src, int ld,
 }
 
 // Same tile with cp.async for the in-range part (zero padding written
-// directly); complete with cp_async_wait_all() and a barrier.
-template <class R>
-__device__ void load_tile_async(cplx<R> *dst, const cplx<R> *__restrict__ src, int ld, int rows,
-                                int cols)
-{
-    for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-        int i = e % TB, j = e / TB;
-        if (i < rows && j < cols) cp_async_elem<R>(&dst[i + j * TLD], &src[i + (int64_t)j * ld]);
-        else dst[i + j * TLD] = cplx<R>{0, 0};
-    }
-}
-
-// The same for one 128-thread group: lt = thread index within the group.
+// directly), by one 128-thread group (lt = thread index within the group);
+// complete with cp_async_wait_all() and the group's barrier.
 template <class R>
 __device__ void load_tile_async_g(cplx<R> *dst, const cplx<R> *__restrict__ src, int ld, int rows, int cols, int lt)
 {
@@ -254,50 +245,64 @@ trisqrt_diag_kernel(const cplx<R> *__restrict__ T, int ldt, cplx<R> *S, int lds,
 }
 
 template <class R>
-__global__ void __launch_bounds__(kTriThreads)
+__global__ void __launch_bounds__(SylCfg<R>::THREADS)
 trisqrt_off_kernel(const cplx<R> *__restrict__ T, int ldt, cplx<R> *S, int lds, int n, int b,
                    int dblk, int *status)
 {
     extern __shared__ unsigned char smraw[];
+    constexpr int TT = TB * TLD, G = SylCfg<R>::G;
     cplx<R> *tc = reinterpret_cast<cplx<R> *>(smraw);
-    cplx<R> *ta = tc + TB * TLD;
-    cplx<R> *tb = ta + TB * TLD;
-    cplx<R> *ta2 = tb + TB * TLD;
-    cplx<R> *tb2 = ta2 + TB * TLD;
     __shared__ int bad;
     const int Nb = (n + b - 1) / b;
     const int I = blockIdx.x, J = I + dblk;
     if (J >= Nb) return;
+    const int g = threadIdx.x / kTriThreads, lt = threadIdx.x % kTriThreads;
+    cplx<R> *ta = tc + TT * (1 + 4 * g), *tb = ta + TT, *ta2 = tb + TT, *tb2 = ta2 + TT;
     if (threadIdx.x == 0) bad = 0;
     const int i0 = I * b, j0 = J * b;
     const int bm = min(b, n - i0), bn = min(b, n - j0);
     load_tile(tc, T + i0 + (int64_t)j0 * ldt, ldt, bm, bn);
     __syncthreads();
     cplx<R> acc[8];
-    const int r = threadIdx.x & 31, c0 = threadIdx.x >> 5;
+    const int r = lt & 31, c0 = lt >> 5;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = tc[r + (c0 + 4 * q) * TLD];
-    const int nterm = J - I - 1;  // K = I+1 .. J-1
+    for (int q = 0; q < 8; ++q) acc[q] = g == 0 ? tc[r + (c0 + 4 * q) * TLD] : cplx<R>{0, 0};
+    // K = I+1 .. J-1, dealt round-robin to the G groups of 128 threads
+    const int nterm = J - I - 1;
     auto issue = [&](int t, cplx<R> *da, cplx<R> *db) {
         const int k0 = (I + 1 + t) * b, bk = min(b, n - k0);
-        load_tile_async(da, S + i0 + (int64_t)k0 * lds, lds, bm, bk);
-        load_tile_async(db, S + k0 + (int64_t)j0 * lds, lds, bk, bn);
+        load_tile_async_g(da, S + i0 + (int64_t)k0 * lds, lds, bm, bk, lt);
+        load_tile_async_g(db, S + k0 + (int64_t)j0 * lds, lds, bk, bn, lt);
     };
-    if (nterm > 0) issue(0, ta, tb);
-    for (int t = 0; t < nterm; ++t) {
-        cplx<R> *ca = (t & 1) ? ta2 : ta, *cb = (t & 1) ? tb2 : tb;
+    if (g < nterm) issue(g, ta, tb);
+    for (int t = g, it = 0; t < nterm; t += G, ++it) {
+        cplx<R> *ca = (it & 1) ? ta2 : ta, *cb = (it & 1) ? tb2 : tb;
         cp_async_wait_all();
-        __syncthreads();
-        if (t + 1 < nterm) issue(t + 1, (t & 1) ? ta : ta2, (t & 1) ? tb : tb2);
-        tile_mms(acc, ca, cb, min(b, n - (I + 1 + t) * b), (int)threadIdx.x);
+        group_bar(g);
+        if (t + G < nterm) issue(t + G, (it & 1) ? ta : ta2, (it & 1) ? tb : tb2);
+        tile_mms(acc, ca, cb, min(b, n - (I + 1 + t) * b), lt);
     }
     __syncthreads();
+    if (g > 0) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) tc[r + (c0 + 4 * q) * TLD] = acc[q];
-    load_tile(ta, S + i0 + (int64_t)i0 * lds, lds, bm, bm);
-    load_tile(tb, S + j0 + (int64_t)j0 * lds, lds, bn, bn);
+        for (int q = 0; q < 8; ++q) ta[r + (c0 + 4 * q) * TLD] = acc[q];
+    }
     __syncthreads();
-    leaf_sylvester(ta, tb, tc, bm, bn, &bad);
+    if (g == 0) {
+        for (int h = 1; h < G; ++h) {
+            const cplx<R> *ph = tc + TT * (1 + 4 * h);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q] += ph[r + (c0 + 4 * q) * TLD];
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) tc[r + (c0 + 4 * q) * TLD] = acc[q];
+    }
+    __syncthreads();
+    cplx<R> *la = tc + TT, *lb = la + TT;
+    load_tile(la, S + i0 + (int64_t)i0 * lds, lds, bm, bm);
+    load_tile(lb, S + j0 + (int64_t)j0 * lds, lds, bn, bn);
+    __syncthreads();
+    leaf_sylvester(la, lb, tc, bm, bn, &bad);
     for (int q = threadIdx.x; q < bm * bn; q += blockDim.x) {
         int i = q % bm, j = q / bm;
         S[(i0 + i) + (int64_t)(j0 + j) * lds] = tc[i + j * TLD];
@@ -324,12 +329,12 @@ cudaError_t launch_trisqrt(const cplx<R> *T, int ldt, cplx<R> *S, int lds, int n
     if (n <= 0) return cudaSuccess;
     int b = blks < 1 ? 1 : (blks > TB ? TB : blks);
     int Nb = (n + b - 1) / b;
-    size_t sm1 = TB * TLD * sizeof(cplx<R>), sm3 = 5 * sm1;
+    size_t sm1 = TB * TLD * sizeof(cplx<R>), sm3 = (1 + 4 * SylCfg<R>::G) * sm1;
     cudaError_t err;
     if ((err = set_smem<R>((const void *)trisqrt_off_kernel<R>, sm3))) return err;
     trisqrt_diag_kernel<R><<<Nb, kTriThreads, sm1, s>>>(T, ldt, S, lds, n, b, d_status); count_launch();
     for (int dblk = 1; dblk < Nb; ++dblk)
-        trisqrt_off_kernel<R><<<Nb - dblk, kTriThreads, sm3, s>>>(T, ldt, S, lds, n, b, dblk, d_status); count_launch();
+        trisqrt_off_kernel<R><<<Nb - dblk, SylCfg<R>::THREADS, sm3, s>>>(T, ldt, S, lds, n, b, dblk, d_status); count_launch();
     return cudaGetLastError();
 }
 
