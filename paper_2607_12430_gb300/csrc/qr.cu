@@ -175,6 +175,107 @@ __device__ __forceinline__ void givens_approx<float>(cplx<float> x, cplx<float> 
 // one warp: lane j updates column j of a row rotation and row j of a column
 // rotation.  Only the active block is updated.  M is destroyed; out[0..nb-1]
 // receives the eigenvalues.
+template <class R>
+__device__ __forceinline__ cplx<R> shfl_c(cplx<R> v, int src)
+{
+    return cplx<R>{__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src)};
+}
+
+// One implicit single-shift sweep on rows / columns lo .. hi of the small
+// Hessenberg matrix M (ld LDM, one warp, lane j = column j in the row half
+// and row j in the column half of each rotation), optionally accumulating
+// the rotations into U (U <- U G^H).  The shared-memory copy is kept up to
+// date, but the entries the next step needs -- its rotation's x and y, the
+// 2 x 2 block where the row and column halves overlap, the next pair of rows
+// -- travel between lanes by shuffles from the lanes that computed them, so
+// a rotation costs no shared-memory round trip on the critical path.  The
+// arithmetic (and hence every value) is that of the plain two-phase sweep.
+template <class R, int LDM, bool ACC, bool APPROX>
+__device__ __forceinline__ void warp_sweep(cplx<R> *M, cplx<R> *U, int m, int lo, int hi, cplx<R> mu, int *nrot)
+{
+    const int lane = threadIdx.x & 31;
+    const int ccols = ACC ? m : hi + 1;  // the row half runs to this column (exclusive)
+    // row half of rotation k: lane j >= js holds p = M(k, j), q = M(k+1, j)
+    cplx<R> p{0, 0}, q{0, 0};
+    if (lane >= lo && lane < ccols) {
+        p = M[lo + lane * LDM];
+        q = M[(lo + 1) + lane * LDM];
+    }
+    cplx<R> x = shfl_c(p, lo), y = shfl_c(q, lo);
+    x = x - mu;
+    for (int k = lo; k < hi; ++k) {
+        const int js = (k == lo) ? k : k - 1;
+        // row k+2 of the columns right of k+1 is untouched until rotation k+1
+        cplx<R> nxt{0, 0};
+        if (k + 2 <= hi && lane >= k + 2 && lane < ccols) nxt = M[(k + 2) + lane * LDM];
+        const cplx<R> sub2 = (k + 2 <= hi) ? M[(k + 2) + (k + 1) * LDM] : cplx<R>{0, 0};
+        R c;
+        cplx<R> s, r;
+        if (APPROX) givens_approx(x, y, c, s, r);
+        else givens_fast(x, y, c, s, r);
+        const bool lj = lane >= js && lane < ccols;
+        cplx<R> np = c * p + s * q, nq = c * q - conj(s) * p;
+        if (lane == js && k > lo) {
+            np = r;
+            nq = cplx<R>{0, 0};
+        }
+        if (lj) {
+            M[k + lane * LDM] = np;
+            M[(k + 1) + lane * LDM] = nq;
+        }
+        // column half: rows lo .. min(k+2, hi) of columns k, k+1
+        const cplx<R> np_k1 = shfl_c(np, k + 1), nq_k = shfl_c(nq, k);
+        const int rmax = min(k + 2, hi);
+        cplx<R> pp{0, 0}, qq{0, 0};
+        if (lane == k) {
+            pp = np;
+            qq = np_k1;
+        } else if (lane == k + 1) {
+            pp = nq_k;
+            qq = nq;
+        } else if (lane == k + 2) {
+            pp = cplx<R>{0, 0};
+            qq = sub2;
+        } else if (lane >= (ACC ? 0 : lo) && lane < k) {
+            pp = M[lane + k * LDM];
+            qq = M[lane + (k + 1) * LDM];
+        }
+        const cplx<R> npp = c * pp + conj(s) * qq, nqq = c * qq - s * pp;
+        __syncwarp();  // the row half's stores land before the column half's
+        if (lane >= (ACC ? 0 : lo) && lane <= rmax) {
+            M[lane + k * LDM] = npp;
+            M[lane + (k + 1) * LDM] = nqq;
+        }
+        if (ACC && lane < m) {
+            const cplx<R> up = U[lane + k * LDM], uq = U[lane + (k + 1) * LDM];
+            U[lane + k * LDM] = c * up + conj(s) * uq;
+            U[lane + (k + 1) * LDM] = c * uq - s * up;
+        }
+        // the next rotation: x = M(k+1, k), y = M(k+2, k) as the column half
+        // left them; rows k+1, k+2 of columns k, k+1 from the column half
+        const cplx<R> a1 = shfl_c(npp, k + 1), b1 = shfl_c(nqq, k + 1);
+        const cplx<R> a2 = shfl_c(npp, k + 2), b2 = shfl_c(nqq, k + 2);
+        x = a1;
+        y = (k + 2 <= hi) ? a2 : cplx<R>{0, 0};
+        if (lane == k) {
+            p = a1;
+            q = a2;
+        } else if (lane == k + 1) {
+            p = b1;
+            q = b2;
+        } else {
+            p = nq;
+            q = nxt;
+        }
+        __syncwarp();
+        if (nrot) ++*nrot;
+    }
+}
+
+// Eigenvalues of a small upper Hessenberg matrix M (nb x nb, nb <= 32,
+// column-major, leading dimension LDM) by single-shift QR without vectors,
+// one warp (warp_sweep).  Only the active block is updated.  M is
+// destroyed; out[0..nb-1] receives the eigenvalues.
 template <class R, int LDM>
 __device__ void warp_small_eigvals(cplx<R> *M, int nb, cplx<R> *out)
 {
@@ -207,38 +308,8 @@ __device__ void warp_small_eigvals(cplx<R> *M, int nb, cplx<R> *out)
         }
         const cplx<R> mu = wilkinson(M[(hi - 1) + (hi - 1) * LDM], M[(hi - 1) + hi * LDM],
                                      M[hi + (hi - 1) * LDM], M[hi + hi * LDM]);
-        for (int k = lo; k < hi; ++k) {
-            // lane j < 32 owns column j of the row pair; x, y sit in column js
-            const int js = (k == lo) ? k : k - 1;
-            const bool lj = lane >= js && lane <= hi;
-            cplx<R> p{0, 0}, q{0, 0};
-            if (lj) {
-                p = M[k + lane * LDM];
-                q = M[(k + 1) + lane * LDM];
-            }
-            cplx<R> x{__shfl_sync(0xffffffffu, p.x, js), __shfl_sync(0xffffffffu, p.y, js)};
-            const cplx<R> y{__shfl_sync(0xffffffffu, q.x, js), __shfl_sync(0xffffffffu, q.y, js)};
-            if (k == lo) x = x - mu;
-            R c;
-            cplx<R> s, r;
-            givens_approx(x, y, c, s, r);
-            if (lj) {
-                cplx<R> np = c * p + s * q, nq = c * q - conj(s) * p;
-                if (lane == js && k > lo) {
-                    np = r;
-                    nq = cplx<R>{0, 0};
-                }
-                M[k + lane * LDM] = np;
-                M[(k + 1) + lane * LDM] = nq;
-            }
-            __syncwarp();
-            if (lane >= lo && lane <= min(k + 2, hi)) {
-                const cplx<R> pp = M[lane + k * LDM], qq = M[lane + (k + 1) * LDM];
-                M[lane + k * LDM] = c * pp + conj(s) * qq;
-                M[lane + (k + 1) * LDM] = c * qq - s * pp;
-            }
-            __syncwarp();
-        }
+        __syncwarp();
+        warp_sweep<R, LDM, false, true>(M, nullptr, nb, lo, hi, mu, nullptr);
     }
     if (hi == 0 && lane == 0) out[0] = M[0];
     __syncwarp();
@@ -291,43 +362,7 @@ __device__ bool warp_tiny_schur(cplx<R> *M, cplx<R> *U, int m, int *sweeps, int 
                            M[hi + hi * LDM]);
         }
         __syncwarp();
-        for (int k = lo; k < hi; ++k) {
-            const int js = (k == lo) ? k : k - 1;
-            const bool lj = lane >= js && lane < m;
-            cplx<R> p{0, 0}, q{0, 0};
-            if (lj) {
-                p = M[k + lane * LDM];
-                q = M[(k + 1) + lane * LDM];
-            }
-            cplx<R> x{__shfl_sync(0xffffffffu, p.x, js), __shfl_sync(0xffffffffu, p.y, js)};
-            const cplx<R> y{__shfl_sync(0xffffffffu, q.x, js), __shfl_sync(0xffffffffu, q.y, js)};
-            if (k == lo) x = x - mu;
-            R c;
-            cplx<R> s, r;
-            givens_fast(x, y, c, s, r);
-            if (lj) {
-                cplx<R> np = c * p + s * q, nq = c * q - conj(s) * p;
-                if (lane == js && k > lo) {
-                    np = r;
-                    nq = cplx<R>{0, 0};
-                }
-                M[k + lane * LDM] = np;
-                M[(k + 1) + lane * LDM] = nq;
-            }
-            __syncwarp();
-            if (lane <= min(k + 2, m - 1)) {
-                const cplx<R> pp = M[lane + k * LDM], qq = M[lane + (k + 1) * LDM];
-                M[lane + k * LDM] = c * pp + conj(s) * qq;
-                M[lane + (k + 1) * LDM] = c * qq - s * pp;
-            }
-            if (lane < m) {
-                const cplx<R> pp = U[lane + k * LDM], qq = U[lane + (k + 1) * LDM];
-                U[lane + k * LDM] = c * pp + conj(s) * qq;
-                U[lane + (k + 1) * LDM] = c * qq - s * pp;
-            }
-            __syncwarp();
-            ++nrot;
-        }
+        warp_sweep<R, LDM, true, false>(M, U, m, lo, hi, mu, &nrot);
     }
     *sweeps = nsw;
     *rots = nrot;

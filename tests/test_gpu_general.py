@@ -201,6 +201,22 @@ def test_sqrtm_mixed_general(n):
     assert oracle.rel_residual(X2.cpu().numpy(), A) <= 5 * n * U64
 
 
+@pytest.mark.parametrize("n", [600, 1024])
+def test_sqrtm_mixed_general_large(n):
+    # n = 600: the shared-memory layout of the cluster Hessenberg reduction
+    # (above 512); n = 1024: the two-launch-per-column reduction and the
+    # cooperative chase with 16 helper CTAs over several rounds
+    A = synth.shifted_gaussian(n, 3.0, seed=97 + n)
+    Xo = oracle.sqrtm_schur(A)
+    errs = []
+    for k in (2, 3):
+        X, info = mp.sqrtm_mixed(torch.from_numpy(A).cuda(), kind=mp.KIND_GENERAL, steps=k)
+        assert info["status"] == 0
+        errs.append(oracle.rel_err(X.cpu().numpy(), Xo))
+    assert min(errs) <= 1e-12, errs
+    assert oracle.rel_residual(X.cpu().numpy(), A) <= 5 * n * U64
+
+
 @pytest.mark.parametrize("n", [1, 3, 64, 201, 512])
 def test_sqrtm_schur_fp64(n):
     A = synth.shifted_gaussian(n, 3.0, seed=95 + n)
