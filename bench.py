@@ -112,7 +112,7 @@ def _peaks():
 # this workload (the chase runs in rounds, four launches per call here),
 # summed from the ncu capture summarised in profiles/qr_chase_general512.md;
 # valid only for the qr.cu it was taken with (SHA-256 below), else null.
-CHASE_TRAFFIC = {"sha256": "1e00164e90be5163226e7ebe48b181ce2b41461ae1fa07ef943e1b3914ac0378", "bytes": 4612352}
+CHASE_TRAFFIC = {"sha256": "01ef1a0c7f8ed99d845eb63e01146276d94d06590087393c1d09269a2f8f05ca", "bytes": 4749056}
 
 
 def _chase_traffic():

@@ -252,7 +252,6 @@ hess_cluster_kernel(cplx<R> *__restrict__ T, cplx<R> *__restrict__ Q, int n, int
             for (int i = tid; i < m; i += nt) Vg[(k + 1 + i) + (int64_t)k * n] = beta != R(0) ? vbuf[i] : R(0);
             if (beta != R(0))
                 for (int i = tid; i < m; i += nt) col[i] = (i == 0) ? s_scal[1] : R(0);
-            __threadfence();
         }
         cl.sync();
         const R beta = *cl.map_shared_rank(&s_scal[0], o);  // the same in every CTA
@@ -295,7 +294,8 @@ hess_cluster_kernel(cplx<R> *__restrict__ T, cplx<R> *__restrict__ Q, int n, int
         }
         __syncthreads();
     }
-    cl.sync();  // no CTA reads another's shared memory after this point
+    __threadfence();  // V and beta (global) before the other CTAs read them for Q
+    cl.sync();        // and no CTA reads another's shared memory after this point
     for (int e = tid; e < n * ncl; e += nt) {
         const int i = e % n, jl = e / n;
         T[i + (int64_t)gcol(jl) * ld] = cplx<R>{Hs[i + (size_t)jl * n], R(0)};
@@ -412,7 +412,6 @@ hess_cluster_reg_kernel(cplx<R> *__restrict__ T, cplx<R> *__restrict__ Q, int n,
                 s_scal[0] = beta;
                 betas[k] = beta;
             }
-            __threadfence();
         }
         cl.sync();
         const R beta = *cl.map_shared_rank(&s_scal[0], o);  // the same in every CTA
@@ -477,7 +476,8 @@ hess_cluster_reg_kernel(cplx<R> *__restrict__ T, cplx<R> *__restrict__ Q, int n,
         }
         __syncthreads();
     }
-    cl.sync();  // no CTA reads another's shared memory after this point
+    __threadfence();  // V and beta (global) before the other CTAs read them for Q
+    cl.sync();        // and no CTA reads another's shared memory after this point
 #pragma unroll
     for (int c = 0; c < CPW; ++c) {
         const int jl = warp + NW * c;
