@@ -1304,9 +1304,9 @@ int qr_rows_per_cta(int nmax)
     size_t per = (size_t)(std::max(nmax, 1) + 1) * sizeof(cplx<R>);
     size_t avail = 200 * 1024 - 2 * (size_t)RRMAX * RRMAX * sizeof(cplx<R>) - (size_t)std::max(nmax, 1) * sizeof(int);
     size_t r = avail / per;
-    // about 64 row blocks per matrix: the passes of the last round are not
+    // about 128 row blocks per matrix: the passes of the last round are not
     // overlapped with a chase, so they should spread over many SMs
-    const size_t want = (size_t)cdiv_i(std::max(nmax, 1), 64);
+    const size_t want = (size_t)cdiv_i(std::max(nmax, 1), 128);
     return (int)std::max<size_t>(1, std::min<size_t>(std::min<size_t>(32, r), want));
 }
 
