@@ -47,6 +47,22 @@ def _dist():
     return ws, rank
 
 
+def share_kstar(dist, kstar, device):
+    """Replicas: rank 0's step count k* (fixed against the oracle) on every rank."""
+    import torch
+    kt = torch.tensor([kstar if kstar is not None else 0], device=device)
+    dist.broadcast(kt, 0)
+    return int(kt.item())
+
+
+def slowest_rank_ms(dist, ms, device):
+    """Replicas: the time of the slowest rank (max over ranks)."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -197,9 +213,7 @@ def run_ours(args):
         if kstar is None:
             raise SystemExit(f"no step count reached {TARGET}: {errs}")
     if ws > 1:
-        kt = torch.tensor([kstar if kstar is not None else 0], device=dev)
-        dist.broadcast(kt, 0)
-        kstar = int(kt.item())
+        kstar = share_kstar(dist, kstar, dev)
 
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
@@ -236,9 +250,7 @@ def run_ours(args):
     step_ms = [s.elapsed_time(e) for s, e in evs]
     ms = statistics.mean(step_ms)
     if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = slowest_rank_ms(dist, ms, dev)
 
     # ---- phase breakdown (CUDA events recorded by the library on its stream) ----
     ph = {k: statistics.mean([i[k] for i in infos]) for k in
