@@ -214,8 +214,12 @@ trisqrt_diag_kernel(const cplx<R> *__restrict__ T, int ldt, cplx<R> *S, int lds,
         int i = threadIdx.x;
         cplx<R> t = ts[i + i * TLD];
         R at = hypot(t.x, t.y);
-        // eigenvalue on (or within rounding of) the closed negative real axis
-        if (t.x <= R(0) && fabs(t.y) <= R(10) * eps * at) bad = 1;
+        // eigenvalue on (or within rounding of) the closed negative real axis:
+        // a real eigenvalue of the real input comes out of the complex Schur
+        // form with an imaginary part of about u ||A_s|| (not u |t|), and the
+        // scaled matrix has ||A_s||_F / sqrt(n) in [1/4, 1), so "within
+        // rounding" is |Im t| <= max(10 u |t|, n u)
+        if (t.x <= R(0) && fabs(t.y) <= fmax(R(10) * eps * at, (R)n * eps)) bad = 1;
         ts[i + i * TLD] = csqrt_(t);
     }
     __syncthreads();

@@ -114,27 +114,39 @@ def hilbert(n: int) -> np.ndarray:
     return np.asfortranarray(1.0 / (i[:, None] + i[None, :] + 1.0))
 
 
-def table1_case(set_id: str, n: int, seed: int) -> np.ndarray:
-    """Table 1 generators.  Shift (the paper does not state it): bulk spectral
-    radius plus one -- nonsymmetric N(0,1): sqrt(n)+1; nonsymmetric U(0,1):
-    sqrt(n/12)+1 (the rank-one mean part n/2 is a positive real eigenvalue);
-    symmetric N(0,1): 2 sqrt(n)+1; symmetric U(0,1): 2 sqrt(n/12)+1; set VII:
-    H_n + 1e-6 I."""
+def table1_case(set_id: str, n: int, seed: int, bulk_shift_only: bool = False) -> np.ndarray:
+    """Table 1 generators.  The paper shifts the random sets so that their
+    real eigenvalues are strictly positive and safe from 0 without stating
+    the amount; here the shift is the bulk spectral radius plus one --
+    nonsymmetric N(0,1): sqrt(n)+1; nonsymmetric U(0,1): sqrt(n/12)+1 (the
+    rank-one mean part n/2 is a positive real eigenvalue); symmetric N(0,1):
+    2 sqrt(n)+1; symmetric U(0,1): 2 sqrt(n/12)+1 -- raised, where a draw's
+    edge eigenvalue falls further out, until every real eigenvalue is >= 1
+    (bulk_shift_only=True keeps the bulk shift).  Set VII: H_n + 1e-6 I."""
     g = rng(seed)
+    sym = set_id in ("V", "VI")
     if set_id in ("I", "III"):
-        A = g.uniform(0.0, 1.0, (n, n)); A[np.diag_indices(n)] += np.sqrt(n / 12.0) + 1.0
+        A = g.uniform(0.0, 1.0, (n, n)); shift = np.sqrt(n / 12.0) + 1.0
     elif set_id in ("II", "IV"):
-        A = g.standard_normal((n, n)); A[np.diag_indices(n)] += np.sqrt(n) + 1.0
+        A = g.standard_normal((n, n)); shift = np.sqrt(n) + 1.0
     elif set_id == "V":
         L = np.tril(g.uniform(0.0, 1.0, (n, n))); A = L + np.tril(L, -1).T
-        A[np.diag_indices(n)] += 2.0 * np.sqrt(n / 12.0) + 1.0
+        shift = 2.0 * np.sqrt(n / 12.0) + 1.0
     elif set_id == "VI":
         L = np.tril(g.standard_normal((n, n))); A = L + np.tril(L, -1).T
-        A[np.diag_indices(n)] += 2.0 * np.sqrt(n) + 1.0
+        shift = 2.0 * np.sqrt(n) + 1.0
     elif set_id == "VII":
         A = hilbert(n); A[np.diag_indices(n)] += 1e-6
+        return np.asfortranarray(A)
     else:
         raise ValueError(set_id)
+    if not bulk_shift_only:
+        ev = np.linalg.eigvalsh(A) if sym else np.linalg.eigvals(A)
+        ev = np.asarray(ev)
+        real = ev.real[np.abs(ev.imag) <= 1e-8 * np.abs(ev).max()] if not sym else ev
+        if real.size:
+            shift = max(shift, 1.0 - real.min())
+    A[np.diag_indices(n)] += shift
     return np.asfortranarray(A)
 
 

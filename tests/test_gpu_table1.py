@@ -1,0 +1,62 @@
+"""The paper's Table 1 test sets (Sec. 5) as a second accuracy suite.  Sets
+I-VI (random, shifted; the paper uses n = 2048 and 4096) at n = 512 against
+the FP64 Schur oracle: the paper reports that the refinement reaches double
+precision in 1-3 steps when the matrix is not too ill-conditioned (Sec. 5.1).
+Plus the input the shift must exclude: a real eigenvalue below zero has no
+real principal square root, and both methods must say so (status 2)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import U64
+
+pytestmark = pytest.mark.gpu
+
+mp = pytest.importorskip("paper_2607_12430_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    mp.lib()
+
+
+@pytest.mark.parametrize("sid", ["I", "II", "III", "IV", "V", "VI"])
+def test_table1_random_sets_reach_fp64_accuracy_in_1_to_3_steps(sid):
+    n = 512
+    A = synth.table1_case(sid, n, seed=20260712 + 20 + "I II III IV V VI".split().index(sid))
+    Xo = oracle.sqrtm_schur(A)
+    Ad = torch.from_numpy(A).cuda()
+    errs = []
+    for k in range(0, 5):
+        X, info = mp.sqrtm_mixed(Ad, steps=k)
+        assert info["status"] == 0
+        errs.append(oracle.rel_err(X.cpu().numpy(), Xo))
+    kstar = next((k for k, e in enumerate(errs) if e <= 1e-12), None)
+    assert kstar is not None and 1 <= kstar <= 3, errs
+    # the library's own stopping test (relative residual <= 1e-12)
+    X, info = mp.sqrtm_mixed(Ad)
+    assert info["status"] == 0 and 1 <= info["iterations"] <= 3
+    assert oracle.rel_residual(X.cpu().numpy(), A) <= 1e-12
+
+
+@pytest.mark.parametrize("seed", [119, 126])
+def test_real_negative_eigenvalue_status(seed):
+    # the bulk shift sqrt(n) + 1 alone leaves a real eigenvalue of these draws
+    # just below zero (about -0.06)
+    n = 256
+    A = synth.table1_case("II", n, seed=seed, bulk_shift_only=True)
+    ev = np.linalg.eigvals(A)
+    real = ev.real[np.abs(ev.imag) <= 1e-8 * np.abs(ev).max()]
+    assert real.min() < 0
+    for fn in (mp.sqrtm_mixed, mp.sqrtm_schur_fp64):
+        _, info = fn(torch.from_numpy(A).cuda(), raise_on_error=False, kind=mp.KIND_GENERAL)
+        assert info["status"] == 2, fn.__name__
+    # with the shift that keeps every real eigenvalue >= 1 it is an ordinary input
+    B = synth.table1_case("II", n, seed=seed)
+    X, info = mp.sqrtm_mixed(torch.from_numpy(B).cuda(), kind=mp.KIND_GENERAL)
+    assert info["status"] == 0
+    assert oracle.rel_residual(X.cpu().numpy(), B) <= 1e-12
