@@ -15,7 +15,9 @@
 //      T - lam I = L D+ L^T = U D- U^T (two lanes per eigenvalue, FP64):
 //      with r = argmin |D+_r + D-_r - (d_r - lam)|, z_r = 1,
 //      z_i = -(e_i / D+_i) z_{i+1} above r, z_{i+1} = -(e_i / D-_{i+1}) z_i
-//      below r, normalised;
+//      below r, normalised; members of eigenvalue clusters (closer than the
+//      eigenvalues' accuracy) are recomputed as the part of a pseudo-random
+//      vector orthogonal to every other eigenvector;
 //   4. V = Q Z: the reflectors applied to Z in blocks of 64 in compact WY
 //      form (three products per block).
 // Steps 2-3 are O(n^2) work; the O(n^3) steps 1 and 4 run in R.
@@ -29,6 +31,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "handle.h"
 #include "spd_internal.h"
@@ -589,6 +592,147 @@ __global__ void __launch_bounds__(32) twisted_kernel(const double *__restrict__ 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Eigenvalue clusters.  Twisted factorisations of eigenvalues that lie closer
+// together than the eigenvalues' own accuracy give (nearly) the same vector.
+// Eigenvalue j is a cluster member when
+//   lam_j - lam_{j-1} <= rtol max(|lam_j|, |lam_{j-1}|) + atol ||T||;
+// the members of one cluster are consecutive, and a member's vector is
+// recomputed as the part of a pseudo-random vector orthogonal to every
+// eigenvector outside its cluster and to the members of its cluster done
+// before it, by classical Gram-Schmidt in two passes, then normalised: for a
+// symmetric T the cluster's invariant subspace is the orthogonal complement
+// of the other eigenvectors (other clusters' vectors count with their
+// twisted approximations).  ZT row k = eigenvector k (ZT[k + i n]); mask[k]
+// = 0 for the members of the cluster in hand not yet done.
+// ---------------------------------------------------------------------------
+static constexpr int kClP = 8;  // row chunks of the projection products
+
+// clusters as member ranges [first[c], last[c]]; mask = 1 everywhere
+__global__ void cluster_scan_kernel(const double *__restrict__ lam, int n, double rtol, double atol_rel,
+                                    const double *__restrict__ bounds, int *__restrict__ first,
+                                    int *__restrict__ last, int *__restrict__ ncl, int *__restrict__ mask)
+{
+    if (blockIdx.x || threadIdx.x) return;
+    const double atol = atol_rel * fmax(fabs(bounds[0]), fabs(bounds[1]));
+    int m = 0;
+    bool prev = false;
+    mask[0] = 1;
+    for (int j = 1; j < n; ++j) {
+        mask[j] = 1;
+        const bool mem = lam[j] - lam[j - 1] <= rtol * fmax(fabs(lam[j]), fabs(lam[j - 1])) + atol;
+        if (mem && !prev) first[m++] = j;
+        if (mem) last[m - 1] = j;
+        prev = mem;
+    }
+    *ncl = m;
+}
+
+// x_i uniform in [-1, 1): a counter-based hash (SplitMix64 finaliser) of (j, i)
+__global__ void cluster_start_kernel(double *__restrict__ x, int n, int j)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t z = ((uint64_t)(uint32_t)j << 32 | (uint32_t)i) + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    x[i] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+// part[p n + k] = sum over the p-th chunk of i of ZT[k + i n] x_i
+__global__ void __launch_bounds__(256) cluster_dots_kernel(const double *__restrict__ ZT, const double *__restrict__ x,
+                                                           int n, double *__restrict__ part)
+{
+    __shared__ double xs[256];
+    const int k = blockIdx.x * 256 + threadIdx.x;
+    const int ilen = (n + kClP - 1) / kClP, i0 = blockIdx.y * ilen, i1 = min(n, i0 + ilen);
+    double acc = 0.0;
+    for (int t0 = i0; t0 < i1; t0 += 256) {
+        __syncthreads();
+        if (t0 + threadIdx.x < i1) xs[threadIdx.x] = x[t0 + threadIdx.x];
+        __syncthreads();
+        const int tn = min(256, i1 - t0);
+        if (k < n)
+            for (int t = 0; t < tn; ++t) acc = fma(ZT[k + (int64_t)(t0 + t) * n], xs[t], acc);
+    }
+    if (k < n) part[(int64_t)blockIdx.y * n + k] = acc;
+}
+
+// c_k = mask_k sum_p part[p n + k]
+__global__ void cluster_csum_kernel(const double *__restrict__ part, const int *__restrict__ mask, int n,
+                                    double *__restrict__ c)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    double acc = 0.0;
+    for (int p = 0; p < kClP; ++p) acc += part[(int64_t)p * n + k];
+    c[k] = mask[k] ? acc : 0.0;
+}
+
+// x_i -= sum_k c_k ZT[k + i n], one warp per i
+__global__ void __launch_bounds__(256) cluster_sub_kernel(const double *__restrict__ ZT, const double *__restrict__ c,
+                                                          int n, double *__restrict__ x)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;  // whole warps
+    double acc = 0.0;
+    for (int k = lane; k < n; k += 32) acc = fma(c[k], ZT[k + (int64_t)i * n], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) x[i] -= acc;
+}
+
+// ZT row j = x / ||x||, mask[j] = 1 (one CTA)
+__global__ void __launch_bounds__(256) cluster_store_kernel(double *__restrict__ ZT, int *__restrict__ mask,
+                                                            const double *__restrict__ x, int n, int j)
+{
+    __shared__ double red[8];
+    double a = 0.0;
+    for (int i = threadIdx.x; i < n; i += 256) a = fma(x[i], x[i], a);
+    a = warp_sum(a);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    __syncthreads();
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += red[q];
+    const double inv = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
+    for (int i = threadIdx.x; i < n; i += 256) ZT[j + (int64_t)i * n] = x[i] * inv;
+    if (threadIdx.x == 0) mask[j] = 1;
+}
+
+// the members' vectors (clusters of size >= 2); scratch: >= (kClP + 2) n doubles
+// + 3 n + 1 ints
+static cudaError_t fix_clusters(const double *lam, const double *bounds, int n, double rtol, double atol_rel,
+                                double *ZT, double *scratch, cudaStream_t s)
+{
+    double *part = scratch, *x = part + (size_t)kClP * n, *c = x + n;
+    int *first = (int *)(c + n), *last = first + n, *mask = last + n, *ncl = mask + n;
+    cluster_scan_kernel<<<1, 32, 0, s>>>(lam, n, rtol, atol_rel, bounds, first, last, ncl, mask); count_launch();
+    int m = 0;
+    cudaError_t err = cudaMemcpyAsync(&m, ncl, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (!err) err = cudaStreamSynchronize(s);
+    if (err || m == 0) return err;
+    std::vector<int> f(m), l(m);
+    if ((err = cudaMemcpyAsync(f.data(), first, sizeof(int) * m, cudaMemcpyDeviceToHost, s)) ||
+        (err = cudaMemcpyAsync(l.data(), last, sizeof(int) * m, cudaMemcpyDeviceToHost, s)))
+        return err;
+    if ((err = cudaStreamSynchronize(s))) return err;
+    const int g1 = (int)cdiv_i(n, 256);
+    for (int q = 0; q < m; ++q) {
+        if ((err = cudaMemsetAsync(mask + f[q], 0, sizeof(int) * (size_t)(l[q] - f[q] + 1), s))) return err;
+        for (int j = f[q]; j <= l[q]; ++j) {
+            cluster_start_kernel<<<g1, 256, 0, s>>>(x, n, j); count_launch();
+            for (int pass = 0; pass < 2; ++pass) {
+                cluster_dots_kernel<<<dim3(g1, kClP), 256, 0, s>>>(ZT, x, n, part); count_launch();
+                cluster_csum_kernel<<<g1, 256, 0, s>>>(part, mask, n, c); count_launch();
+                cluster_sub_kernel<<<(int)cdiv_i((int64_t)n * 32, 256), 256, 0, s>>>(ZT, c, n, x); count_launch();
+            }
+            cluster_store_kernel<<<1, 256, 0, s>>>(ZT, mask, x, n, j); count_launch();
+        }
+    }
+    return cudaGetLastError();
+}
+
 template <class R>
 cudaError_t launch_tridiag_eig(const R *A, int n, int ld, double *lam, double *ZT,
                                double *scratch, int chunk, cudaStream_t s)
@@ -623,6 +767,14 @@ cudaError_t launch_tridiag_eig(const R *A, int n, int ld, double *lam, double *Z
         int cnt = std::min(chunk, n - j0);
         twisted_kernel<<<(int)cdiv_i(2 * (int64_t)cnt, 32), 32, 0, s>>>(d, e, e2, n, bounds, lam, j0, cnt, Dp, Dm, ZT);
         count_launch();
+    }
+    // clusters: eigenvalues closer than their accuracy allows (FP32 method:
+    // 1e-10 relative, vectors needed to ~1e-5; FP64 method: 2u, to ~1e-8,
+    // which the Newton-Schulz step then squares)
+    {
+        const bool f32 = sizeof(R) == sizeof(float);
+        cudaError_t err = fix_clusters(lam, bounds, n, f32 ? 1e-5 : 1e-8, f32 ? 4.4e-11 : 2.2e-13, ZT, Dp, s);
+        if (err) return err;
     }
     return cudaGetLastError();
 }

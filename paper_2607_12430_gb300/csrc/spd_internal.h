@@ -49,8 +49,10 @@ cudaError_t launch_back_transform(const R *Y, int ldy, const R *betas, R *Z, int
 
 // Eigen-decomposition of the symmetric tridiagonal matrix held on the
 // diagonal / first subdiagonal of A (FP64 arithmetic): lam (ascending) and
-// ZT (row j = unit eigenvector j, n x n, ld n).  scratch: 2 n * chunk doubles
-// plus 2 n + 8.
+// ZT (row j = unit eigenvector j, n x n, ld n); eigenvectors of eigenvalue
+// clusters (closer than the eigenvalues' accuracy) are recomputed by
+// projection against all the others.  scratch: 2 n * chunk doubles plus
+// 7 n + 16.
 template <class R>
 cudaError_t launch_tridiag_eig(const R *A, int n, int ld, double *lam, double *ZT,
                                double *scratch, int chunk, cudaStream_t s);

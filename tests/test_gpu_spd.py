@@ -104,6 +104,28 @@ def test_sqrtm_schur_fp64_spd64():
     assert oracle.rel_err(X.cpu().numpy(), oracle.sqrtm_spd(A)) <= 1e-13
 
 
+@pytest.mark.parametrize("n,mult", [(64, 2), (256, 4), (256, 32), (512, 300), (1024, 1000)])
+def test_repeated_eigenvalue(n, mult):
+    # a repeated eigenvalue: the twisted factorisations of its copies would
+    # all return the same vector; both methods must still find an orthonormal
+    # basis of its eigenspace
+    g = np.random.default_rng(n + mult)
+    V = synth.haar_orthogonal(n, g)
+    lam = 10.0 ** g.uniform(-2, 2, n)
+    lam[:mult] = 0.5
+    A = (V * lam[None, :]) @ V.T
+    A = (A + A.T) / 2
+    Xo = oracle.sqrtm_from_eig(V, lam)
+    X, info = mp.sqrtm_schur_fp64(torch.from_numpy(A).cuda())
+    assert info["kind_used"] == mp.KIND_SPD
+    assert oracle.rel_err(X.cpu().numpy(), Xo) <= 1e-13
+    errs = []
+    for k in (2, 3, 4):
+        X, info = mp.sqrtm_mixed(torch.from_numpy(A).cuda(), steps=k)
+        errs.append(oracle.rel_err(X.cpu().numpy(), Xo))
+    assert min(errs) <= 1e-13, errs
+
+
 def test_spd_indefinite_status():
     A = np.diag([1.0, -1.0, 2.0, 3.0])
     _, info = mp.sqrtm_mixed(torch.from_numpy(A).cuda(), raise_on_error=False)

