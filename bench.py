@@ -369,6 +369,55 @@ def run_profile_mode(args):
     return 0
 
 
+def run_table1_suite(args):
+    """The paper's Table 1 test sets (Sec. 5) at the paper's sizes, one JSON
+    line per set: k* (the first correction count whose forward error against
+    the FP64 method on the same GPU -- the paper's ground truth is the FP64
+    Schur method -- is <= 1e-12), the CUDA-event time of sqrtm_mixed with k*
+    corrections and of sqrtm_schur_fp64 (mean of --steps runs after one
+    warm-up), and the library's own stopping test (tol 1e-12)."""
+    import torch
+    import paper_2607_12430_gb300 as mp
+    mp.lib()
+    sizes = {"I": 2048, "II": 2048, "III": 4096, "IV": 4096, "V": 4096, "VI": 4096, "VII": 1024}
+    sets = args.sets or list(sizes)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(max(1, args.steps)):
+            s_ = torch.cuda.Event(enable_timing=True)
+            e_ = torch.cuda.Event(enable_timing=True)
+            s_.record()
+            out = fn()
+            e_.record()
+            torch.cuda.synchronize()
+            ts.append(s_.elapsed_time(e_))
+        return statistics.mean(ts), out
+
+    for sid in sets:
+        n = sizes[sid]
+        A = torch.from_numpy(np.ascontiguousarray(synth.table1_case(sid, n, seed=synth.BASE_SEED + 10))).cuda()
+        ms64, (X64, i64) = timed(lambda: mp.sqrtm_schur_fp64(A, raise_on_error=False))
+        nx = X64.norm().item()
+        errs = []
+        kmax = 14 if sid == "VII" else 6
+        for k in range(kmax + 1):
+            X, info = mp.sqrtm_mixed(A, steps=k, raise_on_error=False)
+            errs.append((X - X64).norm().item() / nx)
+        kstar = next((k for k, e in enumerate(errs) if e <= 1e-12), None)
+        msk, (Xk, ik) = timed(lambda: mp.sqrtm_mixed(A, steps=kstar if kstar is not None else kmax,
+                                                     raise_on_error=False))
+        Xd, idf = mp.sqrtm_mixed(A, raise_on_error=False)
+        print(json.dumps({"suite": "table1", "set": sid, "n": n, "kind": int(ik["kind_used"]), "k_star": kstar,
+                          "errors_by_step": [float("%.3g" % e) for e in errs], "mixed_ms": msk,
+                          "fp64_ms": ms64, "fp64_status": int(i64["status"]),
+                          "default_status": int(idf["status"]), "default_iterations": int(idf["iterations"])}),
+              flush=True)
+    return 0
+
+
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--profile-mode", action="store_true",
@@ -381,11 +430,16 @@ def main():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--suite", choices=["table1"], default=None,
+                   help="the paper's Table 1 sets (one JSON line each) instead of the benchmark")
+    p.add_argument("--sets", nargs="*", default=None, help="--suite table1: which sets (default all)")
     args = p.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_mode:
         return run_profile_mode(args)
+    if args.suite == "table1":
+        return run_table1_suite(args)
     return run_ours(args)
 
 
