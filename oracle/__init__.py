@@ -14,6 +14,9 @@ Two layers:
   Algorithms 2 and 3 (residual, transform, Sylvester solve, back-transform,
   update), written in FP64 with plain matrix products as the only library
   primitive, plus Kronecker-form solves (Eq. (vec)) used as independent checks.
+* the principal cube root (Sec. 4, p = 3): the triangular cube root by its
+  point recurrence, the point solve of Eq. (3rd-order) and the FP64 Schur
+  method (C), with the refinement steps of Sec. 4 in numpy.
 
 Readings of the paper that the oracle fixes (the paper is silent on them):
 
@@ -59,6 +62,12 @@ def load(path):
     L.orc_bs_solve.restype = i
     L.orc_rtrsyl.argtypes = [i, i, P, i, P, i, P, i, i]
     L.orc_rtrsyl.restype = i
+    L.orc_tricbrt.argtypes = [i, P, i, P, i, P, i]
+    L.orc_tricbrt.restype = i
+    L.orc_rtrsyl3.argtypes = [i, i, P, i, P, i, P, i, P, i, P, i]
+    L.orc_rtrsyl3.restype = i
+    L.orc_cbrtm_schur.argtypes = [i, P, i, P, i, P, P, P, P]
+    L.orc_cbrtm_schur.restype = i
     return L
 
 
@@ -319,3 +328,116 @@ def rel_residual(X, A):
     X = np.asarray(X, dtype=np.float64)
     A = np.asarray(A, dtype=np.float64)
     return float(np.linalg.norm(X @ X - A) / np.linalg.norm(A))
+
+
+# ---------------------------------------------------------------------------
+# Principal cube root (Sec. 4, p = 3)
+# ---------------------------------------------------------------------------
+def tricbrt(T):
+    """``S = T^{1/3}`` of upper triangular ``T`` and ``V = S^2`` by the point
+    recurrence of the Schur method for p-th roots (Sec. 4): for i < j,
+    ``s_ij (s_ii^2 + s_ii s_jj + s_jj^2) = t_ij - s_ii sum s_ik s_kj -
+    sum s_ik v_kj`` (k strictly between i and j), ``v_ij = s_ij (s_ii + s_jj)
+    + sum s_ik s_kj``; ``s_ii`` the principal cube root (argument in
+    (-pi/3, pi/3]).  Returns (S, V)."""
+    n = T.shape[0]
+    Tf = _f(T, np.complex128)
+    S = np.zeros((n, n), dtype=np.complex128, order="F")
+    V = np.zeros((n, n), dtype=np.complex128, order="F")
+    st = lib().orc_tricbrt(n, _p(Tf), max(n, 1), _p(S), max(n, 1), _p(V), max(n, 1))
+    if st:
+        raise OracleError(st, "tricbrt")
+    return S, V
+
+
+def ccbrt(z):
+    """Principal cube root of a complex scalar (the 1-by-1 case of
+    ``tricbrt``, whose diagonal step it is)."""
+    return tricbrt(np.array([[complex(z)]]))[0][0, 0]
+
+
+def rtrsyl3(S, V, St, Vt, C):
+    """Point solve of ``S^2 Y + S Y St + Y St^2 = C`` (Eq. (3rd-order)),
+    ``V = S^2``, ``Vt = St^2``, upper triangular."""
+    m, n = C.shape
+    Y = _f(C, np.complex128)
+    args = []
+    for M in (S, V, St, Vt):
+        Mf = _f(M, np.complex128)
+        args.append(Mf)
+    st = lib().orc_rtrsyl3(m, n, _p(args[0]), max(m, 1), _p(args[1]), max(m, 1), _p(args[2]), max(n, 1),
+                           _p(args[3]), max(n, 1), _p(Y), max(m, 1))
+    if st:
+        raise OracleError(st, "rtrsyl3")
+    return Y
+
+
+def sylvester3_kron(S, St, C):
+    """Kronecker-form solve of Eq. (3rd-order):
+    ``(I (x) S^2 + St^T (x) S + (St^2)^T (x) I) vec(Y) = vec(C)``."""
+    m, n = C.shape
+    S = np.asarray(S, dtype=np.complex128)
+    St = np.asarray(St, dtype=np.complex128)
+    K = np.kron(np.eye(n), S @ S) + np.kron(St.T, S) + np.kron((St @ St).T, np.eye(m))
+    y = np.linalg.solve(K, np.asarray(C, dtype=np.complex128).reshape(-1, order="F"))
+    return y.reshape((m, n), order="F")
+
+
+def cbrtm_schur(A, return_factors=False):
+    """The FP64 Schur method for the principal cube root (Sec. 4):
+    ``X = Q T^{1/3} Q^H``, real part for real ``A``."""
+    n = A.shape[0]
+    Af = _f(A, np.float64)
+    X = np.zeros((n, n), dtype=np.float64, order="F")
+    Q, T, S, V = (np.zeros((n, n), dtype=np.complex128, order="F") for _ in range(4))
+    st = lib().orc_cbrtm_schur(n, _p(Af), max(n, 1), _p(X), max(n, 1), _p(Q), _p(T), _p(S), _p(V))
+    if st:
+        raise OracleError(st, "cbrtm_schur")
+    if return_factors:
+        return X, Q, T, S, V
+    return X
+
+
+def scale_exponent3(A):
+    """Power-of-8 scaling for the cube root: ``e`` such that
+    ``A_s = 8^-e A`` has ``||A_s||_F / sqrt(n)`` in ``[1/8, 1)``; then
+    ``A^{1/3} = 2^e A_s^{1/3}`` exactly.  With ``r = m 2^p``, ``m`` in
+    ``[1/2, 1)``: ``e = ceil(p / 3)``."""
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[0]
+    if n == 0:
+        return 0
+    r = math.sqrt(float(np.sum(A * A)) / n)
+    if r == 0.0 or not math.isfinite(r):
+        return 0
+    _, p = math.frexp(r)
+    return -((-p) // 3)
+
+
+def residual3(A, X):
+    """Sec. 4 step 2 (p = 3): ``R = A - X^3`` in working precision."""
+    X = np.asarray(X, dtype=np.float64)
+    R = np.asarray(A, dtype=np.float64) - X @ (X @ X)
+    return R, float(np.linalg.norm(R))
+
+
+def refine3(A, Q, S, V, X0, steps):
+    """Sec. 4 steps 2-4 (p = 3) with frozen factors and the stopping test
+    nullified: ``R = A - X^3``; ``Y`` solves Eq. (3rd-order) with ``St = S``
+    for ``Q^H R Q``; ``X += Re(Q Y Q^H)``; all in FP64.  Returns the iterates
+    ``[X0, ..., X_steps]``."""
+    X = np.asarray(X0, dtype=np.float64).copy()
+    out = [X.copy()]
+    for _ in range(steps):
+        R, _ = residual3(A, X)
+        Y = rtrsyl3(S, V, S, V, transform_in(Q, R))
+        X = X + transform_out(Q, Y)
+        out.append(X.copy())
+    return out
+
+
+def rel_residual3(X, A):
+    """``||X^3 - A||_F / ||A||_F``."""
+    X = np.asarray(X, dtype=np.float64)
+    A = np.asarray(A, dtype=np.float64)
+    return float(np.linalg.norm(X @ (X @ X) - A) / np.linalg.norm(A))

@@ -458,3 +458,121 @@ int orc_rtrsyl(int m, int n, const zc *S, int lds, const zc *St, int ldst, zc *C
     orc_gemm_sub(m1, n2, n1, C11, ldc, St12, ldst, C12, ldc);
     return orc_rtrsyl(m1, n2, S, lds, St22, ldst, C12, ldc, blks);
 }
+
+/* ---------------------------------------------------------------------------
+ * Principal cube root (Sec. 4, p = 3).
+ *
+ * orc_ccbrt: z^(1/3) = |z|^(1/3) e^(i arg(z) / 3) with arg in (-pi, pi], the
+ * root whose argument lies in (-pi/3, pi/3] (the sector of the principal
+ * root).
+ *
+ * orc_tricbrt: S = T^(1/3) of upper triangular T (the Schur method for p-th
+ * roots, Sec. 4), with V = S^2 kept alongside: from T = S V and V = S S,
+ * for i < j (superdiagonal by superdiagonal)
+ *   s_ij (s_ii^2 + s_ii s_jj + s_jj^2)
+ *       = t_ij - s_ii sum_{i<k<j} s_ik s_kj - sum_{i<k<j} s_ik v_kj,
+ *   v_ij = s_ij (s_ii + s_jj) + sum_{i<k<j} s_ik s_kj.
+ *
+ * orc_rtrsyl3: S^2 Y + S Y St + Y St^2 = C (Eq. (3rd-order)), S (m x m) and
+ * St (n x n) upper triangular with V = S^2, Vt = St^2 given, point by point
+ * in the order of Bartels-Stewart (column j left to right, row i bottom to
+ * top), with W = Y St kept alongside:
+ *   y_ij (v_ii + s_ii st_jj + vt_jj) = c_ij - sum_{k>i} v_ik y_kj
+ *       - sum_{l<j} y_il vt_lj - s_ii w'_ij - sum_{k>i} s_ik w_kj,
+ *   w'_ij = sum_{l<j} y_il st_lj,  w_ij = w'_ij + y_ij st_jj.
+ * ------------------------------------------------------------------------- */
+zc orc_ccbrt(zc z)
+{
+    double r = cabs(z);
+    if (r == 0.0) return 0.0;
+    double th = carg(z) / 3.0;
+    double m = cbrt(r);
+    return m * cos(th) + I * (m * sin(th));
+}
+
+int orc_tricbrt(int n, const zc *T, int ldt, zc *S, int lds, zc *V, int ldv)
+{
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) { S[IDX(i, j, lds)] = 0.0; V[IDX(i, j, ldv)] = 0.0; }
+    for (int j = 0; j < n; ++j) {
+        zc s = orc_ccbrt(T[IDX(j, j, ldt)]);
+        S[IDX(j, j, lds)] = s;
+        V[IDX(j, j, ldv)] = s * s;
+    }
+    for (int d = 1; d < n; ++d) {
+        for (int i = 0; i + d < n; ++i) {
+            int j = i + d;
+            zc sv = 0.0, st = 0.0;
+            for (int k = i + 1; k < j; ++k) {
+                sv += S[IDX(i, k, lds)] * S[IDX(k, j, lds)];
+                st += S[IDX(i, k, lds)] * V[IDX(k, j, ldv)];
+            }
+            zc si = S[IDX(i, i, lds)], sj = S[IDX(j, j, lds)];
+            zc den = si * si + si * sj + sj * sj;
+            if (den == 0.0) return 2;
+            zc sij = (T[IDX(i, j, ldt)] - si * sv - st) / den;
+            S[IDX(i, j, lds)] = sij;
+            V[IDX(i, j, ldv)] = sij * (si + sj) + sv;
+        }
+    }
+    return 0;
+}
+
+int orc_rtrsyl3(int m, int n, const zc *S, int lds, const zc *V, int ldv, const zc *St, int ldst,
+                const zc *Vt, int ldvt, zc *C, int ldc)
+{
+    zc *W = (zc *)calloc((size_t)(m > 0 ? m : 1) * (size_t)(n > 0 ? n : 1), sizeof(zc));
+    if (!W) return 7;
+    for (int j = 0; j < n; ++j) {
+        for (int i = m - 1; i >= 0; --i) {
+            zc acc = C[IDX(i, j, ldc)];
+            zc wp = 0.0;
+            for (int l = 0; l < j; ++l) wp += C[IDX(i, l, ldc)] * St[IDX(l, j, ldst)];
+            for (int k = i + 1; k < m; ++k)
+                acc -= V[IDX(i, k, ldv)] * C[IDX(k, j, ldc)] + S[IDX(i, k, lds)] * W[IDX(k, j, m)];
+            for (int l = 0; l < j; ++l) acc -= C[IDX(i, l, ldc)] * Vt[IDX(l, j, ldvt)];
+            acc -= S[IDX(i, i, lds)] * wp;
+            zc den = V[IDX(i, i, ldv)] + S[IDX(i, i, lds)] * St[IDX(j, j, ldst)] + Vt[IDX(j, j, ldvt)];
+            if (den == 0.0) { free(W); return 2; }
+            zc y = acc / den;
+            C[IDX(i, j, ldc)] = y;
+            W[IDX(i, j, m)] = wp + y * St[IDX(j, j, ldst)];
+        }
+    }
+    free(W);
+    return 0;
+}
+
+/* X = Q T^(1/3) Q^H (real part), the FP64 Schur method for the cube root */
+int orc_cbrtm_schur(int n, const double *A, int lda, double *X, int ldx, zc *Qout, zc *Tout, zc *Sout,
+                    zc *Vout)
+{
+    size_t nn = (size_t)n * (size_t)n;
+    if (nn == 0) nn = 1;
+    zc *T = (zc *)calloc(nn, sizeof(zc));
+    zc *Q = (zc *)calloc(nn, sizeof(zc));
+    zc *S = (zc *)calloc(nn, sizeof(zc));
+    zc *V = (zc *)calloc(nn, sizeof(zc));
+    zc *W = (zc *)calloc(nn, sizeof(zc));
+    zc *P = (zc *)calloc(nn, sizeof(zc));
+    int st = orc_schur(n, A, lda, Q, T);
+    if (st == 0) {
+        for (int i = 0; i < n; ++i) {
+            zc t = T[IDX(i, i, n)];
+            if (creal(t) <= 0.0 && cimag(t) == 0.0) st = 2;
+        }
+    }
+    if (st == 0) st = orc_tricbrt(n, T, n, S, n, V, n);
+    if (st == 0) {
+        orc_zgemm('N', 'N', n, 1.0, Q, n, S, n, 0.0, W, n);
+        orc_zgemm('N', 'C', n, 1.0, W, n, Q, n, 0.0, P, n); /* P = Q S Q^H */
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) X[IDX(i, j, ldx)] = creal(P[IDX(i, j, n)]);
+    }
+    if (Qout) memcpy(Qout, Q, sizeof(zc) * (size_t)n * (size_t)n);
+    if (Tout) memcpy(Tout, T, sizeof(zc) * (size_t)n * (size_t)n);
+    if (Sout) memcpy(Sout, S, sizeof(zc) * (size_t)n * (size_t)n);
+    if (Vout) memcpy(Vout, V, sizeof(zc) * (size_t)n * (size_t)n);
+    free(T); free(Q); free(S); free(V); free(W); free(P);
+    return st;
+}

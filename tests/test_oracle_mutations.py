@@ -42,6 +42,12 @@ MUTATIONS = [
      "double tau = (A[IDX(p, p, lda)] - A[IDX(q, q, lda)]) / (2.0 * apq);"),
     ("schur_final_product_no_conj", "orc_zgemm('N', 'C', n, 1.0, W, n, Q, n, 0.0, P, n);",
      "orc_zgemm('N', 'N', n, 1.0, W, n, Q, n, 0.0, P, n);"),
+    ("tricbrt_drops_cross_term", "zc den = si * si + si * sj + sj * sj;", "zc den = si * si + sj * sj;"),
+    ("tricbrt_v_update_drops_sum", "V[IDX(i, j, ldv)] = sij * (si + sj) + sv;", "V[IDX(i, j, ldv)] = sij * (si + sj);"),
+    ("ccbrt_other_branch", "double th = carg(z) / 3.0;", "double th = (carg(z) + 6.283185307179586) / 3.0;"),
+    ("rtrsyl3_w_without_new_entry", "W[IDX(i, j, m)] = wp + y * St[IDX(j, j, ldst)];", "W[IDX(i, j, m)] = wp;"),
+    ("rtrsyl3_transposed_vt", "for (int l = 0; l < j; ++l) acc -= C[IDX(i, l, ldc)] * Vt[IDX(l, j, ldvt)];",
+     "for (int l = 0; l < j; ++l) acc -= C[IDX(i, l, ldc)] * Vt[IDX(j, l, ldvt)];"),
 ]
 
 
@@ -99,6 +105,35 @@ def _checks(orc):
             ok &= np.linalg.norm(orc.bs_solve(S, St, C) - Yk) <= 1e4 * U * np.linalg.norm(Yk)
         return ok
     run("rtrsyl_kron", rtrsyl_kron)
+
+    def cbrtm_residual():
+        X = orc.cbrtm_schur(A)
+        ev = np.linalg.eigvals(X)
+        return orc.rel_residual3(X, A) <= 10 * 20 * U and np.all(np.abs(np.angle(ev)) < np.pi / 3)
+    run("cbrtm_residual", cbrtm_residual)
+
+    def tricbrt_cube():
+        S0 = synth.random_upper_rhp(9, seed=4, re_lo=1.0)  # diagonal within |arg| < pi/4
+        S, V = orc.tricbrt(np.triu(S0 @ S0 @ S0))
+        return (np.linalg.norm(S - S0) <= 1e4 * U * np.linalg.norm(S0)
+                and np.linalg.norm(V - S0 @ S0) <= 1e4 * U * np.linalg.norm(S0 @ S0))
+    run("tricbrt_cube", tricbrt_cube)
+
+    def ccbrt_values():
+        return abs(orc.ccbrt(-8.0) - (1 + 3 ** 0.5 * 1j)) < 1e-14 and abs(orc.ccbrt(8j) - (3 ** 0.5 + 1j)) < 1e-14
+    run("ccbrt_values", ccbrt_values)
+
+    def rtrsyl3_kron():
+        ok = True
+        for m, n in ((9, 9), (7, 3), (3, 7), (1, 1)):
+            S = synth.random_upper_rhp(m, seed=m + 1, re_lo=1.0)
+            St = synth.random_upper_rhp(n, seed=60 + n, re_lo=1.0)
+            C = synth.gaussian((m, n), seed=m * n + 1) + 0j
+            Yk = orc.sylvester3_kron(S, St, C)
+            Y = orc.rtrsyl3(S, S @ S, St, St @ St, C)
+            ok &= np.linalg.norm(Y - Yk) <= 1e4 * U * np.linalg.norm(Yk)
+        return ok
+    run("rtrsyl3_kron", rtrsyl3_kron)
 
     def jacobi():
         As, V, lam = synth.spd_case(12, -1, 1, seed=9)

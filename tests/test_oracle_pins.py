@@ -372,3 +372,90 @@ def test_refinement_spd_diag_solve(orc):
     e = [orc.rel_err(Xi, Xtrue) for Xi in its]
     assert e[0] > 1e-7
     assert e[-1] <= 1e-13
+
+
+# ---------------------------------------------------------------------------
+# principal cube root (Sec. 4, p = 3)
+# ---------------------------------------------------------------------------
+def test_tricbrt_exact_integer_case(orc):
+    # S = [[2, 1], [0, 3]]: T = S^3 = [[8, 19], [0, 27]] has this exact root
+    T = np.array([[8.0, 19.0], [0.0, 27.0]], dtype=np.complex128)
+    S, V = orc.tricbrt(T)
+    # (the C library's cbrt need not be correctly rounded: a few ulps)
+    assert np.abs(S - np.array([[2.0, 1.0], [0.0, 3.0]])).max() <= 8 * U * 3.0
+    assert np.abs(V - np.array([[4.0, 5.0], [0.0, 9.0]])).max() <= 16 * U * 9.0
+
+
+def test_ccbrt_principal_branch(orc):
+    # the root with argument in (-pi/3, pi/3]; -8 sits on the branch cut
+    # (argument pi), whose root is 2 e^{i pi/3}
+    for z, w in ((27.0, 3.0), (-8.0, 1 + 3 ** 0.5 * 1j), (8j, 3 ** 0.5 + 1j), (-8j, 3 ** 0.5 - 1j)):
+        assert abs(orc.ccbrt(z) - w) <= 4 * U * abs(w)
+
+
+@pytest.mark.parametrize("n", [1, 5, 16, 40])
+def test_tricbrt_cubes_back(orc, n):
+    S0 = synth.random_upper_rhp(n, seed=300 + n, re_lo=1.0)
+    T = np.triu(S0 @ S0 @ S0)
+    S, V = orc.tricbrt(T)
+    assert np.linalg.norm(S - S0) <= 1e3 * n * U * np.linalg.norm(S0)
+    assert np.linalg.norm(V - S @ S) <= 100 * n * U * np.linalg.norm(V)
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (6, 6), (9, 4), (4, 9)])
+def test_rtrsyl3_matches_kronecker_solve(orc, m, n):
+    S = synth.random_upper_rhp(m, seed=310 + m, re_lo=1.0)
+    St = synth.random_upper_rhp(n, seed=320 + n, re_lo=1.0)
+    C = synth.gaussian((m, n), seed=330 + m * n) + 1j * synth.gaussian((m, n), seed=331 + m * n)
+    Yk = orc.sylvester3_kron(S, St, C)
+    Y = orc.rtrsyl3(S, S @ S, St, St @ St, C)
+    assert np.linalg.norm(Y - Yk) <= 1e3 * U * np.linalg.norm(Yk)
+    # the equation itself
+    assert np.linalg.norm(S @ S @ Y + S @ Y @ St + Y @ St @ St - C) <= 1e3 * U * np.linalg.norm(C)
+
+
+@pytest.mark.parametrize("n", [3, 30, 80])
+def test_cbrtm_schur_against_scipy_and_residual(orc, n):
+    A = synth.shifted_gaussian(n, 3.0, seed=340 + n)
+    X = orc.cbrtm_schur(A)
+    assert orc.rel_residual3(X, A) <= 10 * n * U
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    Xs = scipy_linalg.fractional_matrix_power(A, 1.0 / 3.0)
+    assert np.linalg.norm(Xs.imag) <= 1e-12 * np.linalg.norm(Xs)
+    assert orc.rel_err(X, Xs.real) <= 1e-12
+    ev = np.linalg.eigvals(X)
+    assert np.all(np.abs(np.angle(ev)) < np.pi / 3)
+
+
+def test_cbrtm_schur_known_similarity(orc):
+    # A = P diag(d^3) P^-1 has the principal cube root P diag(d) P^-1 (d real > 0)
+    g = np.random.default_rng(350)
+    n = 12
+    P = np.eye(n) + 0.3 * g.standard_normal((n, n))
+    d = g.uniform(0.5, 2.0, n)
+    A = P @ np.diag(d ** 3) @ np.linalg.inv(P)
+    X = orc.cbrtm_schur(A)
+    Xk = P @ np.diag(d) @ np.linalg.inv(P)
+    assert orc.rel_err(X, Xk) <= 1e-12
+
+
+def test_cbrtm_scaling_exponent(orc):
+    for r in (1e-9, 0.3, 1.0, 7.0, 1e12):
+        A = np.full((4, 4), r)
+        e = orc.scale_exponent3(A)
+        rs = np.linalg.norm(A * 8.0 ** -e) / 2.0
+        assert 1 / 8 <= rs < 1
+
+
+def test_refine3_contracts(orc):
+    # Sec. 4 steps 2-4 with the exact factors from a perturbed start: the
+    # correction is Newton's with a frozen derivative, so each step gains
+    # several digits until rounding
+    n = 20
+    A = synth.shifted_gaussian(n, 3.0, seed=360)
+    X, Q, T, S, V = orc.cbrtm_schur(A, return_factors=True)
+    X0 = X + 1e-6 * synth.gaussian((n, n), seed=361)
+    its = orc.refine3(A, Q, S, V, X0, 3)
+    errs = [orc.rel_err(Xk, X) for Xk in its]
+    assert errs[1] <= 1e-3 * errs[0]
+    assert errs[2] <= 1e-13
