@@ -126,9 +126,9 @@ def _peaks():
 # ---------------------------------------------------------------------------
 # DRAM bytes (read + write) of the qr_chase_kernel launches of one call on
 # this workload (the chase runs in rounds, four launches per call here),
-# summed from the ncu capture summarised in profiles/qr_chase_general512.md;
+# summed from the ncu dram-bytes capture summarised in profiles/qr_chase_general512.md;
 # valid only for the qr.cu it was taken with (SHA-256 below), else null.
-CHASE_TRAFFIC = {"sha256": "01ef1a0c7f8ed99d845eb63e01146276d94d06590087393c1d09269a2f8f05ca", "bytes": 4749056}
+CHASE_TRAFFIC = {"sha256": "69f21d6b266a5db47f1462c0f9b583861d87620d8a3668790e3b8461c38c2a20", "bytes": 5474560}
 
 
 def _chase_traffic():
@@ -369,18 +369,13 @@ def run_profile_mode(args):
     return 0
 
 
-def run_table1_suite(args):
-    """The paper's Table 1 test sets (Sec. 5) at the paper's sizes, one JSON
-    line per set: k* (the first correction count whose forward error against
-    the FP64 method on the same GPU -- the paper's ground truth is the FP64
-    Schur method -- is <= 1e-12), the CUDA-event time of sqrtm_mixed with k*
-    corrections and of sqrtm_schur_fp64 (mean of --steps runs after one
-    warm-up), and the library's own stopping test (tol 1e-12)."""
+def _suite_case(args, suite, label, n, A, mixed, fp64, kmax):
+    """One suite line: k* (the first correction count whose forward error
+    against the FP64 Schur method on the same GPU is <= 1e-12), the
+    CUDA-event time of the mixed method with k* corrections and of the FP64
+    method (mean of --steps runs after one warm-up), and the library's own
+    stopping test (tol 1e-12)."""
     import torch
-    import paper_2607_12430_gb300 as mp
-    mp.lib()
-    sizes = {"I": 2048, "II": 2048, "III": 4096, "IV": 4096, "V": 4096, "VI": 4096, "VII": 1024}
-    sets = args.sets or list(sizes)
 
     def timed(fn):
         fn()
@@ -396,25 +391,55 @@ def run_table1_suite(args):
             ts.append(s_.elapsed_time(e_))
         return statistics.mean(ts), out
 
-    for sid in sets:
+    ms64, (X64, i64) = timed(lambda: fp64(A, raise_on_error=False))
+    nx = X64.norm().item()
+    errs = []
+    for k in range(kmax + 1):
+        X, info = mixed(A, steps=k, raise_on_error=False)
+        errs.append((X - X64).norm().item() / nx)
+    kstar = next((k for k, e in enumerate(errs) if e <= 1e-12), None)
+    msk, (Xk, ik) = timed(lambda: mixed(A, steps=kstar if kstar is not None else kmax, raise_on_error=False))
+    Xd, idf = mixed(A, raise_on_error=False)
+    line = {"suite": suite, "set": label, "n": n, "kind": int(ik["kind_used"]), "k_star": kstar,
+            "errors_by_step": [float("%.3g" % e) for e in errs], "mixed_ms": msk,
+            "fp64_ms": ms64, "fp64_status": int(i64["status"]),
+            "default_status": int(idf["status"]), "default_iterations": int(idf["iterations"])}
+    if suite == "cbrt":
+        line["residual_mixed"] = float("%.3g" % ((Xk @ (Xk @ Xk) - A).norm() / A.norm()).item())
+        line["residual_fp64"] = float("%.3g" % ((X64 @ (X64 @ X64) - A).norm() / A.norm()).item())
+    print(json.dumps(line), flush=True)
+
+
+def run_table1_suite(args):
+    """The paper's Table 1 test sets (Sec. 5) at the paper's sizes, one JSON
+    line per set (the paper's ground truth is the FP64 Schur method)."""
+    import torch
+    import paper_2607_12430_gb300 as mp
+    mp.lib()
+    sizes = {"I": 2048, "II": 2048, "III": 4096, "IV": 4096, "V": 4096, "VI": 4096, "VII": 1024}
+    for sid in args.sets or list(sizes):
         n = sizes[sid]
         A = torch.from_numpy(np.ascontiguousarray(synth.table1_case(sid, n, seed=synth.BASE_SEED + 10))).cuda()
-        ms64, (X64, i64) = timed(lambda: mp.sqrtm_schur_fp64(A, raise_on_error=False))
-        nx = X64.norm().item()
-        errs = []
-        kmax = 14 if sid == "VII" else 6
-        for k in range(kmax + 1):
-            X, info = mp.sqrtm_mixed(A, steps=k, raise_on_error=False)
-            errs.append((X - X64).norm().item() / nx)
-        kstar = next((k for k, e in enumerate(errs) if e <= 1e-12), None)
-        msk, (Xk, ik) = timed(lambda: mp.sqrtm_mixed(A, steps=kstar if kstar is not None else kmax,
-                                                     raise_on_error=False))
-        Xd, idf = mp.sqrtm_mixed(A, raise_on_error=False)
-        print(json.dumps({"suite": "table1", "set": sid, "n": n, "kind": int(ik["kind_used"]), "k_star": kstar,
-                          "errors_by_step": [float("%.3g" % e) for e in errs], "mixed_ms": msk,
-                          "fp64_ms": ms64, "fp64_status": int(i64["status"]),
-                          "default_status": int(idf["status"]), "default_iterations": int(idf["iterations"])}),
-              flush=True)
+        _suite_case(args, "table1", sid, n, A, mp.sqrtm_mixed, mp.sqrtm_schur_fp64, 14 if sid == "VII" else 6)
+    return 0
+
+
+def run_cbrt_suite(args):
+    """The principal cube root (Sec. 4, p = 3) on the nonsymmetric Table 1
+    sets I and II (n = 2048; their shift keeps every real eigenvalue >= 1,
+    away from the closed negative real axis) and, as "G512", the general
+    n = 512 workload of the square root benchmark; one JSON line each, with
+    the residuals ||X^3 - A|| / ||A|| of both methods."""
+    import torch
+    import paper_2607_12430_gb300 as mp
+    mp.lib()
+    for sid in args.sets or ["G512", "I", "II"]:
+        if sid == "G512":
+            n, M = 512, synth.config_general512()
+        else:
+            n, M = 2048, synth.table1_case(sid, 2048, seed=synth.BASE_SEED + 10)
+        A = torch.from_numpy(np.ascontiguousarray(M)).cuda()
+        _suite_case(args, "cbrt", sid, n, A, mp.cbrtm_mixed, mp.cbrtm_schur_fp64, 6)
     return 0
 
 
@@ -430,9 +455,10 @@ def main():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--suite", choices=["table1"], default=None,
-                   help="the paper's Table 1 sets (one JSON line each) instead of the benchmark")
-    p.add_argument("--sets", nargs="*", default=None, help="--suite table1: which sets (default all)")
+    p.add_argument("--suite", choices=["table1", "cbrt"], default=None,
+                   help="the paper's Table 1 sets, or the cube root on sets I, II and the n = 512 "
+                        "workload (one JSON line each) instead of the benchmark")
+    p.add_argument("--sets", nargs="*", default=None, help="--suite: which sets (default all)")
     args = p.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -440,6 +466,8 @@ def main():
         return run_profile_mode(args)
     if args.suite == "table1":
         return run_table1_suite(args)
+    if args.suite == "cbrt":
+        return run_cbrt_suite(args)
     return run_ours(args)
 
 

@@ -147,6 +147,27 @@ SQRTM_API int sqrtm_schur_fp64(sqrtm_handle_t handle, const double *dA, int64_t 
                      double tol, double *dX, int64_t ldx, const sqrtm_opts *opts,
                      sqrtm_info *info);
 
+/* Mixed-precision principal cube root (Sec. 4, p = 3): the X with X^3 = A
+ * whose eigenvalues have arguments in (-pi/3, pi/3], for A with no
+ * eigenvalue on the closed negative real axis.  The steps of Algorithm 2
+ * with the order raised: A_s = 8^-e A, FP32 Schur form, the triangular cube
+ * root S = T^{1/3} with V = S^2 (blocked recurrence from S^3 = T), X_0 =
+ * 2^e Q S Q^H rounded to FP32, then X_{k+1} = X_k + 2^e Q Y Q^H with
+ * S^2 Y + S Y S + Y S^2 = Q^H (A - X_k^3) Q 8^-e (Eq. (3rd-order)), the
+ * residual (X_k X_k in FP64, then A - X_k (X_k X_k)) and the update in FP64.
+ * Arguments, opts, info and return codes as for sqrtm_mixed; opts->kind is
+ * ignored (every input takes the Schur form); no factors are kept for
+ * sqrtm_backward. */
+SQRTM_API int sqrtm_cbrtm_mixed(sqrtm_handle_t handle, const double *dA, int64_t n, int64_t lda, double tol,
+                                double *dX, int64_t ldx, const sqrtm_opts *opts, sqrtm_info *info);
+
+/* Plain FP64 Schur method for the principal cube root (Sec. 4, p = 3):
+ * X = 2^e Q S Q^H with S = T^{1/3}, all in FP64, no refinement.  Arguments
+ * as for sqrtm_schur_fp64. */
+SQRTM_API int sqrtm_cbrtm_schur_fp64(sqrtm_handle_t handle, const double *dA, int64_t n, int64_t lda,
+                                     double tol, double *dX, int64_t ldx, const sqrtm_opts *opts,
+                                     sqrtm_info *info);
+
 /* Adjoint of the square root at the last sqrtm_mixed call on this handle:
  * given a cotangent Gbar (n x n, ldg), returns the gradient of <Gbar, X> with
  * respect to A, i.e. the solution Y (ldy) of X^T Y + Y X^T = Gbar.  Uses the

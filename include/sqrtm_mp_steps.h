@@ -48,6 +48,18 @@ SQRTM_API int sqrtm_step_syevd(sqrtm_handle_t h, const void *dAs, void *dV, void
 SQRTM_API int sqrtm_step_trisqrt(sqrtm_handle_t h, const void *dT, void *dS, int64_t n, int blks,
                        int fp64);
 
+/* Triangular cube root (Sec. 4, p = 3): S = T^{1/3} with every diagonal
+ * entry the principal cube root (argument in (-pi/3, pi/3]) and V = S^2, by
+ * the blocked recurrence from S^3 = T (b x b blocks, b = min(blks, 32);
+ * inside a block the point recurrence s_ij (s_ii^2 + s_ii s_jj + s_jj^2) =
+ * t_ij - s_ii p_ij - sum_{i<k<j} s_ik v_kj with p_ij = sum_{i<k<j} s_ik s_kj).
+ * dT, dS, dV: upper triangular n x n (ld n), complex of the precision fp64
+ * selects (c64 or c128); the strict lower triangles of dS and dV are
+ * written with zeros.  Returns 0, or 2 for an eigenvalue on or next to the
+ * closed negative real axis. */
+SQRTM_API int sqrtm_step_tricbrt(sqrtm_handle_t h, const void *dT, void *dS, void *dV, int64_t n, int blks,
+                                 int fp64);
+
 /* X_0 = Re(Q S Q^H) (Algorithm 2, step 3), computed in the storage
  * precision of Q and S, rounded to that precision and written widened to
  * FP64 into dX (ldx), times 2^e (undoing the scaling). */
@@ -71,6 +83,15 @@ SQRTM_API int sqrtm_step_transform_in(sqrtm_handle_t h, const void *dQ, const fl
  * or 2. */
 SQRTM_API int sqrtm_step_rtrsyl(sqrtm_handle_t h, const void *dS, int64_t m, const void *dSt,
                       int64_t nn, void *dC, int blks);
+
+/* Correction equation of the cube root's refinement (Eq. (3rd-order)):
+ * S^2 Y + S Y S + Y S^2 = C for upper triangular S with V = S^2 (from
+ * sqrtm_step_tricbrt), by b x b block anti-diagonal wavefronts that keep
+ * Z = Y S alongside Y.  dS, dV, dC: n x n (ld n), complex of the precision
+ * fp64 selects; dC is overwritten by Y.  Returns 0, or 2 for a vanishing
+ * denominator s_ii^2 + s_ii s_jj + s_jj^2. */
+SQRTM_API int sqrtm_step_rtrsyl3(sqrtm_handle_t h, const void *dS, const void *dV, void *dC, int64_t n, int blks,
+                                 int fp64);
 
 /* Back-transform and update (Algorithm 2, steps 10-11): dX += 2^e Re(Q Y
  * Q^H), product in low precision, addition in FP64.  Q, Y c64. */

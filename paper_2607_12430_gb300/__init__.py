@@ -84,6 +84,8 @@ _SIGS = {
     "sqrtm_default_opts": ([ctypes.POINTER(Opts)], None),
     "sqrtm_mixed": ([_P, _P, _L, _L, _D, _P, _L, ctypes.POINTER(Opts), ctypes.POINTER(Info)], _I),
     "sqrtm_schur_fp64": ([_P, _P, _L, _L, _D, _P, _L, ctypes.POINTER(Opts), ctypes.POINTER(Info)], _I),
+    "sqrtm_cbrtm_mixed": ([_P, _P, _L, _L, _D, _P, _L, ctypes.POINTER(Opts), ctypes.POINTER(Info)], _I),
+    "sqrtm_cbrtm_schur_fp64": ([_P, _P, _L, _L, _D, _P, _L, ctypes.POINTER(Opts), ctypes.POINTER(Info)], _I),
     "sqrtm_backward": ([_P, _P, _L, _L, _D, _P, _L, ctypes.POINTER(Info)], _I),
     "sqrtm_mixed_batched": ([_P, _I, _P, _P, _P, _D, _P, _P, ctypes.POINTER(Opts), _P], _I),
     "sqrtm_status_string": ([_I], ctypes.c_char_p),
@@ -93,6 +95,8 @@ _SIGS = {
     "sqrtm_step_schur": ([_P, _P, _P, _L, _I], _I),
     "sqrtm_step_syevd": ([_P, _P, _P, _P, _L, _I], _I),
     "sqrtm_step_trisqrt": ([_P, _P, _P, _L, _I, _I], _I),
+    "sqrtm_step_tricbrt": ([_P, _P, _P, _P, _L, _I, _I], _I),
+    "sqrtm_step_rtrsyl3": ([_P, _P, _P, _P, _L, _I, _I], _I),
     "sqrtm_step_form_x0": ([_P, _P, _P, _L, _I, _P, _L, _I], _I),
     "sqrtm_step_residual": ([_P, _P, _L, _P, _L, _L, _I, _P, ctypes.POINTER(_D)], _I),
     "sqrtm_step_transform_in": ([_P, _P, _P, _P, _L], _I),
@@ -232,6 +236,40 @@ def sqrtm_schur_fp64(A, out=None, raise_on_error=True, **kw):
     return X, d
 
 
+def cbrtm_mixed(A, tol=1e-12, out=None, raise_on_error=True, **kw):
+    """Mixed-precision principal cube root (Sec. 4, p = 3).  Returns
+    ``(X, info_dict)``."""
+    A = _check_square(A)
+    n = A.shape[0]
+    X = _out_like(out, A)
+    o = make_opts(tol=tol, **kw)
+    info = Info()
+    ld = max(1, n)
+    rc = lib().sqrtm_cbrtm_mixed(handle(), _ptr(A), n, ld, tol, _ptr(X), ld, ctypes.byref(o), ctypes.byref(info))
+    if rc and raise_on_error:
+        raise SqrtmError(rc, "sqrtm_cbrtm_mixed")
+    d = info.as_dict()
+    d["status"] = rc
+    return X, d
+
+
+def cbrtm_schur_fp64(A, out=None, raise_on_error=True, **kw):
+    """Plain FP64 Schur method for the principal cube root on the GPU."""
+    A = _check_square(A)
+    n = A.shape[0]
+    X = _out_like(out, A)
+    o = make_opts(**kw)
+    info = Info()
+    ld = max(1, n)
+    rc = lib().sqrtm_cbrtm_schur_fp64(handle(), _ptr(A), n, ld, 0.0, _ptr(X), ld, ctypes.byref(o),
+                                      ctypes.byref(info))
+    if rc and raise_on_error:
+        raise SqrtmError(rc, "sqrtm_cbrtm_schur_fp64")
+    d = info.as_dict()
+    d["status"] = rc
+    return X, d
+
+
 def sqrtm_backward(G, tol=1e-12, out=None, raise_on_error=True):
     """Gradient of <G, sqrtm(A)> for the last sqrtm_mixed call on this
     stream's handle: Y with X^T Y + Y X^T = G."""
@@ -335,6 +373,20 @@ def step_trisqrt(T_cm, n, blks=32, fp64=False):
     S = torch.empty_like(T_cm)
     _rc(lib().sqrtm_step_trisqrt(handle(), _ptr(T_cm), _ptr(S), n, blks, int(fp64)), "trisqrt")
     return S
+
+
+def step_tricbrt(T_cm, n, blks=32, fp64=False):
+    """Triangular cube root: returns (S_cm, V_cm) with V = S^2."""
+    S = torch.empty_like(T_cm)
+    V = torch.empty_like(T_cm)
+    _rc(lib().sqrtm_step_tricbrt(handle(), _ptr(T_cm), _ptr(S), _ptr(V), n, blks, int(fp64)), "tricbrt")
+    return S, V
+
+
+def step_rtrsyl3(S_cm, V_cm, C_cm, n, blks=32, fp64=False):
+    """In place: C_cm (n x n column-major) becomes Y of S^2 Y + S Y S + Y S^2 = C."""
+    _rc(lib().sqrtm_step_rtrsyl3(handle(), _ptr(S_cm), _ptr(V_cm), _ptr(C_cm), n, blks, int(fp64)), "rtrsyl3")
+    return C_cm
 
 
 def step_form_x0(Q_cm, S_cm, n, e=0, fp64=False):

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "handle.h"
+#include "spd_internal.h"
 
 using namespace sqm;
 
@@ -243,12 +244,15 @@ static bool is_bitwise_symmetric(sqrtm_handle_t h, const double *dA, int64_t n, 
 
 // ---------------------------------------------------------------------------
 // general path (Algorithm 2) in storage precision R; refine = false gives the
-// plain Schur method
+// plain Schur method.  root = 3 gives the principal cube root (Sec. 4, p = 3)
+// by the same steps: the triangular cube root S with V = S^2 in place of the
+// triangular square root, the residual A - X (X X), and the correction
+// equation S^2 Y + S Y S + Y S^2 = Q^H R Q (Eq. (3rd-order)).
 // ---------------------------------------------------------------------------
 template <class R>
 static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, double tol,
                         double *dX, int64_t ldx, const sqrtm_opts &o, sqrtm_info *info,
-                        bool refine)
+                        bool refine, int root = 2)
 {
     cudaStream_t s = h->stream;
     const size_t nn = (size_t)n * (size_t)n;
@@ -260,7 +264,8 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
                     Carve::round(2 * sizeof(SchurDesc<R>)) +
                     2 * (Carve::round(qr_log_capacity(n) * sizeof(RotLog<R>)) +
                          Carve::round(qr_win_capacity(n) * sizeof(WinRec)) + Carve::round(qr_u_capacity(n) * cb)) +
-                    Carve::round(kQrStateInts * sizeof(int)) + Carve::round(4 * sizeof(int)) + Carve::round(32 * sizeof(int)) + Carve::round(qr_win_capacity(n) * sizeof(int)) + 4096;
+                    Carve::round(kQrStateInts * sizeof(int)) + Carve::round(4 * sizeof(int)) + Carve::round(32 * sizeof(int)) + Carve::round(qr_win_capacity(n) * sizeof(int)) + 4096 +
+                    (root == 3 ? Carve::round(nn * cb) : 0);
     if (ensure(h->fact, fbytes, h) || ensure(h->ws, wbytes, h)) return 7;
     Carve cf(h->fact.p);
     cplx<R> *Q = cf.take<cplx<R>>(nn);
@@ -290,12 +295,16 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     int *rstate = cw.take<int>(4);
     int *qsync = cw.take<int>(32);
     int *qpost = cw.take<int>(qr_win_capacity(n));
+    // cube root: V = S^2 beside S; X X in FP64 shares Rt's bytes (it is read
+    // by the residual before Rt is next written)
+    cplx<R> *V = root == 3 ? cw.take<cplx<R>>(nn) : nullptr;
+    double *XX = (double *)Rt;
     h->fact_n = -1;
 
     SQM_CU(cudaMemsetAsync(sc.e, 0, 16 * sizeof(int), s));
     SQM_CU(cudaEventRecord(h->ev[0], s));
-    SQM_CU(launch_norm_scale(dA, n, lda, sc.partials, (int)std::min<int64_t>(n, 1024), sc.norm, sc.e, s));
-    SQM_CU(launch_cast_scaled<R>(dA, n, lda, sc.e, T, n, s));
+    SQM_CU(launch_norm_scale(dA, n, lda, sc.partials, (int)std::min<int64_t>(n, 1024), sc.norm, sc.e, s, root));
+    SQM_CU(launch_cast_scaled<R>(dA, n, lda, sc.e, T, n, s, root));
     double norm_a = 0.0;
     int e = 0;
     if (int rc = read_scalars(h, sc, &norm_a, nullptr, &e, nullptr, nullptr)) return rc;
@@ -342,7 +351,8 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     SQM_CU(launch_qr_sweeps<R>(ddesc, 1, (int)n, (int *)h->staging.p + 512, qstate, s, &ms_chase, ddesc + 1, h->side,
                                h->qev, qsync));
     SQM_CU(cudaEventRecord(h->ev[1], s));
-    SQM_CU(launch_trisqrt<R>(T, (int)n, S, (int)n, (int)n, o.blks, sc.st_solve, s));
+    if (root == 3) SQM_CU(launch_tricbrt<R>(T, (int)n, S, (int)n, V, (int)n, (int)n, o.blks, sc.st_solve, s));
+    else SQM_CU(launch_trisqrt<R>(T, (int)n, S, (int)n, (int)n, o.blks, sc.st_solve, s));
     // X_0 = Re(Q S Q^H), rounded to R, times 2^e
     SQM_CU(launch_cgemm<R>(OP_N, OP_N, (int)n, (int)n, (int)n, Q, (int)n, false, S, (int)n, EPI_STORE, W, (int)n, nullptr, 0, 0.0, s));
     SQM_CU(launch_cgemm<R>(OP_N, OP_H, (int)n, (int)n, (int)n, W, (int)n, false, Q, (int)n, EPI_REAL_TO_F64, nullptr, 0, dX, ldx, ldexp(1.0, e), s));
@@ -367,7 +377,7 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     if (st_solve) return st_solve;
     if (!refine) return 0;
 
-    const double norm_as = ldexp(norm_a, -2 * e);
+    const double norm_as = ldexp(norm_a, -root * e);
     const bool fixed = o.steps >= 0;
     const int max_corr = fixed ? o.steps : o.maxit + 1;
     int status = 0, applied = 0, grew = 0;
@@ -377,7 +387,14 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
         if (k >= max_corr && fixed) break;
         if (need_res) {
             int np = 0;
-            SQM_CU(launch_residual_f64(dA, lda, dX, ldx, (int)n, e, Rhat, (int)n, sc.partials, &np, s));
+            if (root == 3) {
+                SQM_CU(launch_rgemm<double>(0, 0, (int)n, (int)n, (int)n, dX, (int)ldx, dX, (int)ldx, RG_STORE, XX,
+                                            (int)n, nullptr, nullptr, 0, 0.0, s));
+                SQM_CU(launch_residual_f64_ab(dA, lda, dX, ldx, XX, n, (int)n, 3 * e, Rhat, (int)n, sc.partials,
+                                              &np, s));
+            } else {
+                SQM_CU(launch_residual_f64(dA, lda, dX, ldx, (int)n, e, Rhat, (int)n, sc.partials, &np, s));
+            }
             SQM_CU(launch_sum_partials(sc.partials, np, sc.rnorm, s));
             double rn = 0.0;
             if (!fixed) {
@@ -395,14 +412,17 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
         // R~ = Q^H Rhat Q; Y solves S Y + Y S = R~; X += 2^e Re(Q Y Q^H)
         SQM_CU(launch_cgemm<R>(OP_N, OP_N, (int)n, (int)n, (int)n, Rhat, (int)n, true, Q, (int)n, EPI_STORE, W, (int)n, nullptr, 0, 0.0, s));
         SQM_CU(launch_cgemm<R>(OP_H, OP_N, (int)n, (int)n, (int)n, Q, (int)n, false, W, (int)n, EPI_STORE, Rt, (int)n, nullptr, 0, 0.0, s));
-        SQM_CU(launch_rtrsyl<R>(S, (int)n, (int)n, S, (int)n, (int)n, Rt, (int)n, o.blks, sc.st_solve, s));
+        if (root == 3)  // W is free between the transforms: it holds Z = Y S
+            SQM_CU(launch_rtrsyl3<R>(S, (int)n, V, (int)n, Rt, (int)n, W, (int)n, (int)n, o.blks, sc.st_solve, s));
+        else
+            SQM_CU(launch_rtrsyl<R>(S, (int)n, (int)n, S, (int)n, (int)n, Rt, (int)n, o.blks, sc.st_solve, s));
         SQM_CU(launch_cgemm<R>(OP_N, OP_N, (int)n, (int)n, (int)n, Q, (int)n, false, Rt, (int)n, EPI_STORE, W, (int)n, nullptr, 0, 0.0, s));
         SQM_CU(launch_cgemm<R>(OP_N, OP_H, (int)n, (int)n, (int)n, W, (int)n, false, Q, (int)n, EPI_REAL_ADD_F64, nullptr, 0, dX, ldx, ldexp(1.0, e), s));
         ++applied;
     }
     SQM_CU(cudaEventRecord(h->ev[3], s));
     if (int rc = read_scalars(h, sc, nullptr, nullptr, nullptr, nullptr, &st_solve)) return rc;
-    if (!st_solve && (status == 0 || status == 1)) {
+    if (!st_solve && (status == 0 || status == 1) && root == 2) {
         // keep the factors and X for sqrtm_backward
         SQM_CU(cudaMemcpy2DAsync(Xsave, n * sizeof(double), dX, ldx * sizeof(double), n * sizeof(double), n,
                                  cudaMemcpyDeviceToDevice, s));
@@ -476,6 +496,35 @@ extern "C" int sqrtm_schur_fp64(sqrtm_handle_t h, const double *dA, int64_t n, i
     if (kind == SQRTM_KIND_SPD && spd_enabled()) rc = spd_schur_fp64(h, dA, n, lda, dX, ldx, o, info);
     else rc = general_path<double>(h, dA, n, lda, 0.0, dX, ldx, o, info, false);
     h->fact_n = -1;  // the FP64 method keeps no low-precision factors
+    if (info) info->status = rc;
+    return rc;
+}
+
+extern "C" int sqrtm_cbrtm_mixed(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, double tol,
+                                 double *dX, int64_t ldx, const sqrtm_opts *opts, sqrtm_info *info)
+{
+    info_reset(info);
+    if (!h) return -1;
+    if (int rc = check_args(dA, n, lda, dX, ldx)) return rc;
+    sqrtm_opts o;
+    if (int rc = resolve_opts(opts, tol, &o)) return rc;
+    if (n == 0) return 0;
+    int rc = general_path<float>(h, dA, n, lda, o.tol, dX, ldx, o, info, true, 3);
+    if (info) info->status = rc;
+    return rc;
+}
+
+extern "C" int sqrtm_cbrtm_schur_fp64(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, double tol,
+                                      double *dX, int64_t ldx, const sqrtm_opts *opts, sqrtm_info *info)
+{
+    info_reset(info);
+    if (!h) return -1;
+    if (int rc = check_args(dA, n, lda, dX, ldx)) return rc;
+    sqrtm_opts o;
+    if (int rc = resolve_opts(opts, tol, &o)) return rc;
+    if (n == 0) return 0;
+    int rc = general_path<double>(h, dA, n, lda, 0.0, dX, ldx, o, info, false, 3);
+    h->fact_n = -1;
     if (info) info->status = rc;
     return rc;
 }

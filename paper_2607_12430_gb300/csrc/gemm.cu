@@ -156,8 +156,8 @@ template cudaError_t launch_cgemm<double>(int, int, int, int, int, const void *,
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(G_THREADS)
 residual_f64_kernel(const double *__restrict__ A, int64_t lda, const double *__restrict__ X,
-                    int64_t ldx, int n, double sc, float *__restrict__ Rhat, int ldr,
-                    double *__restrict__ partials)
+                    int64_t ldx, const double *__restrict__ B, int64_t ldb, int n, double sc,
+                    float *__restrict__ Rhat, int ldr, double *__restrict__ partials)
 {
     __shared__ double As[GB_K][GB_M + 1];
     __shared__ double Bs[GB_K][GB_N + 1];
@@ -181,7 +181,7 @@ residual_f64_kernel(const double *__restrict__ A, int64_t lda, const double *__r
         for (int q = 0; q < 4; ++q) {
             int kk = tid % GB_K, j = tid / GB_K + 16 * q;
             int gk = k0 + kk, gj = n0 + j;
-            Bs[kk][j] = (gk < n && gj < n) ? X[gk + gj * ldx] : 0.0;
+            Bs[kk][j] = (gk < n && gj < n) ? B[gk + gj * ldb] : 0.0;
         }
         __syncthreads();
 #pragma unroll
@@ -229,7 +229,20 @@ cudaError_t launch_residual_f64(const double *A, int64_t lda, const double *X, i
     dim3 g((unsigned)cdiv_i(n, GB_M), (unsigned)cdiv_i(n, GB_N));
     *nparts = (int)(g.x * g.y);
     if (n <= 0) return cudaSuccess;
-    residual_f64_kernel<<<g, G_THREADS, 0, s>>>(A, lda, X, ldx, n, ldexp(1.0, -2 * e), Rhat, ldr, partials); count_launch();
+    residual_f64_kernel<<<g, G_THREADS, 0, s>>>(A, lda, X, ldx, X, ldx, n, ldexp(1.0, -2 * e), Rhat, ldr, partials);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual_f64_ab(const double *A, int64_t lda, const double *X, int64_t ldx,
+                                   const double *B, int64_t ldb, int n, int shift, float *Rhat, int ldr,
+                                   double *partials, int *nparts, cudaStream_t s)
+{
+    dim3 g((unsigned)cdiv_i(n, GB_M), (unsigned)cdiv_i(n, GB_N));
+    *nparts = (int)(g.x * g.y);
+    if (n <= 0) return cudaSuccess;
+    residual_f64_kernel<<<g, G_THREADS, 0, s>>>(A, lda, X, ldx, B, ldb, n, ldexp(1.0, -shift), Rhat, ldr, partials);
+    count_launch();
     return cudaGetLastError();
 }
 

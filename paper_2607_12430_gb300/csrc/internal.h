@@ -68,12 +68,14 @@ struct SchurDesc {
 };
 
 // ---- scaling / norms (scale.cu) ----
-// Deterministic ||A||_F: partials[nblk] then finalize; writes norm, e.
+// Deterministic ||A||_F: partials[nblk] then finalize; writes norm and e, the
+// scaling exponent for a root of order `root`: A_s = 2^(-root e) A has
+// ||A_s||_F / sqrt(n) in [2^-root, 1), and A^(1/root) = 2^e A_s^(1/root).
 cudaError_t launch_norm_scale(const double *A, int64_t n, int64_t lda, double *partials,
-                              int nblk, double *d_norm, int *d_e, cudaStream_t s);
+                              int nblk, double *d_norm, int *d_e, cudaStream_t s, int root = 2);
 template <class R>
 cudaError_t launch_cast_scaled(const double *A, int64_t n, int64_t lda, const int *d_e,
-                               cplx<R> *As, int64_t ldas, cudaStream_t s);
+                               cplx<R> *As, int64_t ldas, cudaStream_t s, int root = 2);
 template <class R>
 cudaError_t launch_cast_scaled_real(const double *A, int64_t n, int64_t lda, const int *d_e,
                                     R *As, int64_t ldas, cudaStream_t s);
@@ -123,6 +125,17 @@ inline int64_t qr_u_capacity(int64_t n) { return std::max<int64_t>(24 * n * n, 6
 template <class R>
 cudaError_t launch_trisqrt(const cplx<R> *T, int ldt, cplx<R> *S, int lds, int n, int blks,
                            int *d_status, cudaStream_t s);
+// Principal cube root (Sec. 4, p = 3) of upper triangular T: S = T^(1/3) and
+// V = S^2 (both n x n, upper triangular); status 2 for an eigenvalue on or
+// near the closed negative real axis or a zero leaf denominator.
+template <class R>
+cudaError_t launch_tricbrt(const cplx<R> *T, int ldt, cplx<R> *S, int lds, cplx<R> *V, int ldv, int n, int blks,
+                           int *d_status, cudaStream_t s);
+// S^2 Y + S Y S + Y S^2 = C (Eq. (3rd-order)) for upper triangular S with
+// V = S^2: C (n x n) is overwritten by Y; Z (n x n) is scratch (Y S).
+template <class R>
+cudaError_t launch_rtrsyl3(const cplx<R> *S, int lds, const cplx<R> *V, int ldv, cplx<R> *C, int ldc, cplx<R> *Z,
+                           int ldz, int n, int blks, int *d_status, cudaStream_t s);
 // S Y + Y St = C (C overwritten by Y), blocked wavefront.
 template <class R>
 cudaError_t launch_rtrsyl(const cplx<R> *S, int lds, int m, const cplx<R> *St, int ldst, int nn,
@@ -145,6 +158,11 @@ cudaError_t launch_cgemm(int opA, int opB, int m, int n, int k, const void *A, i
 cudaError_t launch_residual_f64(const double *A, int64_t lda, const double *X, int64_t ldx,
                                 int n, int e, float *Rhat, int ldr, double *partials,
                                 int *nparts, cudaStream_t s);
+// The same with a second factor: R = (A - X B) * 2^-shift (the cube root's
+// residual A - X (X X) with B = X X and shift = 3 e).
+cudaError_t launch_residual_f64_ab(const double *A, int64_t lda, const double *X, int64_t ldx,
+                                   const double *B, int64_t ldb, int n, int shift, float *Rhat, int ldr,
+                                   double *partials, int *nparts, cudaStream_t s);
 // Adjoint residual Res = G - (X^T Y + Y X^T) in FP64; Rhat = fl32(Res) and
 // per-CTA partial sums of |Res|^2.
 cudaError_t launch_adjoint_residual_f64(const double *G, int64_t ldg, const double *X, int64_t ldx,

@@ -37,7 +37,7 @@ __global__ void norm_partials_kernel(const double *__restrict__ A, int64_t n, in
 }
 
 __global__ void norm_finalize_kernel(const double *__restrict__ partials, int np, int64_t n,
-                                     double *d_norm, int *d_e)
+                                     double *d_norm, int *d_e, int root)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double s = 0.0;
@@ -49,26 +49,26 @@ __global__ void norm_finalize_kernel(const double *__restrict__ partials, int np
         double r = sqrt(s / (double)n);
         int p;
         frexp(r, &p);
-        e = (p >= 0) ? (p + 1) / 2 : -((-p) / 2);  // ceil(p / 2)
+        e = (p >= 0) ? (p + root - 1) / root : -((-p) / root);  // ceil(p / root)
     }
     *d_e = e;
 }
 
 cudaError_t launch_norm_scale(const double *A, int64_t n, int64_t lda, double *partials,
-                              int nblk, double *d_norm, int *d_e, cudaStream_t s)
+                              int nblk, double *d_norm, int *d_e, cudaStream_t s, int root)
 {
     if (nblk < 1) nblk = 1;
     norm_partials_kernel<<<nblk, kNormThreads, 0, s>>>(A, n, lda, partials); count_launch();
-    norm_finalize_kernel<<<1, 32, 0, s>>>(partials, nblk, n, d_norm, d_e); count_launch();
+    norm_finalize_kernel<<<1, 32, 0, s>>>(partials, nblk, n, d_norm, d_e, root); count_launch();
     return cudaGetLastError();
 }
 
 template <class R>
 __global__ void cast_scaled_kernel(const double *__restrict__ A, int64_t n, int64_t lda,
                                    const int *__restrict__ d_e, cplx<R> *__restrict__ As,
-                                   int64_t ldas)
+                                   int64_t ldas, int root)
 {
-    double sc = ldexp(1.0, -2 * (*d_e));
+    double sc = ldexp(1.0, -root * (*d_e));
     int64_t total = n * n;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -101,9 +101,9 @@ static int grid_for(int64_t total)
 
 template <class R>
 cudaError_t launch_cast_scaled(const double *A, int64_t n, int64_t lda, const int *d_e,
-                               cplx<R> *As, int64_t ldas, cudaStream_t s)
+                               cplx<R> *As, int64_t ldas, cudaStream_t s, int root)
 {
-    cast_scaled_kernel<R><<<grid_for(n * n), 256, 0, s>>>(A, n, lda, d_e, As, ldas); count_launch();
+    cast_scaled_kernel<R><<<grid_for(n * n), 256, 0, s>>>(A, n, lda, d_e, As, ldas, root); count_launch();
     return cudaGetLastError();
 }
 
@@ -116,9 +116,9 @@ cudaError_t launch_cast_scaled_real(const double *A, int64_t n, int64_t lda, con
 }
 
 template cudaError_t launch_cast_scaled<float>(const double *, int64_t, int64_t, const int *,
-                                               cplx<float> *, int64_t, cudaStream_t);
+                                                cplx<float> *, int64_t, cudaStream_t, int);
 template cudaError_t launch_cast_scaled<double>(const double *, int64_t, int64_t, const int *,
-                                                cplx<double> *, int64_t, cudaStream_t);
+                                                cplx<double> *, int64_t, cudaStream_t, int);
 template cudaError_t launch_cast_scaled_real<float>(const double *, int64_t, int64_t,
                                                     const int *, float *, int64_t, cudaStream_t);
 template cudaError_t launch_cast_scaled_real<double>(const double *, int64_t, int64_t,

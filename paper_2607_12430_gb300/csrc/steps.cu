@@ -126,6 +126,25 @@ extern "C" int sqrtm_step_trisqrt(sqrtm_handle_t h, const void *dT, void *dS, in
     return st;
 }
 
+extern "C" int sqrtm_step_tricbrt(sqrtm_handle_t h, const void *dT, void *dS, void *dV, int64_t n, int blks,
+                                  int fp64)
+{
+    if (!h) return -1;
+    if (n < 0) return -5;
+    if (blks < 1) return -6;
+    if (n == 0) return 0;
+    StepScratch ss; void *ex;
+    if (int rc = step_scratch(h, n, 0, &ss, &ex)) return rc;
+    cudaError_t err = fp64 ? launch_tricbrt<double>((const cplx<double> *)dT, (int)n, (cplx<double> *)dS, (int)n,
+                                                    (cplx<double> *)dV, (int)n, (int)n, blks, ss.iscal + 1, h->stream)
+                           : launch_tricbrt<float>((const cplx<float> *)dT, (int)n, (cplx<float> *)dS, (int)n,
+                                                   (cplx<float> *)dV, (int)n, (int)n, blks, ss.iscal + 1, h->stream);
+    if (err) return 7;
+    int st = 0;
+    if (fetch(h, &st, ss.iscal + 1, sizeof(int))) return 7;
+    return st;
+}
+
 template <class R>
 static int form_x0(sqrtm_handle_t h, const cplx<R> *Q, const cplx<R> *S, int64_t n, int e,
                    double *dX, int64_t ldx)
@@ -232,6 +251,28 @@ extern "C" int sqrtm_step_rtrsyl(sqrtm_handle_t h, const void *dS, int64_t m, co
     if (int rc = step_scratch(h, std::max(m, nn), 0, &ss, &ex)) return rc;
     if (launch_rtrsyl<float>((const cplx<float> *)dS, (int)m, (int)m, (const cplx<float> *)dSt, (int)nn, (int)nn,
                              (cplx<float> *)dC, (int)m, blks, ss.iscal + 1, h->stream)) return 7;
+    int st = 0;
+    if (fetch(h, &st, ss.iscal + 1, sizeof(int))) return 7;
+    return st;
+}
+
+extern "C" int sqrtm_step_rtrsyl3(sqrtm_handle_t h, const void *dS, const void *dV, void *dC, int64_t n, int blks,
+                                  int fp64)
+{
+    if (!h) return -1;
+    if (n < 0) return -5;
+    if (blks < 1) return -6;
+    if (n == 0) return 0;
+    StepScratch ss; void *ex;
+    const size_t zb = (size_t)n * n * (fp64 ? sizeof(cplx<double>) : sizeof(cplx<float>));
+    if (int rc = step_scratch(h, n, zb, &ss, &ex)) return rc;
+    cudaError_t err = fp64 ? launch_rtrsyl3<double>((const cplx<double> *)dS, (int)n, (const cplx<double> *)dV, (int)n,
+                                                    (cplx<double> *)dC, (int)n, (cplx<double> *)ex, (int)n, (int)n,
+                                                    blks, ss.iscal + 1, h->stream)
+                           : launch_rtrsyl3<float>((const cplx<float> *)dS, (int)n, (const cplx<float> *)dV, (int)n,
+                                                   (cplx<float> *)dC, (int)n, (cplx<float> *)ex, (int)n, (int)n, blks,
+                                                   ss.iscal + 1, h->stream);
+    if (err) return 7;
     int st = 0;
     if (fetch(h, &st, ss.iscal + 1, sizeof(int))) return 7;
     return st;

@@ -319,6 +319,302 @@ trisqrt_off_kernel(const cplx<R> *__restrict__ T, int ldt, cplx<R> *S, int lds, 
     if (threadIdx.x == 0 && bad) atomicExch(status, 2);
 }
 
+// ---------------------------------------------------------------------------
+// Principal cube root (Sec. 4, p = 3): S = T^(1/3) of upper triangular T with
+// V = S^2 alongside, and the refinement's generalized triangular Sylvester
+// equation S^2 Y + S Y S + Y S^2 = C (Eq. (3rd-order)), both by b x b block
+// wavefronts whose leaves solve A^2 Y + A Y B + Y B^2 = C point by point.
+// Block equations (I < J): the cube root's off-diagonal blocks satisfy
+//   S_II^2 S_IJ + S_II S_IJ S_JJ + S_IJ S_JJ^2
+//       = T_IJ - S_II P_IJ - sum_{I<K<J} S_IK V_KJ,  P_IJ = sum_{I<K<J} S_IK S_KJ,
+//   V_IJ = S_II S_IJ + S_IJ S_JJ + P_IJ;
+// the Sylvester blocks, with Z = Y S kept alongside,
+//   S_II^2 Y_IJ + S_II Y_IJ S_JJ + Y_IJ S_JJ^2 = C_IJ - sum_{K>I} (V_IK Y_KJ
+//       + S_IK Z_KJ) - sum_{L<J} Y_IL V_LJ - S_II Z'_IJ,
+//   Z'_IJ = sum_{L<J} Y_IL S_LJ,  Z_IJ = Z'_IJ + Y_IJ S_JJ.
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ cplx<R> ccbrt_(cplx<R> z)
+{
+    const R r = hypot(z.x, z.y);
+    if (r == R(0)) return cplx<R>{0, 0};
+    const R th = atan2(z.y, z.x) / R(3);  // argument in (-pi/3, pi/3]: the principal root
+    const R m = cbrt(r);
+    return cplx<R>{m * cos(th), m * sin(th)};
+}
+
+// acc(r, c_q) += sum_k A(r, k) B(k, c_q) (the outputs of tile_mms)
+template <class R>
+__device__ __forceinline__ void tile_mma(cplx<R> (&acc)[8], const cplx<R> *A, const cplx<R> *B, int kk, int lt)
+{
+    const int r = lt & 31, c0 = lt >> 5;
+    for (int k = 0; k < kk; ++k) {
+        const cplx<R> a = A[r + k * TLD];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) cfma(acc[q], a, B[k + (c0 + 4 * q) * TLD]);
+    }
+}
+
+template <class R>
+__device__ __forceinline__ void tile_store(cplx<R> *D, const cplx<R> (&acc)[8])
+{
+    const int r = threadIdx.x & 31, c0 = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) D[r + (c0 + 4 * q) * TLD] = acc[q];
+}
+
+// Point solve of A2 Y + A Y B + Y B2 = C on a leaf (A, A2 = A^2: ma x ma; B,
+// B2 = B^2: nb x nb; upper triangular); C is overwritten by Y and Wt
+// receives W = Y B.  Anti-diagonal by anti-diagonal (entry (i, j) needs the
+// entries below it in column j and left of it in row i), 4 threads per entry:
+//   y_ij (a2_ii + a_ii b_jj + b2_jj) = c_ij - sum_{k>i} (a2_ik y_kj + a_ik w_kj)
+//       - sum_{l<j} y_il b2_lj - a_ii w'_ij,  w'_ij = sum_{l<j} y_il b_lj,
+//   w_ij = w'_ij + y_ij b_jj.
+template <class R>
+__device__ void leaf_p3(const cplx<R> *A, const cplx<R> *A2, const cplx<R> *B, const cplx<R> *B2, cplx<R> *C,
+                        cplx<R> *Wt, int ma, int nb, int *bad)
+{
+    const int e = threadIdx.x >> 2, p = threadIdx.x & 3;
+    for (int w = 0; w <= ma + nb - 2; ++w) {
+        const int ioff = ma - 1 - w;  // j = i - ioff
+        const int ilo = max(0, ioff), ihi = min(ma - 1, ioff + nb - 1);
+        const int i = ilo + e;
+        const bool act = i <= ihi;
+        const int j = i - ioff;
+        cplx<R> acc{0, 0}, wp{0, 0};
+        if (act) {
+            for (int t = p; t < ma - 1 - i; t += 4) {
+                const int k = i + 1 + t;
+                cfma(acc, A2[i + k * TLD], C[k + j * TLD]);
+                cfma(acc, A[i + k * TLD], Wt[k + j * TLD]);
+            }
+            for (int l = p; l < j; l += 4) {
+                const cplx<R> y = C[i + l * TLD];
+                cfma(acc, y, B2[l + j * TLD]);
+                cfma(wp, y, B[l + j * TLD]);
+            }
+        }
+        acc += shfl_xor(acc, 1);
+        acc += shfl_xor(acc, 2);
+        wp += shfl_xor(wp, 1);
+        wp += shfl_xor(wp, 2);
+        if (act && p == 0) {
+            const cplx<R> aii = A[i + i * TLD], bjj = B[j + j * TLD];
+            cfma(acc, aii, wp);
+            cplx<R> den = A2[i + i * TLD] + aii * bjj + B2[j + j * TLD];
+            if (den.x == R(0) && den.y == R(0)) { *bad = 1; den = cplx<R>{R(1), R(0)}; }
+            const cplx<R> y = cdiv(C[i + j * TLD] - acc, den);
+            C[i + j * TLD] = y;
+            Wt[i + j * TLD] = wp + y * bjj;
+        }
+        __syncthreads();
+    }
+}
+
+// diagonal blocks: the point recurrence of the triangular cube root
+template <class R>
+__global__ void __launch_bounds__(kTriThreads)
+tricbrt_diag_kernel(const cplx<R> *__restrict__ T, int ldt, cplx<R> *S, int lds, cplx<R> *V, int ldv, int n, int b,
+                    int *status)
+{
+    extern __shared__ unsigned char smraw[];
+    cplx<R> *ts = reinterpret_cast<cplx<R> *>(smraw), *tv = ts + TB * TLD;
+    __shared__ int bad;
+    const int I = blockIdx.x;
+    const int i0 = I * b, bm = min(b, n - i0);
+    if (threadIdx.x == 0) bad = 0;
+    load_tile(ts, T + i0 + (int64_t)i0 * ldt, ldt, bm, bm);
+    for (int e = threadIdx.x; e < TB * TLD; e += blockDim.x) tv[e] = cplx<R>{0, 0};
+    __syncthreads();
+    const R eps = num<R>::eps;
+    if (threadIdx.x < bm) {
+        const int i = threadIdx.x;
+        const cplx<R> t = ts[i + i * TLD];
+        // on or near the closed negative real axis (the rule of trisqrt_diag_kernel)
+        if (t.x <= R(0) && fabs(t.y) <= fmax(R(10) * eps * hypot(t.x, t.y), (R)n * eps)) bad = 1;
+        const cplx<R> sv = ccbrt_(t);
+        ts[i + i * TLD] = sv;
+        tv[i + i * TLD] = sv * sv;
+    }
+    __syncthreads();
+    const int e = threadIdx.x >> 2, p = threadIdx.x & 3;
+    for (int dd = 1; dd < bm; ++dd) {
+        const int i = e, j = e + dd;
+        const bool act = j < bm;
+        cplx<R> sv{0, 0}, st{0, 0};
+        if (act)
+            for (int k = i + 1 + p; k < j; k += 4) {
+                cfma(sv, ts[i + k * TLD], ts[k + j * TLD]);
+                cfma(st, ts[i + k * TLD], tv[k + j * TLD]);
+            }
+        sv += shfl_xor(sv, 1);
+        sv += shfl_xor(sv, 2);
+        st += shfl_xor(st, 1);
+        st += shfl_xor(st, 2);
+        if (act && p == 0) {
+            const cplx<R> si = ts[i + i * TLD], sj = ts[j + j * TLD];
+            cplx<R> den = si * si + si * sj + sj * sj;
+            if (den.x == R(0) && den.y == R(0)) { bad = 1; den = cplx<R>{R(1), R(0)}; }
+            const cplx<R> sij = cdiv(ts[i + j * TLD] - si * sv - st, den);
+            ts[i + j * TLD] = sij;
+            tv[i + j * TLD] = sij * (si + sj) + sv;
+        }
+        __syncthreads();
+    }
+    for (int q = threadIdx.x; q < bm * bm; q += blockDim.x) {
+        const int i = q % bm, j = q / bm;
+        S[(i0 + i) + (int64_t)(i0 + j) * lds] = (i <= j) ? ts[i + j * TLD] : cplx<R>{0, 0};
+        V[(i0 + i) + (int64_t)(i0 + j) * ldv] = (i <= j) ? tv[i + j * TLD] : cplx<R>{0, 0};
+    }
+    if (threadIdx.x == 0 && bad) atomicExch(status, 2);
+}
+
+// block superdiagonal dblk >= 1 of the cube root
+template <class R>
+__global__ void __launch_bounds__(kTriThreads)
+tricbrt_off_kernel(const cplx<R> *__restrict__ T, int ldt, cplx<R> *S, int lds, cplx<R> *V, int ldv, int n, int b,
+                   int dblk, int *status)
+{
+    extern __shared__ unsigned char smraw[];
+    constexpr int TT = TB * TLD;
+    cplx<R> *t0 = reinterpret_cast<cplx<R> *>(smraw), *t1 = t0 + TT, *t2 = t1 + TT, *t3 = t2 + TT,
+            *t4 = t3 + TT, *t5 = t4 + TT, *t6 = t5 + TT;
+    __shared__ int bad;
+    const int Nb = (n + b - 1) / b;
+    const int I = blockIdx.x, J = I + dblk;
+    if (J >= Nb) return;
+    if (threadIdx.x == 0) bad = 0;
+    const int i0 = I * b, j0 = J * b;
+    const int bm = min(b, n - i0), bn = min(b, n - j0);
+    const int lt = threadIdx.x;
+    cplx<R> pacc[8], qacc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) pacc[q] = qacc[q] = cplx<R>{0, 0};
+    for (int K = I + 1; K < J; ++K) {
+        const int k0 = K * b, bk = min(b, n - k0);
+        load_tile(t0, S + i0 + (int64_t)k0 * lds, lds, bm, bk);
+        load_tile(t1, S + k0 + (int64_t)j0 * lds, lds, bk, bn);
+        load_tile(t2, V + k0 + (int64_t)j0 * ldv, ldv, bk, bn);
+        __syncthreads();
+        tile_mma(pacc, t0, t1, bk, lt);  // P += S_IK S_KJ
+        tile_mma(qacc, t0, t2, bk, lt);  // sum S_IK V_KJ
+        __syncthreads();
+    }
+    // right-hand side T_IJ - S_II P - sum S_IK V_KJ
+    tile_store(t3, pacc);
+    load_tile(t0, S + i0 + (int64_t)i0 * lds, lds, bm, bm);
+    load_tile(t4, T + i0 + (int64_t)j0 * ldt, ldt, bm, bn);
+    __syncthreads();
+    {
+        cplx<R> racc[8];
+        const int r = lt & 31, c0 = lt >> 5;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) racc[q] = t4[r + (c0 + 4 * q) * TLD] - qacc[q];
+        tile_mms(racc, t0, t3, bm, lt);
+        __syncthreads();
+        tile_store(t4, racc);
+    }
+    load_tile(t1, V + i0 + (int64_t)i0 * ldv, ldv, bm, bm);
+    load_tile(t2, S + j0 + (int64_t)j0 * lds, lds, bn, bn);
+    load_tile(t5, V + j0 + (int64_t)j0 * ldv, ldv, bn, bn);
+    for (int e = threadIdx.x; e < TT; e += blockDim.x) t6[e] = cplx<R>{0, 0};
+    __syncthreads();
+    leaf_p3(t0, t1, t2, t5, t4, t6, bm, bn, &bad);  // t4 = S_IJ
+    // V_IJ = S_II S_IJ + S_IJ S_JJ + P
+    tile_mma(pacc, t0, t4, bm, lt);
+    tile_mma(pacc, t4, t2, bn, lt);
+    {
+        const int r = lt & 31, c0 = lt >> 5;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int c = c0 + 4 * q;
+            if (r < bm && c < bn) {
+                S[(i0 + r) + (int64_t)(j0 + c) * lds] = t4[r + c * TLD];
+                V[(i0 + r) + (int64_t)(j0 + c) * ldv] = pacc[q];
+            }
+        }
+    }
+    // the mirrored blocks below the diagonal are zero
+    for (int q = threadIdx.x; q < bn * bm; q += blockDim.x) {
+        const int i = q % bn, j = q / bn;
+        S[(j0 + i) + (int64_t)(i0 + j) * lds] = cplx<R>{0, 0};
+        V[(j0 + i) + (int64_t)(i0 + j) * ldv] = cplx<R>{0, 0};
+    }
+    if (threadIdx.x == 0 && bad) atomicExch(status, 2);
+}
+
+// one anti-diagonal wavefront of S^2 Y + S Y S + Y S^2 = C (C becomes Y; Z = Y S)
+template <class R>
+__global__ void __launch_bounds__(kTriThreads)
+rtrsyl3_wave_kernel(const cplx<R> *__restrict__ S, int lds, const cplx<R> *__restrict__ V, int ldv, int n,
+                    cplx<R> *C, int ldc, cplx<R> *Z, int ldz, int b, int w, int *status)
+{
+    extern __shared__ unsigned char smraw[];
+    constexpr int TT = TB * TLD;
+    cplx<R> *t0 = reinterpret_cast<cplx<R> *>(smraw), *t1 = t0 + TT, *t2 = t1 + TT, *t3 = t2 + TT,
+            *t4 = t3 + TT, *t5 = t4 + TT, *t6 = t5 + TT;
+    __shared__ int bad;
+    const int Nb = (n + b - 1) / b;
+    const int I = max(0, (Nb - 1) - w) + blockIdx.x;
+    const int J = I + w - (Nb - 1);
+    if (I >= Nb || J >= Nb || J < 0) return;
+    if (threadIdx.x == 0) bad = 0;
+    const int i0 = I * b, j0 = J * b;
+    const int bm = min(b, n - i0), bn = min(b, n - j0);
+    const int lt = threadIdx.x, r = lt & 31, c0 = lt >> 5;
+    cplx<R> acc[8], zp[8];
+    load_tile(t5, C + i0 + (int64_t)j0 * ldc, ldc, bm, bn);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        acc[q] = t5[r + (c0 + 4 * q) * TLD];
+        zp[q] = cplx<R>{0, 0};
+    }
+    __syncthreads();
+    for (int K = I + 1; K < Nb; ++K) {  // - V_IK Y_KJ - S_IK Z_KJ
+        const int k0 = K * b, bk = min(b, n - k0);
+        load_tile(t0, V + i0 + (int64_t)k0 * ldv, ldv, bm, bk);
+        load_tile(t1, C + k0 + (int64_t)j0 * ldc, ldc, bk, bn);
+        load_tile(t2, S + i0 + (int64_t)k0 * lds, lds, bm, bk);
+        load_tile(t3, Z + k0 + (int64_t)j0 * ldz, ldz, bk, bn);
+        __syncthreads();
+        tile_mms(acc, t0, t1, bk, lt);
+        tile_mms(acc, t2, t3, bk, lt);
+        __syncthreads();
+    }
+    for (int L = 0; L < J; ++L) {  // - Y_IL V_LJ; Z' += Y_IL S_LJ
+        const int l0 = L * b, bl = min(b, n - l0);
+        load_tile(t0, C + i0 + (int64_t)l0 * ldc, ldc, bm, bl);
+        load_tile(t1, V + l0 + (int64_t)j0 * ldv, ldv, bl, bn);
+        load_tile(t2, S + l0 + (int64_t)j0 * lds, lds, bl, bn);
+        __syncthreads();
+        tile_mms(acc, t0, t1, bl, lt);
+        tile_mma(zp, t0, t2, bl, lt);
+        __syncthreads();
+    }
+    tile_store(t4, zp);
+    load_tile(t0, S + i0 + (int64_t)i0 * lds, lds, bm, bm);
+    __syncthreads();
+    tile_mms(acc, t0, t4, bm, lt);  // - S_II Z'
+    tile_store(t5, acc);
+    load_tile(t1, V + i0 + (int64_t)i0 * ldv, ldv, bm, bm);
+    load_tile(t2, S + j0 + (int64_t)j0 * lds, lds, bn, bn);
+    load_tile(t3, V + j0 + (int64_t)j0 * ldv, ldv, bn, bn);
+    for (int e = threadIdx.x; e < TT; e += blockDim.x) t6[e] = cplx<R>{0, 0};
+    __syncthreads();
+    leaf_p3(t0, t1, t2, t3, t5, t6, bm, bn, &bad);  // t5 = Y_IJ
+    tile_mma(zp, t5, t2, bn, lt);                   // Z_IJ = Z' + Y_IJ S_JJ
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int c = c0 + 4 * q;
+        if (r < bm && c < bn) {
+            C[(i0 + r) + (int64_t)(j0 + c) * ldc] = t5[r + c * TLD];
+            Z[(i0 + r) + (int64_t)(j0 + c) * ldz] = zp[q];
+        }
+    }
+    if (threadIdx.x == 0 && bad) atomicExch(status, 2);
+}
+
 template <class R>
 static cudaError_t set_smem(const void *fn, size_t bytes)
 {
@@ -362,6 +658,53 @@ cudaError_t launch_rtrsyl(const cplx<R> *S, int lds, int m, const cplx<R> *St, i
     return cudaGetLastError();
 }
 
+template <class R>
+cudaError_t launch_tricbrt(const cplx<R> *T, int ldt, cplx<R> *S, int lds, cplx<R> *V, int ldv, int n, int blks,
+                           int *d_status, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int b = blks < 1 ? 1 : (blks > TB ? TB : blks);
+    const int Nb = (n + b - 1) / b;
+    const size_t sm1 = TB * TLD * sizeof(cplx<R>);
+    cudaError_t err;
+    if ((err = set_smem<R>((const void *)tricbrt_diag_kernel<R>, 2 * sm1))) return err;
+    if ((err = set_smem<R>((const void *)tricbrt_off_kernel<R>, 7 * sm1))) return err;
+    tricbrt_diag_kernel<R><<<Nb, kTriThreads, 2 * sm1, s>>>(T, ldt, S, lds, V, ldv, n, b, d_status); count_launch();
+    for (int dblk = 1; dblk < Nb; ++dblk) {
+        tricbrt_off_kernel<R><<<Nb - dblk, kTriThreads, 7 * sm1, s>>>(T, ldt, S, lds, V, ldv, n, b, dblk, d_status);
+        count_launch();
+    }
+    return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_rtrsyl3(const cplx<R> *S, int lds, const cplx<R> *V, int ldv, cplx<R> *C, int ldc, cplx<R> *Z,
+                           int ldz, int n, int blks, int *d_status, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int b = blks < 1 ? 1 : (blks > TB ? TB : blks);
+    const int Nb = (n + b - 1) / b;
+    const size_t sm7 = 7 * TB * TLD * sizeof(cplx<R>);
+    cudaError_t err;
+    if ((err = set_smem<R>((const void *)rtrsyl3_wave_kernel<R>, sm7))) return err;
+    for (int w = 0; w <= 2 * Nb - 2; ++w) {
+        const int ilo = max(0, (Nb - 1) - w), ihi = min(Nb - 1, (Nb - 1) - w + (Nb - 1));
+        const int cnt = ihi - ilo + 1;
+        if (cnt <= 0) continue;
+        rtrsyl3_wave_kernel<R><<<cnt, kTriThreads, sm7, s>>>(S, lds, V, ldv, n, C, ldc, Z, ldz, b, w, d_status);
+        count_launch();
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_tricbrt<float>(const cplx<float> *, int, cplx<float> *, int, cplx<float> *, int, int, int,
+                                           int *, cudaStream_t);
+template cudaError_t launch_tricbrt<double>(const cplx<double> *, int, cplx<double> *, int, cplx<double> *, int, int,
+                                            int, int *, cudaStream_t);
+template cudaError_t launch_rtrsyl3<float>(const cplx<float> *, int, const cplx<float> *, int, cplx<float> *, int,
+                                           cplx<float> *, int, int, int, int *, cudaStream_t);
+template cudaError_t launch_rtrsyl3<double>(const cplx<double> *, int, const cplx<double> *, int, cplx<double> *, int,
+                                            cplx<double> *, int, int, int, int *, cudaStream_t);
 template cudaError_t launch_trisqrt<float>(const cplx<float> *, int, cplx<float> *, int, int, int, int *, cudaStream_t);
 template cudaError_t launch_trisqrt<double>(const cplx<double> *, int, cplx<double> *, int, int, int, int *, cudaStream_t);
 template cudaError_t launch_rtrsyl<float>(const cplx<float> *, int, int, const cplx<float> *, int, int, cplx<float> *, int, int, int *, cudaStream_t);

@@ -21,7 +21,8 @@ def test_headers_declare_entry_points():
     names = _declared()
     for must in ("sqrtm_mixed", "sqrtm_schur_fp64", "sqrtm_backward", "sqrtm_create",
                  "sqrtm_destroy", "sqrtm_mixed_batched", "sqrtm_step_residual",
-                 "sqrtm_step_rtrsyl", "sqrtm_step_schur", "sqrtm_step_trisqrt"):
+                 "sqrtm_step_rtrsyl", "sqrtm_step_schur", "sqrtm_step_trisqrt", "sqrtm_cbrtm_mixed",
+                 "sqrtm_cbrtm_schur_fp64", "sqrtm_step_tricbrt", "sqrtm_step_rtrsyl3"):
         assert must in names
 
 
