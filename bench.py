@@ -352,6 +352,16 @@ def run_profile_mode(args):
     import torch
     import paper_2607_12430_gb300 as mp
     mp.lib()
+    if args.workload == "batch":
+        As = [torch.from_numpy(np.ascontiguousarray(it[1])).cuda()
+              for it in synth.batch_case(count=2048, seed=synth.BASE_SEED + 3)]
+        t0 = time.perf_counter()
+        for _ in range(args.warmup + args.steps):
+            _, st = mp.sqrtm_mixed_batched(As)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_mode": True, "workload": "batch", "calls": args.warmup + args.steps,
+                          "wall_s": time.perf_counter() - t0, "status_nonzero": sum(1 for x in st if x)}), flush=True)
+        return 0
     if args.workload == "spd":
         A_np, _, _ = synth.config_spd4096(n=args.n)
         kind = mp.KIND_SPD
@@ -443,19 +453,70 @@ def run_cbrt_suite(args):
     return 0
 
 
+def run_batch_suite(args):
+    """The batch workload: 2048 matrices, n ~ U{16..256}, half SPD with
+    lambda log-uniform in [1e-2, 1e2], half 2I + G/sqrt(n), through
+    sqrtm_mixed_batched with the default stopping test (tol 1e-12).  One
+    JSON line per mode: "batched" (every matrix through the batched general
+    path) and "per-matrix" (SQRTM_BATCH_MAXN=0: per-matrix calls on 12
+    worker streams); CUDA-event time of one call, mean of --steps calls after
+    one warm-up, the largest relative residual ||X^2 - A|| / ||A|| over all
+    matrices and the statuses."""
+    import torch
+    import paper_2607_12430_gb300 as mp
+    mp.lib()
+    items = synth.batch_case(count=2048, seed=synth.BASE_SEED + 3)
+    As = [torch.from_numpy(np.ascontiguousarray(it[1])).cuda() for it in items]
+    sizes = [A.shape[0] for A in As]
+    modes = [("batched", None), ("per-matrix", "0")]
+    for name, env in modes:
+        old = os.environ.get("SQRTM_BATCH_MAXN")
+        if env is None:
+            os.environ.pop("SQRTM_BATCH_MAXN", None)
+        else:
+            os.environ["SQRTM_BATCH_MAXN"] = env
+        try:
+            Xs, st = mp.sqrtm_mixed_batched(As)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(max(1, args.steps)):
+                s_ = torch.cuda.Event(enable_timing=True)
+                e_ = torch.cuda.Event(enable_timing=True)
+                l0 = mp.kernel_launches()
+                s_.record()
+                Xs, st = mp.sqrtm_mixed_batched(As)
+                e_.record()
+                torch.cuda.synchronize()
+                ts.append(s_.elapsed_time(e_))
+                launches = mp.kernel_launches() - l0
+        finally:
+            if old is None:
+                os.environ.pop("SQRTM_BATCH_MAXN", None)
+            else:
+                os.environ["SQRTM_BATCH_MAXN"] = old
+        res = max(((X @ X - A).norm() / A.norm()).item() for X, A in zip(Xs, As))
+        ms = statistics.mean(ts)
+        print(json.dumps({"suite": "batch", "mode": name, "matrices": len(As), "n_range": [min(sizes), max(sizes)],
+                          "sum_n3": float(sum(float(n) ** 3 for n in sizes)), "ms": ms,
+                          "matrices_per_s": len(As) / (ms / 1e3), "max_rel_residual": res,
+                          "status_counts": {str(k): st.count(k) for k in sorted(set(st))},
+                          "gpu_launches": launches}), flush=True)
+    return 0
+
+
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--profile-mode", action="store_true",
                    help="run only the timed calls (for ncu launch lists)")
     p.add_argument("--kstar", type=int, default=2, help="corrections per call in --profile-mode")
-    p.add_argument("--workload", choices=["general512", "spd"], default="general512",
+    p.add_argument("--workload", choices=["general512", "spd", "batch"], default="general512",
                    help="--profile-mode workload")
     p.add_argument("--n", type=int, default=4096, help="--profile-mode SPD size")
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--suite", choices=["table1", "cbrt"], default=None,
+    p.add_argument("--suite", choices=["table1", "cbrt", "batch"], default=None,
                    help="the paper's Table 1 sets, or the cube root on sets I, II and the n = 512 "
                         "workload (one JSON line each) instead of the benchmark")
     p.add_argument("--sets", nargs="*", default=None, help="--suite: which sets (default all)")
@@ -468,6 +529,8 @@ def main():
         return run_table1_suite(args)
     if args.suite == "cbrt":
         return run_cbrt_suite(args)
+    if args.suite == "batch":
+        return run_batch_suite(args)
     return run_ours(args)
 
 

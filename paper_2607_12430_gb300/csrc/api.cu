@@ -132,6 +132,8 @@ extern "C" int sqrtm_destroy(sqrtm_handle_t h)
     for (auto &e : h->qev)
         if (e) cudaEventDestroy(e);
     if (h->ws.p) cudaFree(h->ws.p);
+    if (h->bws.p) cudaFree(h->bws.p);
+    if (h->bpin) cudaFreeHost(h->bpin);
     if (h->fact.p) cudaFree(h->fact.p);
     if (h->staging.p) cudaFreeHost(h->staging.p);
     for (auto &e : h->ev)
@@ -590,9 +592,25 @@ extern "C" int sqrtm_mixed_batched(sqrtm_handle_t h, int batch, const double *co
     if (!dA || !n || !lda || !dX || !ldx) return -3;
     for (int i = 0; i < batch; ++i)
         if (int rc = check_args(dA[i], n[i], lda[i], dX[i], ldx[i])) return rc;
-    int nw = std::min(batch, 12);
-    if (const char *env = getenv("SQRTM_BATCH_WORKERS")) nw = std::max(1, std::min(batch, atoi(env)));
-    if (int rc = ensure_workers(h, nw)) return rc;
+    sqrtm_opts o;
+    if (int rc = resolve_opts(opts, tol, &o)) return rc;
+    std::vector<int> st(batch, 0);
+    // matrices up to the batched size limit go through the batched general
+    // path (one set of launches for all of them); larger ones, and every
+    // matrix when the SPD algorithm is forced, through per-matrix calls on
+    // worker threads with their own handles and streams, largest first
+    int nbmax = 256;
+    if (const char *env = getenv("SQRTM_BATCH_MAXN")) nbmax = atoi(env);
+    std::vector<int> small, large;
+    for (int i = 0; i < batch; ++i) {
+        if (n[i] == 0) continue;
+        if (o.kind != SQRTM_KIND_SPD && n[i] <= nbmax) small.push_back(i);
+        else large.push_back(i);
+    }
+    const int nw = std::min<int>((int)large.size(), 12);
+    if (nw > 0) {
+        if (int rc = ensure_workers(h, nw)) return rc;
+    }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 7;
     // fence: workers start after the work already on the caller's stream
@@ -600,24 +618,20 @@ extern "C" int sqrtm_mixed_batched(sqrtm_handle_t h, int batch, const double *co
     if (cudaEventCreateWithFlags(&start, cudaEventDisableTiming) != cudaSuccess) return 7;
     cudaEventRecord(start, h->stream);
     for (int w = 0; w < nw; ++w) cudaStreamWaitEvent(h->worker_streams[w], start, 0);
-    std::vector<int> order(batch);
-    for (int i = 0; i < batch; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
-    std::vector<int> st(batch, 0);
+    std::stable_sort(large.begin(), large.end(), [&](int a, int b) { return n[a] > n[b]; });
     std::atomic<int> next{0};
     auto work = [&](int w) {
         cudaSetDevice(dev);
         for (;;) {
             int q = next.fetch_add(1);
-            if (q >= batch) break;
-            int i = order[q];
+            if (q >= (int)large.size()) break;
+            int i = large[q];
             st[i] = sqrtm_mixed(h->workers[w], dA[i], n[i], lda[i], tol, dX[i], ldx[i], opts, nullptr);
-
         }
     };
     std::vector<std::thread> threads;
-    for (int w = 1; w < nw; ++w) threads.emplace_back(work, w);
-    work(0);
+    for (int w = 0; w < nw; ++w) threads.emplace_back(work, w);
+    int rc_small = batched_general(h, small.data(), (int)small.size(), dA, n, lda, dX, ldx, o, st.data());
     for (auto &t : threads) t.join();
     // fence: the caller's stream waits for every worker
     for (int w = 0; w < nw; ++w) {
@@ -625,6 +639,8 @@ extern "C" int sqrtm_mixed_batched(sqrtm_handle_t h, int batch, const double *co
         cudaStreamWaitEvent(h->stream, start, 0);
     }
     cudaEventDestroy(start);
+    if (rc_small)
+        for (int i : small) st[i] = rc_small;
     int first = 0;
     for (int i = 0; i < batch; ++i) {
         if (status) status[i] = st[i];

@@ -16,13 +16,21 @@ template <class R, int OPA, int OPB, bool AREAL, int EPI>
 __global__ void __launch_bounds__(G_THREADS)
 cgemm_kernel(int m, int n, int k, const void *__restrict__ Av, int lda,
              const cplx<R> *__restrict__ B, int ldb, cplx<R> *__restrict__ C, int ldc,
-             double *__restrict__ X, int64_t ldx, double scale)
+             double *__restrict__ X, int64_t ldx, double scale, const GemmJob<R> *__restrict__ jobs)
 {
     __shared__ cplx<R> As[GB_K][GB_M + 1];
     __shared__ cplx<R> Bs[GB_K][GB_N + 1];
     const int tid = threadIdx.x;
     const int tx = tid % 16, ty = tid / 16;
     const int m0 = blockIdx.x * GB_M, n0 = blockIdx.y * GB_N;
+    if (jobs) {  // batched: the n x n product of matrix blockIdx.z, scale 2^e
+        const GemmJob<R> jb = jobs[blockIdx.z];
+        if (!*jb.active) return;
+        m = n = k = lda = ldb = ldc = jb.n;
+        if (m0 >= m || n0 >= n) return;
+        Av = jb.A; B = jb.B; C = jb.C; X = jb.X; ldx = jb.ldx;
+        scale = ldexp(1.0, *jb.e);
+    }
     cplx<R> acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -109,20 +117,20 @@ cgemm_kernel(int m, int n, int k, const void *__restrict__ Av, int lda,
 template <class R, int OPA, int OPB, bool AREAL>
 static cudaError_t dispatch_epi(int epi, dim3 g, cudaStream_t s, int m, int n, int k,
                                 const void *A, int lda, const cplx<R> *B, int ldb, cplx<R> *C,
-                                int ldc, double *X, int64_t ldx, double scale)
+                                int ldc, double *X, int64_t ldx, double scale, const GemmJob<R> *jobs = nullptr)
 {
     switch (epi) {
     case EPI_STORE:
-        cgemm_kernel<R, OPA, OPB, AREAL, EPI_STORE><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale); count_launch();
+        cgemm_kernel<R, OPA, OPB, AREAL, EPI_STORE><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale, jobs); count_launch();
         break;
     case EPI_REAL_TO_F64:
-        cgemm_kernel<R, OPA, OPB, AREAL, EPI_REAL_TO_F64><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale); count_launch();
+        cgemm_kernel<R, OPA, OPB, AREAL, EPI_REAL_TO_F64><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale, jobs); count_launch();
         break;
     case EPI_REAL_ADD_F64:
-        cgemm_kernel<R, OPA, OPB, AREAL, EPI_REAL_ADD_F64><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale); count_launch();
+        cgemm_kernel<R, OPA, OPB, AREAL, EPI_REAL_ADD_F64><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale, jobs); count_launch();
         break;
     default:
-        cgemm_kernel<R, OPA, OPB, AREAL, EPI_REAL_ADD_F64_T><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale); count_launch();
+        cgemm_kernel<R, OPA, OPB, AREAL, EPI_REAL_ADD_F64_T><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale, jobs); count_launch();
     }
     return cudaGetLastError();
 }
@@ -148,6 +156,26 @@ cudaError_t launch_cgemm(int opA, int opB, int m, int n, int k, const void *A, i
 #undef SQM_D
 }
 
+template <class R>
+cudaError_t launch_cgemm_batched(int opA, int opB, bool a_real, int epi, const GemmJob<R> *jobs, int batch, int nmax,
+                                 cudaStream_t s)
+{
+    if (nmax <= 0 || batch <= 0) return cudaSuccess;
+    dim3 g((unsigned)cdiv_i(nmax, GB_M), (unsigned)cdiv_i(nmax, GB_N), (unsigned)batch);
+#define SQM_D(OA, OB, AR) return dispatch_epi<R, OA, OB, AR>(epi, g, s, 0, 0, 0, nullptr, 0, nullptr, 0, nullptr, 0, nullptr, 0, 0.0, jobs)
+    if (a_real) {
+        if (opA == OP_N && opB == OP_N) SQM_D(OP_N, OP_N, true);
+        return cudaErrorInvalidValue;
+    }
+    if (opA == OP_N && opB == OP_N) SQM_D(OP_N, OP_N, false);
+    if (opA == OP_N && opB == OP_H) SQM_D(OP_N, OP_H, false);
+    if (opA == OP_H && opB == OP_N) SQM_D(OP_H, OP_N, false);
+    return cudaErrorInvalidValue;
+#undef SQM_D
+}
+
+template cudaError_t launch_cgemm_batched<float>(int, int, bool, int, const GemmJob<float> *, int, int, cudaStream_t);
+template cudaError_t launch_cgemm_batched<double>(int, int, bool, int, const GemmJob<double> *, int, int, cudaStream_t);
 template cudaError_t launch_cgemm<float>(int, int, int, int, int, const void *, int, bool, const cplx<float> *, int, int, cplx<float> *, int, double *, int64_t, double, cudaStream_t);
 template cudaError_t launch_cgemm<double>(int, int, int, int, int, const void *, int, bool, const cplx<double> *, int, int, cplx<double> *, int, double *, int64_t, double, cudaStream_t);
 
@@ -157,7 +185,8 @@ template cudaError_t launch_cgemm<double>(int, int, int, int, int, const void *,
 __global__ void __launch_bounds__(G_THREADS)
 residual_f64_kernel(const double *__restrict__ A, int64_t lda, const double *__restrict__ X,
                     int64_t ldx, const double *__restrict__ B, int64_t ldb, int n, double sc,
-                    float *__restrict__ Rhat, int ldr, double *__restrict__ partials)
+                    float *__restrict__ Rhat, int ldr, double *__restrict__ partials,
+                    const ResJob *__restrict__ jobs)
 {
     __shared__ double As[GB_K][GB_M + 1];
     __shared__ double Bs[GB_K][GB_N + 1];
@@ -165,6 +194,16 @@ residual_f64_kernel(const double *__restrict__ A, int64_t lda, const double *__r
     const int tid = threadIdx.x;
     const int tx = tid % 16, ty = tid / 16;
     const int m0 = blockIdx.x * GB_M, n0 = blockIdx.y * GB_N;
+    int part = blockIdx.x + blockIdx.y * gridDim.x;
+    if (jobs) {  // batched: R = (A - X X) 4^-e of matrix blockIdx.z
+        const ResJob jb = jobs[blockIdx.z];
+        if (!*jb.active) return;
+        n = ldr = jb.n;
+        if (m0 >= n || n0 >= n) return;
+        A = jb.A; lda = jb.lda; X = B = jb.X; ldx = ldb = jb.ldx; Rhat = jb.Rhat; partials = jb.partials;
+        sc = ldexp(1.0, -2 * *jb.e);
+        part = blockIdx.x + blockIdx.y * cdiv_i(n, GB_M);
+    }
     double acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -218,7 +257,7 @@ residual_f64_kernel(const double *__restrict__ A, int64_t lda, const double *__r
     if (tid == 0) {
         double t = 0.0;
         for (int w = 0; w < G_THREADS / 32; ++w) t += red[w];
-        partials[blockIdx.x + blockIdx.y * gridDim.x] = t;
+        partials[part] = t;
     }
 }
 
@@ -229,7 +268,17 @@ cudaError_t launch_residual_f64(const double *A, int64_t lda, const double *X, i
     dim3 g((unsigned)cdiv_i(n, GB_M), (unsigned)cdiv_i(n, GB_N));
     *nparts = (int)(g.x * g.y);
     if (n <= 0) return cudaSuccess;
-    residual_f64_kernel<<<g, G_THREADS, 0, s>>>(A, lda, X, ldx, X, ldx, n, ldexp(1.0, -2 * e), Rhat, ldr, partials);
+    residual_f64_kernel<<<g, G_THREADS, 0, s>>>(A, lda, X, ldx, X, ldx, n, ldexp(1.0, -2 * e), Rhat, ldr, partials,
+                                                nullptr);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual_batched(const ResJob *jobs, int batch, int nmax, cudaStream_t s)
+{
+    if (nmax <= 0 || batch <= 0) return cudaSuccess;
+    dim3 g((unsigned)cdiv_i(nmax, GB_M), (unsigned)cdiv_i(nmax, GB_N), (unsigned)batch);
+    residual_f64_kernel<<<g, G_THREADS, 0, s>>>(nullptr, 0, nullptr, 0, nullptr, 0, 0, 0.0, nullptr, 0, nullptr, jobs);
     count_launch();
     return cudaGetLastError();
 }
@@ -241,7 +290,8 @@ cudaError_t launch_residual_f64_ab(const double *A, int64_t lda, const double *X
     dim3 g((unsigned)cdiv_i(n, GB_M), (unsigned)cdiv_i(n, GB_N));
     *nparts = (int)(g.x * g.y);
     if (n <= 0) return cudaSuccess;
-    residual_f64_kernel<<<g, G_THREADS, 0, s>>>(A, lda, X, ldx, B, ldb, n, ldexp(1.0, -shift), Rhat, ldr, partials);
+    residual_f64_kernel<<<g, G_THREADS, 0, s>>>(A, lda, X, ldx, B, ldb, n, ldexp(1.0, -shift), Rhat, ldr, partials,
+                                                nullptr);
     count_launch();
     return cudaGetLastError();
 }

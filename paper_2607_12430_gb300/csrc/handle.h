@@ -48,6 +48,10 @@ struct sqrtm_handle_s {
     };
     std::vector<Graph> graphs;
     cudaStream_t cap_stream = nullptr;
+    // batched general path: device arena and pinned host buffer
+    Buf bws;
+    void *bpin = nullptr;
+    size_t bpin_bytes = 0;
     // batched calls: worker handles, each on its own non-blocking stream
     char last_error[160] = {0};
     std::vector<sqrtm_handle_s *> workers;
@@ -95,6 +99,11 @@ void note_error(sqrtm_handle_t h, const char *what, int line, int code);
         }                                                     \
     } while (0)
 
+
+// The batched general path (batch.cu) for the matrices idx[0 .. count) of a
+// batched call (n <= 46340 each); statuses into st_out[idx[i]].  Returns 0 or 7.
+int batched_general(sqrtm_handle_t h, const int *idx, int count, const double *const *dA, const int64_t *n,
+                    const int64_t *lda, double *const *dX, const int64_t *ldx, const sqrtm_opts &o, int *st_out);
 
 // SPD path (Algorithm 3) and its FP64 counterpart, spd.cu
 int spd_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, double tol, double *dX,

@@ -67,6 +67,51 @@ struct SchurDesc {
     int ld;
 };
 
+// ---- batched general path: one entry per matrix (device arrays) ----
+// Every batched launch covers all matrices (grid y or z = matrix index);
+// an entry whose *active is 0 returns at once, as do the tiles beyond its n.
+// All matrices are n x n with leading dimension n unless stated.
+template <class R>
+struct TriJob {
+    const cplx<R> *T;   // triangular square root: T in, S out
+    cplx<R> *S;
+    cplx<R> *C;         // Sylvester solve S Y + Y S = C: C in, Y out
+    int *status;        // receives 2 (see launch_trisqrt)
+    const int *active;
+    int n;
+};
+template <class R>
+struct GemmJob {
+    const void *A;      // R (a_real) or cplx<R>
+    const cplx<R> *B;
+    cplx<R> *C;         // EPI_STORE output
+    double *X;          // FP64 epilogues: X (ldx), scaled by 2^(*e)
+    int64_t ldx;
+    const int *e;
+    const int *active;
+    int n;
+};
+struct ResJob {
+    const double *A;    // R = (A - X X) 4^-e into Rhat (FP32, ld n) and the
+    int64_t lda;        // per-tile partial sums of |R|^2 into partials
+    const double *X;    // (tile (i, j) at i + j cdiv(n, 64))
+    int64_t ldx;
+    float *Rhat;
+    double *partials;
+    const int *e;
+    const int *active;
+    int n;
+};
+template <class R>
+cudaError_t launch_trisqrt_batched(const TriJob<R> *jobs, int batch, int nmax, int blks, cudaStream_t s);
+template <class R>
+cudaError_t launch_rtrsyl_batched(const TriJob<R> *jobs, int batch, int nmax, int blks, cudaStream_t s);
+// op pairs: (N, N), (N, H), (H, N); a_real only with (N, N)
+template <class R>
+cudaError_t launch_cgemm_batched(int opA, int opB, bool a_real, int epi, const GemmJob<R> *jobs, int batch, int nmax,
+                                 cudaStream_t s);
+cudaError_t launch_residual_batched(const ResJob *jobs, int batch, int nmax, cudaStream_t s);
+
 // ---- scaling / norms (scale.cu) ----
 // Deterministic ||A||_F: partials[nblk] then finalize; writes norm and e, the
 // scaling exponent for a root of order `root`: A_s = 2^(-root e) A has

@@ -117,12 +117,19 @@ __device__ void leaf_sylvester(const cplx<R> *A, const cplx<R> *B, cplx<R> *C, i
 template <class R>
 __global__ void __launch_bounds__(SylCfg<R>::THREADS)
 rtrsyl_wave_kernel(const cplx<R> *__restrict__ S, int lds, int m, const cplx<R> *__restrict__ St,
-                   int ldst, int nn, cplx<R> *C, int ldc, int b, int w, int *status)
+                   int ldst, int nn, cplx<R> *C, int ldc, int b, int w, int *status,
+                   const TriJob<R> *__restrict__ jobs)
 {
     extern __shared__ unsigned char smraw[];
     constexpr int TT = TB * TLD, kSylGroups = SylCfg<R>::G;
     cplx<R> *tc = reinterpret_cast<cplx<R> *>(smraw);
     __shared__ int bad;
+    if (jobs) {  // batched: matrix blockIdx.y solves S Y + Y S = C
+        const TriJob<R> jb = jobs[blockIdx.y];
+        if (!*jb.active) return;
+        S = jb.S; St = jb.S; C = jb.C; status = jb.status;
+        m = nn = lds = ldst = ldc = jb.n;
+    }
     const int Mb = (m + b - 1) / b, Nb = (nn + b - 1) / b;
     const int I = max(0, (Mb - 1) - w) + blockIdx.x;
     const int J = I + w - (Mb - 1);
@@ -199,13 +206,20 @@ rtrsyl_wave_kernel(const cplx<R> *__restrict__ S, int lds, int m, const cplx<R> 
 template <class R>
 __global__ void __launch_bounds__(kTriThreads)
 trisqrt_diag_kernel(const cplx<R> *__restrict__ T, int ldt, cplx<R> *S, int lds, int n, int b,
-                    int *status)
+                    int *status, const TriJob<R> *__restrict__ jobs)
 {
     extern __shared__ unsigned char smraw[];
     cplx<R> *ts = reinterpret_cast<cplx<R> *>(smraw);  // T block, overwritten by S
     __shared__ int bad;
+    if (jobs) {  // batched: matrix blockIdx.y
+        const TriJob<R> jb = jobs[blockIdx.y];
+        if (!*jb.active) return;
+        T = jb.T; S = jb.S; status = jb.status;
+        n = ldt = lds = jb.n;
+    }
     const int I = blockIdx.x;
     const int i0 = I * b, bm = min(b, n - i0);
+    if (bm <= 0) return;
     if (threadIdx.x == 0) bad = 0;
     load_tile(ts, T + i0 + (int64_t)i0 * ldt, ldt, bm, bm);
     __syncthreads();
@@ -251,12 +265,18 @@ trisqrt_diag_kernel(const cplx<R> *__restrict__ T, int ldt, cplx<R> *S, int lds,
 template <class R>
 __global__ void __launch_bounds__(SylCfg<R>::THREADS)
 trisqrt_off_kernel(const cplx<R> *__restrict__ T, int ldt, cplx<R> *S, int lds, int n, int b,
-                   int dblk, int *status)
+                   int dblk, int *status, const TriJob<R> *__restrict__ jobs)
 {
     extern __shared__ unsigned char smraw[];
     constexpr int TT = TB * TLD, G = SylCfg<R>::G;
     cplx<R> *tc = reinterpret_cast<cplx<R> *>(smraw);
     __shared__ int bad;
+    if (jobs) {  // batched: matrix blockIdx.y
+        const TriJob<R> jb = jobs[blockIdx.y];
+        if (!*jb.active) return;
+        T = jb.T; S = jb.S; status = jb.status;
+        n = ldt = lds = jb.n;
+    }
     const int Nb = (n + b - 1) / b;
     const int I = blockIdx.x, J = I + dblk;
     if (J >= Nb) return;
@@ -632,9 +652,30 @@ cudaError_t launch_trisqrt(const cplx<R> *T, int ldt, cplx<R> *S, int lds, int n
     size_t sm1 = TB * TLD * sizeof(cplx<R>), sm3 = (1 + 4 * SylCfg<R>::G) * sm1;
     cudaError_t err;
     if ((err = set_smem<R>((const void *)trisqrt_off_kernel<R>, sm3))) return err;
-    trisqrt_diag_kernel<R><<<Nb, kTriThreads, sm1, s>>>(T, ldt, S, lds, n, b, d_status); count_launch();
-    for (int dblk = 1; dblk < Nb; ++dblk)
-        trisqrt_off_kernel<R><<<Nb - dblk, SylCfg<R>::THREADS, sm3, s>>>(T, ldt, S, lds, n, b, dblk, d_status); count_launch();
+    trisqrt_diag_kernel<R><<<Nb, kTriThreads, sm1, s>>>(T, ldt, S, lds, n, b, d_status, nullptr); count_launch();
+    for (int dblk = 1; dblk < Nb; ++dblk) {
+        trisqrt_off_kernel<R><<<Nb - dblk, SylCfg<R>::THREADS, sm3, s>>>(T, ldt, S, lds, n, b, dblk, d_status, nullptr);
+        count_launch();
+    }
+    return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_trisqrt_batched(const TriJob<R> *jobs, int batch, int nmax, int blks, cudaStream_t s)
+{
+    if (nmax <= 0 || batch <= 0) return cudaSuccess;
+    const int b = blks < 1 ? 1 : (blks > TB ? TB : blks);
+    const int Nb = (nmax + b - 1) / b;
+    const size_t sm1 = TB * TLD * sizeof(cplx<R>), sm3 = (1 + 4 * SylCfg<R>::G) * sm1;
+    cudaError_t err;
+    if ((err = set_smem<R>((const void *)trisqrt_off_kernel<R>, sm3))) return err;
+    trisqrt_diag_kernel<R><<<dim3(Nb, batch), kTriThreads, sm1, s>>>(nullptr, 0, nullptr, 0, 0, b, nullptr, jobs);
+    count_launch();
+    for (int dblk = 1; dblk < Nb; ++dblk) {
+        trisqrt_off_kernel<R><<<dim3(Nb - dblk, batch), SylCfg<R>::THREADS, sm3, s>>>(nullptr, 0, nullptr, 0, 0, b, dblk,
+                                                                                      nullptr, jobs);
+        count_launch();
+    }
     return cudaGetLastError();
 }
 
@@ -653,7 +694,27 @@ cudaError_t launch_rtrsyl(const cplx<R> *S, int lds, int m, const cplx<R> *St, i
         int ihi = min(Mb - 1, (Mb - 1) - w + (Nb - 1));
         int cnt = ihi - ilo + 1;
         if (cnt <= 0) continue;
-        rtrsyl_wave_kernel<R><<<cnt, SylCfg<R>::THREADS, sm3, s>>>(S, lds, m, St, ldst, nn, C, ldc, b, w, d_status); count_launch();
+        rtrsyl_wave_kernel<R><<<cnt, SylCfg<R>::THREADS, sm3, s>>>(S, lds, m, St, ldst, nn, C, ldc, b, w, d_status, nullptr); count_launch();
+    }
+    return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_rtrsyl_batched(const TriJob<R> *jobs, int batch, int nmax, int blks, cudaStream_t s)
+{
+    if (nmax <= 0 || batch <= 0) return cudaSuccess;
+    const int b = blks < 1 ? 1 : (blks > TB ? TB : blks);
+    const int Nb = (nmax + b - 1) / b;
+    const size_t sm3 = (1 + 4 * SylCfg<R>::G) * TB * TLD * sizeof(cplx<R>);
+    cudaError_t err;
+    if ((err = set_smem<R>((const void *)rtrsyl_wave_kernel<R>, sm3))) return err;
+    // wavefront w of every matrix at once (a matrix with fewer blocks is done
+    // after its own 2 Nb_i - 1 wavefronts; its blocks of later ones return)
+    for (int w = 0; w <= 2 * Nb - 2; ++w) {
+        const int cnt = min(w, 2 * Nb - 2 - w) + 1;
+        rtrsyl_wave_kernel<R><<<dim3(cnt, batch), SylCfg<R>::THREADS, sm3, s>>>(nullptr, 0, 0, nullptr, 0, 0, nullptr, 0, b,
+                                                                                 w, nullptr, jobs);
+        count_launch();
     }
     return cudaGetLastError();
 }
@@ -701,6 +762,10 @@ template cudaError_t launch_tricbrt<float>(const cplx<float> *, int, cplx<float>
                                            int *, cudaStream_t);
 template cudaError_t launch_tricbrt<double>(const cplx<double> *, int, cplx<double> *, int, cplx<double> *, int, int,
                                             int, int *, cudaStream_t);
+template cudaError_t launch_trisqrt_batched<float>(const TriJob<float> *, int, int, int, cudaStream_t);
+template cudaError_t launch_trisqrt_batched<double>(const TriJob<double> *, int, int, int, cudaStream_t);
+template cudaError_t launch_rtrsyl_batched<float>(const TriJob<float> *, int, int, int, cudaStream_t);
+template cudaError_t launch_rtrsyl_batched<double>(const TriJob<double> *, int, int, int, cudaStream_t);
 template cudaError_t launch_rtrsyl3<float>(const cplx<float> *, int, const cplx<float> *, int, cplx<float> *, int,
                                            cplx<float> *, int, int, int, int *, cudaStream_t);
 template cudaError_t launch_rtrsyl3<double>(const cplx<double> *, int, const cplx<double> *, int, cplx<double> *, int,
