@@ -37,7 +37,7 @@ struct BState {
     int st_schur;            // Schur stage status
     int st_solve;            // triangular square root / Sylvester status
     int hist_len;
-    int pad;
+    int k;                   // convergence tests done (the step index)
     double hist[SQRTM_MAX_HISTORY];
 };
 
@@ -51,6 +51,7 @@ struct BParams {
     double tol;
     int fixed;     // 1: apply exactly `steps` corrections, no test
     int max_corr;  // adaptive: at most this many corrections
+    int nactive;   // matrices still taking corrections after the last test
 };
 
 static constexpr int kBNormThreads = 256;
@@ -90,7 +91,7 @@ bnorm_kernel(const BInput *__restrict__ in, BState *__restrict__ st)
     q.prev = INFINITY;
     q.e = e;
     q.active = status == 0;
-    q.applied = q.grew = q.hist_len = 0;
+    q.applied = q.grew = q.hist_len = q.k = 0;
     q.status = status;
     q.st_schur = q.st_solve = 0;
 }
@@ -130,7 +131,7 @@ __global__ void bfold_kernel(BState *__restrict__ st, int batch)
 // matrix, on the device: ||R||_F from the residual's partial sums (fixed
 // order), then stop on the tolerance, the step limit (status 1), a non-finite
 // residual or two growths in a row (status 4)
-__global__ void bdecide_kernel(BState *__restrict__ st, int batch, int k, const BParams *__restrict__ prm)
+__global__ void bdecide_kernel(BState *__restrict__ st, int batch, BParams *__restrict__ prm)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= batch) return;
@@ -141,12 +142,14 @@ __global__ void bdecide_kernel(BState *__restrict__ st, int batch, int k, const 
         q.active = 0;
         return;
     }
+    const int k = q.k++;
     double s = 0.0;
     for (int i = 0; i < q.np; ++i) s += q.partials[i];
     const double rn = sqrt(s), rel = rn / q.norm_as;
     if (q.hist_len < SQRTM_MAX_HISTORY) q.hist[q.hist_len++] = rel;
     if (prm->fixed) {
         ++q.applied;
+        atomicAdd(&prm->nactive, 1);
         return;
     }
     int stop = -1;
@@ -164,6 +167,7 @@ __global__ void bdecide_kernel(BState *__restrict__ st, int batch, int k, const 
     }
     q.prev = rn;
     ++q.applied;
+    atomicAdd(&prm->nactive, 1);
 }
 
 namespace {
@@ -174,6 +178,7 @@ namespace {
 template <class R>
 struct BLayout {
     SchurDesc<R> *desc;
+    HessJob<R> *hj;
     TriJob<R> *tri;
     GemmJob<R> *gj;  // 6 sets of `batch` products
     ResJob *rj;
@@ -189,6 +194,7 @@ BLayout<R> carve_header(Carve &c, int batch)
 {
     BLayout<R> L;
     L.desc = c.take<SchurDesc<R>>(batch);
+    L.hj = c.take<HessJob<R>>(batch);
     L.tri = c.take<TriJob<R>>(batch);
     L.gj = c.take<GemmJob<R>>(6 * (size_t)batch);
     L.rj = c.take<ResJob>(batch);
@@ -215,12 +221,15 @@ size_t matrix_bytes(int64_t n)
 struct LoopCtx {
     const void *tri, *gj, *rj;
     BState *st;
-    const BParams *prm;
-    int batch, nmax, blks, iters;
+    BParams *prm;
+    int batch, nmax, blks;
 };
 
+// one step of the refinement for every matrix still active: R = (A - X X)
+// 4^-e and ||R||_F, the test (which also counts the matrices that go on),
+// then R~ = Q^H Rhat Q, S Y + Y S = R~, X += 2^e Re(Q Y Q^H)
 template <class R>
-cudaError_t enqueue_refine(void *p, cudaStream_t s)
+cudaError_t enqueue_refine_step(void *p, cudaStream_t s)
 {
     const LoopCtx *c = (const LoopCtx *)p;
     const TriJob<R> *tri = (const TriJob<R> *)c->tri;
@@ -228,17 +237,14 @@ cudaError_t enqueue_refine(void *p, cudaStream_t s)
     const ResJob *rj = (const ResJob *)c->rj;
     const int B = c->batch, nm = c->nmax;
     cudaError_t err;
-    for (int k = 0; k < c->iters; ++k) {
-        // R = (A - X X) 4^-e, ||R||_F, the test; then R~ = Q^H Rhat Q,
-        // S Y + Y S = R~, X += 2^e Re(Q Y Q^H) for the matrices still active
-        if ((err = launch_residual_batched(rj, B, nm, s))) return err;
-        bdecide_kernel<<<cdiv_i(B, 128), 128, 0, s>>>(c->st, B, k, c->prm); count_launch();
-        if ((err = launch_cgemm_batched<R>(OP_N, OP_N, true, EPI_STORE, gj + 2 * B, B, nm, s))) return err;
-        if ((err = launch_cgemm_batched<R>(OP_H, OP_N, false, EPI_STORE, gj + 3 * B, B, nm, s))) return err;
-        if ((err = launch_rtrsyl_batched<R>(tri, B, nm, c->blks, s))) return err;
-        if ((err = launch_cgemm_batched<R>(OP_N, OP_N, false, EPI_STORE, gj + 4 * B, B, nm, s))) return err;
-        if ((err = launch_cgemm_batched<R>(OP_N, OP_H, false, EPI_REAL_ADD_F64, gj + 5 * B, B, nm, s))) return err;
-    }
+    if ((err = cudaMemsetAsync(&c->prm->nactive, 0, sizeof(int), s))) return err;
+    if ((err = launch_residual_batched(rj, B, nm, s))) return err;
+    bdecide_kernel<<<cdiv_i(B, 128), 128, 0, s>>>(c->st, B, c->prm); count_launch();
+    if ((err = launch_cgemm_batched<R>(OP_N, OP_N, true, EPI_STORE, gj + 2 * B, B, nm, s))) return err;
+    if ((err = launch_cgemm_batched<R>(OP_H, OP_N, false, EPI_STORE, gj + 3 * B, B, nm, s))) return err;
+    if ((err = launch_rtrsyl_batched<R>(tri, B, nm, c->blks, s))) return err;
+    if ((err = launch_cgemm_batched<R>(OP_N, OP_N, false, EPI_STORE, gj + 4 * B, B, nm, s))) return err;
+    if ((err = launch_cgemm_batched<R>(OP_N, OP_H, false, EPI_REAL_ADD_F64, gj + 5 * B, B, nm, s))) return err;
     return cudaGetLastError();
 }
 
@@ -296,6 +302,7 @@ int batched_general(sqrtm_handle_t h, const int *idx, int count, const double *c
     hdr.assign(L.hdr_bytes, 0);
     auto host = [&](const void *dev) { return hdr.data() + ((const char *)dev - (const char *)h->bws.p); };
     SchurDesc<R> *hdesc = (SchurDesc<R> *)host(L.desc);
+    HessJob<R> *hhj = (HessJob<R> *)host(L.hj);
     TriJob<R> *htri = (TriJob<R> *)host(L.tri);
     GemmJob<R> *hgj = (GemmJob<R> *)host(L.gj);
     ResJob *hrj = (ResJob *)host(L.rj);
@@ -333,6 +340,7 @@ int batched_general(sqrtm_handle_t h, const int *idx, int count, const double *c
         BState *q = L.st + i;
         d.status = &q->st_schur;
         htri[i] = TriJob<R>{T, S, Rt, &q->st_solve, &q->active, (int)nm};
+        hhj[i] = HessJob<R>{T, Q, (R *)W, (R *)Rt, (int)nm};  // W, Rt: free until the Schur form is done
         hin[i] = BInput{dA[m], lda[m], (int)nm};
         // products: 0 W = Q S, 1 X = 2^e Re(W Q^H), 2 W = Rhat Q, 3 Rt = Q^H W,
         // 4 W = Q Rt, 5 X += 2^e Re(W Q^H)
@@ -352,9 +360,23 @@ int batched_general(sqrtm_handle_t h, const int *idx, int count, const double *c
     bcast_kernel<R><<<dim3(std::max(1, std::min(64, nmax * nmax / 1024)), B), 256, 0, s>>>(L.in, L.st, L.desc);
     count_launch();
     SQM_CU(cudaGetLastError());
-    {
-        HessCtx hc{L.desc, B, nmax};
-        if (run_graph(h, 300, L.desc, nmax, B, enqueue_hess<R>, &hc)) return 7;
+    // Hessenberg reduction: one cluster per matrix, one launch per size
+    // class (the sizes are sorted, so each class is a contiguous range);
+    // the per-column kernels for sizes beyond the cluster kernel's
+    for (int i0 = 0; i0 < B;) {
+        const int nc = (int)n[ord[i0]];
+        const int cap = nc <= 64 ? 0 : nc <= 128 ? 64 : nc <= 256 ? 128 : nc <= 512 ? 256 : 512;
+        int i1 = i0;
+        while (i1 < B && (int)n[ord[i1]] > cap) ++i1;
+        cudaError_t err = launch_hessenberg_cluster_batched<R>(L.hj + i0, i1 - i0, nc, s);
+        if (err == cudaErrorNotSupported) {
+            cudaGetLastError();
+            HessCtx hc{L.desc + i0, i1 - i0, nc};
+            if (run_graph(h, 300, L.desc + i0, nc, i1 - i0, enqueue_hess<R>, &hc)) return 7;
+        } else {
+            SQM_CU(err);
+        }
+        i0 = i1;
     }
     SQM_CU(launch_qr_sweeps<R>(L.desc, B, nmax, (int *)h->bpin, L.qstate, s));
     SQM_CU(launch_trisqrt_batched<R>(L.tri, B, nmax, o.blks, s));
@@ -362,10 +384,15 @@ int batched_general(sqrtm_handle_t h, const int *idx, int count, const double *c
     // X_0 = 2^e Re(Q S Q^H), rounded to FP32
     SQM_CU(launch_cgemm_batched<R>(OP_N, OP_N, false, EPI_STORE, L.gj, B, nmax, s));
     SQM_CU(launch_cgemm_batched<R>(OP_N, OP_H, false, EPI_REAL_TO_F64, L.gj + B, B, nmax, s));
-    if (iters > 0) {
-        LoopCtx lc{L.tri, L.gj, L.rj, L.st, L.prm, B, nmax, o.blks, iters};
-        if (run_graph(h, 100000 + 1000 * o.blks + 2 * iters + (int)fixed, L.desc, nmax, B, enqueue_refine<R>, &lc))
-            return 7;
+    // the refinement, one replayed graph per step; after each step the host
+    // reads how many matrices go on and stops when none does
+    int *h_nact = (int *)((char *)h->bpin + sizeof(int) * kQrStateInts * (size_t)B + sizeof(BState) * (size_t)B);
+    for (int k = 0; k < iters; ++k) {
+        LoopCtx lc{L.tri, L.gj, L.rj, L.st, L.prm, B, nmax, o.blks};
+        if (run_graph(h, 100000 + o.blks, L.desc, nmax, B, enqueue_refine_step<R>, &lc)) return 7;
+        SQM_CU(cudaMemcpyAsync(h_nact, &L.prm->nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SQM_CU(cudaStreamSynchronize(s));
+        if (*h_nact == 0) break;
     }
     bfold_kernel<<<cdiv_i(B, 128), 128, 0, s>>>(L.st, B); count_launch();
     BState *hst = (BState *)((char *)h->bpin + sizeof(int) * kQrStateInts * (size_t)B);

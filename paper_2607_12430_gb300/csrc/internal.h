@@ -138,6 +138,20 @@ template <class R>
 int hess_cluster_size(int n);
 template <class R>
 cudaError_t launch_hessenberg_cluster(cplx<R> *T, cplx<R> *Q, int n, int ld, R *V, R *betas, cudaStream_t s);
+// The register-resident cluster reduction for count matrices of sizes
+// n_i <= nmax (nmax <= 512; FP64: <= 128), one cluster per matrix in one
+// launch.  V: n_i x n_i of R scratch, betas: n_i of R, per job.
+// cudaErrorNotSupported when nmax is too large for the kernel.
+template <class R>
+struct HessJob {
+    cplx<R> *T;
+    cplx<R> *Q;
+    R *V;
+    R *betas;
+    int n;
+};
+template <class R>
+cudaError_t launch_hessenberg_cluster_batched(const HessJob<R> *jobs, int count, int nmax, cudaStream_t s);
 // d_state_all: the kQrStateInts-int state blocks of all matrices, contiguous
 // (descs[b].state == d_state_all + kQrStateInts b); h_state: pinned host
 // buffer of kQrStateInts * batch ints.  ms_chase (may be null) receives the

@@ -1298,15 +1298,18 @@ __global__ void qr_mark_unfinished_kernel(const SchurDesc<R> *__restrict__ descs
 }
 
 template <class R>
-int qr_rows_per_cta(int nmax)
+int qr_rows_per_cta(int nmax, int batch)
 {
     constexpr int RRMAX = QrDims<R>::RR;
     size_t per = (size_t)(std::max(nmax, 1) + 1) * sizeof(cplx<R>);
     size_t avail = 200 * 1024 - 2 * (size_t)RRMAX * RRMAX * sizeof(cplx<R>) - (size_t)std::max(nmax, 1) * sizeof(int);
     size_t r = avail / per;
-    // about 128 row blocks per matrix: the passes of the last round are not
-    // overlapped with a chase, so they should spread over many SMs
-    const size_t want = (size_t)cdiv_i(std::max(nmax, 1), 128);
+    // one matrix: about 128 row blocks, as the passes of the last round are
+    // not overlapped with a chase and should spread over many SMs; a batch:
+    // about 8 CTAs per SM over all matrices, since every CTA reads each
+    // window's rotation product once, whatever its number of rows
+    const size_t want = batch > 1 ? (size_t)cdiv_i((int64_t)std::max(nmax, 1) * batch, 152 * 8)
+                                  : (size_t)cdiv_i(std::max(nmax, 1), 128);
     return (int)std::max<size_t>(1, std::min<size_t>(std::min<size_t>(32, r), want));
 }
 
@@ -1317,7 +1320,7 @@ cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, in
                              int *d_sync)
 {
     constexpr int RRMAX = QrDims<R>::RR;
-    const int rpc = qr_rows_per_cta<R>(nmax);
+    const int rpc = qr_rows_per_cta<R>(nmax, batch);
     const size_t ubytes = 2 * (size_t)RRMAX * RRMAX * sizeof(cplx<R>);
     const size_t mbytes = (size_t)std::max(nmax, 1) * sizeof(int);  // write-back masks
     const size_t rows_bytes = (size_t)rpc * nmax * sizeof(cplx<R>) + ubytes + mbytes;

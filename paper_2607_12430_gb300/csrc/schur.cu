@@ -339,11 +339,16 @@ hess_cluster_kernel(cplx<R> *__restrict__ T, cplx<R> *__restrict__ Q, int n, int
 template <class R, int RPL>
 __global__ void __launch_bounds__(kHessClThreads, 1)
 hess_cluster_reg_kernel(cplx<R> *__restrict__ T, cplx<R> *__restrict__ Q, int n, int ld, R *__restrict__ Vg,
-                        R *__restrict__ betas)
+                        R *__restrict__ betas, const HessJob<R> *__restrict__ jobs)
 {
     constexpr int NW = kHessClThreads / 32, CPW = 4, PLD = 32 * RPL + 1;
     cg::cluster_group cl = cg::this_cluster();
     const int CL = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    if (jobs) {  // batched: cluster c of the grid reduces matrix c
+        const HessJob<R> jb = jobs[blockIdx.x / CL];
+        T = jb.T; Q = jb.Q; Vg = jb.V; betas = jb.betas;
+        n = ld = jb.n;
+    }
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ncl = rank < n ? (n - rank + CL - 1) / CL : 0;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -632,10 +637,53 @@ static cudaError_t launch_hess_reg(cplx<R> *T, cplx<R> *Q, int n, int ld, R *V, 
     cfg.stream = s;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    err = cudaLaunchKernelEx(&cfg, hess_cluster_reg_kernel<R, RPL>, T, Q, n, ld, V, betas);
+    err = cudaLaunchKernelEx(&cfg, hess_cluster_reg_kernel<R, RPL>, T, Q, n, ld, V, betas,
+                             (const HessJob<R> *)nullptr);
     count_launch();
     return err;
 }
+
+template <class R, int RPL>
+static cudaError_t launch_hess_reg_batched(const HessJob<R> *jobs, int count, int CL, cudaStream_t s)
+{
+    constexpr size_t smem = hess_reg_smem<R, RPL>();
+    cudaError_t err = cudaFuncSetAttribute((const void *)hess_cluster_reg_kernel<R, RPL>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err) return err;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(CL * count);
+    cfg.blockDim = dim3(kHessClThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    err = cudaLaunchKernelEx(&cfg, hess_cluster_reg_kernel<R, RPL>, (cplx<R> *)nullptr, (cplx<R> *)nullptr, 0, 0,
+                             (R *)nullptr, (R *)nullptr, jobs);
+    count_launch();
+    return err;
+}
+
+template <class R>
+cudaError_t launch_hessenberg_cluster_batched(const HessJob<R> *jobs, int count, int nmax, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    const int rpl = hess_reg_rpl<R>(std::max(nmax, 3));
+    if (!rpl || hess_cluster_size<R>(std::max(nmax, 3)) == 0) return cudaErrorNotSupported;
+    int CL = 1;
+    while ((std::max(nmax, 3) + CL - 1) / CL > 64) CL *= 2;
+    switch (rpl) {
+    case 2: return launch_hess_reg_batched<R, 2>(jobs, count, CL, s);
+    case 4: return launch_hess_reg_batched<R, 4>(jobs, count, CL, s);
+    case 8: return launch_hess_reg_batched<R, sizeof(R) == sizeof(double) ? 4 : 8>(jobs, count, CL, s);
+    default: return launch_hess_reg_batched<R, sizeof(R) == sizeof(double) ? 4 : 16>(jobs, count, CL, s);
+    }
+}
+
+template cudaError_t launch_hessenberg_cluster_batched<float>(const HessJob<float> *, int, int, cudaStream_t);
+template cudaError_t launch_hessenberg_cluster_batched<double>(const HessJob<double> *, int, int, cudaStream_t);
 
 template <class R>
 cudaError_t launch_hessenberg_cluster(cplx<R> *T, cplx<R> *Q, int n, int ld, R *V, R *betas, cudaStream_t s)

@@ -114,14 +114,14 @@ __device__ void leaf_sylvester(const cplx<R> *A, const cplx<R> *B, cplx<R> *C, i
 // (each with its own double-buffered tiles and named barrier); the partial
 // sums are added in group order, then the leaf is solved.
 // ---------------------------------------------------------------------------
-template <class R>
-__global__ void __launch_bounds__(SylCfg<R>::THREADS)
+template <class R, int G = SylCfg<R>::G>
+__global__ void __launch_bounds__(kTriThreads * G)
 rtrsyl_wave_kernel(const cplx<R> *__restrict__ S, int lds, int m, const cplx<R> *__restrict__ St,
                    int ldst, int nn, cplx<R> *C, int ldc, int b, int w, int *status,
                    const TriJob<R> *__restrict__ jobs)
 {
     extern __shared__ unsigned char smraw[];
-    constexpr int TT = TB * TLD, kSylGroups = SylCfg<R>::G;
+    constexpr int TT = TB * TLD, kSylGroups = G;
     cplx<R> *tc = reinterpret_cast<cplx<R> *>(smraw);
     __shared__ int bad;
     if (jobs) {  // batched: matrix blockIdx.y solves S Y + Y S = C
@@ -262,13 +262,13 @@ trisqrt_diag_kernel(const cplx<R> *__restrict__ T, int ldt, cplx<R> *S, int lds,
     if (threadIdx.x == 0 && bad) atomicExch(status, 2);
 }
 
-template <class R>
-__global__ void __launch_bounds__(SylCfg<R>::THREADS)
+template <class R, int G_ = SylCfg<R>::G>
+__global__ void __launch_bounds__(kTriThreads * G_)
 trisqrt_off_kernel(const cplx<R> *__restrict__ T, int ldt, cplx<R> *S, int lds, int n, int b,
                    int dblk, int *status, const TriJob<R> *__restrict__ jobs)
 {
     extern __shared__ unsigned char smraw[];
-    constexpr int TT = TB * TLD, G = SylCfg<R>::G;
+    constexpr int TT = TB * TLD, G = G_;
     cplx<R> *tc = reinterpret_cast<cplx<R> *>(smraw);
     __shared__ int bad;
     if (jobs) {  // batched: matrix blockIdx.y
@@ -666,14 +666,17 @@ cudaError_t launch_trisqrt_batched(const TriJob<R> *jobs, int batch, int nmax, i
     if (nmax <= 0 || batch <= 0) return cudaSuccess;
     const int b = blks < 1 ? 1 : (blks > TB ? TB : blks);
     const int Nb = (nmax + b - 1) / b;
-    const size_t sm1 = TB * TLD * sizeof(cplx<R>), sm3 = (1 + 4 * SylCfg<R>::G) * sm1;
+    // one group of 128 threads per block: a batch of small matrices has few
+    // update terms per block and many blocks, so the smaller footprint (5
+    // tiles) lets several blocks share an SM
+    const size_t sm1 = TB * TLD * sizeof(cplx<R>), sm3 = 5 * sm1;
     cudaError_t err;
-    if ((err = set_smem<R>((const void *)trisqrt_off_kernel<R>, sm3))) return err;
+    if ((err = set_smem<R>((const void *)trisqrt_off_kernel<R, 1>, sm3))) return err;
     trisqrt_diag_kernel<R><<<dim3(Nb, batch), kTriThreads, sm1, s>>>(nullptr, 0, nullptr, 0, 0, b, nullptr, jobs);
     count_launch();
     for (int dblk = 1; dblk < Nb; ++dblk) {
-        trisqrt_off_kernel<R><<<dim3(Nb - dblk, batch), SylCfg<R>::THREADS, sm3, s>>>(nullptr, 0, nullptr, 0, 0, b, dblk,
-                                                                                      nullptr, jobs);
+        trisqrt_off_kernel<R, 1><<<dim3(Nb - dblk, batch), kTriThreads, sm3, s>>>(nullptr, 0, nullptr, 0, 0, b, dblk,
+                                                                                nullptr, jobs);
         count_launch();
     }
     return cudaGetLastError();
@@ -705,15 +708,15 @@ cudaError_t launch_rtrsyl_batched(const TriJob<R> *jobs, int batch, int nmax, in
     if (nmax <= 0 || batch <= 0) return cudaSuccess;
     const int b = blks < 1 ? 1 : (blks > TB ? TB : blks);
     const int Nb = (nmax + b - 1) / b;
-    const size_t sm3 = (1 + 4 * SylCfg<R>::G) * TB * TLD * sizeof(cplx<R>);
+    const size_t sm3 = 5 * TB * TLD * sizeof(cplx<R>);  // one group of 128 threads per block
     cudaError_t err;
-    if ((err = set_smem<R>((const void *)rtrsyl_wave_kernel<R>, sm3))) return err;
+    if ((err = set_smem<R>((const void *)rtrsyl_wave_kernel<R, 1>, sm3))) return err;
     // wavefront w of every matrix at once (a matrix with fewer blocks is done
     // after its own 2 Nb_i - 1 wavefronts; its blocks of later ones return)
     for (int w = 0; w <= 2 * Nb - 2; ++w) {
         const int cnt = min(w, 2 * Nb - 2 - w) + 1;
-        rtrsyl_wave_kernel<R><<<dim3(cnt, batch), SylCfg<R>::THREADS, sm3, s>>>(nullptr, 0, 0, nullptr, 0, 0, nullptr, 0, b,
-                                                                                 w, nullptr, jobs);
+        rtrsyl_wave_kernel<R, 1><<<dim3(cnt, batch), kTriThreads, sm3, s>>>(nullptr, 0, 0, nullptr, 0, 0, nullptr, 0, b,
+                                                                             w, nullptr, jobs);
         count_launch();
     }
     return cudaGetLastError();
