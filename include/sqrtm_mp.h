@@ -70,7 +70,7 @@ enum { SQRTM_KIND_AUTO = 0, SQRTM_KIND_GENERAL = 1, SQRTM_KIND_SPD = 2 };
  * n 2^(rho_i + rho_j - 56), 2^rho_i bounding row i of X, i.e. within the
  * FP64 product's own error bound); RESID_FP64 forces the FP64 product on
  * the CUDA cores. */
-enum { SQRTM_PREC_FP32 = 0, SQRTM_PREC_TF32X3 = 1, SQRTM_PREC_RESID_FP64 = 2 };
+enum { SQRTM_PREC_AUTO = -1, SQRTM_PREC_FP32 = 0, SQRTM_PREC_TF32X3 = 1, SQRTM_PREC_RESID_FP64 = 2 };
 
 typedef struct {
     double tol;      /* stop when ||A - X^2||_F <= tol ||A||_F (Algorithm 2,
@@ -78,9 +78,11 @@ typedef struct {
     int maxit;       /* refinement loop runs k = 0..maxit (Algorithm 2, step
                         4); default 10 */
     int blks;        /* block size of the Sylvester and triangular square
-                        root solvers (Algorithm 1); default 32 (Sec. 5) */
+                        root solvers (Algorithm 1), 1..32; 0 (default): the
+                        handle's tuning table, else 32 (Sec. 5) */
     int kind;        /* SQRTM_KIND_* */
-    int precision;   /* SQRTM_PREC_* flags */
+    int precision;   /* SQRTM_PREC_* flags; SQRTM_PREC_AUTO (default): the
+                        handle's tuning table, else SQRTM_PREC_FP32 */
     int steps;       /* >= 0: apply exactly this many corrections with the
                         stopping test nullified (the accuracy-run protocol of
                         Sec. 5.1); -1 (default): use tol / maxit */
@@ -114,6 +116,31 @@ typedef struct {
     int64_t schur_work;
 } sqrtm_info;
 
+/* Tuning table of a handle, written by the project's autotuner
+ * (paper_2607_12430_gb300.autotune) from timings on the GPU at hand.  Entry
+ * i applies to sizes n <= n_max (entries in ascending n_max; larger n use
+ * the last entry).  Fields:
+ *   blks          block size of the triangular square root and Sylvester
+ *                 solvers, 1..32 (used when opts->blks == 0);
+ *   qr_helpers    helper CTAs of the cooperative QR chase: 0 (chase CTA
+ *                 alone), 1..24, or -1 (built-in rule: 8, 16 from n = 1024);
+ *   batched       sqrtm_mixed_batched: 1 sends matrices of these sizes
+ *                 through the batched general path, 0 through per-matrix
+ *                 calls on worker streams;
+ *   spd_precision SQRTM_PREC_* flags of Algorithm 3 (used when
+ *                 opts->precision == SQRTM_PREC_AUTO).
+ * Without a table the built-in values apply: blks 32, helpers -1, batched
+ * for n <= 256, SQRTM_PREC_FP32. */
+typedef struct {
+    int64_t n_max;
+    int blks;
+    int qr_helpers;
+    int batched;
+    int spd_precision;
+} sqrtm_tune_entry;
+
+#define SQRTM_MAX_TUNE 32
+
 /* Create a handle bound to a CUDA stream (cudaStream_t passed as void*;
  * NULL = legacy default stream).  Returns 0 or 7. */
 SQRTM_API int sqrtm_create(sqrtm_handle_t *handle, void *stream);
@@ -126,6 +153,14 @@ SQRTM_API int sqrtm_set_stream(sqrtm_handle_t handle, void *stream);
 
 /* Fill opts with the defaults listed above. */
 SQRTM_API void sqrtm_default_opts(sqrtm_opts *opts);
+
+/* Install (count <= SQRTM_MAX_TUNE entries, validated and copied; count 0
+ * clears) or read (returns the number of entries, copying at most cap) the
+ * handle's tuning table.  set returns 0, -2 (table NULL with count > 0),
+ * -3 (count out of range) or -4 (an entry out of range or n_max not
+ * ascending). */
+SQRTM_API int sqrtm_set_tuning(sqrtm_handle_t handle, const sqrtm_tune_entry *table, int count);
+SQRTM_API int sqrtm_get_tuning(sqrtm_handle_t handle, sqrtm_tune_entry *table, int cap);
 
 /* Mixed-precision principal square root, Algorithm 2 (general A) or
  * Algorithm 3 (symmetric positive definite A):

@@ -30,8 +30,9 @@ STATUS = {
 }
 
 KIND_AUTO, KIND_GENERAL, KIND_SPD = 0, 1, 2
-PREC_FP32, PREC_TF32X3, PREC_RESID_FP64 = 0, 1, 2
+PREC_AUTO, PREC_FP32, PREC_TF32X3, PREC_RESID_FP64 = -1, 0, 1, 2
 MAX_HISTORY = 64
+MAX_TUNE = 32
 
 
 class SqrtmError(RuntimeError):
@@ -49,6 +50,11 @@ class SqrtmError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("blks", ctypes.c_int),
                 ("kind", ctypes.c_int), ("precision", ctypes.c_int), ("steps", ctypes.c_int)]
+
+
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("n_max", ctypes.c_int64), ("blks", ctypes.c_int), ("qr_helpers", ctypes.c_int),
+                ("batched", ctypes.c_int), ("spd_precision", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -82,6 +88,8 @@ _SIGS = {
     "sqrtm_destroy": ([_P], _I),
     "sqrtm_set_stream": ([_P, _P], _I),
     "sqrtm_default_opts": ([ctypes.POINTER(Opts)], None),
+    "sqrtm_set_tuning": ([_P, ctypes.POINTER(TuneEntry), _I], _I),
+    "sqrtm_get_tuning": ([_P, ctypes.POINTER(TuneEntry), _I], _I),
     "sqrtm_mixed": ([_P, _P, _L, _L, _D, _P, _L, ctypes.POINTER(Opts), ctypes.POINTER(Info)], _I),
     "sqrtm_schur_fp64": ([_P, _P, _L, _L, _D, _P, _L, ctypes.POINTER(Opts), ctypes.POINTER(Info)], _I),
     "sqrtm_cbrtm_mixed": ([_P, _P, _L, _L, _D, _P, _L, ctypes.POINTER(Opts), ctypes.POINTER(Info)], _I),
@@ -163,7 +171,37 @@ def handle():
             raise SqrtmError(rc, "sqrtm_create")
         h = hp
         _handles[key] = h
+        _install_shipped_tuning(h)
     return h
+
+
+TUNING_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning")
+
+
+def _install_shipped_tuning(h):
+    """A new handle takes the tuning table the autotuner stored for this
+    device model under tuning/ (if any); SQRTM_NO_TUNING=1 skips it."""
+    if os.environ.get("SQRTM_NO_TUNING") == "1" or not os.path.isdir(TUNING_DIR):
+        return
+    import json
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    key = f"{p.name} sm_{p.major}{p.minor} x{p.multi_processor_count}"
+    for f in sorted(os.listdir(TUNING_DIR)):
+        if not f.endswith(".json"):
+            continue
+        with open(os.path.join(TUNING_DIR, f)) as fh:
+            res = json.load(fh)
+        if res.get("device") != key:
+            continue
+        t = res["table"]
+        arr = (TuneEntry * max(1, len(t)))()
+        for i, e in enumerate(t):
+            arr[i] = TuneEntry(int(e["n_max"]), int(e["blks"]), int(e["qr_helpers"]), int(e["batched"]),
+                               int(e["spd_precision"]))
+        rc = lib().sqrtm_set_tuning(h, arr, len(t))
+        if rc:
+            raise SqrtmError(rc, "sqrtm_set_tuning (" + f + ")")
+        return
 
 
 def _check_square(A, name="A"):
@@ -193,7 +231,28 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else ctypes.c_void_p(0)
 
 
-def make_opts(tol=1e-12, maxit=10, blks=32, kind=KIND_AUTO, precision=PREC_FP32, steps=-1):
+def set_tuning(entries):
+    """Install a tuning table (list of dicts with n_max, blks, qr_helpers,
+    batched, spd_precision; ascending n_max) on this stream's handle; an
+    empty list clears it."""
+    arr = (TuneEntry * max(1, len(entries)))()
+    for i, e in enumerate(entries):
+        arr[i] = TuneEntry(int(e["n_max"]), int(e["blks"]), int(e["qr_helpers"]), int(e["batched"]),
+                           int(e["spd_precision"]))
+    rc = lib().sqrtm_set_tuning(handle(), arr, len(entries))
+    if rc:
+        raise SqrtmError(rc, "sqrtm_set_tuning")
+
+
+def get_tuning():
+    """The tuning table of this stream's handle (list of dicts)."""
+    arr = (TuneEntry * MAX_TUNE)()
+    cnt = lib().sqrtm_get_tuning(handle(), arr, MAX_TUNE)
+    return [{"n_max": arr[i].n_max, "blks": arr[i].blks, "qr_helpers": arr[i].qr_helpers,
+             "batched": arr[i].batched, "spd_precision": arr[i].spd_precision} for i in range(cnt)]
+
+
+def make_opts(tol=1e-12, maxit=10, blks=0, kind=KIND_AUTO, precision=PREC_AUTO, steps=-1):
     o = Opts()
     lib().sqrtm_default_opts(ctypes.byref(o))
     o.tol, o.maxit, o.blks, o.kind, o.precision, o.steps = tol, maxit, blks, kind, precision, steps

@@ -154,10 +154,49 @@ extern "C" void sqrtm_default_opts(sqrtm_opts *o)
     if (!o) return;
     o->tol = 1e-12;
     o->maxit = 10;
-    o->blks = 32;
+    o->blks = 0;
     o->kind = SQRTM_KIND_AUTO;
-    o->precision = SQRTM_PREC_FP32;
+    o->precision = SQRTM_PREC_AUTO;
     o->steps = -1;
+}
+
+extern "C" int sqrtm_set_tuning(sqrtm_handle_t h, const sqrtm_tune_entry *table, int count)
+{
+    if (!h) return -1;
+    if (count < 0 || count > SQRTM_MAX_TUNE) return -3;
+    if (count > 0 && !table) return -2;
+    for (int i = 0; i < count; ++i) {
+        const sqrtm_tune_entry &t = table[i];
+        if (t.n_max < 1 || (i > 0 && t.n_max <= table[i - 1].n_max)) return -4;
+        if (t.blks < 1 || t.blks > 32 || t.qr_helpers < -1 || t.qr_helpers > 24) return -4;
+        if ((t.batched != 0 && t.batched != 1) || t.spd_precision < 0 || t.spd_precision > 3) return -4;
+    }
+    h->tuning.assign(table, table + count);
+    for (auto *w : h->workers) w->tuning = h->tuning;
+    return 0;
+}
+
+extern "C" int sqrtm_get_tuning(sqrtm_handle_t h, sqrtm_tune_entry *table, int cap)
+{
+    if (!h) return -1;
+    const int cnt = (int)h->tuning.size();
+    for (int i = 0; i < cnt && i < cap && table; ++i) table[i] = h->tuning[i];
+    return cnt;
+}
+
+const sqrtm_tune_entry *tune_for(sqrtm_handle_t h, int64_t n)
+{
+    if (!h || h->tuning.empty()) return nullptr;
+    for (const auto &t : h->tuning)
+        if (n <= t.n_max) return &t;
+    return &h->tuning.back();
+}
+
+void apply_tuning(sqrtm_handle_t h, int64_t n, sqrtm_opts *o)
+{
+    const sqrtm_tune_entry *t = tune_for(h, n);
+    if (o->blks == 0) o->blks = t ? t->blks : 32;
+    if (o->precision == SQRTM_PREC_AUTO) o->precision = t ? t->spd_precision : SQRTM_PREC_FP32;
 }
 
 extern "C" const char *sqrtm_status_string(int code)
@@ -350,8 +389,9 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     SQM_CU(cudaEventCreate(&ev_red));
     SQM_CU(cudaEventRecord(ev_red, s));
     float ms_chase = 0.0f;
+    const sqrtm_tune_entry *tune = tune_for(h, n);
     SQM_CU(launch_qr_sweeps<R>(ddesc, 1, (int)n, (int *)h->staging.p + 512, qstate, s, &ms_chase, ddesc + 1, h->side,
-                               h->qev, qsync));
+                               h->qev, qsync, tune ? tune->qr_helpers : -1));
     SQM_CU(cudaEventRecord(h->ev[1], s));
     if (root == 3) SQM_CU(launch_tricbrt<R>(T, (int)n, S, (int)n, V, (int)n, (int)n, o.blks, sc.st_solve, s));
     else SQM_CU(launch_trisqrt<R>(T, (int)n, S, (int)n, (int)n, o.blks, sc.st_solve, s));
@@ -445,7 +485,8 @@ static int resolve_opts(const sqrtm_opts *opts, double tol, sqrtm_opts *o)
     sqrtm_default_opts(o);
     if (opts) *o = *opts;
     else o->tol = tol;
-    if (o->blks < 1) return -8;
+    if (o->blks < 0 || o->blks > 4096) return -8;
+    if (o->precision < SQRTM_PREC_AUTO) return -8;
     if (o->maxit < 0 || o->maxit > SQRTM_MAX_HISTORY - 2) return -8;
     return 0;
 }
@@ -460,6 +501,7 @@ extern "C" int sqrtm_mixed(sqrtm_handle_t h, const double *dA, int64_t n, int64_
     sqrtm_opts o;
     if (int rc = resolve_opts(opts, tol, &o)) return rc;
     if (n == 0) return 0;
+    apply_tuning(h, n, &o);
     int kind = o.kind;
     if (kind == SQRTM_KIND_AUTO) {
         int rc = 0;
@@ -486,6 +528,7 @@ extern "C" int sqrtm_schur_fp64(sqrtm_handle_t h, const double *dA, int64_t n, i
     sqrtm_opts o;
     if (int rc = resolve_opts(opts, tol, &o)) return rc;
     if (n == 0) return 0;
+    apply_tuning(h, n, &o);
     int kind = o.kind;
     if (kind == SQRTM_KIND_AUTO) {
         int rc = 0;
@@ -511,6 +554,7 @@ extern "C" int sqrtm_cbrtm_mixed(sqrtm_handle_t h, const double *dA, int64_t n, 
     sqrtm_opts o;
     if (int rc = resolve_opts(opts, tol, &o)) return rc;
     if (n == 0) return 0;
+    apply_tuning(h, n, &o);
     int rc = general_path<float>(h, dA, n, lda, o.tol, dX, ldx, o, info, true, 3);
     if (info) info->status = rc;
     return rc;
@@ -525,6 +569,7 @@ extern "C" int sqrtm_cbrtm_schur_fp64(sqrtm_handle_t h, const double *dA, int64_
     sqrtm_opts o;
     if (int rc = resolve_opts(opts, tol, &o)) return rc;
     if (n == 0) return 0;
+    apply_tuning(h, n, &o);
     int rc = general_path<double>(h, dA, n, lda, 0.0, dX, ldx, o, info, false, 3);
     h->fact_n = -1;
     if (info) info->status = rc;
@@ -575,6 +620,7 @@ static int ensure_workers(sqrtm_handle_t h, int count)
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return 7;
         sqrtm_handle_t w = nullptr;
         if (int rc = sqrtm_create(&w, (void *)st)) { cudaStreamDestroy(st); return rc; }
+        w->tuning = h->tuning;
         h->workers.push_back(w);
         h->worker_streams.push_back(st);
     }
@@ -599,14 +645,21 @@ extern "C" int sqrtm_mixed_batched(sqrtm_handle_t h, int batch, const double *co
     // path (one set of launches for all of them); larger ones, and every
     // matrix when the SPD algorithm is forced, through per-matrix calls on
     // worker threads with their own handles and streams, largest first
-    int nbmax = 256;
-    if (const char *env = getenv("SQRTM_BATCH_MAXN")) nbmax = atoi(env);
+    // which sizes take the batched path: SQRTM_BATCH_MAXN (a size limit) if
+    // set, else the tuning table, else n <= 256
+    const char *env = getenv("SQRTM_BATCH_MAXN");
+    const int nbmax = env ? atoi(env) : 256;
     std::vector<int> small, large;
+    int64_t nsmall = 0;
     for (int i = 0; i < batch; ++i) {
         if (n[i] == 0) continue;
-        if (o.kind != SQRTM_KIND_SPD && n[i] <= nbmax) small.push_back(i);
+        const sqrtm_tune_entry *t = env ? nullptr : tune_for(h, n[i]);
+        const bool b = t ? t->batched == 1 : n[i] <= nbmax;
+        if (o.kind != SQRTM_KIND_SPD && b) { small.push_back(i); nsmall = std::max(nsmall, n[i]); }
         else large.push_back(i);
     }
+    sqrtm_opts ob = o;  // the batched path's block size: that of its largest matrix
+    apply_tuning(h, std::max<int64_t>(nsmall, 1), &ob);
     const int nw = std::min<int>((int)large.size(), 12);
     if (nw > 0) {
         if (int rc = ensure_workers(h, nw)) return rc;
@@ -631,7 +684,7 @@ extern "C" int sqrtm_mixed_batched(sqrtm_handle_t h, int batch, const double *co
     };
     std::vector<std::thread> threads;
     for (int w = 0; w < nw; ++w) threads.emplace_back(work, w);
-    int rc_small = batched_general(h, small.data(), (int)small.size(), dA, n, lda, dX, ldx, o, st.data());
+    int rc_small = batched_general(h, small.data(), (int)small.size(), dA, n, lda, dX, ldx, ob, st.data());
     for (auto &t : threads) t.join();
     // fence: the caller's stream waits for every worker
     for (int w = 0; w < nw; ++w) {

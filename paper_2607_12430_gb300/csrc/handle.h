@@ -48,6 +48,8 @@ struct sqrtm_handle_s {
     };
     std::vector<Graph> graphs;
     cudaStream_t cap_stream = nullptr;
+    // tuning table (sqrtm_set_tuning), ascending n_max
+    std::vector<sqrtm_tune_entry> tuning;
     // batched general path: device arena and pinned host buffer
     Buf bws;
     void *bpin = nullptr;
@@ -99,6 +101,12 @@ void note_error(sqrtm_handle_t h, const char *what, int line, int code);
         }                                                     \
     } while (0)
 
+
+// The tuning entry for size n (nullptr without a table), and the automatic
+// fields of opts resolved for size n: blks 0 -> tuned or 32, precision
+// SQRTM_PREC_AUTO -> tuned or SQRTM_PREC_FP32.
+const sqrtm_tune_entry *tune_for(sqrtm_handle_t h, int64_t n);
+void apply_tuning(sqrtm_handle_t h, int64_t n, sqrtm_opts *o);
 
 // The batched general path (batch.cu) for the matrices idx[0 .. count) of a
 // batched call (n <= 46340 each); statuses into st_out[idx[i]].  Returns 0 or 7.

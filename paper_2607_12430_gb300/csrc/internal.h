@@ -164,13 +164,14 @@ cudaError_t launch_hessenberg_cluster_batched(const HessJob<R> *jobs, int count,
 // chase never reads.  d_sync (may be null; >= 32 ints, the descriptors'
 // `sync`): with batch == 1 and a large enough n the chase runs as one
 // cooperative grid of a chase CTA and helper CTAs that take the
-// out-of-window updates of the active block.
+// out-of-window updates of the active block.  helpers: number of helper
+// CTAs (0: no cooperative grid; -1: 8, 16 from n = 1024).
 constexpr int kQrStateInts = 16;
 template <class R>
 cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, int *h_state,
                              const int *d_state_all, cudaStream_t s, float *ms_chase = nullptr,
                              const SchurDesc<R> *d_desc_alt = nullptr, cudaStream_t side = nullptr,
-                             const cudaEvent_t *qev = nullptr, int *d_sync = nullptr);
+                             const cudaEvent_t *qev = nullptr, int *d_sync = nullptr, int helpers = -1);
 // scratch sizes per matrix of size n: rotation log entries, window records,
 // elements of accumulated window products (one round of the QR iteration
 // stops at a sweep boundary before any of them would overflow)

@@ -1317,7 +1317,7 @@ template <class R>
 cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, int *h_state,
                              const int *d_state_all, cudaStream_t s, float *ms_chase,
                              const SchurDesc<R> *d_desc_alt, cudaStream_t side, const cudaEvent_t *qev,
-                             int *d_sync)
+                             int *d_sync, int helpers)
 {
     constexpr int RRMAX = QrDims<R>::RR;
     const int rpc = qr_rows_per_cta<R>(nmax, batch);
@@ -1329,8 +1329,8 @@ cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, in
     if ((err = allow_max_smem((const void *)qr_chase_kernel<R, false>))) return err;
     if ((err = allow_max_smem((const void *)qr_chase_kernel<R, true>))) return err;
     // cooperative chase (one chase CTA + H helper CTAs) for one large matrix
-    const bool coop = d_sync != nullptr && batch == 1 && nmax >= kQrCoopMinN;
-    int H = nmax >= 1024 ? 16 : 8;
+    const bool coop = d_sync != nullptr && batch == 1 && nmax >= kQrCoopMinN && helpers != 0;
+    int H = helpers > 0 ? std::min(helpers, 24) : nmax >= 1024 ? 16 : 8;  // d_sync holds 4 + H counters
     if ((err = allow_max_smem((const void *)qr_build_u_kernel<R>))) return err;
     if ((err = allow_max_smem((const void *)qr_apply_rows_kernel<R>))) return err;
     if ((err = allow_max_smem((const void *)qr_apply_cols_kernel<R>))) return err;
@@ -1404,8 +1404,8 @@ cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, in
 }
 
 template cudaError_t launch_qr_sweeps<float>(const SchurDesc<float> *, int, int, int *, const int *, cudaStream_t, float *,
-                                             const SchurDesc<float> *, cudaStream_t, const cudaEvent_t *, int *);
+                                             const SchurDesc<float> *, cudaStream_t, const cudaEvent_t *, int *, int);
 template cudaError_t launch_qr_sweeps<double>(const SchurDesc<double> *, int, int, int *, const int *, cudaStream_t, float *,
-                                              const SchurDesc<double> *, cudaStream_t, const cudaEvent_t *, int *);
+                                              const SchurDesc<double> *, cudaStream_t, const cudaEvent_t *, int *, int);
 
 }  // namespace sqm
