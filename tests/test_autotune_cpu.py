@@ -17,6 +17,9 @@ def test_pick_precision_respects_accuracy_gate():
     assert at.pick_precision(times, {0: 1e-15, 1: 1e-14}) == 1
     assert at.pick_precision(times, {0: 1e-15, 1: 1e-12}) == 0
     assert at.pick_precision(times, {0: math.inf, 1: math.inf}) == 0
+    # neither reaches the target: the faster plan if no worse than 1.5x FP32's
+    assert at.pick_precision(times, {0: 7.4e-13, 1: 7.3e-13}) == 1
+    assert at.pick_precision(times, {0: 7.4e-13, 1: 2e-12}) == 0
 
 
 def test_build_table_orders_buckets_and_fills_builtins():
