@@ -128,15 +128,21 @@ typedef struct {
  *                 through the batched general path, 0 through per-matrix
  *                 calls on worker streams;
  *   spd_precision SQRTM_PREC_* flags of Algorithm 3 (used when
- *                 opts->precision == SQRTM_PREC_AUTO).
+ *                 opts->precision == SQRTM_PREC_AUTO);
+ *   trisqrt_cutoff 0: the blocked triangular square root (Sec. 2.2.1);
+ *                 >= 64: the recursive splitting of Sec. 2.2.1 (S_11, S_22
+ *                 recursively, S_12 from a Sylvester solve) down to blocks
+ *                 of at most this size, which take the blocked method.
  * Without a table the built-in values apply: blks 32, helpers -1, batched
- * for n <= 256, SQRTM_PREC_FP32. */
+ * for n <= 256, SQRTM_PREC_FP32, cutoff 0. */
 typedef struct {
     int64_t n_max;
     int blks;
     int qr_helpers;
     int batched;
     int spd_precision;
+    int trisqrt_cutoff;
+    int reserved;  /* 0 */
 } sqrtm_tune_entry;
 
 #define SQRTM_MAX_TUNE 32

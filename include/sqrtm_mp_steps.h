@@ -60,6 +60,15 @@ SQRTM_API int sqrtm_step_trisqrt(sqrtm_handle_t h, const void *dT, void *dS, int
 SQRTM_API int sqrtm_step_tricbrt(sqrtm_handle_t h, const void *dT, void *dS, void *dV, int64_t n, int blks,
                                  int fp64);
 
+/* The same triangular square root by the recursive splitting of Sec. 2.2.1
+ * (the Deadman-Higham-Ralha recursion): T split at m (n/2 rounded up to a
+ * multiple of 32), S_11 and S_22 recursively, S_12 from S_11 S_12 + S_12
+ * S_22 = T_12 by the blocked Sylvester solver; blocks of at most cutoff
+ * (>= 64; smaller values are raised to 64) take the blocked method.
+ * Returns 0 or 2. */
+SQRTM_API int sqrtm_step_trisqrt_rec(sqrtm_handle_t h, const void *dT, void *dS, int64_t n, int blks, int cutoff,
+                                     int fp64);
+
 /* X_0 = Re(Q S Q^H) (Algorithm 2, step 3), computed in the storage
  * precision of Q and S, rounded to that precision and written widened to
  * FP64 into dX (ldx), times 2^e (undoing the scaling). */

@@ -54,7 +54,8 @@ class Opts(ctypes.Structure):
 
 class TuneEntry(ctypes.Structure):
     _fields_ = [("n_max", ctypes.c_int64), ("blks", ctypes.c_int), ("qr_helpers", ctypes.c_int),
-                ("batched", ctypes.c_int), ("spd_precision", ctypes.c_int)]
+                ("batched", ctypes.c_int), ("spd_precision", ctypes.c_int), ("trisqrt_cutoff", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -103,6 +104,7 @@ _SIGS = {
     "sqrtm_step_schur": ([_P, _P, _P, _L, _I], _I),
     "sqrtm_step_syevd": ([_P, _P, _P, _P, _L, _I], _I),
     "sqrtm_step_trisqrt": ([_P, _P, _P, _L, _I, _I], _I),
+    "sqrtm_step_trisqrt_rec": ([_P, _P, _P, _L, _I, _I, _I], _I),
     "sqrtm_step_tricbrt": ([_P, _P, _P, _P, _L, _I, _I], _I),
     "sqrtm_step_rtrsyl3": ([_P, _P, _P, _P, _L, _I, _I], _I),
     "sqrtm_step_form_x0": ([_P, _P, _P, _L, _I, _P, _L, _I], _I),
@@ -194,11 +196,7 @@ def _install_shipped_tuning(h):
         if res.get("device") != key:
             continue
         t = res["table"]
-        arr = (TuneEntry * max(1, len(t)))()
-        for i, e in enumerate(t):
-            arr[i] = TuneEntry(int(e["n_max"]), int(e["blks"]), int(e["qr_helpers"]), int(e["batched"]),
-                               int(e["spd_precision"]))
-        rc = lib().sqrtm_set_tuning(h, arr, len(t))
+        rc = lib().sqrtm_set_tuning(h, _tune_array(t), len(t))
         if rc:
             raise SqrtmError(rc, "sqrtm_set_tuning (" + f + ")")
         return
@@ -233,13 +231,9 @@ def _ptr(t):
 
 def set_tuning(entries):
     """Install a tuning table (list of dicts with n_max, blks, qr_helpers,
-    batched, spd_precision; ascending n_max) on this stream's handle; an
-    empty list clears it."""
-    arr = (TuneEntry * max(1, len(entries)))()
-    for i, e in enumerate(entries):
-        arr[i] = TuneEntry(int(e["n_max"]), int(e["blks"]), int(e["qr_helpers"]), int(e["batched"]),
-                           int(e["spd_precision"]))
-    rc = lib().sqrtm_set_tuning(handle(), arr, len(entries))
+    batched, spd_precision and optionally trisqrt_cutoff; ascending n_max)
+    on this stream's handle; an empty list clears it."""
+    rc = lib().sqrtm_set_tuning(handle(), _tune_array(entries), len(entries))
     if rc:
         raise SqrtmError(rc, "sqrtm_set_tuning")
 
@@ -249,7 +243,16 @@ def get_tuning():
     arr = (TuneEntry * MAX_TUNE)()
     cnt = lib().sqrtm_get_tuning(handle(), arr, MAX_TUNE)
     return [{"n_max": arr[i].n_max, "blks": arr[i].blks, "qr_helpers": arr[i].qr_helpers,
-             "batched": arr[i].batched, "spd_precision": arr[i].spd_precision} for i in range(cnt)]
+             "batched": arr[i].batched, "spd_precision": arr[i].spd_precision,
+             "trisqrt_cutoff": arr[i].trisqrt_cutoff} for i in range(cnt)]
+
+
+def _tune_array(entries):
+    arr = (TuneEntry * max(1, len(entries)))()
+    for i, e in enumerate(entries):
+        arr[i] = TuneEntry(int(e["n_max"]), int(e["blks"]), int(e["qr_helpers"]), int(e["batched"]),
+                           int(e["spd_precision"]), int(e.get("trisqrt_cutoff", 0)), 0)
+    return arr
 
 
 def make_opts(tol=1e-12, maxit=10, blks=0, kind=KIND_AUTO, precision=PREC_AUTO, steps=-1):
@@ -431,6 +434,12 @@ def step_syevd(As_cm, n, fp64=False):
 def step_trisqrt(T_cm, n, blks=32, fp64=False):
     S = torch.empty_like(T_cm)
     _rc(lib().sqrtm_step_trisqrt(handle(), _ptr(T_cm), _ptr(S), n, blks, int(fp64)), "trisqrt")
+    return S
+
+
+def step_trisqrt_rec(T_cm, n, blks=32, cutoff=256, fp64=False):
+    S = torch.empty_like(T_cm)
+    _rc(lib().sqrtm_step_trisqrt_rec(handle(), _ptr(T_cm), _ptr(S), n, blks, cutoff, int(fp64)), "trisqrt_rec")
     return S
 
 

@@ -16,6 +16,8 @@ the SPD path):
   one among those whose forward error against the FP64 method on the same
   GPU, after SPD_STEPS corrections (the stopping test nullified, as in the
   accuracy runs of Sec. 5.1), stays within the SPD accuracy target (1e-13);
+* trisqrt_cutoff -- the blocked triangular square root (0) or the
+  recursive splitting of Sec. 2.2.1 down to blocks of 256 or 512 (n >= 512);
 * batched -- for sqrtm_mixed_batched, whether matrices of the bucket's size
   go through the batched general path or per-matrix calls (a batch of
   `batch_count` matrices timed both ways).
@@ -31,6 +33,7 @@ import numpy as np
 
 BLKS_CANDIDATES = (8, 16, 32)
 HELPER_CANDIDATES = (0, 8, 16)
+CUTOFF_CANDIDATES = (0, 256, 512)
 SPD_TARGET = 1e-13
 SPD_STEPS = 4  # corrections of the SPD accuracy runs (the protocol of Sec. 5.1: the test nullified)
 DEFAULT_SIZES = (64, 128, 256, 512, 1024, 2048)
@@ -70,6 +73,7 @@ def build_table(measured):
         e["blks"] = int(pick_fastest(m["blks"])) if m.get("blks") else BUILTIN["blks"]
         e["qr_helpers"] = int(pick_fastest(m["helpers"])) if m.get("helpers") else BUILTIN["qr_helpers"]
         e["spd_precision"] = int(pick_precision(m["spd"], m["spd_err"])) if m.get("spd") else BUILTIN["spd_precision"]
+        e["trisqrt_cutoff"] = int(pick_fastest(m["cutoff"])) if m.get("cutoff") else 0
         if "batched" in m and "per_matrix" in m:
             e["batched"] = int(m["batched"] <= m["per_matrix"])
         else:
@@ -115,7 +119,7 @@ def measure_bucket(n, reps=3, batch_count=32, seed=20260712, log=None):
     import torch
     import paper_2607_12430_gb300 as mp
     A = torch.from_numpy(_general(n, seed + n)).cuda()
-    m = {"n": n, "blks": {}, "helpers": {}, "spd": {}, "spd_err": {}}
+    m = {"n": n, "blks": {}, "helpers": {}, "cutoff": {}, "spd": {}, "spd_err": {}}
     saved = mp.get_tuning()
     try:
         mp.set_tuning([])
@@ -127,6 +131,12 @@ def measure_bucket(n, reps=3, batch_count=32, seed=20260712, log=None):
                                 "spd_precision": 0}])
                 m["helpers"][hcount] = _timer(lambda: mp.sqrtm_mixed(A, kind=mp.KIND_GENERAL, steps=2, blks=32),
                                               reps)
+            for c in CUTOFF_CANDIDATES:
+                if c and c >= n:
+                    continue
+                mp.set_tuning([{"n_max": 1 << 40, "blks": 32, "qr_helpers": -1, "batched": 1, "spd_precision": 0,
+                                "trisqrt_cutoff": c}])
+                m["cutoff"][c] = _timer(lambda: mp.sqrtm_mixed(A, kind=mp.KIND_GENERAL, steps=2, blks=32), reps)
             mp.set_tuning([])
         S = torch.from_numpy(_spd(n, seed + 7 * n)).cuda()
         X64, _ = mp.sqrtm_schur_fp64(S, kind=mp.KIND_SPD)

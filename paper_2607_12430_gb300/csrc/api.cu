@@ -170,6 +170,7 @@ extern "C" int sqrtm_set_tuning(sqrtm_handle_t h, const sqrtm_tune_entry *table,
         if (t.n_max < 1 || (i > 0 && t.n_max <= table[i - 1].n_max)) return -4;
         if (t.blks < 1 || t.blks > 32 || t.qr_helpers < -1 || t.qr_helpers > 24) return -4;
         if ((t.batched != 0 && t.batched != 1) || t.spd_precision < 0 || t.spd_precision > 3) return -4;
+        if (t.trisqrt_cutoff < 0 || t.reserved != 0) return -4;
     }
     h->tuning.assign(table, table + count);
     for (auto *w : h->workers) w->tuning = h->tuning;
@@ -394,6 +395,8 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
                                h->qev, qsync, tune ? tune->qr_helpers : -1));
     SQM_CU(cudaEventRecord(h->ev[1], s));
     if (root == 3) SQM_CU(launch_tricbrt<R>(T, (int)n, S, (int)n, V, (int)n, (int)n, o.blks, sc.st_solve, s));
+    else if (tune && tune->trisqrt_cutoff > 0 && n > tune->trisqrt_cutoff)
+        SQM_CU(launch_trisqrt_rec<R>(T, (int)n, S, (int)n, (int)n, o.blks, tune->trisqrt_cutoff, sc.st_solve, s));
     else SQM_CU(launch_trisqrt<R>(T, (int)n, S, (int)n, (int)n, o.blks, sc.st_solve, s));
     // X_0 = Re(Q S Q^H), rounded to R, times 2^e
     SQM_CU(launch_cgemm<R>(OP_N, OP_N, (int)n, (int)n, (int)n, Q, (int)n, false, S, (int)n, EPI_STORE, W, (int)n, nullptr, 0, 0.0, s));

@@ -185,6 +185,11 @@ inline int64_t qr_u_capacity(int64_t n) { return std::max<int64_t>(24 * n * n, 6
 template <class R>
 cudaError_t launch_trisqrt(const cplx<R> *T, int ldt, cplx<R> *S, int lds, int n, int blks,
                            int *d_status, cudaStream_t s);
+// The same by the recursive (Deadman-Higham-Ralha) splitting, with blocks of
+// at most cutoff (>= 64) done by launch_trisqrt.
+template <class R>
+cudaError_t launch_trisqrt_rec(const cplx<R> *T, int ldt, cplx<R> *S, int lds, int n, int blks, int cutoff,
+                               int *d_status, cudaStream_t s);
 // Principal cube root (Sec. 4, p = 3) of upper triangular T: S = T^(1/3) and
 // V = S^2 (both n x n, upper triangular); status 2 for an eigenvalue on or
 // near the closed negative real axis or a zero leaf denominator.

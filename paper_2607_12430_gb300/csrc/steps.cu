@@ -145,6 +145,25 @@ extern "C" int sqrtm_step_tricbrt(sqrtm_handle_t h, const void *dT, void *dS, vo
     return st;
 }
 
+extern "C" int sqrtm_step_trisqrt_rec(sqrtm_handle_t h, const void *dT, void *dS, int64_t n, int blks, int cutoff,
+                                      int fp64)
+{
+    if (!h) return -1;
+    if (n < 0) return -4;
+    if (blks < 1) return -5;
+    if (n == 0) return 0;
+    StepScratch ss; void *ex;
+    if (int rc = step_scratch(h, n, 0, &ss, &ex)) return rc;
+    cudaError_t err = fp64 ? launch_trisqrt_rec<double>((const cplx<double> *)dT, (int)n, (cplx<double> *)dS, (int)n,
+                                                        (int)n, blks, cutoff, ss.iscal + 1, h->stream)
+                           : launch_trisqrt_rec<float>((const cplx<float> *)dT, (int)n, (cplx<float> *)dS, (int)n,
+                                                       (int)n, blks, cutoff, ss.iscal + 1, h->stream);
+    if (err) return 7;
+    int st = 0;
+    if (fetch(h, &st, ss.iscal + 1, sizeof(int))) return 7;
+    return st;
+}
+
 template <class R>
 static int form_x0(sqrtm_handle_t h, const cplx<R> *Q, const cplx<R> *S, int64_t n, int e,
                    double *dX, int64_t ldx)

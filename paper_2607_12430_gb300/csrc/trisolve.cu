@@ -765,6 +765,40 @@ template cudaError_t launch_tricbrt<float>(const cplx<float> *, int, cplx<float>
                                            int *, cudaStream_t);
 template cudaError_t launch_tricbrt<double>(const cplx<double> *, int, cplx<double> *, int, cplx<double> *, int, int,
                                             int, int *, cudaStream_t);
+// Recursive (Deadman-Higham-Ralha) triangular square root: split T at m,
+// S_11 = T_11^{1/2} and S_22 = T_22^{1/2} recursively, then S_12 from the
+// Sylvester equation S_11 S_12 + S_12 S_22 = T_12 (Sec. 2.2.1), down to
+// blocks of at most `cutoff`, which take the blocked method.  The split is
+// rounded to a multiple of 32 so that the Sylvester solves keep whole tiles.
+template <class R>
+cudaError_t launch_trisqrt_rec(const cplx<R> *T, int ldt, cplx<R> *S, int lds, int n, int blks, int cutoff,
+                               int *d_status, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    if (cutoff < 64) cutoff = 64;
+    if (n <= cutoff) return launch_trisqrt<R>(T, ldt, S, lds, n, blks, d_status, s);
+    int m = ((n / 2 + 31) / 32) * 32;
+    if (m >= n) m = n / 2;
+    cudaError_t err;
+    if ((err = launch_trisqrt_rec<R>(T, ldt, S, lds, m, blks, cutoff, d_status, s))) return err;
+    if ((err = launch_trisqrt_rec<R>(T + m + (int64_t)m * ldt, ldt, S + m + (int64_t)m * lds, lds, n - m, blks, cutoff,
+                                     d_status, s)))
+        return err;
+    cplx<R> *S12 = S + (int64_t)m * lds;
+    if ((err = cudaMemcpy2DAsync(S12, (size_t)lds * sizeof(cplx<R>), T + (int64_t)m * ldt,
+                                 (size_t)ldt * sizeof(cplx<R>), (size_t)m * sizeof(cplx<R>), (size_t)(n - m),
+                                 cudaMemcpyDeviceToDevice, s)))
+        return err;
+    if ((err = cudaMemset2DAsync(S + m, (size_t)lds * sizeof(cplx<R>), 0, (size_t)(n - m) * sizeof(cplx<R>),
+                                 (size_t)m, s)))
+        return err;
+    return launch_rtrsyl<R>(S, lds, m, S + m + (int64_t)m * lds, lds, n - m, S12, lds, blks, d_status, s);
+}
+
+template cudaError_t launch_trisqrt_rec<float>(const cplx<float> *, int, cplx<float> *, int, int, int, int, int *,
+                                               cudaStream_t);
+template cudaError_t launch_trisqrt_rec<double>(const cplx<double> *, int, cplx<double> *, int, int, int, int, int *,
+                                                cudaStream_t);
 template cudaError_t launch_trisqrt_batched<float>(const TriJob<float> *, int, int, int, cudaStream_t);
 template cudaError_t launch_trisqrt_batched<double>(const TriJob<double> *, int, int, int, cudaStream_t);
 template cudaError_t launch_rtrsyl_batched<float>(const TriJob<float> *, int, int, int, cudaStream_t);

@@ -25,6 +25,7 @@ def test_pick_precision_respects_accuracy_gate():
 def test_build_table_orders_buckets_and_fills_builtins():
     measured = [
         {"n": 512, "blks": {8: 3.0, 16: 2.0, 32: 2.1}, "helpers": {0: 5.0, 8: 3.0, 16: 3.5},
+         "cutoff": {0: 2.0, 256: 1.5},
          "spd": {0: 1.0, 1: 0.8}, "spd_err": {0: 1e-15, 1: 2e-15}, "batched": 0.5, "per_matrix": 0.4},
         {"n": 64, "blks": {8: 1.0, 16: 1.0, 32: 1.0}, "helpers": {}, "spd": {}, "spd_err": {},
          "batched": 0.1, "per_matrix": 0.9},
@@ -32,9 +33,11 @@ def test_build_table_orders_buckets_and_fills_builtins():
     ]
     t = at.build_table(measured)
     assert [e["n_max"] for e in t] == [64, 512, 4096]
-    assert t[0] == {"n_max": 64, "blks": 8, "qr_helpers": -1, "spd_precision": 0, "batched": 1}
-    assert t[1] == {"n_max": 512, "blks": 16, "qr_helpers": 8, "spd_precision": 1, "batched": 0}
-    assert t[2] == {"n_max": 4096, "blks": 32, "qr_helpers": -1, "spd_precision": 0, "batched": 0}
+    assert t[0] == {"n_max": 64, "blks": 8, "qr_helpers": -1, "spd_precision": 0, "batched": 1, "trisqrt_cutoff": 0}
+    assert t[1] == {"n_max": 512, "blks": 16, "qr_helpers": 8, "spd_precision": 1, "batched": 0,
+                    "trisqrt_cutoff": 256}
+    assert t[2] == {"n_max": 4096, "blks": 32, "qr_helpers": -1, "spd_precision": 0, "batched": 0,
+                    "trisqrt_cutoff": 0}
 
 
 def test_shipped_tables_are_valid():
@@ -53,3 +56,4 @@ def test_shipped_tables_are_valid():
         for e in t:
             assert 1 <= e["blks"] <= 32 and -1 <= e["qr_helpers"] <= 24
             assert e["batched"] in (0, 1) and 0 <= e["spd_precision"] <= 3
+            assert e.get("trisqrt_cutoff", 0) == 0 or e["trisqrt_cutoff"] >= 64

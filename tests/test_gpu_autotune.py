@@ -23,8 +23,9 @@ def _lib():
     mp.set_tuning(saved)
 
 
-def _entry(n_max, blks=32, helpers=-1, batched=1, prec=0):
-    return {"n_max": n_max, "blks": blks, "qr_helpers": helpers, "batched": batched, "spd_precision": prec}
+def _entry(n_max, blks=32, helpers=-1, batched=1, prec=0, cutoff=0):
+    return {"n_max": n_max, "blks": blks, "qr_helpers": helpers, "batched": batched, "spd_precision": prec,
+            "trisqrt_cutoff": cutoff}
 
 
 @pytest.mark.parametrize("bad,code", [
@@ -32,6 +33,7 @@ def _entry(n_max, blks=32, helpers=-1, batched=1, prec=0):
     ([_entry(256, blks=0)], -4),               # block size out of range
     ([_entry(256, helpers=25)], -4),
     ([_entry(256, batched=2)], -4),
+    ([_entry(256, cutoff=-1)], -4),
     ([_entry(i + 1) for i in range(33)], -3),  # too many entries
 ])
 def test_set_tuning_rejects(bad, code):
@@ -41,7 +43,7 @@ def test_set_tuning_rejects(bad, code):
 
 
 def test_tuning_round_trip():
-    t = [_entry(128, blks=8), _entry(1024, blks=16, helpers=0, batched=0, prec=1)]
+    t = [_entry(128, blks=8), _entry(1024, blks=16, helpers=0, batched=0, prec=1, cutoff=256)]
     mp.set_tuning(t)
     assert mp.get_tuning() == t
     mp.set_tuning([])

@@ -262,3 +262,34 @@ def test_status_codes():
     # empty input
     X, info = mp.sqrtm_mixed(torch.zeros((0, 0), dtype=torch.float64, device="cuda"))
     assert info["status"] == 0 and X.shape == (0, 0)
+
+
+# --------------------------------------------------------------------------
+# a3 by the recursive splitting (Deadman-Higham-Ralha) against the oracle
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("fp64", [False, True])
+@pytest.mark.parametrize("n,cutoff", [(100, 64), (130, 64), (300, 64), (300, 128), (700, 256)])
+def test_trisqrt_recursive(n, cutoff, fp64):
+    S0 = synth.random_upper_rhp(n, seed=35 + n)
+    T = np.triu(S0 @ S0)
+    dt = torch.complex128 if fp64 else torch.complex64
+    u = U64 if fp64 else U32
+    Tin = T if fp64 else _c64(T)
+    S = host_cm(mp.step_trisqrt_rec(dev_cm(Tin, dt), n, cutoff=cutoff, fp64=fp64), n).astype(np.complex128)
+    So = oracle.trisqrt(Tin.astype(np.complex128))
+    assert np.all(np.tril(S, -1) == 0)
+    assert np.linalg.norm(S - So) <= 100 * n * u * np.linalg.norm(So)
+
+
+def test_sqrtm_mixed_recursive_trisqrt_from_tuning():
+    n = 600
+    A = torch.from_numpy(synth.shifted_gaussian(n, 3.0, seed=36)).cuda()
+    saved = mp.get_tuning()
+    try:
+        mp.set_tuning([{"n_max": 1 << 20, "blks": 32, "qr_helpers": -1, "batched": 1, "spd_precision": 0,
+                        "trisqrt_cutoff": 256}])
+        X, info = mp.sqrtm_mixed(A, kind=mp.KIND_GENERAL, steps=3)
+    finally:
+        mp.set_tuning(saved)
+    assert info["status"] == 0
+    assert oracle.rel_residual(X.cpu().numpy(), A.cpu().numpy()) <= 5 * n * U64
