@@ -56,6 +56,8 @@ def load(path):
     L.orc_trisqrt.restype = i
     L.orc_sqrtm_schur.argtypes = [i, P, i, P, i, P, P, P]
     L.orc_sqrtm_schur.restype = i
+    L.orc_zsqrtm_schur.argtypes = [i, P, i, P, i, P, P, P]
+    L.orc_zsqrtm_schur.restype = i
     L.orc_jacobi_eig.argtypes = [i, P, i, P, i, P]
     L.orc_jacobi_eig.restype = i
     L.orc_bs_solve.argtypes = [i, i, P, i, P, i, P, i]
@@ -163,6 +165,39 @@ def sqrtm_schur(A, return_factors=False):
     if return_factors:
         return X, Q, T, S
     return X
+
+
+def sqrtm_schur_complex(A, return_factors=False):
+    """The FP64 Schur method for a complex matrix (the method is stated for
+    A in C^{n x n}, Sec. 1): ``X = Q T^{1/2} Q^H``, all complex."""
+    n = A.shape[0]
+    Af = _f(A, np.complex128)
+    X = np.zeros((n, n), dtype=np.complex128, order="F")
+    Q = np.zeros((n, n), dtype=np.complex128, order="F")
+    T = np.zeros((n, n), dtype=np.complex128, order="F")
+    S = np.zeros((n, n), dtype=np.complex128, order="F")
+    st = lib().orc_zsqrtm_schur(n, _p(Af), max(n, 1), _p(X), max(n, 1), _p(Q), _p(T), _p(S))
+    if st:
+        raise OracleError(st, "zsqrtm_schur")
+    if return_factors:
+        return X, Q, T, S
+    return X
+
+
+def refine_complex(A, Q, S, X0, steps, blks=32):
+    """Algorithm 2 steps 5-11 for complex A with frozen factors and the
+    stopping test nullified, in FP64: ``R = A - X X``, ``Y`` from
+    ``S Y + Y S = Q^H R Q`` (Algorithm 1), ``X += Q Y Q^H`` (no real part
+    taken: X is complex).  Returns the iterates ``[X0, ..., X_steps]``."""
+    X = np.asarray(X0, dtype=np.complex128).copy()
+    Q = np.asarray(Q, dtype=np.complex128)
+    out = [X.copy()]
+    for _ in range(steps):
+        R = np.asarray(A, dtype=np.complex128) - X @ X
+        Y = rtrsyl(S, S, Q.conj().T @ R @ Q, blks)
+        X = X + Q @ Y @ Q.conj().T
+        out.append(X.copy())
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -325,6 +325,46 @@ int orc_sqrtm_schur(int n, const double *A, int lda, double *X, int ldx, zc *Qou
 }
 
 /* ------------------------------------------------------------------------ */
+/* The same Schur method for a COMPLEX matrix (the method is stated for     */
+/* A in C^{n x n}; Sec. 1): A = Q T Q^H by the complex Householder          */
+/* Hessenberg reduction and single-shift QR, S = T^{1/2} by Eq. (subst),    */
+/* X = Q S Q^H, all complex.  A complex n x n (lda); X complex (ldx);        */
+/* Qout, Tout, Sout as above (may be NULL).  Returns 0, 2 or 3.             */
+/* ------------------------------------------------------------------------ */
+int orc_zsqrtm_schur(int n, const zc *A, int lda, zc *X, int ldx, zc *Qout, zc *Tout, zc *Sout)
+{
+    size_t nn = (size_t)n * (size_t)n;
+    if (nn == 0) nn = 1;
+    zc *T = (zc *)calloc(nn, sizeof(zc));
+    zc *Q = (zc *)calloc(nn, sizeof(zc));
+    zc *S = (zc *)calloc(nn, sizeof(zc));
+    zc *W = (zc *)calloc(nn, sizeof(zc));
+    zc *P = (zc *)calloc(nn, sizeof(zc));
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) T[IDX(i, j, n)] = A[IDX(i, j, lda)];
+    orc_hessenberg(n, T, n, Q, n);
+    int st = orc_schur_qr(n, T, n, Q, n);
+    if (st == 0) {
+        for (int i = 0; i < n; ++i) {
+            zc t = T[IDX(i, i, n)];
+            if (creal(t) <= 0.0 && cimag(t) == 0.0) st = 2;
+        }
+    }
+    if (st == 0) st = orc_trisqrt(n, T, n, S, n);
+    if (st == 0) {
+        orc_zgemm('N', 'N', n, 1.0, Q, n, S, n, 0.0, W, n);
+        orc_zgemm('N', 'C', n, 1.0, W, n, Q, n, 0.0, P, n); /* P = Q S Q^H */
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) X[IDX(i, j, ldx)] = P[IDX(i, j, n)];
+    }
+    if (Qout) memcpy(Qout, Q, sizeof(zc) * (size_t)n * (size_t)n);
+    if (Tout) memcpy(Tout, T, sizeof(zc) * (size_t)n * (size_t)n);
+    if (Sout) memcpy(Sout, S, sizeof(zc) * (size_t)n * (size_t)n);
+    free(T); free(Q); free(S); free(W); free(P);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Cyclic two-sided Jacobi for real symmetric A = V diag(lam) V^T.          */
 /* A (in, destroyed), V (out, orthogonal), lam (out, unsorted).             */
 /* Each rotation zeroes a_pq with t = sign(tau)/(|tau| + sqrt(1 + tau^2)),  */

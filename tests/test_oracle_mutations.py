@@ -46,6 +46,7 @@ MUTATIONS = [
     ("tricbrt_v_update_drops_sum", "V[IDX(i, j, ldv)] = sij * (si + sj) + sv;", "V[IDX(i, j, ldv)] = sij * (si + sj);"),
     ("ccbrt_other_branch", "double th = carg(z) / 3.0;", "double th = (carg(z) + 6.283185307179586) / 3.0;"),
     ("rtrsyl3_w_without_new_entry", "W[IDX(i, j, m)] = wp + y * St[IDX(j, j, ldst)];", "W[IDX(i, j, m)] = wp;"),
+    ("zsqrtm_conjugated_result", "X[IDX(i, j, ldx)] = P[IDX(i, j, n)];", "X[IDX(i, j, ldx)] = conj(P[IDX(i, j, n)]);"),
     ("rtrsyl3_transposed_vt", "for (int l = 0; l < j; ++l) acc -= C[IDX(i, l, ldc)] * Vt[IDX(l, j, ldvt)];",
      "for (int l = 0; l < j; ++l) acc -= C[IDX(i, l, ldc)] * Vt[IDX(j, l, ldvt)];"),
 ]
@@ -69,6 +70,14 @@ def _checks(orc):
         X = orc.sqrtm_schur(A)
         return orc.rel_residual(X, A) <= 5 * 20 * U and np.all(np.linalg.eigvals(X).real > 0)
     run("sqrtm_residual", sqrtm_residual)
+
+    def zsqrtm_residual():
+        g = np.random.default_rng(43)
+        Ac = 3.0 * np.eye(16) + (g.standard_normal((16, 16)) + 1j * g.standard_normal((16, 16))) / 6.0
+        X = orc.sqrtm_schur_complex(Ac)
+        return (np.linalg.norm(X @ X - Ac) <= 20 * 16 * U * np.linalg.norm(Ac)
+                and np.all(np.linalg.eigvals(X).real > 0))
+    run("zsqrtm_residual", zsqrtm_residual)
 
     def schur_similarity():
         Q, T = orc.schur(A)

@@ -459,3 +459,71 @@ def test_refine3_contracts(orc):
     errs = [orc.rel_err(Xk, X) for Xk in its]
     assert errs[1] <= 1e-3 * errs[0]
     assert errs[2] <= 1e-13
+
+
+# --------------------------------------------------------------------------
+# complex input (the method is stated for A in C^{n x n}, Sec. 1)
+# --------------------------------------------------------------------------
+def _crandom(n, seed, shift=3.0):
+    g = np.random.default_rng(seed)
+    return shift * np.eye(n) + (g.standard_normal((n, n)) + 1j * g.standard_normal((n, n))) / np.sqrt(2 * n)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 30, 90])
+def test_zsqrtm_schur_invariants(orc, n):
+    A = _crandom(n, 700 + n)
+    X = orc.sqrtm_schur_complex(A)
+    assert np.linalg.norm(X @ X - A) <= 20 * n * U * np.linalg.norm(A)
+    assert np.all(np.linalg.eigvals(X).real > 0)
+
+
+def test_zsqrtm_schur_known_similarity(orc):
+    # A = P diag(d^2) P^-1 with complex d in the open right half plane has
+    # the principal square root P diag(d) P^-1
+    g = np.random.default_rng(710)
+    n = 14
+    P = np.eye(n) + 0.25 * (g.standard_normal((n, n)) + 1j * g.standard_normal((n, n)))
+    d = g.uniform(0.5, 2.0, n) + 1j * g.uniform(-1.5, 1.5, n)
+    Pi = np.linalg.inv(P)
+    X = orc.sqrtm_schur_complex(P @ np.diag(d * d) @ Pi)
+    assert orc.rel_err(X, P @ np.diag(d) @ Pi) <= 1e-12
+
+
+def test_zsqrtm_schur_hermitian_closed_form(orc):
+    # Hermitian positive definite A = U diag(lam) U^H: X = U diag(sqrt(lam)) U^H
+    g = np.random.default_rng(720)
+    n = 25
+    U_, _ = np.linalg.qr(g.standard_normal((n, n)) + 1j * g.standard_normal((n, n)))
+    lam = 10.0 ** g.uniform(-2.0, 2.0, n)
+    X = orc.sqrtm_schur_complex((U_ * lam) @ U_.conj().T)
+    assert orc.rel_err(X, (U_ * np.sqrt(lam)) @ U_.conj().T) <= 1e-12
+
+
+def test_zsqrtm_schur_real_input_matches_real_method(orc):
+    A = synth.shifted_gaussian(40, 3.0, seed=730)
+    Xc = orc.sqrtm_schur_complex(A.astype(np.complex128))
+    assert np.linalg.norm(Xc.imag) <= 1e-13 * np.linalg.norm(Xc)
+    assert orc.rel_err(Xc.real, orc.sqrtm_schur(A)) <= 1e-13
+
+
+def test_zsqrtm_schur_vs_scipy(orc):
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    A = _crandom(50, 740)
+    assert orc.rel_err(orc.sqrtm_schur_complex(A), scipy_linalg.sqrtm(A)) <= 1e-12
+
+
+def test_zsqrtm_negative_real_eigenvalue_status(orc):
+    T = np.diag([2.0 + 1j, -3.0 + 0j, 1.0])
+    with pytest.raises(orc.OracleError) as e:
+        orc.sqrtm_schur_complex(T)
+    assert e.value.code == 2
+
+
+def test_refine_complex_contracts(orc):
+    n = 24
+    A = _crandom(n, 750)
+    X, Q, T, S = orc.sqrtm_schur_complex(A, return_factors=True)
+    X0 = X + 1e-6 * (np.random.default_rng(751).standard_normal((n, n)) + 0j)
+    its = orc.refine_complex(A, Q, S, X0, 3)
+    errs = [orc.rel_err(Xk, X) for Xk in its]
+    assert errs[1] <= 1e-3 * errs[0] and errs[3] <= 1e-14
