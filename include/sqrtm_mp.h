@@ -188,6 +188,23 @@ SQRTM_API int sqrtm_schur_fp64(sqrtm_handle_t handle, const double *dA, int64_t 
                      double tol, double *dX, int64_t ldx, const sqrtm_opts *opts,
                      sqrtm_info *info);
 
+/* Complex input (the method is stated for A in C^{n x n}, Sec. 1): the
+ * same general path (Algorithm 2) with complex iterates.  dA, dX: n x n
+ * complex FP64 matrices stored as interleaved (re, im) pairs
+ * (cuDoubleComplex / std::complex<double> layout), column-major, lda and
+ * ldx counted in complex elements.  The residual A - X_k^2 and the update
+ * are complex FP64; X_0 = Q S Q^H and the corrections Q Y Q^H are complex
+ * (no real part taken).  opts->kind is ignored (Hermitian input takes the
+ * Schur form too); no factors are kept for sqrtm_backward.  Other arguments
+ * and return codes as for sqrtm_mixed. */
+SQRTM_API int sqrtm_mixed_complex(sqrtm_handle_t handle, const void *dA, int64_t n, int64_t lda, double tol,
+                                  void *dX, int64_t ldx, const sqrtm_opts *opts, sqrtm_info *info);
+
+/* Plain FP64 Schur method for complex input: X = Q T^{1/2} Q^H in FP64,
+ * no refinement; layout as for sqrtm_mixed_complex. */
+SQRTM_API int sqrtm_schur_fp64_complex(sqrtm_handle_t handle, const void *dA, int64_t n, int64_t lda, double tol,
+                                       void *dX, int64_t ldx, const sqrtm_opts *opts, sqrtm_info *info);
+
 /* Mixed-precision principal cube root (Sec. 4, p = 3): the X with X^3 = A
  * whose eigenvalues have arguments in (-pi/3, pi/3], for A with no
  * eigenvalue on the closed negative real axis.  The steps of Algorithm 2

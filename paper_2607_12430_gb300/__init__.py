@@ -93,6 +93,8 @@ _SIGS = {
     "sqrtm_get_tuning": ([_P, ctypes.POINTER(TuneEntry), _I], _I),
     "sqrtm_mixed": ([_P, _P, _L, _L, _D, _P, _L, ctypes.POINTER(Opts), ctypes.POINTER(Info)], _I),
     "sqrtm_schur_fp64": ([_P, _P, _L, _L, _D, _P, _L, ctypes.POINTER(Opts), ctypes.POINTER(Info)], _I),
+    "sqrtm_mixed_complex": ([_P, _P, _L, _L, _D, _P, _L, ctypes.POINTER(Opts), ctypes.POINTER(Info)], _I),
+    "sqrtm_schur_fp64_complex": ([_P, _P, _L, _L, _D, _P, _L, ctypes.POINTER(Opts), ctypes.POINTER(Info)], _I),
     "sqrtm_cbrtm_mixed": ([_P, _P, _L, _L, _D, _P, _L, ctypes.POINTER(Opts), ctypes.POINTER(Info)], _I),
     "sqrtm_cbrtm_schur_fp64": ([_P, _P, _L, _L, _D, _P, _L, ctypes.POINTER(Opts), ctypes.POINTER(Info)], _I),
     "sqrtm_backward": ([_P, _P, _L, _L, _D, _P, _L, ctypes.POINTER(Info)], _I),
@@ -202,11 +204,11 @@ def _install_shipped_tuning(h):
         return
 
 
-def _check_square(A, name="A"):
+def _check_square(A, name="A", dtype=torch.float64):
     if not isinstance(A, torch.Tensor) or not A.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
-    if A.dtype != torch.float64:
-        raise TypeError(f"{name} must be float64")
+    if A.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
     if A.dim() != 2 or A.shape[0] != A.shape[1]:
         raise ValueError(f"{name} must be square")
     if not A.is_contiguous():
@@ -293,6 +295,40 @@ def sqrtm_schur_fp64(A, out=None, raise_on_error=True, **kw):
     rc = lib().sqrtm_schur_fp64(handle(), _ptr(A), n, ld, 0.0, _ptr(X), ld, ctypes.byref(o), ctypes.byref(info))
     if rc and raise_on_error:
         raise SqrtmError(rc, "sqrtm_schur_fp64")
+    d = info.as_dict()
+    d["status"] = rc
+    return X, d
+
+
+def sqrtm_mixed_complex(A, tol=1e-12, out=None, raise_on_error=True, **kw):
+    """Mixed-precision principal square root of a complex128 CUDA matrix
+    (Algorithm 2 with complex iterates).  Returns ``(X, info_dict)``."""
+    A = _check_square(A, dtype=torch.complex128)
+    n = A.shape[0]
+    X = _out_like(out, A)
+    o = make_opts(tol=tol, **kw)
+    info = Info()
+    ld = max(1, n)
+    rc = lib().sqrtm_mixed_complex(handle(), _ptr(A), n, ld, tol, _ptr(X), ld, ctypes.byref(o), ctypes.byref(info))
+    if rc and raise_on_error:
+        raise SqrtmError(rc, "sqrtm_mixed_complex")
+    d = info.as_dict()
+    d["status"] = rc
+    return X, d
+
+
+def sqrtm_schur_fp64_complex(A, out=None, raise_on_error=True, **kw):
+    """Plain FP64 Schur method for a complex128 CUDA matrix."""
+    A = _check_square(A, dtype=torch.complex128)
+    n = A.shape[0]
+    X = _out_like(out, A)
+    o = make_opts(**kw)
+    info = Info()
+    ld = max(1, n)
+    rc = lib().sqrtm_schur_fp64_complex(handle(), _ptr(A), n, ld, 0.0, _ptr(X), ld, ctypes.byref(o),
+                                        ctypes.byref(info))
+    if rc and raise_on_error:
+        raise SqrtmError(rc, "sqrtm_schur_fp64_complex")
     d = info.as_dict()
     d["status"] = rc
     return X, d

@@ -289,19 +289,21 @@ static bool is_bitwise_symmetric(sqrtm_handle_t h, const double *dA, int64_t n, 
 // plain Schur method.  root = 3 gives the principal cube root (Sec. 4, p = 3)
 // by the same steps: the triangular cube root S with V = S^2 in place of the
 // triangular square root, the residual A - X (X X), and the correction
-// equation S^2 Y + S Y S + Y S^2 = Q^H R Q (Eq. (3rd-order)).
+// equation S^2 Y + S Y S + Y S^2 = Q^H R Q (Eq. (3rd-order)).  cin: A and
+// X are complex (interleaved FP64 pairs, lda / ldx in complex elements); the
+// steps are the same with complex iterates (no real part taken).
 // ---------------------------------------------------------------------------
 template <class R>
 static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, double tol,
                         double *dX, int64_t ldx, const sqrtm_opts &o, sqrtm_info *info,
-                        bool refine, int root = 2)
+                        bool refine, int root = 2, bool cin = false)
 {
     cudaStream_t s = h->stream;
     const size_t nn = (size_t)n * (size_t)n;
     const size_t cb = sizeof(cplx<R>);
     // factors: Q, S persist for the adjoint
     size_t fbytes = 2 * Carve::round(nn * cb) + Carve::round(nn * sizeof(double)) + 1024;
-    size_t wbytes = scalars_bytes(n) + 3 * Carve::round(nn * cb) + Carve::round(nn * sizeof(float)) +
+    size_t wbytes = scalars_bytes(n) + 3 * Carve::round(nn * cb) + Carve::round(nn * sizeof(float) * (cin ? 2 : 1)) +
                     Carve::round((n + 8) * cb) + Carve::round(8 * sizeof(R)) +
                     Carve::round(2 * sizeof(SchurDesc<R>)) +
                     2 * (Carve::round(qr_log_capacity(n) * sizeof(RotLog<R>)) +
@@ -318,7 +320,7 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     cplx<R> *T = cw.take<cplx<R>>(nn);
     cplx<R> *W = cw.take<cplx<R>>(nn);
     cplx<R> *Rt = cw.take<cplx<R>>(nn);
-    float *Rhat = cw.take<float>(nn);
+    float *Rhat = cw.take<float>(cin ? 2 * nn : nn);  // complex input: fl32 of a complex residual
     cplx<R> *v = cw.take<cplx<R>>(n + 8);
     R *beta = cw.take<R>(8);
     // two descriptors of the same matrix with separate log / window / U
@@ -345,8 +347,13 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
 
     SQM_CU(cudaMemsetAsync(sc.e, 0, 16 * sizeof(int), s));
     SQM_CU(cudaEventRecord(h->ev[0], s));
-    SQM_CU(launch_norm_scale(dA, n, lda, sc.partials, (int)std::min<int64_t>(n, 1024), sc.norm, sc.e, s, root));
-    SQM_CU(launch_cast_scaled<R>(dA, n, lda, sc.e, T, n, s, root));
+    if (cin) {
+        SQM_CU(launch_norm_scale_z(dA, n, lda, sc.partials, (int)std::min<int64_t>(n, 1024), sc.norm, sc.e, s));
+        SQM_CU(launch_cast_scaled_z<R>(dA, n, lda, sc.e, T, n, s));
+    } else {
+        SQM_CU(launch_norm_scale(dA, n, lda, sc.partials, (int)std::min<int64_t>(n, 1024), sc.norm, sc.e, s, root));
+        SQM_CU(launch_cast_scaled<R>(dA, n, lda, sc.e, T, n, s, root));
+    }
     double norm_a = 0.0;
     int e = 0;
     if (int rc = read_scalars(h, sc, &norm_a, nullptr, &e, nullptr, nullptr)) return rc;
@@ -374,7 +381,7 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     memcpy(h->staging.p, hd2, sizeof(hd2));
     SQM_CU(cudaMemcpyAsync(ddesc, h->staging.p, sizeof(hd2), cudaMemcpyHostToDevice, s));
     SQM_CU(cudaStreamSynchronize(s));
-    if (hess_cluster_size<R>((int)n) > 0) {
+    if (!cin && hess_cluster_size<R>((int)n) > 0) {
         // A is real: the cluster-resident real reduction (W and Rt are free
         // until the Schur form is done)
         SQM_CU(launch_hessenberg_cluster<R>(T, Q, (int)n, (int)n, (R *)W, (R *)Rt, s));
@@ -400,7 +407,8 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     else SQM_CU(launch_trisqrt<R>(T, (int)n, S, (int)n, (int)n, o.blks, sc.st_solve, s));
     // X_0 = Re(Q S Q^H), rounded to R, times 2^e
     SQM_CU(launch_cgemm<R>(OP_N, OP_N, (int)n, (int)n, (int)n, Q, (int)n, false, S, (int)n, EPI_STORE, W, (int)n, nullptr, 0, 0.0, s));
-    SQM_CU(launch_cgemm<R>(OP_N, OP_H, (int)n, (int)n, (int)n, W, (int)n, false, Q, (int)n, EPI_REAL_TO_F64, nullptr, 0, dX, ldx, ldexp(1.0, e), s));
+    SQM_CU(launch_cgemm<R>(OP_N, OP_H, (int)n, (int)n, (int)n, W, (int)n, false, Q, (int)n,
+                           cin ? EPI_CPLX_TO_F64 : EPI_REAL_TO_F64, nullptr, 0, dX, ldx, ldexp(1.0, e), s));
     SQM_CU(cudaEventRecord(h->ev[2], s));
     int st_schur = 0, st_solve = 0;
     if (int rc = read_scalars(h, sc, nullptr, nullptr, nullptr, &st_schur, &st_solve)) return rc;
@@ -437,6 +445,9 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
                                             (int)n, nullptr, nullptr, 0, 0.0, s));
                 SQM_CU(launch_residual_f64_ab(dA, lda, dX, ldx, XX, n, (int)n, 3 * e, Rhat, (int)n, sc.partials,
                                               &np, s));
+            } else if (cin) {
+                SQM_CU(launch_zresidual_f64(dA, lda, dX, ldx, (int)n, e, (cplx<float> *)Rhat, (int)n, sc.partials, &np,
+                                            s));
             } else {
                 SQM_CU(launch_residual_f64(dA, lda, dX, ldx, (int)n, e, Rhat, (int)n, sc.partials, &np, s));
             }
@@ -455,19 +466,20 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
             }
         }
         // R~ = Q^H Rhat Q; Y solves S Y + Y S = R~; X += 2^e Re(Q Y Q^H)
-        SQM_CU(launch_cgemm<R>(OP_N, OP_N, (int)n, (int)n, (int)n, Rhat, (int)n, true, Q, (int)n, EPI_STORE, W, (int)n, nullptr, 0, 0.0, s));
+        SQM_CU(launch_cgemm<R>(OP_N, OP_N, (int)n, (int)n, (int)n, Rhat, (int)n, !cin, Q, (int)n, EPI_STORE, W, (int)n, nullptr, 0, 0.0, s));
         SQM_CU(launch_cgemm<R>(OP_H, OP_N, (int)n, (int)n, (int)n, Q, (int)n, false, W, (int)n, EPI_STORE, Rt, (int)n, nullptr, 0, 0.0, s));
         if (root == 3)  // W is free between the transforms: it holds Z = Y S
             SQM_CU(launch_rtrsyl3<R>(S, (int)n, V, (int)n, Rt, (int)n, W, (int)n, (int)n, o.blks, sc.st_solve, s));
         else
             SQM_CU(launch_rtrsyl<R>(S, (int)n, (int)n, S, (int)n, (int)n, Rt, (int)n, o.blks, sc.st_solve, s));
         SQM_CU(launch_cgemm<R>(OP_N, OP_N, (int)n, (int)n, (int)n, Q, (int)n, false, Rt, (int)n, EPI_STORE, W, (int)n, nullptr, 0, 0.0, s));
-        SQM_CU(launch_cgemm<R>(OP_N, OP_H, (int)n, (int)n, (int)n, W, (int)n, false, Q, (int)n, EPI_REAL_ADD_F64, nullptr, 0, dX, ldx, ldexp(1.0, e), s));
+        SQM_CU(launch_cgemm<R>(OP_N, OP_H, (int)n, (int)n, (int)n, W, (int)n, false, Q, (int)n,
+                               cin ? EPI_CPLX_ADD_F64 : EPI_REAL_ADD_F64, nullptr, 0, dX, ldx, ldexp(1.0, e), s));
         ++applied;
     }
     SQM_CU(cudaEventRecord(h->ev[3], s));
     if (int rc = read_scalars(h, sc, nullptr, nullptr, nullptr, nullptr, &st_solve)) return rc;
-    if (!st_solve && (status == 0 || status == 1) && root == 2) {
+    if (!st_solve && (status == 0 || status == 1) && root == 2 && !cin) {
         // keep the factors and X for sqrtm_backward
         SQM_CU(cudaMemcpy2DAsync(Xsave, n * sizeof(double), dX, ldx * sizeof(double), n * sizeof(double), n,
                                  cudaMemcpyDeviceToDevice, s));
@@ -544,6 +556,37 @@ extern "C" int sqrtm_schur_fp64(sqrtm_handle_t h, const double *dA, int64_t n, i
     if (kind == SQRTM_KIND_SPD && spd_enabled()) rc = spd_schur_fp64(h, dA, n, lda, dX, ldx, o, info);
     else rc = general_path<double>(h, dA, n, lda, 0.0, dX, ldx, o, info, false);
     h->fact_n = -1;  // the FP64 method keeps no low-precision factors
+    if (info) info->status = rc;
+    return rc;
+}
+
+extern "C" int sqrtm_mixed_complex(sqrtm_handle_t h, const void *dA, int64_t n, int64_t lda, double tol, void *dX,
+                                   int64_t ldx, const sqrtm_opts *opts, sqrtm_info *info)
+{
+    info_reset(info);
+    if (!h) return -1;
+    if (int rc = check_args(dA, n, lda, dX, ldx)) return rc;
+    sqrtm_opts o;
+    if (int rc = resolve_opts(opts, tol, &o)) return rc;
+    if (n == 0) return 0;
+    apply_tuning(h, n, &o);
+    int rc = general_path<float>(h, (const double *)dA, n, lda, o.tol, (double *)dX, ldx, o, info, true, 2, true);
+    if (info) info->status = rc;
+    return rc;
+}
+
+extern "C" int sqrtm_schur_fp64_complex(sqrtm_handle_t h, const void *dA, int64_t n, int64_t lda, double tol,
+                                        void *dX, int64_t ldx, const sqrtm_opts *opts, sqrtm_info *info)
+{
+    info_reset(info);
+    if (!h) return -1;
+    if (int rc = check_args(dA, n, lda, dX, ldx)) return rc;
+    sqrtm_opts o;
+    if (int rc = resolve_opts(opts, tol, &o)) return rc;
+    if (n == 0) return 0;
+    apply_tuning(h, n, &o);
+    int rc = general_path<double>(h, (const double *)dA, n, lda, 0.0, (double *)dX, ldx, o, info, false, 2, true);
+    h->fact_n = -1;
     if (info) info->status = rc;
     return rc;
 }

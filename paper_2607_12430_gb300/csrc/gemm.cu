@@ -109,7 +109,15 @@ cgemm_kernel(int m, int n, int k, const void *__restrict__ Av, int lda,
             if (EPI == EPI_STORE) C[gi + (int64_t)gj * ldc] = acc[i][j];
             else if (EPI == EPI_REAL_TO_F64) X[gi + gj * ldx] = (double)((R)acc[i][j].x) * scale;
             else if (EPI == EPI_REAL_ADD_F64) X[gi + gj * ldx] += (double)acc[i][j].x * scale;
-            else X[gj + gi * ldx] += (double)acc[i][j].x * scale;
+            else if (EPI == EPI_CPLX_TO_F64) {
+                double *x = X + 2 * (gi + gj * ldx);
+                x[0] = (double)((R)acc[i][j].x) * scale;
+                x[1] = (double)((R)acc[i][j].y) * scale;
+            } else if (EPI == EPI_CPLX_ADD_F64) {
+                double *x = X + 2 * (gi + gj * ldx);
+                x[0] += (double)acc[i][j].x * scale;
+                x[1] += (double)acc[i][j].y * scale;
+            } else X[gj + gi * ldx] += (double)acc[i][j].x * scale;
         }
     }
 }
@@ -128,6 +136,14 @@ static cudaError_t dispatch_epi(int epi, dim3 g, cudaStream_t s, int m, int n, i
         break;
     case EPI_REAL_ADD_F64:
         cgemm_kernel<R, OPA, OPB, AREAL, EPI_REAL_ADD_F64><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale, jobs); count_launch();
+        break;
+    case EPI_CPLX_TO_F64:
+        if (AREAL) return cudaErrorInvalidValue;
+        cgemm_kernel<R, OPA, OPB, AREAL, EPI_CPLX_TO_F64><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale, jobs); count_launch();
+        break;
+    case EPI_CPLX_ADD_F64:
+        if (AREAL) return cudaErrorInvalidValue;
+        cgemm_kernel<R, OPA, OPB, AREAL, EPI_CPLX_ADD_F64><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale, jobs); count_launch();
         break;
     default:
         cgemm_kernel<R, OPA, OPB, AREAL, EPI_REAL_ADD_F64_T><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale, jobs); count_launch();
@@ -270,6 +286,90 @@ cudaError_t launch_residual_f64(const double *A, int64_t lda, const double *X, i
     if (n <= 0) return cudaSuccess;
     residual_f64_kernel<<<g, G_THREADS, 0, s>>>(A, lda, X, ldx, X, ldx, n, ldexp(1.0, -2 * e), Rhat, ldr, partials,
                                                 nullptr);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP64 residual of a complex iterate: R = (A - X X) 4^-e, complex
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(G_THREADS)
+zresidual_f64_kernel(const double *__restrict__ A, int64_t lda, const double *__restrict__ X, int64_t ldx, int n,
+                     double sc, cplx<float> *__restrict__ Rhat, int ldr, double *__restrict__ partials)
+{
+    __shared__ cplx<double> As[GB_K][GB_M + 1];
+    __shared__ cplx<double> Bs[GB_K][GB_N + 1];
+    __shared__ double red[G_THREADS / 32];
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    const int m0 = blockIdx.x * GB_M, n0 = blockIdx.y * GB_N;
+    const cplx<double> *Xc = reinterpret_cast<const cplx<double> *>(X);
+    const cplx<double> *Ac = reinterpret_cast<const cplx<double> *>(A);
+    cplx<double> acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = cplx<double>{0.0, 0.0};
+    for (int k0 = 0; k0 < n; k0 += GB_K) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int i = tid % GB_M, kk = tid / GB_M + 4 * q;
+            int gi = m0 + i, gk = k0 + kk;
+            As[kk][i] = (gi < n && gk < n) ? Xc[gi + gk * ldx] : cplx<double>{0.0, 0.0};
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int kk = tid % GB_K, j = tid / GB_K + 16 * q;
+            int gk = k0 + kk, gj = n0 + j;
+            Bs[kk][j] = (gk < n && gj < n) ? Xc[gk + gj * ldx] : cplx<double>{0.0, 0.0};
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GB_K; ++kk) {
+            cplx<double> a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], b[j]);
+        }
+        __syncthreads();
+    }
+    double ss = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int gi = m0 + ty * 4 + i;
+        if (gi >= n) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int gj = n0 + tx * 4 + j;
+            if (gj >= n) continue;
+            const cplx<double> a = Ac[gi + gj * lda];
+            const double rx = (a.x - acc[i][j].x) * sc, ry = (a.y - acc[i][j].y) * sc;
+            Rhat[gi + (int64_t)gj * ldr] = cplx<float>{(float)rx, (float)ry};
+            ss = fma(rx, rx, fma(ry, ry, ss));
+        }
+    }
+    ss = warp_sum(ss);
+    if ((tid & 31) == 0) red[tid >> 5] = ss;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < G_THREADS / 32; ++w) t += red[w];
+        partials[blockIdx.x + blockIdx.y * gridDim.x] = t;
+    }
+}
+
+cudaError_t launch_zresidual_f64(const double *A, int64_t lda, const double *X, int64_t ldx, int n, int e,
+                                 cplx<float> *Rhat, int ldr, double *partials, int *nparts, cudaStream_t s)
+{
+    dim3 g((unsigned)cdiv_i(n, GB_M), (unsigned)cdiv_i(n, GB_N));
+    *nparts = (int)(g.x * g.y);
+    if (n <= 0) return cudaSuccess;
+    zresidual_f64_kernel<<<g, G_THREADS, 0, s>>>(A, lda, X, ldx, n, ldexp(1.0, -2 * e), Rhat, ldr, partials);
     count_launch();
     return cudaGetLastError();
 }

@@ -121,6 +121,13 @@ cudaError_t launch_norm_scale(const double *A, int64_t n, int64_t lda, double *p
 template <class R>
 cudaError_t launch_cast_scaled(const double *A, int64_t n, int64_t lda, const int *d_e,
                                cplx<R> *As, int64_t ldas, cudaStream_t s, int root = 2);
+// complex input A (interleaved FP64 pairs, lda in complex elements): the
+// same norm, exponent (root 2) and scaled cast
+cudaError_t launch_norm_scale_z(const double *A, int64_t n, int64_t lda, double *partials, int nblk, double *d_norm,
+                                int *d_e, cudaStream_t s);
+template <class R>
+cudaError_t launch_cast_scaled_z(const double *A, int64_t n, int64_t lda, const int *d_e, cplx<R> *As, int64_t ldas,
+                                 cudaStream_t s);
 template <class R>
 cudaError_t launch_cast_scaled_real(const double *A, int64_t n, int64_t lda, const int *d_e,
                                     R *As, int64_t ldas, cudaStream_t s);
@@ -208,12 +215,16 @@ cudaError_t launch_rtrsyl(const cplx<R> *S, int lds, int m, const cplx<R> *St, i
 
 // ---- dense products (gemm.cu) ----
 enum OpT { OP_N = 0, OP_H = 1 };
-enum Epi { EPI_STORE = 0, EPI_REAL_TO_F64 = 1, EPI_REAL_ADD_F64 = 2, EPI_REAL_ADD_F64_T = 3 };
+enum Epi { EPI_STORE = 0, EPI_REAL_TO_F64 = 1, EPI_REAL_ADD_F64 = 2, EPI_REAL_ADD_F64_T = 3, EPI_CPLX_TO_F64 = 4,
+           EPI_CPLX_ADD_F64 = 5 };
 // C = op(A) op(B) (m x n, inner k).  A complex or (a_real) real R.
 // EPI_STORE:        C (complex) = result
 // EPI_REAL_TO_F64:  X[i,j] = double(R(Re(result))) * scale
 // EPI_REAL_ADD_F64: X[i,j] += double(Re(result)) * scale
 // EPI_REAL_ADD_F64_T: X[j,i] += double(Re(result)) * scale (transposed)
+// EPI_CPLX_TO_F64:  X (complex, interleaved FP64 pairs, ldx in complex
+//                   elements)[i,j] = widened R-rounded result * scale
+// EPI_CPLX_ADD_F64: X[i,j] += widened result * scale (complex)
 template <class R>
 cudaError_t launch_cgemm(int opA, int opB, int m, int n, int k, const void *A, int lda,
                          bool a_real, const cplx<R> *B, int ldb, int epi, cplx<R> *C, int ldc,
@@ -228,6 +239,11 @@ cudaError_t launch_residual_f64(const double *A, int64_t lda, const double *X, i
 cudaError_t launch_residual_f64_ab(const double *A, int64_t lda, const double *X, int64_t ldx,
                                    const double *B, int64_t ldb, int n, int shift, float *Rhat, int ldr,
                                    double *partials, int *nparts, cudaStream_t s);
+// Complex residual R = (A - X X) 4^-e in FP64 (A, X interleaved FP64 pairs,
+// lda / ldx in complex elements); Rhat = fl32(R) (complex, ld ldr) and
+// per-CTA partial sums of |R|^2.
+cudaError_t launch_zresidual_f64(const double *A, int64_t lda, const double *X, int64_t ldx, int n, int e,
+                                 cplx<float> *Rhat, int ldr, double *partials, int *nparts, cudaStream_t s);
 // Adjoint residual Res = G - (X^T Y + Y X^T) in FP64; Rhat = fl32(Res) and
 // per-CTA partial sums of |Res|^2.
 cudaError_t launch_adjoint_residual_f64(const double *G, int64_t ldg, const double *X, int64_t ldx,
