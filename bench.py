@@ -461,6 +461,22 @@ def run_cbrt_suite(args):
     return 0
 
 
+def run_complex_suite(args):
+    """Complex input (the method is stated for A in C^{n x n}, Sec. 1):
+    A = 3I + (G1 + i G2)/sqrt(2n), G1, G2 i.i.d. N(0,1), at n = 512 and
+    2048; one JSON line each (k*, times of the mixed method with k*
+    corrections and of the FP64 Schur method on the same GPU)."""
+    import torch
+    import paper_2607_12430_gb300 as mp
+    mp.lib()
+    for n in [int(x) for x in (args.sets or ["512", "2048"])]:
+        g = np.random.default_rng(synth.BASE_SEED + 20 + n)
+        M = 3.0 * np.eye(n) + (g.standard_normal((n, n)) + 1j * g.standard_normal((n, n))) / np.sqrt(2 * n)
+        A = torch.from_numpy(np.ascontiguousarray(M)).cuda()
+        _suite_case(args, "complex", "C%d" % n, n, A, mp.sqrtm_mixed_complex, mp.sqrtm_schur_fp64_complex, 6)
+    return 0
+
+
 def run_batch_suite(args):
     """The batch workload: 2048 matrices, n ~ U{16..256}, half SPD with
     lambda log-uniform in [1e-2, 1e2], half 2I + G/sqrt(n), through
@@ -524,9 +540,10 @@ def main():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--suite", choices=["table1", "cbrt", "batch"], default=None,
-                   help="the paper's Table 1 sets, or the cube root on sets I, II and the n = 512 "
-                        "workload (one JSON line each) instead of the benchmark")
+    p.add_argument("--suite", choices=["table1", "cbrt", "batch", "complex"], default=None,
+                   help="instead of the benchmark, one JSON line per case: the paper's Table 1 sets "
+                        "(table1), the cube root on sets I, II and the n = 512 workload (cbrt), the "
+                        "2048-matrix batch (batch), complex input at n = 512, 2048 (complex)")
     p.add_argument("--sets", nargs="*", default=None, help="--suite: which sets (default all)")
     args = p.parse_args()
     if args.impl == "reference":
@@ -539,6 +556,8 @@ def main():
         return run_cbrt_suite(args)
     if args.suite == "batch":
         return run_batch_suite(args)
+    if args.suite == "complex":
+        return run_complex_suite(args)
     return run_ours(args)
 
 
