@@ -58,6 +58,14 @@ def load(path):
     L.orc_sqrtm_schur.restype = i
     L.orc_zsqrtm_schur.argtypes = [i, P, i, P, i, P, P, P]
     L.orc_zsqrtm_schur.restype = i
+    L.orc_real_schur_qr.argtypes = [i, P, i, P, i]
+    L.orc_real_schur_qr.restype = i
+    L.orc_real_schur.argtypes = [i, P, i, P, P]
+    L.orc_real_schur.restype = i
+    L.orc_qtrisqrt.argtypes = [i, P, i, P, i]
+    L.orc_qtrisqrt.restype = i
+    L.orc_qrtrsyl.argtypes = [i, i, P, i, P, i, P, i]
+    L.orc_qrtrsyl.restype = i
     L.orc_jacobi_eig.argtypes = [i, P, i, P, i, P]
     L.orc_jacobi_eig.restype = i
     L.orc_bs_solve.argtypes = [i, i, P, i, P, i, P, i]
@@ -196,6 +204,70 @@ def refine_complex(A, Q, S, X0, steps, blks=32):
         R = np.asarray(A, dtype=np.complex128) - X @ X
         Y = rtrsyl(S, S, Q.conj().T @ R @ Q, blks)
         X = X + Q @ Y @ Q.conj().T
+        out.append(X.copy())
+    return out
+
+
+# ---------------------------------------------------------------------------
+# real arithmetic for real A (Remark 2.1): quasi-triangular Schur form
+# ---------------------------------------------------------------------------
+def real_schur(A):
+    """Real Schur decomposition ``A = Q T Q^T``: Q orthogonal, T
+    quasi-upper-triangular (2x2 diagonal blocks only for complex conjugate
+    eigenvalue pairs).  Returns (Q, T)."""
+    n = A.shape[0]
+    Af = _f(A, np.float64)
+    Q = np.zeros((n, n), dtype=np.float64, order="F")
+    T = np.zeros((n, n), dtype=np.float64, order="F")
+    st = lib().orc_real_schur(n, _p(Af), max(n, 1), _p(Q), _p(T))
+    if st:
+        raise OracleError(st, "real_schur")
+    return Q, T
+
+
+def qtrisqrt(T):
+    """``S = T^{1/2}`` of real quasi-upper-triangular ``T`` (real
+    arithmetic, 2x2 blocks kept whole)."""
+    n = T.shape[0]
+    Tf = _f(T, np.float64)
+    S = np.zeros((n, n), dtype=np.float64, order="F")
+    st = lib().orc_qtrisqrt(n, _p(Tf), max(n, 1), _p(S), max(n, 1))
+    if st:
+        raise OracleError(st, "qtrisqrt")
+    return S
+
+
+def qrtrsyl(S, St, C):
+    """``S Y + Y St = C`` for real quasi-upper-triangular S and St."""
+    m, n = C.shape
+    Sf, Stf, Y = _f(S, np.float64), _f(St, np.float64), _f(C, np.float64)
+    st = lib().orc_qrtrsyl(m, n, _p(Sf), max(m, 1), _p(Stf), max(n, 1), _p(Y), max(m, 1))
+    if st:
+        raise OracleError(st, "qrtrsyl")
+    return Y
+
+
+def sqrtm_real_schur(A, return_factors=False):
+    """The FP64 Schur method in real arithmetic (Remark 2.1):
+    ``X = Q T^{1/2} Q^T`` with the real Schur form."""
+    Q, T = real_schur(A)
+    S = qtrisqrt(T)
+    X = Q @ S @ Q.T
+    if return_factors:
+        return X, Q, T, S
+    return X
+
+
+def refine_real(A, Q, S, X0, steps):
+    """Algorithm 2 steps 5-11 with real factors (Remark 2.1), stopping test
+    nullified, in FP64: ``R = A - X X``; ``S Y + Y S = Q^T R Q``
+    (quasi-triangular); ``X += Q Y Q^T``.  Returns ``[X0, ..., X_steps]``."""
+    X = np.asarray(X0, dtype=np.float64).copy()
+    out = [X.copy()]
+    for _ in range(steps):
+        R = np.asarray(A, dtype=np.float64) - X @ X
+        Y = qrtrsyl(S, S, Q.T @ R @ Q)
+        X = X + Q @ Y @ Q.T
         out.append(X.copy())
     return out
 

@@ -616,3 +616,315 @@ int orc_cbrtm_schur(int n, const double *A, int lda, double *X, int ldx, zc *Qou
     free(T); free(Q); free(S); free(V); free(W); free(P);
     return st;
 }
+
+/* ======================================================================== */
+/* Real arithmetic for real A (Remark 2.1): A = Q T Q^T with Q orthogonal    */
+/* and T quasi-upper-triangular (1x1 blocks for real eigenvalues, 2x2       */
+/* blocks for complex conjugate pairs); the square root and the Sylvester   */
+/* solves in the same block structure, never cutting a 2x2 block.           */
+/* ======================================================================== */
+
+/* Householder reflector of a real 3-vector (or 2-vector, z unused when     */
+/* len == 2): P = I - beta v v^T with v(0) = 1 and P x = (r, 0, 0).         */
+static void orc_house3(int len, double x, double y, double z, double v[3], double *beta)
+{
+    double sig = y * y + (len == 3 ? z * z : 0.0);
+    v[0] = 1.0; v[1] = y; v[2] = len == 3 ? z : 0.0;
+    if (sig == 0.0) { *beta = 0.0; return; }
+    double mu = sqrt(x * x + sig);
+    double v0 = x <= 0.0 ? x - mu : -sig / (x + mu);
+    *beta = 2.0 * v0 * v0 / (sig + v0 * v0);
+    v[1] = y / v0;
+    v[2] = len == 3 ? z / v0 : 0.0;
+}
+
+/* rows r0 .. r0+len-1 of M, columns c0 .. c1-1: M <- P M */
+static void orc_house_rows(double *M, int ld, int r0, int len, int c0, int c1, const double v[3], double beta)
+{
+    if (beta == 0.0) return;
+    for (int j = c0; j < c1; ++j) {
+        double s = 0.0;
+        for (int l = 0; l < len; ++l) s += v[l] * M[IDX(r0 + l, j, ld)];
+        s *= beta;
+        for (int l = 0; l < len; ++l) M[IDX(r0 + l, j, ld)] -= s * v[l];
+    }
+}
+
+/* columns c0 .. c0+len-1 of M, rows r0 .. r1-1: M <- M P */
+static void orc_house_cols(double *M, int ld, int c0, int len, int r0, int r1, const double v[3], double beta)
+{
+    if (beta == 0.0) return;
+    for (int i = r0; i < r1; ++i) {
+        double s = 0.0;
+        for (int l = 0; l < len; ++l) s += M[IDX(i, c0 + l, ld)] * v[l];
+        s *= beta;
+        for (int l = 0; l < len; ++l) M[IDX(i, c0 + l, ld)] -= s * v[l];
+    }
+}
+
+/* A 2x2 block at (k, k) with real eigenvalues is split by a rotation that  */
+/* maps an eigenvector onto e_1 (applied to T and Q); one with complex      */
+/* eigenvalues is left as it is.                                             */
+static void orc_split_2x2(int n, double *H, int ldh, double *Z, int ldz, int k)
+{
+    double a = H[IDX(k, k, ldh)], b = H[IDX(k, k + 1, ldh)];
+    double c = H[IDX(k + 1, k, ldh)], d = H[IDX(k + 1, k + 1, ldh)];
+    if (c == 0.0) return;
+    double p = 0.5 * (a - d), disc = p * p + b * c;
+    if (disc < 0.0) return; /* complex pair: a genuine 2x2 block */
+    double lam = 0.5 * (a + d) + (p >= 0.0 ? sqrt(disc) : -sqrt(disc));
+    /* eigenvector for lam: (lam - d, c) (c != 0) */
+    double e0 = lam - d, e1 = c, nr = hypot(e0, e1);
+    double cs = e0 / nr, sn = e1 / nr;
+    /* G = [cs -sn; sn cs], first column the eigenvector: H <- G^T H G */
+    for (int j = k; j < n; ++j) {
+        double x = H[IDX(k, j, ldh)], y = H[IDX(k + 1, j, ldh)];
+        H[IDX(k, j, ldh)] = cs * x + sn * y;
+        H[IDX(k + 1, j, ldh)] = -sn * x + cs * y;
+    }
+    for (int i = 0; i <= k + 1; ++i) {
+        double x = H[IDX(i, k, ldh)], y = H[IDX(i, k + 1, ldh)];
+        H[IDX(i, k, ldh)] = cs * x + sn * y;
+        H[IDX(i, k + 1, ldh)] = -sn * x + cs * y;
+    }
+    for (int i = 0; i < n; ++i) {
+        double x = Z[IDX(i, k, ldz)], y = Z[IDX(i, k + 1, ldz)];
+        Z[IDX(i, k, ldz)] = cs * x + sn * y;
+        Z[IDX(i, k + 1, ldz)] = -sn * x + cs * y;
+    }
+    H[IDX(k + 1, k, ldh)] = 0.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Real Schur form of a real upper Hessenberg H by implicit double-shift    */
+/* (Francis) QR sweeps: each sweep uses the two eigenvalues of the trailing */
+/* 2x2 block as a conjugate (or real) shift pair, starts from the first     */
+/* column of (H - s1 I)(H - s2 I) and restores the Hessenberg form with     */
+/* 3x3 Householder reflectors.  Deflation as in orc_schur_qr.  Z (in/out)   */
+/* is right-multiplied by every reflector.  Returns 0 or 3.                 */
+/* ------------------------------------------------------------------------ */
+int orc_real_schur_qr(int n, double *H, int ldh, double *Z, int ldz)
+{
+    int hi = n - 1, iter = 0;
+    while (hi >= 0) {
+        int lo = hi;
+        while (lo > 0) {
+            double sub = fabs(H[IDX(lo, lo - 1, ldh)]);
+            double dsum = fabs(H[IDX(lo, lo, ldh)]) + fabs(H[IDX(lo - 1, lo - 1, ldh)]);
+            if (sub <= ORC_EPS * dsum || sub == 0.0) {
+                H[IDX(lo, lo - 1, ldh)] = 0.0;
+                break;
+            }
+            --lo;
+        }
+        if (lo == hi) { --hi; iter = 0; continue; }
+        if (lo == hi - 1) {
+            orc_split_2x2(n, H, ldh, Z, ldz, hi - 1);
+            hi -= 2;
+            iter = 0;
+            continue;
+        }
+        if (++iter > 60) return 3;
+        double s, t;
+        const double h11 = H[IDX(hi - 1, hi - 1, ldh)], h12 = H[IDX(hi - 1, hi, ldh)];
+        const double h21 = H[IDX(hi, hi - 1, ldh)], h22 = H[IDX(hi, hi, ldh)];
+        if (iter % 10 == 0) {
+            /* exceptional shift pair after a run of sweeps without deflation */
+            double w = fabs(h21) + fabs(H[IDX(hi - 1, hi - 2, ldh)]);
+            s = 1.5 * w + h22;
+            t = w * w;
+        } else {
+            s = h11 + h22;             /* s1 + s2 */
+            t = h11 * h22 - h12 * h21; /* s1 s2 */
+        }
+        const double a00 = H[IDX(lo, lo, ldh)], a01 = H[IDX(lo, lo + 1, ldh)];
+        const double a10 = H[IDX(lo + 1, lo, ldh)], a11 = H[IDX(lo + 1, lo + 1, ldh)];
+        double x = a00 * a00 + a01 * a10 - s * a00 + t;
+        double y = a10 * (a00 + a11 - s);
+        double z = a10 * H[IDX(lo + 2, lo + 1, ldh)];
+        for (int k = lo; k <= hi - 2; ++k) {
+            double v[3], beta;
+            orc_house3(3, x, y, z, v, &beta);
+            const int c0 = k > lo ? k - 1 : lo;
+            orc_house_rows(H, ldh, k, 3, c0, n, v, beta);
+            const int r1 = (k + 4 < hi + 1) ? k + 4 : hi + 1;
+            orc_house_cols(H, ldh, k, 3, 0, r1, v, beta);
+            orc_house_cols(Z, ldz, k, 3, 0, n, v, beta);
+            if (k > lo) H[IDX(k + 1, k - 1, ldh)] = H[IDX(k + 2, k - 1, ldh)] = 0.0;
+            x = H[IDX(k + 1, k, ldh)];
+            y = H[IDX(k + 2, k, ldh)];
+            if (k < hi - 2) z = H[IDX(k + 3, k, ldh)];
+        }
+        /* last step: a 2-vector reflector on rows / columns hi-1, hi */
+        double v[3], beta;
+        orc_house3(2, x, y, 0.0, v, &beta);
+        orc_house_rows(H, ldh, hi - 1, 2, hi - 2, n, v, beta);
+        orc_house_cols(H, ldh, hi - 1, 2, 0, hi + 1, v, beta);
+        orc_house_cols(Z, ldz, hi - 1, 2, 0, n, v, beta);
+        H[IDX(hi, hi - 2, ldh)] = 0.0;
+    }
+    /* below the first subdiagonal, and the subdiagonal outside 2x2 blocks,
+     * is zero in exact arithmetic */
+    for (int j = 0; j < n; ++j)
+        for (int i = j + 2; i < n; ++i) H[IDX(i, j, ldh)] = 0.0;
+    return 0;
+}
+
+/* Real Schur decomposition A = Q T Q^T of a real matrix: the Householder   */
+/* Hessenberg reduction (real reflectors: the complex routine on a real     */
+/* matrix keeps every quantity real) and the double-shift sweeps.           */
+int orc_real_schur(int n, const double *A, int lda, double *Q, double *T)
+{
+    size_t nn = (size_t)n * (size_t)n;
+    if (nn == 0) return 0;
+    zc *H = (zc *)calloc(nn, sizeof(zc));
+    zc *Qc = (zc *)calloc(nn, sizeof(zc));
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) H[IDX(i, j, n)] = A[IDX(i, j, lda)];
+    orc_hessenberg(n, H, n, Qc, n);
+    for (size_t e = 0; e < nn; ++e) { T[e] = creal(H[e]); Q[e] = creal(Qc[e]); }
+    for (int j = 0; j < n; ++j)
+        for (int i = j + 2; i < n; ++i) T[IDX(i, j, n)] = 0.0;
+    free(H); free(Qc);
+    return orc_real_schur_qr(n, T, n, Q, n);
+}
+
+/* start of each diagonal block of quasi-triangular T (blk[b] .. blk[b+1]-1) */
+static int orc_blocks(int n, const double *T, int ldt, int *blk)
+{
+    int nb = 0, i = 0;
+    while (i < n) {
+        blk[nb++] = i;
+        i += (i + 1 < n && T[IDX(i + 1, i, ldt)] != 0.0) ? 2 : 1;
+    }
+    blk[nb] = n;
+    return nb;
+}
+
+/* solve the p x q Sylvester equation A Y + Y B = C (p, q <= 2) through its  */
+/* Kronecker form (I (x) A + B^T (x) I) vec(Y) = vec(C), Gaussian           */
+/* elimination with partial pivoting; A (lda), B (ldb), C -> Y (ldc).        */
+static int orc_small_sylv(int p, int q, const double *A, int lda, const double *B, int ldb, double *C, int ldc)
+{
+    const int m = p * q;
+    double K[4][5];
+    for (int c = 0; c < q; ++c)
+        for (int r = 0; r < p; ++r) {
+            const int row = r + c * p;
+            for (int cc = 0; cc < q; ++cc)
+                for (int rr = 0; rr < p; ++rr) {
+                    double v = 0.0;
+                    if (cc == c) v += A[IDX(r, rr, lda)];
+                    if (rr == r) v += B[IDX(cc, c, ldb)];
+                    K[row][rr + cc * p] = v;
+                }
+            K[row][m] = C[IDX(r, c, ldc)];
+        }
+    for (int col = 0; col < m; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < m; ++r)
+            if (fabs(K[r][col]) > fabs(K[piv][col])) piv = r;
+        if (K[piv][col] == 0.0) return 2;
+        if (piv != col)
+            for (int e = 0; e <= m; ++e) { double tmp = K[col][e]; K[col][e] = K[piv][e]; K[piv][e] = tmp; }
+        for (int r = col + 1; r < m; ++r) {
+            const double f = K[r][col] / K[col][col];
+            for (int e = col; e <= m; ++e) K[r][e] -= f * K[col][e];
+        }
+    }
+    double y[4];
+    for (int r = m - 1; r >= 0; --r) {
+        double acc = K[r][m];
+        for (int e = r + 1; e < m; ++e) acc -= K[r][e] * y[e];
+        y[r] = acc / K[r][r];
+    }
+    for (int c = 0; c < q; ++c)
+        for (int r = 0; r < p; ++r) C[IDX(r, c, ldc)] = y[r + c * p];
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* S = T^{1/2} for real quasi-triangular T (Remark 2.1; the recurrence of   */
+/* Eq. (subst) over the diagonal blocks): a 1x1 block t > 0 gives sqrt(t);  */
+/* a 2x2 block with eigenvalues theta +- i mu gives                          */
+/*   S_ii = alpha I + (T_ii - theta I) / (2 alpha),                          */
+/* alpha = Re sqrt(theta + i mu) (the principal root of the pair); block    */
+/* (i, j) then solves S_ii S_ij + S_ij S_jj = T_ij - sum_{i<k<j} S_ik S_kj. */
+/* Returns 0, or 2 for a real eigenvalue <= 0 or a singular block system.   */
+/* ------------------------------------------------------------------------ */
+int orc_qtrisqrt(int n, const double *T, int ldt, double *S, int lds)
+{
+    int *blk = (int *)malloc(sizeof(int) * (size_t)(n + 1));
+    const int nb = orc_blocks(n, T, ldt, blk);
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) S[IDX(i, j, lds)] = 0.0;
+    int st = 0;
+    for (int b = 0; b < nb && !st; ++b) {
+        const int i0 = blk[b], p = blk[b + 1] - blk[b];
+        if (p == 1) {
+            const double t = T[IDX(i0, i0, ldt)];
+            if (t <= 0.0) st = 2;
+            else S[IDX(i0, i0, lds)] = sqrt(t);
+        } else {
+            const double a = T[IDX(i0, i0, ldt)], bb = T[IDX(i0, i0 + 1, ldt)];
+            const double c = T[IDX(i0 + 1, i0, ldt)], d = T[IDX(i0 + 1, i0 + 1, ldt)];
+            const double theta = 0.5 * (a + d);
+            const double mu2 = -(0.25 * (a - d) * (a - d) + bb * c);
+            if (mu2 <= 0.0) { st = 2; break; }
+            const double alpha = creal(orc_csqrt(theta + I * sqrt(mu2)));
+            S[IDX(i0, i0, lds)] = alpha + (a - theta) / (2.0 * alpha);
+            S[IDX(i0, i0 + 1, lds)] = bb / (2.0 * alpha);
+            S[IDX(i0 + 1, i0, lds)] = c / (2.0 * alpha);
+            S[IDX(i0 + 1, i0 + 1, lds)] = alpha + (d - theta) / (2.0 * alpha);
+        }
+    }
+    for (int dist = 1; dist < nb && !st; ++dist)
+        for (int bi = 0; bi + dist < nb && !st; ++bi) {
+            const int bj = bi + dist;
+            const int i0 = blk[bi], p = blk[bi + 1] - i0, j0 = blk[bj], q = blk[bj + 1] - j0;
+            double C[4];
+            for (int c = 0; c < q; ++c)
+                for (int r = 0; r < p; ++r) {
+                    double acc = T[IDX(i0 + r, j0 + c, ldt)];
+                    for (int k = blk[bi + 1]; k < j0; ++k) acc -= S[IDX(i0 + r, k, lds)] * S[IDX(k, j0 + c, lds)];
+                    C[r + c * p] = acc;
+                }
+            st = orc_small_sylv(p, q, &S[IDX(i0, i0, lds)], lds, &S[IDX(j0, j0, lds)], lds, C, p);
+            for (int c = 0; c < q; ++c)
+                for (int r = 0; r < p; ++r) S[IDX(i0 + r, j0 + c, lds)] = C[r + c * p];
+        }
+    free(blk);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* S Y + Y St = C for real quasi-triangular S (m x m) and St (n x n): block */
+/* Bartels-Stewart over their diagonal blocks, block rows bottom-up and     */
+/* block columns left to right,                                              */
+/*   S_II Y_IJ + Y_IJ St_JJ = C_IJ - sum_{K>I} S_IK Y_KJ - sum_{L<J} Y_IL St_LJ. */
+/* C (ldc) is overwritten by Y.  Returns 0 or 2 (singular block system).     */
+/* ------------------------------------------------------------------------ */
+int orc_qrtrsyl(int m, int n, const double *S, int lds, const double *St, int ldst, double *C, int ldc)
+{
+    int *bm = (int *)malloc(sizeof(int) * (size_t)(m + 1));
+    int *bn = (int *)malloc(sizeof(int) * (size_t)(n + 1));
+    const int nbm = orc_blocks(m, S, lds, bm), nbn = orc_blocks(n, St, ldst, bn);
+    int st = 0;
+    for (int J = 0; J < nbn && !st; ++J)
+        for (int Ib = nbm - 1; Ib >= 0 && !st; --Ib) {
+            const int i0 = bm[Ib], p = bm[Ib + 1] - i0, j0 = bn[J], q = bn[J + 1] - j0;
+            double R[4];
+            for (int c = 0; c < q; ++c)
+                for (int r = 0; r < p; ++r) {
+                    double acc = C[IDX(i0 + r, j0 + c, ldc)];
+                    for (int k = bm[Ib + 1]; k < m; ++k) acc -= S[IDX(i0 + r, k, lds)] * C[IDX(k, j0 + c, ldc)];
+                    for (int l = 0; l < j0; ++l) acc -= C[IDX(i0 + r, l, ldc)] * St[IDX(l, j0 + c, ldst)];
+                    R[r + c * p] = acc;
+                }
+            st = orc_small_sylv(p, q, &S[IDX(i0, i0, lds)], lds, &St[IDX(j0, j0, ldst)], ldst, R, p);
+            for (int c = 0; c < q; ++c)
+                for (int r = 0; r < p; ++r) C[IDX(i0 + r, j0 + c, ldc)] = R[r + c * p];
+        }
+    free(bm); free(bn);
+    return st;
+}

@@ -100,6 +100,28 @@ def random_upper_rhp(n: int, seed: int, offdiag_scale: float = 1.0,
     return np.asfortranarray(S)
 
 
+def random_quasi_upper(n: int, seed: int, pair_frac: float = 0.5) -> np.ndarray:
+    """Real quasi-upper-triangular matrix (a stand-in for a real Schur factor):
+    diagonal blocks 1x1 with entries in [0.5, 2], or 2x2 [[t, m r], [-m / r, t]]
+    with t in [0.5, 2], m in [0.2, 1], r in [0.5, 2] (eigenvalues t +- i m, in
+    the right half plane), about pair_frac of the rows in 2x2 blocks; N(0,1)/sqrt(n)
+    above the blocks."""
+    g = rng(seed)
+    T = np.triu(g.standard_normal((n, n)) / np.sqrt(max(n, 1)), 1)
+    i = 0
+    while i < n:
+        if i + 1 < n and g.uniform() < pair_frac:
+            t, m, r = g.uniform(0.5, 2.0), g.uniform(0.2, 1.0), g.uniform(0.5, 2.0)
+            T[i, i] = T[i + 1, i + 1] = t
+            T[i, i + 1] = m * r
+            T[i + 1, i] = -m / r
+            i += 2
+        else:
+            T[i, i] = g.uniform(0.5, 2.0)
+            i += 1
+    return np.asfortranarray(T)
+
+
 def random_unitary(n: int, seed: int) -> np.ndarray:
     g = rng(seed)
     Z = g.standard_normal((n, n)) + 1j * g.standard_normal((n, n))

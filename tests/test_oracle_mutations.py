@@ -47,6 +47,10 @@ MUTATIONS = [
     ("ccbrt_other_branch", "double th = carg(z) / 3.0;", "double th = (carg(z) + 6.283185307179586) / 3.0;"),
     ("rtrsyl3_w_without_new_entry", "W[IDX(i, j, m)] = wp + y * St[IDX(j, j, ldst)];", "W[IDX(i, j, m)] = wp;"),
     ("zsqrtm_conjugated_result", "X[IDX(i, j, ldx)] = P[IDX(i, j, n)];", "X[IDX(i, j, ldx)] = conj(P[IDX(i, j, n)]);"),
+    ("qtrisqrt_2x2_sign", "S[IDX(i0, i0, lds)] = alpha + (a - theta) / (2.0 * alpha);",
+     "S[IDX(i0, i0, lds)] = alpha - (a - theta) / (2.0 * alpha);"),
+    ("qrtrsyl_drop_right_coupling", "for (int l = 0; l < j0; ++l) acc -= C[IDX(i0 + r, l, ldc)] * St[IDX(l, j0 + c, ldst)];", ";"),
+    ("real_schur_skip_z", "orc_house_cols(Z, ldz, k, 3, 0, n, v, beta);", ";"),
     ("rtrsyl3_transposed_vt", "for (int l = 0; l < j; ++l) acc -= C[IDX(i, l, ldc)] * Vt[IDX(l, j, ldvt)];",
      "for (int l = 0; l < j; ++l) acc -= C[IDX(i, l, ldc)] * Vt[IDX(j, l, ldvt)];"),
 ]
@@ -78,6 +82,18 @@ def _checks(orc):
         return (np.linalg.norm(X @ X - Ac) <= 20 * 16 * U * np.linalg.norm(Ac)
                 and np.all(np.linalg.eigvals(X).real > 0))
     run("zsqrtm_residual", zsqrtm_residual)
+
+    def real_schur_route():
+        Ar = synth.shifted_gaussian(18, 0.5, seed=44)
+        Q, T = orc.real_schur(Ar)
+        ok = np.linalg.norm(Q @ T @ Q.T - Ar) <= 2000 * U * np.linalg.norm(Ar)
+        Ap = synth.shifted_gaussian(18, 3.0, seed=45)
+        ok = ok and orc.rel_err(orc.sqrtm_real_schur(Ap), orc.sqrtm_schur(Ap)) <= 1e-12
+        Tq = synth.random_quasi_upper(9, seed=46)
+        C = synth.gaussian((9, 9), seed=47)
+        Y = orc.qrtrsyl(Tq, Tq, C)
+        return ok and np.linalg.norm(Tq @ Y + Y @ Tq - C) <= 1e3 * U * np.linalg.norm(C)
+    run("real_schur_route", real_schur_route)
 
     def schur_similarity():
         Q, T = orc.schur(A)

@@ -527,3 +527,84 @@ def test_refine_complex_contracts(orc):
     its = orc.refine_complex(A, Q, S, X0, 3)
     errs = [orc.rel_err(Xk, X) for Xk in its]
     assert errs[1] <= 1e-3 * errs[0] and errs[3] <= 1e-14
+
+
+# --------------------------------------------------------------------------
+# real arithmetic for real A (Remark 2.1): real Schur form, quasi-triangular
+# square root and Sylvester solve
+# --------------------------------------------------------------------------
+def _blocks(T):
+    n = T.shape[0]
+    out, i = [], 0
+    while i < n:
+        p = 2 if i + 1 < n and T[i + 1, i] != 0.0 else 1
+        out.append((i, p))
+        i += p
+    return out
+
+
+@pytest.mark.parametrize("n,shift", [(1, 0.0), (2, 0.0), (3, 0.5), (9, 0.0), (40, 0.5), (120, 0.3)])
+def test_real_schur_invariants(orc, n, shift):
+    A = synth.shifted_gaussian(n, shift, seed=900 + n)
+    Q, T = orc.real_schur(A)
+    assert np.linalg.norm(Q @ T @ Q.T - A) <= 200 * n * U * np.linalg.norm(A)
+    assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= 200 * n * U
+    assert np.all(np.tril(T, -2) == 0)
+    for i, p in _blocks(T):
+        if p == 2:  # a 2x2 block holds a complex conjugate pair
+            a, b, c, d = T[i, i], T[i, i + 1], T[i + 1, i], T[i + 1, i + 1]
+            assert 0.25 * (a - d) ** 2 + b * c < 0
+    ev = np.sort_complex(np.linalg.eigvals(T))
+    assert np.allclose(ev, np.sort_complex(np.linalg.eigvals(A)), atol=1e-10 * np.linalg.norm(A))
+
+
+def test_qtrisqrt_2x2_closed_form(orc):
+    # [[t, m], [-m, t]] has eigenvalues t +- i m; its principal square root is
+    # [[a, m/(2a)], [-m/(2a), a]] with a = Re sqrt(t + i m)
+    for t, m in [(1.0, 1.0), (0.3, 2.0), (-0.5, 1.0), (4.0, 0.01)]:
+        a = cmath.sqrt(complex(t, m)).real
+        S = orc.qtrisqrt(np.array([[t, m], [-m, t]]))
+        assert np.allclose(S, [[a, m / (2 * a)], [-m / (2 * a), a]], rtol=4 * U, atol=4 * U)
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 30, 90])
+def test_qtrisqrt_squares_back_and_principal(orc, n):
+    T = synth.random_quasi_upper(n, seed=910 + n)
+    S = orc.qtrisqrt(T)
+    assert np.linalg.norm(S @ S - T) <= 50 * n * U * np.linalg.norm(T)
+    assert np.all(np.linalg.eigvals(S).real > 0)
+    # same block structure
+    assert np.all(np.tril(S, -2) == 0)
+    assert np.all((np.diag(S, -1) != 0) == (np.diag(T, -1) != 0))
+
+
+def test_real_method_matches_complex_method(orc):
+    A = synth.shifted_gaussian(60, 3.0, seed=920)
+    assert orc.rel_err(orc.sqrtm_real_schur(A), orc.sqrtm_schur(A)) <= 1e-13
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (4, 3), (9, 12), (25, 20)])
+def test_qrtrsyl_matches_kronecker(orc, m, n):
+    S = synth.random_quasi_upper(m, seed=930 + m)
+    St = synth.random_quasi_upper(n, seed=940 + n)
+    C = synth.gaussian((m, n), seed=950 + m * n)
+    Y = orc.qrtrsyl(S, St, C)
+    K = np.kron(np.eye(n), S) + np.kron(St.T, np.eye(m))
+    Yk = np.linalg.solve(K, C.reshape(-1, order="F")).reshape((m, n), order="F")
+    assert np.linalg.norm(Y - Yk) <= 1e3 * U * np.linalg.norm(Yk)
+
+
+def test_qtrisqrt_negative_real_eigenvalue_status(orc):
+    T = np.array([[1.0, 2.0, 0.5], [0.0, -4.0, 1.0], [0.0, 0.0, 9.0]])
+    with pytest.raises(orc.OracleError) as e:
+        orc.qtrisqrt(T)
+    assert e.value.code == 2
+
+
+def test_refine_real_contracts(orc):
+    n = 30
+    A = synth.shifted_gaussian(n, 3.0, seed=960)
+    X, Q, T, S = orc.sqrtm_real_schur(A, return_factors=True)
+    X0 = X + 1e-6 * synth.gaussian((n, n), seed=961)
+    errs = [orc.rel_err(Xk, X) for Xk in orc.refine_real(A, Q, S, X0, 3)]
+    assert errs[1] <= 1e-3 * errs[0] and errs[3] <= 1e-14
