@@ -69,6 +69,24 @@ SQRTM_API int sqrtm_step_tricbrt(sqrtm_handle_t h, const void *dT, void *dS, voi
 SQRTM_API int sqrtm_step_trisqrt_rec(sqrtm_handle_t h, const void *dT, void *dS, int64_t n, int blks, int cutoff,
                                      int fp64);
 
+/* Real quasi-triangular square root (Remark 2.1): S = T^{1/2} for real
+ * quasi-upper-triangular T (1x1 diagonal blocks for real eigenvalues, 2x2
+ * blocks for complex conjugate pairs, a 2x2 block marked by a nonzero
+ * subdiagonal entry).  A 1x1 block gives sqrt(t); a 2x2 block with
+ * eigenvalues theta +- i mu gives alpha I + (T_ii - theta I) / (2 alpha),
+ * alpha = Re sqrt(theta + i mu); block (i, j) then solves S_ii S_ij +
+ * S_ij S_jj = T_ij - sum_k S_ik S_kj, one block diagonal per launch.  dT,
+ * dS: real n x n (ld n), float (fp64 = 0) or double.  Returns 0, or 2 for a
+ * real eigenvalue <= 0 or a singular block equation. */
+SQRTM_API int sqrtm_step_qtrisqrt(sqrtm_handle_t h, const void *dT, void *dS, int64_t n, int fp64);
+
+/* S Y + Y St = C for real quasi-upper-triangular S (m x m, ld m) and St
+ * (nn x nn, ld nn), never cutting a 2x2 block: block anti-diagonals of the
+ * block grid in order, each block from its p x q Sylvester equation
+ * (p, q <= 2).  dC (m x nn, ld m) is overwritten by Y.  Returns 0 or 2. */
+SQRTM_API int sqrtm_step_qrtrsyl(sqrtm_handle_t h, const void *dS, int64_t m, const void *dSt, int64_t nn, void *dC,
+                                 int fp64);
+
 /* X_0 = Re(Q S Q^H) (Algorithm 2, step 3), computed in the storage
  * precision of Q and S, rounded to that precision and written widened to
  * FP64 into dX (ldx), times 2^e (undoing the scaling). */

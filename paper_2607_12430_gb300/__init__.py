@@ -107,6 +107,8 @@ _SIGS = {
     "sqrtm_step_syevd": ([_P, _P, _P, _P, _L, _I], _I),
     "sqrtm_step_trisqrt": ([_P, _P, _P, _L, _I, _I], _I),
     "sqrtm_step_trisqrt_rec": ([_P, _P, _P, _L, _I, _I, _I], _I),
+    "sqrtm_step_qtrisqrt": ([_P, _P, _P, _L, _I], _I),
+    "sqrtm_step_qrtrsyl": ([_P, _P, _L, _P, _L, _P, _I], _I),
     "sqrtm_step_tricbrt": ([_P, _P, _P, _P, _L, _I, _I], _I),
     "sqrtm_step_rtrsyl3": ([_P, _P, _P, _P, _L, _I, _I], _I),
     "sqrtm_step_form_x0": ([_P, _P, _P, _L, _I, _P, _L, _I], _I),
@@ -477,6 +479,21 @@ def step_trisqrt_rec(T_cm, n, blks=32, cutoff=256, fp64=False):
     S = torch.empty_like(T_cm)
     _rc(lib().sqrtm_step_trisqrt_rec(handle(), _ptr(T_cm), _ptr(S), n, blks, cutoff, int(fp64)), "trisqrt_rec")
     return S
+
+
+def step_qtrisqrt(T_cm, n, fp64=False):
+    """Real quasi-triangular square root: T_cm real (float32 / float64)
+    column-major; returns S_cm."""
+    S = torch.empty_like(T_cm)
+    _rc(lib().sqrtm_step_qtrisqrt(handle(), _ptr(T_cm), _ptr(S), n, int(fp64)), "qtrisqrt")
+    return S
+
+
+def step_qrtrsyl(S_cm, m, St_cm, nn, C_cm, fp64=False):
+    """In place: C_cm (real, m x nn column-major) becomes Y of
+    S Y + Y St = C with real quasi-triangular S, St."""
+    _rc(lib().sqrtm_step_qrtrsyl(handle(), _ptr(S_cm), m, _ptr(St_cm), nn, _ptr(C_cm), int(fp64)), "qrtrsyl")
+    return C_cm
 
 
 def step_tricbrt(T_cm, n, blks=32, fp64=False):

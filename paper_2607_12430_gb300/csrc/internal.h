@@ -213,6 +213,20 @@ template <class R>
 cudaError_t launch_rtrsyl(const cplx<R> *S, int lds, int m, const cplx<R> *St, int ldst, int nn,
                           cplx<R> *C, int ldc, int blks, int *d_status, cudaStream_t s);
 
+// ---- real quasi-triangular factors (quasi.cu; Remark 2.1) ----
+// S = T^{1/2} for real quasi-upper-triangular T (n x n, ld): d_blk n + 1
+// ints and d_nb 1 int of device scratch; synchronizes s once (the number of
+// diagonal blocks sets the launch count).  status 2: a real eigenvalue <= 0
+// or a singular block equation.
+template <class R>
+cudaError_t launch_qtrisqrt(const R *T, int ldt, R *S, int lds, int n, int *d_blk, int *d_nb, int *d_status,
+                            cudaStream_t s);
+// S Y + Y St = C (C overwritten by Y) for real quasi-upper-triangular S
+// (m x m) and St (nn x nn): scratch d_bm m + 1, d_bn nn + 1, d_nbs 2 ints.
+template <class R>
+cudaError_t launch_qrtrsyl(const R *S, int lds, int m, const R *St, int ldst, int nn, R *C, int ldc, int *d_bm,
+                           int *d_bn, int *d_nbs, int *d_status, cudaStream_t s);
+
 // ---- dense products (gemm.cu) ----
 enum OpT { OP_N = 0, OP_H = 1 };
 enum Epi { EPI_STORE = 0, EPI_REAL_TO_F64 = 1, EPI_REAL_ADD_F64 = 2, EPI_REAL_ADD_F64_T = 3, EPI_CPLX_TO_F64 = 4,

@@ -164,6 +164,46 @@ extern "C" int sqrtm_step_trisqrt_rec(sqrtm_handle_t h, const void *dT, void *dS
     return st;
 }
 
+extern "C" int sqrtm_step_qtrisqrt(sqrtm_handle_t h, const void *dT, void *dS, int64_t n, int fp64)
+{
+    if (!h) return -1;
+    if (n < 0) return -4;
+    if (n == 0) return 0;
+    StepScratch ss; void *ex;
+    if (int rc = step_scratch(h, n, (size_t)(n + 8) * sizeof(int), &ss, &ex)) return rc;
+    int *blk = (int *)ex;
+    cudaError_t err = fp64 ? launch_qtrisqrt<double>((const double *)dT, (int)n, (double *)dS, (int)n, (int)n, blk,
+                                                     ss.iscal + 2, ss.iscal + 1, h->stream)
+                           : launch_qtrisqrt<float>((const float *)dT, (int)n, (float *)dS, (int)n, (int)n, blk,
+                                                    ss.iscal + 2, ss.iscal + 1, h->stream);
+    if (err) return 7;
+    int st = 0;
+    if (fetch(h, &st, ss.iscal + 1, sizeof(int))) return 7;
+    return st;
+}
+
+extern "C" int sqrtm_step_qrtrsyl(sqrtm_handle_t h, const void *dS, int64_t m, const void *dSt, int64_t nn, void *dC,
+                                  int fp64)
+{
+    if (!h) return -1;
+    if (m < 0) return -3;
+    if (nn < 0) return -5;
+    if (m == 0 || nn == 0) return 0;
+    StepScratch ss; void *ex;
+    if (int rc = step_scratch(h, std::max(m, nn), (size_t)(m + nn + 16) * sizeof(int), &ss, &ex)) return rc;
+    int *bm = (int *)ex, *bn = bm + m + 8;
+    cudaError_t err = fp64 ? launch_qrtrsyl<double>((const double *)dS, (int)m, (int)m, (const double *)dSt, (int)nn,
+                                                    (int)nn, (double *)dC, (int)m, bm, bn, ss.iscal + 2, ss.iscal + 1,
+                                                    h->stream)
+                           : launch_qrtrsyl<float>((const float *)dS, (int)m, (int)m, (const float *)dSt, (int)nn,
+                                                   (int)nn, (float *)dC, (int)m, bm, bn, ss.iscal + 2, ss.iscal + 1,
+                                                   h->stream);
+    if (err) return 7;
+    int st = 0;
+    if (fetch(h, &st, ss.iscal + 1, sizeof(int))) return 7;
+    return st;
+}
+
 template <class R>
 static int form_x0(sqrtm_handle_t h, const cplx<R> *Q, const cplx<R> *S, int64_t n, int e,
                    double *dX, int64_t ldx)
