@@ -239,7 +239,16 @@ SQRTM_API int sqrtm_backward(sqrtm_handle_t handle, const double *dGbar, int64_t
 /* Batched mixed-precision square roots of independent matrices of varying
  * sizes.  dA, dX: HOST arrays of `batch` device pointers; n, lda, ldx: HOST
  * arrays of sizes.  status: HOST array of `batch` ints receiving each
- * matrix's code.  opts may be NULL.  Returns the first nonzero code, else 0. */
+ * matrix's code.  opts may be NULL.  Returns the first nonzero code, else 0.
+ * Matrices of the sizes the tuning table marks `batched` (without a table:
+ * n <= 256; the environment variable SQRTM_BATCH_MAXN, if set, is the size
+ * limit instead) go through one batched general path: every stage of
+ * Algorithm 2 is one launch over all of them, the convergence test runs per
+ * matrix on the device and each refinement step is replayed from a CUDA
+ * graph until no matrix is active (a symmetric matrix takes Algorithm 2 there
+ * too).  The others, and every matrix when opts->kind is SQRTM_KIND_SPD, are
+ * solved by per-matrix calls on up to 12 worker streams, concurrently with
+ * the batched path. */
 SQRTM_API int sqrtm_mixed_batched(sqrtm_handle_t handle, int batch, const double *const *dA,
                         const int64_t *n, const int64_t *lda, double tol,
                         double *const *dX, const int64_t *ldx, const sqrtm_opts *opts,
