@@ -55,7 +55,14 @@ typedef struct sqrtm_handle_s *sqrtm_handle_t;
 
 /* Matrix kind: AUTO takes the symmetric positive definite path (Algorithm 3)
  * when A is bitwise symmetric, the general path (Algorithm 2) otherwise. */
-enum { SQRTM_KIND_AUTO = 0, SQRTM_KIND_GENERAL = 1, SQRTM_KIND_SPD = 2 };
+enum { SQRTM_KIND_AUTO = 0, SQRTM_KIND_GENERAL = 1, SQRTM_KIND_SPD = 2, SQRTM_KIND_REAL = 3 };
+/* SQRTM_KIND_REAL (never chosen by AUTO): Algorithm 2 in real arithmetic
+ * (Remark 2.1) -- real Schur form A = Q T Q^T with T quasi-triangular (2x2
+ * blocks for complex conjugate pairs, never cut), the quasi-triangular
+ * square root, and corrections from quasi-triangular Sylvester solves with
+ * real transforms.  Its Schur stage is a single-CTA double-shift iteration
+ * (n <= 8192), much slower than the complex multi-bulge stage of
+ * SQRTM_KIND_GENERAL for large n. */
 
 /* Precision options (bit flags).
  * Low-precision dense products (transforms of Algorithm 2/3 steps 3, 8 and

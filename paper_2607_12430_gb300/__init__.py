@@ -29,7 +29,7 @@ STATUS = {
     7: "CUDA error", 8: "no saved factors",
 }
 
-KIND_AUTO, KIND_GENERAL, KIND_SPD = 0, 1, 2
+KIND_AUTO, KIND_GENERAL, KIND_SPD, KIND_REAL = 0, 1, 2, 3
 PREC_AUTO, PREC_FP32, PREC_TF32X3, PREC_RESID_FP64 = -1, 0, 1, 2
 MAX_HISTORY = 64
 MAX_TUNE = 32
@@ -108,6 +108,7 @@ _SIGS = {
     "sqrtm_step_trisqrt": ([_P, _P, _P, _L, _I, _I], _I),
     "sqrtm_step_trisqrt_rec": ([_P, _P, _P, _L, _I, _I, _I], _I),
     "sqrtm_step_qtrisqrt": ([_P, _P, _P, _L, _I], _I),
+    "sqrtm_step_real_schur": ([_P, _P, _P, _L, _I], _I),
     "sqrtm_step_qrtrsyl": ([_P, _P, _L, _P, _L, _P, _I], _I),
     "sqrtm_step_tricbrt": ([_P, _P, _P, _P, _L, _I, _I], _I),
     "sqrtm_step_rtrsyl3": ([_P, _P, _P, _P, _L, _I, _I], _I),
@@ -479,6 +480,14 @@ def step_trisqrt_rec(T_cm, n, blks=32, cutoff=256, fp64=False):
     S = torch.empty_like(T_cm)
     _rc(lib().sqrtm_step_trisqrt_rec(handle(), _ptr(T_cm), _ptr(S), n, blks, cutoff, int(fp64)), "trisqrt_rec")
     return S
+
+
+def step_real_schur(A_cm, n, fp64=False):
+    """In place: A_cm (real, column-major) becomes the quasi-triangular T;
+    returns Q_cm with A = Q T Q^T."""
+    Q = torch.empty_like(A_cm)
+    _rc(lib().sqrtm_step_real_schur(handle(), _ptr(A_cm), _ptr(Q), n, int(fp64)), "real_schur")
+    return Q
 
 
 def step_qtrisqrt(T_cm, n, fp64=False):

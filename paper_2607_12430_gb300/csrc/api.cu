@@ -495,6 +495,116 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     return status;
 }
 
+// ---------------------------------------------------------------------------
+// the real variant of Algorithm 2 (Remark 2.1) in storage precision R: real
+// Schur form, quasi-triangular square root and Sylvester solves, real
+// transforms; refine = false gives the plain real Schur method
+// ---------------------------------------------------------------------------
+template <class R>
+static int real_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, double tol, double *dX,
+                     int64_t ldx, const sqrtm_opts &o, sqrtm_info *info, bool refine)
+{
+    if (n > 8192) {
+        note_error(h, "SQRTM_KIND_REAL: n > 8192", __LINE__, 7);
+        return 7;
+    }
+    cudaStream_t s = h->stream;
+    const size_t nn = (size_t)n * (size_t)n;
+    size_t wbytes = scalars_bytes(n) + 5 * Carve::round(nn * sizeof(R)) + Carve::round(nn * sizeof(float)) +
+                    Carve::round((size_t)(2 * n + 64) * sizeof(int)) + 4096;
+    if (ensure(h->ws, wbytes, h)) return 7;
+    Carve cw(h->ws.p);
+    Scalars sc = carve_scalars(cw, n);
+    R *T = cw.take<R>(nn);
+    R *Q = cw.take<R>(nn);
+    R *S = cw.take<R>(nn);
+    R *W = cw.take<R>(nn);
+    R *Rt = cw.take<R>(nn);
+    float *Rhat = cw.take<float>(nn);
+    int *bscr = cw.take<int>(2 * n + 64);  // block starts of S (n + 1), of the second operand (n + 1), counts (2)
+    h->fact_n = -1;
+    SQM_CU(cudaMemsetAsync(sc.e, 0, 16 * sizeof(int), s));
+    SQM_CU(cudaEventRecord(h->ev[0], s));
+    SQM_CU(launch_norm_scale(dA, n, lda, sc.partials, (int)std::min<int64_t>(n, 1024), sc.norm, sc.e, s));
+    SQM_CU(launch_cast_scaled_real<R>(dA, n, lda, sc.e, T, n, s));
+    double norm_a = 0.0;
+    int e = 0;
+    if (int rc = read_scalars(h, sc, &norm_a, nullptr, &e, nullptr, nullptr)) return rc;
+    if (info) { info->norm_a = norm_a; info->scale_exponent = e; info->kind_used = SQRTM_KIND_REAL; }
+    if (!isfinite(norm_a)) return 5;
+    if (norm_a == 0.0) return 2;
+    SQM_CU(launch_real_schur<R>(T, Q, (int)n, sc.st_schur, sc.st_schur + 3, s));
+    SQM_CU(cudaEventRecord(h->ev[1], s));
+    SQM_CU(launch_qtrisqrt<R>(T, (int)n, S, (int)n, (int)n, bscr, bscr + 2 * n + 8, sc.st_solve, s));
+    // X_0 = 2^e Q S Q^T, the product rounded to R
+    SQM_CU(launch_rgemm<R>(0, 0, (int)n, (int)n, (int)n, Q, (int)n, S, (int)n, RG_STORE, W, (int)n, nullptr, nullptr, 0,
+                           0.0, s));
+    SQM_CU(cudaMemset2DAsync(dX, (size_t)ldx * sizeof(double), 0, (size_t)n * sizeof(double), (size_t)n, s));
+    SQM_CU(launch_rgemm<R>(0, 1, (int)n, (int)n, (int)n, W, (int)n, Q, (int)n, RG_ADD_F64, nullptr, 0, nullptr, dX, ldx,
+                           ldexp(1.0, e), s));
+    SQM_CU(cudaEventRecord(h->ev[2], s));
+    int st_schur = 0, st_solve = 0;
+    if (int rc = read_scalars(h, sc, nullptr, nullptr, nullptr, &st_schur, &st_solve)) return rc;
+    if (info) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]); info->ms_schur = ms;
+        cudaEventElapsedTime(&ms, h->ev[1], h->ev[2]); info->ms_trisqrt = ms;
+        int cnt = 0;
+        SQM_CU(cudaMemcpy(&cnt, sc.st_schur + 3, sizeof(int), cudaMemcpyDeviceToHost));
+        info->schur_sweeps = cnt;
+    }
+    if (st_schur) return st_schur;
+    if (st_solve) return st_solve;
+    if (!refine) return 0;
+    if (sizeof(R) != sizeof(float)) return 7;  // the corrections take the FP32 residual
+
+    const double norm_as = ldexp(norm_a, -2 * e);
+    const bool fixed = o.steps >= 0;
+    const int max_corr = fixed ? o.steps : o.maxit + 1;
+    int status = 0, applied = 0, grew = 0;
+    double prev = INFINITY;
+    for (int k = 0;; ++k) {
+        if (k >= max_corr && fixed) break;
+        int np = 0;
+        SQM_CU(launch_residual_f64(dA, lda, dX, ldx, (int)n, e, Rhat, (int)n, sc.partials, &np, s));
+        SQM_CU(launch_sum_partials(sc.partials, np, sc.rnorm, s));
+        if (!fixed) {
+            double rn = 0.0;
+            if (int rc = read_scalars(h, sc, nullptr, &rn, nullptr, nullptr, nullptr)) return rc;
+            const double rel = rn / norm_as;
+            if (info && info->history_len < SQRTM_MAX_HISTORY) info->history[info->history_len++] = rel;
+            if (!isfinite(rel)) { status = 4; break; }
+            if (rel <= tol) { status = 0; break; }
+            if (k >= max_corr) { status = 1; break; }
+            grew = (rn > prev) ? grew + 1 : 0;
+            if (grew >= 2) { status = 4; break; }
+            prev = rn;
+        }
+        // R~ = Q^T Rhat Q; S Y + Y S = R~ (quasi-triangular); X += 2^e Q Y Q^T
+        const float *Rh = Rhat;
+        SQM_CU(launch_rgemm<R>(0, 0, (int)n, (int)n, (int)n, (const R *)Rh, (int)n, Q, (int)n, RG_STORE, W, (int)n,
+                               nullptr, nullptr, 0, 0.0, s));
+        SQM_CU(launch_rgemm<R>(1, 0, (int)n, (int)n, (int)n, Q, (int)n, W, (int)n, RG_STORE, Rt, (int)n, nullptr,
+                               nullptr, 0, 0.0, s));
+        SQM_CU(launch_qrtrsyl<R>(S, (int)n, (int)n, S, (int)n, (int)n, Rt, (int)n, bscr, bscr + n + 4,
+                                 bscr + 2 * n + 8, sc.st_solve, s));
+        SQM_CU(launch_rgemm<R>(0, 0, (int)n, (int)n, (int)n, Q, (int)n, Rt, (int)n, RG_STORE, W, (int)n, nullptr,
+                               nullptr, 0, 0.0, s));
+        SQM_CU(launch_rgemm<R>(0, 1, (int)n, (int)n, (int)n, W, (int)n, Q, (int)n, RG_ADD_F64, nullptr, 0, nullptr, dX,
+                               ldx, ldexp(1.0, e), s));
+        ++applied;
+    }
+    SQM_CU(cudaEventRecord(h->ev[3], s));
+    if (int rc = read_scalars(h, sc, nullptr, nullptr, nullptr, nullptr, &st_solve)) return rc;
+    if (info) {
+        info->iterations = applied;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]); info->ms_refine = ms;
+    }
+    if (st_solve) return st_solve;
+    return status;
+}
+
 static int resolve_opts(const sqrtm_opts *opts, double tol, sqrtm_opts *o)
 {
     sqrtm_default_opts(o);
@@ -527,6 +637,7 @@ extern "C" int sqrtm_mixed(sqrtm_handle_t h, const double *dA, int64_t n, int64_
     }
     int rc;
     if (kind == SQRTM_KIND_SPD && spd_enabled()) rc = spd_path(h, dA, n, lda, o.tol, dX, ldx, o, info);
+    else if (kind == SQRTM_KIND_REAL) rc = real_path<float>(h, dA, n, lda, o.tol, dX, ldx, o, info, true);
     else rc = general_path<float>(h, dA, n, lda, o.tol, dX, ldx, o, info, true);
     if (info) info->status = rc;
     return rc;
@@ -554,6 +665,7 @@ extern "C" int sqrtm_schur_fp64(sqrtm_handle_t h, const double *dA, int64_t n, i
     }
     int rc;
     if (kind == SQRTM_KIND_SPD && spd_enabled()) rc = spd_schur_fp64(h, dA, n, lda, dX, ldx, o, info);
+    else if (kind == SQRTM_KIND_REAL) rc = real_path<double>(h, dA, n, lda, 0.0, dX, ldx, o, info, false);
     else rc = general_path<double>(h, dA, n, lda, 0.0, dX, ldx, o, info, false);
     h->fact_n = -1;  // the FP64 method keeps no low-precision factors
     if (info) info->status = rc;

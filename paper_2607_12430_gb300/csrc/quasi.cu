@@ -165,6 +165,284 @@ qrtrsyl_wave_kernel(const R *__restrict__ S, int lds, const int *__restrict__ bm
         for (int r = 0; r < p; ++r) C[(i0 + r) + (int64_t)(j0 + c) * ldc] = y[r + c * p];
 }
 
+// ---------------------------------------------------------------------------
+// Real Schur form A = Q T Q^T of a real matrix in one CTA (Remark 2.1):
+// Householder Hessenberg reduction, then implicit double-shift (Francis)
+// sweeps with 3x3 reflectors, the shift pair being the eigenvalues of the
+// trailing 2x2 block of the active block (an exceptional pair every 10
+// sweeps without deflation); a deflated 2x2 block with real eigenvalues is
+// split by a rotation through an eigenvector.  Thread 0 takes the scalar
+// decisions, all threads apply each reflector (rows: one thread per column;
+// columns and Q: one thread per row).  Bounded: 60 sweeps per deflation,
+// then status 3.  T (in: A_s, out: quasi-triangular) and Q (out) are n x n
+// with ld n in global memory (the matrix of one call stays in L2).
+// ---------------------------------------------------------------------------
+static constexpr int kRsThreads = 1024;
+
+template <class R>
+__device__ __forceinline__ R block_sum_rs(R v, R *red)
+{
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    R t = R(0);
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    return t;  // valid in thread 0
+}
+
+// Householder vector of a 3- (or 2-) vector: P = I - beta v v^T, v0 = 1,
+// P x = (||x||, 0, 0)
+template <class R>
+__device__ void house3_dev(int len, R x, R y, R z, R v[3], R &beta)
+{
+    const R sig = y * y + (len == 3 ? z * z : R(0));
+    v[0] = R(1); v[1] = y; v[2] = len == 3 ? z : R(0);
+    if (sig == R(0)) { beta = R(0); return; }
+    const R mu = sqrt(x * x + sig);
+    const R v0 = x <= R(0) ? x - mu : -sig / (x + mu);
+    beta = R(2) * v0 * v0 / (sig + v0 * v0);
+    v[1] = y / v0;
+    v[2] = len == 3 ? z / v0 : R(0);
+}
+
+template <class R>
+__global__ void __launch_bounds__(kRsThreads, 1)
+real_schur_kernel(R *__restrict__ T, R *__restrict__ Q, int n, int *status, int *counters)
+{
+    extern __shared__ unsigned char smraw[];
+    R *vb = reinterpret_cast<R *>(smraw);  // n: Householder vector of the reduction
+    __shared__ R red[kRsThreads / 32];
+    __shared__ R s_v[3], s_beta, s_cs, s_sn;
+    __shared__ int s_act, s_k, s_lo, s_hi, s_len, s_c0, s_r1;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const R eps = num<R>::eps;
+    for (int e = tid; e < n * n; e += nt) Q[e] = (e % n == e / n) ? R(1) : R(0);
+    __syncthreads();
+    // ---- Hessenberg reduction: column k, reflector on rows k+1 .. n-1 ----
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1;
+        R part = R(0);
+        for (int i = tid; i < m; i += nt) {
+            const R x = T[(k + 1 + i) + (int64_t)k * n];
+            vb[i] = x;
+            if (i > 0) part += x * x;
+        }
+        const R sig = block_sum_rs(part, red);
+        if (tid == 0) {
+            const R x0 = vb[0];
+            R beta = R(0), v0 = R(1), r = x0;
+            if (sig != R(0)) {
+                const R mu = sqrt(x0 * x0 + sig);
+                v0 = x0 <= R(0) ? x0 - mu : -sig / (x0 + mu);
+                beta = R(2) * v0 * v0 / (sig + v0 * v0);
+                r = mu;
+            }
+            s_beta = beta;
+            s_v[0] = v0;
+            s_v[1] = r;
+        }
+        __syncthreads();
+        const R beta = s_beta, v0 = s_v[0];
+        if (beta != R(0)) {
+            for (int i = tid; i < m; i += nt) vb[i] = i == 0 ? R(1) : vb[i] / v0;
+            __syncthreads();
+            // left: columns k+1 .. n-1 (one warp per column), column k set exactly
+            const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+            for (int j = k + 1 + warp; j < n; j += nw) {
+                R d = R(0);
+                for (int i = lane; i < m; i += 32) d += vb[i] * T[(k + 1 + i) + (int64_t)j * n];
+                d = warp_sum(d) * beta;
+                for (int i = lane; i < m; i += 32) T[(k + 1 + i) + (int64_t)j * n] -= d * vb[i];
+            }
+            for (int i = tid; i < m; i += nt) T[(k + 1 + i) + (int64_t)k * n] = i == 0 ? s_v[1] : R(0);
+            __syncthreads();
+            // right: rows 0 .. n-1 of T and Q, columns k+1 .. n-1
+            for (int i = tid; i < n; i += nt) {
+                R u = R(0), w = R(0);
+                for (int l = 0; l < m; ++l) {
+                    u += T[i + (int64_t)(k + 1 + l) * n] * vb[l];
+                    w += Q[i + (int64_t)(k + 1 + l) * n] * vb[l];
+                }
+                u *= beta;
+                w *= beta;
+                for (int l = 0; l < m; ++l) {
+                    T[i + (int64_t)(k + 1 + l) * n] -= u * vb[l];
+                    Q[i + (int64_t)(k + 1 + l) * n] -= w * vb[l];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < n * n; e += nt)
+        if (e % n > e / n + 1) T[e] = R(0);
+    __syncthreads();
+    // ---- double-shift sweeps ----
+    int hi = n - 1, iter = 0, total = 0, sweeps = 0;  // thread 0's copies
+    for (;;) {
+        // thread 0: deflate, then choose: 0 sweep, 1 split at s_k, 2 done, 3 failed
+        if (tid == 0) {
+            s_act = 2;
+            while (hi >= 0) {
+                int lo = hi;
+                while (lo > 0) {
+                    const R sub = fabs(T[lo + (int64_t)(lo - 1) * n]);
+                    const R dsum = fabs(T[lo + (int64_t)lo * n]) + fabs(T[(lo - 1) + (int64_t)(lo - 1) * n]);
+                    if (sub <= eps * dsum || sub == R(0)) {
+                        T[lo + (int64_t)(lo - 1) * n] = R(0);
+                        break;
+                    }
+                    --lo;
+                }
+                if (lo == hi) { --hi; iter = 0; continue; }
+                if (lo == hi - 1) {
+                    const int k = hi - 1;
+                    const R a = T[k + (int64_t)k * n], b = T[k + (int64_t)(k + 1) * n];
+                    const R c = T[(k + 1) + (int64_t)k * n], d = T[(k + 1) + (int64_t)(k + 1) * n];
+                    const R p = R(0.5) * (a - d), disc = p * p + b * c;
+                    hi -= 2;
+                    iter = 0;
+                    if (disc < R(0)) continue;  // a conjugate pair: a 2x2 block stays
+                    const R lam = R(0.5) * (a + d) + (p >= R(0) ? sqrt(disc) : -sqrt(disc));
+                    const R e0 = lam - d, nr = hypot(e0, c);
+                    s_cs = e0 / nr;
+                    s_sn = c / nr;
+                    s_k = k;
+                    s_act = 1;
+                    break;
+                }
+                if (++iter > 60 || ++total > 60 * n + 60) { s_act = 3; break; }
+                ++sweeps;
+                R sft, tft;
+                const R h11 = T[(hi - 1) + (int64_t)(hi - 1) * n], h12 = T[(hi - 1) + (int64_t)hi * n];
+                const R h21 = T[hi + (int64_t)(hi - 1) * n], h22 = T[hi + (int64_t)hi * n];
+                if (iter % 10 == 0) {
+                    const R w = fabs(h21) + fabs(T[(hi - 1) + (int64_t)(hi - 2) * n]);
+                    sft = R(1.5) * w + h22;
+                    tft = w * w;
+                } else {
+                    sft = h11 + h22;
+                    tft = h11 * h22 - h12 * h21;
+                }
+                const R a00 = T[lo + (int64_t)lo * n], a01 = T[lo + (int64_t)(lo + 1) * n];
+                const R a10 = T[(lo + 1) + (int64_t)lo * n], a11 = T[(lo + 1) + (int64_t)(lo + 1) * n];
+                s_v[0] = a00 * a00 + a01 * a10 - sft * a00 + tft;  // first column of (H - s1)(H - s2)
+                s_v[1] = a10 * (a00 + a11 - sft);
+                s_v[2] = a10 * T[(lo + 2) + (int64_t)(lo + 1) * n];
+                s_lo = lo;
+                s_hi = hi;
+                s_act = 0;
+                break;
+            }
+        }
+        __syncthreads();
+        const int act = s_act;
+        if (act >= 2) {
+            if (act == 3 && tid == 0) atomicExch(status, 3);
+            break;
+        }
+        if (act == 1) {  // rotation G = [cs -sn; sn cs] on rows / columns k, k+1
+            const int k = s_k;
+            const R cs = s_cs, sn = s_sn;
+            for (int j = k + tid; j < n; j += nt) {
+                const R x = T[k + (int64_t)j * n], y = T[(k + 1) + (int64_t)j * n];
+                T[k + (int64_t)j * n] = cs * x + sn * y;
+                T[(k + 1) + (int64_t)j * n] = -sn * x + cs * y;
+            }
+            __syncthreads();
+            for (int i = tid; i < n; i += nt) {
+                if (i <= k + 1) {
+                    const R x = T[i + (int64_t)k * n], y = T[i + (int64_t)(k + 1) * n];
+                    T[i + (int64_t)k * n] = cs * x + sn * y;
+                    T[i + (int64_t)(k + 1) * n] = -sn * x + cs * y;
+                }
+                const R x = Q[i + (int64_t)k * n], y = Q[i + (int64_t)(k + 1) * n];
+                Q[i + (int64_t)k * n] = cs * x + sn * y;
+                Q[i + (int64_t)(k + 1) * n] = -sn * x + cs * y;
+            }
+            __syncthreads();
+            if (tid == 0) T[(k + 1) + (int64_t)k * n] = R(0);
+            continue;
+        }
+        // a sweep over [lo, hi]: steps k = lo .. hi-2 with 3x3 reflectors, then a 2x2 one
+        const int lo = s_lo, hs = s_hi;
+        for (int k = lo; k <= hs - 1; ++k) {
+            if (tid == 0) {
+                R x, y, z;
+                if (k == lo) {
+                    x = s_v[0]; y = s_v[1]; z = s_v[2];
+                } else {
+                    x = T[k + (int64_t)(k - 1) * n];
+                    y = T[(k + 1) + (int64_t)(k - 1) * n];
+                    z = k + 2 <= hs ? T[(k + 2) + (int64_t)(k - 1) * n] : R(0);
+                }
+                const int len = k + 2 <= hs ? 3 : 2;
+                R v[3], beta;
+                house3_dev<R>(len, x, y, z, v, beta);
+                s_v[0] = v[0]; s_v[1] = v[1]; s_v[2] = v[2];
+                s_beta = beta;
+                s_len = len;
+                s_c0 = k > lo ? k - 1 : lo;
+                s_r1 = min(k + len + 1, hs + 1);  // rows 0 .. r1-1 of the right application
+            }
+            __syncthreads();
+            const R beta = s_beta, v0 = s_v[0], v1 = s_v[1], v2 = s_v[2];
+            const int len = s_len, c0 = s_c0, r1 = s_r1;
+            if (beta != R(0)) {
+                for (int j = c0 + tid; j < n; j += nt) {
+                    const R t0 = T[k + (int64_t)j * n], t1 = T[(k + 1) + (int64_t)j * n];
+                    const R t2 = len == 3 ? T[(k + 2) + (int64_t)j * n] : R(0);
+                    const R d = beta * (v0 * t0 + v1 * t1 + v2 * t2);
+                    T[k + (int64_t)j * n] = t0 - d * v0;
+                    T[(k + 1) + (int64_t)j * n] = t1 - d * v1;
+                    if (len == 3) T[(k + 2) + (int64_t)j * n] = t2 - d * v2;
+                }
+                __syncthreads();
+                for (int i = tid; i < n; i += nt) {
+                    if (i < r1) {
+                        const R t0 = T[i + (int64_t)k * n], t1 = T[i + (int64_t)(k + 1) * n];
+                        const R t2 = len == 3 ? T[i + (int64_t)(k + 2) * n] : R(0);
+                        const R d = beta * (t0 * v0 + t1 * v1 + t2 * v2);
+                        T[i + (int64_t)k * n] = t0 - d * v0;
+                        T[i + (int64_t)(k + 1) * n] = t1 - d * v1;
+                        if (len == 3) T[i + (int64_t)(k + 2) * n] = t2 - d * v2;
+                    }
+                    const R q0 = Q[i + (int64_t)k * n], q1 = Q[i + (int64_t)(k + 1) * n];
+                    const R q2 = len == 3 ? Q[i + (int64_t)(k + 2) * n] : R(0);
+                    const R d = beta * (q0 * v0 + q1 * v1 + q2 * v2);
+                    Q[i + (int64_t)k * n] = q0 - d * v0;
+                    Q[i + (int64_t)(k + 1) * n] = q1 - d * v1;
+                    if (len == 3) Q[i + (int64_t)(k + 2) * n] = q2 - d * v2;
+                }
+            }
+            __syncthreads();
+            if (tid == 0 && k > lo) {  // the bulge below the subdiagonal is gone
+                T[(k + 1) + (int64_t)(k - 1) * n] = R(0);
+                if (len == 3) T[(k + 2) + (int64_t)(k - 1) * n] = R(0);
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < n * n; e += nt)
+        if (e % n > e / n + 1) T[e] = R(0);
+    if (tid == 0 && counters) counters[0] = sweeps;
+}
+
+template <class R>
+cudaError_t launch_real_schur(R *T, R *Q, int n, int *d_status, int *d_counters, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const size_t smem = (size_t)(n + 8) * sizeof(R);
+    cudaError_t err;
+    if (smem > 48 * 1024 && (err = allow_max_smem((const void *)real_schur_kernel<R>))) return err;
+    real_schur_kernel<R><<<1, kRsThreads, smem, s>>>(T, Q, n, d_status, d_counters); count_launch();
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_real_schur<float>(float *, float *, int, int *, int *, cudaStream_t);
+template cudaError_t launch_real_schur<double>(double *, double *, int, int *, int *, cudaStream_t);
+
 // scratch: blk (n + 1 ints) and nb (1 int) on the device; h_nb: pinned or
 // pageable host int (the launch count needs nb on the host)
 template <class R>

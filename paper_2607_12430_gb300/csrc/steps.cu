@@ -164,6 +164,21 @@ extern "C" int sqrtm_step_trisqrt_rec(sqrtm_handle_t h, const void *dT, void *dS
     return st;
 }
 
+extern "C" int sqrtm_step_real_schur(sqrtm_handle_t h, void *dT, void *dQ, int64_t n, int fp64)
+{
+    if (!h) return -1;
+    if (n < 0 || n > 8192) return -4;
+    if (n == 0) return 0;
+    StepScratch ss; void *ex;
+    if (int rc = step_scratch(h, n, 0, &ss, &ex)) return rc;
+    cudaError_t err = fp64 ? launch_real_schur<double>((double *)dT, (double *)dQ, (int)n, ss.iscal + 1, nullptr, h->stream)
+                           : launch_real_schur<float>((float *)dT, (float *)dQ, (int)n, ss.iscal + 1, nullptr, h->stream);
+    if (err) return 7;
+    int st = 0;
+    if (fetch(h, &st, ss.iscal + 1, sizeof(int))) return 7;
+    return st;
+}
+
 extern "C" int sqrtm_step_qtrisqrt(sqrtm_handle_t h, const void *dT, void *dS, int64_t n, int fp64)
 {
     if (!h) return -1;

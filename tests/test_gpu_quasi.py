@@ -66,3 +66,66 @@ def test_qrtrsyl(m, nn, fp64):
     Y = host_cm(Cd, m, nn).astype(np.float64)
     Yo = oracle.qrtrsyl(S.astype(np.float64), St.astype(np.float64), C.astype(np.float64))
     assert np.linalg.norm(Y - Yo) <= 100 * (m + nn) * u * np.linalg.norm(Yo)
+
+
+# --------------------------------------------------------------------------
+# real Schur stage and the whole real variant (SQRTM_KIND_REAL)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("fp64", [False, True])
+@pytest.mark.parametrize("n", [1, 2, 3, 8, 41, 130])
+def test_real_schur(n, fp64):
+    A = synth.shifted_gaussian(n, 0.7, seed=1100 + n)
+    dt, u = (torch.float64, U64) if fp64 else (torch.float32, U32)
+    Ain = A if fp64 else A.astype(np.float32)
+    Td = dev_cm(Ain, dt)
+    Qd = mp.step_real_schur(Td, n, fp64=fp64)
+    T = host_cm(Td, n).astype(np.float64)
+    Q = host_cm(Qd, n).astype(np.float64)
+    A64 = Ain.astype(np.float64)
+    assert np.linalg.norm(Q @ T @ Q.T - A64) <= 50 * n * u * np.linalg.norm(A64)
+    assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= 50 * n * u
+    assert np.all(np.tril(T, -2) == 0)
+    sub = np.diag(T, -1)
+    assert not np.any((sub[1:] != 0) & (sub[:-1] != 0))  # 2x2 blocks do not overlap
+    for i in np.nonzero(sub)[0]:
+        a, b, c, d = T[i, i], T[i, i + 1], T[i + 1, i], T[i + 1, i + 1]
+        assert 0.25 * (a - d) ** 2 + b * c < 0  # a complex conjugate pair
+    ev = np.sort_complex(np.linalg.eigvals(T))
+    evo = np.sort_complex(np.linalg.eigvals(oracle.real_schur(A64)[1]))
+    assert np.abs(ev - evo).max() <= 200 * n * u * np.linalg.norm(A64)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 16, 65, 150])
+def test_sqrtm_mixed_real_kind(n):
+    A = synth.shifted_gaussian(n, 1.5, seed=1200 + n)
+    X, info = mp.sqrtm_mixed(torch.from_numpy(A).cuda(), kind=mp.KIND_REAL)
+    assert info["status"] == 0 and info["kind_used"] == mp.KIND_REAL
+    assert 1 <= info["iterations"] <= 4
+    Xo = oracle.sqrtm_real_schur(A)
+    assert oracle.rel_err(X.cpu().numpy(), Xo) <= 1e-12
+    assert oracle.rel_err(Xo, oracle.sqrtm_schur(A)) <= 1e-12
+
+
+def test_real_kind_fp64_method_and_steps():
+    n = 90
+    A = synth.shifted_gaussian(n, 1.5, seed=1300)
+    Xo = oracle.sqrtm_real_schur(A)
+    X64, i64 = mp.sqrtm_schur_fp64(torch.from_numpy(A).cuda(), kind=mp.KIND_REAL)
+    assert i64["status"] == 0 and oracle.rel_err(X64.cpu().numpy(), Xo) <= 1e-12
+    errs = []
+    for k in range(3):
+        X, info = mp.sqrtm_mixed(torch.from_numpy(A).cuda(), kind=mp.KIND_REAL, steps=k)
+        assert info["status"] == 0
+        errs.append(oracle.rel_err(X.cpu().numpy(), Xo))
+    assert errs[0] <= 1e-5 and errs[1] <= 1e-3 * errs[0] and errs[2] <= 1e-13
+
+
+def test_real_kind_negative_eigenvalue_status():
+    g = np.random.default_rng(1400)
+    n = 12
+    P = np.linalg.qr(g.standard_normal((n, n)))[0]
+    d = np.linspace(1.0, 2.0, n)
+    d[5] = -1.0
+    _, info = mp.sqrtm_mixed(torch.from_numpy(P @ np.diag(d) @ P.T).cuda(), kind=mp.KIND_REAL,
+                             raise_on_error=False)
+    assert info["status"] == 2
