@@ -477,6 +477,45 @@ def run_complex_suite(args):
     return 0
 
 
+def run_real_suite(args):
+    """The real variant (SQRTM_KIND_REAL, Remark 2.1) against the complex
+    general path on 3I + G/sqrt(n): one JSON line per size with the time of
+    each (2 fixed corrections, mean of --steps calls after one warm-up), the
+    forward error of each against the FP64 complex Schur method on the same
+    GPU, and the time of the FP64 real Schur method."""
+    import torch
+    import paper_2607_12430_gb300 as mp
+    mp.lib()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(max(1, args.steps)):
+            s_ = torch.cuda.Event(enable_timing=True)
+            e_ = torch.cuda.Event(enable_timing=True)
+            s_.record()
+            out = fn()
+            e_.record()
+            torch.cuda.synchronize()
+            ts.append(s_.elapsed_time(e_))
+        return statistics.mean(ts), out
+
+    for n in [int(x) for x in (args.sets or ["128", "512"])]:
+        A = torch.from_numpy(np.ascontiguousarray(synth.shifted_gaussian(n, 3.0, synth.BASE_SEED + 30 + n))).cuda()
+        X64, _ = mp.sqrtm_schur_fp64(A, kind=mp.KIND_GENERAL)
+        nx = X64.norm().item()
+        ms_r, (Xr, ir) = timed(lambda: mp.sqrtm_mixed(A, kind=mp.KIND_REAL, steps=2))
+        ms_g, (Xg, ig) = timed(lambda: mp.sqrtm_mixed(A, kind=mp.KIND_GENERAL, steps=2))
+        ms_r64, (Xr64, _) = timed(lambda: mp.sqrtm_schur_fp64(A, kind=mp.KIND_REAL))
+        print(json.dumps({"suite": "real", "n": n, "real_ms": ms_r, "general_ms": ms_g, "real_fp64_ms": ms_r64,
+                          "real_schur_ms": ir["ms_schur"], "general_schur_ms": ig["ms_schur"],
+                          "real_err": (Xr - X64).norm().item() / nx, "general_err": (Xg - X64).norm().item() / nx,
+                          "real_fp64_err": (Xr64 - X64).norm().item() / nx,
+                          "status": [int(ir["status"]), int(ig["status"])]}), flush=True)
+    return 0
+
+
 def run_batch_suite(args):
     """The batch workload: 2048 matrices, n ~ U{16..256}, half SPD with
     lambda log-uniform in [1e-2, 1e2], half 2I + G/sqrt(n), through
@@ -540,10 +579,11 @@ def main():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--suite", choices=["table1", "cbrt", "batch", "complex"], default=None,
+    p.add_argument("--suite", choices=["table1", "cbrt", "batch", "complex", "real"], default=None,
                    help="instead of the benchmark, one JSON line per case: the paper's Table 1 sets "
                         "(table1), the cube root on sets I, II and the n = 512 workload (cbrt), the "
-                        "2048-matrix batch (batch), complex input at n = 512, 2048 (complex)")
+                        "2048-matrix batch (batch), complex input at n = 512, 2048 (complex), the real variant "
+                        "against the complex path (real)")
     p.add_argument("--sets", nargs="*", default=None, help="--suite: which sets (default all)")
     args = p.parse_args()
     if args.impl == "reference":
@@ -558,6 +598,8 @@ def main():
         return run_batch_suite(args)
     if args.suite == "complex":
         return run_complex_suite(args)
+    if args.suite == "real":
+        return run_real_suite(args)
     return run_ours(args)
 
 
