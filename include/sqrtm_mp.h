@@ -61,7 +61,7 @@ enum { SQRTM_KIND_AUTO = 0, SQRTM_KIND_GENERAL = 1, SQRTM_KIND_SPD = 2, SQRTM_KI
  * blocks for complex conjugate pairs, never cut), the quasi-triangular
  * square root, and corrections from quasi-triangular Sylvester solves with
  * real transforms.  Its Schur stage is a single-CTA double-shift iteration
- * (n <= 8192), much slower than the complex multi-bulge stage of
+ * (n <= 2048; larger n return 7), much slower than the complex multi-bulge stage of
  * SQRTM_KIND_GENERAL for large n. */
 
 /* Precision options (bit flags).

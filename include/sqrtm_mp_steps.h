@@ -72,7 +72,7 @@ SQRTM_API int sqrtm_step_trisqrt_rec(sqrtm_handle_t h, const void *dT, void *dS,
 /* Real Schur form (Remark 2.1) in one CTA: dT (in: real n x n matrix, out:
  * quasi-upper-triangular T, 2x2 diagonal blocks only for complex conjugate
  * pairs) and dQ (out: orthogonal Q, A = Q T Q^T), float or double (fp64),
- * ld n, n <= 8192; Householder reduction, then double-shift sweeps.
+ * ld n, n <= 2048 (else -4); Householder reduction, then double-shift sweeps.
  * Returns 0 or 3 (iteration cap). */
 SQRTM_API int sqrtm_step_real_schur(sqrtm_handle_t h, void *dT, void *dQ, int64_t n, int fp64);
 

@@ -504,8 +504,8 @@ template <class R>
 static int real_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, double tol, double *dX,
                      int64_t ldx, const sqrtm_opts &o, sqrtm_info *info, bool refine)
 {
-    if (n > 8192) {
-        note_error(h, "SQRTM_KIND_REAL: n > 8192", __LINE__, 7);
+    if (n > 2048) {  // the single-CTA Schur stage would take tens of seconds beyond
+        note_error(h, "SQRTM_KIND_REAL: n > 2048", __LINE__, 7);
         return 7;
     }
     cudaStream_t s = h->stream;

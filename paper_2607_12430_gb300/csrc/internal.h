@@ -222,7 +222,7 @@ template <class R>
 cudaError_t launch_qtrisqrt(const R *T, int ldt, R *S, int lds, int n, int *d_blk, int *d_nb, int *d_status,
                             cudaStream_t s);
 // Real Schur form A = Q T Q^T in one CTA (T: in A, out quasi-triangular;
-// Q out; both n x n, ld n, n <= 8192): status 3 when an eigenvalue needs more
+// Q out; both n x n, ld n, n <= 2048): status 3 when an eigenvalue needs more
 // than 60 double-shift sweeps; counters[0] receives the sweeps.
 template <class R>
 cudaError_t launch_real_schur(R *T, R *Q, int n, int *d_status, int *d_counters, cudaStream_t s);

@@ -167,7 +167,7 @@ extern "C" int sqrtm_step_trisqrt_rec(sqrtm_handle_t h, const void *dT, void *dS
 extern "C" int sqrtm_step_real_schur(sqrtm_handle_t h, void *dT, void *dQ, int64_t n, int fp64)
 {
     if (!h) return -1;
-    if (n < 0 || n > 8192) return -4;
+    if (n < 0 || n > 2048) return -4;
     if (n == 0) return 0;
     StepScratch ss; void *ex;
     if (int rc = step_scratch(h, n, 0, &ss, &ex)) return rc;
