@@ -8,7 +8,7 @@
 // return to the host (to learn whether every matrix has converged).
 //
 // Per matrix i of the batch: A_i (FP64, lda_i) -> X_i (FP64, ldx_i), with the
-// same scaling (reading c1 of the design notes: A_s = 4^-e A), FP32 complex
+// same scaling (A_s = 4^-e A, e = ceil(p / 2) for ||A||_F / sqrt(n) = m 2^p), FP32 complex
 // Schur form, FP32 triangular square root, X_0 = Re(Q S Q^H) and the
 // refinement with FP64 residual and update as sqrtm_mixed's general path.
 #include <math.h>
