@@ -61,8 +61,9 @@ enum { SQRTM_KIND_AUTO = 0, SQRTM_KIND_GENERAL = 1, SQRTM_KIND_SPD = 2, SQRTM_KI
  * blocks for complex conjugate pairs, never cut), the quasi-triangular
  * square root, and corrections from quasi-triangular Sylvester solves with
  * real transforms.  Its Schur stage is a single-CTA double-shift iteration
- * (n <= 2048; larger n return 7), much slower than the complex multi-bulge stage of
- * SQRTM_KIND_GENERAL for large n. */
+ * (n <= 2048; larger n return -3, argument n out of range, as
+ * sqrtm_step_real_schur returns -4 for its n), much slower than the complex
+ * multi-bulge stage of SQRTM_KIND_GENERAL for large n. */
 
 /* Precision options (bit flags).
  * Low-precision dense products (transforms of Algorithm 2/3 steps 3, 8 and
@@ -164,6 +165,16 @@ SQRTM_API int sqrtm_destroy(sqrtm_handle_t handle);
 /* Rebind the handle to another stream. */
 SQRTM_API int sqrtm_set_stream(sqrtm_handle_t handle, void *stream);
 
+/* Limit, in nanoseconds, of each bounded device-side wait between the CTAs
+ * of the cooperative QR chase (the Schur stage of the general path,
+ * n >= 256): the chase CTA waiting for its helper CTAs' progress and the
+ * helpers waiting for the next posted window.  A wait that runs out makes
+ * every CTA of the chase leave and the call return 6; the handle stays
+ * usable and its next call starts afresh.  0 (default) means 2 s.  The
+ * tensor-core kernels' mbarrier waits keep their own limit.  Returns 0,
+ * -1 (handle NULL) or -2 (ns < 0). */
+SQRTM_API int sqrtm_set_wait_limit(sqrtm_handle_t handle, int64_t ns);
+
 /* Fill opts with the defaults listed above. */
 SQRTM_API void sqrtm_default_opts(sqrtm_opts *opts);
 
@@ -243,10 +254,48 @@ SQRTM_API int sqrtm_cbrtm_schur_fp64(sqrtm_handle_t handle, const double *dA, in
 SQRTM_API int sqrtm_backward(sqrtm_handle_t handle, const double *dGbar, int64_t n, int64_t ldg,
                    double tol, double *dY, int64_t ldy, sqrtm_info *info);
 
+/* Factors of one forward call, owned by the caller.  sqrtm_backward always
+ * uses the factors of the handle's LAST forward call, so a program that
+ * differentiates through several square roots (several sqrtm_mixed calls
+ * before their backward passes) must keep each call's factors apart:
+ *
+ *   sqrtm_factors_take moves the factors that the last sqrtm_mixed call on
+ *   the handle saved (general: Q, S in complex FP32; SPD: V, s = sqrt(lam)
+ *   in FP32; both: the FP64 X returned, the scale exponent e) into a new
+ *   factor object, without a copy.  The handle keeps no factors afterwards
+ *   (sqrtm_backward then returns 8) and its next forward call allocates new
+ *   factor storage.  Returns 0, -1 (handle NULL), -2 (out NULL), 8 (no
+ *   factors saved: no forward call yet, or the last one was a method that
+ *   keeps none -- the FP64 Schur method, the cube root, complex input, the
+ *   real variant, or a call that failed), 7 (host allocation failure).
+ *
+ *   sqrtm_backward_factors is sqrtm_backward with the factors of f in place
+ *   of the handle's: the adjoint solve X^T Y + Y X^T = Gbar (Eq.
+ *   (triangsylv) with the transposed operator, refined with FP64 residuals)
+ *   for the X of the call that produced f.  The work runs on the handle's
+ *   stream; f's memory was written on the stream of the handle that
+ *   produced it, so a caller on another stream orders the two itself.
+ *   Arguments: 1 handle, 2 f, 3 dGbar, 4 n (must equal f's size, else 8),
+ *   5 ldg, 6 tol, 7 dY, 8 ldy, 9 info; return codes as sqrtm_backward.
+ *   f is not consumed: it may serve several backward passes.
+ *
+ *   sqrtm_factors_n returns f's matrix size (-1 for NULL).
+ *   sqrtm_factors_destroy frees f and its device memory (cudaFree, which
+ *   waits for the device); NULL is accepted.  Returns 0. */
+typedef struct sqrtm_factors_s *sqrtm_factors_t;
+SQRTM_API int sqrtm_factors_take(sqrtm_handle_t handle, sqrtm_factors_t *f);
+SQRTM_API int sqrtm_backward_factors(sqrtm_handle_t handle, sqrtm_factors_t f, const double *dGbar, int64_t n,
+                                     int64_t ldg, double tol, double *dY, int64_t ldy, sqrtm_info *info);
+SQRTM_API int64_t sqrtm_factors_n(sqrtm_factors_t f);
+SQRTM_API int sqrtm_factors_destroy(sqrtm_factors_t f);
+
 /* Batched mixed-precision square roots of independent matrices of varying
  * sizes.  dA, dX: HOST arrays of `batch` device pointers; n, lda, ldx: HOST
  * arrays of sizes.  status: HOST array of `batch` ints receiving each
  * matrix's code.  opts may be NULL.  Returns the first nonzero code, else 0.
+ * When the call stops before any matrix is solved (an invalid argument --
+ * for a member, the code sqrtm_mixed would return for it -- or a failure
+ * to set up worker streams), every status[i] receives the returned code.
  * Matrices of the sizes the tuning table marks `batched` (without a table:
  * n <= 256; the environment variable SQRTM_BATCH_MAXN, if set, is the size
  * limit instead) go through one batched general path: every stage of

@@ -175,12 +175,19 @@ SQRTM_API int sqrtm_step_residual_sym(sqrtm_handle_t h, const double *dA, int64_
  *   dA, dX: n x n FP64 (lda, ldx); dRhat: n x n FP32 output (ld n) receiving
  *   fl32((4^-e A - (2^-e X)^2)); norm_host: optional host pointer receiving
  *   ||R||_F (when given the call waits for the GPU); stream: cudaStream_t.
- * Limits: n <= 4096, otherwise -5.  Calls no cudaMalloc or cudaFree and no
- * allocating library routine.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  All calls share the one array: calls that overlap on
- * the GPU race on it.  Nothing in it needs to start at zero: each call writes
- * every partial it later reads. */
+ * Argument positions for the error codes: 1 dA, 2 lda, 3 dX, 4 ldx, 5 n,
+ * 6 e, 7 dRhat, 8 norm_host, 9 stream; a NULL dA, dX or dRhat returns -1,
+ * -3 or -7.
+ * Limits: n <= 4096, otherwise -5 (checked before anything is launched).
+ * Calls no cudaMalloc or cudaFree and no allocating library routine.  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * While a stream is being captured, pass norm_host = NULL: reading the norm
+ * back waits for the stream, which a capture does not allow; the norm is
+ * then computed but stays in the library's array, out of the caller's
+ * reach, and only dRhat is the call's result.  All calls share the one
+ * array: calls that overlap on the GPU race on it.  Nothing in it needs to
+ * start at zero: each call writes every partial it later reads. */
 SQRTM_API int sqrtm_step_residual_noalloc(const double *dA, int64_t lda, const double *dX,
                                           int64_t ldx, int64_t n, int e, float *dRhat,
                                           double *norm_host, void *stream);

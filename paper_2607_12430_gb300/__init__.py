@@ -88,6 +88,7 @@ _SIGS = {
     "sqrtm_create": ([ctypes.POINTER(_P), _P], _I),
     "sqrtm_destroy": ([_P], _I),
     "sqrtm_set_stream": ([_P, _P], _I),
+    "sqrtm_set_wait_limit": ([_P, _L], _I),
     "sqrtm_default_opts": ([ctypes.POINTER(Opts)], None),
     "sqrtm_set_tuning": ([_P, ctypes.POINTER(TuneEntry), _I], _I),
     "sqrtm_get_tuning": ([_P, ctypes.POINTER(TuneEntry), _I], _I),
@@ -98,6 +99,10 @@ _SIGS = {
     "sqrtm_cbrtm_mixed": ([_P, _P, _L, _L, _D, _P, _L, ctypes.POINTER(Opts), ctypes.POINTER(Info)], _I),
     "sqrtm_cbrtm_schur_fp64": ([_P, _P, _L, _L, _D, _P, _L, ctypes.POINTER(Opts), ctypes.POINTER(Info)], _I),
     "sqrtm_backward": ([_P, _P, _L, _L, _D, _P, _L, ctypes.POINTER(Info)], _I),
+    "sqrtm_factors_take": ([_P, ctypes.POINTER(_P)], _I),
+    "sqrtm_backward_factors": ([_P, _P, _P, _L, _L, _D, _P, _L, ctypes.POINTER(Info)], _I),
+    "sqrtm_factors_n": ([_P], _L),
+    "sqrtm_factors_destroy": ([_P], _I),
     "sqrtm_mixed_batched": ([_P, _I, _P, _P, _P, _D, _P, _P, ctypes.POINTER(Opts), _P], _I),
     "sqrtm_status_string": ([_I], ctypes.c_char_p),
     "sqrtm_kernel_launches": ([], _L),
@@ -241,6 +246,12 @@ def set_tuning(entries):
     rc = lib().sqrtm_set_tuning(handle(), _tune_array(entries), len(entries))
     if rc:
         raise SqrtmError(rc, "sqrtm_set_tuning")
+
+
+def set_wait_limit(ns):
+    """Limit (ns) of the cooperative QR chase's bounded inter-CTA waits on
+    this stream's handle; 0 restores the default (2 s)."""
+    _rc(lib().sqrtm_set_wait_limit(handle(), int(ns)), "sqrtm_set_wait_limit")
 
 
 def get_tuning():
@@ -387,9 +398,60 @@ def sqrtm_backward(G, tol=1e-12, out=None, raise_on_error=True):
     return Y, d
 
 
-def sqrtm_mixed_batched(As, tol=1e-12, outs=None, **kw):
+class Factors:
+    """The factors of one forward call (sqrtm_factors_take), owned by this
+    object: its device memory is released when it is garbage-collected."""
+
+    def __init__(self, ptr):
+        self._p = ptr
+
+    @property
+    def n(self):
+        return int(lib().sqrtm_factors_n(self._p))
+
+    def close(self):
+        if self._p:
+            lib().sqrtm_factors_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def take_factors():
+    """Detach the factors of the last sqrtm_mixed call on this stream's
+    handle (no copy); the handle keeps none afterwards."""
+    fp = ctypes.c_void_p()
+    rc = lib().sqrtm_factors_take(handle(), ctypes.byref(fp))
+    if rc:
+        raise SqrtmError(rc, "sqrtm_factors_take")
+    return Factors(fp)
+
+
+def sqrtm_backward_factors(factors, G, tol=1e-12, out=None, raise_on_error=True):
+    """Gradient of <G, sqrtm(A)> for the forward call whose factors are
+    ``factors`` (a Factors object): Y with X^T Y + Y X^T = G."""
+    G = _check_square(G, "G")
+    n = G.shape[0]
+    Y = _out_like(out, G)
+    info = Info()
+    ld = max(1, n)
+    rc = lib().sqrtm_backward_factors(handle(), factors._p, _ptr(G), n, ld, tol, _ptr(Y), ld, ctypes.byref(info))
+    if rc and raise_on_error:
+        raise SqrtmError(rc, "sqrtm_backward_factors")
+    d = info.as_dict()
+    d["status"] = rc
+    return Y, d
+
+
+def sqrtm_mixed_batched(As, tol=1e-12, outs=None, raise_on_error=False, **kw):
     """Square roots of a list of square float64 CUDA tensors of any sizes.
-    Returns ``(list_of_X, list_of_status)``."""
+    Returns ``(list_of_X, list_of_status)``.  A negative return code (an
+    invalid argument: nothing was solved) always raises; raise_on_error=True
+    also raises when some matrix failed."""
     As = [_check_square(A) for A in As]
     Xs = [_out_like(o, A) for o, A in zip(outs, As)] if outs is not None else [_out_like(None, A) for A in As]
     b = len(As)
@@ -398,9 +460,11 @@ def sqrtm_mixed_batched(As, tol=1e-12, outs=None, **kw):
     ns = (ctypes.c_int64 * b)(*[A.shape[0] for A in As])
     st = (ctypes.c_int * b)()
     o = make_opts(tol=tol, **kw)
-    lib().sqrtm_mixed_batched(handle(), b, ctypes.cast(pa, _P), ctypes.cast(ns, _P), ctypes.cast(ns, _P),
-                              tol, ctypes.cast(px, _P), ctypes.cast(ns, _P), ctypes.byref(o),
-                              ctypes.cast(st, _P))
+    rc = lib().sqrtm_mixed_batched(handle(), b, ctypes.cast(pa, _P), ctypes.cast(ns, _P), ctypes.cast(ns, _P),
+                                   tol, ctypes.cast(px, _P), ctypes.cast(ns, _P), ctypes.byref(o),
+                                   ctypes.cast(st, _P))
+    if rc < 0 or (rc and raise_on_error):
+        raise SqrtmError(rc, "sqrtm_mixed_batched")
     return Xs, list(st)
 
 
@@ -409,18 +473,22 @@ class _SqrtmFn(torch.autograd.Function):
     def forward(ctx, A, tol):
         X, info = sqrtm_mixed(A, tol=tol)
         ctx.tol = tol
-        ctx.n = A.shape[0]
+        # this call's own factors: later forward calls on the same handle
+        # (another sqrtm in the graph, a plain sqrtm_mixed) cannot replace them
+        ctx.factors = take_factors() if info["kind_used"] in (KIND_GENERAL, KIND_SPD) else None
         return X
 
     @staticmethod
     def backward(ctx, G):
-        Y, _ = sqrtm_backward(G.contiguous(), tol=ctx.tol)
+        if ctx.factors is None:
+            raise SqrtmError(8, "sqrtm backward")
+        Y, _ = sqrtm_backward_factors(ctx.factors, G.contiguous(), tol=ctx.tol)
         return Y, None
 
 
 def sqrtm(A, tol=1e-12):
     """Differentiable principal square root (forward: sqrtm_mixed; backward:
-    sqrtm_backward on the factors of that forward call)."""
+    sqrtm_backward_factors with the factors that forward call computed)."""
     return _SqrtmFn.apply(A, tol)
 
 

@@ -16,29 +16,34 @@
 #include <string.h>
 
 #include <algorithm>
+#include <new>
 
 #include "handle.h"
 #include "spd_internal.h"
 
 using namespace sqm;
 
-extern "C" int sqrtm_backward(sqrtm_handle_t h, const double *dG, int64_t n, int64_t ldg,
-                              double tol, double *dY, int64_t ldy, sqrtm_info *info)
+namespace {
+
+// The factors one backward pass uses: those the handle keeps from its last
+// forward call, or those of a detached factor object.
+struct FactView {
+    int64_t n;
+    int kind, e;
+    const void *q, *s;
+    const double *x;
+};
+
+// The adjoint solve and its refinement on the handle's stream and workspace
+// with the factors f (f.n == n, already checked).
+int backward_impl(sqrtm_handle_t h, const FactView &f, const double *dG, int64_t n, int64_t ldg, double tol,
+                  double *dY, int64_t ldy, sqrtm_info *info)
 {
-    if (info) memset(info, 0, sizeof(*info));
-    if (!h) return -1;
-    if (n < 0) return -3;
-    if (n > 0 && !dG) return -2;
-    if (ldg < std::max<int64_t>(1, n)) return -4;
-    if (n > 0 && !dY) return -6;
-    if (ldy < std::max<int64_t>(1, n)) return -7;
-    if (n == 0) return 0;
-    if (h->fact_n != n || !h->fact_x) return 8;
     cudaStream_t s = h->stream;
     const int ni = (int)n;
     const size_t nn = (size_t)n * n;
-    const bool spd = h->fact_kind == SQRTM_KIND_SPD;
-    const int e = h->fact_e;
+    const bool spd = f.kind == SQRTM_KIND_SPD;
+    const int e = f.e;
     const double scale = ldexp(1.0, -e);
     int64_t nb = (n + 63) / 64;
     size_t np_cap = (size_t)std::max<int64_t>(nb * nb, 2048) + 8;
@@ -60,7 +65,7 @@ extern "C" int sqrtm_backward(sqrtm_handle_t h, const double *dG, int64_t n, int
     double gnorm = -1.0, prev = INFINITY;
     for (int k = 0; k <= maxit + 1; ++k) {
         int np = 0;
-        if (launch_adjoint_residual_f64(dG, ldg, h->fact_x, n, dY, ldy, ni, Rhat, ni, dscal + 2, &np, s)) return 7;
+        if (launch_adjoint_residual_f64(dG, ldg, f.x, n, dY, ldy, ni, Rhat, ni, dscal + 2, &np, s)) return 7;
         if (launch_sum_partials(dscal + 2, np, dscal + 1, s)) return 7;
         if (cudaMemcpyAsync(h->staging.p, dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, s)) return 7;
         if (cudaStreamSynchronize(s)) return 7;
@@ -81,14 +86,14 @@ extern "C" int sqrtm_backward(sqrtm_handle_t h, const double *dG, int64_t n, int
         if (grew >= 2) { status = 4; break; }
         prev = rn;
         if (spd) {
-            const float *V = (const float *)h->fact_q, *sv = (const float *)h->fact_s;
+            const float *V = (const float *)f.q, *sv = (const float *)f.s;
             float *Wf = (float *)W, *Yf = (float *)Rt;
             if (launch_rgemm<float>(0, 0, ni, ni, ni, Rhat, ni, V, ni, RG_STORE, Wf, ni, nullptr, nullptr, 0, 0.0, s)) return 7;
             if (launch_rgemm<float>(1, 0, ni, ni, ni, V, ni, Wf, ni, RG_DIAG_SOLVE, Yf, ni, sv, nullptr, 0, 0.0, s)) return 7;
             if (launch_rgemm<float>(0, 0, ni, ni, ni, V, ni, Yf, ni, RG_STORE, Wf, ni, nullptr, nullptr, 0, 0.0, s)) return 7;
             if (launch_rgemm<float>(0, 1, ni, ni, ni, Wf, ni, V, ni, RG_ADD_F64, nullptr, 0, nullptr, dY, ldy, scale, s)) return 7;
         } else {
-            const cplx<float> *Q = (const cplx<float> *)h->fact_q, *S = (const cplx<float> *)h->fact_s;
+            const cplx<float> *Q = (const cplx<float> *)f.q, *S = (const cplx<float> *)f.s;
             // Rt = Q^H Rhat^T Q; S V + V S = Rt; Y += 2^-e Re(Q V Q^H)^T
             if (launch_cgemm<float>(OP_H, OP_N, ni, ni, ni, Rhat, ni, true, Q, ni, EPI_STORE, W, ni, nullptr, 0, 0.0, s)) return 7;
             if (launch_cgemm<float>(OP_H, OP_N, ni, ni, ni, Q, ni, false, W, ni, EPI_STORE, Rt, ni, nullptr, 0, 0.0, s)) return 7;
@@ -105,7 +110,7 @@ extern "C" int sqrtm_backward(sqrtm_handle_t h, const double *dG, int64_t n, int
     memcpy(&st, h->staging.p, sizeof(int));
     if (info) {
         info->iterations = applied;
-        info->kind_used = h->fact_kind;
+        info->kind_used = f.kind;
         info->scale_exponent = e;
         float ms = 0;
         cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
@@ -113,4 +118,76 @@ extern "C" int sqrtm_backward(sqrtm_handle_t h, const double *dG, int64_t n, int
         info->status = st ? st : status;
     }
     return st ? st : status;
+}
+
+}  // namespace
+
+extern "C" int sqrtm_backward(sqrtm_handle_t h, const double *dG, int64_t n, int64_t ldg,
+                              double tol, double *dY, int64_t ldy, sqrtm_info *info)
+{
+    if (info) memset(info, 0, sizeof(*info));
+    if (!h) return -1;
+    if (n < 0) return -3;
+    if (n > 0 && !dG) return -2;
+    if (ldg < std::max<int64_t>(1, n)) return -4;
+    if (n > 0 && !dY) return -6;
+    if (ldy < std::max<int64_t>(1, n)) return -7;
+    if (n == 0) return 0;
+    if (h->fact_n != n || !h->fact_x) return 8;
+    const FactView f{h->fact_n, h->fact_kind, h->fact_e, h->fact_q, h->fact_s, h->fact_x};
+    return backward_impl(h, f, dG, n, ldg, tol, dY, ldy, info);
+}
+
+extern "C" int sqrtm_backward_factors(sqrtm_handle_t h, sqrtm_factors_t fo, const double *dG, int64_t n,
+                                      int64_t ldg, double tol, double *dY, int64_t ldy, sqrtm_info *info)
+{
+    if (info) memset(info, 0, sizeof(*info));
+    if (!h) return -1;
+    if (!fo) return -2;
+    if (n < 0) return -4;
+    if (n > 0 && !dG) return -3;
+    if (ldg < std::max<int64_t>(1, n)) return -5;
+    if (n > 0 && !dY) return -7;
+    if (ldy < std::max<int64_t>(1, n)) return -8;
+    if (n == 0) return 0;
+    if (fo->n != n || !fo->x) return 8;
+    const FactView f{fo->n, fo->kind, fo->e, fo->q, fo->s, fo->x};
+    return backward_impl(h, f, dG, n, ldg, tol, dY, ldy, info);
+}
+
+extern "C" int sqrtm_factors_take(sqrtm_handle_t h, sqrtm_factors_t *out)
+{
+    if (!h) return -1;
+    if (!out) return -2;
+    *out = nullptr;
+    if (h->fact_n < 0 || !h->fact_x) return 8;
+    sqrtm_factors_s *f = new (std::nothrow) sqrtm_factors_s();
+    if (!f) return 7;
+    // the buffer changes owner; no cached graph takes its address as a key
+    // or bakes it into a launch (the kernels read factor pointers from
+    // descriptors rewritten by every call), so nothing is dropped here
+    f->mem = h->fact;
+    f->n = h->fact_n;
+    f->kind = h->fact_kind;
+    f->e = h->fact_e;
+    f->norm = h->fact_norm;
+    f->q = h->fact_q;
+    f->s = h->fact_s;
+    f->x = h->fact_x;
+    h->fact = Buf{};
+    h->fact_n = -1;
+    h->fact_q = h->fact_s = nullptr;
+    h->fact_x = nullptr;
+    *out = f;
+    return 0;
+}
+
+extern "C" int64_t sqrtm_factors_n(sqrtm_factors_t f) { return f ? f->n : -1; }
+
+extern "C" int sqrtm_factors_destroy(sqrtm_factors_t f)
+{
+    if (!f) return 0;
+    if (f->mem.p) cudaFree(f->mem.p);
+    delete f;
+    return 0;
 }

@@ -149,6 +149,15 @@ extern "C" int sqrtm_set_stream(sqrtm_handle_t h, void *stream)
     return 0;
 }
 
+extern "C" int sqrtm_set_wait_limit(sqrtm_handle_t h, int64_t ns)
+{
+    if (!h) return -1;
+    if (ns < 0) return -2;
+    h->wait_ns = (unsigned long long)ns;
+    for (auto *w : h->workers) w->wait_ns = h->wait_ns;
+    return 0;
+}
+
 extern "C" void sqrtm_default_opts(sqrtm_opts *o)
 {
     if (!o) return;
@@ -369,6 +378,7 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     // their deferred passes with the chase
     hd.win_cap = (int)std::min<int64_t>(qr_win_capacity(n), std::max<int64_t>(64, n / 2));
     hd.u_cap = qr_u_capacity(n);
+    hd.wait_ns = h->wait_ns;
     SchurDesc<R> hd2[2] = {hd, hd};
     for (int q = 0; q < 2; ++q) {
         hd2[q].log = rlog[q];
@@ -504,10 +514,7 @@ template <class R>
 static int real_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, double tol, double *dX,
                      int64_t ldx, const sqrtm_opts &o, sqrtm_info *info, bool refine)
 {
-    if (n > 2048) {  // the single-CTA Schur stage would take tens of seconds beyond
-        note_error(h, "SQRTM_KIND_REAL: n > 2048", __LINE__, 7);
-        return 7;
-    }
+    if (n > 2048) return -3;  // size limit of the single-CTA Schur stage: argument 3 (n) out of range
     cudaStream_t s = h->stream;
     const size_t nn = (size_t)n * (size_t)n;
     size_t wbytes = scalars_bytes(n) + 5 * Carve::round(nn * sizeof(R)) + Carve::round(nn * sizeof(float)) +
@@ -779,6 +786,7 @@ static int ensure_workers(sqrtm_handle_t h, int count)
         sqrtm_handle_t w = nullptr;
         if (int rc = sqrtm_create(&w, (void *)st)) { cudaStreamDestroy(st); return rc; }
         w->tuning = h->tuning;
+        w->wait_ns = h->wait_ns;
         h->workers.push_back(w);
         h->worker_streams.push_back(st);
     }
@@ -790,14 +798,21 @@ extern "C" int sqrtm_mixed_batched(sqrtm_handle_t h, int batch, const double *co
                                    double *const *dX, const int64_t *ldx, const sqrtm_opts *opts,
                                    int *status)
 {
-    if (!h) return -1;
     if (batch < 0) return -2;
     if (batch == 0) return 0;
-    if (!dA || !n || !lda || !dX || !ldx) return -3;
+    // an early exit leaves every matrix's status at the returned code, so
+    // a caller reading status[] never takes an untouched output for success
+    auto fail_all = [&](int rc) {
+        if (status)
+            for (int i = 0; i < batch; ++i) status[i] = rc;
+        return rc;
+    };
+    if (!h) return fail_all(-1);
+    if (!dA || !n || !lda || !dX || !ldx) return fail_all(-3);
     for (int i = 0; i < batch; ++i)
-        if (int rc = check_args(dA[i], n[i], lda[i], dX[i], ldx[i])) return rc;
+        if (int rc = check_args(dA[i], n[i], lda[i], dX[i], ldx[i])) return fail_all(rc);
     sqrtm_opts o;
-    if (int rc = resolve_opts(opts, tol, &o)) return rc;
+    if (int rc = resolve_opts(opts, tol, &o)) return fail_all(rc);
     std::vector<int> st(batch, 0);
     // matrices up to the batched size limit go through the batched general
     // path (one set of launches for all of them); larger ones, and every
@@ -820,13 +835,13 @@ extern "C" int sqrtm_mixed_batched(sqrtm_handle_t h, int batch, const double *co
     apply_tuning(h, std::max<int64_t>(nsmall, 1), &ob);
     const int nw = std::min<int>((int)large.size(), 12);
     if (nw > 0) {
-        if (int rc = ensure_workers(h, nw)) return rc;
+        if (int rc = ensure_workers(h, nw)) return fail_all(rc);
     }
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 7;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail_all(7);
     // fence: workers start after the work already on the caller's stream
     cudaEvent_t start;
-    if (cudaEventCreateWithFlags(&start, cudaEventDisableTiming) != cudaSuccess) return 7;
+    if (cudaEventCreateWithFlags(&start, cudaEventDisableTiming) != cudaSuccess) return fail_all(7);
     cudaEventRecord(start, h->stream);
     for (int w = 0; w < nw; ++w) cudaStreamWaitEvent(h->worker_streams[w], start, 0);
     std::stable_sort(large.begin(), large.end(), [&](int a, int b) { return n[a] > n[b]; });

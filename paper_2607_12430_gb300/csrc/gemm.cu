@@ -277,6 +277,11 @@ residual_f64_kernel(const double *__restrict__ A, int64_t lda, const double *__r
     }
 }
 
+int residual_f64_parts(int n)
+{
+    return n <= 0 ? 0 : (int)(cdiv_i(n, GB_M) * cdiv_i(n, GB_N));
+}
+
 cudaError_t launch_residual_f64(const double *A, int64_t lda, const double *X, int64_t ldx,
                                 int n, int e, float *Rhat, int ldr, double *partials,
                                 int *nparts, cudaStream_t s)

@@ -31,6 +31,8 @@ struct sqrtm_handle_s {
     int fact_kind = 0;
     int fact_e = 0;
     double fact_norm = 0.0;
+    // limit of the cooperative QR chase's inter-CTA waits (ns; 0 = 2 s)
+    unsigned long long wait_ns = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // QR iteration: a second stream for the deferred window products, which
     // run while the next round of the chase does, and its ordering events
@@ -58,6 +60,20 @@ struct sqrtm_handle_s {
     char last_error[160] = {0};
     std::vector<sqrtm_handle_s *> workers;
     std::vector<cudaStream_t> worker_streams;
+};
+
+// Factors of one forward call, detached from the handle that computed them
+// (sqrtm_factors_take): the device buffer that held them on the handle
+// together with the pointers into it.
+struct sqrtm_factors_s {
+    Buf mem;
+    int64_t n = -1;
+    int kind = 0;
+    int e = 0;
+    double norm = 0.0;
+    void *q = nullptr;     // general: Q (c64); SPD: V (float)
+    void *s = nullptr;     // general: S (c64); SPD: s = sqrt(lam) (float)
+    double *x = nullptr;   // FP64 X of that call
 };
 
 void drop_graphs(sqrtm_handle_t h, const void *lo, const void *hi);

@@ -65,6 +65,9 @@ struct SchurDesc {
     int *counters;   // out: [0] sweeps, [1..2] rotations, [3..4] in-block rotation work (int64s split lo/hi)
     int n;
     int ld;
+    // limit of each bounded wait between the CTAs of the cooperative chase,
+    // in ns; 0 = the built-in 2 s
+    unsigned long long wait_ns = 0;
 };
 
 // ---- batched general path: one entry per matrix (device arrays) ----
@@ -253,6 +256,8 @@ cudaError_t launch_cgemm(int opA, int opB, int m, int n, int k, const void *A, i
 cudaError_t launch_residual_f64(const double *A, int64_t lda, const double *X, int64_t ldx,
                                 int n, int e, float *Rhat, int ldr, double *partials,
                                 int *nparts, cudaStream_t s);
+// the number of partial sums launch_residual_f64 writes for size n
+int residual_f64_parts(int n);
 // The same with a second factor: R = (A - X B) * 2^-shift (the cube root's
 // residual A - X (X X) with B = X X and shift = 3 e).
 cudaError_t launch_residual_f64_ab(const double *A, int64_t lda, const double *X, int64_t ldx,

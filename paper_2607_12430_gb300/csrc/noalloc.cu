@@ -63,17 +63,22 @@ extern "C" int sqrtm_step_residual_noalloc(const double *dA, int64_t lda, const 
     if (n > kNoallocMaxN) return -5;
     if (lda < (n > 1 ? n : 1)) return -2;
     if (ldx < (n > 1 ? n : 1)) return -4;
-    if (n > 0 && (!dA || !dX || !dRhat)) return -1;
+    if (n > 0 && !dA) return -1;
+    if (n > 0 && !dX) return -3;
+    if (n > 0 && !dRhat) return -7;
     if (n == 0) {
         if (norm_host) *norm_host = 0.0;
         return 0;
     }
+    // the partials must fit the array before anything is launched
+    const int np = sqm::residual_f64_parts((int)n);
+    if (np > kNoallocParts) return -5;
     double *scratch = nullptr;
     if (int rc = scratch_for_current_device(&scratch)) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    int np = 0;
-    if (sqm::launch_residual_f64(dA, lda, dX, ldx, (int)n, e, dRhat, (int)n, scratch + 8, &np, s)) return 7;
-    if (np > kNoallocParts) return 7;
+    int np_launched = 0;
+    if (sqm::launch_residual_f64(dA, lda, dX, ldx, (int)n, e, dRhat, (int)n, scratch + 8, &np_launched, s)) return 7;
+    if (np_launched != np) return 7;  // the launcher and residual_f64_parts disagree
     if (sqm::launch_sum_partials(scratch + 8, np, scratch, s)) return 7;
     if (norm_host) {
         double v = 0.0;

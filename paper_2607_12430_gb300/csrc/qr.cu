@@ -513,7 +513,13 @@ __device__ __forceinline__ void load_t(cplx<R> *dst, const cplx<R> *src)
     else cp_async_elem<R>(dst, src);
 }
 
-static constexpr uint64_t kQrWaitNs = 2000000000ull;  // bounded inter-CTA waits (~2 s)
+static constexpr uint64_t kQrWaitNs = 2000000000ull;  // bounded inter-CTA waits (~2 s) unless the descriptor sets one
+
+template <class R>
+__device__ __forceinline__ uint64_t wait_limit(const SchurDesc<R> &d)
+{
+    return d.wait_ns ? (uint64_t)d.wait_ns : kQrWaitNs;
+}
 
 // Cooperative chase: every thread of the calling CTA waits until each of
 // the H helpers has finished `target` windows; false if a helper failed or
@@ -524,11 +530,11 @@ __device__ bool wait_helpers(const SchurDesc<R> &d, int H, int target)
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
         volatile int *sy = d.sync;
-        const uint64_t t0 = globaltimer_ns();
+        const uint64_t t0 = globaltimer_ns(), lim = wait_limit(d);
         int ok = 1;
         for (int h = 0; h < H && ok; ++h)
             while (sy[4 + h] < target) {
-                if (sy[2] || globaltimer_ns() - t0 > kQrWaitNs) { ok = 0; break; }
+                if (sy[2] || globaltimer_ns() - t0 > lim) { ok = 0; break; }
             }
         __threadfence();
         s_ok = ok;
@@ -560,12 +566,12 @@ __device__ void qr_helper(const SchurDesc<R> &d, int H, int h, cplx<R> *tile, Ro
     for (int w = 0;; ++w) {
         if (tid == 0) {
             volatile int *sy = d.sync;
-            const uint64_t t0 = globaltimer_ns();
+            const uint64_t t0 = globaltimer_ns(), lim = wait_limit(d);
             int go = 0;
             while (true) {
                 if (sy[0] > w) { go = 1; break; }
                 if (sy[1]) { go = 2; break; }
-                if (sy[2] || globaltimer_ns() - t0 > kQrWaitNs) { go = 3; break; }
+                if (sy[2] || globaltimer_ns() - t0 > lim) { go = 3; break; }
             }
             __threadfence();
             s_go = go;

@@ -11,7 +11,7 @@ import torch
 
 import oracle
 import synth
-from gpu_util import U32, U64, dev_cm, host_cm
+from gpu_util import U32, U64, check_kstar, dev_cm, host_cm
 
 pytestmark = pytest.mark.gpu
 
@@ -36,8 +36,8 @@ def _c64(M):
 def test_scale_exact(n, mag):
     A = synth.gaussian((n, n), seed=10 + n) * mag
     As, e, nrm = mp.step_scale(dev_cm(A, torch.float64), n)
-    e_or = oracle.scale_exponent(A)
-    assert abs(e - e_or) <= 1
+    # the same integer rule on both sides (reading c1): the exponent is exact
+    assert e == oracle.scale_exponent(A)
     assert nrm == pytest.approx(np.linalg.norm(A), rel=1e-14)
     expect = (A * 4.0 ** -e).astype(np.float32).astype(np.complex64)
     assert np.array_equal(host_cm(As, n), expect)
@@ -209,11 +209,12 @@ def test_sqrtm_mixed_general_large(n):
     A = synth.shifted_gaussian(n, 3.0, seed=97 + n)
     Xo = oracle.sqrtm_schur(A)
     errs = []
-    for k in (2, 3):
+    for k in (1, 2, 3, 4):
         X, info = mp.sqrtm_mixed(torch.from_numpy(A).cuda(), kind=mp.KIND_GENERAL, steps=k)
         assert info["status"] == 0
         errs.append(oracle.rel_err(X.cpu().numpy(), Xo))
-    assert min(errs) <= 1e-12, errs
+    # k* corrections reach 1e-12 and later ones stay there
+    assert check_kstar(errs, 1e-12) + 1 <= 3, errs
     assert oracle.rel_residual(X.cpu().numpy(), A) <= 5 * n * U64
 
 
@@ -238,12 +239,13 @@ def test_general512_full_size_parity():
     assert 2 <= info["iterations"] <= 4
     # per-step errors decrease (stopping test nullified, Sec. 5.1)
     errs = []
-    for k in range(0, 4):
+    for k in range(0, 5):
         Xk, _ = mp.sqrtm_mixed(torch.from_numpy(A).cuda(), kind=mp.KIND_GENERAL, steps=k)
         errs.append(oracle.rel_err(Xk.cpu().numpy(), Xo))
     assert errs[0] > 1e-8
-    assert all(errs[k + 1] < errs[k] for k in range(2))
-    assert min(errs) <= 1e-12
+    # 2 to 4 corrections reach 1e-12 (the workload's statement), falling
+    # strictly until then, and later corrections keep it there
+    assert 2 <= check_kstar(errs, 1e-12) <= 4, errs
     X4, _ = mp.sqrtm_mixed(torch.from_numpy(A).cuda(), kind=mp.KIND_GENERAL, steps=4)
     assert oracle.rel_residual(X4.cpu().numpy(), A) <= 5 * 512 * U64
 
@@ -293,3 +295,32 @@ def test_sqrtm_mixed_recursive_trisqrt_from_tuning():
         mp.set_tuning(saved)
     assert info["status"] == 0
     assert oracle.rel_residual(X.cpu().numpy(), A.cpu().numpy()) <= 5 * n * U64
+
+
+# --------------------------------------------------------------------------
+# status 6: a bounded device wait that runs out (no fault, no hang)
+# --------------------------------------------------------------------------
+def test_bounded_wait_gives_up_then_handle_recovers():
+    """The cooperative chase (n >= 256) waits on its helper CTAs and they on
+    it, each wait bounded.  With a 1 ns limit the first wait that has to
+    wait at all gives up: every CTA leaves and the call returns 6.  The same
+    handle then runs a normal call whose result matches the oracle."""
+    n = 512
+    A = synth.config_general512()
+    Ad = torch.from_numpy(A).cuda()
+    saved = mp.get_tuning()
+    try:
+        # the cooperative chase with 8 helper CTAs, whatever the shipped table says
+        mp.set_tuning([{"n_max": 1 << 20, "blks": 32, "qr_helpers": 8, "batched": 1, "spd_precision": 0}])
+        mp.set_wait_limit(1)
+        _, info = mp.sqrtm_mixed(Ad, kind=mp.KIND_GENERAL, raise_on_error=False)
+    finally:
+        mp.set_wait_limit(0)
+        mp.set_tuning(saved)
+    assert info["status"] == 6
+    X, info = mp.sqrtm_mixed(Ad, kind=mp.KIND_GENERAL)
+    assert info["status"] == 0
+    assert oracle.rel_err(X.cpu().numpy(), oracle.sqrtm_schur(A)) <= 1e-12
+    with pytest.raises(mp.SqrtmError) as e:
+        mp.set_wait_limit(-1)
+    assert e.value.code == -2

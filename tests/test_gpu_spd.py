@@ -8,7 +8,7 @@ import torch
 
 import oracle
 import synth
-from gpu_util import U32, U64, dev_cm, host_cm
+from gpu_util import U32, U64, check_kstar, dev_cm, host_cm
 
 pytestmark = pytest.mark.gpu
 
@@ -84,12 +84,12 @@ def test_sqrtm_mixed_spd(n, lo, hi):
     # about kappa-weighted 1e-12 only; the forward-error target is checked on
     # the stopping-test-nullified iterates (Sec. 5.1 protocol)
     errs = []
-    for k in range(2, 9):
+    for k in range(1, 9):
         Xk, _ = mp.sqrtm_mixed(torch.from_numpy(A).cuda(), steps=k)
         Xk = Xk.cpu().numpy()
         assert np.array_equal(Xk, Xk.T)
         errs.append(oracle.rel_err(Xk, Xg))
-    assert min(errs) <= 1e-13, errs
+    check_kstar(errs, 1e-13)
     assert oracle.rel_residual(Xk, A) <= 5 * n * U64
 
 
@@ -120,10 +120,10 @@ def test_repeated_eigenvalue(n, mult):
     assert info["kind_used"] == mp.KIND_SPD
     assert oracle.rel_err(X.cpu().numpy(), Xo) <= 1e-13
     errs = []
-    for k in (2, 3, 4):
+    for k in (1, 2, 3, 4, 5):
         X, info = mp.sqrtm_mixed(torch.from_numpy(A).cuda(), steps=k)
         errs.append(oracle.rel_err(X.cpu().numpy(), Xo))
-    assert min(errs) <= 1e-13, errs
+    check_kstar(errs, 1e-13)
 
 
 def test_spd_indefinite_status():
@@ -141,9 +141,9 @@ def test_spd4096_full_size_parity():
     Xcf = oracle.sqrtm_from_eig(V, lam)
     Xg = oracle.refine(A, V, np.diag(np.sqrt(lam)), Xcf, steps=1, spd=True)[-1]
     errs = []
-    for k in (4, 5, 6, 7):
+    for k in (2, 3, 4, 5, 6, 7):
         X, info = mp.sqrtm_mixed(torch.from_numpy(A).cuda(), steps=k)
         X = X.cpu().numpy()
         errs.append(oracle.rel_err(X, Xg))
         assert np.array_equal(X, X.T)
-    assert min(errs) <= 1e-13, errs
+    check_kstar(errs, 1e-13)
