@@ -78,7 +78,16 @@ def load(path):
     L.orc_rtrsyl3.restype = i
     L.orc_cbrtm_schur.argtypes = [i, P, i, P, i, P, P, P, P]
     L.orc_cbrtm_schur.restype = i
+    L.orc_threads.argtypes = [i]
+    L.orc_threads.restype = i
     return L
+
+
+def threads(count=0):
+    """Thread count of the oracle's parallel loops (independent columns of the
+    Householder updates and plain products; bitwise the same results for any
+    count): count > 0 sets it; returns the count in use."""
+    return int(lib().orc_threads(int(count)))
 
 
 def lib():

@@ -31,17 +31,40 @@
  *
  * Storage: column-major, element (i,j) of an m-by-n array with leading
  * dimension ld at a[i + j*ld].  Complex values use C99 double complex.
+ *
+ * Threads: when compiled with OpenMP, the loops over independent columns
+ * (or rows) of the Householder updates and of the plain products run in
+ * parallel; each column's arithmetic is the same sequence of operations as
+ * in the serial loop, so the results are bitwise the same for any thread
+ * count.  The QR sweep (a chain of dependent rotations) and the triangular
+ * recurrence run serially.  orc_threads sets / reports the thread count.
  */
 #include <complex.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef double complex zc;
 
 #define IDX(i, j, ld) ((size_t)(i) + (size_t)(j) * (size_t)(ld))
 
 static const double ORC_EPS = 1.1102230246251565e-16; /* 2^-53 */
+
+/* Thread count of the parallel loops: nthreads > 0 sets it; returns the
+ * count in use (1 without OpenMP). */
+int orc_threads(int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    return omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* Householder reduction to upper Hessenberg form.                          */
@@ -78,6 +101,7 @@ void orc_hessenberg(int n, zc *H, int ldh, zc *Q, int ldq)
         for (int i = 0; i < m; ++i) vnorm2 += creal(v[i]) * creal(v[i]) + cimag(v[i]) * cimag(v[i]);
         double beta = 2.0 / vnorm2;
         /* left: H(k+1:n, :) <- H - beta v (v^H H) */
+#pragma omp parallel for schedule(static) if (n >= 128)
         for (int j = 0; j < n; ++j) {
             zc w = 0.0;
             for (int i = 0; i < m; ++i) w += conj(v[i]) * H[IDX(k + 1 + i, j, ldh)];
@@ -85,6 +109,7 @@ void orc_hessenberg(int n, zc *H, int ldh, zc *Q, int ldq)
             for (int i = 0; i < m; ++i) H[IDX(k + 1 + i, j, ldh)] -= v[i] * w;
         }
         /* right: H(:, k+1:n) <- H - beta (H v) v^H */
+#pragma omp parallel for schedule(static) if (n >= 128)
         for (int i = 0; i < n; ++i) {
             zc w = 0.0;
             for (int l = 0; l < m; ++l) w += H[IDX(i, k + 1 + l, ldh)] * v[l];
@@ -92,6 +117,7 @@ void orc_hessenberg(int n, zc *H, int ldh, zc *Q, int ldq)
             for (int l = 0; l < m; ++l) H[IDX(i, k + 1 + l, ldh)] -= w * conj(v[l]);
         }
         /* accumulate: Q(:, k+1:n) <- Q - beta (Q v) v^H */
+#pragma omp parallel for schedule(static) if (n >= 128)
         for (int i = 0; i < n; ++i) {
             zc w = 0.0;
             for (int l = 0; l < m; ++l) w += Q[IDX(i, k + 1 + l, ldq)] * v[l];
@@ -251,25 +277,30 @@ int orc_trisqrt(int n, const zc *T, int ldt, zc *S, int lds)
 }
 
 /* C = alpha * op(A) * op(B) + beta * C, all n x n complex; op = 'N', 'C'
- * (conjugate transpose).  Plain triple loop. */
+ * (conjugate transpose).  Plain triple loop; C must not overlap A or B
+ * (columns of C are formed independently). */
 static void orc_zgemm(char ta, char tb, int n, zc alpha, const zc *A, int lda, const zc *B,
                       int ldb, zc beta, zc *C, int ldc)
 {
-    zc *col = (zc *)malloc(sizeof(zc) * (size_t)n);
-    for (int j = 0; j < n; ++j) {
-        for (int i = 0; i < n; ++i) {
-            zc acc = 0.0;
-            for (int k = 0; k < n; ++k) {
-                zc a = (ta == 'N') ? A[IDX(i, k, lda)] : conj(A[IDX(k, i, lda)]);
-                zc b = (tb == 'N') ? B[IDX(k, j, ldb)] : conj(B[IDX(j, k, ldb)]);
-                acc += a * b;
+#pragma omp parallel if (n >= 128)
+    {
+        zc *col = (zc *)malloc(sizeof(zc) * (size_t)(n > 0 ? n : 1));
+#pragma omp for schedule(static)
+        for (int j = 0; j < n; ++j) {
+            for (int i = 0; i < n; ++i) {
+                zc acc = 0.0;
+                for (int k = 0; k < n; ++k) {
+                    zc a = (ta == 'N') ? A[IDX(i, k, lda)] : conj(A[IDX(k, i, lda)]);
+                    zc b = (tb == 'N') ? B[IDX(k, j, ldb)] : conj(B[IDX(j, k, ldb)]);
+                    acc += a * b;
+                }
+                col[i] = acc;
             }
-            col[i] = acc;
+            for (int i = 0; i < n; ++i)
+                C[IDX(i, j, ldc)] = alpha * col[i] + (beta == 0.0 ? 0.0 : beta * C[IDX(i, j, ldc)]);
         }
-        for (int i = 0; i < n; ++i)
-            C[IDX(i, j, ldc)] = alpha * col[i] + (beta == 0.0 ? 0.0 : beta * C[IDX(i, j, ldc)]);
+        free(col);
     }
-    free(col);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -444,6 +475,7 @@ int orc_bs_solve(int m, int n, const zc *S, int lds, const zc *St, int ldst, zc 
 static void orc_gemm_sub(int m, int n, int k, const zc *A, int lda, const zc *B, int ldb, zc *C,
                          int ldc)
 {
+#pragma omp parallel for schedule(static) if ((long)m * n * k >= 262144L)
     for (int j = 0; j < n; ++j)
         for (int i = 0; i < m; ++i) {
             zc acc = 0.0;

@@ -607,3 +607,18 @@ def test_refine_real_contracts(orc):
     X0 = X + 1e-6 * synth.gaussian((n, n), seed=961)
     errs = [orc.rel_err(Xk, X) for Xk in orc.refine_real(A, Q, S, X0, 3)]
     assert errs[1] <= 1e-3 * errs[0] and errs[3] <= 1e-14
+
+
+def test_threads_do_not_change_results(orc):
+    # the parallel loops run each column's arithmetic unchanged: the FP64
+    # Schur method gives bitwise the same X on 1 thread and on all of them
+    A = synth.shifted_gaussian(160, 3.0, seed=4242)
+    old = orc.threads()
+    try:
+        orc.threads(1)
+        X1, Q1, T1, S1 = orc.sqrtm_schur(A, return_factors=True)
+        orc.threads(max(2, os.cpu_count() or 2))
+        Xp, Qp, Tp, Sp = orc.sqrtm_schur(A, return_factors=True)
+    finally:
+        orc.threads(old)
+    assert np.array_equal(X1, Xp) and np.array_equal(Q1, Qp) and np.array_equal(T1, Tp)
