@@ -12,6 +12,14 @@ refinement steps after which the relative forward error is <= 1e-12, and each
 timed step is one sqrtm_mixed call with exactly k* corrections (the
 stopping test nullified, as in the paper's accuracy runs).
 
+Two more legs ride on the same JSON line ("legs"), each with its own k*,
+timing, FP64-method time and dominant-kernel roofline: "c3", the SPD
+n = 4096, kappa = 1e6 workload (reference: the closed form V diag(sqrt(lam))
+V^T of the generator's decomposition polished by one FP64 refinement step,
+target 1e-13), and "set_iii", Table 1 set III at n = 4096 (general; reference:
+the FP64 Schur method on the same GPU, the paper's ground truth, Sec. 5.1,
+target 1e-12).  --no-legs skips them.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N > 1) every rank runs an independent replica (the single
 matrix does not shard); rank 0 prints one JSON line.
@@ -126,11 +134,10 @@ def _peaks():
 # ---------------------------------------------------------------------------
 # DRAM bytes (read + write) of the qr_chase_kernel launches of one call on
 # this workload (the chase runs in rounds, four launches per call here),
-# summed from the ncu dram-bytes capture summarised in
-# profiles/qr_chase_general512.md; valid only for the chase kernel's source
-# it was taken with: SHA-256 of qr.cu up to the first kernel after the chase
-# (the deferred-pass kernels and the host code follow it) plus common.cuh,
-# else null.
+# summed from one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum;
+# valid only for the chase kernel's source it was taken with: SHA-256 of
+# qr.cu up to the first kernel after the chase (the deferred-pass kernels and
+# the host code follow it) plus common.cuh, else null.
 CHASE_TRAFFIC = {"sha256": "2fb4cfd45e9c5102053eaf06d56d1c6d128db9e245a23170822923a3144da96f", "bytes": 5474560}
 _CHASE_END = "__global__ void __launch_bounds__(128) qr_build_u_kernel"
 
@@ -155,6 +162,7 @@ def run_reference(args):
         return 0
     import oracle
     oracle.lib()
+    cores = oracle.threads(os.cpu_count() or 1)
     A = synth.config_general512(n=N)
     for _ in range(args.warmup):
         oracle.sqrtm_schur(A)
@@ -169,12 +177,161 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N},
-        "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle",
-                         "sample": "one full FP64 Schur-method sqrtm of the n=512 workload per step"},
+        "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle",
+                         "sample": "one full FP64 Schur-method sqrtm of the n=512 workload per step "
+                                   "(OpenMP over the independent columns of the Householder updates and "
+                                   "products; the QR sweep is serial)"},
         "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def cpu_baseline_leg(oracle, A_np):
+    """The oracle (FP64 Schur method) on the workload: on all host cores (the
+    reported cpu_baseline), on one thread, and scipy.linalg.sqrtm (a tuned
+    FP64 blocked Schur method) when scipy is importable.  The all-core run's
+    result is returned under "_X" (it fixes k*)."""
+    cores = oracle.threads(os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    X = oracle.sqrtm_schur(A_np)
+    ms_all = (time.perf_counter() - t0) * 1e3
+    oracle.threads(1)
+    t0 = time.perf_counter()
+    oracle.sqrtm_schur(A_np)
+    ms_one = (time.perf_counter() - t0) * 1e3
+    oracle.threads(cores)
+    scipy_ms = None
+    try:
+        import scipy.linalg
+        scipy.linalg.sqrtm(A_np[:8, :8] + 8 * np.eye(8))
+        t0 = time.perf_counter()
+        scipy.linalg.sqrtm(A_np)
+        scipy_ms = (time.perf_counter() - t0) * 1e3
+    except Exception:
+        pass
+    return {"value": ms_all, "unit": "ms", "cores": cores, "kind": "oracle",
+            "sample": f"one full FP64 Schur-method sqrtm of the n={A_np.shape[0]} workload on {cores} threads "
+                      "(OpenMP over the independent columns of the Householder updates and products; the "
+                      "QR sweep is serial)",
+            "one_thread_ms": ms_one, "scipy_sqrtm_ms": scipy_ms, "_X": X}
+
+
+def _timed_calls(torch, fn, count, flush):
+    """CUDA-event times (ms) of `count` calls on the current stream, L2
+    flushed before each."""
+    stream = torch.cuda.current_stream()
+    ts, out = [], None
+    for _ in range(count):
+        flush.add_(1.0)
+        s_ = torch.cuda.Event(enable_timing=True)
+        e_ = torch.cuda.Event(enable_timing=True)
+        s_.record(stream)
+        out = fn()
+        e_.record(stream)
+        torch.cuda.synchronize()
+        ts.append(s_.elapsed_time(e_))
+    return ts, out
+
+
+def leg_c3(args, mp, torch, flush, peaks):
+    """SPD n = 4096, kappa = 1e6 (lambda log-uniform in [1e-3, 1e3], ends
+    pinned): k* against the closed form polished by one FP64 step, the time
+    of sqrtm_mixed with k* corrections, the FP64 method on the same GPU, and
+    the roofline of the decomposition's dominant kernels (the per-column
+    Householder tridiagonalisation, bound by memory traffic)."""
+    import oracle
+    t_gen = time.perf_counter()
+    A_np, V, lam = synth.config_spd4096()
+    n = A_np.shape[0]
+    Xcf = (V * np.sqrt(lam)[None, :]) @ V.T
+    Xg = oracle.refine(A_np, V, np.diag(np.sqrt(lam)), Xcf, steps=1, spd=True)[-1]
+    gen_s = time.perf_counter() - t_gen
+    A = torch.from_numpy(np.ascontiguousarray(A_np)).cuda()
+    X = torch.empty_like(A)
+    errs, kstar = {}, None
+    for k in range(1, 9):
+        mp.sqrtm_mixed(A, steps=k, out=X)
+        errs[k] = oracle.rel_err(X.cpu().numpy(), Xg)
+        if errs[k] <= 1e-13:
+            kstar = k
+            break
+    if kstar is None:
+        return {"error": "no step count reached 1e-13", "errors_by_step": errs}
+    reps = max(2, min(args.steps, 5))
+    ts, (_, info) = _timed_calls(torch, lambda: mp.sqrtm_mixed(A, steps=kstar, out=X), reps + 1, flush)
+    ts = ts[1:]
+    ts64, (X64, _) = _timed_calls(torch, lambda: mp.sqrtm_schur_fp64(A, out=X), 2, flush)
+    ms, ms64 = statistics.mean(ts), ts64[-1]
+    err64 = oracle.rel_err(X64.cpu().numpy(), Xg)
+    # tridiagonalisation: every column step reads and writes the trailing
+    # symmetric block once, 4 (n-k)^2 / 2 bytes each way summed over k:
+    # 4 n^3 / 3 bytes of algorithmic traffic per decomposition (FP32)
+    red_ms = info["ms_reduction"]
+    byts = 4.0 * n ** 3 / 3.0
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    achieved = byts / (red_ms * 1e-3) / 1e9
+    return {"workload": "SPD n=4096 A=V diag(lam) V^T, V Haar, lam=10^U(-3,3) ends pinned, kappa=1e6, seed 20260712+2",
+            "n": n, "target": 1e-13, "k_star": kstar, "forward_error": errs[kstar],
+            "errors_by_step": errs, "reference": "closed form V diag(sqrt(lam)) V^T + one FP64 refinement step",
+            "ms": ms, "timed_calls": reps, "fp64_schur_ms": ms64, "fp64_schur_forward_error": err64,
+            "speedup_vs_fp64_schur": ms64 / ms, "kind_used": int(info["kind_used"]),
+            "phases_ms": {"ms_decomposition": info["ms_schur"], "ms_reduction": red_ms,
+                          "ms_refine": info["ms_refine"]},
+            "roofline": {"kernel": "tri_step_kernel<float> (tridiagonalisation, one launch per column)",
+                         "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None,
+                         "note": "algorithmic 4n^3/3 B per decomposition over the library's CUDA-event time of "
+                                 "the reduction phase; peak: measured HBM copy bandwidth (the trailing block "
+                                 "is L2-resident, so the kernel is bound by L2 and launch latency)"},
+            "input_prep_s": gen_s}
+
+
+def leg_set_iii(args, mp, torch, flush, fp32_peak_tflops):
+    """Table 1 set III (U(0,1) entries plus the shift, nonsymmetric, n = 4096):
+    the FP64 Schur method on the same GPU (timed once; its result is the
+    reference, as the paper's ground truth is the FP64 Schur method), k*
+    (first correction count within 1e-12 of it), and sqrtm_mixed with k*
+    corrections (one warm-up, then timed).  The QR chase's roofline as in
+    the headline."""
+    import oracle
+    t_gen = time.perf_counter()
+    A_np = synth.table1_case("III", 4096, seed=synth.BASE_SEED + 10)
+    gen_s = time.perf_counter() - t_gen
+    n = A_np.shape[0]
+    A = torch.from_numpy(np.ascontiguousarray(A_np)).cuda()
+    X = torch.empty_like(A)
+    ts64, (X64, i64) = _timed_calls(torch, lambda: mp.sqrtm_schur_fp64(A, kind=mp.KIND_GENERAL), 1, flush)
+    ref = X64.cpu().numpy()
+    res64 = float(((X64 @ X64 - A).norm() / A.norm()).item())
+    errs, kstar = {}, None
+    for k in range(0, 5):
+        mp.sqrtm_mixed(A, kind=mp.KIND_GENERAL, steps=k, out=X)
+        errs[k] = oracle.rel_err(X.cpu().numpy(), ref)
+        if errs[k] <= 1e-12:
+            kstar = k
+            break
+    if kstar is None:
+        return {"error": "no step count reached 1e-12", "errors_by_step": errs}
+    reps = max(1, min(args.steps, 2))
+    ts, (_, info) = _timed_calls(torch, lambda: mp.sqrtm_mixed(A, kind=mp.KIND_GENERAL, steps=kstar, out=X),
+                                 reps, flush)
+    ms = statistics.mean(ts)
+    chase_flops = 20.0 * info["schur_work"]
+    achieved = chase_flops / (info["ms_qr_chase"] * 1e-3) / 1e12
+    return {"workload": "Table 1 set III: U(0,1) n=4096 plus shift (real eigenvalues >= 1), seed 20260712+10",
+            "n": n, "target": 1e-12, "k_star": kstar, "forward_error": errs[kstar], "errors_by_step": errs,
+            "reference": "FP64 Schur method on the same GPU (the paper's ground truth)",
+            "reference_rel_residual": res64,
+            "ms": ms, "timed_calls": reps, "fp64_schur_ms": ts64[0], "speedup_vs_fp64_schur": ts64[0] / ms,
+            "phases_ms": {"ms_reduction": info["ms_reduction"], "ms_schur": info["ms_schur"],
+                          "ms_qr_chase": info["ms_qr_chase"], "ms_trisqrt": info["ms_trisqrt"],
+                          "ms_refine": info["ms_refine"]},
+            "schur_sweeps": info["schur_sweeps"], "schur_rotations": info["schur_rotations"],
+            "roofline": {"kernel": "qr_chase_kernel<float>", "bound": "alu", "achieved": achieved,
+                         "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
+                         "traffic": None, "flops_per_call": chase_flops},
+            "input_prep_s": gen_s}
 
 
 # ---------------------------------------------------------------------------
@@ -206,11 +363,8 @@ def run_ours(args):
     if rank == 0:
         import oracle
         oracle.lib()
-        t0 = time.perf_counter()
-        Xo = oracle.sqrtm_schur(A_np)
-        cpu_ms = (time.perf_counter() - t0) * 1e3
-        cpu_baseline = {"value": cpu_ms, "unit": "ms", "cores": 1, "kind": "oracle",
-                        "sample": "one full FP64 Schur-method sqrtm of the n=512 workload (single thread)"}
+        cpu_baseline = cpu_baseline_leg(oracle, A_np)
+        Xo = cpu_baseline.pop("_X")
         for k in range(0, 8):
             Xk, info = mp.sqrtm_mixed(A, kind=mp.KIND_GENERAL, steps=k)
             errs[k] = oracle.rel_err(Xk.cpu().numpy(), Xo)
@@ -315,15 +469,19 @@ def run_ours(args):
     work = statistics.mean([i["schur_work"] for i in infos])
     chase_ms = statistics.mean([i["ms_qr_chase"] for i in infos])
     chase_flops = 20.0 * work
-    fp32_peak_tflops = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 FFMA lanes x 2 flops x max clock
-    one_sm_peak = fp32_peak_tflops / 152
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    # FP32 FFMA lanes (128 per SM on sm_103) x 2 flops x the device's maximum SM clock
+    fp32_peak_tflops = sms * 128 * 2 * mhz * 1e6 / 1e12
+    one_sm_peak = fp32_peak_tflops / sms
     achieved = chase_flops / (chase_ms * 1e-3) / 1e12
     roofline = {"kernel": "qr_chase_kernel<float>", "bound": "alu", "achieved": achieved,
                 "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
                 "traffic": _chase_traffic(),
                 "kernel_ms_per_step": chase_ms, "flops_per_step": chase_flops,
                 "peak_one_sm": one_sm_peak, "frac_one_sm": achieved / one_sm_peak,
-                "note": "peak derived (152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz), not measured; the "
+                "note": f"peak derived ({sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz, read from the "
+                        "device), not measured; the "
                         "bulge chain runs on one chase CTA (8 helper CTAs take the out-of-window "
                         "updates), so the one-SM fraction is the meaningful one; achieved and traffic "
                         "are per step, summed over the chase launches of one call (ncu dram bytes, "
@@ -346,6 +504,10 @@ def run_ours(args):
         "clocks": clocks,
         "gpu_launches": launches,
     }
+    if rank == 0 and not args.no_legs:
+        # the n >= 2048 comparisons (after the headline's timed region)
+        line["legs"] = {"c3": leg_c3(args, mp, torch, flush, peaks),
+                        "set_iii": leg_set_iii(args, mp, torch, flush, fp32_peak_tflops)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -579,6 +741,8 @@ def main():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-legs", action="store_true",
+                   help="skip the n = 4096 legs (SPD kappa = 1e6, Table 1 set III) of the benchmark line")
     p.add_argument("--suite", choices=["table1", "cbrt", "batch", "complex", "real"], default=None,
                    help="instead of the benchmark, one JSON line per case: the paper's Table 1 sets "
                         "(table1), the cube root on sets I, II and the n = 512 workload (cbrt), the "
