@@ -310,6 +310,21 @@ SQRTM_API int sqrtm_mixed_batched(sqrtm_handle_t handle, int batch, const double
                         double *const *dX, const int64_t *ldx, const sqrtm_opts *opts,
                         int *status);
 
+/* Split a batch of independent matrices over `parts` GPUs (one process per
+ * GPU, each calling sqrtm_mixed_batched on its share; no data crosses GPUs,
+ * so no collective is needed on the data path).  Longest-processing-time
+ * rule with the cost n^3 of the O(n^3) stages (Schur decomposition,
+ * transforms, Sylvester solves): matrices in decreasing cost (ties: lower
+ * index first), each to the part with the smallest total so far (ties:
+ * lowest part), which bounds the largest part by 4/3 of the optimum.
+ * Deterministic, so every process computes the same partition.
+ *   n: HOST array of `batch` sizes; owner: HOST array receiving each
+ *   matrix's part (0 .. parts-1); load: optional HOST array of `parts`
+ *   doubles receiving each part's total cost.
+ * Host-only (no CUDA call).  Returns 0, -1 (batch < 0), -2 (n NULL or a
+ * negative size), -3 (parts < 1), -4 (owner NULL). */
+SQRTM_API int sqrtm_batch_partition(int batch, const int64_t *n, int parts, int *owner, double *load);
+
 /* Number of CUDA kernel launches this library has issued in the process so
  * far (all handles, all threads).  Diagnostic; never resets. */
 SQRTM_API int64_t sqrtm_kernel_launches(void);

@@ -104,6 +104,7 @@ _SIGS = {
     "sqrtm_factors_n": ([_P], _L),
     "sqrtm_factors_destroy": ([_P], _I),
     "sqrtm_mixed_batched": ([_P, _I, _P, _P, _P, _D, _P, _P, ctypes.POINTER(Opts), _P], _I),
+    "sqrtm_batch_partition": ([_I, _P, _I, _P, _P], _I),
     "sqrtm_status_string": ([_I], ctypes.c_char_p),
     "sqrtm_kernel_launches": ([], _L),
     "sqrtm_last_error": ([_P], ctypes.c_char_p),
@@ -466,6 +467,63 @@ def sqrtm_mixed_batched(As, tol=1e-12, outs=None, raise_on_error=False, **kw):
     if rc < 0 or (rc and raise_on_error):
         raise SqrtmError(rc, "sqrtm_mixed_batched")
     return Xs, list(st)
+
+
+def batch_partition(sizes, parts):
+    """LPT partition of a batch over `parts` GPUs (sqrtm_batch_partition):
+    returns (owner list, per-part cost list)."""
+    b = len(sizes)
+    ns = (ctypes.c_int64 * max(1, b))(*[int(x) for x in sizes])
+    own = (ctypes.c_int * max(1, b))()
+    load = (ctypes.c_double * max(1, parts))()
+    _rc(lib().sqrtm_batch_partition(b, ctypes.cast(ns, _P), int(parts), ctypes.cast(own, _P),
+                                    ctypes.cast(load, _P)), "sqrtm_batch_partition")
+    return [own[i] for i in range(b)], [load[p] for p in range(parts)]
+
+
+def sharded_run(sizes, rank, world, solve, gather):
+    """The multi-GPU batch protocol, independent of how a share is solved:
+    every rank computes the same LPT partition, solves its own matrices with
+    ``solve(indices) -> statuses`` and the statuses are collected with
+    ``gather(obj) -> list of every rank's obj`` (a host-side exchange of
+    small integers; the matrices never leave their GPU).  Returns
+    ``(own indices, statuses of the whole batch in input order)``."""
+    owner, _ = batch_partition(sizes, world)
+    mine = [i for i, o in enumerate(owner) if o == rank]
+    st = solve(mine) if mine else []
+    parts = gather((mine, list(st)))
+    full = [None] * len(sizes)
+    for idx, sts in parts:
+        for i, v in zip(idx, sts):
+            full[i] = int(v)
+    return mine, full
+
+
+def sqrtm_mixed_batched_sharded(As, tol=1e-12, group=None, **kw):
+    """The batch split over the processes of torch.distributed (one GPU
+    each): rank r solves the matrices the LPT partition gives it, on its own
+    GPU, through sqrtm_mixed_batched; statuses are gathered on every rank.
+    ``As`` is the whole batch as host (CPU) float64 tensors; each rank copies
+    only its own share to its GPU.  Returns ``({index: X on this GPU},
+    statuses of the whole batch)``."""
+    import torch.distributed as dist
+    rank, world = dist.get_rank(group), dist.get_world_size(group)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = {}
+
+    def solve(idx):
+        mats = [As[i].to(dev) for i in idx]
+        Xs, st = sqrtm_mixed_batched(mats, tol=tol, **kw)
+        out.update(zip(idx, Xs))
+        return st
+
+    def gather(obj):
+        res = [None] * world
+        dist.all_gather_object(res, obj, group=group)
+        return res
+
+    _, full = sharded_run([A.shape[0] for A in As], rank, world, solve, gather)
+    return out, full
 
 
 class _SqrtmFn(torch.autograd.Function):

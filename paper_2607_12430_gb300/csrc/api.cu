@@ -793,6 +793,35 @@ static int ensure_workers(sqrtm_handle_t h, int count)
     return 0;
 }
 
+// Longest-processing-time partition of a batch over `parts` workers (GPUs):
+// matrices by decreasing cost n^3 (ties: lower index first), each to the
+// part with the smallest load so far (ties: lowest part index).
+extern "C" int sqrtm_batch_partition(int batch, const int64_t *n, int parts, int *owner, double *load)
+{
+    if (batch < 0) return -1;
+    if (batch > 0 && !n) return -2;
+    if (parts < 1) return -3;
+    if (batch > 0 && !owner) return -4;
+    std::vector<double> ld((size_t)parts, 0.0);
+    std::vector<int> ord((size_t)batch);
+    for (int i = 0; i < batch; ++i) {
+        if (n[i] < 0) return -2;
+        ord[i] = i;
+    }
+    auto cost = [&](int i) { return (double)n[i] * (double)n[i] * (double)n[i]; };
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    for (int i : ord) {
+        int best = 0;
+        for (int p = 1; p < parts; ++p)
+            if (ld[p] < ld[best]) best = p;
+        owner[i] = best;
+        ld[best] += cost(i);
+    }
+    if (load)
+        for (int p = 0; p < parts; ++p) load[p] = ld[p];
+    return 0;
+}
+
 extern "C" int sqrtm_mixed_batched(sqrtm_handle_t h, int batch, const double *const *dA,
                                    const int64_t *n, const int64_t *lda, double tol,
                                    double *const *dX, const int64_t *ldx, const sqrtm_opts *opts,

@@ -99,3 +99,22 @@ def test_batched_iteration_limit_status():
     As = [torch.from_numpy(it[1]).cuda() for it in items]
     _, st = mp.sqrtm_mixed_batched(As, tol=1e-15, maxit=0)
     assert st == [1] * len(As)
+
+
+def test_sharded_batch_single_rank_matches_batched_call(tmp_path):
+    """The multi-GPU batch call with one rank (a gloo process group on a file
+    store): the LPT share is the whole batch, solved by sqrtm_mixed_batched
+    on this GPU, and the statuses come back in input order."""
+    import torch.distributed as dist
+    items = synth.batch_case(count=12, seed=synth.BASE_SEED + 31)
+    host = [torch.from_numpy(np.ascontiguousarray(it[1])) for it in items]
+    dist.init_process_group("gloo", init_method="file://" + str(tmp_path / "pg"), rank=0, world_size=1)
+    try:
+        out, st = mp.sqrtm_mixed_batched_sharded(host, steps=4)
+    finally:
+        dist.destroy_process_group()
+    assert st == [0] * len(items)
+    assert sorted(out) == list(range(len(items)))
+    for i, it in enumerate(items):
+        tol = 1e-13 if it[0] == "spd" else 1e-12
+        assert oracle.rel_err(out[i].cpu().numpy(), _reference(it)) <= tol
