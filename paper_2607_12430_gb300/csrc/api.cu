@@ -38,10 +38,10 @@ cudaError_t sqm::allow_max_smem(const void *kernel)
 // captured launch sequences
 // ---------------------------------------------------------------------------
 int run_graph(sqrtm_handle_t h, int tag, const void *key, int64_t n, int batch,
-              cudaError_t (*enqueue)(void *ctx, cudaStream_t s), void *ctx)
+              cudaError_t (*enqueue)(void *ctx, cudaStream_t s), void *ctx, uint64_t sig)
 {
     for (auto &g : h->graphs) {
-        if (g.tag == tag && g.key == key && g.n == n && g.batch == batch) {
+        if (g.tag == tag && g.key == key && g.n == n && g.batch == batch && g.sig == sig) {
             if (cudaGraphLaunch(g.exec, h->stream) != cudaSuccess) return 7;
             g_launches.fetch_add(g.launches, std::memory_order_relaxed);
             return 0;
@@ -66,10 +66,46 @@ int run_graph(sqrtm_handle_t h, int tag, const void *key, int64_t n, int batch,
     err = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (err != cudaSuccess) { note_error(h, cudaGetErrorName(err), __LINE__, 7); return 7; }
-    h->graphs.push_back({tag, key, n, batch, exec, nl});
+    h->graphs.push_back({tag, key, n, batch, sig, exec, nl});
     if (cudaGraphLaunch(exec, h->stream) != cudaSuccess) return 7;
     g_launches.fetch_add(nl, std::memory_order_relaxed);
     return 0;
+}
+
+cudaError_t sqm::capture_while(cudaStream_t s, cudaStream_t body_stream, unsigned init, CondFn body, void *ctx,
+                               CondFn pre)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *edges = nullptr;
+    size_t nd = 0;
+    cudaError_t err = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &edges, &nd);
+    if (err) return err;
+    if (cs != cudaStreamCaptureStatusActive || !g) return cudaErrorStreamCaptureUnmatched;
+    cudaGraphConditionalHandle cond;
+    if ((err = cudaGraphConditionalHandleCreate(&cond, g, init, cudaGraphCondAssignDefault))) return err;
+    if (pre) {
+        if ((err = pre(ctx, s, cond))) return err;
+        // the node goes after what pre added
+        if ((err = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &edges, &nd))) return err;
+    }
+    cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = cond;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    if ((err = cudaGraphAddNode(&node, g, deps, edges, nd, &p))) return err;
+    cudaGraph_t body_graph = p.conditional.phGraph_out[0];
+    if ((err = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies))) return err;
+    if ((err = cudaStreamBeginCaptureToGraph(body_stream, body_graph, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeRelaxed)))
+        return err;
+    cudaError_t e1 = body(ctx, body_stream, cond);
+    cudaGraph_t out = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(body_stream, &out);
+    return e1 ? e1 : e2;
 }
 
 void note_error(sqrtm_handle_t h, const char *what, int line, int code)
@@ -125,6 +161,7 @@ extern "C" int sqrtm_destroy(sqrtm_handle_t h)
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->body_stream) cudaStreamDestroy(h->body_stream);
     if (h->side) {
         cudaStreamSynchronize(h->side);
         cudaStreamDestroy(h->side);
@@ -857,7 +894,10 @@ extern "C" int sqrtm_mixed_batched(sqrtm_handle_t h, int batch, const double *co
         if (n[i] == 0) continue;
         const sqrtm_tune_entry *t = env ? nullptr : tune_for(h, n[i]);
         const bool b = t ? t->batched == 1 : n[i] <= nbmax;
-        if (o.kind != SQRTM_KIND_SPD && b) { small.push_back(i); nsmall = std::max(nsmall, n[i]); }
+        // the batched path's spectral (Algorithm 3) stage takes n <= 256;
+        // larger matrices of a forced SPD call go to per-matrix calls
+        const bool ok = o.kind != SQRTM_KIND_SPD || n[i] <= 256;
+        if (b && ok) { small.push_back(i); nsmall = std::max(nsmall, n[i]); }
         else large.push_back(i);
     }
     sqrtm_opts ob = o;  // the batched path's block size: that of its largest matrix

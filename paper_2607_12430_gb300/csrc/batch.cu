@@ -1,16 +1,24 @@
-// batch.cu -- the batched general path: many independent small matrices
-// through Algorithm 2 in one set of launches.  Every stage is one launch (or
-// one short sequence) over all matrices, each kernel indexing its matrix by
-// blockIdx; the Hessenberg reduction and the whole refinement loop (residual,
-// convergence test, transforms, Sylvester solve, update, for every step) are
-// replayed from CUDA graphs, and the convergence test runs on the device, so
-// the loop needs no host round trip.  Only the rounds of the QR iteration
-// return to the host (to learn whether every matrix has converged).
+// batch.cu -- the batched path: many independent small matrices through
+// Algorithm 2 (general members) and Algorithm 3 (symmetric members) in ONE
+// CUDA graph launch per call.  Every stage is one launch (or one short
+// sequence) over all matrices, each kernel indexing its matrix by blockIdx.
+// The two loops of the method run on the device as conditional WHILE nodes
+// of the graph: the rounds of the QR iteration (a one-thread kernel tests
+// every matrix's done flag after each round) and the refinement steps (the
+// convergence test runs per matrix on the device, and a one-thread kernel
+// ends the loop when no matrix takes another correction).  The host reads
+// the statuses once, after the graph.
 //
 // Per matrix i of the batch: A_i (FP64, lda_i) -> X_i (FP64, ldx_i), with the
-// same scaling (A_s = 4^-e A, e = ceil(p / 2) for ||A||_F / sqrt(n) = m 2^p), FP32 complex
-// Schur form, FP32 triangular square root, X_0 = Re(Q S Q^H) and the
-// refinement with FP64 residual and update as sqrtm_mixed's general path.
+// same scaling (A_s = 4^-e A, e = ceil(p / 2) for ||A||_F / sqrt(n) = m 2^p) as
+// the single-matrix paths.  General members: FP32 complex Schur form and
+// triangular square root.  Symmetric members (bitwise symmetric under
+// SQRTM_KIND_AUTO, or every member under SQRTM_KIND_SPD): the FP32 spectral
+// decomposition A_s = V diag(lam) V^T by cyclic Jacobi (Algorithm 3, step 1),
+// handed to the shared stages as Q = V and T = diag(lam), so that the
+// triangular square root gives s_i = sqrt(lam_i) (step 2) and the Sylvester
+// solve with the diagonal S is y_ij = r_ij / (s_i + s_j) (step 9).  Then
+// X_0 = Re(Q S Q^H) and the refinement with FP64 residual and update.
 #include <math.h>
 #include <string.h>
 
@@ -52,7 +60,206 @@ struct BParams {
     int fixed;     // 1: apply exactly `steps` corrections, no test
     int max_corr;  // adaptive: at most this many corrections
     int nactive;   // matrices still taking corrections after the last test
+    int iters;     // refinement steps at most (graph loop bound)
+    int iter;      // refinement steps done (device loop counter)
+    int round;     // QR rounds done (device loop counter)
 };
+
+// the refinement loop's condition: before the loop (any step at all?) and
+// after each step (did some matrix go on, and is a step left?)
+__global__ void brefine_init_kernel(BParams *prm, cudaGraphConditionalHandle cond)
+{
+    prm->iter = 0;
+    prm->nactive = 0;
+    cudaGraphSetConditional(cond, prm->iters > 0 ? 1u : 0u);
+}
+
+__global__ void brefine_next_kernel(BParams *prm, cudaGraphConditionalHandle cond)
+{
+    const bool go = prm->nactive > 0 && ++prm->iter < prm->iters;
+    prm->nactive = 0;
+    cudaGraphSetConditional(cond, go ? 1u : 0u);
+}
+
+// ---------------------------------------------------------------------------
+// symmetric members: FP32 spectral decomposition by cyclic Jacobi
+// ---------------------------------------------------------------------------
+// A symmetric A_s = V diag(lam) V^T (Algorithm 3, step 1) by two-sided
+// Jacobi rotations in the parallel (round-robin) order: the n indices (plus
+// one padding slot when n is odd) form n/2 disjoint pairs per step, each
+// pair (p, q) zeroes a_pq by J = [c s; -s c] with t = tan from
+// theta = (a_qq - a_pp) / (2 a_pq), t = sign(theta) / (|theta| +
+// sqrt(1 + theta^2)), c = 1 / sqrt(1 + t^2), s = t c; the N - 1 steps of a
+// sweep meet every pair once.  A pair is skipped (identity) when |a_pq| <=
+// 2^-23 sqrt(|a_pp a_qq|) or |a_pq| <= 2^-24 ||A||_F (FP32 rounding level);
+// the iteration stops after a sweep with no rotation (at most 30 sweeps,
+// then status 3).  One step updates A <- J^T A J as 2 x 2 blocks
+// J_k^T A({p_k, q_k}, {p_l, q_l}) J_l over the pairs k >= l -- every block
+// is a disjoint set of entries -- on the packed lower triangle of A in
+// shared memory (exactly symmetric), and V <- V J column pair by column pair.
+struct JacJob {
+    cplx<float> *T;   // in: A_s in the real parts; out: diag(lam)
+    cplx<float> *Q;   // out: V (imaginary parts zero)
+    float *Vw;        // scratch n x n: V when it is not kept in shared memory
+    int *status;      // receives 3 (no convergence) or 7 (n out of range)
+    int n;
+};
+
+static constexpr int kJacThreads = 1024;
+static constexpr int kJacMaxN = 256;       // packed A: n(n+1)/2 floats in shared memory
+static constexpr int kJacVsmemMaxN = 190;  // V in shared memory as well up to this size
+static constexpr int kJacSweeps = 30;
+
+__device__ __forceinline__ int jac_idx(int i, int j, int n)  // (i, j) of the lower triangle, i >= j
+{
+    return i + j * (2 * n - j - 1) / 2;
+}
+
+inline size_t jac_smem_bytes(int n, bool vsmem)
+{
+    const size_t np = ((size_t)n * (n + 1) / 2 + 3) & ~(size_t)3;
+    return (np + (vsmem ? (size_t)n * n : 0)) * sizeof(float);
+}
+
+template <bool VSMEM>
+__global__ void __launch_bounds__(kJacThreads) bjacobi_kernel(const JacJob *__restrict__ jobs)
+{
+    extern __shared__ __align__(16) float jsm[];
+    __shared__ float s_c[kJacMaxN / 2], s_s[kJacMaxN / 2];
+    __shared__ int s_p[kJacMaxN / 2], s_q[kJacMaxN / 2];
+    __shared__ float red[kJacThreads / 32];
+    __shared__ float s_floor;
+    __shared__ int s_rot;
+    const JacJob J = jobs[blockIdx.x];
+    const int n = J.n, tid = threadIdx.x;
+    constexpr int nt = kJacThreads;
+    if (n <= 0) return;
+    if (n > kJacMaxN || (VSMEM && n > kJacVsmemMaxN)) {
+        if (tid == 0) atomicExch(J.status, 7);
+        return;
+    }
+    float *P = jsm;
+    const int np = n * (n + 1) / 2;
+    float *V = VSMEM ? jsm + ((np + 3) & ~3) : J.Vw;
+    float ss = 0.0f;
+    for (int e = tid; e < n * n; e += nt) {
+        const int i = e % n, j = e / n;
+        const float a = J.T[e].x;
+        if (i >= j) P[jac_idx(i, j, n)] = a;
+        ss = fmaf(a, a, ss);
+        V[e] = (i == j) ? 1.0f : 0.0f;
+    }
+    ss = warp_sum(ss);
+    if ((tid & 31) == 0) red[tid >> 5] = ss;
+    __syncthreads();
+    if (tid == 0) {
+        float t = 0.0f;
+        for (int w = 0; w < nt / 32; ++w) t += red[w];
+        s_floor = ldexpf(sqrtf(t), -24);
+    }
+    __syncthreads();
+    const int N = n + (n & 1), H = N / 2;
+    const float eps = 1.1920929e-7f;  // 2^-23
+    bool conv = false;
+    for (int sw = 0; sw < kJacSweeps && !conv; ++sw) {
+        if (tid == 0) s_rot = 0;
+        __syncthreads();
+        for (int r = 0; r < N - 1; ++r) {
+            if (tid < H) {
+                const int a = tid == 0 ? r : (r + tid) % (N - 1);
+                const int b = tid == 0 ? N - 1 : (r - tid + N - 1) % (N - 1);
+                const int p = min(a, b);
+                int q = max(a, b);
+                float c = 1.0f, sn = 0.0f;
+                if (q < n) {
+                    const float app = P[jac_idx(p, p, n)], aqq = P[jac_idx(q, q, n)], apq = P[jac_idx(q, p, n)];
+                    const float aa = fabsf(apq);
+                    if (apq != 0.0f && aa > eps * sqrtf(fabsf(app * aqq)) && aa > s_floor) {
+                        const float th = (aqq - app) / (2.0f * apq);
+                        const float t = fabsf(th) > 1e18f ? 0.5f / th
+                                                         : copysignf(1.0f, th) / (fabsf(th) + sqrtf(1.0f + th * th));
+                        c = 1.0f / sqrtf(1.0f + t * t);
+                        sn = t * c;
+                        s_rot = 1;
+                    }
+                } else {
+                    q = -1;  // partner is the padding slot: a group of one, no rotation
+                }
+                s_p[tid] = p;
+                s_q[tid] = q;
+                s_c[tid] = c;
+                s_s[tid] = sn;
+            }
+            __syncthreads();
+            auto at = [&](int i, int j) -> float {
+                if (i < 0 || j < 0) return 0.0f;
+                return i >= j ? P[jac_idx(i, j, n)] : P[jac_idx(j, i, n)];
+            };
+            auto put = [&](int i, int j, float v) {
+                if (i >= j) P[jac_idx(i, j, n)] = v;
+                else P[jac_idx(j, i, n)] = v;
+            };
+            for (int e = tid; e < H * H; e += nt) {
+                const int k = e / H, l = e % H;
+                if (l > k) continue;
+                const float sk = s_s[k], sl = s_s[l];
+                if (sk == 0.0f && sl == 0.0f) continue;
+                const float ck = s_c[k], cl = s_c[l];
+                const int pk = s_p[k], qk = s_q[k], pl = s_p[l], ql = s_q[l];
+                const float b00 = at(pk, pl), b01 = at(pk, ql), b10 = at(qk, pl), b11 = at(qk, ql);
+                const float r00 = ck * b00 - sk * b10, r01 = ck * b01 - sk * b11;
+                const float r10 = sk * b00 + ck * b10, r11 = sk * b01 + ck * b11;
+                const float c00 = cl * r00 - sl * r01, c01 = sl * r00 + cl * r01;
+                const float c10 = cl * r10 - sl * r11, c11 = sl * r10 + cl * r11;
+                if (k == l) {
+                    P[jac_idx(pk, pk, n)] = c00;
+                    if (qk >= 0) {
+                        P[jac_idx(qk, pk, n)] = c10;
+                        P[jac_idx(qk, qk, n)] = c11;
+                    }
+                } else {
+                    put(pk, pl, c00);
+                    if (ql >= 0) put(pk, ql, c01);
+                    if (qk >= 0) put(qk, pl, c10);
+                    if (qk >= 0 && ql >= 0) put(qk, ql, c11);
+                }
+            }
+            for (int e = tid; e < H * n; e += nt) {
+                const int k = e / n, i = e % n;
+                const float sk = s_s[k];
+                if (sk == 0.0f) continue;
+                const float ck = s_c[k];
+                const int p = s_p[k], q = s_q[k];
+                const float vp = V[i + p * n], vq = V[i + q * n];
+                V[i + p * n] = ck * vp - sk * vq;
+                V[i + q * n] = sk * vp + ck * vq;
+            }
+            __syncthreads();
+        }
+        conv = s_rot == 0;
+        __syncthreads();
+    }
+    if (!conv && tid == 0) atomicExch(J.status, 3);
+    for (int e = tid; e < n * n; e += nt) {
+        const int i = e % n, j = e / n;
+        J.Q[e] = cplx<float>{V[e], 0.0f};
+        J.T[e] = cplx<float>{i == j ? P[jac_idx(i, i, n)] : 0.0f, 0.0f};
+    }
+}
+
+// flag[b] = 1 when matrix b is not bitwise symmetric
+__global__ void bsym_kernel(const BInput *__restrict__ in, int *__restrict__ nonsym)
+{
+    const BInput a = in[blockIdx.y];
+    const int64_t nn = (int64_t)a.n * a.n;
+    bool bad = false;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nn; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t % a.n, j = t / a.n;
+        if (i > j && __double_as_longlong(a.A[i + j * a.lda]) != __double_as_longlong(a.A[j + i * a.lda]))
+            bad = true;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) nonsym[blockIdx.y] = 1;
+}
 
 static constexpr int kBNormThreads = 256;
 
@@ -177,8 +384,9 @@ namespace {
 // only, which keeps the cached graphs valid across calls
 template <class R>
 struct BLayout {
-    SchurDesc<R> *desc;
+    SchurDesc<R> *desc;  // general members first (entries 0 .. Bg-1)
     HessJob<R> *hj;
+    JacJob *jj;          // symmetric members (entries Bg .. B-1)
     TriJob<R> *tri;
     GemmJob<R> *gj;  // 6 sets of `batch` products
     ResJob *rj;
@@ -195,6 +403,7 @@ BLayout<R> carve_header(Carve &c, int batch)
     BLayout<R> L;
     L.desc = c.take<SchurDesc<R>>(batch);
     L.hj = c.take<HessJob<R>>(batch);
+    L.jj = c.take<JacJob>(batch);
     L.tri = c.take<TriJob<R>>(batch);
     L.gj = c.take<GemmJob<R>>(6 * (size_t)batch);
     L.rj = c.take<ResJob>(batch);
@@ -218,46 +427,101 @@ size_t matrix_bytes(int64_t n)
            Carve::round(8 * sizeof(int)) + 256;
 }
 
-struct LoopCtx {
-    const void *tri, *gj, *rj;
-    BState *st;
-    BParams *prm;
-    int batch, nmax, blks;
+// what the captured launches depend on beyond the layout's addresses: the
+// sizes (size classes, grids) and kinds in batch order, the block size
+struct Pipe {
+    BLayout<float> L;
+    const int *nord;  // sizes in batch order (host)
+    int B, Bg, nmax, blks;
+    cudaStream_t body_stream;
 };
 
-// one step of the refinement for every matrix still active: R = (A - X X)
-// 4^-e and ||R||_F, the test (which also counts the matrices that go on),
-// then R~ = Q^H Rhat Q, S Y + Y S = R~, X += 2^e Re(Q Y Q^H)
-template <class R>
-cudaError_t enqueue_refine_step(void *p, cudaStream_t s)
+cudaError_t enqueue_refine_body(void *p, cudaStream_t s, cudaGraphConditionalHandle cond)
 {
-    const LoopCtx *c = (const LoopCtx *)p;
-    const TriJob<R> *tri = (const TriJob<R> *)c->tri;
-    const GemmJob<R> *gj = (const GemmJob<R> *)c->gj;
-    const ResJob *rj = (const ResJob *)c->rj;
-    const int B = c->batch, nm = c->nmax;
+    using R = float;
+    const Pipe *c = (const Pipe *)p;
+    const BLayout<R> &L = c->L;
+    const int B = c->B, nm = c->nmax;
     cudaError_t err;
-    if ((err = cudaMemsetAsync(&c->prm->nactive, 0, sizeof(int), s))) return err;
-    if ((err = launch_residual_batched(rj, B, nm, s))) return err;
-    bdecide_kernel<<<cdiv_i(B, 128), 128, 0, s>>>(c->st, B, c->prm); count_launch();
-    if ((err = launch_cgemm_batched<R>(OP_N, OP_N, true, EPI_STORE, gj + 2 * B, B, nm, s))) return err;
-    if ((err = launch_cgemm_batched<R>(OP_H, OP_N, false, EPI_STORE, gj + 3 * B, B, nm, s))) return err;
-    if ((err = launch_rtrsyl_batched<R>(tri, B, nm, c->blks, s))) return err;
-    if ((err = launch_cgemm_batched<R>(OP_N, OP_N, false, EPI_STORE, gj + 4 * B, B, nm, s))) return err;
-    if ((err = launch_cgemm_batched<R>(OP_N, OP_H, false, EPI_REAL_ADD_F64, gj + 5 * B, B, nm, s))) return err;
+    // R = (A - X X) 4^-e and ||R||_F, the per-matrix test (counting the
+    // matrices that go on), R~ = Q^H Rhat Q, S Y + Y S = R~, X += 2^e Re(Q Y Q^H)
+    if ((err = launch_residual_batched(L.rj, B, nm, s))) return err;
+    bdecide_kernel<<<cdiv_i(B, 128), 128, 0, s>>>(L.st, B, L.prm); count_launch();
+    if ((err = launch_cgemm_batched<R>(OP_N, OP_N, true, EPI_STORE, L.gj + 2 * B, B, nm, s))) return err;
+    if ((err = launch_cgemm_batched<R>(OP_H, OP_N, false, EPI_STORE, L.gj + 3 * B, B, nm, s))) return err;
+    if ((err = launch_rtrsyl_batched<R>(L.tri, B, nm, c->blks, s))) return err;
+    if ((err = launch_cgemm_batched<R>(OP_N, OP_N, false, EPI_STORE, L.gj + 4 * B, B, nm, s))) return err;
+    if ((err = launch_cgemm_batched<R>(OP_N, OP_H, false, EPI_REAL_ADD_F64, L.gj + 5 * B, B, nm, s))) return err;
+    brefine_next_kernel<<<1, 1, 0, s>>>(L.prm, cond); count_launch();
     return cudaGetLastError();
 }
 
-struct HessCtx {
-    const void *desc;
-    int batch, nmax;
-};
-
-template <class R>
-cudaError_t enqueue_hess(void *p, cudaStream_t s)
+cudaError_t enqueue_refine_init(void *p, cudaStream_t s, cudaGraphConditionalHandle cond)
 {
-    const HessCtx *c = (const HessCtx *)p;
-    return launch_hessenberg<R>((const SchurDesc<R> *)c->desc, c->batch, c->nmax, std::max(1, c->nmax / 32), s);
+    const Pipe *c = (const Pipe *)p;
+    brefine_init_kernel<<<1, 1, 0, s>>>(c->L.prm, cond); count_launch();
+    return cudaGetLastError();
+}
+
+// the whole batched call, for capture into one graph
+cudaError_t enqueue_pipeline(void *p, cudaStream_t s)
+{
+    using R = float;
+    const Pipe *c = (const Pipe *)p;
+    const BLayout<R> &L = c->L;
+    const int B = c->B, Bg = c->Bg, nmax = c->nmax;
+    cudaError_t err;
+    bnorm_kernel<<<B, kBNormThreads, 0, s>>>(L.in, L.st); count_launch();
+    bcast_kernel<R><<<dim3(std::max(1, std::min(64, nmax * nmax / 1024)), B), 256, 0, s>>>(L.in, L.st, L.desc);
+    count_launch();
+    // general members: Hessenberg reduction (one cluster per matrix, one
+    // launch per size class; the per-column kernels beyond the cluster
+    // kernel's sizes), then the QR rounds on the device
+    for (int i0 = 0; i0 < Bg;) {
+        const int nc = c->nord[i0];
+        const int cap = nc <= 64 ? 0 : nc <= 128 ? 64 : nc <= 256 ? 128 : nc <= 512 ? 256 : 512;
+        int i1 = i0;
+        while (i1 < Bg && c->nord[i1] > cap) ++i1;
+        err = launch_hessenberg_cluster_batched<R>(L.hj + i0, i1 - i0, nc, s);
+        if (err == cudaErrorNotSupported) {  // refused before any launch
+            cudaGetLastError();
+            err = launch_hessenberg<R>(L.desc + i0, i1 - i0, nc, std::max(1, nc / 32), s);
+        }
+        if (err) return err;
+        i0 = i1;
+    }
+    if (Bg > 0 && (err = enqueue_qr_sweeps_device<R>(L.desc, Bg, c->nord[0], &L.prm->round, s, c->body_stream)))
+        return err;
+    // symmetric members: Jacobi, V in global memory above kJacVsmemMaxN
+    for (int i0 = Bg; i0 < B;) {
+        const bool vs = c->nord[i0] <= kJacVsmemMaxN;
+        int i1 = i0;
+        while (i1 < B && (c->nord[i1] <= kJacVsmemMaxN) == vs) ++i1;
+        const size_t smem = jac_smem_bytes(c->nord[i0], vs);
+        if (vs) bjacobi_kernel<true><<<i1 - i0, kJacThreads, smem, s>>>(L.jj + i0);
+        else bjacobi_kernel<false><<<i1 - i0, kJacThreads, smem, s>>>(L.jj + i0);
+        count_launch();
+        if ((err = cudaGetLastError())) return err;
+        i0 = i1;
+    }
+    if ((err = launch_trisqrt_batched<R>(L.tri, B, nmax, c->blks, s))) return err;
+    bfold_kernel<<<cdiv_i(B, 128), 128, 0, s>>>(L.st, B); count_launch();
+    // X_0 = 2^e Re(Q S Q^H), rounded to FP32
+    if ((err = launch_cgemm_batched<R>(OP_N, OP_N, false, EPI_STORE, L.gj, B, nmax, s))) return err;
+    if ((err = launch_cgemm_batched<R>(OP_N, OP_H, false, EPI_REAL_TO_F64, L.gj + B, B, nmax, s))) return err;
+    // the refinement loop
+    if ((err = capture_while(s, c->body_stream, 0u, enqueue_refine_body, (void *)c, enqueue_refine_init))) return err;
+    bfold_kernel<<<cdiv_i(B, 128), 128, 0, s>>>(L.st, B); count_launch();
+    return cudaGetLastError();
+}
+
+uint64_t fnv(uint64_t h, uint64_t v)
+{
+    for (int b = 0; b < 8; ++b) {
+        h ^= (v >> (8 * b)) & 0xff;
+        h *= 1099511628211ull;
+    }
+    return h;
 }
 
 }  // namespace
@@ -265,29 +529,16 @@ cudaError_t enqueue_hess(void *p, cudaStream_t s)
 
 using namespace sqm;
 
-// The batched general path for the matrices idx[0 .. count) of a batched
-// call; writes their statuses into st_out[idx[i]].
+// The batched path for the matrices idx[0 .. count) of a batched call;
+// writes their statuses into st_out[idx[i]].
 int batched_general(sqrtm_handle_t h, const int *idx, int count, const double *const *dA, const int64_t *n,
                     const int64_t *lda, double *const *dX, const int64_t *ldx, const sqrtm_opts &o, int *st_out)
 {
     using R = float;
     if (count <= 0) return 0;
     cudaStream_t s = h->stream;
-    // largest first: the Schur stage's CTAs are scheduled in matrix order
-    std::vector<int> ord(idx, idx + count);
-    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return n[a] > n[b]; });
     const int B = count;
-    const int nmax = (int)n[ord[0]];
-    size_t bytes;
-    {
-        Carve c(nullptr);
-        BLayout<R> L = carve_header<R>(c, B);
-        bytes = L.hdr_bytes;
-        for (int i = 0; i < B; ++i) bytes += matrix_bytes<R>(n[ord[i]]);
-        bytes += 4096;
-    }
-    if (ensure(h->bws, bytes, h)) return 7;
-    const size_t pin_need = sizeof(int) * kQrStateInts * (size_t)B + sizeof(BState) * (size_t)B + 4096;
+    const size_t pin_need = sizeof(BState) * (size_t)B + sizeof(int) * (size_t)B + 4096;
     if (h->bpin_bytes < pin_need) {
         if (h->bpin) cudaFreeHost(h->bpin);
         h->bpin = nullptr;
@@ -295,6 +546,60 @@ int batched_general(sqrtm_handle_t h, const int *idx, int count, const double *c
         if (cudaHostAlloc(&h->bpin, pin_need, cudaHostAllocDefault) != cudaSuccess) return 7;
         h->bpin_bytes = pin_need;
     }
+    // which members take Algorithm 3: every one under SQRTM_KIND_SPD, none
+    // under SQRTM_KIND_GENERAL, the bitwise symmetric ones under AUTO (one
+    // check over all matrices, read back once)
+    std::vector<int> sym(B, o.kind == SQRTM_KIND_SPD ? 1 : 0);
+    if (o.kind == SQRTM_KIND_AUTO) {
+        const size_t need = Carve::round(sizeof(BInput) * (size_t)B) + Carve::round(sizeof(int) * (size_t)B) + 512;
+        if (ensure(h->ws, need, h)) return 7;
+        Carve cw(h->ws.p);
+        BInput *din = cw.take<BInput>(B);
+        int *dflag = cw.take<int>(B);
+        std::vector<BInput> hin(B);
+        int64_t nmx = 1;
+        for (int i = 0; i < B; ++i) {
+            hin[i] = BInput{dA[idx[i]], lda[idx[i]], (int)n[idx[i]]};
+            nmx = std::max(nmx, n[idx[i]]);
+        }
+        SQM_CU(cudaMemcpyAsync(din, hin.data(), sizeof(BInput) * (size_t)B, cudaMemcpyHostToDevice, s));
+        SQM_CU(cudaMemsetAsync(dflag, 0, sizeof(int) * (size_t)B, s));
+        bsym_kernel<<<dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>(16, nmx * nmx / 4096)), B), 256, 0, s>>>(
+            din, dflag);
+        count_launch();
+        int *hflag = (int *)((char *)h->bpin + sizeof(BState) * (size_t)B);
+        SQM_CU(cudaMemcpyAsync(hflag, dflag, sizeof(int) * (size_t)B, cudaMemcpyDeviceToHost, s));
+        SQM_CU(cudaStreamSynchronize(s));
+        for (int i = 0; i < B; ++i) sym[i] = (hflag[i] == 0 && n[idx[i]] <= kJacMaxN) ? 1 : 0;
+    } else if (o.kind == SQRTM_KIND_SPD) {
+        for (int i = 0; i < B; ++i) sym[i] = n[idx[i]] <= kJacMaxN ? 1 : 0;
+    }
+    // batch order: general members by decreasing size, then symmetric ones
+    // (the Schur stage's CTAs are scheduled in matrix order)
+    std::vector<int> pos(B);
+    std::iota(pos.begin(), pos.end(), 0);
+    std::stable_sort(pos.begin(), pos.end(), [&](int a, int b) {
+        if (sym[a] != sym[b]) return sym[a] < sym[b];
+        return n[idx[a]] > n[idx[b]];
+    });
+    std::vector<int> ord(B), nord(B);
+    int Bg = 0;
+    for (int i = 0; i < B; ++i) {
+        ord[i] = idx[pos[i]];
+        nord[i] = (int)n[ord[i]];
+        if (!sym[pos[i]]) ++Bg;
+    }
+    int nmax = 1;
+    for (int i = 0; i < B; ++i) nmax = std::max(nmax, nord[i]);
+    size_t bytes;
+    {
+        Carve c(nullptr);
+        BLayout<R> L = carve_header<R>(c, B);
+        bytes = L.hdr_bytes;
+        for (int i = 0; i < B; ++i) bytes += matrix_bytes<R>(nord[i]);
+        bytes += 4096;
+    }
+    if (ensure(h->bws, bytes, h)) return 7;
     // the header, built on the host with the device offsets, then one copy
     std::vector<char> hdr;
     Carve cd(h->bws.p);
@@ -303,6 +608,7 @@ int batched_general(sqrtm_handle_t h, const int *idx, int count, const double *c
     auto host = [&](const void *dev) { return hdr.data() + ((const char *)dev - (const char *)h->bws.p); };
     SchurDesc<R> *hdesc = (SchurDesc<R> *)host(L.desc);
     HessJob<R> *hhj = (HessJob<R> *)host(L.hj);
+    JacJob *hjj = (JacJob *)host(L.jj);
     TriJob<R> *htri = (TriJob<R> *)host(L.tri);
     GemmJob<R> *hgj = (GemmJob<R> *)host(L.gj);
     ResJob *hrj = (ResJob *)host(L.rj);
@@ -312,10 +618,10 @@ int batched_general(sqrtm_handle_t h, const int *idx, int count, const double *c
     hprm->tol = o.tol;
     hprm->fixed = fixed;
     hprm->max_corr = fixed ? o.steps : o.maxit + 1;
-    const int iters = fixed ? o.steps : o.maxit + 2;
+    hprm->iters = fixed ? o.steps : o.maxit + 2;
     for (int i = 0; i < B; ++i) {
         const int m = ord[i];
-        const int64_t nm = n[m];
+        const int64_t nm = nord[i];
         const size_t nn = (size_t)nm * nm;
         cplx<R> *T = cd.take<cplx<R>>(nn), *Q = cd.take<cplx<R>>(nn), *S = cd.take<cplx<R>>(nn);
         cplx<R> *W = cd.take<cplx<R>>(nn), *Rt = cd.take<cplx<R>>(nn);
@@ -341,6 +647,7 @@ int batched_general(sqrtm_handle_t h, const int *idx, int count, const double *c
         d.status = &q->st_schur;
         htri[i] = TriJob<R>{T, S, Rt, &q->st_solve, &q->active, (int)nm};
         hhj[i] = HessJob<R>{T, Q, (R *)W, (R *)Rt, (int)nm};  // W, Rt: free until the Schur form is done
+        hjj[i] = JacJob{T, Q, (float *)W, &q->st_schur, (int)nm};  // W: free until X_0 is formed
         hin[i] = BInput{dA[m], lda[m], (int)nm};
         // products: 0 W = Q S, 1 X = 2^e Re(W Q^H), 2 W = Rhat Q, 3 Rt = Q^H W,
         // 4 W = Q Rt, 5 X += 2^e Re(W Q^H)
@@ -356,46 +663,19 @@ int batched_general(sqrtm_handle_t h, const int *idx, int count, const double *c
         hq->np = (int)(nt * nt);
     }
     SQM_CU(cudaMemcpyAsync(h->bws.p, hdr.data(), L.hdr_bytes, cudaMemcpyHostToDevice, s));
-    bnorm_kernel<<<B, kBNormThreads, 0, s>>>(L.in, L.st); count_launch();
-    bcast_kernel<R><<<dim3(std::max(1, std::min(64, nmax * nmax / 1024)), B), 256, 0, s>>>(L.in, L.st, L.desc);
-    count_launch();
-    SQM_CU(cudaGetLastError());
-    // Hessenberg reduction: one cluster per matrix, one launch per size
-    // class (the sizes are sorted, so each class is a contiguous range);
-    // the per-column kernels for sizes beyond the cluster kernel's
-    for (int i0 = 0; i0 < B;) {
-        const int nc = (int)n[ord[i0]];
-        const int cap = nc <= 64 ? 0 : nc <= 128 ? 64 : nc <= 256 ? 128 : nc <= 512 ? 256 : 512;
-        int i1 = i0;
-        while (i1 < B && (int)n[ord[i1]] > cap) ++i1;
-        cudaError_t err = launch_hessenberg_cluster_batched<R>(L.hj + i0, i1 - i0, nc, s);
-        if (err == cudaErrorNotSupported) {
-            cudaGetLastError();
-            HessCtx hc{L.desc + i0, i1 - i0, nc};
-            if (run_graph(h, 300, L.desc + i0, nc, i1 - i0, enqueue_hess<R>, &hc)) return 7;
-        } else {
-            SQM_CU(err);
-        }
-        i0 = i1;
-    }
-    SQM_CU(launch_qr_sweeps<R>(L.desc, B, nmax, (int *)h->bpin, L.qstate, s));
-    SQM_CU(launch_trisqrt_batched<R>(L.tri, B, nmax, o.blks, s));
-    bfold_kernel<<<cdiv_i(B, 128), 128, 0, s>>>(L.st, B); count_launch();
-    // X_0 = 2^e Re(Q S Q^H), rounded to FP32
-    SQM_CU(launch_cgemm_batched<R>(OP_N, OP_N, false, EPI_STORE, L.gj, B, nmax, s));
-    SQM_CU(launch_cgemm_batched<R>(OP_N, OP_H, false, EPI_REAL_TO_F64, L.gj + B, B, nmax, s));
-    // the refinement, one replayed graph per step; after each step the host
-    // reads how many matrices go on and stops when none does
-    int *h_nact = (int *)((char *)h->bpin + sizeof(int) * kQrStateInts * (size_t)B + sizeof(BState) * (size_t)B);
-    for (int k = 0; k < iters; ++k) {
-        LoopCtx lc{L.tri, L.gj, L.rj, L.st, L.prm, B, nmax, o.blks};
-        if (run_graph(h, 100000 + o.blks, L.desc, nmax, B, enqueue_refine_step<R>, &lc)) return 7;
-        SQM_CU(cudaMemcpyAsync(h_nact, &L.prm->nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
-        SQM_CU(cudaStreamSynchronize(s));
-        if (*h_nact == 0) break;
-    }
-    bfold_kernel<<<cdiv_i(B, 128), 128, 0, s>>>(L.st, B); count_launch();
-    BState *hst = (BState *)((char *)h->bpin + sizeof(int) * kQrStateInts * (size_t)B);
+    if (!h->body_stream) SQM_CU(cudaStreamCreateWithFlags(&h->body_stream, cudaStreamNonBlocking));
+    SQM_CU(allow_max_smem((const void *)bjacobi_kernel<true>));
+    SQM_CU(allow_max_smem((const void *)bjacobi_kernel<false>));
+    // one graph for the whole call, keyed by the sizes and kinds in batch
+    // order and the block size (its launches take every pointer from the
+    // header just copied)
+    Pipe pipe{L, nord.data(), B, Bg, nmax, o.blks, h->body_stream};
+    uint64_t sig = 1469598103934665603ull;
+    sig = fnv(sig, (uint64_t)Bg);
+    sig = fnv(sig, (uint64_t)o.blks);
+    for (int i = 0; i < B; ++i) sig = fnv(sig, (uint64_t)nord[i]);
+    if (run_graph(h, 400, L.desc, nmax, B, enqueue_pipeline, &pipe, sig)) return 7;
+    BState *hst = (BState *)h->bpin;
     SQM_CU(cudaMemcpyAsync(hst, L.st, sizeof(BState) * (size_t)B, cudaMemcpyDeviceToHost, s));
     SQM_CU(cudaStreamSynchronize(s));
     for (int i = 0; i < B; ++i) st_out[ord[i]] = hst[i].status;

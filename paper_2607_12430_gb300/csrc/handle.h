@@ -45,11 +45,13 @@ struct sqrtm_handle_s {
         const void *key;
         int64_t n;
         int batch;
+        uint64_t sig;  // anything else the captured launches depend on (0: nothing)
         cudaGraphExec_t exec;
         long long launches;
     };
     std::vector<Graph> graphs;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t body_stream = nullptr;  // captures the bodies of conditional nodes
     // tuning table (sqrtm_set_tuning), ascending n_max
     std::vector<sqrtm_tune_entry> tuning;
     // batched general path: device arena and pinned host buffer
@@ -143,6 +145,6 @@ inline bool spd_enabled() { return true; }
 // device memory (descriptors), so a replay stays valid while `key` (the
 // descriptor buffer) is the same allocation.  Returns 0 or 7.
 int run_graph(sqrtm_handle_t h, int tag, const void *key, int64_t n, int batch,
-              cudaError_t (*enqueue)(void *ctx, cudaStream_t s), void *ctx);
+              cudaError_t (*enqueue)(void *ctx, cudaStream_t s), void *ctx, uint64_t sig = 0);
 // drop cached graphs whose key lies in [lo, hi) (a buffer being released)
 void drop_graphs(sqrtm_handle_t h, const void *lo, const void *hi);

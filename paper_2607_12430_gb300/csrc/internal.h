@@ -182,6 +182,23 @@ cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, in
                              const int *d_state_all, cudaStream_t s, float *ms_chase = nullptr,
                              const SchurDesc<R> *d_desc_alt = nullptr, cudaStream_t side = nullptr,
                              const cudaEvent_t *qev = nullptr, int *d_sync = nullptr, int helpers = -1);
+// Inside a stream capture on s: appends a conditional WHILE node whose
+// condition is `init` at every launch of the graph and whose body is
+// captured from body(ctx, body_stream, cond) (a kernel in the body sets the
+// condition with cudaGraphSetConditional); pre(ctx, s, cond), if given, is
+// captured on s just before the node (a kernel there may set the first
+// value).  The capture on s continues after the node.
+typedef cudaError_t (*CondFn)(void *ctx, cudaStream_t st, cudaGraphConditionalHandle cond);
+cudaError_t capture_while(cudaStream_t s, cudaStream_t body_stream, unsigned init, CondFn body, void *ctx,
+                          CondFn pre = nullptr);
+// The QR rounds of a batch for capture into a graph: state initialisation,
+// a WHILE node whose body is one round (chase with one CTA per matrix,
+// window products, deferred passes, and a one-thread test of every
+// matrix's done flag; at most 256 rounds, then status 3), and the final
+// clean-up of T.  d_round: one device int of scratch.
+template <class R>
+cudaError_t enqueue_qr_sweeps_device(const SchurDesc<R> *d_desc, int batch, int nmax, int *d_round, cudaStream_t s,
+                                     cudaStream_t body_stream);
 // scratch sizes per matrix of size n: rotation log entries, window records,
 // elements of accumulated window products (one round of the QR iteration
 // stops at a sweep boundary before any of them would overflow)

@@ -1054,7 +1054,8 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
 // right rotations in log order applied to the rows of I).  Then a row
 // segment x (indices kmin .. kmin+rr-1) receiving the window's right
 // rotations becomes x U, and a column segment y receiving its left rotations
-// becomes U^H y.  One CTA per window, thread r owns row r of U.
+// becomes U^H y.  CTA x takes the windows x, x + gridDim.x, ... (one each
+// when the grid covers the round's windows); thread r owns row r of U.
 template <class R>
 __global__ void __launch_bounds__(128) qr_build_u_kernel(const SchurDesc<R> *__restrict__ descs)
 {
@@ -1065,13 +1066,14 @@ __global__ void __launch_bounds__(128) qr_build_u_kernel(const SchurDesc<R> *__r
     cplx<R> *u = reinterpret_cast<cplx<R> *>(lg + W * NB);
     const SchurDesc<R> d = descs[blockIdx.y];
     const int nwin = d.rstate[0];
-    if ((int)blockIdx.x >= nwin) return;
-    const WinRec w = d.win[blockIdx.x];
-    if (w.nsteps < 0) return;  // dense window: U written by the chase
+    for (int wi = blockIdx.x; wi < nwin; wi += gridDim.x) {
+    __syncthreads();  // the previous window's shared-memory reads are done
+    const WinRec w = d.win[wi];
+    if (w.nsteps < 0) continue;  // dense window: U written by the chase
     const int rr = w.rr, r = threadIdx.x;
     if (rr > D::RR || rr < 2) {
         if (r == 0) atomicExch(d.status, 7);
-        return;
+        continue;
     }
     for (int e = threadIdx.x; e < W * NB; e += blockDim.x) lg[e] = d.log[w.start + e];
     if (r < rr)
@@ -1101,6 +1103,7 @@ __global__ void __launch_bounds__(128) qr_build_u_kernel(const SchurDesc<R> *__r
     for (int e = threadIdx.x; e < rr * rr; e += blockDim.x) {
         const int q = e % rr, c = e / rr;  // U(q, c), column-major
         U[e] = u[q * ULD + c];
+    }
     }
 }
 
@@ -1408,6 +1411,81 @@ cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, in
     qr_finish_kernel<R><<<dim3(64, batch), 256, 0, s>>>(d_desc); count_launch();
     return cudaGetLastError();
 }
+
+// Device-driven rounds for a batch (every launch one CTA per matrix, no
+// cooperative chase): after each round a single thread reads every
+// matrix's done flag and sets the WHILE condition of the enclosing graph;
+// after max_rounds rounds the unfinished matrices get status 3.
+template <class R>
+__global__ void qr_round_decide_kernel(const SchurDesc<R> *__restrict__ descs, int batch, int *round,
+                                       cudaGraphConditionalHandle cond, int max_rounds)
+{
+    __shared__ int s_open;
+    if (threadIdx.x == 0) s_open = 0;
+    __syncthreads();
+    for (int b = threadIdx.x; b < batch; b += blockDim.x)
+        if (!descs[b].state[2]) atomicOr(&s_open, 1);
+    __syncthreads();
+    const int r = *round + 1;
+    const bool more = s_open && r < max_rounds;
+    if (s_open && !more)
+        for (int b = threadIdx.x; b < batch; b += blockDim.x)
+            if (!descs[b].state[2]) atomicExch(descs[b].status, 3);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *round = r;
+        cudaGraphSetConditional(cond, more ? 1u : 0u);
+    }
+}
+
+namespace {
+template <class R>
+struct RoundCtx {
+    const SchurDesc<R> *desc;
+    int batch, nmax, *round;
+};
+
+template <class R>
+cudaError_t enqueue_round(void *p, cudaStream_t s, cudaGraphConditionalHandle cond)
+{
+    const RoundCtx<R> *c = (const RoundCtx<R> *)p;
+    constexpr int RRMAX = QrDims<R>::RR;
+    const int rpc = qr_rows_per_cta<R>(c->nmax, c->batch);
+    const size_t ubytes = 2 * (size_t)RRMAX * RRMAX * sizeof(cplx<R>);
+    const size_t mbytes = (size_t)std::max(c->nmax, 1) * sizeof(int);
+    const size_t rows_bytes = (size_t)rpc * c->nmax * sizeof(cplx<R>) + ubytes + mbytes;
+    const size_t cols_bytes = (size_t)rpc * (c->nmax + 1) * sizeof(cplx<R>) + ubytes + mbytes;
+    const int ctas = (int)cdiv_i(c->nmax, rpc);
+    // windows of a round: at most the window capacity of the largest matrix
+    const int ubx = (int)std::min<int64_t>(qr_win_capacity(c->nmax), 64);
+    qr_chase_kernel<R, false><<<c->batch, kQrThreads, QrDims<R>::chase_smem, s>>>(c->desc, 0); count_launch();
+    qr_build_u_kernel<R><<<dim3(ubx, c->batch), 128, QrDims<R>::build_smem, s>>>(c->desc); count_launch();
+    qr_apply_rows_kernel<R><<<dim3(2 * ctas, c->batch), 256, rows_bytes, s>>>(c->desc, rpc, ctas); count_launch();
+    qr_apply_cols_kernel<R><<<dim3(ctas, c->batch), 256, cols_bytes, s>>>(c->desc, rpc); count_launch();
+    qr_round_decide_kernel<R><<<1, 256, 0, s>>>(c->desc, c->batch, c->round, cond, 256); count_launch();
+    return cudaGetLastError();
+}
+}  // namespace
+
+template <class R>
+cudaError_t enqueue_qr_sweeps_device(const SchurDesc<R> *d_desc, int batch, int nmax, int *d_round, cudaStream_t s,
+                                     cudaStream_t body_stream)
+{
+    if (batch <= 0) return cudaSuccess;
+    cudaError_t err;
+    if ((err = allow_max_smem((const void *)qr_chase_kernel<R, false>))) return err;
+    if ((err = allow_max_smem((const void *)qr_build_u_kernel<R>))) return err;
+    if ((err = allow_max_smem((const void *)qr_apply_rows_kernel<R>))) return err;
+    if ((err = allow_max_smem((const void *)qr_apply_cols_kernel<R>))) return err;
+    qr_state_init_kernel<R><<<1, 256, 0, s>>>(d_desc, batch); count_launch();
+    if ((err = cudaMemsetAsync(d_round, 0, sizeof(int), s))) return err;
+    RoundCtx<R> ctx{d_desc, batch, nmax, d_round};
+    if ((err = capture_while(s, body_stream, 1u, enqueue_round<R>, &ctx))) return err;
+    qr_finish_kernel<R><<<dim3(64, batch), 256, 0, s>>>(d_desc); count_launch();
+    return cudaGetLastError();
+}
+
+template cudaError_t enqueue_qr_sweeps_device<float>(const SchurDesc<float> *, int, int, int *, cudaStream_t, cudaStream_t);
 
 template cudaError_t launch_qr_sweeps<float>(const SchurDesc<float> *, int, int, int *, const int *, cudaStream_t, float *,
                                              const SchurDesc<float> *, cudaStream_t, const cudaEvent_t *, int *, int);
