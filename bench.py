@@ -287,6 +287,43 @@ def leg_c3(args, mp, torch, flush, peaks):
             "input_prep_s": gen_s}
 
 
+def leg_batch(args, mp, torch, dist, dev, flush):
+    """The batch workload: 2048 matrices, n ~ U{16..256}, even items SPD
+    (lambda log-uniform in [1e-2, 1e2]), odd items 2I + G/sqrt(n), with the
+    default stopping test (tol 1e-12).  One sqrtm_mixed_batched call per
+    step (one graph launch); under torchrun every rank solves its LPT share
+    (by n^3) on its own GPU and the step time is the slowest rank's."""
+    items = synth.batch_case(count=2048, seed=synth.BASE_SEED + 3)
+    ws = dist.get_world_size() if dist else 1
+    rank = dist.get_rank() if dist else 0
+    owner, load = mp.batch_partition([it[1].shape[0] for it in items], ws)
+    mine = [i for i, o in enumerate(owner) if o == rank]
+    As = [torch.from_numpy(np.ascontiguousarray(items[i][1])).to(dev) for i in mine]
+
+    def run():
+        return mp.sqrtm_mixed_batched(As)
+
+    run()
+    if dist:
+        dist.barrier()
+    reps = max(2, min(args.steps, 5))
+    ts, (Xs, st) = _timed_calls(torch, run, reps, flush)
+    ms = statistics.mean(ts)
+    phases = mp.batched_phases()
+    if dist:
+        ms = slowest_rank_ms(dist, ms, dev)
+    res = max(((X @ X - A).norm() / A.norm()).item() for X, A in zip(Xs, As)) if As else 0.0
+    return {"workload": "2048 matrices, n ~ U{16..256}; even items SPD lambda=10^U(-2,2), odd 2I+G/sqrt(n); "
+                        "seed 20260712+3; default tol 1e-12",
+            "matrices": len(items), "matrices_this_rank": len(mine), "ms": ms,
+            "matrices_per_s": len(items) / (ms / 1e3), "timed_calls": reps,
+            "sharding": {"ranks": ws, "rule": "LPT by n^3", "max_over_mean_load": max(load) / (sum(load) / ws)},
+            "status_counts_this_rank": {str(k): st.count(k) for k in sorted(set(st))},
+            "max_rel_residual_this_rank": res, "phases_ms_this_rank": phases["ms"],
+            "spectral_members_this_rank": phases["matrices"] - phases["general"],
+            "graph_launches_per_call": 1}
+
+
 def leg_set_iii(args, mp, torch, flush, fp32_peak_tflops):
     """Table 1 set III (U(0,1) entries plus the shift, nonsymmetric, n = 4096):
     the FP64 Schur method on the same GPU (timed once; its result is the
@@ -504,10 +541,13 @@ def run_ours(args):
         "clocks": clocks,
         "gpu_launches": launches,
     }
-    if rank == 0 and not args.no_legs:
-        # the n >= 2048 comparisons (after the headline's timed region)
-        line["legs"] = {"c3": leg_c3(args, mp, torch, flush, peaks),
-                        "set_iii": leg_set_iii(args, mp, torch, flush, fp32_peak_tflops)}
+    if not args.no_legs:
+        # after the headline's timed region: the batch (every rank, sharded),
+        # then the n >= 2048 comparisons (rank 0)
+        batch = leg_batch(args, mp, torch, dist, dev, flush)
+        if rank == 0:
+            line["legs"] = {"batch": batch, "c3": leg_c3(args, mp, torch, flush, peaks),
+                            "set_iii": leg_set_iii(args, mp, torch, flush, fp32_peak_tflops)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -693,15 +733,24 @@ def run_batch_suite(args):
     items = synth.batch_case(count=2048, seed=synth.BASE_SEED + 3)
     As = [torch.from_numpy(np.ascontiguousarray(it[1])).cuda() for it in items]
     sizes = [A.shape[0] for A in As]
-    modes = [("batched", None), ("per-matrix", "0")]
-    for name, env in modes:
+    # batched: symmetric members through the Jacobi spectral stage
+    # (Algorithm 3); batched-alg2: every member through Algorithm 2;
+    # per-matrix: one call per matrix on 12 worker streams
+    # batched: the handle's tuning table decides, per size, whether symmetric
+    # members take the spectral stage; batched-alg3: every symmetric member
+    # through it (the built-in rule, table cleared)
+    modes = [("batched", None, mp.KIND_AUTO), ("batched-alg3", None, mp.KIND_AUTO),
+             ("batched-alg2", None, mp.KIND_GENERAL), ("per-matrix", "0", mp.KIND_AUTO)]
+    shipped = mp.get_tuning()
+    for name, env, kind in modes:
+        mp.set_tuning([] if name == "batched-alg3" else shipped)
         old = os.environ.get("SQRTM_BATCH_MAXN")
         if env is None:
             os.environ.pop("SQRTM_BATCH_MAXN", None)
         else:
             os.environ["SQRTM_BATCH_MAXN"] = env
         try:
-            Xs, st = mp.sqrtm_mixed_batched(As)
+            Xs, st = mp.sqrtm_mixed_batched(As, kind=kind)
             torch.cuda.synchronize()
             ts = []
             for _ in range(max(1, args.steps)):
@@ -709,7 +758,7 @@ def run_batch_suite(args):
                 e_ = torch.cuda.Event(enable_timing=True)
                 l0 = mp.kernel_launches()
                 s_.record()
-                Xs, st = mp.sqrtm_mixed_batched(As)
+                Xs, st = mp.sqrtm_mixed_batched(As, kind=kind)
                 e_.record()
                 torch.cuda.synchronize()
                 ts.append(s_.elapsed_time(e_))
@@ -719,13 +768,15 @@ def run_batch_suite(args):
                 os.environ.pop("SQRTM_BATCH_MAXN", None)
             else:
                 os.environ["SQRTM_BATCH_MAXN"] = old
+        phases = mp.batched_phases() if name != "per-matrix" else None
+        mp.set_tuning(shipped)
         res = max(((X @ X - A).norm() / A.norm()).item() for X, A in zip(Xs, As))
         ms = statistics.mean(ts)
         print(json.dumps({"suite": "batch", "mode": name, "matrices": len(As), "n_range": [min(sizes), max(sizes)],
                           "sum_n3": float(sum(float(n) ** 3 for n in sizes)), "ms": ms,
                           "matrices_per_s": len(As) / (ms / 1e3), "max_rel_residual": res,
                           "status_counts": {str(k): st.count(k) for k in sorted(set(st))},
-                          "gpu_launches": launches}), flush=True)
+                          "gpu_launches": launches, "phases": phases}), flush=True)
     return 0
 
 

@@ -140,9 +140,14 @@ typedef struct {
  *   trisqrt_cutoff 0: the blocked triangular square root (Sec. 2.2.1);
  *                 >= 64: the recursive splitting of Sec. 2.2.1 (S_11, S_22
  *                 recursively, S_12 from a Sylvester solve) down to blocks
- *                 of at most this size, which take the blocked method.
+ *                 of at most this size, which take the blocked method;
+ *   batched_spd   sqrtm_mixed_batched with SQRTM_KIND_AUTO: 1 sends the
+ *                 bitwise symmetric matrices of these sizes (n <= 256) that
+ *                 take the batched path through its spectral stage
+ *                 (Algorithm 3: FP32 Jacobi decomposition), 0 through the
+ *                 complex Schur stage of Algorithm 2 with the other members.
  * Without a table the built-in values apply: blks 32, helpers -1, batched
- * for n <= 256, SQRTM_PREC_FP32, cutoff 0. */
+ * for n <= 256, SQRTM_PREC_FP32, cutoff 0, batched_spd 1. */
 typedef struct {
     int64_t n_max;
     int blks;
@@ -150,7 +155,7 @@ typedef struct {
     int batched;
     int spd_precision;
     int trisqrt_cutoff;
-    int reserved;  /* 0 */
+    int batched_spd;
 } sqrtm_tune_entry;
 
 #define SQRTM_MAX_TUNE 32
@@ -309,6 +314,16 @@ SQRTM_API int sqrtm_mixed_batched(sqrtm_handle_t handle, int batch, const double
                         const int64_t *n, const int64_t *lda, double tol,
                         double *const *dX, const int64_t *ldx, const sqrtm_opts *opts,
                         int *status);
+
+/* Phase times of the last batched-path graph on this handle (diagnostic,
+ * device clock, ms): [0] norms, scaling and Hessenberg reductions, [1] QR
+ * rounds of the general members, [2] Jacobi decompositions of the
+ * symmetric members, [3] triangular square roots and X_0, [4] refinement
+ * loop.  Copies min(cap, 5) values into ms (HOST), the number of matrices
+ * the batched path took into *count and how many of them took Algorithm 2
+ * into *general (either may be NULL).  Returns 5, or -1 / -2 (NULL handle /
+ * ms). */
+SQRTM_API int sqrtm_batched_phases(sqrtm_handle_t handle, double *ms, int cap, int *count, int *general);
 
 /* Split a batch of independent matrices over `parts` GPUs (one process per
  * GPU, each calling sqrtm_mixed_batched on its share; no data crosses GPUs,

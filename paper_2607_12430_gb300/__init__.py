@@ -55,7 +55,7 @@ class Opts(ctypes.Structure):
 class TuneEntry(ctypes.Structure):
     _fields_ = [("n_max", ctypes.c_int64), ("blks", ctypes.c_int), ("qr_helpers", ctypes.c_int),
                 ("batched", ctypes.c_int), ("spd_precision", ctypes.c_int), ("trisqrt_cutoff", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("batched_spd", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -105,6 +105,7 @@ _SIGS = {
     "sqrtm_factors_destroy": ([_P], _I),
     "sqrtm_mixed_batched": ([_P, _I, _P, _P, _P, _D, _P, _P, ctypes.POINTER(Opts), _P], _I),
     "sqrtm_batch_partition": ([_I, _P, _I, _P, _P], _I),
+    "sqrtm_batched_phases": ([_P, _P, _I, _P, _P], _I),
     "sqrtm_status_string": ([_I], ctypes.c_char_p),
     "sqrtm_kernel_launches": ([], _L),
     "sqrtm_last_error": ([_P], ctypes.c_char_p),
@@ -242,7 +243,8 @@ def _ptr(t):
 
 def set_tuning(entries):
     """Install a tuning table (list of dicts with n_max, blks, qr_helpers,
-    batched, spd_precision and optionally trisqrt_cutoff; ascending n_max)
+    batched, spd_precision and optionally trisqrt_cutoff and batched_spd;
+    ascending n_max)
     on this stream's handle; an empty list clears it."""
     rc = lib().sqrtm_set_tuning(handle(), _tune_array(entries), len(entries))
     if rc:
@@ -261,14 +263,14 @@ def get_tuning():
     cnt = lib().sqrtm_get_tuning(handle(), arr, MAX_TUNE)
     return [{"n_max": arr[i].n_max, "blks": arr[i].blks, "qr_helpers": arr[i].qr_helpers,
              "batched": arr[i].batched, "spd_precision": arr[i].spd_precision,
-             "trisqrt_cutoff": arr[i].trisqrt_cutoff} for i in range(cnt)]
+             "trisqrt_cutoff": arr[i].trisqrt_cutoff, "batched_spd": arr[i].batched_spd} for i in range(cnt)]
 
 
 def _tune_array(entries):
     arr = (TuneEntry * max(1, len(entries)))()
     for i, e in enumerate(entries):
         arr[i] = TuneEntry(int(e["n_max"]), int(e["blks"]), int(e["qr_helpers"]), int(e["batched"]),
-                           int(e["spd_precision"]), int(e.get("trisqrt_cutoff", 0)), 0)
+                           int(e["spd_precision"]), int(e.get("trisqrt_cutoff", 0)), int(e.get("batched_spd", 1)))
     return arr
 
 
@@ -467,6 +469,17 @@ def sqrtm_mixed_batched(As, tol=1e-12, outs=None, raise_on_error=False, **kw):
     if rc < 0 or (rc and raise_on_error):
         raise SqrtmError(rc, "sqrtm_mixed_batched")
     return Xs, list(st)
+
+
+def batched_phases():
+    """Phase times (ms, device clock) of the last batched-path graph on this
+    stream's handle, with the number of matrices it took and how many of
+    them were general."""
+    ms = (ctypes.c_double * 5)()
+    cnt, gen = ctypes.c_int(), ctypes.c_int()
+    lib().sqrtm_batched_phases(handle(), ctypes.cast(ms, _P), 5, ctypes.byref(cnt), ctypes.byref(gen))
+    names = ["prepare_and_hessenberg", "qr_rounds", "jacobi", "trisqrt_x0", "refinement"]
+    return {"ms": dict(zip(names, list(ms))), "matrices": cnt.value, "general": gen.value}
 
 
 def batch_partition(sizes, parts):

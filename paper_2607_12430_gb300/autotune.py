@@ -20,7 +20,11 @@ the SPD path):
   recursive splitting of Sec. 2.2.1 down to blocks of 256 or 512 (n >= 512);
 * batched -- for sqrtm_mixed_batched, whether matrices of the bucket's size
   go through the batched general path or per-matrix calls (a batch of
-  `batch_count` matrices timed both ways).
+  `batch_count` matrices timed both ways);
+* batched_spd -- for sqrtm_mixed_batched (n <= 256), whether symmetric
+  matrices of the bucket's size take the batched path's spectral stage
+  (Algorithm 3) or its complex Schur stage (Algorithm 2): a batch of
+  `batch_count` SPD matrices timed both ways with the default tolerance.
 
 The choice functions are pure (measurements in, table out) so that they are
 testable without a GPU; `autotune()` runs the measurements and `save` /
@@ -78,6 +82,10 @@ def build_table(measured):
             e["batched"] = int(m["batched"] <= m["per_matrix"])
         else:
             e["batched"] = int(m["n"] <= 256)
+        if "batched_spectral" in m and "batched_schur" in m:
+            e["batched_spd"] = int(m["batched_spectral"] <= m["batched_schur"])
+        else:
+            e["batched_spd"] = 1
         table.append(e)
     return table
 
@@ -145,6 +153,15 @@ def measure_bucket(n, reps=3, batch_count=32, seed=20260712, log=None):
             m["spd_err"][p] = ((X - X64).norm() / X64.norm()).item() if info["status"] == 0 else np.inf
             m["spd"][p] = _timer(lambda: mp.sqrtm_mixed(S, kind=mp.KIND_SPD, precision=p, steps=SPD_STEPS,
                                                         raise_on_error=False), reps)
+        if n <= 256:
+            Ss = [torch.from_numpy(_spd(n, seed + 2000 + i)).cuda() for i in range(batch_count)]
+            mp.set_tuning([{"n_max": 1 << 40, "blks": 32, "qr_helpers": -1, "batched": 1, "spd_precision": 0,
+                            "batched_spd": 1}])
+            m["batched_spectral"] = _timer(lambda: mp.sqrtm_mixed_batched(Ss), reps)
+            mp.set_tuning([{"n_max": 1 << 40, "blks": 32, "qr_helpers": -1, "batched": 1, "spd_precision": 0,
+                            "batched_spd": 0}])
+            m["batched_schur"] = _timer(lambda: mp.sqrtm_mixed_batched(Ss), reps)
+            mp.set_tuning([])
         if n <= 1024:
             As = [torch.from_numpy(_general(n, seed + 1000 + i)).cuda() for i in range(batch_count)]
             old = os.environ.get("SQRTM_BATCH_MAXN")

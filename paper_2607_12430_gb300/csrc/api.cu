@@ -216,7 +216,7 @@ extern "C" int sqrtm_set_tuning(sqrtm_handle_t h, const sqrtm_tune_entry *table,
         if (t.n_max < 1 || (i > 0 && t.n_max <= table[i - 1].n_max)) return -4;
         if (t.blks < 1 || t.blks > 32 || t.qr_helpers < -1 || t.qr_helpers > 24) return -4;
         if ((t.batched != 0 && t.batched != 1) || t.spd_precision < 0 || t.spd_precision > 3) return -4;
-        if (t.trisqrt_cutoff < 0 || t.reserved != 0) return -4;
+        if (t.trisqrt_cutoff < 0 || (t.batched_spd != 0 && t.batched_spd != 1)) return -4;
     }
     h->tuning.assign(table, table + count);
     for (auto *w : h->workers) w->tuning = h->tuning;
@@ -833,6 +833,16 @@ static int ensure_workers(sqrtm_handle_t h, int count)
 // Longest-processing-time partition of a batch over `parts` workers (GPUs):
 // matrices by decreasing cost n^3 (ties: lower index first), each to the
 // part with the smallest load so far (ties: lowest part index).
+extern "C" int sqrtm_batched_phases(sqrtm_handle_t h, double *ms, int cap, int *count, int *general)
+{
+    if (!h) return -1;
+    if (cap > 0 && !ms) return -2;
+    for (int q = 0; q < cap && q < kBatchPhases; ++q) ms[q] = h->bphase_ms[q];
+    if (count) *count = h->bphase_count;
+    if (general) *general = h->bphase_general;
+    return kBatchPhases;
+}
+
 extern "C" int sqrtm_batch_partition(int batch, const int64_t *n, int parts, int *owner, double *load)
 {
     if (batch < 0) return -1;

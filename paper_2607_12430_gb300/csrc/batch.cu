@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "handle.h"
+#include "tc_common.cuh"
 
 namespace sqm {
 
@@ -127,6 +128,7 @@ __global__ void __launch_bounds__(kJacThreads) bjacobi_kernel(const JacJob *__re
     extern __shared__ __align__(16) float jsm[];
     __shared__ float s_c[kJacMaxN / 2], s_s[kJacMaxN / 2];
     __shared__ int s_p[kJacMaxN / 2], s_q[kJacMaxN / 2];
+    __shared__ int s_col[kJacMaxN + 1];  // packed offset of column j: P(i, j) = P[i + s_col[j]], i >= j
     __shared__ float red[kJacThreads / 32];
     __shared__ float s_floor;
     __shared__ int s_rot;
@@ -141,11 +143,13 @@ __global__ void __launch_bounds__(kJacThreads) bjacobi_kernel(const JacJob *__re
     float *P = jsm;
     const int np = n * (n + 1) / 2;
     float *V = VSMEM ? jsm + ((np + 3) & ~3) : J.Vw;
+    for (int j = tid; j <= n; j += nt) s_col[j] = j * (2 * n - j - 1) / 2;
+    __syncthreads();
     float ss = 0.0f;
     for (int e = tid; e < n * n; e += nt) {
         const int i = e % n, j = e / n;
         const float a = J.T[e].x;
-        if (i >= j) P[jac_idx(i, j, n)] = a;
+        if (i >= j) P[i + s_col[j]] = a;
         ss = fmaf(a, a, ss);
         V[e] = (i == j) ? 1.0f : 0.0f;
     }
@@ -159,7 +163,11 @@ __global__ void __launch_bounds__(kJacThreads) bjacobi_kernel(const JacJob *__re
     }
     __syncthreads();
     const int N = n + (n & 1), H = N / 2;
-    const float eps = 1.1920929e-7f;  // 2^-23
+    const int ntri = H * (H + 1) / 2;  // blocks (k, l), l <= k
+    const float eps = 1.1920929e-7f;   // 2^-23
+    // this thread's first block: (k0, l0) with k0 (k0 + 1) / 2 + l0 = tid
+    int k0 = 0, l0 = tid;
+    while (l0 > k0) { l0 -= k0 + 1; ++k0; }
     bool conv = false;
     for (int sw = 0; sw < kJacSweeps && !conv; ++sw) {
         if (tid == 0) s_rot = 0;
@@ -172,13 +180,19 @@ __global__ void __launch_bounds__(kJacThreads) bjacobi_kernel(const JacJob *__re
                 int q = max(a, b);
                 float c = 1.0f, sn = 0.0f;
                 if (q < n) {
-                    const float app = P[jac_idx(p, p, n)], aqq = P[jac_idx(q, q, n)], apq = P[jac_idx(q, p, n)];
+                    const float app = P[p + s_col[p]], aqq = P[q + s_col[q]], apq = P[q + s_col[p]];
                     const float aa = fabsf(apq);
                     if (apq != 0.0f && aa > eps * sqrtf(fabsf(app * aqq)) && aa > s_floor) {
-                        const float th = (aqq - app) / (2.0f * apq);
-                        const float t = fabsf(th) > 1e18f ? 0.5f / th
-                                                         : copysignf(1.0f, th) / (fabsf(th) + sqrtf(1.0f + th * th));
-                        c = 1.0f / sqrtf(1.0f + t * t);
+                        // t = tan of the angle that zeroes a_pq: with d = a_qq - a_pp and
+                        // e = 2 a_pq, t = sign(d) e / (|d| + sqrt(d^2 + e^2)) (the root of
+                        // t^2 + 2 t d / e - 1 = 0 of modulus <= 1); c = 1 / sqrt(1 + t^2)
+                        const float d = aqq - app, e2 = 2.0f * apq;
+                        const float h2 = fmaf(d, d, e2 * e2);
+                        const float t = copysignf(1.0f, d) * e2 / (fabsf(d) + sqrtf(h2));
+                        // 1 / sqrt(v) refined by one Newton step with fused multiply-adds,
+                        // so that c^2 + s^2 = 1 to rounding (every rotation is orthogonal)
+                        const float v = fmaf(t, t, 1.0f), y0 = rsqrtf(v);
+                        c = fmaf(0.5f * y0, fmaf(-(v * y0), y0, 1.0f), y0);
                         sn = t * c;
                         s_rot = 1;
                     }
@@ -191,41 +205,44 @@ __global__ void __launch_bounds__(kJacThreads) bjacobi_kernel(const JacJob *__re
                 s_s[tid] = sn;
             }
             __syncthreads();
-            auto at = [&](int i, int j) -> float {
-                if (i < 0 || j < 0) return 0.0f;
-                return i >= j ? P[jac_idx(i, j, n)] : P[jac_idx(j, i, n)];
-            };
-            auto put = [&](int i, int j, float v) {
-                if (i >= j) P[jac_idx(i, j, n)] = v;
-                else P[jac_idx(j, i, n)] = v;
-            };
-            for (int e = tid; e < H * H; e += nt) {
-                const int k = e / H, l = e % H;
-                if (l > k) continue;
+            // A <- J^T A J as 2 x 2 blocks over the pairs k >= l (triangular
+            // enumeration, each thread advancing nt blocks at a time)
+            for (int k = k0, l = l0, e = tid; e < ntri;) {
                 const float sk = s_s[k], sl = s_s[l];
-                if (sk == 0.0f && sl == 0.0f) continue;
-                const float ck = s_c[k], cl = s_c[l];
-                const int pk = s_p[k], qk = s_q[k], pl = s_p[l], ql = s_q[l];
-                const float b00 = at(pk, pl), b01 = at(pk, ql), b10 = at(qk, pl), b11 = at(qk, ql);
-                const float r00 = ck * b00 - sk * b10, r01 = ck * b01 - sk * b11;
-                const float r10 = sk * b00 + ck * b10, r11 = sk * b01 + ck * b11;
-                const float c00 = cl * r00 - sl * r01, c01 = sl * r00 + cl * r01;
-                const float c10 = cl * r10 - sl * r11, c11 = sl * r10 + cl * r11;
-                if (k == l) {
-                    P[jac_idx(pk, pk, n)] = c00;
-                    if (qk >= 0) {
-                        P[jac_idx(qk, pk, n)] = c10;
-                        P[jac_idx(qk, qk, n)] = c11;
+                if (sk != 0.0f || sl != 0.0f) {
+                    const float ck = s_c[k], cl = s_c[l];
+                    const int pk = s_p[k], qk = s_q[k], pl = s_p[l], ql = s_q[l];
+                    // entry (i, j) of the block lives at the packed (max, min)
+                    const int i00 = pk >= pl ? pk + s_col[pl] : pl + s_col[pk];
+                    const int i01 = ql < 0 ? -1 : (pk >= ql ? pk + s_col[ql] : ql + s_col[pk]);
+                    const int i10 = qk < 0 ? -1 : (qk >= pl ? qk + s_col[pl] : pl + s_col[qk]);
+                    const int i11 = (qk < 0 || ql < 0) ? -1 : (qk >= ql ? qk + s_col[ql] : ql + s_col[qk]);
+                    const float b00 = P[i00];
+                    const float b01 = i01 >= 0 ? P[i01] : 0.0f;
+                    const float b10 = i10 >= 0 ? P[i10] : 0.0f;
+                    const float b11 = i11 >= 0 ? P[i11] : 0.0f;
+                    const float r00 = ck * b00 - sk * b10, r01 = ck * b01 - sk * b11;
+                    const float r10 = sk * b00 + ck * b10, r11 = sk * b01 + ck * b11;
+                    const float c00 = cl * r00 - sl * r01, c01 = sl * r00 + cl * r01;
+                    const float c10 = cl * r10 - sl * r11, c11 = sl * r10 + cl * r11;
+                    P[i00] = c00;
+                    if (k == l) {
+                        if (i10 >= 0) {  // diagonal block: (q, p) and (q, q); (p, q) is the same entry as (q, p)
+                            P[i10] = c10;
+                            P[i11] = c11;
+                        }
+                    } else {
+                        if (i01 >= 0) P[i01] = c01;
+                        if (i10 >= 0) P[i10] = c10;
+                        if (i11 >= 0) P[i11] = c11;
                     }
-                } else {
-                    put(pk, pl, c00);
-                    if (ql >= 0) put(pk, ql, c01);
-                    if (qk >= 0) put(qk, pl, c10);
-                    if (qk >= 0 && ql >= 0) put(qk, ql, c11);
                 }
+                e += nt;
+                l += nt;
+                while (l > k) { l -= k + 1; ++k; }
             }
             for (int e = tid; e < H * n; e += nt) {
-                const int k = e / n, i = e % n;
+                const int k = e / n, i = e - k * n;
                 const float sk = s_s[k];
                 if (sk == 0.0f) continue;
                 const float ck = s_c[k];
@@ -243,8 +260,15 @@ __global__ void __launch_bounds__(kJacThreads) bjacobi_kernel(const JacJob *__re
     for (int e = tid; e < n * n; e += nt) {
         const int i = e % n, j = e / n;
         J.Q[e] = cplx<float>{V[e], 0.0f};
-        J.T[e] = cplx<float>{i == j ? P[jac_idx(i, i, n)] : 0.0f, 0.0f};
+        J.T[e] = cplx<float>{i == j ? P[i + s_col[i]] : 0.0f, 0.0f};
     }
+}
+
+// phase boundary of a batched call: the device clock at this point of the
+// graph (one thread)
+__global__ void bstamp_kernel(unsigned long long *stamps, int i)
+{
+    stamps[i] = globaltimer_ns();
 }
 
 // flag[b] = 1 when matrix b is not bitwise symmetric
@@ -394,6 +418,7 @@ struct BLayout {
     BInput *in;
     BParams *prm;
     int *qstate;
+    unsigned long long *stamps;  // kBatchPhases + 1 phase boundaries (device clock, ns)
     size_t hdr_bytes;
 };
 
@@ -411,6 +436,7 @@ BLayout<R> carve_header(Carve &c, int batch)
     L.in = c.take<BInput>(batch);
     L.prm = c.take<BParams>(1);
     L.qstate = c.take<int>(kQrStateInts * (size_t)batch);
+    L.stamps = c.take<unsigned long long>(kBatchPhases + 1);
     L.hdr_bytes = Carve::round(c.off);
     return L;
 }
@@ -471,6 +497,7 @@ cudaError_t enqueue_pipeline(void *p, cudaStream_t s)
     const BLayout<R> &L = c->L;
     const int B = c->B, Bg = c->Bg, nmax = c->nmax;
     cudaError_t err;
+    bstamp_kernel<<<1, 1, 0, s>>>(L.stamps, 0); count_launch();
     bnorm_kernel<<<B, kBNormThreads, 0, s>>>(L.in, L.st); count_launch();
     bcast_kernel<R><<<dim3(std::max(1, std::min(64, nmax * nmax / 1024)), B), 256, 0, s>>>(L.in, L.st, L.desc);
     count_launch();
@@ -490,8 +517,10 @@ cudaError_t enqueue_pipeline(void *p, cudaStream_t s)
         if (err) return err;
         i0 = i1;
     }
+    bstamp_kernel<<<1, 1, 0, s>>>(L.stamps, 1); count_launch();
     if (Bg > 0 && (err = enqueue_qr_sweeps_device<R>(L.desc, Bg, c->nord[0], &L.prm->round, s, c->body_stream)))
         return err;
+    bstamp_kernel<<<1, 1, 0, s>>>(L.stamps, 2); count_launch();
     // symmetric members: Jacobi, V in global memory above kJacVsmemMaxN
     for (int i0 = Bg; i0 < B;) {
         const bool vs = c->nord[i0] <= kJacVsmemMaxN;
@@ -504,14 +533,17 @@ cudaError_t enqueue_pipeline(void *p, cudaStream_t s)
         if ((err = cudaGetLastError())) return err;
         i0 = i1;
     }
+    bstamp_kernel<<<1, 1, 0, s>>>(L.stamps, 3); count_launch();
     if ((err = launch_trisqrt_batched<R>(L.tri, B, nmax, c->blks, s))) return err;
     bfold_kernel<<<cdiv_i(B, 128), 128, 0, s>>>(L.st, B); count_launch();
     // X_0 = 2^e Re(Q S Q^H), rounded to FP32
     if ((err = launch_cgemm_batched<R>(OP_N, OP_N, false, EPI_STORE, L.gj, B, nmax, s))) return err;
     if ((err = launch_cgemm_batched<R>(OP_N, OP_H, false, EPI_REAL_TO_F64, L.gj + B, B, nmax, s))) return err;
+    bstamp_kernel<<<1, 1, 0, s>>>(L.stamps, 4); count_launch();
     // the refinement loop
     if ((err = capture_while(s, c->body_stream, 0u, enqueue_refine_body, (void *)c, enqueue_refine_init))) return err;
     bfold_kernel<<<cdiv_i(B, 128), 128, 0, s>>>(L.st, B); count_launch();
+    bstamp_kernel<<<1, 1, 0, s>>>(L.stamps, 5); count_launch();
     return cudaGetLastError();
 }
 
@@ -538,7 +570,8 @@ int batched_general(sqrtm_handle_t h, const int *idx, int count, const double *c
     if (count <= 0) return 0;
     cudaStream_t s = h->stream;
     const int B = count;
-    const size_t pin_need = sizeof(BState) * (size_t)B + sizeof(int) * (size_t)B + 4096;
+    const size_t pin_need = sizeof(BState) * (size_t)B + sizeof(int) * (size_t)B +
+                            sizeof(unsigned long long) * (kBatchPhases + 1) + 4096;
     if (h->bpin_bytes < pin_need) {
         if (h->bpin) cudaFreeHost(h->bpin);
         h->bpin = nullptr;
@@ -570,7 +603,11 @@ int batched_general(sqrtm_handle_t h, const int *idx, int count, const double *c
         int *hflag = (int *)((char *)h->bpin + sizeof(BState) * (size_t)B);
         SQM_CU(cudaMemcpyAsync(hflag, dflag, sizeof(int) * (size_t)B, cudaMemcpyDeviceToHost, s));
         SQM_CU(cudaStreamSynchronize(s));
-        for (int i = 0; i < B; ++i) sym[i] = (hflag[i] == 0 && n[idx[i]] <= kJacMaxN) ? 1 : 0;
+        for (int i = 0; i < B; ++i) {
+            const sqrtm_tune_entry *t = tune_for(h, n[idx[i]]);
+            const bool spectral = t ? t->batched_spd == 1 : true;  // the tuning table's choice, else Algorithm 3
+            sym[i] = (hflag[i] == 0 && n[idx[i]] <= kJacMaxN && spectral) ? 1 : 0;
+        }
     } else if (o.kind == SQRTM_KIND_SPD) {
         for (int i = 0; i < B; ++i) sym[i] = n[idx[i]] <= kJacMaxN ? 1 : 0;
     }
@@ -676,8 +713,13 @@ int batched_general(sqrtm_handle_t h, const int *idx, int count, const double *c
     for (int i = 0; i < B; ++i) sig = fnv(sig, (uint64_t)nord[i]);
     if (run_graph(h, 400, L.desc, nmax, B, enqueue_pipeline, &pipe, sig)) return 7;
     BState *hst = (BState *)h->bpin;
+    unsigned long long *hstamp = (unsigned long long *)((char *)h->bpin + sizeof(BState) * (size_t)B);
     SQM_CU(cudaMemcpyAsync(hst, L.st, sizeof(BState) * (size_t)B, cudaMemcpyDeviceToHost, s));
+    SQM_CU(cudaMemcpyAsync(hstamp, L.stamps, sizeof(unsigned long long) * (kBatchPhases + 1), cudaMemcpyDeviceToHost, s));
     SQM_CU(cudaStreamSynchronize(s));
     for (int i = 0; i < B; ++i) st_out[ord[i]] = hst[i].status;
+    for (int q = 0; q < kBatchPhases; ++q) h->bphase_ms[q] = 1e-6 * (double)(hstamp[q + 1] - hstamp[q]);
+    h->bphase_count = B;
+    h->bphase_general = Bg;
     return 0;
 }

@@ -14,6 +14,8 @@
 // ---------------------------------------------------------------------------
 // handle
 // ---------------------------------------------------------------------------
+constexpr int kBatchPhases = 5;
+
 struct Buf {
     void *p = nullptr;
     size_t bytes = 0;
@@ -58,6 +60,11 @@ struct sqrtm_handle_s {
     Buf bws;
     void *bpin = nullptr;
     size_t bpin_bytes = 0;
+    // phases of the last batched-path graph (device clock): norms and casts,
+    // Hessenberg reductions, QR rounds, Jacobi, triangular roots + X_0,
+    // refinement loop; and the matrices it took (all, general)
+    double bphase_ms[kBatchPhases] = {0, 0, 0, 0, 0};
+    int bphase_count = 0, bphase_general = 0;
     // batched calls: worker handles, each on its own non-blocking stream
     char last_error[160] = {0};
     std::vector<sqrtm_handle_s *> workers;

@@ -28,16 +28,17 @@ def test_build_table_orders_buckets_and_fills_builtins():
          "cutoff": {0: 2.0, 256: 1.5},
          "spd": {0: 1.0, 1: 0.8}, "spd_err": {0: 1e-15, 1: 2e-15}, "batched": 0.5, "per_matrix": 0.4},
         {"n": 64, "blks": {8: 1.0, 16: 1.0, 32: 1.0}, "helpers": {}, "spd": {}, "spd_err": {},
-         "batched": 0.1, "per_matrix": 0.9},
+         "batched": 0.1, "per_matrix": 0.9, "batched_spectral": 0.3, "batched_schur": 0.2},
         {"n": 4096, "blks": {}, "helpers": {}, "spd": {}, "spd_err": {}},
     ]
     t = at.build_table(measured)
     assert [e["n_max"] for e in t] == [64, 512, 4096]
-    assert t[0] == {"n_max": 64, "blks": 8, "qr_helpers": -1, "spd_precision": 0, "batched": 1, "trisqrt_cutoff": 0}
+    assert t[0] == {"n_max": 64, "blks": 8, "qr_helpers": -1, "spd_precision": 0, "batched": 1, "trisqrt_cutoff": 0,
+                    "batched_spd": 0}
     assert t[1] == {"n_max": 512, "blks": 16, "qr_helpers": 8, "spd_precision": 1, "batched": 0,
-                    "trisqrt_cutoff": 256}
+                    "trisqrt_cutoff": 256, "batched_spd": 1}
     assert t[2] == {"n_max": 4096, "blks": 32, "qr_helpers": -1, "spd_precision": 0, "batched": 0,
-                    "trisqrt_cutoff": 0}
+                    "trisqrt_cutoff": 0, "batched_spd": 1}
 
 
 def test_shipped_tables_are_valid():
