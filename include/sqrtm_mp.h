@@ -78,7 +78,18 @@ enum { SQRTM_KIND_AUTO = 0, SQRTM_KIND_GENERAL = 1, SQRTM_KIND_SPD = 2, SQRTM_KI
  * n 2^(rho_i + rho_j - 56), 2^rho_i bounding row i of X, i.e. within the
  * FP64 product's own error bound); RESID_FP64 forces the FP64 product on
  * the CUDA cores. */
-enum { SQRTM_PREC_AUTO = -1, SQRTM_PREC_FP32 = 0, SQRTM_PREC_TF32X3 = 1, SQRTM_PREC_RESID_FP64 = 2 };
+enum {
+    SQRTM_PREC_AUTO = -1,
+    SQRTM_PREC_FP32 = 0,
+    SQRTM_PREC_TF32X3 = 1,
+    SQRTM_PREC_RESID_FP64 = 2,
+    SQRTM_PREC_TF32X3_GENERAL = 4
+};
+/* SQRTM_PREC_TF32X3_GENERAL: the dense products of the general path
+ * (Algorithm 2 steps 3, 8 and 10 for real A and even n >= 128: X_0 = Q S Q^H,
+ * R~ = Q^H Rhat Q, X += Re(Q Y Q^H)) as split-TF32 products on the tensor
+ * cores, each complex product computed as one real product over the
+ * interleaved (re, im) operands; otherwise the FP32 CUDA-core products. */
 
 typedef struct {
     double tol;      /* stop when ||A - X^2||_F <= tol ||A||_F (Algorithm 2,
@@ -135,8 +146,9 @@ typedef struct {
  *   batched       sqrtm_mixed_batched: 1 sends matrices of these sizes
  *                 through the batched general path, 0 through per-matrix
  *                 calls on worker streams;
- *   spd_precision SQRTM_PREC_* flags of Algorithm 3 (used when
- *                 opts->precision == SQRTM_PREC_AUTO);
+ *   spd_precision SQRTM_PREC_* flags used when opts->precision ==
+ *                 SQRTM_PREC_AUTO (the TF32X3 and RESID_FP64 bits act on
+ *                 Algorithm 3, TF32X3_GENERAL on Algorithm 2);
  *   trisqrt_cutoff 0: the blocked triangular square root (Sec. 2.2.1);
  *                 >= 64: the recursive splitting of Sec. 2.2.1 (S_11, S_22
  *                 recursively, S_12 from a Sylvester solve) down to blocks

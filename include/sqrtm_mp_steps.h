@@ -154,6 +154,22 @@ SQRTM_API int sqrtm_step_gemm_tf32x3(sqrtm_handle_t h, int64_t M, int64_t N, int
                                      const float *dA, int64_t lda, const float *dB, int64_t ldb,
                                      float *dC, int64_t ldc);
 
+/* Complex low-precision product on the tensor cores (the transforms of
+ * Algorithm 2, steps 3, 8 and 10, in split-TF32): C = op(A) op(Y), complex
+ * FP32 interleaved (re, im), with row i of A stored contiguously,
+ * A(i, l) = dA[l + i*lda] (M x K), op(A) = conj(A) when conj_a; Y (K x N)
+ * column-major, Y(l, j) = dY[l + j*ldy], op(Y) = conj(Y) when conj_y; C
+ * (M x N) column-major (ldc); all leading dimensions in complex elements.
+ * Y is re-laid into a real 2K x 2N matrix (in the handle's workspace) so
+ * that one real split-TF32 product over the interleaved operands gives the
+ * real and imaginary parts side by side.  Returns -2 (a negative size), -5
+ * (a NULL pointer), -6 (a leading dimension too small, or lda odd / a base
+ * not 16-byte aligned: the TMA rules), 6 if a device-side bounded wait gave
+ * up. */
+SQRTM_API int sqrtm_step_cgemm_tf32x3(sqrtm_handle_t h, int64_t M, int64_t N, int64_t K, const void *dA,
+                                      int64_t lda, int conj_a, const void *dY, int64_t ldy, int conj_y, void *dC,
+                                      int64_t ldc);
+
 /* Residual of the symmetric positive definite path (Algorithm 3, step 5)
  * for symmetric X: R = 4^-e A - X_s X_s with X_s = 2^-e X, FP64 accuracy;
  * writes fl32(R) (mirrored) into dRhat (float n x n) and ||R||_F into

@@ -30,7 +30,7 @@ STATUS = {
 }
 
 KIND_AUTO, KIND_GENERAL, KIND_SPD, KIND_REAL = 0, 1, 2, 3
-PREC_AUTO, PREC_FP32, PREC_TF32X3, PREC_RESID_FP64 = -1, 0, 1, 2
+PREC_AUTO, PREC_FP32, PREC_TF32X3, PREC_RESID_FP64, PREC_TF32X3_GENERAL = -1, 0, 1, 2, 4
 MAX_HISTORY = 64
 MAX_TUNE = 32
 
@@ -127,6 +127,7 @@ _SIGS = {
     "sqrtm_step_transform_in_spd": ([_P, _P, _P, _P, _P, _L], _I),
     "sqrtm_step_transform_out_update_spd": ([_P, _P, _P, _L, _I, _P, _L], _I),
     "sqrtm_step_gemm_tf32x3": ([_P, _L, _L, _L, _P, _L, _P, _L, _P, _L], _I),
+    "sqrtm_step_cgemm_tf32x3": ([_P, _L, _L, _L, _P, _L, _I, _P, _L, _I, _P, _L], _I),
     "sqrtm_step_residual_sym": ([_P, _P, _L, _P, _L, _L, _I, _P, ctypes.POINTER(_D), _I], _I),
     "sqrtm_step_residual_noalloc": ([_P, _L, _P, _L, _L, _I, _P, ctypes.POINTER(_D), _P], _I),
 }
@@ -727,4 +728,14 @@ def step_gemm_tf32x3(A_rows, B_cols, M, N, K):
     C = torch.empty(M * N, dtype=torch.float32, device=A_rows.device)
     _rc(lib().sqrtm_step_gemm_tf32x3(handle(), M, N, K, _ptr(A_rows), K, _ptr(B_cols), K, _ptr(C), M),
         "gemm_tf32x3")
+    return C
+
+
+def step_cgemm_tf32x3(A_rows, Y_cm, M, N, K, conj_a=False, conj_y=False):
+    """C = op(A) op(Y) on the tensor cores (split TF32), complex64.  A_rows:
+    complex64 tensor whose storage holds A row by row; Y_cm: Y column-major.
+    Returns C column-major (M*N complex64)."""
+    C = torch.empty(M * N, dtype=torch.complex64, device=A_rows.device)
+    _rc(lib().sqrtm_step_cgemm_tf32x3(handle(), M, N, K, _ptr(A_rows), K, int(conj_a), _ptr(Y_cm), K,
+                                      int(conj_y), _ptr(C), M), "cgemm_tf32x3")
     return C

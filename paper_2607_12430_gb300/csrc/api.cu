@@ -12,6 +12,7 @@
 
 #include "handle.h"
 #include "spd_internal.h"
+#include "tc_gemm.h"
 
 using namespace sqm;
 
@@ -215,7 +216,7 @@ extern "C" int sqrtm_set_tuning(sqrtm_handle_t h, const sqrtm_tune_entry *table,
         const sqrtm_tune_entry &t = table[i];
         if (t.n_max < 1 || (i > 0 && t.n_max <= table[i - 1].n_max)) return -4;
         if (t.blks < 1 || t.blks > 32 || t.qr_helpers < -1 || t.qr_helpers > 24) return -4;
-        if ((t.batched != 0 && t.batched != 1) || t.spd_precision < 0 || t.spd_precision > 3) return -4;
+        if ((t.batched != 0 && t.batched != 1) || t.spd_precision < 0 || t.spd_precision > 7) return -4;
         if (t.trisqrt_cutoff < 0 || (t.batched_spd != 0 && t.batched_spd != 1)) return -4;
     }
     h->tuning.assign(table, table + count);
@@ -356,6 +357,16 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
                          Carve::round(qr_win_capacity(n) * sizeof(WinRec)) + Carve::round(qr_u_capacity(n) * cb)) +
                     Carve::round(kQrStateInts * sizeof(int)) + Carve::round(4 * sizeof(int)) + Carve::round(32 * sizeof(int)) + Carve::round(qr_win_capacity(n) * sizeof(int)) + 4096 +
                     (root == 3 ? Carve::round(nn * cb) : 0);
+    // split-TF32 tensor-core transforms (X_0 = Q S Q^H, R~ = Q^H Rhat Q,
+    // X += Re(Q Y Q^H)) for the FP32 square root of a real matrix of even
+    // size: each complex product is one real product over interleaved
+    // operands (tc_gemm.h), with Q^T and two re-laid copies of Q formed once
+    // per factorisation; the re-laid right operands need 2n-float columns
+    const bool use_tc = sizeof(R) == sizeof(float) && root == 2 && !cin && refine && (n % 2) == 0 && n >= 128 &&
+                        (o.precision & SQRTM_PREC_TF32X3_GENERAL) != 0;
+    const size_t tcf = 4 * nn;  // floats of one full re-laid n x n complex operand (2n x 2n)
+    if (use_tc)
+        wbytes += Carve::round(nn * cb) + 3 * Carve::round(tcf * sizeof(float)) + Carve::round(2 * nn * sizeof(float));
     if (ensure(h->fact, fbytes, h) || ensure(h->ws, wbytes, h)) return 7;
     Carve cf(h->fact.p);
     cplx<R> *Q = cf.take<cplx<R>>(nn);
@@ -389,6 +400,14 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     // by the residual before Rt is next written)
     cplx<R> *V = root == 3 ? cw.take<cplx<R>>(nn) : nullptr;
     double *XX = (double *)Rt;
+    // tensor-core operands: Q^T; Q re-laid (for M Q); Q^H re-laid, real
+    // part only (for Re(W Q^H)); the per-step re-laid Rhat and Y
+    cplx<R> *Qt = use_tc ? cw.take<cplx<R>>(nn) : nullptr;
+    float *QB = use_tc ? cw.take<float>(tcf) : nullptr;
+    float *RB = use_tc ? cw.take<float>(tcf) : nullptr;
+    float *YB = use_tc ? cw.take<float>(tcf) : nullptr;
+    float *QhB = use_tc ? cw.take<float>(2 * nn) : nullptr;
+    const int ld2 = 2 * (int)n;  // leading dimension of the re-laid operands (floats)
     h->fact_n = -1;
 
     SQM_CU(cudaMemsetAsync(sc.e, 0, 16 * sizeof(int), s));
@@ -453,9 +472,25 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
         SQM_CU(launch_trisqrt_rec<R>(T, (int)n, S, (int)n, (int)n, o.blks, tune->trisqrt_cutoff, sc.st_solve, s));
     else SQM_CU(launch_trisqrt<R>(T, (int)n, S, (int)n, (int)n, o.blks, sc.st_solve, s));
     // X_0 = Re(Q S Q^H), rounded to R, times 2^e
+    const int ni = (int)n;
+    if (use_tc) {
+        // W <- (Q S)^T from Q^T's columns (the rows of Q); then
+        // X_0 = 2^e Re(W Q^H) from W^T's columns, the FP32 accumulator
+        // widened to FP64 (the rounding to FP32 of reading c10)
+        TcEpilogue ep{};
+        SQM_CU(launch_ctranspose(Q, Qt, ni, s));
+        SQM_CU(launch_tc_relayout_cplx(Q, n, ni, ni, 1.0f, 1.0f, false, QB, ld2, s));
+        SQM_CU(launch_tc_relayout_cplx(Qt, n, ni, ni, 1.0f, -1.0f, true, QhB, ld2, s));
+        SQM_CU(launch_tc_relayout_cplx(S, n, ni, ni, 1.0f, 1.0f, false, YB, ld2, s));
+        ep.C = (float *)W; ep.ldc = n;
+        SQM_CU(launch_tc_cgemm(ni, ni, ni, Qt, ni, YB, ld2, TC_EPI_CSTORE_T, ep, sc.st_solve, s));
+        ep = TcEpilogue{}; ep.X = dX; ep.ldx = ldx; ep.scale = ldexp(1.0, e);
+        SQM_CU(launch_tc_cgemm(ni, ni, ni, W, ni, QhB, ld2, TC_EPI_RE_F64_STORE, ep, sc.st_solve, s));
+    } else {
     SQM_CU(launch_cgemm<R>(OP_N, OP_N, (int)n, (int)n, (int)n, Q, (int)n, false, S, (int)n, EPI_STORE, W, (int)n, nullptr, 0, 0.0, s));
     SQM_CU(launch_cgemm<R>(OP_N, OP_H, (int)n, (int)n, (int)n, W, (int)n, false, Q, (int)n,
                            cin ? EPI_CPLX_TO_F64 : EPI_REAL_TO_F64, nullptr, 0, dX, ldx, ldexp(1.0, e), s));
+    }
     SQM_CU(cudaEventRecord(h->ev[2], s));
     int st_schur = 0, st_solve = 0;
     if (int rc = read_scalars(h, sc, nullptr, nullptr, nullptr, &st_schur, &st_solve)) return rc;
@@ -511,6 +546,25 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
                 if (grew >= 2) { status = 4; break; }
                 prev = rn;
             }
+        }
+        if (use_tc) {
+            // (Q^H Rhat)^T into W from Q's columns (conjugated rows of Q^H);
+            // R~ = (Q^H Rhat) Q; S Y + Y S = R~; W <- (Q Y)^T;
+            // X += 2^e Re(W Q^H) in the FP64 epilogue
+            TcEpilogue ep{};
+            SQM_CU(launch_tc_relayout_real(Rhat, n, ni, ni, -1.0f, RB, ld2, s));
+            ep.C = (float *)W; ep.ldc = n;
+            SQM_CU(launch_tc_cgemm(ni, ni, ni, Q, ni, RB, ld2, TC_EPI_CSTORE_T, ep, sc.st_solve, s));
+            ep.C = (float *)Rt;
+            SQM_CU(launch_tc_cgemm(ni, ni, ni, W, ni, QB, ld2, TC_EPI_CSTORE, ep, sc.st_solve, s));
+            SQM_CU(launch_rtrsyl<R>(S, ni, ni, S, ni, ni, Rt, ni, o.blks, sc.st_solve, s));
+            SQM_CU(launch_tc_relayout_cplx(Rt, n, ni, ni, 1.0f, 1.0f, false, YB, ld2, s));
+            ep.C = (float *)W;
+            SQM_CU(launch_tc_cgemm(ni, ni, ni, Qt, ni, YB, ld2, TC_EPI_CSTORE_T, ep, sc.st_solve, s));
+            ep = TcEpilogue{}; ep.X = dX; ep.ldx = ldx; ep.scale = ldexp(1.0, e);
+            SQM_CU(launch_tc_cgemm(ni, ni, ni, W, ni, QhB, ld2, TC_EPI_RE_F64_ADD, ep, sc.st_solve, s));
+            ++applied;
+            continue;
         }
         // R~ = Q^H Rhat Q; Y solves S Y + Y S = R~; X += 2^e Re(Q Y Q^H)
         SQM_CU(launch_cgemm<R>(OP_N, OP_N, (int)n, (int)n, (int)n, Rhat, (int)n, !cin, Q, (int)n, EPI_STORE, W, (int)n, nullptr, 0, 0.0, s));

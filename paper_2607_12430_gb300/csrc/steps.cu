@@ -385,3 +385,29 @@ extern "C" int sqrtm_step_gemm_tf32x3(sqrtm_handle_t h, int64_t M, int64_t N, in
     if (fetch(h, &st, ss.iscal + 1, sizeof(int))) return 7;
     return st;
 }
+
+extern "C" int sqrtm_step_cgemm_tf32x3(sqrtm_handle_t h, int64_t M, int64_t N, int64_t K, const void *dA,
+                                       int64_t lda, int conj_a, const void *dY, int64_t ldy, int conj_y, void *dC,
+                                       int64_t ldc)
+{
+    if (!h) return -1;
+    if (M < 0 || N < 0 || K < 0) return -2;
+    if (M == 0 || N == 0) return 0;
+    if (!dA || !dY || !dC) return -5;
+    if (K == 0 || lda < K || ldy < K || ldc < M) return -6;
+    const int64_t ldb = (2 * K + 3) / 4 * 4;  // re-laid Y: 2K floats per column, TMA-aligned
+    if (!tc_cgemm_supported(lda, ldb, dA, dA)) return -6;
+    StepScratch ss; void *ex;
+    if (int rc = step_scratch(h, 1, (size_t)ldb * 2 * N * sizeof(float), &ss, &ex)) return rc;
+    float *B = (float *)ex;
+    if (launch_tc_relayout_cplx(dY, ldy, (int)K, (int)N, conj_a ? -1.0f : 1.0f, conj_y ? -1.0f : 1.0f, false, B, ldb,
+                                h->stream))
+        return 7;
+    TcEpilogue ep{};
+    ep.C = (float *)dC; ep.ldc = ldc;
+    if (launch_tc_cgemm((int)M, (int)N, (int)K, dA, (int)lda, B, (int)ldb, TC_EPI_CSTORE, ep, ss.iscal + 1, h->stream))
+        return 7;
+    int st = 0;
+    if (fetch(h, &st, ss.iscal + 1, sizeof(int))) return 7;
+    return st;
+}

@@ -52,6 +52,7 @@ tc3_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_BN;
     if ((EPI == TC_EPI_SYM_ADD_F64) && m0 > n0) return;  // mirrored epilogue: upper block triangle only
+    static_assert(TC_BN % 2 == 0, "complex column pairs stay within a tile");
 
     // 1024-aligned stage ring, then barriers and the TMEM address slot
     unsigned char *base = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
@@ -185,6 +186,30 @@ tc3_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
                         ep.X[row + (int64_t)col * ep.ldx] = x;
                         ep.X[col + (int64_t)row * ep.ldx] = x;
                     }
+                } else if (EPI == TC_EPI_CSTORE || EPI == TC_EPI_CSTORE_T) {
+                    // accumulator columns (2q, 2q+1) = (Re, Im) of complex column q
+#pragma unroll
+                    for (int j = 0; j < 32; j += 2) {
+                        const int col = n0 + c0 + j;
+                        if (col >= N) continue;  // N even: col + 1 < N as well
+                        const int q = col >> 1;
+                        const int64_t at = EPI == TC_EPI_CSTORE ? (row + (int64_t)q * ep.ldc) : (q + (int64_t)row * ep.ldc);
+                        *reinterpret_cast<float2 *>(ep.C + 2 * at) =
+                            make_float2(__uint_as_float(r[j]), __uint_as_float(r[j + 1]));
+                    }
+                } else if (EPI == TC_EPI_RE_F64_STORE || EPI == TC_EPI_RE_F64_ADD) {
+                    double old[32];
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = n0 + c0 + j;
+                        old[j] = (EPI == TC_EPI_RE_F64_ADD && col < N) ? ep.X[row + (int64_t)col * ep.ldx] : 0.0;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = n0 + c0 + j;
+                        if (col >= N) continue;
+                        ep.X[row + (int64_t)col * ep.ldx] = old[j] + (double)__uint_as_float(r[j]) * ep.scale;
+                    }
                 } else {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
@@ -230,6 +255,17 @@ bool tc_gemm_supported(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb
     return encode_fn() != nullptr;
 }
 
+template <int EPI>
+static cudaError_t launch_epi(dim3 g, const CUtensorMap &ma, const CUtensorMap &mb, int M, int N, int K,
+                              const TcEpilogue &ep, int *err, cudaStream_t s)
+{
+    cudaError_t e;
+    if ((e = allow_max_smem((const void *)tc3_gemm_kernel<EPI>))) return e;
+    tc3_gemm_kernel<EPI><<<g, TC_THREADS, TC_SMEM, s>>>(ma, mb, M, N, K, ep, err);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tc3_gemm(int M, int N, int K, const float *A, int lda, const float *B, int ldb, int epi,
                             const TcEpilogue &ep, int *err, cudaStream_t s)
 {
@@ -238,6 +274,13 @@ cudaError_t launch_tc3_gemm(int M, int N, int K, const float *A, int lda, const 
     if (!make_map(&ma, A, K, M, lda) || !make_map(&mb, B, K, N, ldb)) return cudaErrorInvalidValue;
     dim3 g((unsigned)cdiv_i(M, TC_BM), (unsigned)cdiv_i(N, TC_BN));
     cudaError_t e;
+    switch (epi) {
+    case TC_EPI_CSTORE: return launch_epi<TC_EPI_CSTORE>(g, ma, mb, M, N, K, ep, err, s);
+    case TC_EPI_CSTORE_T: return launch_epi<TC_EPI_CSTORE_T>(g, ma, mb, M, N, K, ep, err, s);
+    case TC_EPI_RE_F64_STORE: return launch_epi<TC_EPI_RE_F64_STORE>(g, ma, mb, M, N, K, ep, err, s);
+    case TC_EPI_RE_F64_ADD: return launch_epi<TC_EPI_RE_F64_ADD>(g, ma, mb, M, N, K, ep, err, s);
+    default: break;
+    }
     switch (epi) {
     case TC_EPI_STORE:
         if ((e = allow_max_smem((const void *)tc3_gemm_kernel<TC_EPI_STORE>))) return e;
@@ -252,6 +295,99 @@ cudaError_t launch_tc3_gemm(int M, int N, int K, const float *A, int lda, const 
         tc3_gemm_kernel<TC_EPI_SYM_ADD_F64><<<g, TC_THREADS, TC_SMEM, s>>>(ma, mb, M, N, K, ep, err); count_launch();
     }
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// complex products as real ones
+// ---------------------------------------------------------------------------
+// B column 2j (and 2j+1 unless re_only) from column j of Y, one thread per
+// (l, j): rows 2l, 2l+1
+__global__ void tc_relayout_cplx_kernel(const float2 *__restrict__ Y, int64_t ldy, int k, int n, float sa, float sy,
+                                        int re_only, float *__restrict__ B, int64_t ldb)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)k * n) return;
+    const int l = (int)(t % k), j = (int)(t / k);
+    const float2 y = Y[l + (int64_t)j * ldy];
+    const int64_t c0 = re_only ? j : 2 * (int64_t)j;
+    B[2 * l + c0 * ldb] = y.x;
+    B[2 * l + 1 + c0 * ldb] = -sa * sy * y.y;
+    if (!re_only) {
+        B[2 * l + (c0 + 1) * ldb] = sy * y.y;
+        B[2 * l + 1 + (c0 + 1) * ldb] = sa * y.x;
+    }
+}
+
+__global__ void tc_relayout_real_kernel(const float *__restrict__ Y, int64_t ldy, int k, int n, float sa,
+                                        float *__restrict__ B, int64_t ldb)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)k * n) return;
+    const int l = (int)(t % k), j = (int)(t / k);
+    const float y = Y[l + (int64_t)j * ldy];
+    const int64_t c0 = 2 * (int64_t)j;
+    B[2 * l + c0 * ldb] = y;
+    B[2 * l + 1 + c0 * ldb] = 0.0f;
+    B[2 * l + (c0 + 1) * ldb] = 0.0f;
+    B[2 * l + 1 + (c0 + 1) * ldb] = sa * y;
+}
+
+// Qt = Q^T through 32 x 32 shared-memory tiles
+__global__ void ctranspose_kernel(const float2 *__restrict__ Q, float2 *__restrict__ Qt, int n)
+{
+    __shared__ float2 tile[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int i = bx + threadIdx.x, j = by + r;
+        if (i < n && j < n) tile[r][threadIdx.x] = Q[i + (int64_t)j * n];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int j = by + threadIdx.x, i = bx + r;
+        if (i < n && j < n) Qt[j + (int64_t)i * n] = tile[threadIdx.x][r];
+    }
+}
+
+cudaError_t launch_tc_relayout_cplx(const void *Y, int64_t ldy, int k, int n, float sa, float sy, bool re_only,
+                                    float *B, int64_t ldb, cudaStream_t s)
+{
+    const int64_t tot = (int64_t)k * n;
+    if (tot <= 0) return cudaSuccess;
+    tc_relayout_cplx_kernel<<<(unsigned)cdiv_i(tot, 256), 256, 0, s>>>((const float2 *)Y, ldy, k, n, sa, sy,
+                                                                        re_only ? 1 : 0, B, ldb);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_relayout_real(const float *Y, int64_t ldy, int k, int n, float sa, float *B, int64_t ldb,
+                                    cudaStream_t s)
+{
+    const int64_t tot = (int64_t)k * n;
+    if (tot <= 0) return cudaSuccess;
+    tc_relayout_real_kernel<<<(unsigned)cdiv_i(tot, 256), 256, 0, s>>>(Y, ldy, k, n, sa, B, ldb);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ctranspose(const void *Q, void *Qt, int n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    ctranspose_kernel<<<dim3((unsigned)cdiv_i(n, 32), (unsigned)cdiv_i(n, 32)), dim3(32, 8), 0, s>>>(
+        (const float2 *)Q, (float2 *)Qt, n);
+    count_launch();
+    return cudaGetLastError();
+}
+
+bool tc_cgemm_supported(int64_t lda_c, int64_t ldb, const void *A, const void *B)
+{
+    return tc_gemm_supported(1, 1, 1, 2 * lda_c, ldb, A, B);
+}
+
+cudaError_t launch_tc_cgemm(int M, int N, int K, const void *A, int lda_c, const float *B, int ldb, int epi,
+                            const TcEpilogue &ep, int *err, cudaStream_t s)
+{
+    const bool cplx_out = epi == TC_EPI_CSTORE || epi == TC_EPI_CSTORE_T;
+    return launch_tc3_gemm(M, cplx_out ? 2 * N : N, 2 * K, (const float *)A, 2 * lda_c, B, ldb, epi, ep, err, s);
 }
 
 }  // namespace sqm

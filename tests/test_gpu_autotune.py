@@ -23,9 +23,9 @@ def _lib():
     mp.set_tuning(saved)
 
 
-def _entry(n_max, blks=32, helpers=-1, batched=1, prec=0, cutoff=0):
+def _entry(n_max, blks=32, helpers=-1, batched=1, prec=0, cutoff=0, batched_spd=1):
     return {"n_max": n_max, "blks": blks, "qr_helpers": helpers, "batched": batched, "spd_precision": prec,
-            "trisqrt_cutoff": cutoff}
+            "trisqrt_cutoff": cutoff, "batched_spd": batched_spd}
 
 
 @pytest.mark.parametrize("bad,code", [
@@ -34,6 +34,7 @@ def _entry(n_max, blks=32, helpers=-1, batched=1, prec=0, cutoff=0):
     ([_entry(256, helpers=25)], -4),
     ([_entry(256, batched=2)], -4),
     ([_entry(256, cutoff=-1)], -4),
+    ([_entry(256, batched_spd=2)], -4),
     ([_entry(i + 1) for i in range(33)], -3),  # too many entries
 ])
 def test_set_tuning_rejects(bad, code):
@@ -43,7 +44,7 @@ def test_set_tuning_rejects(bad, code):
 
 
 def test_tuning_round_trip():
-    t = [_entry(128, blks=8), _entry(1024, blks=16, helpers=0, batched=0, prec=1, cutoff=256)]
+    t = [_entry(128, blks=8), _entry(1024, blks=16, helpers=0, batched=0, prec=1, cutoff=256, batched_spd=0)]
     mp.set_tuning(t)
     assert mp.get_tuning() == t
     mp.set_tuning([])
