@@ -31,6 +31,23 @@ extern "C" {
 SQRTM_API int sqrtm_step_scale(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, void *dAs,
                      int fp64, int *e_host, double *norm_host);
 
+/* Householder reduction of a REAL matrix to upper Hessenberg form, the
+ * first stage of the Schur decomposition (Algorithm 2, step 1) as the
+ * general path runs it beyond the sizes its one-cluster kernel holds:
+ * A = Q H Q^T with Q = P_0 ... P_{n-3}, P_k = I - beta_k v_k v_k^T acting
+ * on rows / columns k+1 .. n-1, v_k = x + sign(x_0) ||x|| e_1 for
+ * x = H(k+1:n, k) (the sign convention of the complex reduction with the
+ * phase of x_0).  The reduction runs in real arithmetic in the storage
+ * precision (fp64 ? FP64 : FP32), three launches per column over the whole
+ * GPU; Q is formed from the stored reflectors by the blocked compact-WY
+ * back-transform.  dA: real FP64 n x n (lda), rounded to the storage
+ * precision first; dH, dQ: complex (complex64 or complex128 by fp64) n x n
+ * outputs, ld n, imaginary parts zero, H zero below the subdiagonal.
+ * Returns -2/-5/-6 for a NULL dA/dH/dQ, -3 (n < 0 or n > 46340), -4
+ * (lda < n), 7 on a CUDA error. */
+SQRTM_API int sqrtm_step_hessenberg(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, void *dH, void *dQ,
+                                    int fp64);
+
 /* Complex Schur decomposition (Algorithm 2, step 1): dT (in: A_s, out: T
  * upper triangular) and dQ (out: unitary) with A_s = Q T Q^H: Householder
  * Hessenberg reduction, then single-shift QR sweeps.  Returns 0 or 3. */

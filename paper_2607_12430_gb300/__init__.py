@@ -111,6 +111,7 @@ _SIGS = {
     "sqrtm_last_error": ([_P], ctypes.c_char_p),
     "sqrtm_step_scale": ([_P, _P, _L, _L, _P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
     "sqrtm_step_schur": ([_P, _P, _P, _L, _I], _I),
+    "sqrtm_step_hessenberg": ([_P, _P, _L, _L, _P, _P, _I], _I),
     "sqrtm_step_syevd": ([_P, _P, _P, _P, _L, _I], _I),
     "sqrtm_step_trisqrt": ([_P, _P, _P, _L, _I, _I], _I),
     "sqrtm_step_trisqrt_rec": ([_P, _P, _P, _L, _I, _I, _I], _I),
@@ -593,6 +594,16 @@ def step_scale(A_cm, n, fp64=False):
     nrm = ctypes.c_double()
     _rc(lib().sqrtm_step_scale(handle(), _ptr(A_cm), n, n, _ptr(As), int(fp64), ctypes.byref(e), ctypes.byref(nrm)), "scale")
     return As, e.value, nrm.value
+
+
+def step_hessenberg(A_cm, n, fp64=False):
+    """Real Householder Hessenberg reduction: A_cm float64 column-major
+    (n*n).  Returns (H_cm, Q_cm) complex with zero imaginary parts."""
+    dt = torch.complex128 if fp64 else torch.complex64
+    H = torch.empty(n * n, dtype=dt, device=A_cm.device)
+    Q = torch.empty(n * n, dtype=dt, device=A_cm.device)
+    _rc(lib().sqrtm_step_hessenberg(handle(), _ptr(A_cm), n, n, _ptr(H), _ptr(Q), int(fp64)), "hessenberg")
+    return H, Q
 
 
 def step_schur(T_cm, n, fp64=False):

@@ -451,6 +451,19 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
         // A is real: the cluster-resident real reduction (W and Rt are free
         // until the Schur form is done)
         SQM_CU(launch_hessenberg_cluster<R>(T, Q, (int)n, (int)n, (R *)W, (R *)Rt, s));
+    } else if (!cin && hessenberg_real_scratch<R>((int)n) <= nn) {
+        // A is real, beyond the cluster's sizes: the real per-column
+        // reduction over the whole GPU and Q from the stored reflectors, one
+        // captured graph (W holds H and the reflectors, Rt the real Q and the
+        // scratch; both are free until the Schur form is done); the complex
+        // T and Q are written outside the graph
+        struct Ctx { const cplx<R> *T; R *H, *Y, *Qr, *scr; int n; } ctx{T, (R *)W, (R *)W + nn, (R *)Rt, (R *)Rt + nn, (int)n};
+        auto enq = [](void *p, cudaStream_t st) -> cudaError_t {
+            Ctx *c = (Ctx *)p;
+            return enqueue_hessenberg_real<R>(c->T, c->H, c->Y, c->Qr, c->scr, c->n, st);
+        };
+        if (run_graph(h, 120 + (int)sizeof(R), W, n, 1, enq, &ctx)) return 7;
+        SQM_CU(launch_hessenberg_real_finish<R>((R *)W, (R *)Rt, T, Q, (int)n, s));
     } else {
         struct Ctx { SchurDesc<R> *d; int n; } ctx{ddesc, (int)n};
         auto enq = [](void *p, cudaStream_t st) -> cudaError_t {

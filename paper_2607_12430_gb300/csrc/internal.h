@@ -182,6 +182,20 @@ cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, in
                              const int *d_state_all, cudaStream_t s, float *ms_chase = nullptr,
                              const SchurDesc<R> *d_desc_alt = nullptr, cudaStream_t side = nullptr,
                              const cudaEvent_t *qev = nullptr, int *d_sync = nullptr, int helpers = -1);
+// Real Householder Hessenberg reduction of a real matrix of any size
+// (schur.cu): from the real parts of the complex A_s in T, H (real, ld n)
+// becomes upper Hessenberg and Qr = P_0 ... P_{n-3} (real, ld n); Y
+// receives the reflectors (n x n, ld n); scratch holds
+// hessenberg_real_scratch<R>(n) elements.  Three launches per column plus
+// the blocked back-transform, all capturable.  Then
+// launch_hessenberg_real_finish writes T = H and Q = Qr as complex.
+template <class R>
+size_t hessenberg_real_scratch(int n);
+template <class R>
+cudaError_t enqueue_hessenberg_real(const cplx<R> *T, R *H, R *Y, R *Qr, R *scratch, int n, cudaStream_t s);
+template <class R>
+cudaError_t launch_hessenberg_real_finish(const R *H, const R *Qr, cplx<R> *T, cplx<R> *Q, int n, cudaStream_t s);
+
 // Inside a stream capture on s: appends a conditional WHILE node whose
 // condition is `init` at every launch of the graph and whose body is
 // captured from body(ctx, body_stream, cond) (a kernel in the body sets the

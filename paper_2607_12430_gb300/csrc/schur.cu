@@ -20,6 +20,7 @@
 #include <atomic>
 
 #include "internal.h"
+#include "spd_internal.h"
 
 namespace sqm {
 
@@ -718,6 +719,244 @@ template cudaError_t launch_hessenberg_cluster<float>(cplx<float> *, cplx<float>
                                                       cudaStream_t);
 template cudaError_t launch_hessenberg_cluster<double>(cplx<double> *, cplx<double> *, int, int, double *, double *,
                                                        cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Real Householder Hessenberg reduction of a real matrix beyond the cluster
+// kernel's sizes: H (n x n, ld, real) <- Q^T H Q with Q = P_0 ... P_{n-3},
+// P_k = I - beta_k v_k v_k^T acting on rows / columns k+1 .. n-1.  Three
+// launches per column, each spread over the whole GPU:
+//   hessr_left:  every CTA forms v_k from column k (which no launch of this
+//                column writes), CTA 0 stores v_k into column k of Y (rows
+//                k+1..) and beta_k; each warp applies P_k to one column
+//                j > k of the trailing rows (w_j = beta v^T H(k+1:, j),
+//                H(k+1:, j) -= v w_j);
+//   hessr_rpart: partial products u_s = H(:, seg_s) v over S column segments
+//                (a thread per row);
+//   hessr_rupd:  u = beta sum_s u_s in segment order, H(:, seg_s) -= u v^T,
+//                and column k becomes (.., -sign(x_0) ||x||, 0, ..).
+// Q is not updated column by column: it is formed at the end from the
+// stored reflectors by the blocked compact-WY back-transform (GEMMs).
+// ---------------------------------------------------------------------------
+static constexpr int kHrThreads = 256;
+
+template <class R>
+__device__ void real_reflector(const R *__restrict__ col, int m, R *vsh, R *s_scal /* [beta, alpha] */)
+{
+    __shared__ R red[2][kHrThreads / 32];
+    R t_all = 0, t_tail = 0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const R x = col[i];
+        vsh[i] = x;
+        t_all += x * x;
+        if (i > 0) t_tail += x * x;
+    }
+    t_all = warp_sum(t_all);
+    t_tail = warp_sum(t_tail);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { red[0][w] = t_all; red[1][w] = t_tail; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        R xn2 = 0, tail2 = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { xn2 += red[0][q]; tail2 += red[1][q]; }
+        if (tail2 == R(0) || m <= 0) {
+            s_scal[0] = 0;                      // no reflection
+            s_scal[1] = m > 0 ? vsh[0] : R(0);  // the subdiagonal entry stays
+        } else {
+            const R xn = sqrt(xn2), x0 = vsh[0];
+            const R sg = x0 >= R(0) ? R(1) : R(-1);
+            const R v0 = x0 + sg * xn;          // no cancellation
+            vsh[0] = v0;
+            s_scal[0] = R(2) / (v0 * v0 + tail2);
+            s_scal[1] = -sg * xn;
+        }
+    }
+    __syncthreads();
+}
+
+template <class R>
+__global__ void __launch_bounds__(kHrThreads) hessr_left_kernel(R *__restrict__ H, int n, int ld, R *__restrict__ Y,
+                                                                R *__restrict__ scal, int k)
+{
+    extern __shared__ unsigned char smraw[];
+    R *vsh = reinterpret_cast<R *>(smraw);
+    __shared__ R s_scal[2];
+    const int m = n - k - 1;
+    real_reflector<R>(H + (k + 1) + (int64_t)k * ld, m, vsh, s_scal);
+    const R beta = s_scal[0];
+    if (blockIdx.x == 0) {
+        for (int i = threadIdx.x; i < m; i += blockDim.x) Y[(k + 1) + i + (int64_t)k * ld] = beta == R(0) ? R(0) : vsh[i];
+        if (threadIdx.x == 0) {
+            scal[2 * k] = beta;
+            scal[2 * k + 1] = s_scal[1];
+        }
+    }
+    if (beta == R(0)) return;
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int j = k + 1 + gw; j < n; j += nw) {
+        R *c = H + (k + 1) + (int64_t)j * ld;
+        R acc = 0;
+#pragma unroll 8
+        for (int i = lane; i < m; i += 32) acc = fma(vsh[i], c[i], acc);
+        const R wj = beta * warp_sum(acc);
+#pragma unroll 8
+        for (int i = lane; i < m; i += 32) c[i] = fma(-vsh[i], wj, c[i]);
+    }
+}
+
+// grid (row tiles of kHrThreads rows, S column segments of width seg)
+template <class R>
+__global__ void __launch_bounds__(kHrThreads) hessr_rpart_kernel(const R *__restrict__ H, int n, int ld,
+                                                                 const R *__restrict__ Y, const R *__restrict__ scal,
+                                                                 R *__restrict__ part, int k, int seg)
+{
+    __shared__ R vs[1024];
+    const int m = n - k - 1;
+    if (scal[2 * k] == R(0)) return;
+    const int j0 = k + 1 + blockIdx.y * seg, j1 = min(n, j0 + seg);
+    const int i = blockIdx.x * kHrThreads + threadIdx.x;
+    R acc = 0;
+    for (int c0 = j0; c0 < j1; c0 += 1024) {
+        const int c1 = min(j1, c0 + 1024);
+        __syncthreads();
+        for (int j = c0 + threadIdx.x; j < c1; j += blockDim.x) vs[j - c0] = Y[j + (int64_t)k * ld];
+        __syncthreads();
+        if (i < n) {
+            const R *row = H + i;
+#pragma unroll 4
+            for (int j = c0; j < c1; ++j) acc = fma(row[(int64_t)j * ld], vs[j - c0], acc);
+        }
+    }
+    (void)m;
+    if (i < n) part[(int64_t)blockIdx.y * n + i] = acc;
+}
+
+template <class R>
+__global__ void __launch_bounds__(kHrThreads) hessr_rupd_kernel(R *__restrict__ H, int n, int ld,
+                                                                const R *__restrict__ Y, const R *__restrict__ scal,
+                                                                const R *__restrict__ part, int S, int k, int seg)
+{
+    __shared__ R vs[1024];
+    const R beta = scal[2 * k];
+    const int m = n - k - 1;
+    if (blockIdx.x == 0 && blockIdx.y == 0) {
+        // column k: the reflected subdiagonal entry, zeros below it
+        for (int i = threadIdx.x; i < m; i += blockDim.x)
+            H[(k + 1) + i + (int64_t)k * ld] = i == 0 ? scal[2 * k + 1] : (beta == R(0) ? H[(k + 1) + i + (int64_t)k * ld] : R(0));
+    }
+    if (beta == R(0)) return;
+    const int j0 = k + 1 + blockIdx.y * seg, j1 = min(n, j0 + seg);
+    const int i = blockIdx.x * kHrThreads + threadIdx.x;
+    R u = 0;
+    if (i < n) {
+        for (int q = 0; q < S; ++q) u += part[(int64_t)q * n + i];
+        u *= beta;
+    }
+    for (int c0 = j0; c0 < j1; c0 += 1024) {
+        const int c1 = min(j1, c0 + 1024);
+        __syncthreads();
+        for (int j = c0 + threadIdx.x; j < c1; j += blockDim.x) vs[j - c0] = Y[j + (int64_t)k * ld];
+        __syncthreads();
+        if (i < n) {
+            R *row = H + i;
+#pragma unroll 4
+            for (int j = c0; j < c1; ++j) row[(int64_t)j * ld] = fma(-u, vs[j - c0], row[(int64_t)j * ld]);
+        }
+    }
+}
+
+// complex A_s (real parts) -> real H; Y <- 0; Qr <- I
+template <class R>
+__global__ void hessr_prologue_kernel(const cplx<R> *__restrict__ T, R *__restrict__ H, R *__restrict__ Y,
+                                      R *__restrict__ Qr, int n)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)n * n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t % n), j = (int)(t / n);
+        H[t] = T[t].x;
+        Y[t] = R(0);
+        Qr[t] = (i == j) ? R(1) : R(0);
+    }
+}
+
+// real H (zero below the subdiagonal), real Q -> complex T, Q
+template <class R>
+__global__ void hessr_epilogue_kernel(const R *__restrict__ H, const R *__restrict__ Qr, cplx<R> *__restrict__ T,
+                                      cplx<R> *__restrict__ Q, int n)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)n * n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t % n), j = (int)(t / n);
+        T[t] = cplx<R>{i > j + 1 ? R(0) : H[t], R(0)};
+        Q[t] = cplx<R>{Qr[t], R(0)};
+    }
+}
+
+template <class R>
+__global__ void hessr_betas_kernel(const R *__restrict__ scal, R *__restrict__ betas, int n)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+        betas[k] = k + 2 < n ? scal[2 * k] : R(0);
+}
+
+template <class R>
+size_t hessenberg_real_scratch(int n)
+{
+    // [beta_k, alpha_k] pairs, the betas gathered, 64 partial vectors, and
+    // the back-transform's scratch
+    return (size_t)2 * n + 64 + (size_t)n + 64 + (size_t)64 * n + (size_t)kBackNb * (kBackNb + 2 * (size_t)n) +
+           (size_t)kBackNb * kBackNb + 64;
+}
+
+template <class R>
+cudaError_t enqueue_hessenberg_real(const cplx<R> *T, R *H, R *Y, R *Qr, R *scratch, int n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t vbytes = (size_t)n * sizeof(R);
+    cudaError_t err;
+    if (vbytes > 48 * 1024 && (err = allow_max_smem((const void *)hessr_left_kernel<R>))) return err;
+    R *scal = scratch, *betas = scal + 2 * (size_t)n + 64, *part = betas + n + 64, *bt = part + (size_t)64 * n;
+    const int tiles = (int)cdiv_i(n, kHrThreads);
+    const int S = std::max(1, std::min(64, (2 * sms + tiles - 1) / tiles));
+    hessr_prologue_kernel<R><<<2 * sms, 256, 0, s>>>(T, H, Y, Qr, n); count_launch();
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1;
+        const int seg = (int)cdiv_i(m, S);
+        const int lctas = (int)std::max<int64_t>(1, std::min<int64_t>(2 * sms, cdiv_i(m, kHrThreads / 32)));
+        hessr_left_kernel<R><<<lctas, kHrThreads, vbytes, s>>>(H, n, n, Y, scal, k); count_launch();
+        hessr_rpart_kernel<R><<<dim3(tiles, S), kHrThreads, 0, s>>>(H, n, n, Y, scal, part, k, seg); count_launch();
+        hessr_rupd_kernel<R><<<dim3(tiles, S), kHrThreads, 0, s>>>(H, n, n, Y, scal, part, S, k, seg); count_launch();
+    }
+    // Q = P_0 P_1 ... P_{n-3} applied to I by the blocked compact-WY
+    // back-transform (the reflectors' betas gathered contiguously first)
+    hessr_betas_kernel<R><<<cdiv_i(n, 256), 256, 0, s>>>(scal, betas, n); count_launch();
+    if ((err = launch_back_transform<R>(Y, n, betas, Qr, n, n, bt, s))) return err;
+    return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_hessenberg_real_finish(const R *H, const R *Qr, cplx<R> *T, cplx<R> *Q, int n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    hessr_epilogue_kernel<R><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(1024, cdiv_i((int64_t)n * n, 256))), 256,
+                               0, s>>>(H, Qr, T, Q, n);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template size_t hessenberg_real_scratch<float>(int);
+template size_t hessenberg_real_scratch<double>(int);
+template cudaError_t enqueue_hessenberg_real<float>(const cplx<float> *, float *, float *, float *, float *, int,
+                                                    cudaStream_t);
+template cudaError_t enqueue_hessenberg_real<double>(const cplx<double> *, double *, double *, double *, double *,
+                                                     int, cudaStream_t);
+template cudaError_t launch_hessenberg_real_finish<float>(const float *, const float *, cplx<float> *, cplx<float> *,
+                                                          int, cudaStream_t);
+template cudaError_t launch_hessenberg_real_finish<double>(const double *, const double *, cplx<double> *,
+                                                           cplx<double> *, int, cudaStream_t);
 
 template <class R>
 __global__ void eye_kernel(const SchurDesc<R> *__restrict__ descs)

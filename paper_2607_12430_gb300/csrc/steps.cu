@@ -100,6 +100,47 @@ static int schur_step(sqrtm_handle_t h, cplx<R> *T, cplx<R> *Q, int64_t n)
     return st;
 }
 
+// complex T = fl_R(A) (imaginary parts zero)
+template <class R>
+__global__ void cast_real_to_cplx_kernel(const double *__restrict__ A, int64_t lda, int n, cplx<R> *__restrict__ T)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)n * n;
+         t += (int64_t)gridDim.x * blockDim.x)
+        T[t] = cplx<R>{(R)A[(t % n) + (t / n) * lda], R(0)};
+}
+
+template <class R>
+static int hess_step(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, cplx<R> *H, cplx<R> *Q)
+{
+    const size_t nn = (size_t)n * n;
+    StepScratch ss; void *ex;
+    const size_t extra = 3 * Carve::round(nn * sizeof(R)) + Carve::round(hessenberg_real_scratch<R>((int)n) * sizeof(R));
+    if (int rc = step_scratch(h, n, extra, &ss, &ex)) return rc;
+    Carve c(ex);
+    R *Hr = c.take<R>(nn), *Y = c.take<R>(nn), *Qr = c.take<R>(nn);
+    R *scr = c.take<R>(hessenberg_real_scratch<R>((int)n));
+    cast_real_to_cplx_kernel<R><<<256, 256, 0, h->stream>>>(dA, lda, (int)n, H); count_launch();
+    if (enqueue_hessenberg_real<R>(H, Hr, Y, Qr, scr, (int)n, h->stream)) return 7;
+    if (launch_hessenberg_real_finish<R>(Hr, Qr, H, Q, (int)n, h->stream)) return 7;
+    if (cudaStreamSynchronize(h->stream)) return 7;
+    return 0;
+}
+
+extern "C" int sqrtm_step_hessenberg(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda, void *dH, void *dQ,
+                                     int fp64)
+{
+    if (!h) return -1;
+    if (n < 0) return -3;
+    if (lda < std::max<int64_t>(1, n)) return -4;
+    if (n == 0) return 0;
+    if (!dA) return -2;
+    if (!dH) return -5;
+    if (!dQ) return -6;
+    if (n > 46340) return -3;
+    return fp64 ? hess_step<double>(h, dA, n, lda, (cplx<double> *)dH, (cplx<double> *)dQ)
+                : hess_step<float>(h, dA, n, lda, (cplx<float> *)dH, (cplx<float> *)dQ);
+}
+
 extern "C" int sqrtm_step_schur(sqrtm_handle_t h, void *dT, void *dQ, int64_t n, int fp64)
 {
     if (!h) return -1;

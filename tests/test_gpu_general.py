@@ -72,6 +72,30 @@ def test_schur(n, fp64):
     assert _match(np.diag(T), np.diag(To)) <= 200 * n * u * np.linalg.norm(Asn)
 
 
+@pytest.mark.parametrize("fp64", [False, True])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 64, 130, 700])
+def test_hessenberg_real(n, fp64):
+    """The real per-column reduction (the general path beyond the cluster
+    kernel's sizes) against the oracle's Householder reduction, which takes
+    the same reflector signs: H agrees to rounding, Q is orthogonal and
+    Q H Q^T reproduces A."""
+    A = synth.shifted_gaussian(n, 3.0, seed=25 + n)
+    u = U64 if fp64 else U32
+    Ar = A if fp64 else A.astype(np.float32).astype(np.float64)
+    H, Q = mp.step_hessenberg(dev_cm(A, torch.float64), n, fp64=fp64)
+    H = host_cm(H, n).astype(np.complex128)
+    Q = host_cm(Q, n).astype(np.complex128)
+    assert np.all(np.imag(H) == 0) and np.all(np.imag(Q) == 0)
+    H, Q = np.real(H), np.real(Q)
+    assert np.all(np.tril(H, -2) == 0)
+    nA = np.linalg.norm(Ar)
+    assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= 20 * n * u
+    assert np.linalg.norm(Q @ H @ Q.T - Ar) <= 20 * n * u * nA
+    Ho, Qo = oracle.hessenberg(Ar)
+    assert np.linalg.norm(H - np.real(Ho)) <= 50 * n * u * nA
+    assert np.linalg.norm(Q - np.real(Qo)) <= 50 * n * u * np.sqrt(n)
+
+
 # --------------------------------------------------------------------------
 # a3: triangular square root
 # --------------------------------------------------------------------------
@@ -201,7 +225,7 @@ def test_sqrtm_mixed_general(n):
     assert oracle.rel_residual(X2.cpu().numpy(), A) <= 5 * n * U64
 
 
-@pytest.mark.parametrize("n", [600, 1024])
+@pytest.mark.parametrize("n", [600, 700, 1024])
 def test_sqrtm_mixed_general_large(n):
     # n = 600: the shared-memory layout of the cluster Hessenberg reduction
     # (above 512); n = 1024: the two-launch-per-column reduction and the
