@@ -130,8 +130,11 @@ SQRTM_API int sqrtm_step_transform_in(sqrtm_handle_t h, const void *dQ, const fl
 
 /* Triangular Sylvester solve S Y + Y St = C (Algorithm 2, step 9;
  * Algorithm 1 computes the same Y): S m x m and St nn x nn upper triangular
- * (c64, ld m and nn), dC (c64, m x nn, ld m) overwritten by Y.  Returns 0
- * or 2. */
+ * (c64, ld m and nn), dC (c64, m x nn, ld m) overwritten by Y.  With
+ * blks = 32, m a multiple of 16 and more than one block, one launch ordered
+ * by block dependencies; otherwise one launch per block wavefront (the same
+ * block equations and sums either way).  Returns 0, 2, or 6 if a bounded
+ * wait between blocks gave up. */
 SQRTM_API int sqrtm_step_rtrsyl(sqrtm_handle_t h, const void *dS, int64_t m, const void *dSt,
                       int64_t nn, void *dC, int blks);
 

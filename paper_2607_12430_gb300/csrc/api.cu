@@ -356,7 +356,7 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
                     2 * (Carve::round(qr_log_capacity(n) * sizeof(RotLog<R>)) +
                          Carve::round(qr_win_capacity(n) * sizeof(WinRec)) + Carve::round(qr_u_capacity(n) * cb)) +
                     Carve::round(kQrStateInts * sizeof(int)) + Carve::round(4 * sizeof(int)) + Carve::round(32 * sizeof(int)) + Carve::round(qr_win_capacity(n) * sizeof(int)) + 4096 +
-                    (root == 3 ? Carve::round(nn * cb) : 0);
+                    (root == 3 ? Carve::round(nn * cb) : 0) + Carve::round(rtrsyl_flow_ints((int)n, (int)n) * sizeof(int));
     // split-TF32 tensor-core transforms (X_0 = Q S Q^H, R~ = Q^H Rhat Q,
     // X += Re(Q Y Q^H)) for the FP32 square root of a real matrix of even
     // size: each complex product is one real product over interleaved
@@ -400,6 +400,9 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     // by the residual before Rt is next written)
     cplx<R> *V = root == 3 ? cw.take<cplx<R>>(nn) : nullptr;
     double *XX = (double *)Rt;
+    // dependency flags of the one-launch Sylvester solve
+    const int64_t flow_cap = (int64_t)rtrsyl_flow_ints((int)n, (int)n);
+    int *flow = cw.take<int>((size_t)flow_cap);
     // tensor-core operands: Q^T; Q re-laid (for M Q); Q^H re-laid, real
     // part only (for Re(W Q^H)); the per-step re-laid Rhat and Y
     cplx<R> *Qt = use_tc ? cw.take<cplx<R>>(nn) : nullptr;
@@ -570,7 +573,7 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
             SQM_CU(launch_tc_cgemm(ni, ni, ni, Q, ni, RB, ld2, TC_EPI_CSTORE_T, ep, sc.st_solve, s));
             ep.C = (float *)Rt;
             SQM_CU(launch_tc_cgemm(ni, ni, ni, W, ni, QB, ld2, TC_EPI_CSTORE, ep, sc.st_solve, s));
-            SQM_CU(launch_rtrsyl<R>(S, ni, ni, S, ni, ni, Rt, ni, o.blks, sc.st_solve, s));
+            SQM_CU(launch_rtrsyl<R>(S, ni, ni, S, ni, ni, Rt, ni, o.blks, sc.st_solve, s, flow, flow_cap));
             SQM_CU(launch_tc_relayout_cplx(Rt, n, ni, ni, 1.0f, 1.0f, false, YB, ld2, s));
             ep.C = (float *)W;
             SQM_CU(launch_tc_cgemm(ni, ni, ni, Qt, ni, YB, ld2, TC_EPI_CSTORE_T, ep, sc.st_solve, s));
@@ -585,7 +588,8 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
         if (root == 3)  // W is free between the transforms: it holds Z = Y S
             SQM_CU(launch_rtrsyl3<R>(S, (int)n, V, (int)n, Rt, (int)n, W, (int)n, (int)n, o.blks, sc.st_solve, s));
         else
-            SQM_CU(launch_rtrsyl<R>(S, (int)n, (int)n, S, (int)n, (int)n, Rt, (int)n, o.blks, sc.st_solve, s));
+            SQM_CU(launch_rtrsyl<R>(S, (int)n, (int)n, S, (int)n, (int)n, Rt, (int)n, o.blks, sc.st_solve, s, flow,
+                                    flow_cap));
         SQM_CU(launch_cgemm<R>(OP_N, OP_N, (int)n, (int)n, (int)n, Q, (int)n, false, Rt, (int)n, EPI_STORE, W, (int)n, nullptr, 0, 0.0, s));
         SQM_CU(launch_cgemm<R>(OP_N, OP_H, (int)n, (int)n, (int)n, W, (int)n, false, Q, (int)n,
                                cin ? EPI_CPLX_ADD_F64 : EPI_REAL_ADD_F64, nullptr, 0, dX, ldx, ldexp(1.0, e), s));

@@ -242,10 +242,15 @@ cudaError_t launch_tricbrt(const cplx<R> *T, int ldt, cplx<R> *S, int lds, cplx<
 template <class R>
 cudaError_t launch_rtrsyl3(const cplx<R> *S, int lds, const cplx<R> *V, int ldv, cplx<R> *C, int ldc, cplx<R> *Z,
                            int ldz, int n, int blks, int *d_status, cudaStream_t s);
-// S Y + Y St = C (C overwritten by Y), blocked wavefront.
+// S Y + Y St = C (C overwritten by Y), blocked: one launch per block
+// wavefront, or, given `flow` (device ints, flow_cap >= Mb Nb + 2 for
+// Mb x Nb blocks), one launch ordered by block dependencies when the blocks
+// are 32 rows and ldc is a multiple of 16 (else the wavefronts).
+size_t rtrsyl_flow_ints(int m, int n);
 template <class R>
 cudaError_t launch_rtrsyl(const cplx<R> *S, int lds, int m, const cplx<R> *St, int ldst, int nn,
-                          cplx<R> *C, int ldc, int blks, int *d_status, cudaStream_t s);
+                          cplx<R> *C, int ldc, int blks, int *d_status, cudaStream_t s, int *flow = nullptr,
+                          int64_t flow_cap = 0);
 
 // ---- real quasi-triangular factors (quasi.cu; Remark 2.1) ----
 // S = T^{1/2} for real quasi-upper-triangular T (n x n, ld): d_blk n + 1

@@ -363,9 +363,10 @@ extern "C" int sqrtm_step_rtrsyl(sqrtm_handle_t h, const void *dS, int64_t m, co
     if (blks < 1) return -7;
     if (m == 0 || nn == 0) return 0;
     StepScratch ss; void *ex;
-    if (int rc = step_scratch(h, std::max(m, nn), 0, &ss, &ex)) return rc;
+    const size_t fi = rtrsyl_flow_ints((int)m, (int)nn);
+    if (int rc = step_scratch(h, std::max(m, nn), fi * sizeof(int), &ss, &ex)) return rc;
     if (launch_rtrsyl<float>((const cplx<float> *)dS, (int)m, (int)m, (const cplx<float> *)dSt, (int)nn, (int)nn,
-                             (cplx<float> *)dC, (int)m, blks, ss.iscal + 1, h->stream)) return 7;
+                             (cplx<float> *)dC, (int)m, blks, ss.iscal + 1, h->stream, (int *)ex, (int64_t)fi)) return 7;
     int st = 0;
     if (fetch(h, &st, ss.iscal + 1, sizeof(int))) return 7;
     return st;

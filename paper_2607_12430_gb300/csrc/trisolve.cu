@@ -18,6 +18,7 @@
 // The recursion of Algorithm 1 computes the same block equations; only the
 // grouping of the update sums differs.
 #include "internal.h"
+#include "tc_common.cuh"
 
 namespace sqm {
 
@@ -114,29 +115,21 @@ __device__ void leaf_sylvester(const cplx<R> *A, const cplx<R> *B, cplx<R> *C, i
 // (each with its own double-buffered tiles and named barrier); the partial
 // sums are added in group order, then the leaf is solved.
 // ---------------------------------------------------------------------------
-template <class R, int G = SylCfg<R>::G>
-__global__ void __launch_bounds__(kTriThreads * G)
-rtrsyl_wave_kernel(const cplx<R> *__restrict__ S, int lds, int m, const cplx<R> *__restrict__ St,
-                   int ldst, int nn, cplx<R> *C, int ldc, int b, int w, int *status,
-                   const TriJob<R> *__restrict__ jobs)
+// One block equation of the Sylvester solve: S_II Y_IJ + Y_IJ St_JJ =
+// C_IJ - sum_{K>I} S_IK Y_KJ - sum_{K<J} Y_IK St_KJ, written over C_IJ.
+// The update terms are dealt round-robin to G groups of 128 threads (each
+// with its own double-buffered tiles and named barrier); the partial sums
+// are added in group order, then the leaf is solved.  tc: the CTA's
+// dynamic shared memory; bad: a shared flag.
+template <class R, int G>
+__device__ void syl_block(const cplx<R> *__restrict__ S, int lds, int m, const cplx<R> *__restrict__ St, int ldst,
+                          int nn, cplx<R> *C, int ldc, int b, int I, int J, int *status, cplx<R> *tc, int *bad)
 {
-    extern __shared__ unsigned char smraw[];
     constexpr int TT = TB * TLD, kSylGroups = G;
-    cplx<R> *tc = reinterpret_cast<cplx<R> *>(smraw);
-    __shared__ int bad;
-    if (jobs) {  // batched: matrix blockIdx.y solves S Y + Y S = C
-        const TriJob<R> jb = jobs[blockIdx.y];
-        if (!*jb.active) return;
-        S = jb.S; St = jb.S; C = jb.C; status = jb.status;
-        m = nn = lds = ldst = ldc = jb.n;
-    }
-    const int Mb = (m + b - 1) / b, Nb = (nn + b - 1) / b;
-    const int I = max(0, (Mb - 1) - w) + blockIdx.x;
-    const int J = I + w - (Mb - 1);
-    if (I >= Mb || J >= Nb || J < 0) return;
+    const int Mb = (m + b - 1) / b;
     const int g = threadIdx.x / kTriThreads, lt = threadIdx.x % kTriThreads;
     cplx<R> *ta = tc + TT * (1 + 4 * g), *tb = ta + TT, *ta2 = tb + TT, *tb2 = ta2 + TT;
-    if (threadIdx.x == 0) bad = 0;
+    if (threadIdx.x == 0) *bad = 0;
     const int i0 = I * b, j0 = J * b;
     const int bm = min(b, m - i0), bn = min(b, nn - j0);
     load_tile(tc, C + i0 + (int64_t)j0 * ldc, ldc, bm, bn);
@@ -192,12 +185,98 @@ rtrsyl_wave_kernel(const cplx<R> *__restrict__ S, int lds, int m, const cplx<R> 
     load_tile(la, S + i0 + (int64_t)i0 * lds, lds, bm, bm);
     load_tile(lb, St + j0 + (int64_t)j0 * ldst, ldst, bn, bn);
     __syncthreads();
-    leaf_sylvester(la, lb, tc, bm, bn, &bad);
+    leaf_sylvester(la, lb, tc, bm, bn, bad);
     for (int e = threadIdx.x; e < bm * bn; e += blockDim.x) {
         int i = e % bm, j = e / bm;
         C[(i0 + i) + (int64_t)(j0 + j) * ldc] = tc[i + j * TLD];
     }
-    if (threadIdx.x == 0 && bad) atomicExch(status, 2);
+    if (threadIdx.x == 0 && *bad) atomicExch(status, 2);
+}
+
+// ---------------------------------------------------------------------------
+// Sylvester wavefront: blocks (I, J) with J - I = w - (Mb - 1), one per CTA.
+// ---------------------------------------------------------------------------
+template <class R, int G = SylCfg<R>::G>
+__global__ void __launch_bounds__(kTriThreads * G)
+rtrsyl_wave_kernel(const cplx<R> *__restrict__ S, int lds, int m, const cplx<R> *__restrict__ St,
+                   int ldst, int nn, cplx<R> *C, int ldc, int b, int w, int *status,
+                   const TriJob<R> *__restrict__ jobs)
+{
+    extern __shared__ unsigned char smraw[];
+    cplx<R> *tc = reinterpret_cast<cplx<R> *>(smraw);
+    __shared__ int bad;
+    if (jobs) {  // batched: matrix blockIdx.y solves S Y + Y S = C
+        const TriJob<R> jb = jobs[blockIdx.y];
+        if (!*jb.active) return;
+        S = jb.S; St = jb.S; C = jb.C; status = jb.status;
+        m = nn = lds = ldst = ldc = jb.n;
+    }
+    const int Mb = (m + b - 1) / b, Nb = (nn + b - 1) / b;
+    const int I = max(0, (Mb - 1) - w) + blockIdx.x;
+    const int J = I + w - (Mb - 1);
+    if (I >= Mb || J >= Nb || J < 0) return;
+    syl_block<R, G>(S, lds, m, St, ldst, nn, C, ldc, b, I, J, status, tc, &bad);
+}
+
+// ---------------------------------------------------------------------------
+// Sylvester solve in one launch, by dependencies instead of wavefronts: the
+// CTAs (all co-resident) take blocks from a ticket counter in wavefront
+// order and start a block as soon as (I+1, J) and (I, J-1) are done (every
+// other block it needs is done before one of these two).  A finished block
+// is published by a flag after a device-scope fence.  Only for 32-row
+// blocks and a leading dimension of C that is a multiple of 16 entries, so
+// that no 128-byte line holds entries of two blocks: a block is then read
+// by other CTAs only after it is final, and the L1 of the SM that wrote it
+// holds its own stores.  sync: [0] ticket, [1] give-up flag, [2 + I + J Mb]
+// done flags, all zero on entry.  Each wait is bounded (status 6).
+// ---------------------------------------------------------------------------
+template <class R, int G = SylCfg<R>::G>
+__global__ void __launch_bounds__(kTriThreads * G)
+rtrsyl_flow_kernel(const cplx<R> *__restrict__ S, int lds, int m, const cplx<R> *__restrict__ St, int ldst, int nn,
+                   cplx<R> *C, int ldc, int b, int *status, int *sync, unsigned long long wait_ns)
+{
+    extern __shared__ unsigned char smraw[];
+    cplx<R> *tc = reinterpret_cast<cplx<R> *>(smraw);
+    __shared__ int bad, s_t, s_ok;
+    const int Mb = (m + b - 1) / b, Nb = (nn + b - 1) / b, nblk = Mb * Nb;
+    volatile int *flags = sync + 2;
+    for (;;) {
+        if (threadIdx.x == 0) s_t = atomicAdd(&sync[0], 1);
+        __syncthreads();
+        int t = s_t;
+        if (t >= nblk) break;
+        // ticket -> (I, J): wavefront w holds I = ilo(w) .. ihi(w), J = I + w - (Mb - 1)
+        int w = 0, I = 0;
+        for (;; ++w) {
+            const int ilo = max(0, (Mb - 1) - w), ihi = min(Mb - 1, (Mb - 1) - w + (Nb - 1));
+            const int cnt = ihi - ilo + 1;
+            if (cnt > 0 && t < cnt) { I = ilo + t; break; }
+            if (cnt > 0) t -= cnt;
+        }
+        const int J = I + w - (Mb - 1);
+        if (threadIdx.x == 0) {
+            const uint64_t t0 = globaltimer_ns();
+            int ok = 1;
+            while ((I + 1 < Mb && !flags[(I + 1) + J * Mb]) || (J > 0 && !flags[I + (J - 1) * Mb])) {
+                if (((volatile int *)sync)[1] || globaltimer_ns() - t0 > wait_ns) { ok = 0; break; }
+                __nanosleep(128);
+            }
+            __threadfence();
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) {
+            if (threadIdx.x == 0) {
+                atomicExch(status, 6);
+                atomicExch(&sync[1], 1);
+            }
+            break;
+        }
+        syl_block<R, G>(S, lds, m, St, ldst, nn, C, ldc, b, I, J, status, tc, &bad);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) atomicExch(&sync[2 + I + J * Mb], 1);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -682,15 +761,36 @@ cudaError_t launch_trisqrt_batched(const TriJob<R> *jobs, int batch, int nmax, i
     return cudaGetLastError();
 }
 
+size_t rtrsyl_flow_ints(int m, int n)
+{
+    return (size_t)((m + TB - 1) / TB) * ((n + TB - 1) / TB) + 2;
+}
+
 template <class R>
 cudaError_t launch_rtrsyl(const cplx<R> *S, int lds, int m, const cplx<R> *St, int ldst, int nn,
-                          cplx<R> *C, int ldc, int blks, int *d_status, cudaStream_t s)
+                          cplx<R> *C, int ldc, int blks, int *d_status, cudaStream_t s, int *flow, int64_t flow_cap)
 {
     if (m <= 0 || nn <= 0) return cudaSuccess;
     int b = blks < 1 ? 1 : (blks > TB ? TB : blks);
     int Mb = (m + b - 1) / b, Nb = (nn + b - 1) / b;
     size_t sm3 = (1 + 4 * SylCfg<R>::G) * TB * TLD * sizeof(cplx<R>);
     cudaError_t err;
+    if (flow && b == TB && ldc % 16 == 0 && ((uintptr_t)C % 128) == 0 && (int64_t)Mb * Nb + 2 <= flow_cap &&
+        Mb + Nb > 2) {
+        // one launch, ordered by dependencies (rtrsyl_flow_kernel)
+        if ((err = set_smem<R>((const void *)rtrsyl_flow_kernel<R>, sm3))) return err;
+        int dev = 0, sms = 0, per = 0;
+        if ((err = cudaGetDevice(&dev)) || (err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))
+            return err;
+        if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, rtrsyl_flow_kernel<R>, SylCfg<R>::THREADS, sm3)))
+            return err;
+        const int grid = (int)std::min<int64_t>((int64_t)Mb * Nb, (int64_t)std::max(1, per) * sms);
+        if ((err = cudaMemsetAsync(flow, 0, ((size_t)Mb * Nb + 2) * sizeof(int), s))) return err;
+        rtrsyl_flow_kernel<R><<<grid, SylCfg<R>::THREADS, sm3, s>>>(S, lds, m, St, ldst, nn, C, ldc, b, d_status, flow,
+                                                                    2000000000ull);
+        count_launch();
+        return cudaGetLastError();
+    }
     if ((err = set_smem<R>((const void *)rtrsyl_wave_kernel<R>, sm3))) return err;
     for (int w = 0; w <= Mb + Nb - 2; ++w) {
         int ilo = max(0, (Mb - 1) - w);
@@ -809,7 +909,7 @@ template cudaError_t launch_rtrsyl3<double>(const cplx<double> *, int, const cpl
                                             cplx<double> *, int, int, int, int *, cudaStream_t);
 template cudaError_t launch_trisqrt<float>(const cplx<float> *, int, cplx<float> *, int, int, int, int *, cudaStream_t);
 template cudaError_t launch_trisqrt<double>(const cplx<double> *, int, cplx<double> *, int, int, int, int *, cudaStream_t);
-template cudaError_t launch_rtrsyl<float>(const cplx<float> *, int, int, const cplx<float> *, int, int, cplx<float> *, int, int, int *, cudaStream_t);
-template cudaError_t launch_rtrsyl<double>(const cplx<double> *, int, int, const cplx<double> *, int, int, cplx<double> *, int, int, int *, cudaStream_t);
+template cudaError_t launch_rtrsyl<float>(const cplx<float> *, int, int, const cplx<float> *, int, int, cplx<float> *, int, int, int *, cudaStream_t, int *, int64_t);
+template cudaError_t launch_rtrsyl<double>(const cplx<double> *, int, int, const cplx<double> *, int, int, cplx<double> *, int, int, int *, cudaStream_t, int *, int64_t);
 
 }  // namespace sqm

@@ -178,7 +178,9 @@ def test_transform_in(n):
 # a7: triangular Sylvester solve
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("m,nn,blks", [(1, 1, 32), (5, 3, 32), (32, 32, 32), (33, 31, 32), (64, 100, 32),
-                                       (100, 64, 16), (96, 96, 7), (130, 129, 32)])
+                                       (100, 64, 16), (96, 96, 7), (130, 129, 32),
+                                       # blks 32 and m a multiple of 16: the one-launch dependency-ordered solve
+                                       (96, 160, 32), (256, 256, 32), (512, 512, 32), (48, 512, 32)])
 def test_rtrsyl(m, nn, blks):
     S = _c64(synth.random_upper_rhp(m, seed=70 + m))
     St = _c64(synth.random_upper_rhp(nn, seed=71 + nn))
