@@ -807,15 +807,16 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
         }
         const int nb = s_nb;
         if (s_small) {  // shifts: eigenvalues of the trailing nb x nb block
-            if (warp == 0) {
-                const int b0 = hi - nb + 1;
-                for (int e = lane; e < nb * nb; e += 32) {
-                    const int i = e % nb, j = e / nb;
-                    s_m[i + j * (NB + 1)] = (i <= j + 1) ? ldT((b0 + i) + (int64_t)(b0 + j) * ld) : cplx<R>{0, 0};
-                }
-                __syncwarp();
-                warp_small_eigvals<R, NB + 1>(s_m, nb, s_mu);
+            // the block is fetched by the whole CTA (one round trip to L2
+            // instead of a warp's nb*nb/32 dependent ones), then one warp
+            // computes its eigenvalues
+            const int b0 = hi - nb + 1;
+            for (int e = tid; e < nb * nb; e += nt) {
+                const int i = e % nb, j = e / nb;
+                s_m[i + j * (NB + 1)] = (i <= j + 1) ? ldT((b0 + i) + (int64_t)(b0 + j) * ld) : cplx<R>{0, 0};
             }
+            __syncthreads();
+            if (warp == 0) warp_small_eigvals<R, NB + 1>(s_m, nb, s_mu);
             __syncthreads();
         }
         const int nsteps = (hi - lo) + 3 * (nb - 1);
