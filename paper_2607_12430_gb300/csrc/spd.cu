@@ -31,6 +31,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "handle.h"
@@ -299,7 +300,7 @@ __global__ void larft_kernel(const R *__restrict__ G, int ldg, const R *__restri
 }
 
 template <class R>
-cudaError_t launch_back_transform(const R *Y, int ldy, const R *betas, R *Z, int n, int ldz, R *scratch,
+static cudaError_t back_transform_products(const R *Y, int ldy, const R *betas, R *Z, int n, int ldz, R *scratch,
                                   cudaStream_t s)
 {
     const int nref = std::max(0, n - 2);
@@ -317,6 +318,294 @@ cudaError_t launch_back_transform(const R *Y, int ldy, const R *betas, R *Z, int
         if ((err = launch_rgemm<R>(0, 0, mb, n, nb, Yb, ldy, W2, nb, RG_SUB, Z + r0, ldz, nullptr, nullptr, 0, 0.0, s))) return err;
     }
     return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------------------
+// FP32 back-transform in one pass per column panel.  Z <- Q Z with
+// Q = Q_0 Q_1 ... Q_{nblk-1} and Q_b = I - Y_b T_b Y_b^T acts on each column
+// of Z on its own, so a CTA that owns a panel of kBtCols columns applies
+// every block to it, last block first, with no synchronisation between CTAs:
+//   W = Y_b^T Z_p (64 x kBtCols), W <- T_b W, Z_p -= Y_b W.
+// Y_b and Z_p stream through shared memory in cp.async stages; the T_b of
+// all blocks come from one earlier launch (bt_prep_kernel, a CTA per block:
+// G_b = Y_b^T Y_b, then T_b column by column, T(i,i) = beta_i,
+// T(0:i, i) = -beta_i T(0:i, 0:i) G(0:i, i)).  Products on 4 x 4 register
+// tiles; per block and panel 2 * 64 * kBtCols FMAs per row of Y_b.
+// ---------------------------------------------------------------------------
+static constexpr int kBtCols = 32, kBtThreads = 256, kBtStages = 3;
+static constexpr int kBtKa = 32;   // rows of Y_b, Z_p per stage of W = Y_b^T Z_p
+static constexpr int kBtKc = 128;  // rows of Y_b per stage of Z_p -= Y_b W
+static constexpr int kBtStA = kBtKa * (kBackNb + kBtCols), kBtStC = kBackNb * kBtKc;
+static constexpr int kBtStg = kBtStages * (kBtStA > kBtStC ? kBtStA : kBtStC);
+static constexpr size_t kBtApplySmem = (size_t)(kBtStg + 64 * 65 + 2 * 64 * 36) * sizeof(float);
+static constexpr size_t kBtPrepSmem = (size_t)(kBtStages * kBtKa * kBackNb + 2 * 64 * 65) * sizeof(float);
+
+__device__ __forceinline__ void bt_cp4(float *dst, const float *src, bool valid)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void bt_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void bt_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Row-major stage rows (k = row of Y_b / Z_p, i = column): the group of four
+// columns holding i is XOR-ed with bits 2..4 of k, so that the copies (four
+// consecutive rows of a column per thread) and the float4 reads of the
+// products are free of bank conflicts.
+__device__ __forceinline__ int bt_swz(int k, int i) { return (((i >> 2) ^ ((k >> 2) & 7)) << 2) | (i & 3); }
+
+// cp.async copies of rows [r, r + kBtKa) of the leading nc (<= WIDTH)
+// columns of the mb-row block P (ld ldp) into the swizzled stage st (rows of
+// WIDTH floats), a thread taking four consecutive rows of one column; rows
+// at or past mb and columns at or past nc are zero-filled
+template <int WIDTH>
+__device__ __forceinline__ void bt_stage_rows(float *st, const float *P, int ldp, int r, int mb, int nc, int tid)
+{
+    for (int u = tid; u < 8 * WIDTH; u += kBtThreads) {
+        const int kq = u & 7, i = u >> 3;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = 4 * kq + q;
+            const bool v = r + k < mb && i < nc;
+            bt_cp4(st + k * WIDTH + bt_swz(k, i), v ? P + (r + k) + (int64_t)i * ldp : P, v);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBtThreads) bt_prep_kernel(const float *__restrict__ Y, int ldy,
+                                                             const float *__restrict__ betas, int n, int nref,
+                                                             float *__restrict__ Tall)
+{
+    extern __shared__ __align__(16) float btsm[];
+    float *ys = btsm, *gs = ys + kBtStages * kBtKa * kBackNb, *ts = gs + 64 * 65;
+    const int b = blockIdx.x, tid = threadIdx.x;
+    const int k0 = b * kBackNb, nb = min(kBackNb, nref - k0), r0 = k0 + 1, mb = n - r0;
+    const float *Yb = Y + r0 + (int64_t)k0 * ldy;
+    const int nch = (mb + kBtKa - 1) / kBtKa;
+    auto issue = [&](int c) {
+        if (c < nch) bt_stage_rows<kBackNb>(ys + (c % kBtStages) * kBtKa * kBackNb, Yb, ldy, c * kBtKa, mb, nb, tid);
+        bt_commit();
+    };
+    // G = Y_b^T Y_b, thread tile G(4ty.., 4tx..)
+    const int tx = tid & 15, ty = tid >> 4;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int c = 0; c < kBtStages - 1; ++c) issue(c);
+    for (int c = 0; c < nch; ++c) {
+        bt_wait<kBtStages - 2>();
+        __syncthreads();
+        issue(c + kBtStages - 1);
+        const float *st = ys + (c % kBtStages) * kBtKa * kBackNb;
+#pragma unroll 8
+        for (int k = 0; k < kBtKa; ++k) {
+            const int sw = (k >> 2) & 7;
+            const float4 a = *reinterpret_cast<const float4 *>(st + k * kBackNb + ((ty ^ sw) << 2));
+            const float4 g = *reinterpret_cast<const float4 *>(st + k * kBackNb + ((tx ^ sw) << 2));
+            const float av[4] = {a.x, a.y, a.z, a.w}, gv[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], gv[j], acc[i][j]);
+        }
+    }
+    bt_wait<0>();
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) gs[(4 * ty + i) * 65 + 4 * tx + j] = acc[i][j];
+    for (int e = tid; e < 64 * 65; e += kBtThreads) ts[e] = 0.f;
+    __syncthreads();
+    // T column by column (column i needs the columns before it)
+    for (int i = 0; i < nb; ++i) {
+        const float bi = betas[k0 + i];
+        if (tid < i) {
+            float t = 0.f;
+            for (int c = tid; c < i; ++c) t = fmaf(ts[tid * 65 + c], gs[c * 65 + i], t);
+            ts[tid * 65 + i] = -bi * t;
+        } else if (tid == i) {
+            ts[i * 65 + i] = bi;
+        }
+        __syncthreads();
+    }
+    float *Tb = Tall + (size_t)b * kBackNb * kBackNb;  // column-major, zero outside the leading nb x nb
+    for (int e = tid; e < kBackNb * kBackNb; e += kBtThreads) Tb[e] = ts[(e & 63) * 65 + (e >> 6)];
+}
+
+__global__ void __launch_bounds__(kBtThreads) bt_apply_kernel(const float *__restrict__ Y, int ldy,
+                                                              const float *__restrict__ Tall, int n, int nref,
+                                                              float *__restrict__ Z, int ldz)
+{
+    extern __shared__ __align__(16) float btsm[];
+    float *stg = btsm, *ts = stg + kBtStg, *wb = ts + 64 * 65, *w2 = wb + 64 * 36;
+    const int tid = threadIdx.x;
+    const int c0 = blockIdx.x * kBtCols, nc = min(kBtCols, n - c0);
+    const int nblk = (nref + kBackNb - 1) / kBackNb;
+    for (int b = nblk - 1; b >= 0; --b) {
+        const int k0 = b * kBackNb, nb = min(kBackNb, nref - k0), r0 = k0 + 1, mb = n - r0;
+        const float *Yb = Y + r0 + (int64_t)k0 * ldy;
+        float *Zp = Z + r0 + (int64_t)c0 * ldz;
+        {
+            const float *Tb = Tall + (size_t)b * kBackNb * kBackNb;
+            for (int e = tid; e < kBackNb * kBackNb; e += kBtThreads) ts[(e & 63) * 65 + (e >> 6)] = Tb[e];
+        }
+        // W = Y_b^T Z_p: two groups of 128 threads take the two halves of
+        // each stage's rows; thread tile W(4ty.., 4tx..)
+        {
+            const int nch = (mb + kBtKa - 1) / kBtKa;
+            auto issue = [&](int c) {
+                if (c < nch) {
+                    float *ya = stg + (c % kBtStages) * kBtStA, *za = ya + kBtKa * kBackNb;
+                    bt_stage_rows<kBackNb>(ya, Yb, ldy, c * kBtKa, mb, nb, tid);
+                    bt_stage_rows<kBtCols>(za, Zp, ldz, c * kBtKa, mb, nc, tid);
+                }
+                bt_commit();
+            };
+            const int g = tid >> 7, t = tid & 127, tx = t & 7, ty = t >> 3;
+            float acc[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+            for (int c = 0; c < kBtStages - 1; ++c) issue(c);
+            for (int c = 0; c < nch; ++c) {
+                bt_wait<kBtStages - 2>();
+                __syncthreads();
+                issue(c + kBtStages - 1);
+                const float *ya = stg + (c % kBtStages) * kBtStA, *za = ya + kBtKa * kBackNb;
+#pragma unroll 8
+                for (int kk = 0; kk < kBtKa / 2; ++kk) {
+                    const int k = g * (kBtKa / 2) + kk, sw = (k >> 2) & 7;
+                    const float4 a = *reinterpret_cast<const float4 *>(ya + k * kBackNb + ((ty ^ sw) << 2));
+                    const float4 z = *reinterpret_cast<const float4 *>(za + k * kBtCols + ((tx ^ sw) << 2));
+                    const float av[4] = {a.x, a.y, a.z, a.w}, zv[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], zv[j], acc[i][j]);
+                }
+            }
+            bt_wait<0>();
+            __syncthreads();
+            if (g == 1) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) wb[(4 * ty + i) * 36 + 4 * tx + j] = acc[i][j];
+            }
+            __syncthreads();
+            if (g == 0) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) wb[(4 * ty + i) * 36 + 4 * tx + j] += acc[i][j];
+            }
+            __syncthreads();
+        }
+        // W <- T_b W (T_b upper triangular, zero below its diagonal)
+        {
+            const int i = tid >> 2, cc = (tid & 3) * 8;
+            float a[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) a[j] = 0.f;
+#pragma unroll 4
+            for (int l = 0; l < kBackNb; ++l) {
+                const float tl = ts[i * 65 + l];
+                const float4 w0 = *reinterpret_cast<const float4 *>(wb + l * 36 + cc);
+                const float4 w1 = *reinterpret_cast<const float4 *>(wb + l * 36 + cc + 4);
+                a[0] = fmaf(tl, w0.x, a[0]); a[1] = fmaf(tl, w0.y, a[1]);
+                a[2] = fmaf(tl, w0.z, a[2]); a[3] = fmaf(tl, w0.w, a[3]);
+                a[4] = fmaf(tl, w1.x, a[4]); a[5] = fmaf(tl, w1.y, a[5]);
+                a[6] = fmaf(tl, w1.z, a[6]); a[7] = fmaf(tl, w1.w, a[7]);
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) w2[i * 36 + cc + j] = a[j];
+        }
+        __syncthreads();
+        // Z_p -= Y_b W: stages of kBtKc rows of Y_b (column-major, as stored);
+        // thread tile Z_p(4ty.., 4tx..) of each stage, its Z values loaded
+        // before the wait
+        {
+            const int nch = (mb + kBtKc - 1) / kBtKc;
+            auto issue = [&](int c) {
+                if (c < nch) {
+                    float *yc = stg + (c % kBtStages) * kBtStC;
+                    const int r = c * kBtKc;
+                    for (int e = tid; e < kBackNb * kBtKc; e += kBtThreads) {
+                        const int rr = e % kBtKc, l = e / kBtKc;
+                        const bool v = r + rr < mb && l < nb;
+                        bt_cp4(yc + l * kBtKc + rr, v ? Yb + (r + rr) + (int64_t)l * ldy : Yb, v);
+                    }
+                }
+                bt_commit();
+            };
+            const int tx = tid & 7, ty = tid >> 3;
+            for (int c = 0; c < kBtStages - 1; ++c) issue(c);
+            for (int c = 0; c < nch; ++c) {
+                const int r = c * kBtKc;
+                float z[4][4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int row = r + 4 * ty + q, col = 4 * tx + e;
+                        z[q][e] = (row < mb && col < nc) ? Zp[row + (int64_t)col * ldz] : 0.f;
+                    }
+                bt_wait<kBtStages - 2>();
+                __syncthreads();
+                issue(c + kBtStages - 1);
+                const float *yc = stg + (c % kBtStages) * kBtStC;
+                float acc[4][4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc[q][e] = 0.f;
+#pragma unroll 8
+                for (int l = 0; l < kBackNb; ++l) {
+                    const float4 y = *reinterpret_cast<const float4 *>(yc + l * kBtKc + 4 * ty);
+                    const float4 w = *reinterpret_cast<const float4 *>(w2 + l * 36 + 4 * tx);
+                    const float yv[4] = {y.x, y.y, y.z, y.w}, wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) acc[q][e] = fmaf(yv[q], wv[e], acc[q][e]);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int row = r + 4 * ty + q, col = 4 * tx + e;
+                        if (row < mb && col < nc) Zp[row + (int64_t)col * ldz] = z[q][e] - acc[q][e];
+                    }
+            }
+            bt_wait<0>();
+            __syncthreads();
+        }
+    }
+}
+
+template <class R>
+cudaError_t launch_back_transform(const R *Y, int ldy, const R *betas, R *Z, int n, int ldz, R *scratch,
+                                  cudaStream_t s)
+{
+    if constexpr (std::is_same<R, float>::value) {
+        const int nref = std::max(0, n - 2);
+        if (nref == 0) return cudaSuccess;
+        const int nblk = (int)cdiv_i(nref, kBackNb);
+        cudaError_t err;
+        if ((err = allow_max_smem((const void *)bt_prep_kernel)) || (err = allow_max_smem((const void *)bt_apply_kernel)))
+            return err;
+        bt_prep_kernel<<<nblk, kBtThreads, kBtPrepSmem, s>>>(Y, ldy, betas, n, nref, scratch);
+        count_launch();
+        bt_apply_kernel<<<(unsigned)cdiv_i(n, kBtCols), kBtThreads, kBtApplySmem, s>>>(Y, ldy, scratch, n, nref, Z, ldz);
+        count_launch();
+        return cudaGetLastError();
+    } else {
+        return back_transform_products<R>(Y, ldy, betas, Z, n, ldz, scratch, s);
+    }
 }
 
 template cudaError_t launch_back_transform<float>(const float *, int, const float *, float *, int, int, float *, cudaStream_t);

@@ -40,8 +40,10 @@ cudaError_t launch_tridiag(R *A, int n, int ld, R *Y, int ldy, R *betas, R *ws, 
 
 // Z <- Q Z for Q = H_0 ... H_{n-3} from launch_tridiag, applied in blocks of
 // kBackNb reflectors in compact WY form (Q_b = I - Y_b T_b Y_b^T, T_b upper
-// triangular), last block first: three products per block.
-// scratch: >= kBackNb * (kBackNb + 2 n) + kBackNb^2 elements of R.
+// triangular), last block first.  FP32: two launches (every T_b at once,
+// then one CTA per panel of 32 columns of Z applying all blocks to it);
+// FP64: three products per block.  Y must be zero outside the reflectors'
+// supports.  scratch: >= kBackNb * (kBackNb + 2 n) + kBackNb^2 elements of R.
 constexpr int kBackNb = 64;
 template <class R>
 cudaError_t launch_back_transform(const R *Y, int ldy, const R *betas, R *Z, int n, int ldz, R *scratch,
