@@ -29,15 +29,18 @@
 // for s >= 1, so |P_st| <= n 2^b_s 2^b_t): the accumulation stays exact
 // and the FP64 epilogue -- which costs as much as the tensor-core work on a
 // part with few FP64 units -- runs once per group instead of once per pair.
-// One launch per group: 128 x 128 output tiles of the upper block triangle
-// only (R is symmetric), K in steps of 64 BF16 values over each pair of the
-// group in turn; TMA loads both digit tiles (128 rows x 128 bytes, 128-byte
-// swizzle) from one map over all digit slices into a 6-stage ring, one
-// thread issues 4 tcgen05.mma (M = N = 128, K = 16) per stage into a
-// 128-column TMEM accumulator, and the epilogue adds the scaled tile into
-// the FP64 accumulator (the first group starts it from A, the last one
-// writes Rhat = fl32(R 4^-e), mirrored, and per-tile partial sums of
-// |R|^2).  Every mbarrier wait is bounded (status 6 on timeout).
+// One launch per group, persistent (a CTA per SM looping over 128 x 128
+// output tiles of the upper block triangle only: R is symmetric), with
+// warp roles: warp 0 issues the TMA loads of both digit tiles (128 rows x
+// 128 bytes, 128-byte swizzle, from one map over all digit slices) into a
+// 6-stage ring, K in steps of 64 BF16 values over each pair of the group in
+// turn; warp 1 issues 4 tcgen05.mma (M = N = 128, K = 16) per stage into one
+// of two 128-column TMEM accumulators; warps 2-5 run the FP64 epilogue of a
+// tile (the scaled tile added into the FP64 accumulator; the first group
+// starts it from A, the last one writes Rhat = fl32(R 4^-e), mirrored, and
+// per-warp partial sums of |R|^2) while the products of the next tile go to
+// the other accumulator.  Every mbarrier wait is bounded (status 6 on
+// timeout) and ends early once another role has given up.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -48,7 +51,8 @@
 
 namespace sqm {
 
-static constexpr int SP_BM = 128, SP_BN = 128, SP_BK = 64, SP_STAGES = 6, SP_THREADS = 128;
+static constexpr int SP_BM = 128, SP_BN = 128, SP_BK = 64, SP_STAGES = 6;
+static constexpr int SP_THREADS = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 static constexpr int SP_TILE_BYTES = SP_BM * SP_BK * 2;  // 16 KB
 static constexpr int SP_STAGE_BYTES = 2 * SP_TILE_BYTES;
 static constexpr int SP_SMEM = SP_STAGES * SP_STAGE_BYTES + 1024 + 256;
@@ -115,36 +119,59 @@ struct SplitEpi {
     double *partials;
 };
 
+// bounded mbarrier wait that also ends once another role has failed (the
+// role that times out raises the flag)
+__device__ __forceinline__ bool sp_wait(uint64_t *bar, uint32_t parity, volatile int *fail)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*fail) return false;
+        if (globaltimer_ns() - t0 > 2000000000ull) {
+            *fail = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+// 2^e as a double (exact in the normal range)
+__device__ __forceinline__ double sp_pow2(int e)
+{
+    return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(SP_THREADS, 1)
-split_gemm_kernel(const __grid_constant__ CUtensorMap mapX, const SplitGroup grp, int n, int KT, int T, SplitEpi ep,
-                  int *err)
+split_gemm_kernel(const __grid_constant__ CUtensorMap mapX, const SplitGroup grp, int n, int KT, int T, int ntiles,
+                  SplitEpi ep, int *err)
 {
     extern __shared__ unsigned char smraw[];
-    __shared__ int s_fail;
-    __shared__ double s_red[SP_THREADS / 32];
+    __shared__ volatile int s_fail;
+    __shared__ int s_issued, s_consumed, s_committed;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // upper block triangle: tile q -> (I, J), I <= J, row-major over I
-    int q = blockIdx.x, I = 0;
-    while (q >= T - I) { q -= T - I; ++I; }
-    const int J = I + q;
-    const int m0 = I * SP_BM, n0 = J * SP_BN;
-
     unsigned char *base = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(base + SP_STAGES * SP_STAGE_BYTES);
-    uint64_t *done = full + SP_STAGES;
-    uint32_t *tmem_slot = (uint32_t *)(done + SP_STAGES);
+    uint64_t *empty = full + SP_STAGES;
+    uint64_t *accf = empty + SP_STAGES;  // accumulator a holds a finished tile
+    uint64_t *acce = accf + 2;           // accumulator a is free again
+    uint32_t *tmem_slot = (uint32_t *)(acce + 2);
     if (tid == 0) {
         for (int s = 0; s < SP_STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&done[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&accf[a], 1);
+            mbar_init(&acce[a], 4 * 32);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_fail = 0;
+        s_issued = s_consumed = s_committed = 0;
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(128)
+                     "r"(2 * SP_BN)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -154,113 +181,145 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap mapX, const SplitGroup grp
     const uint32_t tmem = *tmem_slot;
 
     auto stage_ptr = [&](int s, int which) { return base + s * SP_STAGE_BYTES + which * SP_TILE_BYTES; };
-    int issued = 0, consumed = 0, committed = 0;
+    // upper block triangle: tile q -> (I, J), I <= J, row-major over I
+    auto tile_origin = [&](int q, int &m0, int &n0) {
+        int I = 0;
+        while (q >= T - I) { q -= T - I; ++I; }
+        m0 = I * SP_BM;
+        n0 = (I + q) * SP_BN;
+    };
     const int KTG = KT * grp.g;  // K steps over every pair of the group
-    if (tid == 0) {
-        // step t: pair t / KT, K block t % KT; digit slice q starts at row q n
-        // of the map (rows past n of a tile read the next slice or the zero
-        // fill; they only reach output rows / columns >= n, never stored)
-        auto issue_load = [&](int t) {
-            const int s = t % SP_STAGES, pr = t / KT, kb = t - pr * KT;
-            mbar_arrive_expect_tx(&full[s], 2 * SP_TILE_BYTES);
-            tma_load_2d(stage_ptr(s, 0), &mapX, &full[s], kb * SP_BK, grp.s[pr] * n + m0);
-            tma_load_2d(stage_ptr(s, 1), &mapX, &full[s], kb * SP_BK, grp.t[pr] * n + n0);
-        };
-        for (; issued < min(SP_STAGES + 0, KTG); ++issued) issue_load(issued);
-        constexpr uint32_t IDESC = idesc_bf16_128x128();
-        for (int t = 0; t < KTG; ++t) {
-            const int s = t % SP_STAGES;
-            if (!mbar_wait(&full[s], (t / SP_STAGES) & 1)) { s_fail = 1; break; }
-            consumed = t + 1;
-            tc_fence_after();
-            const uint32_t a0 = smem_u32(stage_ptr(s, 0)), b0 = smem_u32(stage_ptr(s, 1));
-#pragma unroll
-            for (int kk = 0; kk < SP_BK / 16; ++kk) {
-                const uint32_t off = kk * 32;  // 16 BF16 values = 32 bytes along K
-                mma_bf16(tmem, smem_desc_sw128(a0 + off), smem_desc_sw128(b0 + off), IDESC, (t > 0 || kk > 0) ? 1u : 0u);
-            }
-            mma_commit(&done[s]);
-            committed = t + 1;
-            // refill the stage tile t-1 used once its products are done
-            if (t >= 1 && issued < KTG) {
-                const int sp = (t - 1) % SP_STAGES;
-                if (!mbar_wait(&done[sp], ((t - 1) / SP_STAGES) & 1)) { s_fail = 1; break; }
-                issue_load(issued);
-                ++issued;
-            }
-        }
-    }
-    __syncthreads();
-    if (!s_fail && KTG > 0) {
-        const int tl = KTG - 1;
-        if (!mbar_wait(&done[tl % SP_STAGES], (tl / SP_STAGES) & 1)) s_fail = 1;
-    }
-    __syncthreads();
-    if (s_fail) {
-        if (tid == 0) {
-            atomicExch(err, 6);
-            for (int t = consumed; t < issued; ++t) mbar_wait(&full[t % SP_STAGES], (t / SP_STAGES) & 1);
-            if (committed > 0) mbar_wait(&done[(committed - 1) % SP_STAGES], ((committed - 1) / SP_STAGES) & 1);
-        }
-        __syncthreads();
-    } else {
-        tc_fence_after();
-        const int row = m0 + warp * 32 + lane;
-        const int rho_i = row < n ? ep.rho[row] : 0;
-        double ss = 0.0;
-        for (int c0 = 0; c0 < SP_BN; c0 += 32) {
-            uint32_t r[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-            if (row < n) {
-                // all loads of the chunk first: the stores below go to the
-                // same arrays, so loads issued after them would each wait
-                // out a full memory round trip
-                double old[32];
-                int rj[32];
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int col = n0 + c0 + j;
-                    const bool in = col < n && row <= col;
-                    old[j] = in ? ((MODE & SP_FIRST) ? ep.A[row + (int64_t)col * ep.lda]
-                                                      : ep.Racc[row + (int64_t)col * ep.ldr])
-                                : 0.0;
-                    rj[j] = col < n ? ep.rho[col] : 0;
+    if (warp == 0) {
+        if (lane == 0) {
+            // step t of a tile: pair t / KT, K block t % KT; digit slice q
+            // starts at row q n of the map (rows past n of a tile read the
+            // next slice or the zero fill; they only reach output rows /
+            // columns >= n, never stored)
+            int it = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+                int m0, n0;
+                tile_origin(tile, m0, n0);
+                for (int t = 0; t < KTG; ++t) {
+                    const int s = it % SP_STAGES, u = it / SP_STAGES;
+                    if (u > 0 && !sp_wait(&empty[s], (u - 1) & 1, &s_fail)) { ok = false; break; }
+                    const int pr = t / KT, kb = t - pr * KT;
+                    mbar_arrive_expect_tx(&full[s], 2 * SP_TILE_BYTES);
+                    tma_load_2d(stage_ptr(s, 0), &mapX, &full[s], kb * SP_BK, grp.s[pr] * n + m0);
+                    tma_load_2d(stage_ptr(s, 1), &mapX, &full[s], kb * SP_BK, grp.t[pr] * n + n0);
+                    ++it;
                 }
+            }
+            s_issued = it;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t IDESC = idesc_bf16_128x128();
+            int it = 0, lt = 0, consumed = 0, committed = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++lt) {
+                const int a = lt & 1, v = lt >> 1;
+                if (v > 0 && !sp_wait(&acce[a], (v - 1) & 1, &s_fail)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(a * SP_BN);
+                for (int t = 0; t < KTG; ++t, ++it) {
+                    const int s = it % SP_STAGES;
+                    if (!sp_wait(&full[s], (it / SP_STAGES) & 1, &s_fail)) { ok = false; break; }
+                    consumed = it + 1;
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(stage_ptr(s, 0)), b0 = smem_u32(stage_ptr(s, 1));
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int col = n0 + c0 + j;
-                    if (col >= n || row > col) continue;
-                    const double p = ldexp((double)__uint_as_float(r[j]), rho_i + rj[j] - ep.shift);
-                    const double v = old[j] - p;
-                    if (MODE & SP_LAST) {
-                        const double rs = v * ep.sc;
-                        const float rf = (float)rs;
-                        ep.Rhat[row + (int64_t)col * ep.ldh] = rf;
-                        ep.Rhat[col + (int64_t)row * ep.ldh] = rf;
-                        ss = fma(rs, rs, ss);
-                        if (row != col) ss = fma(rs, rs, ss);  // mirrored entry
-                    } else {
-                        ep.Racc[row + (int64_t)col * ep.ldr] = v;
+                    for (int kk = 0; kk < SP_BK / 16; ++kk) {
+                        const uint32_t off = kk * 32;  // 16 BF16 values = 32 bytes along K
+                        mma_bf16(d, smem_desc_sw128(a0 + off), smem_desc_sw128(b0 + off), IDESC,
+                                 (t > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    mma_commit(&empty[s]);  // the stage is free once these products are done
+                    committed = it + 1;
+                }
+                if (ok) mma_commit(&accf[a]);
+            }
+            s_consumed = consumed;
+            s_committed = committed;
+        }
+    } else {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, i.e. tile rows
+        const int qw = warp & 3;
+        int lt = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
+            const int a = lt & 1, v = lt >> 1;
+            // every lane waits; the warp leaves together if any lane gave up
+            // (the TMEM loads below are warp-collective)
+            const bool ok = sp_wait(&accf[a], v & 1, &s_fail);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc_fence_after();
+            int m0, n0;
+            tile_origin(tile, m0, n0);
+            const int row = m0 + 32 * qw + lane;
+            const int rho_i = row < n ? ep.rho[row] : 0;
+            double ss = 0.0;
+            for (int c0 = 0; c0 < SP_BN; c0 += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)(a * SP_BN + c0), r);
+                if (row < n) {
+                    // all loads of the chunk first: the stores below go to
+                    // the same arrays, so loads issued after them would each
+                    // wait out a full memory round trip
+                    double old[32];
+                    int rj[32];
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = n0 + c0 + j;
+                        const bool in = col < n && row <= col;
+                        old[j] = in ? ((MODE & SP_FIRST) ? ep.A[row + (int64_t)col * ep.lda]
+                                                          : ep.Racc[row + (int64_t)col * ep.ldr])
+                                    : 0.0;
+                        rj[j] = col < n ? ep.rho[col] : 0;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = n0 + c0 + j;
+                        if (col >= n || row > col) continue;
+                        // old - P 2^(rho_i + rho_j - shift): the product is
+                        // exact, so one rounding as in old - ldexp(P, ...)
+                        const double v2 = fma(-(double)__uint_as_float(r[j]), sp_pow2(rho_i + rj[j] - ep.shift), old[j]);
+                        if (MODE & SP_LAST) {
+                            const double rs = v2 * ep.sc;
+                            const float rf = (float)rs;
+                            ep.Rhat[row + (int64_t)col * ep.ldh] = rf;
+                            ep.Rhat[col + (int64_t)row * ep.ldh] = rf;
+                            ss = fma(rs, rs, ss);
+                            if (row != col) ss = fma(rs, rs, ss);  // mirrored entry
+                        } else {
+                            ep.Racc[row + (int64_t)col * ep.ldr] = v2;
+                        }
                     }
                 }
             }
-        }
-        if (MODE & SP_LAST) {
+            tc_fence_before();
+            mbar_arrive(&acce[a]);
+            if (MODE & SP_LAST) {
 #pragma unroll
-            for (int m = 16; m > 0; m >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, m);
-            if (lane == 0) s_red[warp] = ss;
+                for (int m = 16; m > 0; m >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, m);
+                if (lane == 0) ep.partials[4 * tile + qw] = ss;
+            }
         }
     }
     tc_fence_before();
     __syncthreads();
-    if ((MODE & SP_LAST) && tid == 0) {
-        double t = 0.0;
-        if (!s_fail)
-            for (int w = 0; w < SP_THREADS / 32; ++w) t += s_red[w];
-        ep.partials[blockIdx.x] = t;
+    if (s_fail) {
+        // wait (bounded) for the loads and products still in flight before
+        // the shared memory and TMEM are released
+        if (tid == 0) {
+            atomicExch(err, 6);
+            for (int t = s_consumed; t < s_issued; ++t) mbar_wait(&full[t % SP_STAGES], (t / SP_STAGES) & 1);
+            if (s_committed > 0) mbar_wait(&empty[(s_committed - 1) % SP_STAGES], ((s_committed - 1) / SP_STAGES) & 1);
+        }
+        __syncthreads();
     }
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * SP_BN) : "memory");
 }
 
 static bool make_bf16_map(CUtensorMap *m, const void *ptr, int64_t kdim, int64_t rows, int64_t ld)
@@ -337,18 +396,21 @@ cudaError_t launch_residual_sym_split(const double *A, int64_t lda, const double
             used += pb;
         }
     }
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::max(1, std::min(ntiles, sms));
     for (int q = 0; q < ng; ++q) {
         SplitEpi ep{A, lda, Racc, (int64_t)n, rho, shifts[q], Rhat, (int64_t)ldr, ldexp(1.0, -2 * e), partials};
         const int mode = (q == 0 ? SP_FIRST : 0) | (q == ng - 1 ? SP_LAST : 0);
         switch (mode) {
-        case 0: split_gemm_kernel<0><<<ntiles, SP_THREADS, SP_SMEM, s>>>(mapX, groups[q], n, KT, T, ep, err); break;
-        case SP_FIRST: split_gemm_kernel<SP_FIRST><<<ntiles, SP_THREADS, SP_SMEM, s>>>(mapX, groups[q], n, KT, T, ep, err); break;
-        case SP_LAST: split_gemm_kernel<SP_LAST><<<ntiles, SP_THREADS, SP_SMEM, s>>>(mapX, groups[q], n, KT, T, ep, err); break;
-        default: split_gemm_kernel<SP_FIRST | SP_LAST><<<ntiles, SP_THREADS, SP_SMEM, s>>>(mapX, groups[q], n, KT, T, ep, err);
+        case 0: split_gemm_kernel<0><<<grid, SP_THREADS, SP_SMEM, s>>>(mapX, groups[q], n, KT, T, ntiles, ep, err); break;
+        case SP_FIRST: split_gemm_kernel<SP_FIRST><<<grid, SP_THREADS, SP_SMEM, s>>>(mapX, groups[q], n, KT, T, ntiles, ep, err); break;
+        case SP_LAST: split_gemm_kernel<SP_LAST><<<grid, SP_THREADS, SP_SMEM, s>>>(mapX, groups[q], n, KT, T, ntiles, ep, err); break;
+        default: split_gemm_kernel<SP_FIRST | SP_LAST><<<grid, SP_THREADS, SP_SMEM, s>>>(mapX, groups[q], n, KT, T, ntiles, ep, err);
         }
         count_launch();
     }
-    *nparts = ntiles;
+    *nparts = 4 * ntiles;  // a partial sum per epilogue warp and tile
     return cudaGetLastError();
 }
 

@@ -35,12 +35,14 @@ def _dyadic_sym(n, bits, seed, row_exp=None):
     return X
 
 
-@pytest.mark.parametrize("n,bits", [(300, 10), (1000, 12), (513, 10)])
+@pytest.mark.parametrize("n,bits", [(300, 10), (1000, 12), (513, 10), (2200, 12)])
 def test_split_residual_bit_exact_on_dyadic_inputs(n, bits):
-    # every product and partial sum of X X is exact in FP64, and two 7-bit
-    # digits hold every entry of X relative to its row's power of two (rows
-    # scaled by 1 or 2 exercise the per-row exponents), so no digit pair is
-    # left out: both GPU residuals must equal the host's exactly
+    # every product and partial sum of X X is exact in FP64, and two digits
+    # (7 bits up to n = 1024, 6 above) hold every entry of X relative to its
+    # row's power of two (rows scaled by 1 or 2 exercise the per-row
+    # exponents), so no digit pair is left out: both GPU residuals must
+    # equal the host's exactly.  n = 2200 has more 128 x 128 output tiles
+    # than the GPU has SMs, so CTAs take several tiles each
     g = np.random.default_rng(n)
     X = _dyadic_sym(n, bits, seed=n, row_exp=g.integers(0, 2, size=n))
     A = X @ X + _dyadic_sym(n, 8, seed=n + 1) / 2.0 ** 12
