@@ -10,10 +10,12 @@
 //   2. eigenvalues of the tridiagonal matrix: FP32 multisection (one warp
 //      per eigenvalue, 32 Sturm counts per round) to a bracket of FP32
 //      width, checked and finished by FP64 multisection (a few lanes per
-//      eigenvalue, chosen to keep every SM sub-partition busy);
+//      eigenvalue) whose Sturm counts run the division-free recurrence of
+//      the leading principal minors;
 //   3. eigenvectors of the tridiagonal matrix from twisted factorisations
-//      T - lam I = L D+ L^T = U D- U^T (two lanes per eigenvalue, FP64):
-//      with r = argmin |D+_r + D-_r - (d_r - lam)|, z_r = 1,
+//      T - lam I = L D+ L^T = U D- U^T (FP64; the pivots from the leading
+//      and trailing principal minors, computed without division): with
+//      r = argmin |D+_r + D-_r - (d_r - lam)|, z_r = 1,
 //      z_i = -(e_i / D+_i) z_{i+1} above r, z_{i+1} = -(e_i / D-_{i+1}) z_i
 //      below r, normalised; members of eigenvalue clusters (closer than the
 //      eigenvalues' accuracy) are recomputed as the part of a pseudo-random
@@ -26,6 +28,7 @@
 // Y = (V^T Rhat V) ./ (s_i + s_j) with the division fused into the second
 // product, X += 2^e V Y V^T with a mirrored FP64 epilogue (X stays exactly
 // symmetric).
+#include <limits.h>
 #include <math.h>
 #include <string.h>
 
@@ -644,17 +647,90 @@ __global__ void tri_extract_kernel(const R *__restrict__ A, int n, int ld, doubl
     }
 }
 
-// number of eigenvalues of the tridiagonal matrix smaller than x
-__device__ __forceinline__ int sturm_count(const double *__restrict__ d, const double *__restrict__ e2,
-                                           int n, double x, double pivmin)
+// Number of eigenvalues of the symmetric tridiagonal T below x, from the
+// leading principal minors p_i = det((T - x I)(0:i, 0:i)):
+//   p_{-1} = 1,  p_0 = d_0 - x,  p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2}.
+// The pivots q_i = p_i / p_{i-1} of T - x I = L D L^T are negative exactly
+// where consecutive minors change sign, and by Sylvester's law of inertia
+// their number of negatives is the number of eigenvalues below x (the Sturm
+// sequence property of the minors).  A zero minor becomes -2^-500 p_{i-1},
+// a tiny pivot of the sign opposite to its predecessor (counted negative,
+// as the ratio form counts a zero pivot).  Unlike the ratio form q_i =
+// (d_i - x) - e_{i-1}^2 / q_{i-1}, the recurrence needs no division: one
+// FMA per step on the dependency chain, which is what bounds a count on a
+// part whose FP64 operations have long latency.  Every 8 steps the pair
+// (p_i, p_{i-1}) is rescaled by a power of two (exact) to stay in range;
+// the next block's d_i - x and e_{i-1}^2 are formed while the current one
+// runs, and the signs are read from the bits.
+__device__ __forceinline__ double minor_fix(double p, double pm)
 {
-    double q = d[0] - x;
-    if (fabs(q) < pivmin) q = -pivmin;
-    int c = q < 0.0;
-    for (int i = 1; i < n; ++i) {
-        q = (d[i] - x) - e2[i - 1] / q;
-        if (fabs(q) < pivmin) q = -pivmin;
-        c += q < 0.0;
+    // -2^-500 |pm| sign(pm) from the bits (no FP64 instruction: on this
+    // part every FP64 instruction of a warp costs tens of cycles): the sign
+    // flipped, the exponent lowered by 500 (floored at the smallest normal)
+    const long long pb = __double_as_longlong(p);
+    if ((pb << 1) != 0) return p;
+    const long long mb = __double_as_longlong(pm);
+    const long long ex = (mb >> 52) & 0x7FF;
+    const long long nx = ex > 501 ? ex - 500 : 1;
+    return __longlong_as_double(((mb ^ (long long)0x8000000000000000ull) & (long long)0x800FFFFFFFFFFFFFull) | (nx << 52));
+}
+
+__device__ __forceinline__ int sign_flip(double a, double b)
+{
+    return (int)((unsigned long long)(__double_as_longlong(a) ^ __double_as_longlong(b)) >> 63);
+}
+
+__device__ __forceinline__ void minor_rescale(double &p, double &pm)
+{
+    const unsigned long long a = (unsigned long long)__double_as_longlong(p) & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(pm) & 0x7FFFFFFFFFFFFFFFull;
+    const int E = max(-1000, min(1000, (int)((a > b ? a : b) >> 52) - 1023));
+    const double sc = __longlong_as_double((long long)(1023 - E) << 52);  // 2^-E
+    p *= sc;
+    pm *= sc;
+}
+
+__device__ __forceinline__ int sturm_count(const double *__restrict__ d, const double *__restrict__ e2, int n, double x)
+{
+    constexpr int B = 8;
+    double pm = 1.0, p = minor_fix(d[0] - x, 1.0);
+    int c = sign_flip(p, 1.0);
+    int i = 1;
+    double dm[B], ee[B];
+    if (i + B <= n) {
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            dm[u] = d[i + u] - x;
+            ee[u] = e2[i + u - 1];
+        }
+    }
+    for (; i + B <= n; i += B) {
+        const bool more = i + 2 * B <= n;
+        double dn[B], en[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            dn[u] = more ? d[i + B + u] - x : 0.0;
+            en[u] = more ? e2[i + B + u - 1] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            const double pn = minor_fix(fma(dm[u], p, -ee[u] * pm), p);
+            c += sign_flip(pn, p);
+            pm = p;
+            p = pn;
+        }
+        minor_rescale(p, pm);
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            dm[u] = dn[u];
+            ee[u] = en[u];
+        }
+    }
+    for (; i < n; ++i) {
+        const double pn = minor_fix(fma(d[i] - x, p, -e2[i - 1] * pm), p);
+        c += sign_flip(pn, p);
+        pm = p;
+        p = pn;
     }
     return c;
 }
@@ -712,10 +788,9 @@ __global__ void __launch_bounds__(256) multisect_f32_kernel(const float *__restr
 // eigenvalue (K divides 32): each round they count at the K interior points
 // that cut the bracket into K + 1 equal parts, and the bracket shrinks to the
 // part where the count passes j (K = 1 is bisection).  Stops at a bracket of
-// width reltol |lam| + 2u ||T|| (plus the pivot floor).  A Sturm count is a
-// chain of dependent FP64 divisions; one eigenvalue per lane leaves most SM
-// sub-partitions idle for n of a few thousand, so the launcher trades extra
-// counts for more resident warps.
+// width reltol |lam| + 2u ||T|| (plus the pivot floor).  A count costs
+// three FP64 instructions a step; the launcher picks the K that fills the
+// FP64 units of every SM sub-partition with the fewest rounds.
 static constexpr int kBisectThreads = 64;  // two warps per CTA: the warps spread over every SM
 
 template <int K>
@@ -740,10 +815,10 @@ __global__ void __launch_bounds__(kBisectThreads) bisect_f64_kernel(const double
     int c0 = 0, c1 = 0;
     if (valid && (lo < hi)) {
         if (K == 1) {
-            c0 = sturm_count(d, e2, n, lo, pivmin);
-            c1 = sturm_count(d, e2, n, hi, pivmin);
+            c0 = sturm_count(d, e2, n, lo);
+            c1 = sturm_count(d, e2, n, hi);
         } else if (l < 2) {
-            c0 = sturm_count(d, e2, n, l == 0 ? lo : hi, pivmin);
+            c0 = sturm_count(d, e2, n, l == 0 ? lo : hi);
         }
     }
     if (K > 1) {
@@ -764,7 +839,7 @@ __global__ void __launch_bounds__(kBisectThreads) bisect_f64_kernel(const double
         const bool conv = !valid || !(xfirst > lo && xlast < hi) ||
                           hi - lo <= reltol * fmax(fabs(lo), fabs(hi)) + atol;
         if (__all_sync(0xffffffffu, conv)) break;
-        const int c = conv ? 0 : sturm_count(d, e2, n, x, pivmin);
+        const int c = conv ? 0 : sturm_count(d, e2, n, x);
         unsigned above = __ballot_sync(0xffffffffu, c > j);
         if (!conv) {
             above = (K == 32) ? above : (above >> base) & ((1u << K) - 1u);
@@ -778,9 +853,11 @@ __global__ void __launch_bounds__(kBisectThreads) bisect_f64_kernel(const double
     if (valid && l == 0) lam[j] = 0.5 * (lo + hi);
 }
 
-// lanes per eigenvalue for bisect_f64_kernel: the K that minimises the
-// counts per bit of bracket per SM sub-partition in use, K / log2(K + 1)
-// counts for each of n eigenvalues spread over min(4 * SMs, n K / 32) warps
+// lanes per eigenvalue for bisect_f64_kernel.  Each FP64 instruction of a
+// warp occupies its SM sub-partition's FP64 unit for tens of cycles (GB300
+// has few FP64 units), so a round of counts costs about the number of warps
+// a sub-partition holds, ceil(n K / 32 / (4 SMs)), and shrinks the bracket
+// by K + 1: K minimises that over log2(K + 1).
 static int bisect_lanes(int n)
 {
     int dev = 0, sms = 148;
@@ -788,96 +865,270 @@ static int bisect_lanes(int n)
     int best = 1;
     double best_cost = 1e300;
     for (int K = 1; K <= 32; K *= 2) {
-        const double warps = std::min<double>(4.0 * sms, std::ceil((double)n * K / 32.0));
-        const double cost = (double)K / std::log2((double)K + 1.0) * (double)n / warps;
+        const double per_part = std::ceil(std::ceil((double)n * K / 32.0) / (4.0 * sms));
+        const double cost = per_part / std::log2((double)K + 1.0);
         if (cost < best_cost * 0.999) { best_cost = cost; best = K; }
     }
     return best;
 }
 
-// twisted factorisation eigenvectors for eigenvalues [j0, j0 + cnt), two
-// lanes per eigenvalue: lane 0 of the pair runs the backward recurrence and
-// the part of the vector above the twist, lane 1 the forward recurrence and
-// the part below it (the two chains are independent).
-// Dp, Dm: scratch [i * cnt + (j - j0)]; ZT row j (ld n) receives
-// eigenvector j
-__global__ void __launch_bounds__(32) twisted_kernel(const double *__restrict__ d, const double *__restrict__ e,
-                                                     const double *__restrict__ e2, int n,
-                                                     const double *__restrict__ bounds,
-                                                     const double *__restrict__ lam, int j0, int cnt,
-                                                     double *__restrict__ Dp, double *__restrict__ Dm,
-                                                     double *__restrict__ ZT)
+// Twisted factorisation eigenvectors for eigenvalues [j0, j0 + cnt) from the
+// minors of T - lam I, P_i = det((T - lam I)(0:i, 0:i)) (P_{-1} = 1) and
+// Q_i = det((T - lam I)(i:n, i:n)) (Q_n = 1), both by the division-free
+// recurrence of sturm_count and stored rescaled, with one power-of-two
+// exponent per 8 entries.  The pivots of T - lam I = L D+ L^T = U D- U^T are
+// D+_i = P_i / P_{i-1} and D-_i = Q_i / Q_{i+1}, and
+//   gamma_i = D+_i + D-_i - (d_i - lam) = det(T - lam I) / (P_{i-1} Q_{i+1})
+// (the reciprocal of the i-th diagonal entry of (T - lam I)^-1), so the
+// twist index r, where |gamma| is smallest, is where |P_{i-1} Q_{i+1}| is
+// largest (compared by binary exponent and leading bits; the first such i).
+// The vector z_r = 1, z_i = -(e_i / D+_i) z_{i+1} above r, z_{i+1} =
+// -(e_i / D-_{i+1}) z_i below r telescopes to
+//   z_i = P_{i-1} prod_{k=i}^{r-1} (-e_k) / P_{r-1}  (i < r),
+//   z_i = Q_{i+1} prod_{k=r}^{i-1} (-e_k) / Q_{r+1}  (i > r),
+// formed from the prefix products F_i = prod_{k<i} (-e_k) and G_i = 1 / F_i
+// (tw_prefix_kernel; both restart after a zero e, and a component in
+// another block of T than r is zero), so every component is two
+// multiplications and an exponent shift, independent of the others --
+// instead of a division chain along the vector.  A CTA of 128 threads takes
+// 32 eigenvalues: warps 0 and 1 the forward and backward minors, then all
+// four warps a quarter of the rows each for the twist and the vector.
+// P, Q: [i * cnt + (j - j0)]; SP, SQ: [k * cnt + (j - j0)], the exponent of
+// entries 8k-7 .. 8k (k >= 1; entry 0 in k = 0) of P, and of Q counted from
+// the bottom (entry n-1-i); ZT row j (ld n) receives eigenvector j.
+static constexpr int kTwBlk = 8;
+static constexpr int kTwThreads = 128;
+
+static int tw_scale_rows(int n) { return (n + kTwBlk - 2) / kTwBlk + 2; }
+
+// v with |v| in [1, 2) and x += its binary exponent (v finite, nonzero)
+__device__ __forceinline__ void mant_norm(double &v, int &x)
 {
-    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-    const int t = gt >> 1, half = gt & 1;
-    const bool valid = t < cnt;  // the rest of the last warp still synchronises
+    const long long b = __double_as_longlong(v);
+    x += (int)((b >> 52) & 0x7FF) - 1023;
+    v = __longlong_as_double((b & (long long)0x800FFFFFFFFFFFFFull) | (1023ll << 52));
+}
+
+// v 2^k by the exponent field (integer operations); 0 below the normal range
+__device__ __forceinline__ double shift_exp(double v, int k)
+{
+    const long long b = __double_as_longlong(v);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    if (ex == 0) return v;
+    const int ne = ex + k;
+    if (ne <= 0) return __longlong_as_double(b & (long long)0x8000000000000000ull);
+    return __longlong_as_double((b & (long long)0x800FFFFFFFFFFFFFull) | ((long long)min(ne, 2046) << 52));
+}
+
+// F_i = prod_{k = blk_i}^{i-1} (-e_k) and G_i = 1 / F_i as (mantissa in
+// [1, 2), exponent), blk_i the first row of i's block of T (after the last
+// zero e above i).  One CTA: a thread's rows, a segmented scan of the
+// threads' products, then the rows again from the thread's prefix.
+static constexpr int kPfxThreads = 1024;
+__global__ void __launch_bounds__(kPfxThreads) tw_prefix_kernel(const double *__restrict__ e, int n,
+                                                                double *__restrict__ Fm, int *__restrict__ Fx,
+                                                                double *__restrict__ Gm, int *__restrict__ Gx,
+                                                                int *__restrict__ blk)
+{
+    __shared__ double sm[kPfxThreads];
+    __shared__ int sx[kPfxThreads], sr[kPfxThreads], sb[kPfxThreads];
+    const int t = threadIdx.x, L = (n + kPfxThreads - 1) / kPfxThreads;
+    const int i0 = min(n, t * L), i1 = min(n, i0 + L);
+    double m = 1.0;
+    int x = 0, rs = 0, b = 0;
+    for (int i = i0; i < i1; ++i) {
+        if (i == 0 || e[i - 1] == 0.0) { m = 1.0; x = 0; rs = 1; b = i; }
+        else { m *= -e[i - 1]; mant_norm(m, x); }
+    }
+    sm[t] = m; sx[t] = x; sr[t] = rs; sb[t] = b;
+    __syncthreads();
+    for (int off = 1; off < kPfxThreads; off <<= 1) {
+        const bool has = t >= off;
+        const double am = has ? sm[t - off] : 1.0;
+        const int ax = has ? sx[t - off] : 0, ar = has ? sr[t - off] : 0, ab = has ? sb[t - off] : 0;
+        double bm = sm[t];
+        int bx = sx[t], br = sr[t], bb = sb[t];
+        __syncthreads();
+        if (has && !br) { bm *= am; bx += ax; mant_norm(bm, bx); br = ar; bb = ab; }
+        sm[t] = bm; sx[t] = bx; sr[t] = br; sb[t] = bb;
+        __syncthreads();
+    }
+    // the rows again from the product of the threads before this one
+    m = t > 0 ? sm[t - 1] : 1.0;
+    x = t > 0 ? sx[t - 1] : 0;
+    b = t > 0 ? sb[t - 1] : 0;
+    for (int i = i0; i < i1; ++i) {
+        if (i == 0 || e[i - 1] == 0.0) { m = 1.0; x = 0; b = i; }
+        else { m *= -e[i - 1]; mant_norm(m, x); }
+        Fm[i] = m; Fx[i] = x; blk[i] = b;
+        double g = 1.0 / m;
+        int gx = -x;
+        mant_norm(g, gx);
+        Gm[i] = g; Gx[i] = gx;
+    }
+}
+
+// one minors sweep, entry m = 0 .. n-1 from (dd(m), ee(m)) = (d - lam, e^2
+// coupling m to m-1), stored by put(m, value) with the running exponent in
+// sc(k) for the entries of block k
+template <class DF, class EF, class PF, class SF>
+__device__ __forceinline__ void minors_sweep(int n, DF dd, EF ee, PF put, SF sc)
+{
+    double pm = 1.0, p = minor_fix(dd(0), 1.0);
+    int ex = 0;
+    put(0, p);
+    sc(0, 0);
+    if (n > 1) sc(1, 0);
+    for (int m = 1; m < n; m += kTwBlk) {
+        const int hi = min(n, m + kTwBlk);
+        double dv[kTwBlk], ev[kTwBlk];
+#pragma unroll
+        for (int u = 0; u < kTwBlk; ++u) {
+            dv[u] = m + u < hi ? dd(m + u) : 0.0;
+            ev[u] = m + u < hi ? ee(m + u) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kTwBlk; ++u) {
+            if (m + u < hi) {
+                const double pn = minor_fix(fma(dv[u], p, -ev[u] * pm), p);
+                pm = p;
+                p = pn;
+                put(m + u, p);
+            }
+        }
+        if (hi < n) {
+            const unsigned long long a = (unsigned long long)__double_as_longlong(p) & 0x7FFFFFFFFFFFFFFFull;
+            const unsigned long long b = (unsigned long long)__double_as_longlong(pm) & 0x7FFFFFFFFFFFFFFFull;
+            const int E = max(-1000, min(1000, (int)((a > b ? a : b) >> 52) - 1023));
+            const double s2 = __longlong_as_double((long long)(1023 - E) << 52);
+            p *= s2;
+            pm *= s2;
+            ex += E;
+            sc((hi + kTwBlk - 1) / kTwBlk, ex);
+        }
+    }
+}
+
+// binary exponent and leading bits of |v| (v finite, nonzero): |v| in
+// [2^x, 2^(x+1)), f = |v| / 2^x in [1, 2)
+__device__ __forceinline__ void split_exp(double v, int &x, float &f)
+{
+    const long long b = __double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFll;
+    x = (int)(b >> 52) - 1023;
+    f = __int_as_float(0x3F800000 | (int)((b >> 29) & 0x7FFFFF));  // leading 23 bits, integer ops only
+}
+
+__global__ void __launch_bounds__(kTwThreads) twisted_kernel(const double *__restrict__ d, const double *__restrict__ e2,
+                                                             int n, const double *__restrict__ lam, int j0, int cnt,
+                                                             double *__restrict__ P, double *__restrict__ Q,
+                                                             int *__restrict__ SP, int *__restrict__ SQ,
+                                                             const double *__restrict__ Fm, const int *__restrict__ Fx,
+                                                             const double *__restrict__ Gm, const int *__restrict__ Gx,
+                                                             const int *__restrict__ blk, double *__restrict__ ZT)
+{
+    constexpr int W = kTwThreads / 32;
+    __shared__ int s_r[W][32], s_x[W][32];
+    __shared__ float s_f[W][32];
+    __shared__ double s_nrm[W][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int t = blockIdx.x * 32 + lane;
+    const bool valid = t < cnt;
     const int j = j0 + t;
     const double x = valid ? lam[j] : 0.0;
-    const double pivmin = bounds[2];
-    if (valid && half == 0) {
-        // backward: D-_{n-1} = d_{n-1} - x; D-_i = d_i - x - e_i^2 / D-_{i+1}
-        double q = d[n - 1] - x;
-        if (fabs(q) < pivmin) q = -pivmin;
-        Dm[(int64_t)(n - 1) * cnt + t] = q;
-        for (int i = n - 2; i >= 0; --i) {
-            q = (d[i] - x) - e2[i] / q;
-            if (fabs(q) < pivmin) q = -pivmin;
-            Dm[(int64_t)i * cnt + t] = q;
-        }
-    } else if (valid) {
-        // forward: D+_0 = d_0 - x; D+_i = d_i - x - e_{i-1}^2 / D+_{i-1}
-        double p = d[0] - x;
-        if (fabs(p) < pivmin) p = -pivmin;
-        Dp[t] = p;
-        for (int i = 1; i < n; ++i) {
-            p = (d[i] - x) - e2[i - 1] / p;
-            if (fabs(p) < pivmin) p = -pivmin;
-            Dp[(int64_t)i * cnt + t] = p;
-        }
+    const size_t ld = (size_t)cnt;
+    // minors: warp 0 forward (entry m = row m), warp 1 backward (entry m = row n-1-m)
+    if (valid && w == 0) {
+        minors_sweep(n, [&](int m) { return d[m] - x; }, [&](int m) { return e2[m - 1]; },
+                     [&](int m, double v) { P[(size_t)m * ld + t] = v; },
+                     [&](int k, int v) { SP[(size_t)k * ld + t] = v; });
+    } else if (valid && w == 1) {
+        minors_sweep(n, [&](int m) { return d[n - 1 - m] - x; }, [&](int m) { return e2[n - 1 - m]; },
+                     [&](int m, double v) { Q[(size_t)(n - 1 - m) * ld + t] = v; },
+                     [&](int k, int v) { SQ[(size_t)k * ld + t] = v; });
     }
-    __syncwarp();
-    // twist index r: the first i minimising |gamma_i| = |D+_i + D-_i - (d_i - x)|
-    // (lane 0 scans the first half of the indices, lane 1 the second)
-    const int mid = n / 2;
-    int r = -1;
-    double gbest = 0.0;
-    if (valid) {
-        for (int i = half ? mid : 0; i < (half ? n : mid); ++i) {
-            const double g = fabs(Dp[(int64_t)i * cnt + t] + Dm[(int64_t)i * cnt + t] - (d[i] - x));
-            if (r < 0 || g < gbest) { gbest = g; r = i; }
-        }
-    }
+    __syncthreads();
+    // the stored minor of row i with its exponent: P (i = -1: 1) and Q (i = n: 1)
+    auto getP = [&](int i, double &v, int &ex) {
+        if (i < 0) { v = 1.0; ex = 0; return; }
+        v = P[(size_t)i * ld + t];
+        ex = SP[(size_t)((i + kTwBlk - 1) / kTwBlk) * ld + t];
+    };
+    auto getQ = [&](int i, double &v, int &ex) {
+        if (i >= n) { v = 1.0; ex = 0; return; }
+        v = Q[(size_t)i * ld + t];
+        ex = SQ[(size_t)((n - 1 - i + kTwBlk - 1) / kTwBlk) * ld + t];
+    };
+    // twist index: the first i with the largest |P_{i-1} Q_{i+1}|, each warp
+    // over a quarter of the rows
+    const int q0 = (int)((int64_t)n * w / W), q1 = (int)((int64_t)n * (w + 1) / W);
     {
-        const int ro = __shfl_xor_sync(0xffffffffu, r, 1);
-        const double go = __shfl_xor_sync(0xffffffffu, gbest, 1);
-        // the pair's first minimum: lane 0's indices come first
-        if (half == 0) { if (r < 0 || (ro >= 0 && go < gbest)) r = ro; }
-        else if (ro >= 0 && !(gbest < go)) r = ro;
+        int r = -1, bx = 0;
+        float bf = 0.f;
+        if (valid) {
+            for (int i = q0; i < q1; ++i) {
+                double pv, qv;
+                int pe, qe, xp = 0, xq = 0;
+                float fp = 1.f, fq = 1.f;
+                getP(i - 1, pv, pe);
+                getQ(i + 1, qv, qe);
+                split_exp(pv, xp, fp);
+                split_exp(qv, xq, fq);
+                int xe = xp + pe + xq + qe;
+                float f = fp * fq;
+                if (f >= 2.f) { f *= 0.5f; ++xe; }
+                if (r < 0 || xe > bx || (xe == bx && f > bf)) { r = i; bx = xe; bf = f; }
+            }
+        }
+        s_r[w][lane] = r;
+        s_x[w][lane] = bx;
+        s_f[w][lane] = bf;
+        __syncthreads();
     }
-    // ZT holds Z^T column-major: component i of eigenvector j at ZT[j + i n],
-    // so the pairs of a warp (consecutive j) write neighbouring addresses
+    int r = -1;
+    {
+        int bx = 0;
+        float bf = 0.f;
+        for (int q = 0; q < W; ++q) {
+            const int rq = s_r[q][lane];
+            if (rq >= 0 && (r < 0 || s_x[q][lane] > bx || (s_x[q][lane] == bx && s_f[q][lane] > bf))) {
+                r = rq; bx = s_x[q][lane]; bf = s_f[q][lane];
+            }
+        }
+    }
+    // z_i = P_{i-1} G_i F_r / P_{r-1} above r, Q_{i+1} F_i G_r / Q_{r+1} below
     double nrm2 = 0.0;
-    if (valid && half == 0) {
-        ZT[j + (int64_t)r * n] = 1.0;
-        nrm2 = 1.0;
-        double zi = 1.0;
-        for (int i = r - 1; i >= 0; --i) {
-            zi = -(e[i] / Dp[(int64_t)i * cnt + t]) * zi;
-            ZT[j + (int64_t)i * n] = zi;
-            nrm2 = fma(zi, zi, nrm2);
-        }
-    } else if (valid) {
-        double zi = 1.0;
-        for (int i = r; i + 1 < n; ++i) {
-            zi = -(e[i] / Dm[(int64_t)(i + 1) * cnt + t]) * zi;
-            ZT[j + (int64_t)(i + 1) * n] = zi;
-            nrm2 = fma(zi, zi, nrm2);
+    if (valid && r >= 0) {
+        double pr, qr;
+        int per, qer;
+        getP(r - 1, pr, per);
+        getQ(r + 1, qr, qer);
+        const double cu = Fm[r] / pr, cd = Gm[r] / qr;
+        const int xu = Fx[r] - per, xd = Gx[r] - qer;
+        const int br = blk[r];
+        for (int i = q0; i < q1; ++i) {
+            double z = 1.0;
+            if (i < r) {
+                double pv;
+                int pe;
+                getP(i - 1, pv, pe);
+                z = blk[i] == br ? shift_exp(pv * Gm[i] * cu, pe + Gx[i] + xu) : 0.0;
+            } else if (i > r) {
+                double qv;
+                int qe;
+                getQ(i + 1, qv, qe);
+                z = blk[i] == br ? shift_exp(qv * Fm[i] * cd, qe + Fx[i] + xd) : 0.0;
+            }
+            ZT[j + (size_t)i * n] = z;
+            nrm2 = fma(z, z, nrm2);
         }
     }
-    nrm2 += __shfl_xor_sync(0xffffffffu, nrm2, 1);
-    if (valid) {
-        const double inv = 1.0 / sqrt(nrm2);
-        for (int i = half ? r + 1 : 0; i < (half ? n : r + 1); ++i) ZT[j + (int64_t)i * n] *= inv;
+    s_nrm[w][lane] = nrm2;
+    __syncthreads();
+    if (valid && r >= 0) {
+        double tot = 0.0;
+        for (int q = 0; q < W; ++q) tot += s_nrm[q][lane];
+        const double inv = 1.0 / sqrt(tot);
+        for (int i = q0; i < q1; ++i) ZT[j + (size_t)i * n] *= inv;
     }
 }
 
@@ -1052,10 +1303,21 @@ cudaError_t launch_tridiag_eig(const R *A, int n, int ld, double *lam, double *Z
         }
         count_launch();
     }
-    for (int j0 = 0; j0 < n; j0 += chunk) {
-        int cnt = std::min(chunk, n - j0);
-        twisted_kernel<<<(int)cdiv_i(2 * (int64_t)cnt, 32), 32, 0, s>>>(d, e, e2, n, bounds, lam, j0, cnt, Dp, Dm, ZT);
-        count_launch();
+    {
+        // past the region fix_clusters may spill into: the minors' exponents,
+        // then the prefix products of the off-diagonal
+        const int rows = tw_scale_rows(n);
+        int *SP = (int *)(Dm + (size_t)n * chunk + 4 * (size_t)n + 8);
+        int *SQ = SP + (size_t)rows * chunk;
+        double *Fm = (double *)(SQ + (size_t)rows * chunk + ((size_t)rows * chunk & 1)), *Gm = Fm + n;
+        int *Fx = (int *)(Gm + n), *Gx = Fx + n, *blkv = Gx + n;
+        tw_prefix_kernel<<<1, kPfxThreads, 0, s>>>(e, n, Fm, Fx, Gm, Gx, blkv); count_launch();
+        for (int j0 = 0; j0 < n; j0 += chunk) {
+            int cnt = std::min(chunk, n - j0);
+            twisted_kernel<<<(int)cdiv_i(cnt, 32), kTwThreads, 0, s>>>(d, e2, n, lam, j0, cnt, Dp, Dm, SP, SQ, Fm, Fx,
+                                                                        Gm, Gx, blkv, ZT);
+            count_launch();
+        }
     }
     // clusters: eigenvalues closer than their accuracy allows (FP32 method:
     // 1e-10 relative, vectors needed to ~1e-5; FP64 method: 2u, to ~1e-8,
@@ -1170,7 +1432,8 @@ size_t spd_bytes(int64_t n, int chunk)
     size_t np = (size_t)std::max<int64_t>(nb * nb, 2048) + 8;
     return Carve::round(np * sizeof(double)) + 256 + 3 * Carve::round(nn * sizeof(R)) +
            Carve::round(nn * sizeof(float)) + Carve::round(nn * sizeof(double)) +
-           Carve::round((2 * (size_t)n * chunk + 3 * n + 8) * sizeof(double)) +
+           Carve::round((2 * (size_t)n * chunk + 3 * n + 8 + (size_t)tw_scale_rows((int)n) * chunk + 4 * (size_t)n + 8) *
+                        sizeof(double)) +
            Carve::round(n * sizeof(double)) + 2 * Carve::round(n * sizeof(R)) +
            Carve::round((4 * n + 16) * sizeof(R)) + Carve::round((n + 8) * sizeof(R)) +
            Carve::round(((size_t)2 * kBackNb * kBackNb + (size_t)2 * kBackNb * n) * sizeof(R)) +
@@ -1204,7 +1467,8 @@ int spd_carve(sqrtm_handle_t h, int64_t n, SpdWork<R> *w)
     w->Y = w->As;  // As is dead after the tridiagonalisation
     w->Rhat = c.take<float>(nn);
     w->ZT = c.take<double>(nn);
-    w->eigscratch = c.take<double>(2 * (size_t)n * chunk + 3 * n + 8 + (4 * n + 8));
+    w->eigscratch = c.take<double>(2 * (size_t)n * chunk + 3 * n + 8 + (4 * n + 8) +
+                                   (size_t)tw_scale_rows((int)n) * chunk + (4 * n + 8));
     w->lam = c.take<double>(n);
     w->vecws = c.take<R>(4 * n + 16);
     w->betas = c.take<R>(n + 8);

@@ -54,7 +54,7 @@ cudaError_t launch_back_transform(const R *Y, int ldy, const R *betas, R *Z, int
 // ZT (row j = unit eigenvector j, n x n, ld n); eigenvectors of eigenvalue
 // clusters (closer than the eigenvalues' accuracy) are recomputed by
 // projection against all the others.  scratch: 2 n * chunk doubles plus
-// 7 n + 16.
+// 11 n + 24 plus ((n + 6) / 8 + 2) * chunk.
 template <class R>
 cudaError_t launch_tridiag_eig(const R *A, int n, int ld, double *lam, double *ZT,
                                double *scratch, int chunk, cudaStream_t s);
