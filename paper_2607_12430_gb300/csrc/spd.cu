@@ -148,12 +148,29 @@ tri_step_kernel(R *__restrict__ A, int n, int ld, int s, const R *__restrict__ c
     const R beta = cs[0];
     const R *c1 = A + (s + 1) + (int64_t)(s + 1) * ld;  // column s+1 of the block
     R acc = 0;
-    for (int i = tid; i < m; i += blockDim.x) {  // all global reads of the prologue in one pass
-        const R v = cv[i], pp = beta != R(0) ? cp[i] : R(0);
-        vs[i] = v;
-        wsm[i] = pp;
-        cn[i] = c1[i];
-        acc = fma(v, pp, acc);
+    // all global reads of the prologue, kTriPro rows per thread in flight at
+    // once (a step's prologue is a chain of L2 round trips otherwise); the
+    // products v.p are summed in the same order either way
+    constexpr int kTriPro = 8;
+    for (int b0 = tid; b0 < m; b0 += kTriThreads2 * kTriPro) {
+        R v[kTriPro], pq[kTriPro], c[kTriPro];
+#pragma unroll
+        for (int u = 0; u < kTriPro; ++u) {
+            const int i = b0 + u * kTriThreads2;
+            v[u] = i < m ? cv[i] : R(0);
+            pq[u] = (i < m && beta != R(0)) ? cp[i] : R(0);
+            c[u] = i < m ? c1[i] : R(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kTriPro; ++u) {
+            const int i = b0 + u * kTriThreads2;
+            if (i < m) {
+                vs[i] = v[u];
+                wsm[i] = pq[u];
+                cn[i] = c[u];
+                acc = fma(v[u], pq[u], acc);
+            }
+        }
     }
     acc = warp_sum(acc);
     if (lane == 0) red[warp] = acc;
@@ -257,12 +274,22 @@ cudaError_t launch_tridiag(R *A, int n, int ld, R *Y, int ldy, R *betas, R *ws, 
                                                             betas);
         count_launch();
     }
-    // up to four resident CTAs per SM: more warps, more loads in flight
+    // up to four resident CTAs per SM (more warps, more loads in flight), but
+    // never more than fit at once: the four shared vectors of m entries limit
+    // residency for large m, and a second wave of CTAs would double the step
     int dev = 0, sms = 148;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t tri_ctas = 4 * (int64_t)sms;
+    int fit = 0;  // resident CTAs per SM at the current m (grows as m shrinks)
     for (int k = 0; k + 2 < n; ++k) {
         const int m = n - k - 1;
+        if (fit < 4) {
+            int nb = 0;
+            if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tri_step_kernel<R>, kTriThreads2,
+                                                                      (size_t)4 * m * sizeof(R))))
+                return err;
+            fit = std::max(1, std::min(4, nb));
+        }
+        const int64_t tri_ctas = (int64_t)fit * sms;
         const int ctas = (int)std::min<int64_t>(std::max<int64_t>(1, cdiv_i(m - 1, kTriThreads2 / 32)), tri_ctas);
         R *c = set[k & 1], *x = set[(k + 1) & 1];
         tri_step_kernel<R><<<ctas, kTriThreads2, (size_t)4 * m * sizeof(R), s>>>(A, n, ld, k, c, c + n, c + 2 * n, x,

@@ -70,7 +70,16 @@ void split_plan(int n, int *b, int *D)
     *D = dd;
 }
 
-// one warp per row i of X (X symmetric: row i is column i, contiguous)
+// One warp per row i of X (X symmetric: row i is column i, contiguous).
+// Every step of the digit loop
+//   t = x 2^b,  m_s = round-half-even(t),  x <- t - m_s
+// is exact in FP64, so the digits depend only on the exact value of x; they
+// are formed here from that value as a 128-bit fixed-point integer
+// X = x 2^124 (exact for every x the digits can see) with integer
+// operations -- the same digits, without the ~30 FP64 instructions an entry
+// that the FP64 loop costs on a part with few FP64 units:
+//   m_s = round-half-even(X / 2^(124 - b (s + 1))),  X -= m_s 2^(124 - b (s + 1)).
+// An entry with |x| <= 2^-(b S + 1) has no nonzero digit.
 __global__ void __launch_bounds__(256) split_rows_kernel(const double *__restrict__ X, int64_t ldx, int n, int lds,
                                                          int b, int S, __nv_bfloat16 *__restrict__ Xs,
                                                          int *__restrict__ rho)
@@ -79,21 +88,36 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const double *__restric
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;  // whole warps
     const double *col = X + (int64_t)i * ldx;
-    double mx = 0.0;
-    for (int k = lane; k < n; k += 32) mx = fmax(mx, fabs(col[k]));
+    // rho_i: the smallest r with max |x_ik| < 2^r (frexp's exponent), from the bits
+    unsigned long long mx = 0;
+    for (int k = lane; k < n; k += 32)
+        mx = max(mx, (unsigned long long)__double_as_longlong(col[k]) & 0x7FFFFFFFFFFFFFFFull);
 #pragma unroll
-    for (int m = 16; m > 0; m >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, m));
+    for (int m = 16; m > 0; m >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, m));
     int r = 0;
-    if (mx > 0.0) frexp(mx, &r);  // mx < 2^r
+    if (mx != 0) {
+        const int ef = (int)(mx >> 52);
+        r = ef > 0 ? ef - 1022 : 64 - __clzll((long long)mx) - 1074;
+    }
     if (lane == 0) rho[i] = r;
-    const double scale_b = ldexp(1.0, b);
     for (int k = lane; k < lds; k += 32) {
-        double x = (k < n) ? ldexp(col[k], -r) : 0.0;  // |x| < 1, exact
+        const long long vb = k < n ? __double_as_longlong(col[k]) : 0ll;
+        const int ef = (int)((vb >> 52) & 0x7FF);
+        const long long mant = (vb & 0x000FFFFFFFFFFFFFll) | (ef ? (1ll << 52) : 0ll);
+        // |v| = mant 2^(e2), e2 = max(ef, 1) - 1075; x 2^124 = mant 2^(e2 + 124 - r)
+        const int sh = (ef ? ef : 1) - 1075 + 124 - r;
+        // |x| <= 2^-(b S + 1), i.e. mant 2^sh <= 2^(123 - b S): no digit
+        const bool zero = mant == 0 || sh < 0 || (sh + (63 - __clzll(mant)) < 123 - b * S) ||
+                          (sh + (63 - __clzll(mant)) == 123 - b * S && (mant & (mant - 1)) == 0);
+        __int128 rem = zero ? (__int128)0 : ((__int128)mant << sh);
+        if (vb < 0) rem = -rem;
         for (int s = 0; s < S; ++s) {
-            const double t = x * scale_b;  // exact
-            const double m = rint(t);      // |m| <= 2^b
-            x = t - m;  // exact (|t - m| <= 1/2, m within a factor 2 of t or 0)
-            Xs[((int64_t)s * n + i) * lds + k] = __float2bfloat16_rn((float)m);  // |m| <= 2^b: exact
+            const int shift = 124 - b * (s + 1);
+            __int128 q = rem >> shift;  // floor
+            const __int128 frac = rem - (q << shift), half = (__int128)1 << (shift - 1);
+            if (frac > half || (frac == half && (q & 1))) q += 1;
+            rem -= q << shift;
+            Xs[((int64_t)s * n + i) * lds + k] = __float2bfloat16_rn((float)(int)q);  // |m| <= 2^b: exact
         }
     }
 }
