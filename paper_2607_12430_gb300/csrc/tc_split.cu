@@ -29,18 +29,20 @@
 // for s >= 1, so |P_st| <= n 2^b_s 2^b_t): the accumulation stays exact
 // and the FP64 epilogue -- which costs as much as the tensor-core work on a
 // part with few FP64 units -- runs once per group instead of once per pair.
-// One launch per group, persistent (a CTA per SM looping over 128 x 128
-// output tiles of the upper block triangle only: R is symmetric), with
-// warp roles: warp 0 issues the TMA loads of both digit tiles (128 rows x
-// 128 bytes, 128-byte swizzle, from one map over all digit slices) into a
-// 6-stage ring, K in steps of 64 BF16 values over each pair of the group in
-// turn; warp 1 issues 4 tcgen05.mma (M = N = 128, K = 16) per stage into one
-// of two 128-column TMEM accumulators; warps 2-5 run the FP64 epilogue of a
-// tile (the scaled tile added into the FP64 accumulator; the first group
-// starts it from A, the last one writes Rhat = fl32(R 4^-e), mirrored, and
-// per-warp partial sums of |R|^2) while the products of the next tile go to
-// the other accumulator.  Every mbarrier wait is bounded (status 6 on
-// timeout) and ends early once another role has given up.
+// One persistent launch per residual: a CTA per SM loops over 128 x 128
+// output tiles of the upper block triangle only (R is symmetric) and, for
+// each tile, over every group in turn, with warp roles: warp 0 issues the
+// TMA loads of both digit tiles (128 rows x 128 bytes, 128-byte swizzle,
+// from one map over all digit slices) into a 6-stage ring, K in steps of 64
+// BF16 values over each pair of the group; warp 1 issues 4 tcgen05.mma
+// (M = N = 128, K = 16) per stage into one of two 128-column TMEM
+// accumulators; warps 2-5 run the FP64 epilogue of the previous group (its
+// scaled tile added into the tile's FP64 accumulator, which stays in L2
+// while the CTA is on the tile; the first group starts it from A, the last
+// one writes Rhat = fl32(R 4^-e), mirrored, and per-warp partial sums of
+// |R|^2) while the next group's products go to the other accumulator.
+// Every mbarrier wait is bounded (status 6 on timeout) and ends early once
+// another role has given up.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -56,7 +58,6 @@ static constexpr int SP_THREADS = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epi
 static constexpr int SP_TILE_BYTES = SP_BM * SP_BK * 2;  // 16 KB
 static constexpr int SP_STAGE_BYTES = 2 * SP_TILE_BYTES;
 static constexpr int SP_SMEM = SP_STAGES * SP_STAGE_BYTES + 1024 + 256;
-enum { SP_FIRST = 1, SP_LAST = 2 };
 
 // digit width b and pair bound D for an inner dimension n (see above)
 void split_plan(int n, int *b, int *D)
@@ -124,10 +125,16 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const double *__restric
 
 static constexpr int SP_MAXG = 16;  // pairs per group
 
-// digit-slice indices of the pairs of one group (all with the same s + t)
-struct SplitGroup {
-    int g;                 // pairs in the group
-    int s[SP_MAXG], t[SP_MAXG];
+static constexpr int SP_MAXP = SP_MAXG * (SP_MAXG + 1) / 2;  // pairs s + t <= D < SP_MAXG
+
+// the digit pairs of a residual, grouped: group q holds pairs
+// gstart[q] .. gstart[q+1]-1 (all with the same s + t) and its products carry
+// the power of two 2^-shift[q]
+struct SplitPlan {
+    int ng;
+    unsigned char ps[SP_MAXP], pt[SP_MAXP];
+    short gstart[SP_MAXP + 1];
+    short shift[SP_MAXP];
 };
 
 struct SplitEpi {
@@ -136,7 +143,6 @@ struct SplitEpi {
     double *Racc;
     int64_t ldr;
     const int *rho;
-    int shift;      // b (s + t + 2)
     float *Rhat;
     int64_t ldh;
     double sc;      // 4^-e
@@ -165,10 +171,9 @@ __device__ __forceinline__ double sp_pow2(int e)
     return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
 }
 
-template <int MODE>
 __global__ void __launch_bounds__(SP_THREADS, 1)
-split_gemm_kernel(const __grid_constant__ CUtensorMap mapX, const SplitGroup grp, int n, int KT, int T, int ntiles,
-                  SplitEpi ep, int *err)
+split_gemm_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ SplitPlan plan, int n, int KT,
+                  int T, int ntiles, SplitEpi ep, int *err)
 {
     extern __shared__ unsigned char smraw[];
     __shared__ volatile int s_fail;
@@ -177,7 +182,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap mapX, const SplitGroup grp
     unsigned char *base = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(base + SP_STAGES * SP_STAGE_BYTES);
     uint64_t *empty = full + SP_STAGES;
-    uint64_t *accf = empty + SP_STAGES;  // accumulator a holds a finished tile
+    uint64_t *accf = empty + SP_STAGES;  // accumulator a holds a finished group of a tile
     uint64_t *acce = accf + 2;           // accumulator a is free again
     uint32_t *tmem_slot = (uint32_t *)(acce + 2);
     if (tid == 0) {
@@ -212,26 +217,29 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap mapX, const SplitGroup grp
         m0 = I * SP_BM;
         n0 = (I + q) * SP_BN;
     };
-    const int KTG = KT * grp.g;  // K steps over every pair of the group
+    const int ng = plan.ng;
     if (warp == 0) {
         if (lane == 0) {
-            // step t of a tile: pair t / KT, K block t % KT; digit slice q
-            // starts at row q n of the map (rows past n of a tile read the
-            // next slice or the zero fill; they only reach output rows /
-            // columns >= n, never stored)
+            // step t of a group: its pair gstart + t / KT, K block t % KT;
+            // digit slice q starts at row q n of the map (rows past n of a
+            // tile read the next slice or the zero fill; they only reach
+            // output rows / columns >= n, never stored)
             int it = 0;
             bool ok = true;
             for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
                 int m0, n0;
                 tile_origin(tile, m0, n0);
-                for (int t = 0; t < KTG; ++t) {
-                    const int s = it % SP_STAGES, u = it / SP_STAGES;
-                    if (u > 0 && !sp_wait(&empty[s], (u - 1) & 1, &s_fail)) { ok = false; break; }
-                    const int pr = t / KT, kb = t - pr * KT;
-                    mbar_arrive_expect_tx(&full[s], 2 * SP_TILE_BYTES);
-                    tma_load_2d(stage_ptr(s, 0), &mapX, &full[s], kb * SP_BK, grp.s[pr] * n + m0);
-                    tma_load_2d(stage_ptr(s, 1), &mapX, &full[s], kb * SP_BK, grp.t[pr] * n + n0);
-                    ++it;
+                for (int q = 0; ok && q < ng; ++q) {
+                    const int p0 = plan.gstart[q], steps = KT * (plan.gstart[q + 1] - p0);
+                    for (int t = 0; t < steps; ++t) {
+                        const int s = it % SP_STAGES, u = it / SP_STAGES;
+                        if (u > 0 && !sp_wait(&empty[s], (u - 1) & 1, &s_fail)) { ok = false; break; }
+                        const int pr = p0 + t / KT, kb = t % KT;
+                        mbar_arrive_expect_tx(&full[s], 2 * SP_TILE_BYTES);
+                        tma_load_2d(stage_ptr(s, 0), &mapX, &full[s], kb * SP_BK, plan.ps[pr] * n + m0);
+                        tma_load_2d(stage_ptr(s, 1), &mapX, &full[s], kb * SP_BK, plan.pt[pr] * n + n0);
+                        ++it;
+                    }
                 }
             }
             s_issued = it;
@@ -241,27 +249,30 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap mapX, const SplitGroup grp
             constexpr uint32_t IDESC = idesc_bf16_128x128();
             int it = 0, lt = 0, consumed = 0, committed = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++lt) {
-                const int a = lt & 1, v = lt >> 1;
-                if (v > 0 && !sp_wait(&acce[a], (v - 1) & 1, &s_fail)) { ok = false; break; }
-                tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(a * SP_BN);
-                for (int t = 0; t < KTG; ++t, ++it) {
-                    const int s = it % SP_STAGES;
-                    if (!sp_wait(&full[s], (it / SP_STAGES) & 1, &s_fail)) { ok = false; break; }
-                    consumed = it + 1;
+            for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+                for (int q = 0; ok && q < ng; ++q, ++lt) {
+                    const int a = lt & 1, v = lt >> 1;
+                    if (v > 0 && !sp_wait(&acce[a], (v - 1) & 1, &s_fail)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t a0 = smem_u32(stage_ptr(s, 0)), b0 = smem_u32(stage_ptr(s, 1));
+                    const uint32_t d = tmem + (uint32_t)(a * SP_BN);
+                    const int steps = KT * (plan.gstart[q + 1] - plan.gstart[q]);
+                    for (int t = 0; t < steps; ++t, ++it) {
+                        const int s = it % SP_STAGES;
+                        if (!sp_wait(&full[s], (it / SP_STAGES) & 1, &s_fail)) { ok = false; break; }
+                        consumed = it + 1;
+                        tc_fence_after();
+                        const uint32_t a0 = smem_u32(stage_ptr(s, 0)), b0 = smem_u32(stage_ptr(s, 1));
 #pragma unroll
-                    for (int kk = 0; kk < SP_BK / 16; ++kk) {
-                        const uint32_t off = kk * 32;  // 16 BF16 values = 32 bytes along K
-                        mma_bf16(d, smem_desc_sw128(a0 + off), smem_desc_sw128(b0 + off), IDESC,
-                                 (t > 0 || kk > 0) ? 1u : 0u);
+                        for (int kk = 0; kk < SP_BK / 16; ++kk) {
+                            const uint32_t off = kk * 32;  // 16 BF16 values = 32 bytes along K
+                            mma_bf16(d, smem_desc_sw128(a0 + off), smem_desc_sw128(b0 + off), IDESC,
+                                     (t > 0 || kk > 0) ? 1u : 0u);
+                        }
+                        mma_commit(&empty[s]);  // the stage is free once these products are done
+                        committed = it + 1;
                     }
-                    mma_commit(&empty[s]);  // the stage is free once these products are done
-                    committed = it + 1;
+                    if (ok) mma_commit(&accf[a]);
                 }
-                if (ok) mma_commit(&accf[a]);
             }
             s_consumed = consumed;
             s_committed = committed;
@@ -270,62 +281,66 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap mapX, const SplitGroup grp
         // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, i.e. tile rows
         const int qw = warp & 3;
         int lt = 0;
-        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
-            const int a = lt & 1, v = lt >> 1;
-            // every lane waits; the warp leaves together if any lane gave up
-            // (the TMEM loads below are warp-collective)
-            const bool ok = sp_wait(&accf[a], v & 1, &s_fail);
-            if (!__all_sync(0xffffffffu, ok)) break;
-            tc_fence_after();
+        bool ok = true;
+        for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
             int m0, n0;
             tile_origin(tile, m0, n0);
             const int row = m0 + 32 * qw + lane;
             const int rho_i = row < n ? ep.rho[row] : 0;
-            double ss = 0.0;
-            for (int c0 = 0; c0 < SP_BN; c0 += 32) {
-                uint32_t r[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)(a * SP_BN + c0), r);
-                if (row < n) {
-                    // all loads of the chunk first: the stores below go to
-                    // the same arrays, so loads issued after them would each
-                    // wait out a full memory round trip
-                    double old[32];
-                    int rj[32];
+            for (int q = 0; q < ng; ++q, ++lt) {
+                const int a = lt & 1, v = lt >> 1;
+                const bool first = q == 0, last = q == ng - 1;
+                // every lane waits; the warp leaves together if any lane gave
+                // up (the TMEM loads below are warp-collective)
+                const bool okw = sp_wait(&accf[a], v & 1, &s_fail);
+                if (!__all_sync(0xffffffffu, okw)) { ok = false; break; }
+                tc_fence_after();
+                const int shift = plan.shift[q];
+                double ss = 0.0;
+                for (int c0 = 0; c0 < SP_BN; c0 += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)(a * SP_BN + c0), r);
+                    if (row < n) {
+                        // all loads of the chunk first: the stores below go to
+                        // the same arrays, so loads issued after them would
+                        // each wait out a full memory round trip
+                        double old[32];
+                        int rj[32];
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int col = n0 + c0 + j;
-                        const bool in = col < n && row <= col;
-                        old[j] = in ? ((MODE & SP_FIRST) ? ep.A[row + (int64_t)col * ep.lda]
-                                                          : ep.Racc[row + (int64_t)col * ep.ldr])
-                                    : 0.0;
-                        rj[j] = col < n ? ep.rho[col] : 0;
-                    }
+                        for (int j = 0; j < 32; ++j) {
+                            const int col = n0 + c0 + j;
+                            const bool in = col < n && row <= col;
+                            old[j] = in ? (first ? ep.A[row + (int64_t)col * ep.lda] : ep.Racc[row + (int64_t)col * ep.ldr])
+                                        : 0.0;
+                            rj[j] = col < n ? ep.rho[col] : 0;
+                        }
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int col = n0 + c0 + j;
-                        if (col >= n || row > col) continue;
-                        // old - P 2^(rho_i + rho_j - shift): the product is
-                        // exact, so one rounding as in old - ldexp(P, ...)
-                        const double v2 = fma(-(double)__uint_as_float(r[j]), sp_pow2(rho_i + rj[j] - ep.shift), old[j]);
-                        if (MODE & SP_LAST) {
-                            const double rs = v2 * ep.sc;
-                            const float rf = (float)rs;
-                            ep.Rhat[row + (int64_t)col * ep.ldh] = rf;
-                            ep.Rhat[col + (int64_t)row * ep.ldh] = rf;
-                            ss = fma(rs, rs, ss);
-                            if (row != col) ss = fma(rs, rs, ss);  // mirrored entry
-                        } else {
-                            ep.Racc[row + (int64_t)col * ep.ldr] = v2;
+                        for (int j = 0; j < 32; ++j) {
+                            const int col = n0 + c0 + j;
+                            if (col >= n || row > col) continue;
+                            // old - P 2^(rho_i + rho_j - shift): the product is
+                            // exact, so one rounding as in old - ldexp(P, ...)
+                            const double v2 = fma(-(double)__uint_as_float(r[j]), sp_pow2(rho_i + rj[j] - shift), old[j]);
+                            if (last) {
+                                const double rs = v2 * ep.sc;
+                                const float rf = (float)rs;
+                                ep.Rhat[row + (int64_t)col * ep.ldh] = rf;
+                                ep.Rhat[col + (int64_t)row * ep.ldh] = rf;
+                                ss = fma(rs, rs, ss);
+                                if (row != col) ss = fma(rs, rs, ss);  // mirrored entry
+                            } else {
+                                ep.Racc[row + (int64_t)col * ep.ldr] = v2;
+                            }
                         }
                     }
                 }
-            }
-            tc_fence_before();
-            mbar_arrive(&acce[a]);
-            if (MODE & SP_LAST) {
+                tc_fence_before();
+                mbar_arrive(&acce[a]);
+                if (last) {
 #pragma unroll
-                for (int m = 16; m > 0; m >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, m);
-                if (lane == 0) ep.partials[4 * tile + qw] = ss;
+                    for (int m = 16; m > 0; m >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, m);
+                    if (lane == 0) ep.partials[4 * tile + qw] = ss;
+                }
             }
         }
     }
@@ -392,48 +407,36 @@ cudaError_t launch_residual_sym_split(const double *A, int64_t lda, const double
     if (!make_bf16_map(&mapX, Xs, lds, (int64_t)S * n, lds)) return cudaErrorInvalidValue;
     const int T = (int)cdiv_i(n, SP_BM), ntiles = T * (T + 1) / 2, KT = lds / SP_BK;
     cudaError_t er;
-    if ((er = allow_max_smem((const void *)split_gemm_kernel<0>))) return er;
-    if ((er = allow_max_smem((const void *)split_gemm_kernel<SP_FIRST>))) return er;
-    if ((er = allow_max_smem((const void *)split_gemm_kernel<SP_LAST>))) return er;
-    if ((er = allow_max_smem((const void *)split_gemm_kernel<SP_FIRST | SP_LAST>))) return er;
+    if ((er = allow_max_smem((const void *)split_gemm_kernel))) return er;
     // groups of pairs with the same s + t whose integer bounds sum to <= 2^24
-    SplitGroup groups[(SP_MAXG * (SP_MAXG + 1)) / 2];
-    int shifts[(SP_MAXG * (SP_MAXG + 1)) / 2];
-    int ng = 0;
+    SplitPlan plan{};
+    int np = 0;
     for (int d = 0; d <= D; ++d) {
         double used = 0.0;
         bool open = false;
         for (int si = 0; si <= d; ++si) {
             const int ti = d - si;
             const double pb = (double)n * ldexp(1.0, si == 0 ? b : b - 1) * ldexp(1.0, ti == 0 ? b : b - 1);
-            if (!open || used + pb > 16777216.0 || groups[ng - 1].g == SP_MAXG) {
-                groups[ng].g = 0;
-                shifts[ng] = b * (d + 2);
-                ++ng;
+            if (!open || used + pb > 16777216.0 || np - plan.gstart[plan.ng - 1] == SP_MAXG) {
+                plan.gstart[plan.ng] = (short)np;
+                plan.shift[plan.ng] = (short)(b * (d + 2));
+                ++plan.ng;
                 used = 0.0;
                 open = true;
             }
-            SplitGroup &gr = groups[ng - 1];
-            gr.s[gr.g] = si;
-            gr.t[gr.g] = ti;
-            ++gr.g;
+            plan.ps[np] = (unsigned char)si;
+            plan.pt[np] = (unsigned char)ti;
+            ++np;
             used += pb;
         }
     }
+    plan.gstart[plan.ng] = (short)np;
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::max(1, std::min(ntiles, sms));
-    for (int q = 0; q < ng; ++q) {
-        SplitEpi ep{A, lda, Racc, (int64_t)n, rho, shifts[q], Rhat, (int64_t)ldr, ldexp(1.0, -2 * e), partials};
-        const int mode = (q == 0 ? SP_FIRST : 0) | (q == ng - 1 ? SP_LAST : 0);
-        switch (mode) {
-        case 0: split_gemm_kernel<0><<<grid, SP_THREADS, SP_SMEM, s>>>(mapX, groups[q], n, KT, T, ntiles, ep, err); break;
-        case SP_FIRST: split_gemm_kernel<SP_FIRST><<<grid, SP_THREADS, SP_SMEM, s>>>(mapX, groups[q], n, KT, T, ntiles, ep, err); break;
-        case SP_LAST: split_gemm_kernel<SP_LAST><<<grid, SP_THREADS, SP_SMEM, s>>>(mapX, groups[q], n, KT, T, ntiles, ep, err); break;
-        default: split_gemm_kernel<SP_FIRST | SP_LAST><<<grid, SP_THREADS, SP_SMEM, s>>>(mapX, groups[q], n, KT, T, ntiles, ep, err);
-        }
-        count_launch();
-    }
+    SplitEpi ep{A, lda, Racc, (int64_t)n, rho, Rhat, (int64_t)ldr, ldexp(1.0, -2 * e), partials};
+    split_gemm_kernel<<<grid, SP_THREADS, SP_SMEM, s>>>(mapX, plan, n, KT, T, ntiles, ep, err);
+    count_launch();
     *nparts = 4 * ntiles;  // a partial sum per epilogue warp and tile
     return cudaGetLastError();
 }
