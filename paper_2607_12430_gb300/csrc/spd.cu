@@ -43,7 +43,11 @@
 
 namespace sqm {
 
-static constexpr int kTriThreads2 = 256;
+// CTA of the tridiagonalisation steps: every CTA reads the step's v, p and
+// next column (3 m values) from L2 before its columns, so few wide CTAs (one
+// per SM) keep that redundant traffic small; a warp takes one column
+static constexpr int kTriThreads2 = 1024;
+static constexpr int kTriMaxFit = 2048 / kTriThreads2 < 4 ? 2048 / kTriThreads2 : 4;
 static constexpr int kTriBatch = 8;  // rows in flight per lane in tri_step_kernel
 
 // reflector for x = A(k+1:n, k) (real): v = x + sign(x0) ||x|| e1,
@@ -195,29 +199,36 @@ tri_step_kernel(R *__restrict__ A, int n, int ld, int s, const R *__restrict__ c
         real_reflector<R>(cn + 1, m - 1, vn, s_scal);
         bn = s_scal[0];
     }
-    if (blockIdx.x == 0) {
+    // the step's outputs, split over all CTAs (each holds vn and the
+    // scalars): column s's final entries, the reflector of step s+1 (into Y
+    // and nv), its scalars
+    {
+        const int gt = blockIdx.x * blockDim.x + tid, gs = gridDim.x * blockDim.x;
+        const bool lead = blockIdx.x == 0 && tid == 0;
         if (beta != R(0))
-            for (int i = tid; i < m; i += blockDim.x) A[(s + 1 + i) + (int64_t)s * ld] = (i == 0) ? -cs[2] * cs[1] : R(0);
-        if (s >= 1 && tid == 0) A[s + (int64_t)s * ld] = cs[3];
+            for (int i = gt; i < m; i += gs) A[(s + 1 + i) + (int64_t)s * ld] = (i == 0) ? -cs[2] * cs[1] : R(0);
+        if (s >= 1 && lead) A[s + (int64_t)s * ld] = cs[3];
         if (more) {
             R *yk = Y + (s + 2) + (int64_t)(s + 1) * ldy;
-            for (int i = tid; i < m - 1; i += blockDim.x) {
+            for (int i = gt; i < m - 1; i += gs) {
                 nv[i] = vn[i];
                 yk[i] = vn[i];
             }
-            if (tid == 0) {
+            if (lead) {
                 ns[0] = s_scal[0]; ns[1] = s_scal[1]; ns[2] = s_scal[2]; ns[3] = cn[0];
                 betas[s + 1] = bn;
             }
-        } else if (tid == 0) {
+        } else if (lead) {
             ns[4] = cn[0];
             ns[5] = cn[1];
         }
     }
-    const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
+    // columns interleaved over the CTAs (column 1 + CTA + grid * warp), so
+    // that every SM holds columns while there are as many as SMs
+    const int gw = warp * gridDim.x + blockIdx.x;
     const int nwt = gridDim.x * (blockDim.x >> 5);
     // columns of the block: the loads of a batch of kTriBatch rows per lane
-    // are issued before any is used (the pass is bound by L2 latency)
+    // are issued before any is used
     for (int j = 1 + gw; j < m; j += nwt) {
         R *c = A + (s + 1) + (int64_t)(s + 1 + j) * ld;
         const R vj = vs[j], wj = wsm[j];
@@ -274,23 +285,22 @@ cudaError_t launch_tridiag(R *A, int n, int ld, R *Y, int ldy, R *betas, R *ws, 
                                                             betas);
         count_launch();
     }
-    // up to four resident CTAs per SM (more warps, more loads in flight), but
-    // never more than fit at once: the four shared vectors of m entries limit
-    // residency for large m, and a second wave of CTAs would double the step
+    // as many CTAs as fit at once, never a second wave (the four shared
+    // vectors of m entries limit residency for large m)
     int dev = 0, sms = 148;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int fit = 0;  // resident CTAs per SM at the current m (grows as m shrinks)
     for (int k = 0; k + 2 < n; ++k) {
         const int m = n - k - 1;
-        if (fit < 4) {
+        if (fit < kTriMaxFit) {
             int nb = 0;
             if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tri_step_kernel<R>, kTriThreads2,
                                                                       (size_t)4 * m * sizeof(R))))
                 return err;
-            fit = std::max(1, std::min(4, nb));
+            fit = std::max(1, std::min(kTriMaxFit, nb));
         }
         const int64_t tri_ctas = (int64_t)fit * sms;
-        const int ctas = (int)std::min<int64_t>(std::max<int64_t>(1, cdiv_i(m - 1, kTriThreads2 / 32)), tri_ctas);
+        const int ctas = (int)std::min<int64_t>(std::max<int64_t>(1, m - 1), tri_ctas);
         R *c = set[k & 1], *x = set[(k + 1) & 1];
         tri_step_kernel<R><<<ctas, kTriThreads2, (size_t)4 * m * sizeof(R), s>>>(A, n, ld, k, c, c + n, c + 2 * n, x,
                                                                                   x + n, x + 2 * n, Y, ldy, betas);
