@@ -668,13 +668,29 @@ __global__ void tri_extract_kernel(const R *__restrict__ A, int n, int ld, doubl
         e2f[i] = (float)e2[i];
     }
     __syncthreads();
+    // Gershgorin interval and the largest e^2: a block reduction (min, max
+    // and max are exact, so the order does not matter)
+    __shared__ double s_gl[32], s_gu[32], s_em[32];
+    double gl = INFINITY, gu = -INFINITY, emax2 = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double r = fabs(e[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0);
+        gl = fmin(gl, d[i] - r);
+        gu = fmax(gu, d[i] + r);
+        emax2 = fmax(emax2, e2[i]);
+    }
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) {
+        gl = fmin(gl, __shfl_xor_sync(0xffffffffu, gl, m));
+        gu = fmax(gu, __shfl_xor_sync(0xffffffffu, gu, m));
+        emax2 = fmax(emax2, __shfl_xor_sync(0xffffffffu, emax2, m));
+    }
+    if ((threadIdx.x & 31) == 0) { s_gl[threadIdx.x >> 5] = gl; s_gu[threadIdx.x >> 5] = gu; s_em[threadIdx.x >> 5] = emax2; }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        double gl = INFINITY, gu = -INFINITY, emax2 = 0.0;
-        for (int i = 0; i < n; ++i) {
-            double r = fabs(e[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0);
-            gl = fmin(gl, d[i] - r);
-            gu = fmax(gu, d[i] + r);
-            emax2 = fmax(emax2, e2[i]);
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+            gl = fmin(gl, s_gl[q]);
+            gu = fmax(gu, s_gu[q]);
+            emax2 = fmax(emax2, s_em[q]);
         }
         double w = fmax(fabs(gl), fabs(gu));
         bounds[0] = gl - 4.0 * 1.1102230246251565e-16 * w * n - 1e-300;
@@ -1186,23 +1202,40 @@ __global__ void __launch_bounds__(kTwThreads) twisted_kernel(const double *__res
 static constexpr int kClP = 8;  // row chunks of the projection products
 
 // clusters as member ranges [first[c], last[c]]; mask = 1 everywhere
-__global__ void cluster_scan_kernel(const double *__restrict__ lam, int n, double rtol, double atol_rel,
-                                    const double *__restrict__ bounds, int *__restrict__ first,
-                                    int *__restrict__ last, int *__restrict__ ncl, int *__restrict__ mask)
+static constexpr int kClScan = 1024;
+__global__ void __launch_bounds__(kClScan) cluster_scan_kernel(const double *__restrict__ lam, int n, double rtol,
+                                                              double atol_rel, const double *__restrict__ bounds,
+                                                              int *__restrict__ first, int *__restrict__ last,
+                                                              int *__restrict__ ncl, int *__restrict__ mask)
 {
-    if (blockIdx.x || threadIdx.x) return;
+    // one CTA: each thread a chunk of j; member j (j >= 1) when it lies
+    // within the tolerance of j - 1; the starts are numbered by a block scan
+    __shared__ int s_cnt[kClScan];
     const double atol = atol_rel * fmax(fabs(bounds[0]), fabs(bounds[1]));
-    int m = 0;
-    bool prev = false;
-    mask[0] = 1;
-    for (int j = 1; j < n; ++j) {
+    auto member = [&](int j) {
+        return j >= 1 && j < n && lam[j] - lam[j - 1] <= rtol * fmax(fabs(lam[j]), fabs(lam[j - 1])) + atol;
+    };
+    const int t = threadIdx.x, L = (n + kClScan - 1) / kClScan, j0 = min(n, t * L), j1 = min(n, j0 + L);
+    int cnt = 0;
+    for (int j = j0; j < j1; ++j) {
         mask[j] = 1;
-        const bool mem = lam[j] - lam[j - 1] <= rtol * fmax(fabs(lam[j]), fabs(lam[j - 1])) + atol;
-        if (mem && !prev) first[m++] = j;
-        if (mem) last[m - 1] = j;
-        prev = mem;
+        cnt += member(j) && !member(j - 1);
     }
-    *ncl = m;
+    s_cnt[t] = cnt;
+    __syncthreads();
+    for (int off = 1; off < kClScan; off <<= 1) {
+        const int v = t >= off ? s_cnt[t - off] : 0;
+        __syncthreads();
+        s_cnt[t] += v;
+        __syncthreads();
+    }
+    int c = s_cnt[t] - cnt;  // clusters started before this chunk
+    for (int j = j0; j < j1; ++j) {
+        if (!member(j)) continue;
+        if (!member(j - 1)) first[c++] = j;
+        if (!member(j + 1)) last[c - 1] = j;
+    }
+    if (t == kClScan - 1) *ncl = s_cnt[t];
 }
 
 // x_i uniform in [-1, 1): a counter-based hash (SplitMix64 finaliser) of (j, i)
@@ -1284,7 +1317,7 @@ static cudaError_t fix_clusters(const double *lam, const double *bounds, int n, 
 {
     double *part = scratch, *x = part + (size_t)kClP * n, *c = x + n;
     int *first = (int *)(c + n), *last = first + n, *mask = last + n, *ncl = mask + n;
-    cluster_scan_kernel<<<1, 32, 0, s>>>(lam, n, rtol, atol_rel, bounds, first, last, ncl, mask); count_launch();
+    cluster_scan_kernel<<<1, kClScan, 0, s>>>(lam, n, rtol, atol_rel, bounds, first, last, ncl, mask); count_launch();
     int m = 0;
     cudaError_t err = cudaMemcpyAsync(&m, ncl, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (!err) err = cudaStreamSynchronize(s);
