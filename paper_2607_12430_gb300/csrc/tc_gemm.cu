@@ -10,14 +10,18 @@
 // lo = tf32(x - hi); C = A_hi B_hi + A_hi B_lo + A_lo B_hi is accumulated in
 // FP32 in tensor memory (relative error about 2^-21, close to FP32).
 //
-// Per CTA: a 128 x 128 tile of C, K in steps of 32.  TMA loads the FP32 tiles
-// (128 rows x 128 bytes, 128-byte swizzle) into a 3-stage ring; all threads
-// split them in shared memory (hi in place, lo beside it); one thread issues
-// 3 x 4 tcgen05.mma (M = 128, N = 128, K = 8) per stage and commits them to
-// the stage's mbarrier; the accumulator (128 TMEM columns) is read back with
-// tcgen05.ld for a fused epilogue.  Every mbarrier wait is bounded (about
-// 2 s of globaltimer); on timeout the kernel records status 6, drains its
-// outstanding copies (bounded too), frees its TMEM and returns.
+// Persistent: one CTA per SM loops over 128 x 128 tiles of C (the upper
+// block triangle for the mirrored epilogue), K in steps of 32, with warp
+// roles: warp 0 issues the TMA loads of the FP32 tiles (128 rows x 128
+// bytes, 128-byte swizzle) into a 3-stage ring; warps 2-5 split each landed
+// stage in shared memory (hi in place, lo beside it); warp 1 issues 3 x 4
+// tcgen05.mma (M = 128, N = 128, K = 8) per stage into one of two
+// 128-column TMEM accumulators and commits them to the stage's mbarrier;
+// warps 6-9 read the other accumulator back with tcgen05.ld for the fused
+// epilogue of the previous tile.  Every mbarrier wait is bounded (about 2 s
+// of globaltimer) and ends early once another role has given up; then the
+// kernel records status 6, drains its outstanding copies (bounded too),
+// frees its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -29,7 +33,10 @@
 
 namespace sqm {
 
-static constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 32, TC_STAGES = 3, TC_THREADS = 128;
+static constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 32, TC_STAGES = 3;
+static constexpr int TC_SPLIT_WARPS = 4;
+// warp 0 TMA, warp 1 MMA, warps 2-5 split, warps 6-9 epilogue
+static constexpr int TC_THREADS = 32 * (2 + TC_SPLIT_WARPS + 4);
 static constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 4;          // 16 KB
 static constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;          // A, A_lo, B, B_lo
 static constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 256;
@@ -43,35 +50,138 @@ __device__ __forceinline__ float to_tf32(float x)
     return __uint_as_float(b);
 }
 
+// the fused epilogue of one row of a tile for accumulator columns
+// c0 .. c0+31 (r: the row's 32 FP32 values); the FP64 epilogues go in two
+// halves of 16 columns, each with all its loads first (the stores go to the
+// same array, so a load after them would wait out a full round trip)
+template <int EPI>
+__device__ __forceinline__ void tc3_epilogue_chunk(const uint32_t (&r)[32], int row, int n0, int c0, int N,
+                                                   const TcEpilogue &ep)
+{
+    if (EPI == TC_EPI_SYM_ADD_F64) {
+#pragma unroll
+        for (int h = 0; h < 32; h += 16) {
+            double old[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int col = n0 + c0 + h + j;
+                old[j] = (col < N && row <= col) ? ep.X[row + (int64_t)col * ep.ldx] : 0.0;
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int col = n0 + c0 + h + j;
+                if (col >= N || row > col) continue;
+                const double x = old[j] + (double)__uint_as_float(r[h + j]) * ep.scale;
+                ep.X[row + (int64_t)col * ep.ldx] = x;
+                ep.X[col + (int64_t)row * ep.ldx] = x;
+            }
+        }
+    } else if (EPI == TC_EPI_CSTORE || EPI == TC_EPI_CSTORE_T) {
+        // accumulator columns (2q, 2q+1) = (Re, Im) of complex column q
+#pragma unroll
+        for (int j = 0; j < 32; j += 2) {
+            const int col = n0 + c0 + j;
+            if (col >= N) continue;  // N even: col + 1 < N as well
+            const int q = col >> 1;
+            const int64_t at = EPI == TC_EPI_CSTORE ? (row + (int64_t)q * ep.ldc) : (q + (int64_t)row * ep.ldc);
+            *reinterpret_cast<float2 *>(ep.C + 2 * at) = make_float2(__uint_as_float(r[j]), __uint_as_float(r[j + 1]));
+        }
+    } else if (EPI == TC_EPI_RE_F64_STORE || EPI == TC_EPI_RE_F64_ADD) {
+#pragma unroll
+        for (int h = 0; h < 32; h += 16) {
+            double old[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int col = n0 + c0 + h + j;
+                old[j] = (EPI == TC_EPI_RE_F64_ADD && col < N) ? ep.X[row + (int64_t)col * ep.ldx] : 0.0;
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int col = n0 + c0 + h + j;
+                if (col >= N) continue;
+                ep.X[row + (int64_t)col * ep.ldx] = old[j] + (double)__uint_as_float(r[h + j]) * ep.scale;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int col = n0 + c0 + j;
+            if (col >= N) continue;
+            const float v = __uint_as_float(r[j]);
+            if (EPI == TC_EPI_STORE) ep.C[row + (int64_t)col * ep.ldc] = v;
+            else ep.C[row + (int64_t)col * ep.ldc] = v / (ep.s[row] + ep.s[col]);
+        }
+    }
+}
+
+// bounded mbarrier wait that also ends once another role has failed (the
+// role that times out raises the flag)
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, volatile int *fail)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*fail) return false;
+        if (globaltimer_ns() - t0 > 2000000000ull) {
+            *fail = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
 template <int EPI>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc3_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
                 int K, TcEpilogue ep, int *err)
 {
     extern __shared__ unsigned char smraw[];
+    __shared__ volatile int s_fail;
+    __shared__ int s_issued, s_consumed, s_committed;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_BN;
-    if ((EPI == TC_EPI_SYM_ADD_F64) && m0 > n0) return;  // mirrored epilogue: upper block triangle only
     static_assert(TC_BN % 2 == 0, "complex column pairs stay within a tile");
+    // tiles: row-major over the (M / 128) x (N / 128) grid, or its upper
+    // block triangle for the mirrored epilogue
+    const int TM = (M + TC_BM - 1) / TC_BM, TN = (N + TC_BN - 1) / TC_BN;
+    const bool tri = EPI == TC_EPI_SYM_ADD_F64;
+    const int ntiles = tri ? TN * (TN + 1) / 2 : TM * TN;  // the mirrored product is square
+    auto tile_origin = [&](int q, int &m0, int &n0) {
+        if (tri) {
+            int I = 0;
+            while (q >= TN - I) { q -= TN - I; ++I; }
+            m0 = I * TC_BM;
+            n0 = (I + q) * TC_BN;
+        } else {
+            m0 = (q / TN) * TC_BM;
+            n0 = (q % TN) * TC_BN;
+        }
+    };
 
     // 1024-aligned stage ring, then barriers and the TMEM address slot
     unsigned char *base = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-    uint64_t *full = (uint64_t *)(base + TC_STAGES * TC_STAGE_BYTES);
-    uint64_t *done = full + TC_STAGES;
-    uint32_t *tmem_slot = (uint32_t *)(done + TC_STAGES);
-    __shared__ int s_fail;
-
+    uint64_t *full = (uint64_t *)(base + TC_STAGES * TC_STAGE_BYTES);  // FP32 tiles landed
+    uint64_t *split = full + TC_STAGES;                                 // hi / lo written
+    uint64_t *empty = split + TC_STAGES;                                // products of the stage done
+    uint64_t *accf = empty + TC_STAGES;                                 // accumulator holds a tile
+    uint64_t *acce = accf + 2;                                          // accumulator free again
+    uint32_t *tmem_slot = (uint32_t *)(acce + 2);
     if (tid == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&done[s], 1);
+            mbar_init(&split[s], TC_SPLIT_WARPS * 32);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&accf[a], 1);
+            mbar_init(&acce[a], 4 * 32);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_fail = 0;
+        s_issued = s_consumed = s_committed = 0;
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(128)
+                     "r"(2 * TC_BN)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -82,151 +192,123 @@ tc3_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
 
     const int KT = (K + TC_BK - 1) / TC_BK;
     auto stage_ptr = [&](int s, int which) { return base + s * TC_STAGE_BYTES + which * TC_TILE_BYTES; };
-    auto issue_load = [&](int t) {
-        const int s = t % TC_STAGES;
-        mbar_arrive_expect_tx(&full[s], 2 * TC_TILE_BYTES);
-        tma_load_2d(stage_ptr(s, 0), &mapA, &full[s], t * TC_BK, m0);
-        tma_load_2d(stage_ptr(s, 2), &mapB, &full[s], t * TC_BK, n0);
-    };
-    int issued = 0;  // TMA loads issued (thread 0's count)
-    if (tid == 0)
-        for (; issued < std::min(TC_STAGES - 1, KT); ++issued) issue_load(issued);
-
-    constexpr uint32_t IDESC = idesc_tf32_128x128();
-    bool fail = false;
-    int consumed = 0;   // tiles whose TMA completion every thread has observed
-    int committed = 0;  // tiles whose MMAs thread 0 has committed
-    for (int t = 0; t < KT && !fail; ++t) {
-        const int s = t % TC_STAGES;
-        // producer: refill the stage that tile t-1 used, once its MMAs are done
-        if (tid == 0 && issued < KT) {
-            if (t >= 1) {
-                const int sp = (t - 1) % TC_STAGES;
-                if (!mbar_wait(&done[sp], ((t - 1) / TC_STAGES) & 1)) s_fail = 1;
-            }
-            if (!s_fail) { issue_load(issued); ++issued; }
-        }
-        // everyone: wait for tile t
-        if (!mbar_wait(&full[s], (t / TC_STAGES) & 1)) s_fail = 1;
-        __syncthreads();
-        if (s_fail) { fail = true; break; }
-        consumed = t + 1;
-        // split A and B into hi (in place) and lo (beside)
-        {
-            float4 *a = (float4 *)stage_ptr(s, 0), *alo = (float4 *)stage_ptr(s, 1);
-            float4 *b = (float4 *)stage_ptr(s, 2), *blo = (float4 *)stage_ptr(s, 3);
-            constexpr int NV = TC_TILE_BYTES / 16;
-            for (int v = tid; v < NV; v += TC_THREADS) {
-                float4 x = a[v], h, l;
-                h.x = to_tf32(x.x); h.y = to_tf32(x.y); h.z = to_tf32(x.z); h.w = to_tf32(x.w);
-                l.x = to_tf32(x.x - h.x); l.y = to_tf32(x.y - h.y); l.z = to_tf32(x.z - h.z); l.w = to_tf32(x.w - h.w);
-                a[v] = h; alo[v] = l;
-                x = b[v];
-                h.x = to_tf32(x.x); h.y = to_tf32(x.y); h.z = to_tf32(x.z); h.w = to_tf32(x.w);
-                l.x = to_tf32(x.x - h.x); l.y = to_tf32(x.y - h.y); l.z = to_tf32(x.z - h.z); l.w = to_tf32(x.w - h.w);
-                b[v] = h; blo[v] = l;
-            }
-        }
-        fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            const uint32_t a0 = smem_u32(stage_ptr(s, 0)), al = smem_u32(stage_ptr(s, 1));
-            const uint32_t b0 = smem_u32(stage_ptr(s, 2)), bl = smem_u32(stage_ptr(s, 3));
-#pragma unroll
-            for (int kk = 0; kk < TC_BK / 8; ++kk) {
-                const uint32_t off = kk * 32;  // 8 TF32 values = 32 bytes along K
-                const uint32_t acc0 = (t > 0 || kk > 0) ? 1u : 0u;
-                mma_tf32(tmem, smem_desc_sw128(a0 + off), smem_desc_sw128(b0 + off), IDESC, acc0);
-                mma_tf32(tmem, smem_desc_sw128(a0 + off), smem_desc_sw128(bl + off), IDESC, 1u);
-                mma_tf32(tmem, smem_desc_sw128(al + off), smem_desc_sw128(b0 + off), IDESC, 1u);
-            }
-            mma_commit(&done[s]);
-        }
-        committed = t + 1;
-    }
-    // wait for the last tile's MMAs (commits complete in issue order)
-    if (!fail && KT > 0) {
-        const int tl = KT - 1;
-        if (!mbar_wait(&done[tl % TC_STAGES], (tl / TC_STAGES) & 1)) s_fail = 1;
-    }
-    __syncthreads();
-    fail = s_fail != 0;
-    if (fail) {
-        if (tid == 0) {
-            atomicExch(err, 6);
-            // drain what is still in flight (bounded) before shared and tensor
-            // memory are released: TMA copies not yet observed, committed MMAs
-            for (int t = consumed; t < issued; ++t) mbar_wait(&full[t % TC_STAGES], (t / TC_STAGES) & 1);
-            if (committed > 0) mbar_wait(&done[(committed - 1) % TC_STAGES], ((committed - 1) / TC_STAGES) & 1);
-        }
-        __syncthreads();
-    } else {
-        tc_fence_after();
-        // epilogue: warp w owns rows 32w .. 32w+31 of the tile (TMEM lanes)
-        const int row = m0 + warp * 32 + lane;
-        for (int c0 = 0; c0 < TC_BN; c0 += 32) {
-            uint32_t r[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-            if (row < M) {
-                if (EPI == TC_EPI_SYM_ADD_F64) {
-                    // loads of the chunk first (the mirrored stores go to the
-                    // same array and would otherwise serialise every load)
-                    double old[32];
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int col = n0 + c0 + j;
-                        old[j] = (col < N && row <= col) ? ep.X[row + (int64_t)col * ep.ldx] : 0.0;
-                    }
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int col = n0 + c0 + j;
-                        if (col >= N || row > col) continue;
-                        const double x = old[j] + (double)__uint_as_float(r[j]) * ep.scale;
-                        ep.X[row + (int64_t)col * ep.ldx] = x;
-                        ep.X[col + (int64_t)row * ep.ldx] = x;
-                    }
-                } else if (EPI == TC_EPI_CSTORE || EPI == TC_EPI_CSTORE_T) {
-                    // accumulator columns (2q, 2q+1) = (Re, Im) of complex column q
-#pragma unroll
-                    for (int j = 0; j < 32; j += 2) {
-                        const int col = n0 + c0 + j;
-                        if (col >= N) continue;  // N even: col + 1 < N as well
-                        const int q = col >> 1;
-                        const int64_t at = EPI == TC_EPI_CSTORE ? (row + (int64_t)q * ep.ldc) : (q + (int64_t)row * ep.ldc);
-                        *reinterpret_cast<float2 *>(ep.C + 2 * at) =
-                            make_float2(__uint_as_float(r[j]), __uint_as_float(r[j + 1]));
-                    }
-                } else if (EPI == TC_EPI_RE_F64_STORE || EPI == TC_EPI_RE_F64_ADD) {
-                    double old[32];
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int col = n0 + c0 + j;
-                        old[j] = (EPI == TC_EPI_RE_F64_ADD && col < N) ? ep.X[row + (int64_t)col * ep.ldx] : 0.0;
-                    }
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int col = n0 + c0 + j;
-                        if (col >= N) continue;
-                        ep.X[row + (int64_t)col * ep.ldx] = old[j] + (double)__uint_as_float(r[j]) * ep.scale;
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int col = n0 + c0 + j;
-                        if (col >= N) continue;
-                        const float v = __uint_as_float(r[j]);
-                        if (EPI == TC_EPI_STORE) ep.C[row + (int64_t)col * ep.ldc] = v;
-                        else ep.C[row + (int64_t)col * ep.ldc] = v / (ep.s[row] + ep.s[col]);
-                    }
+    if (warp == 0) {
+        // TMA producer
+        if (lane == 0) {
+            int it = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+                int m0, n0;
+                tile_origin(tile, m0, n0);
+                for (int t = 0; t < KT; ++t, ++it) {
+                    const int s = it % TC_STAGES, u = it / TC_STAGES;
+                    if (u > 0 && !tc_wait(&empty[s], (u - 1) & 1, &s_fail)) { ok = false; break; }
+                    mbar_arrive_expect_tx(&full[s], 2 * TC_TILE_BYTES);
+                    tma_load_2d(stage_ptr(s, 0), &mapA, &full[s], t * TC_BK, m0);
+                    tma_load_2d(stage_ptr(s, 2), &mapB, &full[s], t * TC_BK, n0);
                 }
             }
+            s_issued = it;
+        }
+    } else if (warp == 1) {
+        // MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t IDESC = idesc_tf32_128x128();
+            int it = 0, lt = 0, committed = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++lt) {
+                const int a = lt & 1, v = lt >> 1;
+                if (v > 0 && !tc_wait(&acce[a], (v - 1) & 1, &s_fail)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(a * TC_BN);
+                for (int t = 0; t < KT; ++t, ++it) {
+                    const int s = it % TC_STAGES;
+                    if (!tc_wait(&split[s], (it / TC_STAGES) & 1, &s_fail)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(stage_ptr(s, 0)), al = smem_u32(stage_ptr(s, 1));
+                    const uint32_t b0 = smem_u32(stage_ptr(s, 2)), bl = smem_u32(stage_ptr(s, 3));
+#pragma unroll
+                    for (int kk = 0; kk < TC_BK / 8; ++kk) {
+                        const uint32_t off = kk * 32;  // 8 TF32 values = 32 bytes along K
+                        const uint32_t acc0 = (t > 0 || kk > 0) ? 1u : 0u;
+                        mma_tf32(d, smem_desc_sw128(a0 + off), smem_desc_sw128(b0 + off), IDESC, acc0);
+                        mma_tf32(d, smem_desc_sw128(a0 + off), smem_desc_sw128(bl + off), IDESC, 1u);
+                        mma_tf32(d, smem_desc_sw128(al + off), smem_desc_sw128(b0 + off), IDESC, 1u);
+                    }
+                    mma_commit(&empty[s]);
+                    committed = it + 1;
+                }
+                if (ok) mma_commit(&accf[a]);
+            }
+            s_committed = committed;
+        }
+    } else if (warp < 2 + TC_SPLIT_WARPS) {
+        // split each landed stage into hi = tf32(x) (in place) and
+        // lo = tf32(x - hi) (beside it)
+        const int st = tid - 64;
+        int it = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+            for (int t = 0; t < KT; ++t, ++it) {
+                const int s = it % TC_STAGES;
+                if (!tc_wait(&full[s], (it / TC_STAGES) & 1, &s_fail)) { ok = false; break; }
+                if (st == 0) s_consumed = it + 1;
+                float4 *a = (float4 *)stage_ptr(s, 0), *alo = (float4 *)stage_ptr(s, 1);
+                float4 *b = (float4 *)stage_ptr(s, 2), *blo = (float4 *)stage_ptr(s, 3);
+                constexpr int NV = TC_TILE_BYTES / 16;
+#pragma unroll 4
+                for (int v = st; v < NV; v += TC_SPLIT_WARPS * 32) {
+                    float4 x = a[v], h, l;
+                    h.x = to_tf32(x.x); h.y = to_tf32(x.y); h.z = to_tf32(x.z); h.w = to_tf32(x.w);
+                    l.x = to_tf32(x.x - h.x); l.y = to_tf32(x.y - h.y); l.z = to_tf32(x.z - h.z); l.w = to_tf32(x.w - h.w);
+                    a[v] = h; alo[v] = l;
+                    x = b[v];
+                    h.x = to_tf32(x.x); h.y = to_tf32(x.y); h.z = to_tf32(x.z); h.w = to_tf32(x.w);
+                    l.x = to_tf32(x.x - h.x); l.y = to_tf32(x.y - h.y); l.z = to_tf32(x.z - h.z); l.w = to_tf32(x.w - h.w);
+                    b[v] = h; blo[v] = l;
+                }
+                fence_proxy_async();  // the writes, before the tensor cores read them
+                mbar_arrive(&split[s]);
+            }
+        }
+    } else {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, i.e. tile rows
+        const int qw = warp & 3;
+        int lt = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
+            const int a = lt & 1, v = lt >> 1;
+            // every lane waits; the warp leaves together if any lane gave up
+            // (the TMEM loads below are warp-collective)
+            const bool okw = tc_wait(&accf[a], v & 1, &s_fail);
+            if (!__all_sync(0xffffffffu, okw)) break;
+            tc_fence_after();
+            int m0, n0;
+            tile_origin(tile, m0, n0);
+            const int row = m0 + 32 * qw + lane;
+            for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)(a * TC_BN + c0), r);
+                if (row < M) tc3_epilogue_chunk<EPI>(r, row, n0, c0, N, ep);
+            }
+            tc_fence_before();
+            mbar_arrive(&acce[a]);
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
+    if (s_fail) {
+        // drain what is still in flight (bounded) before shared and tensor
+        // memory are released: TMA copies not yet observed, committed MMAs
+        if (tid == 0) {
+            atomicExch(err, 6);
+            for (int t = s_consumed; t < s_issued; ++t) mbar_wait(&full[t % TC_STAGES], (t / TC_STAGES) & 1);
+            if (s_committed > 0) mbar_wait(&empty[(s_committed - 1) % TC_STAGES], ((s_committed - 1) / TC_STAGES) & 1);
+        }
+        __syncthreads();
+    }
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_BN) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -256,7 +338,7 @@ bool tc_gemm_supported(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb
 }
 
 template <int EPI>
-static cudaError_t launch_epi(dim3 g, const CUtensorMap &ma, const CUtensorMap &mb, int M, int N, int K,
+static cudaError_t launch_epi(int g, const CUtensorMap &ma, const CUtensorMap &mb, int M, int N, int K,
                               const TcEpilogue &ep, int *err, cudaStream_t s)
 {
     cudaError_t e;
@@ -272,7 +354,12 @@ cudaError_t launch_tc3_gemm(int M, int N, int K, const float *A, int lda, const 
     if (M <= 0 || N <= 0) return cudaSuccess;
     CUtensorMap ma, mb;
     if (!make_map(&ma, A, K, M, lda) || !make_map(&mb, B, K, N, ldb)) return cudaErrorInvalidValue;
-    dim3 g((unsigned)cdiv_i(M, TC_BM), (unsigned)cdiv_i(N, TC_BN));
+    // persistent: one CTA per SM (at most one per tile)
+    const int64_t TM = cdiv_i(M, TC_BM), TN = cdiv_i(N, TC_BN);
+    const int64_t ntiles = epi == TC_EPI_SYM_ADD_F64 ? TN * (TN + 1) / 2 : TM * TN;
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, sms));
     cudaError_t e;
     switch (epi) {
     case TC_EPI_CSTORE: return launch_epi<TC_EPI_CSTORE>(g, ma, mb, M, N, K, ep, err, s);
