@@ -193,6 +193,116 @@ __device__ void syl_block(const cplx<R> *__restrict__ S, int lds, int m, const c
     if (threadIdx.x == 0 && *bad) atomicExch(status, 2);
 }
 
+// The same block equation for the dependency-ordered solve: each update term
+// waits for its own producer's done flag (block (K, J) for S_IK Y_KJ, block
+// (I, K) for Y_IK St_KJ) right before its tiles are loaded, and the terms go
+// in the order their producers finish (by anti-diagonal), so a block has
+// accumulated all but its last one or two terms when its neighbours finish:
+// only those and the leaf lie on the critical path.  kSylMaxTerms bounds the
+// term list (Mb + Nb); on a wait that gives up the block is abandoned (*fail).
+static constexpr int kSylMaxTerms = 512;
+template <class R, int G>
+__device__ void syl_block_flow(const cplx<R> *__restrict__ S, int lds, int m, const cplx<R> *__restrict__ St,
+                               int ldst, int nn, cplx<R> *C, int ldc, int b, int I, int J, int *status, cplx<R> *tc,
+                               int *bad, volatile int *flags, volatile int *giveup, unsigned long long wait_ns,
+                               int *fail, int *terms)
+{
+    constexpr int TT = TB * TLD, kSylGroups = G;
+    const int Mb = (m + b - 1) / b;
+    const int g = threadIdx.x / kTriThreads, lt = threadIdx.x % kTriThreads;
+    cplx<R> *ta = tc + TT * (1 + 4 * g), *tb = ta + TT;
+    const int i0 = I * b, j0 = J * b;
+    const int bm = min(b, m - i0), bn = min(b, nn - j0);
+    // terms by the anti-diagonal of their producer: S-term K (producer (K, J))
+    // on level J - K + Mb - 1, Y-term K (producer (I, K)) on K - I + Mb - 1;
+    // encoded K (S) or -1 - K (Y)
+    const int w = J - I + Mb - 1;
+    if (threadIdx.x == 0) {
+        *bad = 0;
+        *fail = 0;
+        int c = 0;
+        for (int L = 0; L < w; ++L) {
+            const int ks = J - L + Mb - 1;  // S-term on this level
+            if (ks > I && ks < Mb) terms[c++] = ks;
+            const int ky = L - (Mb - 1) + I;  // Y-term on this level
+            if (ky >= 0 && ky < J) terms[c++] = -1 - ky;
+        }
+    }
+    load_tile(tc, C + i0 + (int64_t)j0 * ldc, ldc, bm, bn);
+    __syncthreads();
+    cplx<R> acc[8];
+    const int r = lt & 31, c0 = lt >> 5;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = g == 0 ? tc[r + (c0 + 4 * q) * TLD] : cplx<R>{0, 0};
+    const int nterm = (Mb - 1 - I) + J;
+    __shared__ int s_gok[8];
+    for (int t = g; t < nterm; t += kSylGroups) {
+        const int code = terms[t];
+        if (lt == 0) {
+            const int pf = code >= 0 ? code + J * Mb : I + (-1 - code) * Mb;
+            int ok = 1;
+            if (!flags[pf]) {
+                const uint64_t t0 = globaltimer_ns();
+                while (!flags[pf]) {
+                    if (*giveup || globaltimer_ns() - t0 > wait_ns) { ok = 0; break; }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+            s_gok[g] = ok;
+        }
+        group_bar(g);
+        if (!s_gok[g]) {
+            if (lt == 0) *fail = 1;
+            break;
+        }
+        int bk;
+        if (code >= 0) {
+            const int k0 = code * b;
+            bk = min(b, m - k0);
+            load_tile_async_g(ta, S + i0 + (int64_t)k0 * lds, lds, bm, bk, lt);
+            load_tile_async_g(tb, C + k0 + (int64_t)j0 * ldc, ldc, bk, bn, lt);
+        } else {
+            const int k0 = (-1 - code) * b;
+            bk = min(b, nn - k0);
+            load_tile_async_g(ta, C + i0 + (int64_t)k0 * ldc, ldc, bm, bk, lt);
+            load_tile_async_g(tb, St + k0 + (int64_t)j0 * ldst, ldst, bk, bn, lt);
+        }
+        cp_async_wait_all();
+        group_bar(g);
+        tile_mms(acc, ta, tb, bk, lt);
+        group_bar(g);  // the tiles are reloaded by the group's next term
+    }
+    __syncthreads();
+    if (*fail) return;
+    // partial sums of groups 1.. into their first tile, added to group 0's in order
+    if (g > 0) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) ta[r + (c0 + 4 * q) * TLD] = acc[q];
+    }
+    __syncthreads();
+    if (g == 0) {
+        for (int h = 1; h < kSylGroups; ++h) {
+            const cplx<R> *ph = tc + TT * (1 + 4 * h);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q] += ph[r + (c0 + 4 * q) * TLD];
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) tc[r + (c0 + 4 * q) * TLD] = acc[q];
+    }
+    __syncthreads();
+    cplx<R> *la = tc + TT, *lb = la + TT;  // group 0's tiles, free now
+    load_tile(la, S + i0 + (int64_t)i0 * lds, lds, bm, bm);
+    load_tile(lb, St + j0 + (int64_t)j0 * ldst, ldst, bn, bn);
+    __syncthreads();
+    leaf_sylvester(la, lb, tc, bm, bn, bad);
+    for (int e = threadIdx.x; e < bm * bn; e += blockDim.x) {
+        int i = e % bm, j = e / bm;
+        C[(i0 + i) + (int64_t)(j0 + j) * ldc] = tc[i + j * TLD];
+    }
+    if (threadIdx.x == 0 && *bad) atomicExch(status, 2);
+}
+
 // ---------------------------------------------------------------------------
 // Sylvester wavefront: blocks (I, J) with J - I = w - (Mb - 1), one per CTA.
 // ---------------------------------------------------------------------------
@@ -237,7 +347,8 @@ rtrsyl_flow_kernel(const cplx<R> *__restrict__ S, int lds, int m, const cplx<R> 
 {
     extern __shared__ unsigned char smraw[];
     cplx<R> *tc = reinterpret_cast<cplx<R> *>(smraw);
-    __shared__ int bad, s_t, s_ok;
+    __shared__ int bad, s_t, s_fail;
+    __shared__ int s_terms[kSylMaxTerms];
     const int Mb = (m + b - 1) / b, Nb = (nn + b - 1) / b, nblk = Mb * Nb;
     volatile int *flags = sync + 2;
     for (;;) {
@@ -254,25 +365,16 @@ rtrsyl_flow_kernel(const cplx<R> *__restrict__ S, int lds, int m, const cplx<R> 
             if (cnt > 0) t -= cnt;
         }
         const int J = I + w - (Mb - 1);
-        if (threadIdx.x == 0) {
-            const uint64_t t0 = globaltimer_ns();
-            int ok = 1;
-            while ((I + 1 < Mb && !flags[(I + 1) + J * Mb]) || (J > 0 && !flags[I + (J - 1) * Mb])) {
-                if (((volatile int *)sync)[1] || globaltimer_ns() - t0 > wait_ns) { ok = 0; break; }
-                __nanosleep(128);
-            }
-            __threadfence();
-            s_ok = ok;
-        }
+        syl_block_flow<R, G>(S, lds, m, St, ldst, nn, C, ldc, b, I, J, status, tc, &bad, flags, sync + 1, wait_ns,
+                             &s_fail, s_terms);
         __syncthreads();
-        if (!s_ok) {
+        if (s_fail) {
             if (threadIdx.x == 0) {
                 atomicExch(status, 6);
                 atomicExch(&sync[1], 1);
             }
             break;
         }
-        syl_block<R, G>(S, lds, m, St, ldst, nn, C, ldc, b, I, J, status, tc, &bad);
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) atomicExch(&sync[2 + I + J * Mb], 1);
@@ -776,7 +878,7 @@ cudaError_t launch_rtrsyl(const cplx<R> *S, int lds, int m, const cplx<R> *St, i
     size_t sm3 = (1 + 4 * SylCfg<R>::G) * TB * TLD * sizeof(cplx<R>);
     cudaError_t err;
     if (flow && b == TB && ldc % 16 == 0 && ((uintptr_t)C % 128) == 0 && (int64_t)Mb * Nb + 2 <= flow_cap &&
-        Mb + Nb > 2) {
+        Mb + Nb > 2 && Mb + Nb <= kSylMaxTerms) {
         // one launch, ordered by dependencies (rtrsyl_flow_kernel)
         if ((err = set_smem<R>((const void *)rtrsyl_flow_kernel<R>, sm3))) return err;
         int dev = 0, sms = 0, per = 0;
