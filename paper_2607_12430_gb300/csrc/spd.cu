@@ -733,7 +733,7 @@ __device__ __forceinline__ int sign_flip(double a, double b)
     return (int)((unsigned long long)(__double_as_longlong(a) ^ __double_as_longlong(b)) >> 63);
 }
 
-__device__ __forceinline__ void minor_rescale(double &p, double &pm)
+__device__ __forceinline__ int minor_rescale(double &p, double &pm)
 {
     const unsigned long long a = (unsigned long long)__double_as_longlong(p) & 0x7FFFFFFFFFFFFFFFull;
     const unsigned long long b = (unsigned long long)__double_as_longlong(pm) & 0x7FFFFFFFFFFFFFFFull;
@@ -741,11 +741,16 @@ __device__ __forceinline__ void minor_rescale(double &p, double &pm)
     const double sc = __longlong_as_double((long long)(1023 - E) << 52);  // 2^-E
     p *= sc;
     pm *= sc;
+    return E;
 }
 
-__device__ __forceinline__ int sturm_count(const double *__restrict__ d, const double *__restrict__ e2, int n, double x)
+// (with fm, fe: also det(T - x I) = fm 2^fe, the last minor and the sum of
+// the rescaling exponents)
+__device__ __forceinline__ int sturm_count(const double *__restrict__ d, const double *__restrict__ e2, int n, double x,
+                                           double *fm = nullptr, int *fe = nullptr)
 {
     constexpr int B = 8;
+    int ex = 0;
     double pm = 1.0, p = minor_fix(d[0] - x, 1.0);
     int c = sign_flip(p, 1.0);
     int i = 1;
@@ -772,7 +777,7 @@ __device__ __forceinline__ int sturm_count(const double *__restrict__ d, const d
             pm = p;
             p = pn;
         }
-        minor_rescale(p, pm);
+        ex += minor_rescale(p, pm);
 #pragma unroll
         for (int u = 0; u < B; ++u) {
             dm[u] = dn[u];
@@ -785,6 +790,7 @@ __device__ __forceinline__ int sturm_count(const double *__restrict__ d, const d
         pm = p;
         p = pn;
     }
+    if (fm) { *fm = p; *fe = ex; }
     return c;
 }
 
@@ -843,7 +849,10 @@ __global__ void __launch_bounds__(256) multisect_f32_kernel(const float *__restr
 // part where the count passes j (K = 1 is bisection).  Stops at a bracket of
 // width reltol |lam| + 2u ||T|| (plus the pivot floor).  A count costs
 // three FP64 instructions a step; the launcher picks the K that fills the
-// FP64 units of every SM sub-partition with the fewest rounds.
+// FP64 units of every SM sub-partition with the fewest rounds.  Once the
+// bracket holds eigenvalue j alone, the points of a round go around the
+// regula falsi estimate from the determinants at the bracket's ends (a
+// by-product of the counts) instead of cutting it into equal parts.
 static constexpr int kBisectThreads = 64;  // two warps per CTA: the warps spread over every SM
 
 template <int K>
@@ -864,43 +873,90 @@ __global__ void __launch_bounds__(kBisectThreads) bisect_f64_kernel(const double
         lo = fmax(gl, blo[j] - widen);
         hi = fmin(gu, bhi[j] + widen);
     }
-    // counts at both ends (two lanes at once where K >= 2)
-    int c0 = 0, c1 = 0;
+    // counts and determinants at both ends (two lanes at once where K >= 2)
+    int c0 = 0, c1 = 0, e0 = 0, e1 = 0;
+    double m0 = 1.0, m1 = 1.0;
     if (valid && (lo < hi)) {
         if (K == 1) {
-            c0 = sturm_count(d, e2, n, lo);
-            c1 = sturm_count(d, e2, n, hi);
+            c0 = sturm_count(d, e2, n, lo, &m0, &e0);
+            c1 = sturm_count(d, e2, n, hi, &m1, &e1);
         } else if (l < 2) {
-            c0 = sturm_count(d, e2, n, l == 0 ? lo : hi);
+            c0 = sturm_count(d, e2, n, l == 0 ? lo : hi, &m0, &e0);
         }
     }
     if (K > 1) {
-        const int a = __shfl_sync(0xffffffffu, c0, base);
+        const int a = __shfl_sync(0xffffffffu, c0, base), ae = __shfl_sync(0xffffffffu, e0, base);
+        const double am = __shfl_sync(0xffffffffu, m0, base);
         c1 = __shfl_sync(0xffffffffu, c0, base + 1);
-        c0 = a;
+        e1 = __shfl_sync(0xffffffffu, e0, base + 1);
+        m1 = __shfl_sync(0xffffffffu, m0, base + 1);
+        c0 = a; e0 = ae; m0 = am;
     }
+    // bracket [lo, hi] with count(lo) = clo <= j < chi = count(hi) and, where
+    // known (hlo, hhi), det(T - x I) at its ends as mantissa and exponent
+    int clo = c0, chi = c1, flx = e0, fhx = e1;
+    double flm = m0, fhm = m1;
+    bool hlo = true, hhi = true;
     if (!(lo < hi) || c0 > j || c1 <= j) {
         lo = gl;
         hi = gu;
+        clo = 0;
+        chi = n;
+        hlo = hhi = false;
     }
     const double atol = 2.0 * 1.1102230246251565e-16 * fmax(fabs(gl), fabs(gu)) + pivmin;
     const double step = 1.0 / (double)(K + 1);
+    double xs_prev = 0.0;
+    bool have_prev = false, plain_next = false;
     for (int it = 0; it < 160; ++it) {
         const double h = (hi - lo) * step;
-        const double x = lo + h * (double)(l + 1);
-        const double xfirst = lo + h, xlast = lo + h * (double)K;
-        const bool conv = !valid || !(xfirst > lo && xlast < hi) ||
+        const bool conv = !valid || !(lo + h > lo && lo + h * (double)K < hi) ||
                           hi - lo <= reltol * fmax(fabs(lo), fabs(hi)) + atol;
         if (__all_sync(0xffffffffu, conv)) break;
-        const int c = conv ? 0 : sturm_count(d, e2, n, x);
+        // points: K equal parts of the bracket, or -- once the bracket holds
+        // eigenvalue j alone and its ends' determinants are known -- points at
+        // +-delta/2, +-2 delta, +-8 delta, ... around the regula falsi estimate
+        // x* (the root of the line through the two determinants), delta the
+        // change of x* since the last round (a secant-type step converges
+        // superlinearly); a round that fails to halve the bracket is followed
+        // by a plain one.  The counts decide the new bracket either way.
+        const bool sec = K >= 2 && hlo && hhi && clo == j && chi == j + 1 && !plain_next;
+        double x = lo + h * (double)(l + 1);
+        double xs = 0.0;
+        if (sec) {
+            const int dx = max(-1000, min(1000, fhx - flx));
+            const double q = (fhm / flm) * __longlong_as_double((long long)(dx + 1023) << 52);  // f(hi) / f(lo)
+            double t = 1.0 / (1.0 - q);
+            if (!(t > 0.0 && t < 1.0)) t = 0.5;
+            xs = lo + (hi - lo) * t;
+            double delta = (hi - lo) * 0.0625;
+            if (have_prev) delta = fmin(delta, fmax(fabs(xs - xs_prev), 0.25 * (reltol * fabs(xs) + atol)));
+            const int half = K / 2, k = l < half ? half - 1 - l : l - half;
+            const double off = delta * 0.5 * (double)(1u << (2 * k));  // delta 2^(2k-1)
+            x = fmin(hi, fmax(lo, l < half ? xs - off : xs + off));
+        }
+        double fm = 1.0;
+        int fe = 0;
+        const int c = conv ? 0 : sturm_count(d, e2, n, x, &fm, &fe);
         unsigned above = __ballot_sync(0xffffffffu, c > j);
+        above = (K == 32) ? above : (above >> base) & ((1u << K) - 1u);
+        const int first = above ? __ffs(above) - 1 : K;  // part (x_{first-1}, x_first]
+        const int sl = base + max(first - 1, 0), sh = base + min(first, K - 1);
+        const double xl = __shfl_sync(0xffffffffu, x, sl), xh = __shfl_sync(0xffffffffu, x, sh);
+        const int cl = __shfl_sync(0xffffffffu, c, sl), ch = __shfl_sync(0xffffffffu, c, sh);
+        const double ml = __shfl_sync(0xffffffffu, fm, sl), mh = __shfl_sync(0xffffffffu, fm, sh);
+        const int el = __shfl_sync(0xffffffffu, fe, sl), eh = __shfl_sync(0xffffffffu, fe, sh);
         if (!conv) {
-            above = (K == 32) ? above : (above >> base) & ((1u << K) - 1u);
-            const int first = above ? __ffs(above) - 1 : K;  // part (x_{first-1}, x_first]
-            const double nlo = first > 0 ? lo + h * (double)first : lo;
-            const double nhi = first < K ? lo + h * (double)(first + 1) : hi;
-            lo = nlo;
-            hi = nhi;
+            const double w0 = hi - lo;
+            if (first > 0) { lo = xl; clo = cl; flm = ml; flx = el; hlo = true; }
+            if (first < K) { hi = xh; chi = ch; fhm = mh; fhx = eh; hhi = true; }
+            if (sec) {
+                plain_next = hi - lo > 0.5 * w0;
+                xs_prev = xs;
+                have_prev = true;
+            } else {
+                plain_next = false;
+            }
         }
     }
     if (valid && l == 0) lam[j] = 0.5 * (lo + hi);

@@ -81,9 +81,11 @@ void split_plan(int n, int *b, int *D)
 // that the FP64 loop costs on a part with few FP64 units:
 //   m_s = round-half-even(X / 2^(124 - b (s + 1))),  X -= m_s 2^(124 - b (s + 1)).
 // An entry with |x| <= 2^-(b S + 1) has no nonzero digit.
+// (b, S compile-time: every shift below is a constant and the digit loop
+// unrolls; a run-time shift of a 128-bit value costs tens of instructions)
+template <int b, int S>
 __global__ void __launch_bounds__(256) split_rows_kernel(const double *__restrict__ X, int64_t ldx, int n, int lds,
-                                                         int b, int S, __nv_bfloat16 *__restrict__ Xs,
-                                                         int *__restrict__ rho)
+                                                         __nv_bfloat16 *__restrict__ Xs, int *__restrict__ rho)
 {
     const int lane = threadIdx.x & 31;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -112,6 +114,7 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const double *__restric
                           (sh + (63 - __clzll(mant)) == 123 - b * S && (mant & (mant - 1)) == 0);
         __int128 rem = zero ? (__int128)0 : ((__int128)mant << sh);
         if (vb < 0) rem = -rem;
+#pragma unroll
         for (int s = 0; s < S; ++s) {
             const int shift = 124 - b * (s + 1);
             __int128 q = rem >> shift;  // floor
@@ -400,8 +403,17 @@ cudaError_t launch_residual_sym_split(const double *A, int64_t lda, const double
     split_plan(n, &b, &D);
     const int S = D + 1, lds = split_lds(n);
     __nv_bfloat16 *Xs = (__nv_bfloat16 *)digits;
-    split_rows_kernel<<<(unsigned)cdiv_i((int64_t)n * 32, 256), 256, 0, s>>>(X, ldx, n, lds, b, S, Xs, rho);
-    count_launch();
+    {
+        const unsigned g = (unsigned)cdiv_i((int64_t)n * 32, 256);
+        // the (b, S) pairs split_plan can give: S = ceil(60 / b) digits of b bits
+        if (b == 8 && S == 8) split_rows_kernel<8, 8><<<g, 256, 0, s>>>(X, ldx, n, lds, Xs, rho);
+        else if (b == 7 && S == 9) split_rows_kernel<7, 9><<<g, 256, 0, s>>>(X, ldx, n, lds, Xs, rho);
+        else if (b == 6 && S == 10) split_rows_kernel<6, 10><<<g, 256, 0, s>>>(X, ldx, n, lds, Xs, rho);
+        else if (b == 5 && S == 12) split_rows_kernel<5, 12><<<g, 256, 0, s>>>(X, ldx, n, lds, Xs, rho);
+        else if (b == 4 && S == 15) split_rows_kernel<4, 15><<<g, 256, 0, s>>>(X, ldx, n, lds, Xs, rho);
+        else return cudaErrorInvalidValue;
+        count_launch();
+    }
     CUtensorMap mapX;
     if (S > SP_MAXG) return cudaErrorInvalidValue;
     if (!make_bf16_map(&mapX, Xs, lds, (int64_t)S * n, lds)) return cudaErrorInvalidValue;
