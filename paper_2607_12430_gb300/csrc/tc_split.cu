@@ -53,11 +53,16 @@
 
 namespace sqm {
 
-static constexpr int SP_BM = 128, SP_BN = 128, SP_BK = 64, SP_STAGES = 6;
+// output tiles of (128 MH) x 128: with MH = 2 two M = 128 MMAs share the B
+// tile (a quarter less operand traffic per flop), used where there are at
+// least as many such tiles as SMs; TMA boxes of 128 rows; 192 KB of stages
+static constexpr int SP_BR = 128, SP_BN = 128, SP_BK = 64;
+template <int MH> struct SpCfg {
+    static constexpr int BM = SP_BR * MH, STAGES = MH == 1 ? 6 : 4;
+};
 static constexpr int SP_THREADS = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
-static constexpr int SP_TILE_BYTES = SP_BM * SP_BK * 2;  // 16 KB
-static constexpr int SP_STAGE_BYTES = 2 * SP_TILE_BYTES;
-static constexpr int SP_SMEM = SP_STAGES * SP_STAGE_BYTES + 1024 + 256;
+static constexpr int SP_TILE_BYTES = SP_BR * SP_BK * 2;  // 16 KB: one box
+static constexpr int SP_SMEM = 6 * 2 * SP_TILE_BYTES + 1024 + 256;  // = 4 stages of 3 boxes
 
 // digit width b and pair bound D for an inner dimension n (see above)
 void split_plan(int n, int *b, int *D)
@@ -174,10 +179,14 @@ __device__ __forceinline__ double sp_pow2(int e)
     return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
 }
 
+template <int SP_MH>
 __global__ void __launch_bounds__(SP_THREADS, 1)
 split_gemm_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ SplitPlan plan, int n, int KT,
                   int T, int ntiles, SplitEpi ep, int *err)
 {
+    constexpr int SP_BM = SpCfg<SP_MH>::BM, SP_STAGES = SpCfg<SP_MH>::STAGES;
+    constexpr int SP_STAGE_BYTES = (SP_MH + 1) * SP_TILE_BYTES;  // the A boxes, then B
+    constexpr int SP_TMEM_COLS = 2 * SP_MH * SP_BN;              // two accumulators of SP_MH halves
     extern __shared__ unsigned char smraw[];
     __shared__ volatile int s_fail;
     __shared__ int s_issued, s_consumed, s_committed;
@@ -203,7 +212,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constan
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(2 * SP_BN)
+                     "r"(SP_TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -213,12 +222,13 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constan
     const uint32_t tmem = *tmem_slot;
 
     auto stage_ptr = [&](int s, int which) { return base + s * SP_STAGE_BYTES + which * SP_TILE_BYTES; };
-    // upper block triangle: tile q -> (I, J), I <= J, row-major over I
+    // tiles meeting the upper triangle: row block I (128 MH rows), column
+    // blocks J >= MH I (128 columns; T of them), row-major over I
     auto tile_origin = [&](int q, int &m0, int &n0) {
         int I = 0;
-        while (q >= T - I) { q -= T - I; ++I; }
+        while (q >= T - SP_MH * I) { q -= T - SP_MH * I; ++I; }
         m0 = I * SP_BM;
-        n0 = (I + q) * SP_BN;
+        n0 = (SP_MH * I + q) * SP_BN;
     };
     const int ng = plan.ng;
     if (warp == 0) {
@@ -238,9 +248,11 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constan
                         const int s = it % SP_STAGES, u = it / SP_STAGES;
                         if (u > 0 && !sp_wait(&empty[s], (u - 1) & 1, &s_fail)) { ok = false; break; }
                         const int pr = p0 + t / KT, kb = t % KT;
-                        mbar_arrive_expect_tx(&full[s], 2 * SP_TILE_BYTES);
-                        tma_load_2d(stage_ptr(s, 0), &mapX, &full[s], kb * SP_BK, plan.ps[pr] * n + m0);
-                        tma_load_2d(stage_ptr(s, 1), &mapX, &full[s], kb * SP_BK, plan.pt[pr] * n + n0);
+                        mbar_arrive_expect_tx(&full[s], (SP_MH + 1) * SP_TILE_BYTES);
+#pragma unroll
+                        for (int h = 0; h < SP_MH; ++h)
+                            tma_load_2d(stage_ptr(s, h), &mapX, &full[s], kb * SP_BK, plan.ps[pr] * n + m0 + h * SP_BR);
+                        tma_load_2d(stage_ptr(s, SP_MH), &mapX, &full[s], kb * SP_BK, plan.pt[pr] * n + n0);
                         ++it;
                     }
                 }
@@ -257,19 +269,23 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constan
                     const int a = lt & 1, v = lt >> 1;
                     if (v > 0 && !sp_wait(&acce[a], (v - 1) & 1, &s_fail)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t d = tmem + (uint32_t)(a * SP_BN);
+                    const uint32_t d = tmem + (uint32_t)(a * SP_MH * SP_BN);
                     const int steps = KT * (plan.gstart[q + 1] - plan.gstart[q]);
                     for (int t = 0; t < steps; ++t, ++it) {
                         const int s = it % SP_STAGES;
                         if (!sp_wait(&full[s], (it / SP_STAGES) & 1, &s_fail)) { ok = false; break; }
                         consumed = it + 1;
                         tc_fence_after();
-                        const uint32_t a0 = smem_u32(stage_ptr(s, 0)), b0 = smem_u32(stage_ptr(s, 1));
+                        const uint32_t b0 = smem_u32(stage_ptr(s, SP_MH));
 #pragma unroll
-                        for (int kk = 0; kk < SP_BK / 16; ++kk) {
-                            const uint32_t off = kk * 32;  // 16 BF16 values = 32 bytes along K
-                            mma_bf16(d, smem_desc_sw128(a0 + off), smem_desc_sw128(b0 + off), IDESC,
-                                     (t > 0 || kk > 0) ? 1u : 0u);
+                        for (int h = 0; h < SP_MH; ++h) {
+                            const uint32_t a0 = smem_u32(stage_ptr(s, h));
+#pragma unroll
+                            for (int kk = 0; kk < SP_BK / 16; ++kk) {
+                                const uint32_t off = kk * 32;  // 16 BF16 values = 32 bytes along K
+                                mma_bf16(d + (uint32_t)(h * SP_BN), smem_desc_sw128(a0 + off), smem_desc_sw128(b0 + off),
+                                         IDESC, (t > 0 || kk > 0) ? 1u : 0u);
+                            }
                         }
                         mma_commit(&empty[s]);  // the stage is free once these products are done
                         committed = it + 1;
@@ -288,8 +304,12 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constan
         for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
             int m0, n0;
             tile_origin(tile, m0, n0);
-            const int row = m0 + 32 * qw + lane;
-            const int rho_i = row < n ? ep.rho[row] : 0;
+            int rho_h[SP_MH];
+#pragma unroll
+            for (int h = 0; h < SP_MH; ++h) {
+                const int row = m0 + h * SP_BR + 32 * qw + lane;
+                rho_h[h] = row < n ? ep.rho[row] : 0;
+            }
             for (int q = 0; q < ng; ++q, ++lt) {
                 const int a = lt & 1, v = lt >> 1;
                 const bool first = q == 0, last = q == ng - 1;
@@ -300,39 +320,45 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constan
                 tc_fence_after();
                 const int shift = plan.shift[q];
                 double ss = 0.0;
-                for (int c0 = 0; c0 < SP_BN; c0 += 32) {
-                    uint32_t r[32];
-                    tmem_ld32(tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)(a * SP_BN + c0), r);
-                    if (row < n) {
-                        // all loads of the chunk first: the stores below go to
-                        // the same arrays, so loads issued after them would
-                        // each wait out a full memory round trip
-                        double old[32];
-                        int rj[32];
+                for (int h = 0; h < SP_MH; ++h) {
+                    const int row = m0 + h * SP_BR + 32 * qw + lane;
+                    const int rho_i = rho_h[h];
+                    for (int c0 = 0; c0 < SP_BN; c0 += 32) {
+                        uint32_t r[32];
+                        tmem_ld32(tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)((a * SP_MH + h) * SP_BN + c0), r);
+                        if (row < n) {
+                            // all loads of the chunk first: the stores below go
+                            // to the same arrays, so loads issued after them
+                            // would each wait out a full memory round trip
+                            double old[32];
+                            int rj[32];
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const int col = n0 + c0 + j;
-                            const bool in = col < n && row <= col;
-                            old[j] = in ? (first ? ep.A[row + (int64_t)col * ep.lda] : ep.Racc[row + (int64_t)col * ep.ldr])
-                                        : 0.0;
-                            rj[j] = col < n ? ep.rho[col] : 0;
-                        }
+                            for (int j = 0; j < 32; ++j) {
+                                const int col = n0 + c0 + j;
+                                const bool in = col < n && row <= col;
+                                old[j] = in ? (first ? ep.A[row + (int64_t)col * ep.lda]
+                                                     : ep.Racc[row + (int64_t)col * ep.ldr])
+                                            : 0.0;
+                                rj[j] = col < n ? ep.rho[col] : 0;
+                            }
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const int col = n0 + c0 + j;
-                            if (col >= n || row > col) continue;
-                            // old - P 2^(rho_i + rho_j - shift): the product is
-                            // exact, so one rounding as in old - ldexp(P, ...)
-                            const double v2 = fma(-(double)__uint_as_float(r[j]), sp_pow2(rho_i + rj[j] - shift), old[j]);
-                            if (last) {
-                                const double rs = v2 * ep.sc;
-                                const float rf = (float)rs;
-                                ep.Rhat[row + (int64_t)col * ep.ldh] = rf;
-                                ep.Rhat[col + (int64_t)row * ep.ldh] = rf;
-                                ss = fma(rs, rs, ss);
-                                if (row != col) ss = fma(rs, rs, ss);  // mirrored entry
-                            } else {
-                                ep.Racc[row + (int64_t)col * ep.ldr] = v2;
+                            for (int j = 0; j < 32; ++j) {
+                                const int col = n0 + c0 + j;
+                                if (col >= n || row > col) continue;
+                                // old - P 2^(rho_i + rho_j - shift): the product
+                                // is exact, so one rounding as in old - ldexp(P, ...)
+                                const double v2 =
+                                    fma(-(double)__uint_as_float(r[j]), sp_pow2(rho_i + rj[j] - shift), old[j]);
+                                if (last) {
+                                    const double rs = v2 * ep.sc;
+                                    const float rf = (float)rs;
+                                    ep.Rhat[row + (int64_t)col * ep.ldh] = rf;
+                                    ep.Rhat[col + (int64_t)row * ep.ldh] = rf;
+                                    ss = fma(rs, rs, ss);
+                                    if (row != col) ss = fma(rs, rs, ss);  // mirrored entry
+                                } else {
+                                    ep.Racc[row + (int64_t)col * ep.ldr] = v2;
+                                }
                             }
                         }
                     }
@@ -361,7 +387,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constan
     }
     tc_fence_after();
     if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * SP_BN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(SP_TMEM_COLS) : "memory");
 }
 
 static bool make_bf16_map(CUtensorMap *m, const void *ptr, int64_t kdim, int64_t rows, int64_t ld)
@@ -370,7 +396,7 @@ static bool make_bf16_map(CUtensorMap *m, const void *ptr, int64_t kdim, int64_t
     if (!fn) return false;
     cuuint64_t dims[2] = {(cuuint64_t)kdim, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-    cuuint32_t box[2] = {SP_BK, SP_BM};
+    cuuint32_t box[2] = {SP_BK, SP_BR};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -417,9 +443,18 @@ cudaError_t launch_residual_sym_split(const double *A, int64_t lda, const double
     CUtensorMap mapX;
     if (S > SP_MAXG) return cudaErrorInvalidValue;
     if (!make_bf16_map(&mapX, Xs, lds, (int64_t)S * n, lds)) return cudaErrorInvalidValue;
-    const int T = (int)cdiv_i(n, SP_BM), ntiles = T * (T + 1) / 2, KT = lds / SP_BK;
+    // T column blocks of 128; row block I (128 MH rows) meets the upper
+    // triangle in column blocks MH I .. T-1
+    const int T = (int)cdiv_i(n, SP_BN), KT = lds / SP_BK;
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int ntiles2 = 0;
+    for (int I = 0; 2 * I < T; ++I) ntiles2 += T - 2 * I;
+    const int mh = ntiles2 >= sms ? 2 : 1;
+    const int ntiles = mh == 2 ? ntiles2 : T * (T + 1) / 2;
     cudaError_t er;
-    if ((er = allow_max_smem((const void *)split_gemm_kernel))) return er;
+    if ((er = allow_max_smem((const void *)split_gemm_kernel<1>)) || (er = allow_max_smem((const void *)split_gemm_kernel<2>)))
+        return er;
     // groups of pairs with the same s + t whose integer bounds sum to <= 2^24
     SplitPlan plan{};
     int np = 0;
@@ -443,11 +478,10 @@ cudaError_t launch_residual_sym_split(const double *A, int64_t lda, const double
         }
     }
     plan.gstart[plan.ng] = (short)np;
-    int dev = 0, sms = 152;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::max(1, std::min(ntiles, sms));
     SplitEpi ep{A, lda, Racc, (int64_t)n, rho, Rhat, (int64_t)ldr, ldexp(1.0, -2 * e), partials};
-    split_gemm_kernel<<<grid, SP_THREADS, SP_SMEM, s>>>(mapX, plan, n, KT, T, ntiles, ep, err);
+    if (mh == 2) split_gemm_kernel<2><<<grid, SP_THREADS, SP_SMEM, s>>>(mapX, plan, n, KT, T, ntiles, ep, err);
+    else split_gemm_kernel<1><<<grid, SP_THREADS, SP_SMEM, s>>>(mapX, plan, n, KT, T, ntiles, ep, err);
     count_launch();
     *nparts = 4 * ntiles;  // a partial sum per epilogue warp and tile
     return cudaGetLastError();
