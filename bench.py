@@ -238,8 +238,8 @@ def leg_c3(args, mp, torch, flush, peaks):
     """SPD n = 4096, kappa = 1e6 (lambda log-uniform in [1e-3, 1e3], ends
     pinned): k* against the closed form polished by one FP64 step, the time
     of sqrtm_mixed with k* corrections, the FP64 method on the same GPU, and
-    the roofline of the decomposition's dominant kernels (the per-column
-    Householder tridiagonalisation, bound by memory traffic)."""
+    the roofline of the decomposition's dominant kernel (the per-column
+    Householder tridiagonalisation, bound by L2 traffic)."""
     import oracle
     t_gen = time.perf_counter()
     A_np, V, lam = synth.config_spd4096()
@@ -283,7 +283,8 @@ def leg_c3(args, mp, torch, flush, peaks):
                          "frac": achieved / hbm, "traffic": None,
                          "note": "algorithmic 4n^3/3 B per decomposition over the library's CUDA-event time of "
                                  "the reduction phase; peak: measured HBM copy bandwidth (the trailing block "
-                                 "is L2-resident, so the kernel is bound by L2 and launch latency)"},
+                                 "is L2-resident: each step's column phase is bound by L2 bandwidth, the rest "
+                                 "is the per-step prologue and launch gap, profiles/tri_step_spd4096.md)"},
             "input_prep_s": gen_s}
 
 
