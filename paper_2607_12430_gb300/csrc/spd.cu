@@ -1435,7 +1435,9 @@ cudaError_t launch_tridiag_eig(const R *A, int n, int ld, double *lam, double *Z
         const int rows = tw_scale_rows(n);
         int *SP = (int *)(Dm + (size_t)n * chunk + 4 * (size_t)n + 8);
         int *SQ = SP + (size_t)rows * chunk;
-        double *Fm = (double *)(SQ + (size_t)rows * chunk + ((size_t)rows * chunk & 1)), *Gm = Fm + n;
+        // SP is 8-byte aligned and SP + 2 rows chunk ints is too: the doubles
+        // follow directly
+        double *Fm = (double *)(SQ + (size_t)rows * chunk), *Gm = Fm + n;
         int *Fx = (int *)(Gm + n), *Gx = Fx + n, *blkv = Gx + n;
         tw_prefix_kernel<<<1, kPfxThreads, 0, s>>>(e, n, Fm, Fx, Gm, Gx, blkv); count_launch();
         for (int j0 = 0; j0 < n; j0 += chunk) {

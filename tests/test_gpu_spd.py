@@ -23,10 +23,11 @@ def _lib():
 
 
 @pytest.mark.parametrize("fp64", [False, True])
-@pytest.mark.parametrize("n", [1, 2, 17, 64, 200, 513, 1100, 2100])
+@pytest.mark.parametrize("n", [1, 2, 17, 25, 41, 64, 200, 513, 1100, 2100])
 def test_syevd(n, fp64):
-    # the sizes span every lane count of the FP64 multisection (32 lanes per
-    # eigenvalue up to n ~ 600, then 16, 8 and 4 at the larger sizes)
+    # the sizes span the lane counts of the FP64 multisection and ragged
+    # warps; n = 25 and 41 make the eigenvector kernel's exponent table an
+    # odd number of ints (the doubles after it must stay 8-byte aligned)
     A, V0, lam0 = synth.spd_case(n, -2.0, 2.0, seed=200 + n)
     e = oracle.scale_exponent(A)
     As = A * 4.0 ** -e
