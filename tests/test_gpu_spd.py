@@ -43,6 +43,21 @@ def test_syevd(n, fp64):
     assert np.abs(np.sort(lam) - np.sort(lam0 * 4.0 ** -e)).max() <= 100 * n * u * nrm2
 
 
+def test_syevd_every_small_size():
+    # every n from 3 to 72: odd and even sizes, ragged warps and every parity
+    # of the scratch tables the eigensolver carves per size
+    for n in range(3, 73):
+        A, _, lam0 = synth.spd_case(n, -2.0, 2.0, seed=900 + n)
+        e = oracle.scale_exponent(A)
+        As = A * 4.0 ** -e
+        V, lam = mp.step_syevd(dev_cm(As.astype(np.float32), torch.float32), n, fp64=False)
+        V = host_cm(V, n).astype(np.float64)
+        lam = lam.cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(V.T @ V - np.eye(n)) <= 100 * n * U32, n
+        assert np.linalg.norm((V * lam[None, :]) @ V.T - As) <= 100 * n * U32 * np.linalg.norm(As), n
+        assert np.abs(np.sort(lam) - np.sort(lam0 * 4.0 ** -e)).max() <= 100 * n * U32 * np.linalg.norm(As, 2), n
+
+
 @pytest.mark.parametrize("n", [1, 33, 128, 300])
 def test_transform_in_spd(n):
     V = synth.haar_orthogonal(n, synth.rng(300 + n)).astype(np.float32)
