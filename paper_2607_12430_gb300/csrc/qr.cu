@@ -7,8 +7,10 @@
 //
 //  * Each sweep applies nb single shifts at once: nb = min(NB, (m - 2) / 4)
 //    for an active block [lo, hi] of size m, the shifts being the eigenvalues
-//    of its trailing nb x nb block (one warp computes them by single-shift QR
-//    in shared memory); nb = 1 uses the Wilkinson shift.  Bulge g starts 3
+//    of its trailing nb x nb block (the whole CTA refines them by the
+//    Ehrlich-Aberth iteration, started from the previous sweep's shifts; one
+//    warp's single-shift QR in shared memory if that does not converge);
+//    nb = 1 uses the Wilkinson shift.  Bulge g starts 3
 //    positions behind bulge g-1 and all bulges advance one position per step,
 //    so the rotations of one step act on disjoint row pairs (left) and
 //    disjoint column pairs (right); warp g moves bulge g.  The result equals
@@ -45,6 +47,7 @@ static constexpr int kItMax = 60;
 static constexpr int kQrCoopMinN = 256;  // smallest n for the cooperative chase
 static constexpr int kQrPostMin = 64;    // fewer out-of-window rows + columns: the chase CTA does them
 static constexpr int kQrTiny = 24;       // active blocks up to this size: one warp, dense U
+static constexpr int kAberthIt = 24;     // iteration limit of the simultaneous shift refinement
 static constexpr int kQrTinyLd = 33;     // leading dimension of its shared-memory block and U
 static constexpr int kQrThreads = 512;           // chase CTA
 static constexpr int kQrTpc = 4;                 // threads per row/column segment in the updates
@@ -312,6 +315,161 @@ __device__ void warp_small_eigvals(cplx<R> *M, int nb, cplx<R> *out)
         warp_sweep<R, LDM, false, true>(M, nullptr, nb, lo, hi, mu, nullptr);
     }
     if (hi == 0 && lane == 0) out[0] = M[0];
+    __syncwarp();
+}
+
+// Shifts by simultaneous refinement of all nb eigenvalue estimates of the
+// small unreduced Hessenberg block M (nb x nb, nb <= 32, leading dimension
+// LDM): the Ehrlich-Aberth iteration (O. Aberth, Math. Comp. 27 (1973)),
+//   z_j <- z_j - N_j / (1 - N_j sum_{k != j} 1 / (z_j - z_k)),
+// with every estimate updated at once, where N_j = p(z_j) / p'(z_j) and
+// p(z) = det(M - z I).  The Newton ratio comes from Hyman's recurrence
+// (Wilkinson, The Algebraic Eigenvalue Problem, 1965, Ch. 7): with
+// x_{nb-1} = 1, row i of (M - z I) x = 0 fixes x_{i-1} through the
+// subdiagonal entry M(i, i-1), for i = nb-1 down to 1; the residual of row 0
+// is then p(z) times a product of subdiagonal entries that does not depend
+// on z, so differentiating the recurrence gives the same multiple of p'(z)
+// and the ratio of the two is N.  A segment of lanes per estimate (16 while
+// nb <= 16, so a warp takes two): lane r keeps the running sums of row r for
+// the residual and its derivative, and each new x_i (formed by lane i) is
+// broadcast and added into the rows above it.  x, its derivative and the
+// sums are rescaled together by powers of two to stay in range, which
+// leaves the ratio unchanged.  No CTA-wide state other than z changes; M is
+// not modified.  On entry z (shared memory) holds nb distinct starting
+// estimates; true means every correction of the last
+// iteration was at most tol (|z_j| + 1e-3 max|M_ij|) and z holds the
+// shifts; false (no convergence within kmax iterations, or a non-finite
+// value) leaves z unusable.  Every thread of the CTA calls it.
+template <class R> __device__ __forceinline__ R aberth_tol();
+template <> __device__ __forceinline__ float aberth_tol<float>() { return 1e-6f; }
+template <> __device__ __forceinline__ double aberth_tol<double>() { return 1e-11; }
+
+template <class R, int LDM>
+__device__ bool cta_aberth_shifts(const cplx<R> *M, int nb, cplx<R> *z, R mnrm, int kmax)
+{
+    __shared__ cplx<R> s_inv[32], s_w[32];
+    __shared__ int s_bad;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (int)(blockDim.x >> 5);
+    // seg lanes per estimate (a half-warp while nb <= 16, so a warp takes two)
+    const int seg = nb <= 16 ? 16 : 32, per = 32 / seg, r = lane % seg, half = lane / seg;
+    const R tol = aberth_tol<R>();
+    const R floor_sub = mnrm * R(1e-20);
+    if (tid < nb) {  // 1 / M(i, i-1) for i = tid >= 1; a vanishing entry is raised to floor_sub
+        cplx<R> sb = tid ? M[tid + (tid - 1) * LDM] : cplx<R>{R(1), R(0)};
+        if (!(fmax(fabs(sb.x), fabs(sb.y)) > floor_sub)) sb = cplx<R>{floor_sub, R(0)};
+        s_inv[tid] = cdiv(cplx<R>{R(1), R(0)}, sb);
+    }
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    for (int it = 0; it < kmax; ++it) {
+        // every lane of a warp runs the same trip counts (the shuffles span the
+        // warp); a segment past nb computes on a copy of estimate nb - 1 and
+        // stores nothing
+        for (int j0 = warp * per; j0 < nb; j0 += nw * per) {
+            const int j = j0 + half;
+            const cplx<R> mu = z[min(j, nb - 1)];
+            cplx<R> s{0, 0}, ds{0, 0}, x{R(1), R(0)}, dx{0, 0};
+#pragma unroll 2
+            for (int i = nb - 1;; --i) {
+                if (r <= i) {  // column i of (M - mu I) into rows 0 .. i
+                    cplx<R> a = M[r + i * LDM];
+                    if (r == i) a = a - mu;
+                    cfma(ds, a, dx);
+                    if (r == i) ds = ds - x;
+                    cfma(s, a, x);
+                }
+                if (i == 0) break;
+                const cplx<R> iv = s_inv[i];
+                const cplx<R> xn = -(s * iv), dxn = -(ds * iv);  // meaningful on lane i of the segment
+                x = cplx<R>{__shfl_sync(0xffffffffu, xn.x, i, seg), __shfl_sync(0xffffffffu, xn.y, i, seg)};
+                dx = cplx<R>{__shfl_sync(0xffffffffu, dxn.x, i, seg), __shfl_sync(0xffffffffu, dxn.y, i, seg)};
+                const R mag = fmax(fmax(fabs(x.x), fabs(x.y)), fmax(fabs(dx.x), fabs(dx.y)));
+                const R f = mag > R(1099511627776.0) ? R(1.0 / 1099511627776.0)  // 2^40
+                            : (mag > R(0) && mag < R(1.0 / 1099511627776.0)) ? R(1099511627776.0) : R(1);
+                x = f * x; dx = f * dx; s = f * s; ds = f * ds;
+            }
+            const cplx<R> q = cdiv(s, ds);  // row 0 (lane 0 of the segment): p / p'
+            const cplx<R> N{__shfl_sync(0xffffffffu, q.x, 0, seg), __shfl_sync(0xffffffffu, q.y, 0, seg)};
+            cplx<R> part{0, 0};
+            if (r < nb && r != j) part = cdiv(cplx<R>{R(1), R(0)}, mu - z[r]);
+            for (int o = seg >> 1; o > 0; o >>= 1) {
+                part.x += __shfl_xor_sync(0xffffffffu, part.x, o);
+                part.y += __shfl_xor_sync(0xffffffffu, part.y, o);
+            }
+            const cplx<R> w = cdiv(N, cplx<R>{R(1), R(0)} - N * part);
+            if (r == 0 && j < nb) s_w[j] = w;
+        }
+        __syncthreads();
+        bool done = true;
+        if (tid < nb) {
+            const cplx<R> w = s_w[tid];
+            const cplx<R> zn = z[tid] - w;
+            if (!(isfinite(zn.x) && isfinite(zn.y))) s_bad = 1;
+            done = hypot(w.x, w.y) <= tol * (hypot(zn.x, zn.y) + R(1e-3) * mnrm);
+            z[tid] = zn;
+        }
+        const int all = __syncthreads_and(done);
+        if (s_bad) return false;
+        if (all) return true;
+    }
+    return false;
+}
+
+// Starting estimates for cta_aberth_shifts (one warp; lane q holds the
+// q-th previous shift).  Warm start: the np shifts of the previous
+// multishift sweep, whose trailing block ended dh rows lower (0 <= dh < nb);
+// for each of the dh eigenvalues deflated since (defl) the nearest previous
+// shift is dropped, then while more than nb remain the one farthest from
+// every diagonal entry of M; the remaining places take diagonal entries of
+// M moved apart by multiples of 1e-4 mnrm.  Cold start (np = 0): the
+// diagonal of M moved by 1e-3 mnrm along the nb-th roots of unity.
+template <class R>
+__device__ __forceinline__ void warp_argbest(R &d, int &l, bool want_min)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const R od = __shfl_xor_sync(0xffffffffu, d, o);
+        const int ol = __shfl_xor_sync(0xffffffffu, l, o);
+        if ((want_min ? od < d : od > d) || (od == d && ol < l)) { d = od; l = ol; }
+    }
+}
+template <class R, int LDM>
+__device__ void warp_aberth_start(const cplx<R> *M, int nb, R mnrm, const cplx<R> *prev, int np, const cplx<R> *defl,
+                                  int dh, cplx<R> *z)
+{
+    const int lane = threadIdx.x & 31;
+    const cplx<R> c = lane < np ? prev[lane] : cplx<R>{0, 0};
+    bool alive = lane < np;
+    for (int q = 0; q < dh; ++q) {
+        R d = alive ? abs2(c - defl[q]) : R(INFINITY);
+        int l = lane;
+        warp_argbest(d, l, true);
+        if (d < R(INFINITY) && lane == l) alive = false;
+    }
+    int cnt = __popc(__ballot_sync(0xffffffffu, alive));
+    while (cnt > nb) {
+        R d = R(-1);
+        if (alive) {
+            d = abs2(c - M[0]);
+            for (int i = 1; i < nb; ++i) d = fmin(d, abs2(c - M[i + i * LDM]));
+        }
+        int l = lane;
+        warp_argbest(d, l, false);
+        if (lane == l) alive = false;
+        --cnt;
+    }
+    const unsigned am = __ballot_sync(0xffffffffu, alive);
+    if (alive) z[__popc(am & ((1u << lane) - 1u))] = c;
+    const int q = lane - cnt;  // places cnt .. nb-1
+    if (q >= 0 && lane < nb) {
+        const cplx<R> d = M[q + q * LDM];
+        if (np > 0) {
+            z[lane] = cplx<R>{d.x + R(q + 1) * R(1e-4) * mnrm, d.y};
+        } else {
+            R sn, cs;
+            sincospi(R(2 * q) / R(nb), &sn, &cs);
+            z[lane] = cplx<R>{d.x + R(1e-3) * mnrm * cs, d.y + R(1e-3) * mnrm * sn};
+        }
+    }
     __syncwarp();
 }
 
@@ -659,6 +817,9 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
     RotLog<R> *rt = reinterpret_cast<RotLog<R> *>(tile + D::TILE);  // rt[q NB + g]
     __shared__ cplx<R> s_mu[NB];
     __shared__ cplx<R> s_m[NB * (NB + 1)];
+    __shared__ cplx<R> s_prev[NB], s_defl[NB];  // the last multishift sweep's shifts; eigenvalues deflated since
+    __shared__ R s_mnrm;
+    __shared__ int s_prevn, s_prevhi;
     __shared__ int s_lo, s_hi, s_iter, s_status, s_done, s_nb, s_sweeps, s_stop, s_nwin, s_nlog, s_small, s_bad, s_npost,
         s_tiny;
     __shared__ long long s_uoff, s_rots, s_work;
@@ -697,6 +858,8 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
         s_stop = 0;
         s_bad = 0;
         s_npost = 0;
+        s_prevn = 0;
+        s_prevhi = 0;
     }
     __syncthreads();
 
@@ -808,15 +971,42 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
         const int nb = s_nb;
         if (s_small) {  // shifts: eigenvalues of the trailing nb x nb block
             // the block is fetched by the whole CTA (one round trip to L2
-            // instead of a warp's nb*nb/32 dependent ones), then one warp
-            // computes its eigenvalues
+            // instead of a warp's nb*nb/32 dependent ones).  Its eigenvalues
+            // come from the Ehrlich-Aberth iteration, started from the
+            // previous sweep's shifts when its trailing block ended less
+            // than nb rows lower; if that fails, one warp computes them by
+            // single-shift QR.
             const int b0 = hi - nb + 1;
+            if (tid == 0) s_mnrm = R(0);
             for (int e = tid; e < nb * nb; e += nt) {
                 const int i = e % nb, j = e / nb;
                 s_m[i + j * (NB + 1)] = (i <= j + 1) ? ldT((b0 + i) + (int64_t)(b0 + j) * ld) : cplx<R>{0, 0};
             }
+            const int dh = s_prevhi - hi;
+            const bool warm = s_prevn > 0 && dh >= 0 && dh < nb;
+            if (warm && tid < dh) s_defl[tid] = ldT((hi + 1 + tid) + (int64_t)(hi + 1 + tid) * ld);
             __syncthreads();
-            if (warp == 0) warp_small_eigvals<R, NB + 1>(s_m, nb, s_mu);
+            if (warp == 0) {
+                R mx = R(0);
+                for (int e = lane; e < nb * nb; e += 32) {
+                    const cplx<R> v = s_m[(e % nb) + (e / nb) * (NB + 1)];
+                    mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+                }
+                for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                if (lane == 0) s_mnrm = mx;
+            }
+            __syncthreads();
+            if (warp == 0) warp_aberth_start<R, NB + 1>(s_m, nb, s_mnrm, s_prev, warm ? s_prevn : 0, s_defl, warm ? dh : 0, s_mu);
+            __syncthreads();
+            if (!cta_aberth_shifts<R, NB + 1>(s_m, nb, s_mu, s_mnrm, kAberthIt)) {
+                if (warp == 0) warp_small_eigvals<R, NB + 1>(s_m, nb, s_mu);
+                __syncthreads();
+            }
+            if (tid < nb) s_prev[tid] = s_mu[tid];
+            if (tid == 0) {
+                s_prevn = nb;
+                s_prevhi = hi;
+            }
             __syncthreads();
         }
         const int nsteps = (hi - lo) + 3 * (nb - 1);
@@ -834,10 +1024,11 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
                 __syncthreads();
                 break;
             }
-            for (int e = tid; e < bw * bw; e += nt) {
-                const int a = e % bw, b = e / bw;
-                load_t<R, HELP>(&blk[a + b * BLD], &T[(r0 + a) + (int64_t)(r0 + b) * ld]);
-            }
+            // only the band a <= b + 2 (Hessenberg part and bulge entries):
+            // the chase never reads or writes the block below it
+            for (int b = warp; b < bw; b += nt / 32)
+                for (int a = lane; a <= min(b + 2, bw - 1); a += 32)
+                    load_t<R, HELP>(&blk[a + b * BLD], &T[(r0 + a) + (int64_t)(r0 + b) * ld]);
             for (int e = tid; e < W * NB; e += nt) rt[e] = RotLog<R>{R(1), R(0), R(0), R(0)};
             cp_async_wait_all();
             __syncthreads();
@@ -914,10 +1105,9 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
                 }
             }
             __syncthreads();
-            for (int e = tid; e < bw * bw; e += nt) {
-                const int a = e % bw, b = e / bw;
-                T[(r0 + a) + (int64_t)(r0 + b) * ld] = blk[a + b * BLD];
-            }
+            for (int b = warp; b < bw; b += nt / 32)
+                for (int a = lane; a <= min(b + 2, bw - 1); a += 32)
+                    T[(r0 + a) + (int64_t)(r0 + b) * ld] = blk[a + b * BLD];
             {
                 RotLog<R> *dst = d.log + s_nlog;
                 for (int e = tid; e < W * NB; e += nt) dst[e] = rt[e];
