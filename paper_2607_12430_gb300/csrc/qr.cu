@@ -679,23 +679,38 @@ __device__ __forceinline__ uint64_t wait_limit(const SchurDesc<R> &d)
     return d.wait_ns ? (uint64_t)d.wait_ns : kQrWaitNs;
 }
 
-// Cooperative chase: every thread of the calling CTA waits until each of
-// the H helpers has finished `target` windows; false if a helper failed or
+// Cooperative chase: one warp waits until each of the H <= 32 helpers has
+// finished `target` windows, lane h watching helper h (one round trip to L2
+// per poll instead of H in a row); false (warp-uniform) if a helper failed or
 // the wait gave up.
+template <class R>
+__device__ bool warp_poll_helpers(const SchurDesc<R> &d, int H, int target)
+{
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+    if (lane < H) {
+        volatile int *sy = d.sync;
+        const uint64_t t0 = globaltimer_ns(), lim = wait_limit(d);
+        while (sy[4 + lane] < target) {
+            if (sy[2] || globaltimer_ns() - t0 > lim) { ok = false; break; }
+            __nanosleep(128);  // keep the polls off the helpers' L2 lines
+        }
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    __threadfence();
+    return ok;
+}
+
+// Every thread of the calling CTA waits until each helper has finished
+// `target` windows (warp 0 polls); false if a helper failed or the wait gave
+// up.
 template <class R>
 __device__ bool wait_helpers(const SchurDesc<R> &d, int H, int target)
 {
     __shared__ int s_ok;
-    if (threadIdx.x == 0) {
-        volatile int *sy = d.sync;
-        const uint64_t t0 = globaltimer_ns(), lim = wait_limit(d);
-        int ok = 1;
-        for (int h = 0; h < H && ok; ++h)
-            while (sy[4 + h] < target) {
-                if (sy[2] || globaltimer_ns() - t0 > lim) { ok = 0; break; }
-            }
-        __threadfence();
-        s_ok = ok;
+    if (threadIdx.x < 32) {
+        const bool ok = warp_poll_helpers(d, H, target);
+        if (threadIdx.x == 0) s_ok = ok;
     }
     __syncthreads();
     const bool ok = s_ok != 0;
@@ -819,7 +834,7 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
     __shared__ cplx<R> s_m[NB * (NB + 1)];
     __shared__ cplx<R> s_prev[NB], s_defl[NB];  // the last multishift sweep's shifts; eigenvalues deflated since
     __shared__ R s_mnrm;
-    __shared__ int s_prevn, s_prevhi;
+    __shared__ int s_prevn, s_prevhi, s_prefail;
     __shared__ int s_lo, s_hi, s_iter, s_status, s_done, s_nb, s_sweeps, s_stop, s_nwin, s_nlog, s_small, s_bad, s_npost,
         s_tiny;
     __shared__ long long s_uoff, s_rots, s_work;
@@ -1030,6 +1045,19 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
                 for (int a = lane; a <= min(b + 2, bw - 1); a += 32)
                     load_t<R, HELP>(&blk[a + b * BLD], &T[(r0 + a) + (int64_t)(r0 + b) * ld]);
             for (int e = tid; e < W * NB; e += nt) rt[e] = RotLog<R>{R(1), R(0), R(0), R(0)};
+            // last column of the next window's block (hi after the last window)
+            const int rnext = (t1 < nsteps) ? min(hi, min(hi - 1, lo + min(t1 + W, nsteps) - 1) + 2) : hi;
+            // cooperative chase: windows with more than kQrPostMin rows and
+            // columns outside the next block go to the helpers (the chase CTA
+            // then updates only the next block's new columns (r1, rnext]);
+            // smaller ones are done here after the helpers have finished every
+            // posted window, so each entry still sees the windows in order
+            const bool post = HELP && (hi - rnext) + (r0 - lo) > kQrPostMin;
+            // a posted window's new columns (at most W) are read during the
+            // chase by the warps that do not chase, once the helpers are done
+            // with every window posted before this one
+            const int pre_cn = post ? rnext - r1 : 0;
+            if (tid == 0) s_prefail = 0;
             cp_async_wait_all();
             __syncthreads();
             // the chase: half-warp h of warp w moves bulge g = 2 w + h.  Each
@@ -1103,25 +1131,56 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
                     }
                     chase_bar<NB * 16>();
                 }
+                if (pre_cn > 0) {
+                    // a posted window: the chasing warps store the block band and
+                    // the rotation table and post the window at once, while the
+                    // other warps may still wait for the helpers
+                    constexpr int NCH = NB * 16;
+                    for (int b = warp; b < bw; b += NCH / 32)
+                        for (int a = lane; a <= min(b + 2, bw - 1); a += 32)
+                            T[(r0 + a) + (int64_t)(r0 + b) * ld] = blk[a + b * BLD];
+                    RotLog<R> *dst = d.log + s_nlog;
+                    for (int e = tid; e < W * NB; e += NCH) dst[e] = rt[e];
+                    if (tid == 0) {
+                        WinRec wr;
+                        wr.start = s_nlog; wr.kbase = kbase; wr.nsteps = ns; wr.kmin = kmin; wr.rr = rr;
+                        wr.lo = lo; wr.hi = hi; wr.t0 = t0; wr.nb = nb; wr.r0 = r0; wr.rnext = rnext; wr.pad = 0;
+                        wr.uoff = s_uoff;
+                        d.win[s_nwin] = wr;
+                        d.postlist[s_npost] = s_nwin;
+                    }
+                    __threadfence();
+                    chase_bar<NCH>();
+                    if (tid == 0) atomicExch(&d.sync[0], s_npost + 1);
+                }
+            } else if (pre_cn > 0) {
+                constexpr int NPRE = kQrThreads - NB * 16;  // threads of the warps that do not chase
+                static_assert(NPRE >= 32, "the prefetch needs a warp");
+                if (warp == NB / 2 && !warp_poll_helpers(d, H, s_npost) && lane == 0) s_prefail = 1;
+                asm volatile("bar.sync 2, %0;" ::"n"(NPRE) : "memory");
+                if (!s_prefail) {
+                    const int pt = tid - NB * 16;
+                    for (int e = pt; e < rr * pre_cn; e += NPRE) {
+                        const int v = e % rr, j = e / rr;
+                        tile[v + j * RLD] = ldcg_c<R>(&T[(kmin + v) + (int64_t)(r1 + 1 + j) * ld]);
+                    }
+                }
             }
             __syncthreads();
-            for (int b = warp; b < bw; b += nt / 32)
-                for (int a = lane; a <= min(b + 2, bw - 1); a += 32)
-                    T[(r0 + a) + (int64_t)(r0 + b) * ld] = blk[a + b * BLD];
-            {
+            if (s_prefail) {
+                if (tid == 0) s_status = 6;
+                __syncthreads();
+                break;
+            }
+            const int off = kbase - kmin;
+            if (pre_cn == 0) {  // (a prefetched window is stored and posted already)
+                for (int b = warp; b < bw; b += nt / 32)
+                    for (int a = lane; a <= min(b + 2, bw - 1); a += 32)
+                        T[(r0 + a) + (int64_t)(r0 + b) * ld] = blk[a + b * BLD];
                 RotLog<R> *dst = d.log + s_nlog;
                 for (int e = tid; e < W * NB; e += nt) dst[e] = rt[e];
             }
-            const int off = kbase - kmin;
-            // last column of the next window's block (hi after the last window)
-            const int rnext = (t1 < nsteps) ? min(hi, min(hi - 1, lo + min(t1 + W, nsteps) - 1) + 2) : hi;
-            // cooperative chase: windows with more than kQrPostMin rows and
-            // columns outside the next block go to the helpers (the chase CTA
-            // then updates only the next block's new columns (r1, rnext]);
-            // smaller ones are done here after the helpers have finished every
-            // posted window, so each entry still sees the windows in order
-            const bool post = HELP && (hi - rnext) + (r0 - lo) > kQrPostMin;
-            if (HELP) {
+            if (HELP && pre_cn == 0) {
                 if (post && tid == 0) {
                     WinRec wr;
                     wr.start = s_nlog; wr.kbase = kbase; wr.nsteps = ns; wr.kmin = kmin; wr.rr = rr;
@@ -1134,7 +1193,8 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
                 __syncthreads();
                 if (post && tid == 0) atomicExch(&d.sync[0], s_npost + 1);
                 // helpers done with every window posted before this one (all of
-                // them if this one is done here)
+                // them if this one is done here; for a posted one the warps that
+                // prefetched its new columns have waited for that already)
                 if (!wait_helpers(d, H, s_npost)) {
                     if (tid == 0) s_status = 6;
                     __syncthreads();
@@ -1145,10 +1205,11 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
             const int aend = post ? rnext : hi;
             for (int c0 = r1 + 1; c0 <= aend; c0 += kQrCh) {
                 const int cn = min(kQrCh, aend - c0 + 1);
-                for (int e = tid; e < rr * cn; e += nt) {
-                    const int v = e % rr, j = e / rr;
-                    load_t<R, HELP>(&tile[v + j * RLD], &T[(kmin + v) + (int64_t)(c0 + j) * ld]);
-                }
+                if (pre_cn == 0)  // else the tile holds them already (one chunk: cn = pre_cn)
+                    for (int e = tid; e < rr * cn; e += nt) {
+                        const int v = e % rr, j = e / rr;
+                        load_t<R, HELP>(&tile[v + j * RLD], &T[(kmin + v) + (int64_t)(c0 + j) * ld]);
+                    }
                 cp_async_wait_all();
                 __syncthreads();
                 if (post) {
