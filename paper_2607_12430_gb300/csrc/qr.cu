@@ -483,7 +483,8 @@ __device__ void warp_aberth_start(const cplx<R> *M, int nb, R mnrm, const cplx<R
 // above the block, Schur vectors) and y <- U^H y (columns right of it).
 // Returns false if some eigenvalue took more than kItMax sweeps.
 template <class R, int LDM>
-__device__ bool warp_tiny_schur(cplx<R> *M, cplx<R> *U, int m, int *sweeps, int *rots)
+__device__ bool warp_tiny_schur(cplx<R> *M, cplx<R> *U, int m, int *sweeps, int *rots, const cplx<R> *cand = nullptr,
+                                int ncand = 0)
 {
     const int lane = threadIdx.x & 31;
     const R eps = num<R>::eps;
@@ -518,6 +519,19 @@ __device__ bool warp_tiny_schur(cplx<R> *M, cplx<R> *U, int m, int *sweeps, int 
         } else {
             mu = wilkinson(M[(hi - 1) + (hi - 1) * LDM], M[(hi - 1) + hi * LDM], M[hi + (hi - 1) * LDM],
                            M[hi + hi * LDM]);
+            if (it == 1 && ncand > 0) {
+                // first sweep on this bottom entry: the nearest of the given
+                // estimates (shifts of the sweep that split this block off,
+                // eigenvalue estimates of the whole matrix) replaces the
+                // Wilkinson shift when both point at the same eigenvalue
+                R db = R(INFINITY);
+                cplx<R> zb = mu;
+                for (int q = 0; q < ncand; ++q) {
+                    const R dq = abs2(cand[q] - mu);
+                    if (dq < db) { db = dq; zb = cand[q]; }
+                }
+                if (db <= R(1e-4) * abs2(mu)) mu = zb;
+            }
         }
         __syncwarp();
         warp_sweep<R, LDM, true, false>(M, U, m, lo, hi, mu, &nrot);
@@ -952,7 +966,7 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
             __syncthreads();
             if (warp == 0) {
                 int nsw = 0, nrot = 0;
-                const bool ok = warp_tiny_schur<R, kQrTinyLd>(Mb, Ub, m, &nsw, &nrot);
+                const bool ok = warp_tiny_schur<R, kQrTinyLd>(Mb, Ub, m, &nsw, &nrot, s_prev, s_prevn);
                 if (lane == 0) {
                     if (!ok) s_status = 3;
                     s_sweeps += nsw;
