@@ -77,12 +77,14 @@ __device__ __forceinline__ void tile_mms(cplx<R> (&acc)[8], const cplx<R> *A, co
 // triangular, C (ma x nb) overwritten by Y with A Y + Y B = C.  Anti-diagonal
 // w holds the entries with j - i = w - (ma - 1); each entry depends on
 // entries below it in its column and left of it in its row, all on earlier
-// anti-diagonals.
+// anti-diagonals.  An anti-diagonal has at most 32 entries, so each gets
+// blockDim.x / 32 consecutive threads (4, 8 or 16) for its dot product.
 template <class R>
 __device__ void leaf_sylvester(const cplx<R> *A, const cplx<R> *B, cplx<R> *C, int ma, int nb,
                                int *bad)
 {
-    const int e = threadIdx.x >> 2, p = threadIdx.x & 3;
+    const int tpe = (int)(blockDim.x >> 5);
+    const int e = threadIdx.x / tpe, p = threadIdx.x % tpe;
     for (int w = 0; w <= ma + nb - 2; ++w) {
         const int ioff = ma - 1 - w;  // j = i - ioff
         const int ilo = max(0, ioff), ihi = min(ma - 1, ioff + nb - 1);
@@ -93,13 +95,12 @@ __device__ void leaf_sylvester(const cplx<R> *A, const cplx<R> *B, cplx<R> *C, i
         if (act) {
             const int la = ma - 1 - i;  // terms A(i, k) C(k, j), k = i+1 .. ma-1
             const int L = la + j;       // plus C(i, k) B(k, j), k = 0 .. j-1
-            for (int t = p; t < L; t += 4) {
+            for (int t = p; t < L; t += tpe) {
                 if (t < la) cfma(acc, A[i + (i + 1 + t) * TLD], C[(i + 1 + t) + j * TLD]);
                 else { int k = t - la; cfma(acc, C[i + k * TLD], B[k + j * TLD]); }
             }
         }
-        acc += shfl_xor(acc, 1);
-        acc += shfl_xor(acc, 2);
+        for (int o = 1; o < tpe; o <<= 1) acc += shfl_xor(acc, o);
         if (act && p == 0) {
             cplx<R> den = A[i + i * TLD] + B[j + j * TLD];
             if (den.x == R(0) && den.y == R(0)) { *bad = 1; den = cplx<R>{R(1), R(0)}; }
