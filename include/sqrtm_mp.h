@@ -76,8 +76,10 @@ enum { SQRTM_KIND_AUTO = 0, SQRTM_KIND_GENERAL = 1, SQRTM_KIND_SPD = 2, SQRTM_KI
  * products of 5- to 8-bit digit slices of X on the BF16 tensor cores and
  * summed in FP64 (error-free splitting; the terms left out are below
  * n 2^(rho_i + rho_j - 56), 2^rho_i bounding row i of X, i.e. within the
- * FP64 product's own error bound); RESID_FP64 forces the FP64 product on
- * the CUDA cores. */
+ * FP64 product's own error bound).  The general path's residual (Algorithm
+ * 2, step 4) of a real iterate of the FP32 method does the same from
+ * n = 512 on, with the digit slices of the rows of X against those of its
+ * columns.  RESID_FP64 forces the FP64 product on the CUDA cores in both. */
 enum {
     SQRTM_PREC_AUTO = -1,
     SQRTM_PREC_FP32 = 0,

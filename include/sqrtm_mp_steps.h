@@ -203,6 +203,22 @@ SQRTM_API int sqrtm_step_residual_sym(sqrtm_handle_t h, const double *dA, int64_
                                       int64_t ldx, int64_t n, int e, float *dRhat, double *norm_host,
                                       int split);
 
+/* Residual of the general path (Algorithm 2, step 4: R = A - X^2 in
+ * double precision) with X^2 from exact BF16 tensor-core products of digit
+ * slices: the rows of X (from a transposed copy) against its columns, every
+ * output tile, products summed in FP64 (error-free splitting as in
+ * sqrtm_step_residual_sym; terms left out below n 2^(rho_i + gamma_j - 56),
+ * 2^rho_i bounding row i and 2^gamma_j column j of X).  Same scaling and
+ * outputs as sqrtm_step_residual: fl32(4^-e A - (2^-e X)^2) into dRhat
+ * (float n x n, ld n), ||R||_F into *norm_host.  Memory: dA, dX n x n FP64
+ * column-major (lda, ldx), device, owned by the caller; the digit slices,
+ * X^T and the FP64 tile accumulator live in the handle's workspace.  Errors:
+ * -1 no handle, -3 lda < n, -5 ldx < n, -6 n < 0 or n > 46340, -10 the
+ * splitting does not apply to n (n 2^(2b) > 2^24 for every digit width b),
+ * 6 a bounded wait inside the tensor-core kernel gave up, 7 a CUDA error. */
+SQRTM_API int sqrtm_step_residual_split(sqrtm_handle_t h, const double *dA, int64_t lda, const double *dX,
+                                        int64_t ldx, int64_t n, int e, float *dRhat, double *norm_host);
+
 /* The residual above for callers that cannot allocate device memory.  The
  * paper has no counterpart: this is a library service.  It takes no handle
  * (a handle allocates its workspace on first use); its scratch -- the norm's

@@ -130,6 +130,7 @@ _SIGS = {
     "sqrtm_step_gemm_tf32x3": ([_P, _L, _L, _L, _P, _L, _P, _L, _P, _L], _I),
     "sqrtm_step_cgemm_tf32x3": ([_P, _L, _L, _L, _P, _L, _I, _P, _L, _I, _P, _L], _I),
     "sqrtm_step_residual_sym": ([_P, _P, _L, _P, _L, _L, _I, _P, ctypes.POINTER(_D), _I], _I),
+    "sqrtm_step_residual_split": ([_P, _P, _L, _P, _L, _L, _I, _P, ctypes.POINTER(_D)], _I),
     "sqrtm_step_residual_noalloc": ([_P, _L, _P, _L, _L, _I, _P, ctypes.POINTER(_D), _P], _I),
 }
 
@@ -690,6 +691,17 @@ def step_residual_sym(A_cm, X_cm, n, e=0, split=False):
     nrm = ctypes.c_double()
     _rc(lib().sqrtm_step_residual_sym(handle(), _ptr(A_cm), n, _ptr(X_cm), n, n, e, _ptr(Rhat),
                                       ctypes.byref(nrm), int(split)), "residual_sym")
+    return Rhat, nrm.value
+
+
+def step_residual_split(A_cm, X_cm, n, e=0):
+    """FP64 residual of the general path with X X from exact BF16
+    tensor-core digit products (rows of X against its columns) summed in
+    FP64."""
+    Rhat = torch.empty(n * n, dtype=torch.float32, device=A_cm.device)
+    nrm = ctypes.c_double()
+    _rc(lib().sqrtm_step_residual_split(handle(), _ptr(A_cm), n, _ptr(X_cm), n, n, e, _ptr(Rhat),
+                                        ctypes.byref(nrm)), "residual_split")
     return Rhat, nrm.value
 
 

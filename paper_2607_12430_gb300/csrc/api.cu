@@ -331,6 +331,10 @@ static int read_scalars(sqrtm_handle_t h, const Scalars &s, double *norm, double
 static bool is_bitwise_symmetric(sqrtm_handle_t h, const double *dA, int64_t n, int64_t lda,
                                  int *flag_dev, int *rc);
 
+// smallest n whose general-path residual uses the split-BF16 tensor-core
+// products (below it the FP64 CUDA-core product is as fast)
+static constexpr int64_t kGenSplitMinN = 512;
+
 // ---------------------------------------------------------------------------
 // general path (Algorithm 2) in storage precision R; refine = false gives the
 // plain Schur method.  root = 3 gives the principal cube root (Sec. 4, p = 3)
@@ -367,6 +371,16 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     const size_t tcf = 4 * nn;  // floats of one full re-laid n x n complex operand (2n x 2n)
     if (use_tc)
         wbytes += Carve::round(nn * cb) + 3 * Carve::round(tcf * sizeof(float)) + Carve::round(2 * nn * sizeof(float));
+    // FP64 residual of a real iterate (the FP32 square root) from exact
+    // split-BF16 tensor-core products (rows of X against its columns) from
+    // kGenSplitMinN on, unless SQRTM_PREC_RESID_FP64 asks for FP64 products
+    const int64_t npart_cap = std::max<int64_t>(((n + 63) / 64) * ((n + 63) / 64), 2048);
+    const bool use_gsplit = sizeof(R) == sizeof(float) && root == 2 && !cin && refine && n >= kGenSplitMinN &&
+                            n <= 46340 && !(o.precision & SQRTM_PREC_RESID_FP64) && split_residual_supported((int)n) &&
+                            residual_gen_split_parts((int)n) <= npart_cap;
+    if (use_gsplit)
+        wbytes += 2 * Carve::round(nn * sizeof(double)) + 2 * Carve::round(split_digit_elems((int)n) * 2) +
+                  2 * Carve::round(n * sizeof(int));
     if (ensure(h->fact, fbytes, h) || ensure(h->ws, wbytes, h)) return 7;
     Carve cf(h->fact.p);
     cplx<R> *Q = cf.take<cplx<R>>(nn);
@@ -411,6 +425,12 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
     float *YB = use_tc ? cw.take<float>(tcf) : nullptr;
     float *QhB = use_tc ? cw.take<float>(2 * nn) : nullptr;
     const int ld2 = 2 * (int)n;  // leading dimension of the re-laid operands (floats)
+    double *gRacc = use_gsplit ? cw.take<double>(nn) : nullptr;  // split residual: FP64 tile sums,
+    double *gXT = use_gsplit ? cw.take<double>(nn) : nullptr;    // X^T, the two digit sets
+    void *gDa = use_gsplit ? (void *)cw.take<uint16_t>(split_digit_elems((int)n)) : nullptr;
+    void *gDb = use_gsplit ? (void *)cw.take<uint16_t>(split_digit_elems((int)n)) : nullptr;
+    int *gRhoA = use_gsplit ? cw.take<int>(n) : nullptr;
+    int *gRhoB = use_gsplit ? cw.take<int>(n) : nullptr;
     h->fact_n = -1;
 
     SQM_CU(cudaMemsetAsync(sc.e, 0, 16 * sizeof(int), s));
@@ -546,6 +566,9 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
             } else if (cin) {
                 SQM_CU(launch_zresidual_f64(dA, lda, dX, ldx, (int)n, e, (cplx<float> *)Rhat, (int)n, sc.partials, &np,
                                             s));
+            } else if (use_gsplit) {
+                SQM_CU(launch_residual_gen_split(dA, lda, dX, ldx, (int)n, e, Rhat, (int)n, gRacc, gXT, gDa, gDb, gRhoA,
+                                                 gRhoB, sc.partials, &np, sc.st_solve, s));
             } else {
                 SQM_CU(launch_residual_f64(dA, lda, dX, ldx, (int)n, e, Rhat, (int)n, sc.partials, &np, s));
             }

@@ -29,6 +29,14 @@ size_t split_digit_elems(int n);
 cudaError_t launch_residual_sym_split(const double *A, int64_t lda, const double *X, int64_t ldx, int n, int e,
                                       float *Rhat, int ldr, double *Racc, void *digits, int *rho,
                                       double *partials, int *nparts, int *err, cudaStream_t s);
+// R = (A - X X) 4^-e for a general X by the same splitting: the rows of X
+// (from XT = X^T, n x n doubles of scratch) against its columns, every
+// output tile.  digitsA, digitsB: split_digit_elems(n) BF16 values each;
+// rhoA, rhoB: n ints each; partials: residual_gen_split_parts(n) doubles.
+int residual_gen_split_parts(int n);
+cudaError_t launch_residual_gen_split(const double *A, int64_t lda, const double *X, int64_t ldx, int n, int e,
+                                      float *Rhat, int ldr, double *Racc, double *XT, void *digitsA, void *digitsB,
+                                      int *rhoA, int *rhoB, double *partials, int *nparts, int *err, cudaStream_t s);
 
 // Householder tridiagonalisation A = Q Tri Q^T (A overwritten: the
 // tridiagonal on its diagonal and first subdiagonal).  Reflector k,

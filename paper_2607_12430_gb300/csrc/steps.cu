@@ -303,6 +303,39 @@ extern "C" int sqrtm_step_residual(sqrtm_handle_t h, const double *dA, int64_t l
     return 0;
 }
 
+extern "C" int sqrtm_step_residual_split(sqrtm_handle_t h, const double *dA, int64_t lda, const double *dX,
+                                         int64_t ldx, int64_t n, int e, float *dRhat, double *norm_host)
+{
+    if (!h) return -1;
+    if (n < 0) return -6;
+    if (lda < std::max<int64_t>(1, n)) return -3;
+    if (ldx < std::max<int64_t>(1, n)) return -5;
+    if (n > 46340) return -6;
+    if (!split_residual_supported((int)n)) return -10;
+    if (n == 0) { if (norm_host) *norm_host = 0; return 0; }
+    const size_t nn = (size_t)n * n;
+    const size_t extra = 2 * Carve::round(nn * sizeof(double)) + 2 * Carve::round(split_digit_elems((int)n) * 2) +
+                         2 * Carve::round(n * sizeof(int));
+    StepScratch ss; void *ex;
+    if (int rc = step_scratch(h, n, extra, &ss, &ex)) return rc;
+    Carve c(ex);
+    double *Racc = c.take<double>(nn);
+    double *XT = c.take<double>(nn);
+    void *da = c.take<uint16_t>(split_digit_elems((int)n));
+    void *db = c.take<uint16_t>(split_digit_elems((int)n));
+    int *rhoA = c.take<int>(n);
+    int *rhoB = c.take<int>(n);
+    int np = 0;
+    if (launch_residual_gen_split(dA, lda, dX, ldx, (int)n, e, dRhat, (int)n, Racc, XT, da, db, rhoA, rhoB,
+                                  ss.dscal + 2, &np, ss.iscal + 1, h->stream)) return 7;
+    if (launch_sum_partials(ss.dscal + 2, np, ss.dscal + 1, h->stream)) return 7;
+    double rn;
+    int st = 0;
+    if (fetch(h, &rn, ss.dscal + 1, sizeof(double)) || fetch(h, &st, ss.iscal + 1, sizeof(int))) return 7;
+    if (norm_host) *norm_host = rn;
+    return st;
+}
+
 extern "C" int sqrtm_step_residual_sym(sqrtm_handle_t h, const double *dA, int64_t lda, const double *dX,
                                        int64_t ldx, int64_t n, int e, float *dRhat, double *norm_host,
                                        int split)

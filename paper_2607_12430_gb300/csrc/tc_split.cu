@@ -150,7 +150,8 @@ struct SplitEpi {
     int64_t lda;
     double *Racc;
     int64_t ldr;
-    const int *rho;
+    const int *rho;   // scaling exponents of the left operand's rows
+    const int *rhoB;  // of the right operand's rows (the same array for X X^T)
     float *Rhat;
     int64_t ldh;
     double sc;      // 4^-e
@@ -179,10 +180,15 @@ __device__ __forceinline__ double sp_pow2(int e)
     return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
 }
 
-template <int SP_MH>
+// GEN = false: R = A - X X for symmetric X, both operands the digit slices of
+// X (mapX), output tiles of the upper block triangle, R mirrored.  GEN = true:
+// R = A - X Y^T for the row digits of X (mapX, exponents ep.rho) and of Y
+// (mapB, ep.rhoB) -- with Y = X^T the residual of a general X -- over every
+// output tile (T column blocks per row block, row-major).
+template <int SP_MH, bool GEN>
 __global__ void __launch_bounds__(SP_THREADS, 1)
-split_gemm_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ SplitPlan plan, int n, int KT,
-                  int T, int ntiles, SplitEpi ep, int *err)
+split_gemm_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapB,
+                  const __grid_constant__ SplitPlan plan, int n, int KT, int T, int ntiles, SplitEpi ep, int *err)
 {
     constexpr int SP_BM = SpCfg<SP_MH>::BM, SP_STAGES = SpCfg<SP_MH>::STAGES;
     constexpr int SP_STAGE_BYTES = (SP_MH + 1) * SP_TILE_BYTES;  // the A boxes, then B
@@ -225,6 +231,11 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constan
     // tiles meeting the upper triangle: row block I (128 MH rows), column
     // blocks J >= MH I (128 columns; T of them), row-major over I
     auto tile_origin = [&](int q, int &m0, int &n0) {
+        if (GEN) {
+            m0 = (q / T) * SP_BM;
+            n0 = (q % T) * SP_BN;
+            return;
+        }
         int I = 0;
         while (q >= T - SP_MH * I) { q -= T - SP_MH * I; ++I; }
         m0 = I * SP_BM;
@@ -252,7 +263,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constan
 #pragma unroll
                         for (int h = 0; h < SP_MH; ++h)
                             tma_load_2d(stage_ptr(s, h), &mapX, &full[s], kb * SP_BK, plan.ps[pr] * n + m0 + h * SP_BR);
-                        tma_load_2d(stage_ptr(s, SP_MH), &mapX, &full[s], kb * SP_BK, plan.pt[pr] * n + n0);
+                        tma_load_2d(stage_ptr(s, SP_MH), GEN ? &mapB : &mapX, &full[s], kb * SP_BK, plan.pt[pr] * n + n0);
                         ++it;
                     }
                 }
@@ -335,16 +346,16 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constan
 #pragma unroll
                             for (int j = 0; j < 32; ++j) {
                                 const int col = n0 + c0 + j;
-                                const bool in = col < n && row <= col;
+                                const bool in = col < n && (GEN || row <= col);
                                 old[j] = in ? (first ? ep.A[row + (int64_t)col * ep.lda]
                                                      : ep.Racc[row + (int64_t)col * ep.ldr])
                                             : 0.0;
-                                rj[j] = col < n ? ep.rho[col] : 0;
+                                rj[j] = col < n ? (GEN ? ep.rhoB[col] : ep.rho[col]) : 0;
                             }
 #pragma unroll
                             for (int j = 0; j < 32; ++j) {
                                 const int col = n0 + c0 + j;
-                                if (col >= n || row > col) continue;
+                                if (col >= n || (!GEN && row > col)) continue;
                                 // old - P 2^(rho_i + rho_j - shift): the product
                                 // is exact, so one rounding as in old - ldexp(P, ...)
                                 const double v2 =
@@ -353,9 +364,9 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constan
                                     const double rs = v2 * ep.sc;
                                     const float rf = (float)rs;
                                     ep.Rhat[row + (int64_t)col * ep.ldh] = rf;
-                                    ep.Rhat[col + (int64_t)row * ep.ldh] = rf;
+                                    if (!GEN) ep.Rhat[col + (int64_t)row * ep.ldh] = rf;
                                     ss = fma(rs, rs, ss);
-                                    if (row != col) ss = fma(rs, rs, ss);  // mirrored entry
+                                    if (!GEN && row != col) ss = fma(rs, rs, ss);  // mirrored entry
                                 } else {
                                     ep.Racc[row + (int64_t)col * ep.ldr] = v2;
                                 }
@@ -420,42 +431,25 @@ bool split_residual_supported(int n)
     return n >= 1 && (int64_t)n * (1 << (2 * b)) <= (1 << 24) && encode_fn() != nullptr;
 }
 
-cudaError_t launch_residual_sym_split(const double *A, int64_t lda, const double *X, int64_t ldx, int n, int e,
-                                      float *Rhat, int ldr, double *Racc, void *digits, int *rho,
-                                      double *partials, int *nparts, int *err, cudaStream_t s)
+// digit slices of the rows i of X (column i in storage: X(k, i) for k < n);
+// the (b, S) pairs split_plan can give: S = ceil(60 / b) digits of b bits
+static cudaError_t launch_split_rows(const double *X, int64_t ldx, int n, int lds, __nv_bfloat16 *Xs, int *rho,
+                                     int b, int S, cudaStream_t s)
 {
-    if (n <= 0) { *nparts = 0; return cudaSuccess; }
-    int b, D;
-    split_plan(n, &b, &D);
-    const int S = D + 1, lds = split_lds(n);
-    __nv_bfloat16 *Xs = (__nv_bfloat16 *)digits;
-    {
-        const unsigned g = (unsigned)cdiv_i((int64_t)n * 32, 256);
-        // the (b, S) pairs split_plan can give: S = ceil(60 / b) digits of b bits
-        if (b == 8 && S == 8) split_rows_kernel<8, 8><<<g, 256, 0, s>>>(X, ldx, n, lds, Xs, rho);
-        else if (b == 7 && S == 9) split_rows_kernel<7, 9><<<g, 256, 0, s>>>(X, ldx, n, lds, Xs, rho);
-        else if (b == 6 && S == 10) split_rows_kernel<6, 10><<<g, 256, 0, s>>>(X, ldx, n, lds, Xs, rho);
-        else if (b == 5 && S == 12) split_rows_kernel<5, 12><<<g, 256, 0, s>>>(X, ldx, n, lds, Xs, rho);
-        else if (b == 4 && S == 15) split_rows_kernel<4, 15><<<g, 256, 0, s>>>(X, ldx, n, lds, Xs, rho);
-        else return cudaErrorInvalidValue;
-        count_launch();
-    }
-    CUtensorMap mapX;
-    if (S > SP_MAXG) return cudaErrorInvalidValue;
-    if (!make_bf16_map(&mapX, Xs, lds, (int64_t)S * n, lds)) return cudaErrorInvalidValue;
-    // T column blocks of 128; row block I (128 MH rows) meets the upper
-    // triangle in column blocks MH I .. T-1
-    const int T = (int)cdiv_i(n, SP_BN), KT = lds / SP_BK;
-    int dev = 0, sms = 152;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int ntiles2 = 0;
-    for (int I = 0; 2 * I < T; ++I) ntiles2 += T - 2 * I;
-    const int mh = ntiles2 >= sms ? 2 : 1;
-    const int ntiles = mh == 2 ? ntiles2 : T * (T + 1) / 2;
-    cudaError_t er;
-    if ((er = allow_max_smem((const void *)split_gemm_kernel<1>)) || (er = allow_max_smem((const void *)split_gemm_kernel<2>)))
-        return er;
-    // groups of pairs with the same s + t whose integer bounds sum to <= 2^24
+    const unsigned g = (unsigned)cdiv_i((int64_t)n * 32, 256);
+    if (b == 8 && S == 8) split_rows_kernel<8, 8><<<g, 256, 0, s>>>(X, ldx, n, lds, Xs, rho);
+    else if (b == 7 && S == 9) split_rows_kernel<7, 9><<<g, 256, 0, s>>>(X, ldx, n, lds, Xs, rho);
+    else if (b == 6 && S == 10) split_rows_kernel<6, 10><<<g, 256, 0, s>>>(X, ldx, n, lds, Xs, rho);
+    else if (b == 5 && S == 12) split_rows_kernel<5, 12><<<g, 256, 0, s>>>(X, ldx, n, lds, Xs, rho);
+    else if (b == 4 && S == 15) split_rows_kernel<4, 15><<<g, 256, 0, s>>>(X, ldx, n, lds, Xs, rho);
+    else return cudaErrorInvalidValue;
+    count_launch();
+    return cudaGetLastError();
+}
+
+// groups of digit pairs with the same s + t whose integer bounds sum to <= 2^24
+static SplitPlan make_split_plan(int n, int b, int D)
+{
     SplitPlan plan{};
     int np = 0;
     for (int d = 0; d <= D; ++d) {
@@ -478,12 +472,112 @@ cudaError_t launch_residual_sym_split(const double *A, int64_t lda, const double
         }
     }
     plan.gstart[plan.ng] = (short)np;
+    return plan;
+}
+
+static int sm_count()
+{
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+cudaError_t launch_residual_sym_split(const double *A, int64_t lda, const double *X, int64_t ldx, int n, int e,
+                                      float *Rhat, int ldr, double *Racc, void *digits, int *rho,
+                                      double *partials, int *nparts, int *err, cudaStream_t s)
+{
+    if (n <= 0) { *nparts = 0; return cudaSuccess; }
+    int b, D;
+    split_plan(n, &b, &D);
+    const int S = D + 1, lds = split_lds(n);
+    if (S > SP_MAXG) return cudaErrorInvalidValue;
+    __nv_bfloat16 *Xs = (__nv_bfloat16 *)digits;
+    cudaError_t er;
+    if ((er = launch_split_rows(X, ldx, n, lds, Xs, rho, b, S, s))) return er;
+    CUtensorMap mapX;
+    if (!make_bf16_map(&mapX, Xs, lds, (int64_t)S * n, lds)) return cudaErrorInvalidValue;
+    // T column blocks of 128; row block I (128 MH rows) meets the upper
+    // triangle in column blocks MH I .. T-1
+    const int T = (int)cdiv_i(n, SP_BN), KT = lds / SP_BK;
+    const int sms = sm_count();
+    int ntiles2 = 0;
+    for (int I = 0; 2 * I < T; ++I) ntiles2 += T - 2 * I;
+    const int mh = ntiles2 >= sms ? 2 : 1;
+    const int ntiles = mh == 2 ? ntiles2 : T * (T + 1) / 2;
+    if ((er = allow_max_smem((const void *)split_gemm_kernel<1, false>)) ||
+        (er = allow_max_smem((const void *)split_gemm_kernel<2, false>)))
+        return er;
+    const SplitPlan plan = make_split_plan(n, b, D);
     const int grid = std::max(1, std::min(ntiles, sms));
-    SplitEpi ep{A, lda, Racc, (int64_t)n, rho, Rhat, (int64_t)ldr, ldexp(1.0, -2 * e), partials};
-    if (mh == 2) split_gemm_kernel<2><<<grid, SP_THREADS, SP_SMEM, s>>>(mapX, plan, n, KT, T, ntiles, ep, err);
-    else split_gemm_kernel<1><<<grid, SP_THREADS, SP_SMEM, s>>>(mapX, plan, n, KT, T, ntiles, ep, err);
+    SplitEpi ep{A, lda, Racc, (int64_t)n, rho, rho, Rhat, (int64_t)ldr, ldexp(1.0, -2 * e), partials};
+    if (mh == 2) split_gemm_kernel<2, false><<<grid, SP_THREADS, SP_SMEM, s>>>(mapX, mapX, plan, n, KT, T, ntiles, ep, err);
+    else split_gemm_kernel<1, false><<<grid, SP_THREADS, SP_SMEM, s>>>(mapX, mapX, plan, n, KT, T, ntiles, ep, err);
     count_launch();
     *nparts = 4 * ntiles;  // a partial sum per epilogue warp and tile
+    return cudaGetLastError();
+}
+
+// X^T of an n x n FP64 matrix into XT (ld n), 32 x 32 tiles through shared memory
+__global__ void __launch_bounds__(256) transpose_f64_kernel(const double *__restrict__ X, int64_t ldx, int n,
+                                                           double *__restrict__ XT)
+{
+    __shared__ double t[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int r = ty; r < 32; r += 8) {
+        const int i = bx + tx, j = by + r;
+        t[r][tx] = (i < n && j < n) ? X[i + (int64_t)j * ldx] : 0.0;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int i = by + tx, j = bx + r;  // XT(i, j) = X(j, i)
+        if (i < n && j < n) XT[i + (int64_t)j * n] = t[tx][r];
+    }
+}
+
+int residual_gen_split_parts(int n)
+{
+    if (n <= 0) return 0;
+    const int T = (int)cdiv_i(n, SP_BN);
+    const int mh = (int)cdiv_i(n, 2 * SP_BR) * T >= sm_count() ? 2 : 1;
+    return 4 * (int)cdiv_i(n, mh * SP_BR) * T;
+}
+
+cudaError_t launch_residual_gen_split(const double *A, int64_t lda, const double *X, int64_t ldx, int n, int e,
+                                      float *Rhat, int ldr, double *Racc, double *XT, void *digitsA, void *digitsB,
+                                      int *rhoA, int *rhoB, double *partials, int *nparts, int *err, cudaStream_t s)
+{
+    if (n <= 0) { *nparts = 0; return cudaSuccess; }
+    int b, D;
+    split_plan(n, &b, &D);
+    const int S = D + 1, lds = split_lds(n);
+    if (S > SP_MAXG) return cudaErrorInvalidValue;
+    cudaError_t er;
+    // left operand: the rows of X (columns of X^T); right operand: the
+    // columns of X, so that (X X)(i, j) = sum_k X(i, k) X(k, j) pairs row i
+    // of the one with row j of the other
+    transpose_f64_kernel<<<dim3((unsigned)cdiv_i(n, 32), (unsigned)cdiv_i(n, 32)), 256, 0, s>>>(X, ldx, n, XT);
+    count_launch();
+    __nv_bfloat16 *Xa = (__nv_bfloat16 *)digitsA, *Xb = (__nv_bfloat16 *)digitsB;
+    if ((er = launch_split_rows(XT, n, n, lds, Xa, rhoA, b, S, s))) return er;
+    if ((er = launch_split_rows(X, ldx, n, lds, Xb, rhoB, b, S, s))) return er;
+    CUtensorMap mapA, mapB;
+    if (!make_bf16_map(&mapA, Xa, lds, (int64_t)S * n, lds) || !make_bf16_map(&mapB, Xb, lds, (int64_t)S * n, lds))
+        return cudaErrorInvalidValue;
+    const int T = (int)cdiv_i(n, SP_BN), KT = lds / SP_BK;
+    const int sms = sm_count();
+    const int mh = (int)cdiv_i(n, 2 * SP_BR) * T >= sms ? 2 : 1;
+    const int ntiles = (int)cdiv_i(n, mh * SP_BR) * T;
+    if ((er = allow_max_smem((const void *)split_gemm_kernel<1, true>)) ||
+        (er = allow_max_smem((const void *)split_gemm_kernel<2, true>)))
+        return er;
+    const SplitPlan plan = make_split_plan(n, b, D);
+    const int grid = std::max(1, std::min(ntiles, sms));
+    SplitEpi ep{A, lda, Racc, (int64_t)n, rhoA, rhoB, Rhat, (int64_t)ldr, ldexp(1.0, -2 * e), partials};
+    if (mh == 2) split_gemm_kernel<2, true><<<grid, SP_THREADS, SP_SMEM, s>>>(mapA, mapB, plan, n, KT, T, ntiles, ep, err);
+    else split_gemm_kernel<1, true><<<grid, SP_THREADS, SP_SMEM, s>>>(mapA, mapB, plan, n, KT, T, ntiles, ep, err);
+    count_launch();
+    *nparts = 4 * ntiles;
     return cudaGetLastError();
 }
 

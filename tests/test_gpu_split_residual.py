@@ -99,3 +99,81 @@ def test_spd_sqrtm_with_split_residual(resid):
         X, info = mp.sqrtm_mixed(torch.from_numpy(np.ascontiguousarray(A)).cuda(), steps=k, precision=prec)
         errs.append(oracle.rel_err(X.cpu().numpy(), Xo))
     check_kstar(errs, 1e-13)
+
+
+# ---------------------------------------------------------------------------
+# general X (Algorithm 2, step 4): rows of X against its columns
+# ---------------------------------------------------------------------------
+def _dyadic_gen(n, bits, seed, row_exp=None, col_exp=None):
+    """General X = D_r M D_c / 2^bits with integer M, |M| < 2^bits."""
+    g = np.random.default_rng(seed)
+    X = g.integers(-(2 ** bits) + 1, 2 ** bits, size=(n, n)).astype(np.float64) / 2.0 ** bits
+    if row_exp is not None:
+        X = (2.0 ** row_exp)[:, None] * X
+    if col_exp is not None:
+        X = X * (2.0 ** col_exp)[None, :]
+    return X
+
+
+@pytest.mark.parametrize("n,bits", [(300, 10), (513, 10), (1000, 12), (2200, 12)])
+def test_gen_split_residual_bit_exact_on_dyadic_inputs(n, bits):
+    # every product and partial sum of X X is exact in FP64 and the digit
+    # slices hold every entry of a row (scaled by its row power of two; the
+    # column scalings 1 or 2 add one bit) and of a column exactly, so no
+    # digit pair is left out: the split residual equals the exact one, as
+    # does the FP64 CUDA-core product.  n = 2200 has more 256 x 128 output
+    # tiles than SMs
+    g = np.random.default_rng(n + 5)
+    X = _dyadic_gen(n, bits, seed=n, row_exp=g.integers(0, 2, size=n), col_exp=g.integers(0, 2, size=n))
+    A = X @ X + _dyadic_gen(n, 8, seed=n + 1) / 2.0 ** 12
+    R = A - X @ X  # exact
+    Ad, Xd = dev_cm(A, torch.float64), dev_cm(X, torch.float64)
+    Rs, ns = mp.step_residual_split(Ad, Xd, n, e=0)
+    assert np.array_equal(host_cm(Rs, n), R.astype(np.float32))
+    assert ns == pytest.approx(np.linalg.norm(R), rel=1e-14)
+    Rf, nf = mp.step_residual(Ad, Xd, n, e=0)
+    assert np.array_equal(host_cm(Rf, n), R.astype(np.float32))
+
+
+@pytest.mark.parametrize("n", [256, 777, 2048])
+def test_gen_split_residual_within_fp64_bound(n):
+    # the refinement's cancellation regime for a nonsymmetric iterate:
+    # A = X X + E, E ~ 1e-13, against the oracle's FP64 residual
+    g = np.random.default_rng(11 + n)
+    X = g.standard_normal((n, n)) / np.sqrt(n) + 2.0 * np.eye(n)
+    A = X @ X + g.standard_normal((n, n)) * 1e-13
+    e = 1
+    R_ref = oracle.residual(A, X)[0] * 4.0 ** -e
+    absXX = np.abs(X) @ np.abs(X) * 4.0 ** -e
+    Ad, Xd = dev_cm(A, torch.float64), dev_cm(X, torch.float64)
+    Rs, ns = mp.step_residual_split(Ad, Xd, n, e=e)
+    Rs = host_cm(Rs, n).astype(np.float64)
+    # the split residual and the oracle's each differ from the exact one by
+    # at most about n u (|X| |X|)_ij, plus the FP32 rounding of Rhat
+    bound = 2 * n * U64 * absXX + 2.0 ** -24 * np.abs(R_ref)
+    assert np.all(np.abs(Rs - R_ref) <= 2 * bound)
+    assert ns == pytest.approx(np.linalg.norm(R_ref), rel=1e-3)
+
+
+def test_gen_split_residual_rejects_bad_arguments():
+    Ad = dev_cm(np.eye(8), torch.float64)
+    Rh = torch.empty(64, dtype=torch.float32, device="cuda")
+    # lda < n is argument 3, ldx < n argument 5, n < 0 argument 6
+    assert mp.lib().sqrtm_step_residual_split(mp.handle(), mp._ptr(Ad), 4, mp._ptr(Ad), 8, 8, 0, mp._ptr(Rh), None) == -3
+    assert mp.lib().sqrtm_step_residual_split(mp.handle(), mp._ptr(Ad), 8, mp._ptr(Ad), 4, 8, 0, mp._ptr(Rh), None) == -5
+    assert mp.lib().sqrtm_step_residual_split(mp.handle(), mp._ptr(Ad), 8, mp._ptr(Ad), 8, -1, 0, mp._ptr(Rh), None) == -6
+
+
+def test_general_path_split_and_fp64_residuals_agree():
+    # the general square root at n = 512 with the split residual (the
+    # default from n = 512) and with FP64 products: both within the 1e-12
+    # target of the oracle, and within rounding of each other
+    A = synth.config_general512()
+    At = torch.from_numpy(A).cuda()
+    X1, i1 = mp.sqrtm_mixed(At, kind=mp.KIND_GENERAL, steps=2)
+    X2, i2 = mp.sqrtm_mixed(At, kind=mp.KIND_GENERAL, steps=2, precision=mp.PREC_RESID_FP64)
+    assert i1["status"] == 0 and i2["status"] == 0
+    Xo = oracle.sqrtm_schur(A)
+    X1, X2 = X1.cpu().numpy(), X2.cpu().numpy()
+    assert oracle.rel_err(X1, Xo) <= 1e-12 and oracle.rel_err(X2, Xo) <= 1e-12
+    assert oracle.rel_err(X1, X2) <= 1e-13
