@@ -138,7 +138,7 @@ def _peaks():
 # valid only for the chase kernel's source it was taken with: SHA-256 of
 # qr.cu up to the first kernel after the chase (the deferred-pass kernels and
 # the host code follow it) plus common.cuh, else null.
-CHASE_TRAFFIC = {"sha256": "20cd0cff6df7234391b794f01376aefc8c4f810241929626bbe3c0a88cc225f1", "bytes": 4790528}
+CHASE_TRAFFIC = {"sha256": "af484c6f8a48c62ec6d9e57a494763b1e6ea105e1d09445498dace07e852b690", "bytes": 4245248}
 _CHASE_END = "__global__ void __launch_bounds__(128) qr_build_u_kernel"
 
 
