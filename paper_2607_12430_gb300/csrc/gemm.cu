@@ -12,17 +12,23 @@ namespace sqm {
 
 static constexpr int GB_M = 64, GB_N = 64, GB_K = 16, G_THREADS = 256;
 
-template <class R, int OPA, int OPB, bool AREAL, int EPI>
+// BM x 64 output tiles (BM = 64, or 32 where 64-row tiles would leave SMs
+// idle); thread (tx, ty) owns rows ty RM .. ty RM + RM - 1 and columns
+// 4 tx .. 4 tx + 3.  Every output is accumulated over k in the same order
+// whatever BM, so both tile shapes give identical results.
+template <class R, int OPA, int OPB, bool AREAL, int EPI, int BM = GB_M>
 __global__ void __launch_bounds__(G_THREADS)
 cgemm_kernel(int m, int n, int k, const void *__restrict__ Av, int lda,
              const cplx<R> *__restrict__ B, int ldb, cplx<R> *__restrict__ C, int ldc,
              double *__restrict__ X, int64_t ldx, double scale, const GemmJob<R> *__restrict__ jobs)
 {
-    __shared__ cplx<R> As[GB_K][GB_M + 1];
+    static_assert(BM == 64 || BM == 32, "tile rows");
+    constexpr int RM = BM / 16;  // rows per thread; also A-tile elements per thread
+    __shared__ cplx<R> As[GB_K][BM + 1];
     __shared__ cplx<R> Bs[GB_K][GB_N + 1];
     const int tid = threadIdx.x;
     const int tx = tid % 16, ty = tid / 16;
-    const int m0 = blockIdx.x * GB_M, n0 = blockIdx.y * GB_N;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * GB_N;
     if (jobs) {  // batched: the n x n product of matrix blockIdx.z, scale 2^e
         const GemmJob<R> jb = jobs[blockIdx.z];
         if (!*jb.active) return;
@@ -31,9 +37,9 @@ cgemm_kernel(int m, int n, int k, const void *__restrict__ Av, int lda,
         Av = jb.A; B = jb.B; C = jb.C; X = jb.X; ldx = jb.ldx;
         scale = ldexp(1.0, *jb.e);
     }
-    cplx<R> acc[4][4];
+    cplx<R> acc[RM][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RM; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = cplx<R>{0, 0};
 
@@ -44,8 +50,8 @@ cgemm_kernel(int m, int n, int k, const void *__restrict__ Av, int lda,
         // A tile: op(A)(m0 + i, k0 + kk)
         if (OPA == OP_N) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                int i = tid % GB_M, kk = tid / GB_M + 4 * q;
+            for (int q = 0; q < RM; ++q) {
+                int i = tid % BM, kk = tid / BM + (G_THREADS / BM) * q;
                 int gi = m0 + i, gk = k0 + kk;
                 cplx<R> v{0, 0};
                 if (gi < m && gk < k) {
@@ -56,7 +62,7 @@ cgemm_kernel(int m, int n, int k, const void *__restrict__ Av, int lda,
             }
         } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < RM; ++q) {
                 int kk = tid % GB_K, i = tid / GB_K + 16 * q;
                 int gi = m0 + i, gk = k0 + kk;
                 cplx<R> v{0, 0};
@@ -86,21 +92,21 @@ cgemm_kernel(int m, int n, int k, const void *__restrict__ Av, int lda,
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < GB_K; ++kk) {
-            cplx<R> a[4], b[4];
+            cplx<R> a[RM], b[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+            for (int i = 0; i < RM; ++i) a[i] = As[kk][ty * RM + i];
 #pragma unroll
             for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < RM; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], b[j]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        int gi = m0 + ty * 4 + i;
+    for (int i = 0; i < RM; ++i) {
+        int gi = m0 + ty * RM + i;
         if (gi >= m) continue;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -122,31 +128,31 @@ cgemm_kernel(int m, int n, int k, const void *__restrict__ Av, int lda,
     }
 }
 
-template <class R, int OPA, int OPB, bool AREAL>
+template <class R, int OPA, int OPB, bool AREAL, int BM = GB_M>
 static cudaError_t dispatch_epi(int epi, dim3 g, cudaStream_t s, int m, int n, int k,
                                 const void *A, int lda, const cplx<R> *B, int ldb, cplx<R> *C,
                                 int ldc, double *X, int64_t ldx, double scale, const GemmJob<R> *jobs = nullptr)
 {
     switch (epi) {
     case EPI_STORE:
-        cgemm_kernel<R, OPA, OPB, AREAL, EPI_STORE><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale, jobs); count_launch();
+        cgemm_kernel<R, OPA, OPB, AREAL, EPI_STORE, BM><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale, jobs); count_launch();
         break;
     case EPI_REAL_TO_F64:
-        cgemm_kernel<R, OPA, OPB, AREAL, EPI_REAL_TO_F64><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale, jobs); count_launch();
+        cgemm_kernel<R, OPA, OPB, AREAL, EPI_REAL_TO_F64, BM><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale, jobs); count_launch();
         break;
     case EPI_REAL_ADD_F64:
-        cgemm_kernel<R, OPA, OPB, AREAL, EPI_REAL_ADD_F64><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale, jobs); count_launch();
+        cgemm_kernel<R, OPA, OPB, AREAL, EPI_REAL_ADD_F64, BM><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale, jobs); count_launch();
         break;
     case EPI_CPLX_TO_F64:
         if (AREAL) return cudaErrorInvalidValue;
-        cgemm_kernel<R, OPA, OPB, AREAL, EPI_CPLX_TO_F64><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale, jobs); count_launch();
+        cgemm_kernel<R, OPA, OPB, AREAL, EPI_CPLX_TO_F64, BM><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale, jobs); count_launch();
         break;
     case EPI_CPLX_ADD_F64:
         if (AREAL) return cudaErrorInvalidValue;
-        cgemm_kernel<R, OPA, OPB, AREAL, EPI_CPLX_ADD_F64><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale, jobs); count_launch();
+        cgemm_kernel<R, OPA, OPB, AREAL, EPI_CPLX_ADD_F64, BM><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale, jobs); count_launch();
         break;
     default:
-        cgemm_kernel<R, OPA, OPB, AREAL, EPI_REAL_ADD_F64_T><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale, jobs); count_launch();
+        cgemm_kernel<R, OPA, OPB, AREAL, EPI_REAL_ADD_F64_T, BM><<<g, G_THREADS, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale, jobs); count_launch();
     }
     return cudaGetLastError();
 }
@@ -157,6 +163,31 @@ cudaError_t launch_cgemm(int opA, int opB, int m, int n, int k, const void *A, i
                          double *X, int64_t ldx, double scale, cudaStream_t s)
 {
     if (m <= 0 || n <= 0) return cudaSuccess;
+    // FP32: 32-row tiles where 64-row ones would not give every SM a tile
+    if constexpr (sizeof(R) == 4) {
+        static const int sms = [] {
+            int dev = 0, v = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                v = 0;
+            return v;
+        }();
+        if (sms > 0 && cdiv_i(m, GB_M) * cdiv_i(n, GB_N) < sms) {
+            dim3 g((unsigned)cdiv_i(m, 32), (unsigned)cdiv_i(n, GB_N));
+#define SQM_D(OA, OB, AR) return dispatch_epi<R, OA, OB, AR, 32>(epi, g, s, m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale)
+            if (a_real) {
+                if (opA == OP_N && opB == OP_N) SQM_D(OP_N, OP_N, true);
+                if (opA == OP_N && opB == OP_H) SQM_D(OP_N, OP_H, true);
+                if (opA == OP_H && opB == OP_N) SQM_D(OP_H, OP_N, true);
+                return cudaErrorInvalidValue;
+            }
+            if (opA == OP_N && opB == OP_N) SQM_D(OP_N, OP_N, false);
+            if (opA == OP_N && opB == OP_H) SQM_D(OP_N, OP_H, false);
+            if (opA == OP_H && opB == OP_N) SQM_D(OP_H, OP_N, false);
+            SQM_D(OP_H, OP_H, false);
+#undef SQM_D
+        }
+    }
     dim3 g((unsigned)cdiv_i(m, GB_M), (unsigned)cdiv_i(n, GB_N));
 #define SQM_D(OA, OB, AR) return dispatch_epi<R, OA, OB, AR>(epi, g, s, m, n, k, A, lda, B, ldb, C, ldc, X, ldx, scale)
     if (a_real) {

@@ -1087,10 +1087,16 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
                     const int k = lo + t - 3 * g;
                     const bool act = g < nb && k >= lo && k < hi;  // uniform per half-warp
                     const int kk = k - r0;
-                    // left rotation of rows kk, kk+1 from column cstart on; the
-                    // half's lane 0 holds x and y in its first column
+                    // left rotation of rows kk, kk+1 from column cstart on; x and y
+                    // (their entries in column cstart) are read by every lane of the
+                    // half at once, off the critical path of the row loads
                     const int cstart = (k == lo) ? kk : kk - 1;
                     const int ni = act ? (bw - cstart + 15) >> 4 : 0;
+                    cplx<R> x{1, 0}, y{0, 0};
+                    if (act) {
+                        x = blk[kk + cstart * BLD];
+                        y = blk[(kk + 1) + cstart * BLD];
+                    }
                     cplx<R> p[NI], q[NI];
 #pragma unroll
                     for (int i = 0; i < NI; ++i) {
@@ -1103,8 +1109,6 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
                             q[i] = cplx<R>{0, 0};
                         }
                     }
-                    cplx<R> x{__shfl_sync(0xffffffffu, p[0].x, 0, 16), __shfl_sync(0xffffffffu, p[0].y, 0, 16)};
-                    const cplx<R> y{__shfl_sync(0xffffffffu, q[0].x, 0, 16), __shfl_sync(0xffffffffu, q[0].y, 0, 16)};
                     if (act && k == lo) x = x - s_mu[g];
                     R c = R(1);
                     cplx<R> s{0, 0}, r{0, 0};
