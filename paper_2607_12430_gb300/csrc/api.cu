@@ -535,11 +535,11 @@ static int general_path(sqrtm_handle_t h, const double *dA, int64_t n, int64_t l
         cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]); info->ms_schur = ms;
         cudaEventElapsedTime(&ms, h->ev[1], h->ev[2]); info->ms_trisqrt = ms;
         cudaEventElapsedTime(&ms, h->ev[0], ev_red); info->ms_reduction = ms;
-        int cnt[5];
+        int cnt[7];  // [5..6]: the small blocks solved by qr_tiny_kernel
         SQM_CU(cudaMemcpy(cnt, sc.st_schur + 3, sizeof(cnt), cudaMemcpyDeviceToHost));
-        info->schur_sweeps = cnt[0];
-        info->schur_rotations = (int64_t)cnt[1] + ((int64_t)cnt[2] << 31);
-        info->schur_work = (int64_t)cnt[3] + ((int64_t)cnt[4] << 31);
+        info->schur_sweeps = cnt[0] + cnt[5];
+        info->schur_rotations = (int64_t)cnt[1] + ((int64_t)cnt[2] << 31) + cnt[6];
+        info->schur_work = (int64_t)cnt[3] + ((int64_t)cnt[4] << 31);  // the chase kernel's own
         info->ms_qr_chase = ms_chase;
     }
     cudaEventDestroy(ev_red);

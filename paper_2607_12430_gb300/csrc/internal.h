@@ -62,7 +62,9 @@ struct SchurDesc {
     cplx<R> *v;      // scratch: Householder vector (>= n entries)
     R *beta;         // scratch: reflector scalars [beta, |x|, phase.x, phase.y]
     int *status;     // out: 0 / 3 (iteration cap)
-    int *counters;   // out: [0] sweeps, [1..2] rotations, [3..4] in-block rotation work (int64s split lo/hi)
+    int *counters;   // out (7 ints): [0] sweeps, [1..2] rotations, [3..4] the chase kernel's in-block
+                     // rotation work (int64s split lo/hi); cooperative chase: [5] sweeps and [6]
+                     // rotations of the small blocks qr_tiny_kernel solves
     int n;
     int ld;
     // limit of each bounded wait between the CTAs of the cooperative chase,
