@@ -37,10 +37,11 @@
 //    shift after every 10 sweeps without deflation; at most kItMax sweeps
 //    per eigenvalue (status 3).
 //  * An active block of at most kQrTiny rows gets its whole Schur form from
-//    one warp, recorded as a window with a dense U.  The cooperative chase
-//    only records such a block and goes on with the blocks above it; after
-//    the launch, qr_tiny_kernel solves every recorded block (one warp each,
-//    concurrently with the next round's chase) before the deferred passes.
+//    one warp, recorded as a window with a dense U.  The chase only records
+//    such a block and goes on with the blocks above it; after the launch,
+//    qr_tiny_kernel solves every recorded block (one warp each; for one
+//    matrix concurrently with the next round's chase) before the deferred
+//    passes.
 #include <algorithm>
 
 #include "internal.h"
@@ -959,71 +960,30 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
         __syncthreads();
         if (s_stop || s_status) break;
         if (s_tiny) {
-            // a small active block: its whole Schur form by one warp, recorded
-            // as one window with a dense U
+            // a small active block: only recorded here, as one window with a
+            // dense U (pad = 1; nb = number of shift estimates, the last
+            // sweep's shifts, stored at the window's log entries);
+            // qr_tiny_kernel gives it its whole Schur form after this launch,
+            // before the deferred passes, while the chase goes on with the
+            // blocks above (in the cooperative chase the helpers are done with
+            // every window that touched it: they were waited for at the end of
+            // the sweep that split it off)
             const int m = hi - lo + 1;
-            if (HELP) {
-                // cooperative chase: only recorded here (pad = 1, nb = number of
-                // shift estimates stored at the window's log entries);
-                // qr_tiny_kernel solves it after this launch, before the
-                // deferred passes, while the chase goes on with the blocks above
-                // (helpers are done with every window that touched it: they were
-                // waited for at the end of the sweep that split it off)
-                const int nc = s_prevn;
-                if (tid < nc) d.log[s_nlog + tid] = RotLog<R>{R(0), s_prev[tid].x, s_prev[tid].y, R(0)};
-                if (tid == 0) {
-                    WinRec wr;
-                    wr.start = s_nlog; wr.kbase = lo; wr.nsteps = -1; wr.kmin = lo; wr.rr = m;
-                    wr.lo = lo; wr.hi = hi; wr.t0 = 0; wr.nb = nc; wr.r0 = lo; wr.rnext = hi; wr.pad = 1;
-                    wr.uoff = s_uoff;
-                    d.win[s_nwin] = wr;
-                    s_nwin += 1;
-                    s_uoff += (long long)m * m;
-                    s_nlog += NB;
-                    s_hi = lo - 1;
-                    s_iter = 0;
-                }
-                __syncthreads();
-                continue;
-            }
-            cplx<R> *Mb = blk, *Ub = tile;  // ld kQrTinyLd
-            for (int e = tid; e < m * m; e += nt) {
-                const int a = e % m, b = e / m;
-                Mb[a + b * kQrTinyLd] = ldT((lo + a) + (int64_t)(lo + b) * ld);
-                Ub[a + b * kQrTinyLd] = cplx<R>{(R)(a == b), R(0)};
-            }
-            __syncthreads();
-            if (warp == 0) {
-                int nsw = 0, nrot = 0;
-                const bool ok = warp_tiny_schur<R, kQrTinyLd>(Mb, Ub, m, &nsw, &nrot, s_prev, s_prevn);
-                if (lane == 0) {
-                    if (!ok) s_status = 3;
-                    s_sweeps += nsw;
-                    s_rots += nrot;
-                    s_work += (long long)nrot * m;
-                }
-            }
-            __syncthreads();
-            cplx<R> *U = d.ubuf + s_uoff;
-            for (int e = tid; e < m * m; e += nt) {
-                const int a = e % m, b = e / m;
-                T[(lo + a) + (int64_t)(lo + b) * ld] = Mb[a + b * kQrTinyLd];
-                U[a + b * m] = Ub[a + b * kQrTinyLd];
-            }
+            const int nc = s_prevn;
+            if (tid < nc) d.log[s_nlog + tid] = RotLog<R>{R(0), s_prev[tid].x, s_prev[tid].y, R(0)};
             if (tid == 0) {
                 WinRec wr;
                 wr.start = s_nlog; wr.kbase = lo; wr.nsteps = -1; wr.kmin = lo; wr.rr = m;
-                wr.lo = lo; wr.hi = hi; wr.t0 = 0; wr.nb = 0; wr.r0 = lo; wr.rnext = hi; wr.pad = 0;
+                wr.lo = lo; wr.hi = hi; wr.t0 = 0; wr.nb = nc; wr.r0 = lo; wr.rnext = hi; wr.pad = 1;
                 wr.uoff = s_uoff;
                 d.win[s_nwin] = wr;
                 s_nwin += 1;
                 s_uoff += (long long)m * m;
+                s_nlog += NB;
                 s_hi = lo - 1;
                 s_iter = 0;
             }
-            if (HELP) __threadfence();
             __syncthreads();
-            if (s_status) break;
             continue;
         }
         const int nb = s_nb;
@@ -1349,59 +1309,61 @@ qr_chase_kernel(const SchurDesc<R> *__restrict__ descs, int H)
     }
 }
 
-// The small active blocks that the cooperative chase recorded without
-// solving them (window records with nsteps < 0 and pad = 1): the complete
-// Schur form of each by one warp (the same one-warp iteration the chase
-// uses inline), written back into T, with its accumulated rotations as the
-// window's dense U.  Launched after the chase launch that recorded them and
-// before the deferred passes that apply those U.  A recorded block [lo, hi]
-// is final when it is recorded, and nothing the chase does afterwards
-// reaches inside it: the later active blocks lie above it, their in-window
-// and helper updates stay within them, and their out-of-block updates are
-// the deferred passes, which touch T only in rows above lo or columns right
-// of a window's hi; rows above lo in columns lo..hi receive both this
-// block's right rotations and the later windows' left rotations, which
-// commute.  One CTA of one warp per window record of the round.
+// The small active blocks that the chase recorded without solving them
+// (window records with nsteps < 0 and pad = 1): the complete Schur form of
+// each by one warp, written back into T, with its accumulated rotations as
+// the window's dense U.  Launched after the chase launch that recorded them
+// and before the deferred passes that apply those U.  A recorded block
+// [lo, hi] is final when it is recorded, and nothing the chase does
+// afterwards reaches inside it: the later active blocks lie above it, their
+// in-window and helper updates stay within them, and their out-of-block
+// updates are the deferred passes, which touch T only in rows above lo or
+// columns right of a window's hi; rows above lo in columns lo..hi receive
+// both this block's right rotations and the later windows' left rotations,
+// which commute.  CTAs of one warp, each taking the window records
+// blockIdx.x, blockIdx.x + gridDim.x, ... of the round.
 template <class R>
 __global__ void __launch_bounds__(32) qr_tiny_kernel(const SchurDesc<R> *__restrict__ descs)
 {
     constexpr int NB = QrCfg<R>::NB;
     __shared__ cplx<R> M[kQrTiny * kQrTinyLd], U[kQrTiny * kQrTinyLd], cand[NB];
     const SchurDesc<R> d = descs[blockIdx.y];
-    const int wi = blockIdx.x;
-    if (wi >= d.rstate[0]) return;
-    const WinRec w = d.win[wi];
-    if (w.nsteps >= 0 || w.pad != 1) return;
-    const int m = w.rr, lo = w.lo, ld = d.ld, lane = threadIdx.x;
-    if (m < 1 || m > kQrTiny || lo < 0 || lo + m > d.n) {
-        if (lane == 0) atomicExch(d.status, 7);
-        return;
-    }
-    for (int e = lane; e < m * m; e += 32) {
-        const int a = e % m, b = e / m;
-        M[a + b * kQrTinyLd] = d.T[(lo + a) + (int64_t)(lo + b) * ld];
-        U[a + b * kQrTinyLd] = cplx<R>{(R)(a == b), R(0)};
-    }
-    const int nc = min(max(w.nb, 0), NB);
-    if (lane < nc) {
-        const RotLog<R> e = d.log[w.start + lane];
-        cand[lane] = cplx<R>{e.sx, e.sy};
-    }
-    __syncwarp();
-    int nsw = 0, nrot = 0;
-    const bool ok = warp_tiny_schur<R, kQrTinyLd>(M, U, m, &nsw, &nrot, cand, nc);
-    __syncwarp();
-    cplx<R> *Ug = d.ubuf + w.uoff;
-    for (int e = lane; e < m * m; e += 32) {
-        const int a = e % m, b = e / m;
-        d.T[(lo + a) + (int64_t)(lo + b) * ld] = M[a + b * kQrTinyLd];
-        Ug[a + b * m] = U[a + b * kQrTinyLd];
-    }
-    if (lane == 0) {
-        if (!ok) atomicExch(d.status, 3);
-        if (d.counters) {
-            atomicAdd(&d.counters[5], nsw);
-            atomicAdd(&d.counters[6], nrot);
+    const int nwin = d.rstate[0], ld = d.ld, lane = threadIdx.x;
+    for (int wi = blockIdx.x; wi < nwin; wi += gridDim.x) {
+        const WinRec w = d.win[wi];
+        if (w.nsteps >= 0 || w.pad != 1) continue;
+        const int m = w.rr, lo = w.lo;
+        if (m < 1 || m > kQrTiny || lo < 0 || lo + m > d.n) {
+            if (lane == 0) atomicExch(d.status, 7);
+            continue;
+        }
+        __syncwarp();  // the previous block's shared-memory reads are done
+        for (int e = lane; e < m * m; e += 32) {
+            const int a = e % m, b = e / m;
+            M[a + b * kQrTinyLd] = d.T[(lo + a) + (int64_t)(lo + b) * ld];
+            U[a + b * kQrTinyLd] = cplx<R>{(R)(a == b), R(0)};
+        }
+        const int nc = min(max(w.nb, 0), NB);
+        if (lane < nc) {
+            const RotLog<R> e = d.log[w.start + lane];
+            cand[lane] = cplx<R>{e.sx, e.sy};
+        }
+        __syncwarp();
+        int nsw = 0, nrot = 0;
+        const bool ok = warp_tiny_schur<R, kQrTinyLd>(M, U, m, &nsw, &nrot, cand, nc);
+        __syncwarp();
+        cplx<R> *Ug = d.ubuf + w.uoff;
+        for (int e = lane; e < m * m; e += 32) {
+            const int a = e % m, b = e / m;
+            d.T[(lo + a) + (int64_t)(lo + b) * ld] = M[a + b * kQrTinyLd];
+            Ug[a + b * m] = U[a + b * kQrTinyLd];
+        }
+        if (lane == 0) {
+            if (!ok) atomicExch(d.status, 3);
+            if (d.counters) {
+                atomicAdd(&d.counters[5], nsw);
+                atomicAdd(&d.counters[6], nrot);
+            }
         }
     }
 }
@@ -1747,7 +1709,7 @@ cudaError_t launch_qr_sweeps(const SchurDesc<R> *d_desc, int batch, int nmax, in
                 if ((err = cudaEventRecord(qev[par], s)) || (err = cudaStreamWaitEvent(side, qev[par], 0))) break;
                 ds = side;
             }
-            if (coop) { qr_tiny_kernel<R><<<dim3(maxwin, batch), 32, 0, ds>>>(dd); count_launch(); }
+            qr_tiny_kernel<R><<<dim3(maxwin, batch), 32, 0, ds>>>(dd); count_launch();
             qr_build_u_kernel<R><<<dim3(maxwin, batch), 128, QrDims<R>::build_smem, ds>>>(dd); count_launch();
             qr_apply_rows_kernel<R><<<dim3(2 * ctas, batch), 256, rows_bytes, ds>>>(dd, rpc, ctas); count_launch();
             qr_apply_cols_kernel<R><<<dim3(ctas, batch), 256, cols_bytes, ds>>>(dd, rpc); count_launch();
@@ -1818,6 +1780,8 @@ cudaError_t enqueue_round(void *p, cudaStream_t s, cudaGraphConditionalHandle co
     // windows of a round: at most the window capacity of the largest matrix
     const int ubx = (int)std::min<int64_t>(qr_win_capacity(c->nmax), 64);
     qr_chase_kernel<R, false><<<c->batch, kQrThreads, QrDims<R>::chase_smem, s>>>(c->desc, 0); count_launch();
+    // (a few small blocks per matrix and round: 8 CTAs per matrix stride over its windows)
+    qr_tiny_kernel<R><<<dim3(std::min(ubx, 8), c->batch), 32, 0, s>>>(c->desc); count_launch();
     qr_build_u_kernel<R><<<dim3(ubx, c->batch), 128, QrDims<R>::build_smem, s>>>(c->desc); count_launch();
     qr_apply_rows_kernel<R><<<dim3(2 * ctas, c->batch), 256, rows_bytes, s>>>(c->desc, rpc, ctas); count_launch();
     qr_apply_cols_kernel<R><<<dim3(ctas, c->batch), 256, cols_bytes, s>>>(c->desc, rpc); count_launch();
