@@ -34,12 +34,14 @@ struct alignas(16) RotLog {
 // acts on indices kbase + q + 3 (NB - 1 - g) and the next one), nsteps steps
 // are used, all rotations act on indices kmin .. kmin + rr - 1, the sweep's
 // active block is [lo, hi], and the window's accumulated rotation product U
-// (rr x rr) is stored at ubuf + uoff.
+// (rr x rr) is stored at ubuf + uoff.  A small active block [lo, hi] recorded
+// for qr_tiny_kernel has nsteps = -1, kmin = lo, rr = hi - lo + 1, pad = 1
+// and nb shift estimates (sx, sy) at log entries start .. start + nb - 1.
 struct WinRec {
     int start, kbase, nsteps, kmin, rr, lo, hi;
     int t0, nb;      // first step of the window within its sweep; bulges of the sweep
     int r0, rnext;   // first row of the window block; last column of the next window's block
-    int pad;
+    int pad;         // 1: a small block for qr_tiny_kernel
     long long uoff;
 };
 

@@ -1387,7 +1387,7 @@ __global__ void __launch_bounds__(128) qr_build_u_kernel(const SchurDesc<R> *__r
     for (int wi = blockIdx.x; wi < nwin; wi += gridDim.x) {
     __syncthreads();  // the previous window's shared-memory reads are done
     const WinRec w = d.win[wi];
-    if (w.nsteps < 0) continue;  // dense window: U written by the chase
+    if (w.nsteps < 0) continue;  // a small block: U written by qr_tiny_kernel
     const int rr = w.rr, r = threadIdx.x;
     if (rr > D::RR || rr < 2) {
         if (r == 0) atomicExch(d.status, 7);
