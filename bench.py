@@ -284,7 +284,7 @@ def leg_c3(args, mp, torch, flush, peaks):
                          "note": "algorithmic 4n^3/3 B per decomposition over the library's CUDA-event time of "
                                  "the reduction phase; peak: measured HBM copy bandwidth (the trailing block "
                                  "is L2-resident: each step's column phase is bound by L2 bandwidth, the rest "
-                                 "is the per-step prologue and launch gap, profiles/tri_step_spd4096.md)"},
+                                 "is the per-step prologue and launch gap)"},
             "input_prep_s": gen_s}
 
 
