@@ -40,3 +40,34 @@ def test_replicas_share_kstar_and_report_slowest_rank():
             p.join(120)
             assert p.exitcode == 0
         assert dict(out) == {0: (2, 5.5), 1: (2, 5.5)}
+
+
+def test_chase_traffic_only_for_the_source_it_was_measured_on(monkeypatch):
+    # the stored DRAM traffic of the chase kernel is reported for the qr.cu
+    # it was captured with and dropped (null) as soon as the chase's source
+    # differs by a byte
+    import builtins
+
+    import bench
+    assert bench._chase_traffic() == bench.CHASE_TRAFFIC["bytes"]
+    real_open = builtins.open
+
+    class _Edited:
+        def __init__(self, f):
+            self._f = f
+
+        def read(self):
+            return self._f.read().replace("chase", "chasE", 1)
+
+        def __enter__(self):
+            return self
+
+        def __exit__(self, *a):
+            self._f.close()
+
+    def fake_open(path, *a, **k):
+        f = real_open(path, *a, **k)
+        return _Edited(f) if str(path).endswith("qr.cu") else f
+
+    monkeypatch.setattr(builtins, "open", fake_open)
+    assert bench._chase_traffic() is None
